@@ -1,0 +1,207 @@
+/*
+ * pic_poisson -- batched Fourier-mode multigrid field solve for a cylindrical
+ * electrostatic particle-in-cell method, on one GB300 (sm_103a).
+ *
+ * The solve (Sec. 3 "Exact Fourier-mode decomposition and batched
+ * matrix-free multigrid"):
+ *   1. a real DFT of the cell-centred charge density along the periodic
+ *      azimuthal coordinate (Eq. azimuthal_dft, forward scale 1/N_theta),
+ *      giving N_m = N_theta/2 + 1 complex modes (Sec. 3.1, last paragraph);
+ *   2. for every mode m the shifted real operator A_m = A_0 + lambda_m M
+ *      (Eqs. matrix_free_mode_operator, shifted_operator_family) with the
+ *      exact discrete eigenvalue lambda_m = 4 sin^2(pi m / N_theta) / dalpha^2
+ *      (Eq. discrete_azimuthal_eigenvalue), right-hand side
+ *      b = s rho_hat + b^D delta_m0 (Eq. mode_rhs), solved for all modes
+ *      together by matrix-free geometric multigrid V-cycles (Sec. 3.3);
+ *   3. the inverse transform phi_j = sum_m phi_hat_m e^{i theta_m j}, no scale
+ *      (Sec. 3.1, inverse transform).
+ *
+ * Geometry: a rectangular annular r-z cross-section with uniform spacing,
+ * r in [r_in, r_out] (r_in > 0), z in [z0, z1], theta periodic over
+ * theta_span.  Walls carry azimuthally invariant Dirichlet potentials; the
+ * face conductances are those of the appendix (Eqs.
+ * interior_face_conductances, dirichlet_face_conductances).
+ *
+ * Memory: every pointer argument named *_dev is caller-owned device memory
+ * (for example a PyTorch tensor's data_ptr()); the library never frees it.
+ * Real 3-D arrays are contiguous FP64, shape (nz, ntheta, nr), r fastest.
+ * Mode-space arrays ("mode layout") are contiguous interleaved complex FP64,
+ * element (k, i, m) at double offset 2*((k*nr + i)*N_m + m) (+0 real,
+ * +1 imaginary): cell-major, mode-fast (Eq. mode_fast_layout with the mode
+ * extent unpadded).  A plan owns its workspace (level vectors, coefficient
+ * tables, coarse-grid factors), allocated at plan time with cudaMalloc and
+ * released by pic_poisson_destroy.  All work is enqueued on the plan's
+ * stream; functions that return a result to the host synchronise that stream.
+ *
+ * Errors: every function returns a PIC_POISSON_* status; no call aborts or
+ * traps on the device.  pic_poisson_last_error() describes the most recent
+ * failure on the calling thread.
+ */
+#ifndef PIC_POISSON_H
+#define PIC_POISSON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_POISSON_OK 0
+#define PIC_POISSON_EINVAL 1          /* bad descriptor, size or argument */
+#define PIC_POISSON_ENOMEM 2          /* device or host allocation failed */
+#define PIC_POISSON_ECUDA 3           /* a CUDA call failed (see last_error) */
+#define PIC_POISSON_ENOTCONVERGED 4   /* tolerance not met in max_cycles; phi holds the last iterate */
+#define PIC_POISSON_ENONFINITE 5      /* non-finite right-hand side or residual */
+
+/* precision */
+#define PIC_POISSON_FP64 0            /* every V-cycle in FP64 */
+#define PIC_POISSON_MIXED 1           /* FP32 V-cycles inside an FP64 defect-correction loop */
+
+/* flags */
+#define PIC_POISSON_USE_INITIAL_GUESS 1u  /* phi_dev is read as the initial iterate */
+#define PIC_POISSON_PROFILE 2u            /* time every kernel class with CUDA events */
+
+/* kernel classes, indices into pic_poisson_info.ms_phase / launches_phase */
+#define PIC_POISSON_PHASE_FORWARD 0   /* azimuthal rFFT + right-hand side */
+#define PIC_POISSON_PHASE_SMOOTH 1    /* red-black Gauss-Seidel half-sweeps */
+#define PIC_POISSON_PHASE_RESTRICT 2  /* residual + restriction (+ norm partials) */
+#define PIC_POISSON_PHASE_COARSE 3    /* coarsest-level direct solve */
+#define PIC_POISSON_PHASE_PROLONG 4   /* prolongation + correction */
+#define PIC_POISSON_PHASE_NORM 5      /* norm reductions */
+#define PIC_POISSON_PHASE_INVERSE 6   /* inverse azimuthal transform */
+#define PIC_POISSON_PHASE_DEFECT 7    /* FP64 defect / update of the mixed loop */
+#define PIC_POISSON_NPHASE 8
+
+#define PIC_POISSON_MAX_LEVELS 16
+
+typedef struct pic_poisson_plan_s *pic_poisson_plan_t;
+
+typedef struct {
+    int nr, ntheta, nz;        /* cells; ntheta a power of two in [2, 1024] */
+    double r_in, r_out;        /* radial walls, 0 < r_in < r_out */
+    double z0, z1;             /* axial walls, z0 < z1 */
+    double theta_span;         /* azimuthal period; <= 0 selects 2*pi */
+    double phi_r_in, phi_r_out;/* Dirichlet potential on the r walls (used when the arrays below are NULL) */
+    double phi_z0, phi_z1;     /* Dirichlet potential on the z walls */
+    const double *phi_r_in_z;  /* host, nz values or NULL: inner r-wall potential per axial cell */
+    const double *phi_r_out_z; /* host, nz values or NULL: outer r-wall potential per axial cell */
+    double eps0;               /* vacuum permittivity; <= 0 selects 8.8541878128e-12 F/m */
+    int precision;             /* PIC_POISSON_FP64 or PIC_POISSON_MIXED */
+    int max_cycles;            /* V-cycle cap; <= 0 selects 200 */
+    int pre_sweeps;            /* red-black sweeps before restriction; < 0 selects 2 */
+    int post_sweeps;           /* red-black sweeps after prolongation; < 0 selects 2 */
+    unsigned flags;            /* PIC_POISSON_* flags */
+} pic_poisson_desc;
+
+typedef struct {
+    int status;                /* return code of the call */
+    int cycles;                /* coarse-grid corrections applied */
+    int outer_iterations;      /* FP64 defect corrections (mixed precision) */
+    int launches;              /* kernels this call launched */
+    double rel_res0;           /* ||b - A phi_0|| / ||b|| of the initial iterate */
+    double rel_res;            /* ||b - A phi|| / ||b|| of the returned iterate (3-D system, Parseval) */
+    double ms_phase[PIC_POISSON_NPHASE];   /* device ms per kernel class (PROFILE flag) */
+    int launches_phase[PIC_POISSON_NPHASE];/* launches per kernel class */
+} pic_poisson_info;
+
+typedef struct {
+    int levels;                            /* multigrid levels (1 = direct solve only) */
+    int nr[PIC_POISSON_MAX_LEVELS];        /* cells per level */
+    int nz[PIC_POISSON_MAX_LEVELS];
+    int n_modes;                           /* N_theta / 2 + 1 */
+    size_t workspace_bytes;                /* device bytes a plan allocates */
+} pic_poisson_layout;
+
+/*
+ * Validate `desc` and describe the plan it would build (levels, sizes,
+ * workspace).  Host only: touches no GPU.  2:1 coarsening in r and z while
+ * both counts are even and at least 8 (Sec. 3.2 shared hierarchy); the
+ * coarsest level is solved directly.  Returns PIC_POISSON_EINVAL for an
+ * invalid descriptor.
+ */
+int pic_poisson_query(const pic_poisson_desc *desc, pic_poisson_layout *out);
+
+/*
+ * Level-0 coefficients of r-z cell (i, k) as the library computes them:
+ * out[0..3] = conductance of the r-, r+, z-, z+ faces (Dirichlet faces use the
+ * half-cell distance, appendix Eq. dirichlet_face_conductances),
+ * out[4..7] = 1 for a Dirichlet face, else 0, out[8] = mu (Eq.
+ * mode_mass_coefficient), out[9] = s (Eq. mode_rhs), out[10] = D0 (Eq.
+ * base_diagonal_with_boundary), out[11] = b^D (Eq. boundary_rhs_appendix).
+ * Host only.  `out` holds 12 doubles.
+ */
+int pic_poisson_cell_coeffs(const pic_poisson_desc *desc, int i, int k, double *out);
+
+/*
+ * Build a plan: coefficient tables for every level, coarsest-level factors,
+ * workspace.  `stream` is a cudaStream_t (NULL = legacy default stream) on
+ * which all of the plan's work is enqueued.  On success *out owns the plan.
+ */
+int pic_poisson_plan(const pic_poisson_desc *desc, void *stream, pic_poisson_plan_t *out);
+
+/* Replace the plan's stream (later calls enqueue there). */
+int pic_poisson_set_stream(pic_poisson_plan_t plan, void *stream);
+
+/*
+ * Full solve: rho_dev (nz, ntheta, nr) FP64 charge density -> phi_dev (same
+ * shape) FP64 potential.  V-cycles run until the relative residual of the
+ * three-dimensional system, ||b - A phi||_2 / ||b||_2, is <= tol (tol <= 0:
+ * until the residual stops decreasing, the rounding floor).  The residual is
+ * measured in mode space with Parseval weights 1 (m = 0, N/2) and 2 (others).
+ * Synchronises the plan's stream once per cycle to test convergence.
+ * rho_dev and phi_dev may not alias.  `info` may be NULL.
+ */
+int pic_poisson_solve(pic_poisson_plan_t plan, const double *rho_dev, double *phi_dev, double tol,
+                      pic_poisson_info *info);
+
+/*
+ * As pic_poisson_solve with host buffers (pinned or pageable): copies rho_host
+ * to the device, solves, copies phi back; returns after phi_host is written.
+ * The device staging buffers are part of the plan's workspace (allocated on
+ * first use).
+ */
+int pic_poisson_solve_host(pic_poisson_plan_t plan, const double *rho_host, double *phi_host, double tol,
+                           pic_poisson_info *info);
+
+/*
+ * Step a-1 alone: bhat_dev (mode layout) = s * rho_hat + b^D delta_m0 where
+ * rho_hat is the forward DFT of rho_dev along theta with scale 1/N_theta
+ * (Eqs. azimuthal_dft, mode_rhs).  Imaginary parts of m = 0 and m = N/2 are
+ * written as exactly 0.
+ */
+int pic_poisson_forward(pic_poisson_plan_t plan, const double *rho_dev, double *bhat_dev);
+
+/*
+ * Step a-8 alone: phi_dev (nz, ntheta, nr) = sum over all N_theta modes of
+ * phihat_m e^{i theta_m j}, using conjugate symmetry for m > N/2 and the real
+ * parts of m = 0 and m = N/2 (Sec. 3.1, inverse transform; no scale).
+ */
+int pic_poisson_inverse(pic_poisson_plan_t plan, const double *phihat_dev, double *phi_dev);
+
+/*
+ * Mode-space residual: rhat_dev = bhat_dev - A_m uhat_dev for every mode
+ * (Eq. matrix_free_mode_operator) and, if rel_res is non-NULL, the
+ * Parseval-weighted ||r|| / ||b|| written to *rel_res (synchronises).
+ * rhat_dev may be NULL when only the norm is wanted.
+ */
+int pic_poisson_mode_residual(pic_poisson_plan_t plan, const double *uhat_dev, const double *bhat_dev,
+                              double *rhat_dev, double *rel_res);
+
+/* Release everything the plan owns.  NULL is accepted. */
+int pic_poisson_destroy(pic_poisson_plan_t plan);
+
+/* Description of the most recent failure on this thread ("" if none). */
+const char *pic_poisson_last_error(void);
+
+/*
+ * Measure this GPU's FP64 and FP32 fused-multiply-add throughput (GFLOP/s,
+ * 2 flops per FMA) with a register-resident kernel on `stream`: the ALU
+ * roofline denominators for FP64-bound kernels.  Synchronises the stream.
+ */
+int pic_poisson_measure_fma_peaks(void *stream, double *fp64_gflops, double *fp32_gflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_POISSON_H */

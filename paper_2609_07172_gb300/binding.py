@@ -1,0 +1,276 @@
+"""ctypes binding of the pic_poisson C ABI (include/pic_poisson.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Device buffers are PyTorch CUDA tensors (their data_ptr() and the
+current stream are handed to the library).  If the shared library is missing
+this module raises instead of falling back to any other implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE = 0, 1, 2, 3, 4, 5
+FP64, MIXED = 0, 1
+USE_INITIAL_GUESS, PROFILE = 1, 2
+PHASES = ("forward", "smooth", "restrict", "coarse", "prolong", "norm", "inverse", "defect")
+MAX_LEVELS = 16
+NPHASE = len(PHASES)
+
+EXPORTS = (
+    "pic_poisson_query", "pic_poisson_cell_coeffs", "pic_poisson_plan", "pic_poisson_set_stream",
+    "pic_poisson_solve", "pic_poisson_solve_host", "pic_poisson_forward", "pic_poisson_inverse",
+    "pic_poisson_mode_residual", "pic_poisson_destroy", "pic_poisson_last_error",
+    "pic_poisson_measure_fma_peaks",
+)
+
+
+class PicPoissonError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"pic_poisson status {status}: {msg}")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [
+        ("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("nz", ctypes.c_int),
+        ("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
+        ("z0", ctypes.c_double), ("z1", ctypes.c_double),
+        ("theta_span", ctypes.c_double),
+        ("phi_r_in", ctypes.c_double), ("phi_r_out", ctypes.c_double),
+        ("phi_z0", ctypes.c_double), ("phi_z1", ctypes.c_double),
+        ("phi_r_in_z", ctypes.c_void_p), ("phi_r_out_z", ctypes.c_void_p),
+        ("eps0", ctypes.c_double),
+        ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
+        ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int),
+        ("flags", ctypes.c_uint),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("cycles", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+        ("launches", ctypes.c_int),
+        ("rel_res0", ctypes.c_double), ("rel_res", ctypes.c_double),
+        ("ms_phase", ctypes.c_double * NPHASE), ("launches_phase", ctypes.c_int * NPHASE),
+    ]
+
+    def as_dict(self):
+        return {
+            "status": self.status, "cycles": self.cycles, "outer_iterations": self.outer_iterations,
+            "launches": self.launches, "rel_res0": self.rel_res0, "rel_res": self.rel_res,
+            "ms_phase": {p: self.ms_phase[i] for i, p in enumerate(PHASES)},
+            "launches_phase": {p: self.launches_phase[i] for i, p in enumerate(PHASES)},
+        }
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int), ("nr", ctypes.c_int * MAX_LEVELS), ("nz", ctypes.c_int * MAX_LEVELS),
+        ("n_modes", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the shared library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        try:
+            path = _build.build()
+        except RuntimeError:
+            if not os.path.exists(path):
+                raise
+    if not os.path.exists(path):
+        raise RuntimeError(f"pic_poisson library not built: {path} is missing")
+    lib = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    sig = {
+        "pic_poisson_query": ([vp, vp], ip),
+        "pic_poisson_cell_coeffs": ([vp, ip, ip, vp], ip),
+        "pic_poisson_plan": ([vp, vp, vp], ip),
+        "pic_poisson_set_stream": ([vp, vp], ip),
+        "pic_poisson_solve": ([vp, vp, vp, dp, vp], ip),
+        "pic_poisson_solve_host": ([vp, vp, vp, dp, vp], ip),
+        "pic_poisson_forward": ([vp, vp, vp], ip),
+        "pic_poisson_inverse": ([vp, vp, vp], ip),
+        "pic_poisson_mode_residual": ([vp, vp, vp, vp, vp], ip),
+        "pic_poisson_destroy": ([vp], ip),
+        "pic_poisson_last_error": ([], ctypes.c_char_p),
+        "pic_poisson_measure_fma_peaks": ([vp, vp, vp], ip),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().pic_poisson_last_error().decode()
+
+
+def _check(status, allow=(OK,)):
+    if status not in allow:
+        raise PicPoissonError(status, last_error())
+    return status
+
+
+def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1, flags=0):
+    """Descriptor for a workloads.Problem; returns (Desc, keep-alive buffers)."""
+    keep = []
+    d = Desc()
+    d.nr, d.ntheta, d.nz = problem.nr, problem.ntheta, problem.nz
+    d.r_in, d.r_out, d.z0, d.z1 = problem.r_in, problem.r_out, problem.z0, problem.z1
+    d.theta_span = problem.theta_span
+    d.phi_r_in, d.phi_r_out = problem.phi_r_in, problem.phi_r_out
+    d.phi_z0, d.phi_z1 = problem.phi_z0, problem.phi_z1
+    for name in ("phi_r_in_z", "phi_r_out_z"):
+        vals = getattr(problem, name)
+        if vals is not None:
+            arr = (ctypes.c_double * len(vals))(*vals)
+            keep.append(arr)
+            setattr(d, name, ctypes.addressof(arr))
+    d.eps0 = problem.eps0
+    d.precision = precision
+    d.max_cycles = max_cycles
+    d.pre_sweeps = pre_sweeps
+    d.post_sweeps = post_sweeps
+    d.flags = flags
+    return d, keep
+
+
+def query(problem, **kw) -> dict:
+    d, _keep = make_desc(problem, **kw)
+    lay = Layout()
+    _check(load().pic_poisson_query(ctypes.byref(d), ctypes.byref(lay)))
+    return {"levels": lay.levels, "nr": list(lay.nr[:lay.levels]), "nz": list(lay.nz[:lay.levels]),
+            "n_modes": lay.n_modes, "workspace_bytes": lay.workspace_bytes}
+
+
+def cell_coeffs(problem, i, k) -> list:
+    d, _keep = make_desc(problem)
+    out = (ctypes.c_double * 12)()
+    _check(load().pic_poisson_cell_coeffs(ctypes.byref(d), int(i), int(k), out))
+    return list(out)
+
+
+def measure_fma_peaks(stream=None):
+    import torch
+    st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().pic_poisson_measure_fma_peaks(ctypes.c_void_p(st), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def _dev_ptr(t, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A solver plan for one problem (wraps pic_poisson_plan / solve / destroy)."""
+
+    def __init__(self, problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
+                 profile=False, initial_guess=False, stream=None):
+        import torch
+        self.problem = problem
+        flags = (PROFILE if profile else 0) | (USE_INITIAL_GUESS if initial_guess else 0)
+        self._desc, self._keep = make_desc(problem, precision, max_cycles, pre_sweeps, post_sweeps, flags)
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        self._plan = ctypes.c_void_p()
+        _check(load().pic_poisson_plan(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
+                                       ctypes.byref(self._plan)))
+        self.shape = (problem.nz, problem.ntheta, problem.nr)
+        self.n_modes = problem.ntheta // 2 + 1
+        self.mode_shape = (problem.nz, problem.nr, self.n_modes, 2)
+
+    def close(self):
+        if self._plan:
+            load().pic_poisson_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(load().pic_poisson_set_stream(self._plan, ctypes.c_void_p(stream.cuda_stream)))
+
+    def solve(self, rho, phi=None, tol=1e-10):
+        """Solve into phi (allocated if None); returns (phi, info dict).
+
+        Raises PicPoissonError for every status except OK and ENOTCONVERGED
+        (reported in info["status"]).
+        """
+        import torch
+        if phi is None:
+            phi = torch.empty(self.shape, dtype=torch.float64, device=rho.device)
+        info = Info()
+        st = load().pic_poisson_solve(self._plan, _dev_ptr(rho, self.shape, "rho"),
+                                      _dev_ptr(phi, self.shape, "phi"), float(tol), ctypes.byref(info))
+        _check(st, allow=(OK, ENOTCONVERGED))
+        return phi, info.as_dict()
+
+    def solve_host(self, rho_host, phi_host, tol=1e-10):
+        """Solve from host tensors (CPU, float64, contiguous; pinned for speed)."""
+        for t, name in ((rho_host, "rho_host"), (phi_host, "phi_host")):
+            if t.is_cuda or not t.is_contiguous() or tuple(t.shape) != self.shape:
+                raise ValueError(f"{name} must be a contiguous CPU tensor of shape {self.shape}")
+        info = Info()
+        st = load().pic_poisson_solve_host(self._plan, ctypes.c_void_p(rho_host.data_ptr()),
+                                           ctypes.c_void_p(phi_host.data_ptr()), float(tol), ctypes.byref(info))
+        _check(st, allow=(OK, ENOTCONVERGED))
+        return info.as_dict()
+
+    def forward(self, rho, bhat=None):
+        import torch
+        if bhat is None:
+            bhat = torch.empty(self.mode_shape, dtype=torch.float64, device=rho.device)
+        _check(load().pic_poisson_forward(self._plan, _dev_ptr(rho, self.shape, "rho"),
+                                          _dev_ptr(bhat, self.mode_shape, "bhat")))
+        return bhat
+
+    def inverse(self, phihat, phi=None):
+        import torch
+        if phi is None:
+            phi = torch.empty(self.shape, dtype=torch.float64, device=phihat.device)
+        _check(load().pic_poisson_inverse(self._plan, _dev_ptr(phihat, self.mode_shape, "phihat"),
+                                          _dev_ptr(phi, self.shape, "phi")))
+        return phi
+
+    def mode_residual(self, uhat, bhat, want_r=True):
+        import torch
+        r = torch.empty(self.mode_shape, dtype=torch.float64, device=uhat.device) if want_r else None
+        rel = ctypes.c_double()
+        _check(load().pic_poisson_mode_residual(
+            self._plan, _dev_ptr(uhat, self.mode_shape, "uhat"), _dev_ptr(bhat, self.mode_shape, "bhat"),
+            _dev_ptr(r, self.mode_shape, "rhat") if want_r else None, ctypes.byref(rel)))
+        return r, rel.value

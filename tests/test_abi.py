@@ -1,0 +1,118 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The library loads, exports every function include/pic_poisson.h declares, and
+its host-only entry points (descriptor validation, multigrid hierarchy,
+level-0 coefficients) behave as documented.  The coefficient builder is
+pinned to the paper's worked stencil example and compared with the oracle's
+independent coefficient routine.
+"""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_07172_gb300 import binding as B, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "pic_poisson.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(pic_poisson_\w+)\s*\(", text, re.M)))
+
+
+def test_library_exports_every_declared_function():
+    lib = B.load()
+    names = header_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(B.EXPORTS)
+
+
+def test_query_hierarchy_paper_grid():
+    q = B.query(W.c1_problem())
+    assert q["levels"] == 5
+    assert q["nr"] == [512, 256, 128, 64, 32]
+    assert q["nz"] == [400, 200, 100, 50, 25]
+    assert q["n_modes"] == 65
+    # two complex FP64 vectors on every level dominate the workspace
+    v0 = 512 * 400 * 65 * 16
+    assert 2 * v0 < q["workspace_bytes"] < 2 * v0 * 1.5
+
+
+def test_query_mixed_has_fp32_levels():
+    q64 = B.query(W.c1_problem())
+    qm = B.query(W.c1_problem(), precision=B.MIXED)
+    assert qm["levels"] == q64["levels"]
+    assert qm["workspace_bytes"] < q64["workspace_bytes"] * 1.5
+
+
+@pytest.mark.parametrize("kw, why", [
+    (dict(ntheta=12), "power of two"),
+    (dict(ntheta=512), "power of two"),
+    (dict(nr=0), "nr and nz"),
+    (dict(r_in=0.0), "r_in"),
+    (dict(r_in=0.06), "r_in"),
+    (dict(z1=-1.0), "z0 < z1"),
+    (dict(nr=127, nz=129), "direct-solve limit"),
+])
+def test_query_rejects_invalid(kw, why):
+    base = dict(nr=32, ntheta=16, nz=32)
+    base.update(kw)
+    with pytest.raises(B.PicPoissonError) as ei:
+        B.query(W.Problem(**base))
+    assert ei.value.status == B.EINVAL
+    assert why in str(ei.value)
+
+
+def test_precision_and_sweeps_validated():
+    d, _ = B.make_desc(W.c0_problem(), precision=7)
+    assert B.load().pic_poisson_query(ctypes.byref(d), None) == B.EINVAL
+    d, _ = B.make_desc(W.c0_problem(), pre_sweeps=0, post_sweeps=0)
+    assert B.load().pic_poisson_query(ctypes.byref(d), None) == B.EINVAL
+
+
+def test_cell_coeffs_worked_example(golden):
+    """Library coefficient builder on the appendix's worked stencil cell."""
+    g0 = golden("worked_stencil.txt")
+    p = W.Problem(nr=3, ntheta=8, nz=3, r_in=0.5, r_out=3.5, z0=-0.5, z1=2.5)
+    c = B.cell_coeffs(p, 1, 1)
+    assert c[0:4] == pytest.approx([g0["G_r_minus"][0], g0["G_r_plus"][0], g0["G_z_minus"][0],
+                                    g0["G_z_plus"][0]], rel=1e-15)
+    assert c[4:8] == [0, 0, 0, 0]
+    assert c[8] == pytest.approx(g0["mu"][0], rel=1e-15)
+    assert c[9] * W.EPS0 == pytest.approx(g0["s_times_eps0"][0], rel=1e-15)
+    assert c[10] == pytest.approx(g0["D0_interior"][0], rel=1e-15)
+    # east Dirichlet face at r = 2.5: two radial cells, the second centred at r = 2
+    pd = W.Problem(nr=2, ntheta=8, nz=3, r_in=0.5, r_out=2.5, z0=-0.5, z1=2.5, phi_r_out=7.0, phi_z0=0.0)
+    cd = B.cell_coeffs(pd, 1, 1)
+    assert cd[5] == 1 and cd[4] == 0
+    assert cd[1] == pytest.approx(g0["GD_r_plus"][0], rel=1e-15)
+    assert cd[10] == pytest.approx(g0["D0_dirichlet_east"][0], rel=1e-15)
+    assert cd[11] == pytest.approx(g0["rhs_dirichlet_factor"][0] * 7.0, rel=1e-15)
+
+
+def test_cell_coeffs_match_oracle_everywhere():
+    p = W.annulus(9, 8, 7, phi_r_in=3.0, phi_r_out=-2.0, phi_z0=11.0, phi_z1=5.0)
+    g = oracle.grid_from_problem(p)
+    b = oracle.rhs3d(g, np.zeros(p.shape))
+    for k in range(p.nz):
+        for i in range(p.nr):
+            lib = np.array(B.cell_coeffs(p, i, k))
+            orc = oracle.cell_coeffs(g, i, k)
+            np.testing.assert_allclose(lib[0:4], orc["G"], rtol=1e-14)
+            np.testing.assert_array_equal(lib[4:8].astype(bool), orc["dirichlet"])
+            assert lib[8] == pytest.approx(orc["mu"], rel=1e-14)
+            assert lib[9] == pytest.approx(orc["s"], rel=1e-14)
+            assert lib[10] == pytest.approx(orc["D0"], rel=1e-14)
+            assert lib[11] == pytest.approx(b[k, 0, i], rel=1e-14, abs=1e-12)
+
+
+def test_cell_coeffs_rejects_outside():
+    with pytest.raises(B.PicPoissonError):
+        B.cell_coeffs(W.c0_problem(), 32, 0)

@@ -1,0 +1,179 @@
+"""CUDA path vs the FP64 CPU oracle, element by element (needs a GPU).
+
+Every step of the path is called through the C ABI (ctypes binding): the
+forward transform + right-hand side (a-1), the mode operator / residual
+(a-3/a-4/a-7 arithmetic), the inverse transform (a-8) and the full solve.
+Sizes span several FFT tiles (32 columns), ragged tails (nr not a multiple of
+32), single-level grids, N_theta = 2 .. 128, and stress geometries where the
+azimuthal shift lambda_m mu dominates.  Tolerance: relative L2 <= 1e-12 in
+phi for the FP64 path (the FP64 parity bound); transforms and residuals agree
+to rounding (1e-13 of the largest entry).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import (discrete_manufactured_rho, from_modes, narrow_span, rel_l2, small_rin, to_modes,
+                     with_bias_walls)
+from paper_2609_07172_gb300 import Plan, PicPoissonError, binding as B, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [(32, 16, 32), (40, 8, 24), (96, 16, 40), (64, 32, 48), (15, 4, 9), (48, 2, 16), (128, 64, 64)]
+FP64_TOL = 1e-12
+
+
+def problems():
+    out = []
+    for nr, nt, nz in DIMS:
+        out.append(pytest.param(with_bias_walls(W.annulus(nr, nt, nz)), id=f"annulus{nr}x{nt}x{nz}"))
+    out.append(pytest.param(narrow_span(), id="narrow_span"))
+    out.append(pytest.param(small_rin(), id="small_rin"))
+    return out
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("p", problems())
+def test_forward_transform_and_rhs(p):
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=5)
+    expect = to_modes(oracle.rhs3d(g, rho))
+    with Plan(p) as plan:
+        got = plan.forward(dev(rho)).cpu().numpy()
+    scale = np.abs(expect).max()
+    np.testing.assert_allclose(got, expect, rtol=0, atol=1e-13 * scale)
+    assert np.all(got[:, :, 0, 1] == 0.0)
+    if p.ntheta >= 2:
+        assert np.all(got[:, :, p.ntheta // 2, 1] == 0.0)
+
+
+@pytest.mark.parametrize("p", problems())
+def test_inverse_transform(p):
+    rng = np.random.default_rng(3)
+    xm = rng.standard_normal((p.nz, p.nr, p.ntheta // 2 + 1, 2))
+    expect = from_modes(xm, p.ntheta)      # imaginary parts of m = 0, N/2 are ignored
+    with Plan(p) as plan:
+        got = plan.inverse(dev(xm)).cpu().numpy()
+    np.testing.assert_allclose(got, expect, rtol=0, atol=1e-13 * np.abs(expect).max())
+
+
+@pytest.mark.parametrize("p", problems())
+def test_mode_operator_matches_3d_operator(p):
+    """b_hat - A_m u_hat on the GPU equals (1/N) DFT of the oracle's b - A_3D phi."""
+    g = oracle.grid_from_problem(p)
+    rng = np.random.default_rng(7)
+    rho = W.rho_plasma(p, seed=9)
+    phi = rng.standard_normal(p.shape) * 50.0
+    r3 = oracle.rhs3d(g, rho) - oracle.apply3d(g, phi)
+    expect = to_modes(r3)
+    with Plan(p) as plan:
+        bhat = plan.forward(dev(rho))
+        r, rel = plan.mode_residual(dev(to_modes(phi)), bhat)
+        got = r.cpu().numpy()
+    np.testing.assert_allclose(got, expect, rtol=0, atol=1e-12 * np.abs(expect).max())
+    rn, bn = oracle.residual(g, rho, phi)
+    assert rel == pytest.approx(rn / bn, rel=1e-10)
+
+
+@pytest.mark.parametrize("p", problems())
+def test_solve_matches_oracle_at_floor(p):
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=1)
+    ref, oinfo = oracle.solve3d(g, rho, tol=1e-15)
+    with Plan(p) as plan:
+        phi, info = plan.solve(dev(rho), tol=0.0)
+    got = phi.cpu().numpy()
+    assert info["status"] == B.OK
+    err = rel_l2(got, ref)
+    assert err <= FP64_TOL, (err, info, oinfo)
+    assert oracle.relres(g, rho, got) <= 1e-12
+
+
+def test_c0_discrete_manufactured():
+    p = W.c0_problem()
+    phi_ex = W.c0_phi_exact(p)
+    rho = discrete_manufactured_rho(p, phi_ex)
+    with Plan(p) as plan:
+        phi, info = plan.solve(dev(rho), tol=0.0)
+    assert rel_l2(phi.cpu().numpy(), phi_ex) <= FP64_TOL
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_stop_at_tolerance_reports_true_residual(tol):
+    p = with_bias_walls(W.annulus(64, 32, 48))
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=2)
+    with Plan(p) as plan:
+        phi, info = plan.solve(dev(rho), tol=tol)
+    assert info["status"] == B.OK
+    assert info["rel_res"] <= tol
+    true = oracle.relres(g, rho, phi.cpu().numpy())
+    assert true == pytest.approx(info["rel_res"], rel=1e-6, abs=1e-14)
+
+
+def test_zero_problem_gives_zero():
+    p = W.annulus(32, 8, 16, phi_z0=0.0)
+    with Plan(p) as plan:
+        phi, info = plan.solve(torch.zeros(p.shape, dtype=torch.float64, device="cuda"), tol=1e-10)
+    assert info["status"] == B.OK and info["rel_res"] == 0.0
+    assert torch.count_nonzero(phi).item() == 0
+
+
+def test_nonfinite_rho_is_reported():
+    p = W.c0_problem()
+    rho = np.zeros(p.shape)
+    rho[3, 2, 1] = np.nan
+    with Plan(p) as plan:
+        with pytest.raises(PicPoissonError) as ei:
+            plan.solve(dev(rho))
+    assert ei.value.status == B.ENONFINITE
+
+
+def test_not_converged_is_reported():
+    p = W.annulus(64, 16, 64)
+    rho = W.rho_plasma(p, seed=4)
+    with Plan(p, max_cycles=1) as plan:
+        phi, info = plan.solve(dev(rho), tol=1e-14)
+    assert info["status"] == B.ENOTCONVERGED
+    assert info["cycles"] == 1 and info["rel_res"] > 1e-14
+
+
+def test_initial_guess_exact_solution_needs_no_cycle():
+    p = W.annulus(64, 16, 48)
+    rho = W.rho_plasma(p, seed=6)
+    with Plan(p) as plan:
+        phi, _ = plan.solve(dev(rho), tol=0.0)
+    with Plan(p, initial_guess=True) as plan:
+        phi2 = phi.clone()
+        phi2, info = plan.solve(dev(rho), phi2, tol=1e-10)
+    assert info["cycles"] == 0 and info["rel_res0"] < 1e-12
+    assert rel_l2(phi2.cpu().numpy(), phi.cpu().numpy()) < 1e-13
+
+
+def test_deterministic_and_host_entry_point_agree():
+    p = W.annulus(96, 16, 40)
+    rho = W.rho_plasma(p, seed=8)
+    with Plan(p) as plan:
+        a, _ = plan.solve(dev(rho), tol=1e-10)
+        b, _ = plan.solve(dev(rho), tol=1e-10)
+        rho_h = torch.from_numpy(rho).pin_memory()
+        phi_h = torch.empty(p.shape, dtype=torch.float64).pin_memory()
+        info = plan.solve_host(rho_h, phi_h, tol=1e-10)
+    assert torch.equal(a, b)
+    assert torch.equal(a.cpu(), phi_h)
+    assert info["status"] == B.OK
+
+
+def test_profile_counts_launches():
+    p = W.annulus(64, 16, 64)
+    rho = W.rho_plasma(p, seed=4)
+    with Plan(p, profile=True) as plan:
+        _, info = plan.solve(dev(rho), tol=1e-10)
+    lp, ms = info["launches_phase"], info["ms_phase"]
+    assert lp["forward"] == 1 and lp["inverse"] == 1
+    assert lp["smooth"] > 0 and ms["smooth"] > 0
+    assert info["launches"] == sum(lp.values())
