@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--extra-forms", action="store_true", help="also time the mixed-precision form")
+    ap.add_argument("--grid", type=int, nargs=3, metavar=("NR", "NTHETA", "NZ"), default=None,
+                    help="override the 512 128 400 grid (profiling of smaller cases)")
     return ap.parse_args()
 
 
@@ -117,7 +119,7 @@ def v_bytes(nr, nz, nm, word=8):
     return nr * nz * nm * 2 * word
 
 
-def algorithmic_model(q, info_list, pre, post, word=8):
+def algorithmic_model(q, info_list, pre, post, word=8, grid=GRID):
     """Compulsory HBM bytes per solve and FP64 flops of the smoother class.
 
     Per level l (V_l = one complex mode vector of the level): a red-black half
@@ -130,7 +132,7 @@ def algorithmic_model(q, info_list, pre, post, word=8):
     nm = q["n_modes"]
     L = q["levels"]
     V = [v_bytes(q["nr"][l], q["nz"][l], nm, word) for l in range(L)]
-    X = GRID[0] * GRID[1] * GRID[2] * 8
+    X = grid[0] * grid[1] * grid[2] * 8
     tot_bytes, sm_bytes, sm_flops, sm_launches = 0.0, 0.0, 0.0, 0
     for info in info_list:
         c = info["cycles"]
@@ -242,7 +244,7 @@ def run_ours(args):
     B.load(build_if_missing=True)
 
     prec = FP64 if args.precision == "fp64" else MIXED
-    p = W.c1_problem()
+    p = W.annulus(*args.grid) if args.grid else W.c1_problem()
     q = query(p, precision=prec)
     seeds = [rank * 1000 + s for s in range(args.seeds)]
     rhos = [torch.from_numpy(W.rho_plasma(p, s)).to(dev) for s in seeds]
@@ -288,7 +290,7 @@ def run_ours(args):
     ph_ms = {k: sum(i["ms_phase"][k] for i in infos) for k in infos[0]["ms_phase"]}
     ph_n = {k: sum(i["launches_phase"][k] for i in infos) for k in infos[0]["launches_phase"]}
     dominant = max(ph_ms, key=ph_ms.get)
-    tot_bytes, sm_bytes, sm_flops, sm_launches = algorithmic_model(q, infos, 2, 2, word)
+    tot_bytes, sm_bytes, sm_flops, sm_launches = algorithmic_model(q, infos, 2, 2, word, (p.nr, p.ntheta, p.nz))
     sm_ms = ph_ms["smooth"]
     sm_gbs = sm_bytes / (sm_ms * 1e-3) / 1e9 if sm_ms > 0 else None
     sm_tflops = sm_flops / (sm_ms * 1e-3) / 1e12 if sm_ms > 0 else None
@@ -313,9 +315,10 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_local, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == FP64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": "annulus 512x128x400, 65 azimuthal modes, %s batched GMG V(2,2), "
-                                   "rho seeds %s (Poisson counts, mean 27, m=8 wave)" % (args.precision, seeds),
-                       "grid_nr_ntheta_nz": list(GRID), "tol": args.tol, "levels": q["levels"],
+            "config": {"workload": "annulus %dx%dx%d, %d azimuthal modes, %s batched GMG V(2,2), "
+                                   "rho seeds %s (Poisson counts, mean 27, m=8 wave)"
+                                   % (p.nr, p.ntheta, p.nz, p.n_modes, args.precision, seeds),
+                       "grid_nr_ntheta_nz": [p.nr, p.ntheta, p.nz], "tol": args.tol, "levels": q["levels"],
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (rho 209.7 MB, mode vector 213 MB per step)"},
             "status": statuses, "cycles": {"min": min(cycles), "max": max(cycles),

@@ -16,7 +16,7 @@ def to_modes(x3d):
     n = x3d.shape[1]
     xh = np.fft.rfft(x3d, axis=1) / n          # (nz, nm, nr)
     xh = np.transpose(xh, (0, 2, 1))           # (nz, nr, nm)
-    return np.stack([xh.real, xh.imag], axis=-1)
+    return np.ascontiguousarray(np.stack([xh.real, xh.imag], axis=-1))
 
 
 def from_modes(xm, ntheta):
