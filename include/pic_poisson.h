@@ -187,6 +187,35 @@ int pic_poisson_inverse(pic_poisson_plan_t plan, const double *phihat_dev, doubl
 int pic_poisson_mode_residual(pic_poisson_plan_t plan, const double *uhat_dev, const double *bhat_dev,
                               double *rhat_dev, double *rel_res);
 
+/*
+ * No-allocation variant of pic_poisson_mode_residual, for callers that cannot
+ * call cudaMalloc: a particle-in-cell code that has handed all device memory to
+ * its particle arrays at start-up, or a real-time step loop that may not pay
+ * cudaMalloc's implicit device synchronisation.  The paper has no counterpart;
+ * it is a library utility.
+ *
+ * Needs no plan: the coefficients of A_m are computed inside the kernel from
+ * desc's uniform geometry (only nr, ntheta, nz, r_in, r_out, z0, z1 and
+ * theta_span are read).  Writes rhat_dev = bhat_dev - A_m uhat_dev (mode
+ * layout; rhat_dev may be NULL) and *rel_res_dev = Parseval-weighted
+ * ||r|| / ||b|| (one device double) on `stream`, asynchronously: the results
+ * are valid once the stream's work up to this call has completed.
+ *
+ * Allocates nothing: its per-block partial sums live in a fixed 1 MiB
+ * file-scope device array that every GPU loading the library holds until the
+ * process exits.  Limit: nr * nz * (ntheta/2 + 1) <= 16,777,216 mode entries
+ * and ntheta <= 256; larger problems are rejected with PIC_POISSON_EINVAL.
+ * The first call on a device looks up that array's device address with
+ * cudaGetSymbolAddress (device current at the call); make that first call
+ * before any stream capture.  Every call reuses the same array; each call
+ * writes every partial it later reads, so nothing needs clearing, but calls
+ * whose work overlaps on the GPU (different streams, or devices sharing a
+ * context) race on the array and must be serialised by the caller.
+ */
+int pic_poisson_mode_residual_noalloc(const pic_poisson_desc *desc, const double *uhat_dev,
+                                      const double *bhat_dev, double *rhat_dev, double *rel_res_dev,
+                                      void *stream);
+
 /* Release everything the plan owns.  NULL is accepted. */
 int pic_poisson_destroy(pic_poisson_plan_t plan);
 

@@ -23,7 +23,7 @@ EXPORTS = (
     "pic_poisson_query", "pic_poisson_cell_coeffs", "pic_poisson_plan", "pic_poisson_set_stream",
     "pic_poisson_solve", "pic_poisson_solve_host", "pic_poisson_forward", "pic_poisson_inverse",
     "pic_poisson_mode_residual", "pic_poisson_destroy", "pic_poisson_last_error",
-    "pic_poisson_measure_fma_peaks",
+    "pic_poisson_measure_fma_peaks", "pic_poisson_mode_residual_noalloc",
 )
 
 
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
         "pic_poisson_destroy": ([vp], ip),
         "pic_poisson_last_error": ([], ctypes.c_char_p),
         "pic_poisson_measure_fma_peaks": ([vp, vp, vp], ip),
+        "pic_poisson_mode_residual_noalloc": ([vp, vp, vp, vp, vp, vp], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
