@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--extra-forms", action="store_true", help="also time the mixed-precision form")
+    ap.add_argument("--no-forms", action="store_true", help="skip timing the other precision form")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NR", "NTHETA", "NZ"), default=None,
                     help="override the 512 128 400 grid (profiling of smaller cases)")
     return ap.parse_args()
@@ -115,59 +115,20 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(pw)}
 
 
-def v_bytes(nr, nz, nm, word=8):
-    return nr * nz * nm * 2 * word
-
-
-def algorithmic_model(q, info_list, pre, post, word=8, grid=GRID):
-    """Compulsory HBM bytes per solve and FP64 flops of the smoother class.
-
-    Per level l (V_l = one complex mode vector of the level): a red-black half
-    sweep reads the other colour of u and this colour of b and writes this
-    colour of u (1.5 V_l, 8 flops per real component); residual + restriction
-    reads u, b and writes coarse b and u (2.5 V_l); prolongation reads coarse
-    u and reads/writes u (2.25 V_l); forward / inverse transforms move one
-    real 3-D array and one mode vector each.
-    """
-    nm = q["n_modes"]
-    L = q["levels"]
-    V = [v_bytes(q["nr"][l], q["nz"][l], nm, word) for l in range(L)]
-    X = grid[0] * grid[1] * grid[2] * 8
-    tot_bytes, sm_bytes, sm_flops, sm_launches = 0.0, 0.0, 0.0, 0
-    for info in info_list:
-        c = info["cycles"]
-        b = 2.0 * (X + V[0])   # forward + inverse
-        # level 0: pre-smoothing once per residual check (c + 1 checks), post once per cycle
-        half0 = 2 * pre * (c + 1) + 2 * post * c
-        sweeps = {0: half0}
-        for l in range(1, L - 1):
-            sweeps[l] = 2 * (pre + post) * c
-        for l, h in sweeps.items():
-            sm_bytes += h * 1.5 * V[l]
-            sm_flops += h * (V[l] / (2 * word)) / 2 * 16     # updated complex entries x 16 flops
-            sm_launches += h
-        b += sm_bytes_total(sweeps, V)
-        b += (c + 1) * 2.5 * V[0] + sum(c * 2.5 * V[l] for l in range(1, L - 1))
-        b += sum(c * 2.25 * V[l] for l in range(0, L - 1))
-        b += c * 2 * V[L - 1]
-        tot_bytes += b
-    return tot_bytes, sm_bytes, sm_flops, sm_launches
-
-
-def sm_bytes_total(sweeps, V):
-    return sum(h * 1.5 * V[l] for l, h in sweeps.items())
-
-
 def traffic_from_profile(name):
     """Per-launch DRAM bytes recorded in a committed ncu summary, or None."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         for line in open(path):
-            if line.startswith("dram_bytes_per_fine_launch:"):
+            if line.startswith("dram_bytes_per_launch_full_size:"):
                 return float(line.split(":")[1])
     except OSError:
         pass
     return None
+
+
+def sum_phase(infos, key):
+    return {k: sum(i[key][k] for i in infos) for k in infos[0][key]}
 
 
 # ------------------------------------------------------------------ CPU oracle timing
@@ -227,6 +188,60 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def time_form(plan, rhos, phi, steps, warmup, tol, world, dist, sampler=None):
+    """Warm up, then time `steps` solves on the plan's stream; returns (ms total, infos, clocks)."""
+    import torch
+    for w in range(warmup):
+        plan.solve(rhos[w % len(rhos)], phi, tol=tol)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(plan.stream)
+    for k in range(steps):
+        _, info = plan.solve(rhos[k % len(rhos)], phi, tol=tol)
+        infos.append(info)
+    e1.record(plan.stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        dist.barrier()
+    return e0.elapsed_time(e1), infos, clocks
+
+
+def roofline(infos, prec_fp64, fp64_tflops, hbm_peak, hbm_src, traffic):
+    """Roofline of the dominant kernel class from the library's PROFILE events
+    and its algorithmic byte / flop accounting over the timed solves."""
+    ms = sum_phase(infos, "ms_phase")
+    by = sum_phase(infos, "bytes_phase")
+    fl = sum_phase(infos, "flops_phase")
+    n = sum_phase(infos, "launches_phase")
+    dom = max(ms, key=ms.get)
+    gbs = by[dom] / (ms[dom] * 1e-3) / 1e9 if ms[dom] > 0 else None
+    tfs = fl[dom] / (ms[dom] * 1e-3) / 1e12 if ms[dom] > 0 else None
+    per_launch_bytes = by[dom] / max(n[dom], 1)
+    out = {"kernel_class": dom, "launches": n[dom], "ms_per_launch": ms[dom] / max(n[dom], 1),
+           "algorithmic_bytes_per_launch": per_launch_bytes,
+           "algorithmic_flops_per_launch": fl[dom] / max(n[dom], 1)}
+    if prec_fp64:
+        out.update({"bound": "alu", "achieved": tfs, "peak": fp64_tflops, "unit": "TFLOP/s",
+                    "frac": tfs / fp64_tflops if tfs else None,
+                    "peak_source": "measured: FP64 FMA throughput probe (pic_poisson_measure_fma_peaks) on this GPU",
+                    "hbm_achieved_gbs": gbs, "hbm_peak_gbs": hbm_peak,
+                    "hbm_frac": gbs / hbm_peak if gbs else None})
+    else:
+        out.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": gbs / hbm_peak if gbs else None, "peak_source": hbm_src,
+                    "fp64_tflops": tfs})
+    out["traffic"] = traffic
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -250,86 +265,42 @@ def run_ours(args):
     rhos = [torch.from_numpy(W.rho_plasma(p, s)).to(dev) for s in seeds]
     phi = torch.empty(p.shape, dtype=torch.float64, device=dev)
     fp64_gflops, fp32_gflops = measure_fma_peaks()
+    hbm_peak, hbm_src = measured_peaks()
+    tag = "%dx%dx%d" % (p.nr, p.ntheta, p.nz)
 
     plan = Plan(p, precision=prec, profile=True)
-    stream = plan.stream
-    for w in range(args.warmup):
-        plan.solve(rhos[w % len(rhos)], phi, tol=args.tol)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    infos = []
-    e0.record(stream)
-    for k in range(args.steps):
-        _, info = plan.solve(rhos[k % len(rhos)], phi, tol=args.tol)
-        infos.append(info)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    if world > 1:
-        dist.barrier()
-    ms_total = e0.elapsed_time(e1)
+    ms_total, infos, clocks = time_form(plan, rhos, phi, args.steps, args.warmup, args.tol, world, dist,
+                                        ClockSampler(local))
     if world > 1:
         t = torch.tensor([ms_total], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_total = float(t.item())
-    ms_per_solve = ms_total / (args.steps * world)
     ms_local = ms_total / args.steps
-    statuses = sorted({i["status"] for i in infos})
+    ms_per_solve = ms_total / (args.steps * world)
     cycles = [i["cycles"] for i in infos]
-    rel = [i["rel_res"] for i in infos]
-
-    # ---- roofline of the dominant kernel class (level-0 + coarse smoother half-sweeps)
-    hbm_peak, hbm_src = measured_peaks()
-    word = 8 if prec == FP64 else 4
-    ph_ms = {k: sum(i["ms_phase"][k] for i in infos) for k in infos[0]["ms_phase"]}
-    ph_n = {k: sum(i["launches_phase"][k] for i in infos) for k in infos[0]["launches_phase"]}
-    dominant = max(ph_ms, key=ph_ms.get)
-    tot_bytes, sm_bytes, sm_flops, sm_launches = algorithmic_model(q, infos, 2, 2, word, (p.nr, p.ntheta, p.nz))
-    sm_ms = ph_ms["smooth"]
-    sm_gbs = sm_bytes / (sm_ms * 1e-3) / 1e9 if sm_ms > 0 else None
-    sm_tflops = sm_flops / (sm_ms * 1e-3) / 1e12 if sm_ms > 0 else None
-    fp64_tf = fp64_gflops / 1e3
-    if prec == FP64:
-        roof = {"bound": "alu", "achieved": sm_tflops, "peak": fp64_tf, "unit": "TFLOP/s",
-                "frac": sm_tflops / fp64_tf if sm_tflops else None,
-                "traffic": traffic_from_profile("smooth_fp64_512x128x400.md"),
-                "kernel": "k_smooth<double> (red-black Gauss-Seidel half-sweep, all levels)",
-                "peak_source": "FP64 FMA throughput measured live by pic_poisson_measure_fma_peaks",
-                "hbm_achieved_gbs": sm_gbs, "hbm_peak_gbs": hbm_peak,
-                "hbm_frac": sm_gbs / hbm_peak if sm_gbs else None,
-                "launches": ph_n["smooth"], "model_launches": sm_launches}
-    else:
-        roof = {"bound": "hbm", "achieved": sm_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": sm_gbs / hbm_peak if sm_gbs else None,
-                "traffic": traffic_from_profile("smooth_fp32_512x128x400.md"),
-                "kernel": "k_smooth<float>", "peak_source": hbm_src}
-    solve_gbs = tot_bytes / len(infos) / (ms_local * 1e-3) / 1e9
+    by = sum_phase(infos, "bytes_phase")
+    solve_gbs = sum(by.values()) / len(infos) / (ms_local * 1e-3) / 1e9
+    ms_ph = sum_phase(infos, "ms_phase")
+    traffic = traffic_from_profile("smooth_%s_%s.md" % (args.precision, tag))
 
     line = {"metric": METRIC, "value": ms_per_solve, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_local, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == FP64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": "annulus %dx%dx%d, %d azimuthal modes, %s batched GMG V(2,2), "
-                                   "rho seeds %s (Poisson counts, mean 27, m=8 wave)"
-                                   % (p.nr, p.ntheta, p.nz, p.n_modes, args.precision, seeds),
+            "config": {"workload": "annulus %s, %d azimuthal modes, %s batched GMG V(2,2), rho seeds %s "
+                                   "(Poisson counts, mean 27, m=8 wave)" % (tag, p.n_modes, args.precision, seeds),
                        "grid_nr_ntheta_nz": [p.nr, p.ntheta, p.nz], "tol": args.tol, "levels": q["levels"],
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (rho 209.7 MB, mode vector 213 MB per step)"},
-            "status": statuses, "cycles": {"min": min(cycles), "max": max(cycles),
-                                           "median": statistics.median(cycles)},
-            "rel_res_max": max(rel),
+            "status": sorted({i["status"] for i in infos}),
+            "cycles": {"min": min(cycles), "max": max(cycles), "median": statistics.median(cycles)},
+            "rel_res_max": max(i["rel_res"] for i in infos),
             "gpu_launches": int(sum(i["launches"] for i in infos)),
-            "phase_ms_per_solve": {k: v / len(infos) for k, v in ph_ms.items()},
-            "dominant_phase": dominant,
-            "roofline": roof,
+            "phase_ms_per_solve": {k: v / len(infos) for k, v in ms_ph.items()},
+            "roofline": roofline(infos, prec == FP64, fp64_gflops / 1e3, hbm_peak, hbm_src, traffic),
             "hbm_roofline_solve": {"achieved_gbs": solve_gbs, "peak_gbs": hbm_peak, "frac": solve_gbs / hbm_peak,
-                                   "bytes_per_solve": tot_bytes / len(infos), "peak_source": hbm_src},
+                                   "algorithmic_bytes_per_solve": sum(by.values()) / len(infos),
+                                   "peak_source": hbm_src},
             "fma_peaks_gflops": {"fp64": fp64_gflops, "fp32": fp32_gflops},
             "clocks": clocks}
 
@@ -340,8 +311,8 @@ def run_ours(args):
         plan.solve_host(rho_h[0], phi_h, tol=args.tol)
         if world > 1:
             dist.barrier()
-        t0 = time.perf_counter()
         ne = max(3, args.steps // 4)
+        t0 = time.perf_counter()
         for k in range(ne):
             plan.solve_host(rho_h[k % len(rho_h)], phi_h, tol=args.tol)
         e2e_ms = (time.perf_counter() - t0) * 1e3 / ne
@@ -351,11 +322,37 @@ def run_ours(args):
             e2e_ms = float(t.item()) / world
         nbytes = p.nr * p.ntheta * p.nz * 8
         line["e2e"] = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                       "steps": ne}
-
-    if args.extra_forms and prec == FP64:
-        line["forms"] = {}
+                       "steps": ne, "api": "pic_poisson_solve_host (pinned host buffers)"}
+    ref_phi = phi.clone()
     plan.close()
+
+    # ---- the other form on the same GPU and inputs (mixed FP32/FP64 when the headline is FP64)
+    if not args.no_forms:
+        other = MIXED if prec == FP64 else FP64
+        name = "mixed" if other == MIXED else "fp64"
+        plan2 = Plan(p, precision=other, profile=True)
+        steps2 = max(4, args.steps // 2)
+        phi2 = torch.empty_like(phi)
+        ms2, infos2, _ = time_form(plan2, rhos, phi2, steps2, 2, args.tol, world, dist)
+        # same input as the last headline step
+        plan2.solve(rhos[(args.steps - 1) % len(rhos)], phi2, tol=args.tol)
+        torch.cuda.synchronize()
+        diff = float(torch.linalg.vector_norm(phi2 - ref_phi) / torch.linalg.vector_norm(ref_phi))
+        by2 = sum_phase(infos2, "bytes_phase")
+        ms2_solve = ms2 / steps2
+        gbs2 = sum(by2.values()) / len(infos2) / (ms2_solve * 1e-3) / 1e9
+        c2 = [i["cycles"] for i in infos2]
+        line["forms"] = {name: {
+            "ms_per_solve": ms2_solve, "steps": steps2, "dtype": "f32+f64" if other == MIXED else "f64",
+            "cycles_median": statistics.median(c2),
+            "outer_iterations_median": statistics.median([i["outer_iterations"] for i in infos2]),
+            "rel_res_max": max(i["rel_res"] for i in infos2),
+            "rel_l2_vs_headline_phi": diff,
+            "phase_ms_per_solve": {k: v / len(infos2) for k, v in sum_phase(infos2, "ms_phase").items()},
+            "roofline": roofline(infos2, other == FP64, fp64_gflops / 1e3, hbm_peak, hbm_src,
+                                 traffic_from_profile("smooth_%s_%s.md" % (name, tag))),
+            "hbm_roofline_solve": {"achieved_gbs": gbs2, "peak_gbs": hbm_peak, "frac": gbs2 / hbm_peak}}}
+        plan2.close()
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         ms, det = oracle_sample()

@@ -63,21 +63,22 @@ extern "C" {
 
 /* kernel classes, indices into pic_poisson_info.ms_phase / launches_phase */
 #define PIC_POISSON_PHASE_FORWARD 0   /* azimuthal rFFT + right-hand side */
-#define PIC_POISSON_PHASE_SMOOTH 1    /* red-black Gauss-Seidel half-sweeps */
-#define PIC_POISSON_PHASE_RESTRICT 2  /* residual + restriction (+ norm partials) */
-#define PIC_POISSON_PHASE_COARSE 3    /* coarsest-level direct solve */
-#define PIC_POISSON_PHASE_PROLONG 4   /* prolongation + correction */
-#define PIC_POISSON_PHASE_NORM 5      /* norm reductions */
-#define PIC_POISSON_PHASE_INVERSE 6   /* inverse azimuthal transform */
-#define PIC_POISSON_PHASE_DEFECT 7    /* FP64 defect / update of the mixed loop */
-#define PIC_POISSON_NPHASE 8
+#define PIC_POISSON_PHASE_SMOOTH 1    /* red-black Gauss-Seidel half-sweeps, finest level */
+#define PIC_POISSON_PHASE_SMOOTH_COARSE 2 /* red-black half-sweeps, coarser levels */
+#define PIC_POISSON_PHASE_RESTRICT 3  /* residual + restriction (+ norm partials) */
+#define PIC_POISSON_PHASE_COARSE 4    /* coarsest-level direct solve */
+#define PIC_POISSON_PHASE_PROLONG 5   /* prolongation + correction */
+#define PIC_POISSON_PHASE_NORM 6      /* norm reductions */
+#define PIC_POISSON_PHASE_INVERSE 7   /* inverse azimuthal transform */
+#define PIC_POISSON_PHASE_DEFECT 8    /* FP64 defect / update of the mixed loop */
+#define PIC_POISSON_NPHASE 9
 
 #define PIC_POISSON_MAX_LEVELS 16
 
 typedef struct pic_poisson_plan_s *pic_poisson_plan_t;
 
 typedef struct {
-    int nr, ntheta, nz;        /* cells; ntheta a power of two in [2, 1024] */
+    int nr, ntheta, nz;        /* cells; ntheta a power of two in [2, 256] */
     double r_in, r_out;        /* radial walls, 0 < r_in < r_out */
     double z0, z1;             /* axial walls, z0 < z1 */
     double theta_span;         /* azimuthal period; <= 0 selects 2*pi */
@@ -90,6 +91,7 @@ typedef struct {
     int max_cycles;            /* V-cycle cap; <= 0 selects 200 */
     int pre_sweeps;            /* red-black sweeps before restriction; < 0 selects 2 */
     int post_sweeps;           /* red-black sweeps after prolongation; < 0 selects 2 */
+    int inner_cycles;          /* mixed precision: FP32 V-cycles per FP64 defect correction; <= 0 selects 2 */
     unsigned flags;            /* PIC_POISSON_* flags */
 } pic_poisson_desc;
 
@@ -102,6 +104,8 @@ typedef struct {
     double rel_res;            /* ||b - A phi|| / ||b|| of the returned iterate (3-D system, Parseval) */
     double ms_phase[PIC_POISSON_NPHASE];   /* device ms per kernel class (PROFILE flag) */
     int launches_phase[PIC_POISSON_NPHASE];/* launches per kernel class */
+    double bytes_phase[PIC_POISSON_NPHASE];/* algorithmic (compulsory) DRAM bytes per kernel class */
+    double flops_phase[PIC_POISSON_NPHASE];/* algorithmic floating-point operations per kernel class */
 } pic_poisson_info;
 
 typedef struct {

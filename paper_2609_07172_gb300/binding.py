@@ -15,7 +15,7 @@ from . import build as _build
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE = 0, 1, 2, 3, 4, 5
 FP64, MIXED = 0, 1
 USE_INITIAL_GUESS, PROFILE = 1, 2
-PHASES = ("forward", "smooth", "restrict", "coarse", "prolong", "norm", "inverse", "defect")
+PHASES = ("forward", "smooth", "smooth_coarse", "restrict", "coarse", "prolong", "norm", "inverse", "defect")
 MAX_LEVELS = 16
 NPHASE = len(PHASES)
 
@@ -45,7 +45,7 @@ class Desc(ctypes.Structure):
         ("eps0", ctypes.c_double),
         ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
         ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int),
-        ("flags", ctypes.c_uint),
+        ("inner_cycles", ctypes.c_int), ("flags", ctypes.c_uint),
     ]
 
 
@@ -55,6 +55,7 @@ class Info(ctypes.Structure):
         ("launches", ctypes.c_int),
         ("rel_res0", ctypes.c_double), ("rel_res", ctypes.c_double),
         ("ms_phase", ctypes.c_double * NPHASE), ("launches_phase", ctypes.c_int * NPHASE),
+        ("bytes_phase", ctypes.c_double * NPHASE), ("flops_phase", ctypes.c_double * NPHASE),
     ]
 
     def as_dict(self):
@@ -63,6 +64,8 @@ class Info(ctypes.Structure):
             "launches": self.launches, "rel_res0": self.rel_res0, "rel_res": self.rel_res,
             "ms_phase": {p: self.ms_phase[i] for i, p in enumerate(PHASES)},
             "launches_phase": {p: self.launches_phase[i] for i, p in enumerate(PHASES)},
+            "bytes_phase": {p: self.bytes_phase[i] for i, p in enumerate(PHASES)},
+            "flops_phase": {p: self.flops_phase[i] for i, p in enumerate(PHASES)},
         }
 
 
@@ -129,7 +132,7 @@ def _check(status, allow=(OK,)):
     return status
 
 
-def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1, flags=0):
+def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1, flags=0, inner_cycles=0):
     """Descriptor for a workloads.Problem; returns (Desc, keep-alive buffers)."""
     keep = []
     d = Desc()
@@ -149,6 +152,7 @@ def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=
     d.max_cycles = max_cycles
     d.pre_sweeps = pre_sweeps
     d.post_sweeps = post_sweeps
+    d.inner_cycles = inner_cycles
     d.flags = flags
     return d, keep
 
@@ -191,11 +195,12 @@ class Plan:
     """A solver plan for one problem (wraps pic_poisson_plan / solve / destroy)."""
 
     def __init__(self, problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
-                 profile=False, initial_guess=False, stream=None):
+                 profile=False, initial_guess=False, stream=None, inner_cycles=0):
         import torch
         self.problem = problem
         flags = (PROFILE if profile else 0) | (USE_INITIAL_GUESS if initial_guess else 0)
-        self._desc, self._keep = make_desc(problem, precision, max_cycles, pre_sweeps, post_sweeps, flags)
+        self._desc, self._keep = make_desc(problem, precision, max_cycles, pre_sweeps, post_sweeps, flags,
+                                           inner_cycles)
         self.stream = torch.cuda.current_stream() if stream is None else stream
         self._plan = ctypes.c_void_p()
         _check(load().pic_poisson_plan(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),

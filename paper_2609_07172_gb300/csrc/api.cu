@@ -41,6 +41,7 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
     if (d->max_cycles <= 0) d->max_cycles = 200;
     if (d->pre_sweeps < 0) d->pre_sweeps = 2;
     if (d->post_sweeps < 0) d->post_sweeps = 2;
+    if (d->inner_cycles <= 0) d->inner_cycles = 2;
     if (d->nr < 1 || d->nz < 1) {
         set_error("nr and nz must be >= 1 (got %d, %d)", d->nr, d->nz);
         return PIC_POISSON_EINVAL;
@@ -131,14 +132,22 @@ void build_level(const pic_poisson_desc &d, int nr, int nz, int nm, LevelHost &h
     if (nz == 1) h.tz = {4.0};
     else if (nz == 2) h.tz = {3.0, 3.0};
     else h.tz = {3.0, 2.0, 3.0};
-    h.diag.assign((size_t)h.ncls * nr * nm, 0.0);
-    h.invd.assign((size_t)h.ncls * nr * nm, 0.0);
+    const size_t nt = (size_t)h.ncls * nr * nm;
+    h.diag.assign(nt, 0.0);
+    h.invd.assign(nt, 0.0);
+    h.hw.assign(nt, 0.0);
+    h.he.assign(nt, 0.0);
+    h.hz.assign(nt, 0.0);
     for (int c = 0; c < h.ncls; ++c)
         for (int i = 0; i < nr; ++i)
             for (int m = 0; m < nm; ++m) {
+                const size_t t = ((size_t)c * nr + i) * nm + m;
                 const double dg = h.d0r[i] + h.tz[c] * h.cz[i] + lambda_m(d, m) * h.mu[i];
-                h.diag[((size_t)c * nr + i) * nm + m] = dg;
-                h.invd[((size_t)c * nr + i) * nm + m] = 1.0 / dg;
+                h.diag[t] = dg;
+                h.invd[t] = 1.0 / dg;
+                h.hw[t] = h.cw[i] / dg;
+                h.he[t] = h.ce[i] / dg;
+                h.hz[t] = h.cz[i] / dg;
             }
 }
 
@@ -180,7 +189,6 @@ struct pic_poisson_plan_s {
     double *hnorm = nullptr;            // pinned, 8 doubles
     double *stage_rho = nullptr, *stage_phi = nullptr;
     std::vector<cudaEvent_t> evs;
-    int inner_cycles = 2;               // FP32 V-cycles per FP64 defect correction
 };
 
 namespace pp {
@@ -197,22 +205,28 @@ void carve(pic_poisson_plan_s &P, Carver &c) {
         LevelDev<double> &v = P.dl[l];
         v.nr = h.nr; v.nz = h.nz; v.nm = nm; v.ncls = h.ncls;
         const size_t n = (size_t)h.nr * h.nz * nm;
+        const size_t nt = (size_t)h.ncls * h.nr * nm;
         v.u = c.take<double2>(n);
         v.b = c.take<double2>(n);
+        v.bh = c.take<double2>(n);
         v.cw = c.take<double>(h.nr); v.ce = c.take<double>(h.nr); v.cz = c.take<double>(h.nr);
-        v.invd = c.take<double>((size_t)h.ncls * h.nr * nm);
-        v.diag = c.take<double>((size_t)h.ncls * h.nr * nm);
+        v.invd = c.take<double>(nt);
+        v.diag = c.take<double>(nt);
+        v.hw = c.take<double>(nt); v.he = c.take<double>(nt); v.hz = c.take<double>(nt);
     }
     for (int l = 0; l < (int)P.fl.size(); ++l) {
         const LevelHost &h = P.lv[l];
         LevelDev<float> &v = P.fl[l];
         v.nr = h.nr; v.nz = h.nz; v.nm = nm; v.ncls = h.ncls;
         const size_t n = (size_t)h.nr * h.nz * nm;
+        const size_t nt = (size_t)h.ncls * h.nr * nm;
         v.u = c.take<float2>(n);
         v.b = c.take<float2>(n);
+        v.bh = c.take<float2>(n);
         v.cw = c.take<float>(h.nr); v.ce = c.take<float>(h.nr); v.cz = c.take<float>(h.nr);
-        v.invd = c.take<float>((size_t)h.ncls * h.nr * nm);
-        v.diag = c.take<float>((size_t)h.ncls * h.nr * nm);
+        v.invd = c.take<float>(nt);
+        v.diag = c.take<float>(nt);
+        v.hw = c.take<float>(nt); v.he = c.take<float>(nt); v.hz = c.take<float>(nt);
     }
     const LevelHost &hc = P.lv[L - 1];
     const size_t nf = (size_t)nm * hc.nz * hc.nr;
@@ -302,6 +316,9 @@ int upload(pic_poisson_plan_s &P) {
         to_dev(h.cz, P.dl[l].cz, tmp, st, err);
         to_dev(h.invd, P.dl[l].invd, tmp, st, err);
         to_dev(h.diag, P.dl[l].diag, tmp, st, err);
+        to_dev(h.hw, P.dl[l].hw, tmp, st, err);
+        to_dev(h.he, P.dl[l].he, tmp, st, err);
+        to_dev(h.hz, P.dl[l].hz, tmp, st, err);
     }
     for (size_t l = 0; l < P.fl.size(); ++l) {
         const LevelHost &h = P.lv[l];
@@ -310,6 +327,9 @@ int upload(pic_poisson_plan_s &P) {
         to_dev(h.cz, P.fl[l].cz, tmp, st, err);
         to_dev(h.invd, P.fl[l].invd, tmp, st, err);
         to_dev(h.diag, P.fl[l].diag, tmp, st, err);
+        to_dev(h.hw, P.fl[l].hw, tmp, st, err);
+        to_dev(h.he, P.fl[l].he, tmp, st, err);
+        to_dev(h.hz, P.fl[l].hz, tmp, st, err);
     }
     std::vector<double> V, e, piv, cpr;
     coarse_factors(P, V, e, piv, cpr);
@@ -410,11 +430,19 @@ struct Runner {
         phase.push_back(ph);
         return cudaEventRecord(P.evs[2 * nev++ + 1], P.stream);
     }
+    double bytes[PIC_POISSON_NPHASE] = {0}, flops[PIC_POISSON_NPHASE] = {0};
+    // algorithmic traffic and arithmetic of the launch just made
+    void account(int ph, double b, double f) {
+        bytes[ph] += b;
+        flops[ph] += f;
+    }
     int finish() {
         if (!info) return PIC_POISSON_OK;
         int tot = 0;
         for (int p = 0; p < PIC_POISSON_NPHASE; ++p) {
             info->launches_phase[p] += launches[p];
+            info->bytes_phase[p] += bytes[p];
+            info->flops_phase[p] += flops[p];
             tot += launches[p];
         }
         info->launches += tot;
@@ -447,31 +475,89 @@ int read_norms(pic_poisson_plan_s &P, int count, double *out) {
     return PIC_POISSON_OK;
 }
 
+// `sweeps` red-black sweeps on one level.  skip_first_red: the first sweep
+// starts at its black half, because the kernel that initialised the level
+// already performed the red half-sweep from a zero iterate.
+// Per-entry models: a complex entry of a level is
+// sizeof(V2<T>) bytes; FMA = 2 flops.
+template <class T> double vbytes(const LevelDev<T> &L) { return (double)L.nr * L.nz * L.nm * sizeof(V2<T>); }
+template <class T> double ventries(const LevelDev<T> &L) { return (double)L.nr * L.nz * L.nm; }
+
+// Half-sweep: read the other colour of u and this colour of b_hat, write this
+// colour of u (1.5 V); 4 operations (7 flops) per real component.
 template <class T>
-int smooth_level(Runner &R, const LevelDev<T> &L, int sweeps) {
+int smooth_level(Runner &R, const LevelDev<T> &L, int sweeps, bool skip_first_red, int phase) {
     for (int s = 0; s < sweeps; ++s) {
-        RUN(R, PIC_POISSON_PHASE_SMOOTH, launch_smooth(L, 0, R.P.stream));
-        RUN(R, PIC_POISSON_PHASE_SMOOTH, launch_smooth(L, 1, R.P.stream));
+        for (int color = (s == 0 && skip_first_red) ? 1 : 0; color < 2; ++color) {
+            RUN(R, phase, launch_smooth(L, color, R.P.stream));
+            R.account(phase, 1.5 * vbytes(L), 14.0 * 0.5 * ventries(L));
+        }
     }
     return PIC_POISSON_OK;
 }
 
-// Coarse-grid correction below level `top` of hierarchy `lv`: levels top+1 .. L-1
-// are assumed to hold the restricted residual (b) and a zero iterate (u).
+// Residual + restriction from fine level F into C: reads u (V_F) and b of the
+// evaluated cells, writes coarse b (and b_hat, u when init > 0); 18 flops per
+// evaluated complex entry (+4 with norms), 2-4 per coarse entry.
+template <class T>
+void account_restrict(Runner &R, const LevelDev<T> &F, bool red_only, int init, bool norms) {
+    const double frac = red_only ? 0.5 : 1.0;
+    const double b = vbytes(F) * (1.0 + frac) + 0.25 * vbytes(F) * (init > 0 ? 3.0 : 1.0);
+    const double f = frac * ventries(F) * (18.0 + (norms ? 4.0 : 0.0)) + 0.25 * ventries(F) * (init > 0 ? 4.0 : 2.0);
+    R.account(PIC_POISSON_PHASE_RESTRICT, b, f);
+}
+
+// Prolongation + correction: reads the coarse correction (V_F / 4), reads and
+// writes u of the corrected cells; 16 flops per corrected complex entry.
+template <class T>
+void account_prolong(Runner &R, const LevelDev<T> &F, bool black_only) {
+    const double frac = black_only ? 0.5 : 1.0;
+    R.account(PIC_POISSON_PHASE_PROLONG, 0.25 * vbytes(F) + 2.0 * frac * vbytes(F), 16.0 * frac * ventries(F));
+}
+
+// Separable coarsest solve: reads b, writes u, reads the Thomas factors;
+// 2 dense axial transforms (4 nz flops per real component each) + Thomas.
+template <class T>
+void account_coarse(Runner &R, const LevelDev<T> &L) {
+    const double fac = 2.0 * L.nm * L.nz * L.nr * sizeof(T);
+    R.account(PIC_POISSON_PHASE_COARSE, 2.0 * vbytes(L) + fac, ventries(L) * (16.0 * L.nz + 20.0));
+}
+
+// Batched real FFT of one length-nt column: ~5 (M/2) log2 M * 2 flops for the
+// complex length-M transform plus ~14 per unpacked mode (M = nt / 2).
+double fft_flops(int nt) {
+    const double M = nt / 2;
+    return 5.0 * M * std::log2(std::max(M, 1.0)) + 14.0 * (M + 1);
+}
+
+// What the restriction from level l writes into level l+1 of an L-level
+// hierarchy: only b into the coarsest level (solved directly); otherwise b_hat
+// and the iterate, which is the first red half-sweep from zero when the
+// coarse level is pre-smoothed.
+int restrict_init(int l, int L, int pre) { return (l + 1 == L - 1) ? 0 : (pre > 0 ? 2 : 1); }
+
+// Coarse-grid correction below level `top`: level top+1 holds the restricted
+// residual and its initialised iterate; returns with the correction
+// prolongated into level `top` and post-smoothed there.
 template <class T>
 int descend_ascend(Runner &R, std::vector<LevelDev<T>> &lv, const CoarseDev<T> &cd, int top) {
     pic_poisson_plan_s &P = R.P;
-    const int L = (int)lv.size();
+    const int L = (int)lv.size(), pre = P.d.pre_sweeps, post = P.d.post_sweeps;
     for (int l = top + 1; l < L - 1; ++l) {
-        int rc = smooth_level(R, lv[l], P.d.pre_sweeps);
+        int rc = smooth_level(R, lv[l], pre, pre > 0, PIC_POISSON_PHASE_SMOOTH_COARSE);
         if (rc) return rc;
         RUN(R, PIC_POISSON_PHASE_RESTRICT,
-            launch_residual_restrict(lv[l], lv[l + 1], P.d.ntheta, (double *)nullptr, (int *)nullptr, P.stream));
+            launch_residual_restrict(lv[l], lv[l + 1], P.d.ntheta, pre > 0, restrict_init(l, L, pre),
+                                     (double *)nullptr, (int *)nullptr, P.stream));
+        account_restrict(R, lv[l], pre > 0, restrict_init(l, L, pre), false);
     }
     RUN(R, PIC_POISSON_PHASE_COARSE, launch_coarse(lv[L - 1], cd, P.stream));
+    account_coarse(R, lv[L - 1]);
     for (int l = L - 2; l >= top; --l) {
-        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_prolong(lv[l], lv[l + 1], P.stream));
-        int rc = smooth_level(R, lv[l], P.d.post_sweeps);
+        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_prolong(lv[l], lv[l + 1], post > 0, P.stream));
+        account_prolong(R, lv[l], post > 0);
+        int rc = smooth_level(R, lv[l], post, false,
+                              l == 0 ? PIC_POISSON_PHASE_SMOOTH : PIC_POISSON_PHASE_SMOOTH_COARSE);
         if (rc) return rc;
     }
     return PIC_POISSON_OK;
@@ -499,12 +585,15 @@ struct StopRule {
 int mg_fp64(Runner &R, double tol, double bnorm2, pic_poisson_info *info, int *status) {
     pic_poisson_plan_s &P = R.P;
     LevelDev<double> &F = P.dl[0];
+    const int pre = P.d.pre_sweeps;
     StopRule stop{tol};
     double rel = 1.0;
     int cycles = 0, nb = 0;
     if (P.L == 1) {
         RUN(R, PIC_POISSON_PHASE_COARSE, launch_coarse(F, P.cd, P.stream));
+        account_coarse(R, F);
         RUN(R, PIC_POISSON_PHASE_RESTRICT, launch_residual(F, (double2 *)nullptr, P.d.ntheta, P.partials, &nb, P.stream));
+        R.account(PIC_POISSON_PHASE_RESTRICT, 2.0 * vbytes(F), 22.0 * ventries(F));
         RUN(R, PIC_POISSON_PHASE_NORM, launch_sum(P.partials, nb, P.dnorm + 1, P.stream));
         double nn[2];
         int rc = read_norms(P, 2, nn);
@@ -515,10 +604,12 @@ int mg_fp64(Runner &R, double tol, double bnorm2, pic_poisson_info *info, int *s
                                        : ((tol > 0 && rel > tol) ? PIC_POISSON_ENOTCONVERGED : PIC_POISSON_OK);
     } else {
         for (;;) {
-            int rc = smooth_level(R, F, P.d.pre_sweeps);
+            int rc = smooth_level(R, F, pre, false, PIC_POISSON_PHASE_SMOOTH);
             if (rc) return rc;
             RUN(R, PIC_POISSON_PHASE_RESTRICT,
-                launch_residual_restrict(F, P.dl[1], P.d.ntheta, P.partials, &nb, P.stream));
+                launch_residual_restrict(F, P.dl[1], P.d.ntheta, pre > 0, restrict_init(0, P.L, pre), P.partials,
+                                         &nb, P.stream));
+            account_restrict(R, F, pre > 0, restrict_init(0, P.L, pre), true);
             RUN(R, PIC_POISSON_PHASE_NORM, launch_sum(P.partials, nb, P.dnorm + 1, P.stream));
             double nn[2];
             rc = read_norms(P, 2, nn);
@@ -548,21 +639,102 @@ int mg_fp64(Runner &R, double tol, double bnorm2, pic_poisson_info *info, int *s
     return PIC_POISSON_OK;
 }
 
+// Power of two closest to 1 / sqrt(mean square): scales the FP32 correction
+// problem to O(1) values exactly (no rounding from the scale itself).
+double pow2_scale(double sumsq, double count) {
+    const double rms = std::sqrt(sumsq / std::max(count, 1.0));
+    if (!(rms > 0) || !std::isfinite(rms)) return 1.0;
+    int ex = 0;
+    std::frexp(rms, &ex);
+    return std::ldexp(1.0, -ex);
+}
+
+// Mixed precision: FP64 defect correction x <- x + A^{-1}_FP32 (b - A x).
+// Each outer step forms the FP64 residual of the current iterate (the
+// convergence test), solves the correction equation approximately with
+// inner_cycles FP32 V-cycles on the FP32 hierarchy, and adds it in FP64.
+int mg_mixed(Runner &R, double tol, double bnorm2, pic_poisson_info *info, int *status) {
+    pic_poisson_plan_s &P = R.P;
+    LevelDev<double> &D = P.dl[0];
+    std::vector<LevelDev<float>> &S = P.fl;
+    const int pre = P.d.pre_sweeps, L = P.L;
+    const double count = (double)D.nr * D.nz * P.d.ntheta;
+    StopRule stop{tol};
+    double rel = 1.0, sigma = pow2_scale(bnorm2, count);
+    int cycles = 0, outer = 0, nb = 0;
+    for (;;) {
+        RUN(R, PIC_POISSON_PHASE_DEFECT,
+            launch_defect(D, S[0], sigma, P.d.ntheta, L > 1 && pre > 0, P.partials, &nb, P.stream));
+        R.account(PIC_POISSON_PHASE_DEFECT, 2.0 * vbytes(D) + 3.0 * vbytes(S[0]), 26.0 * ventries(D));
+        RUN(R, PIC_POISSON_PHASE_NORM, launch_sum(P.partials, nb, P.dnorm + 1, P.stream));
+        double nn[2];
+        int rc = read_norms(P, 2, nn);
+        if (rc) return rc;
+        rel = std::sqrt(nn[1] / bnorm2);
+        if (!std::isfinite(rel)) {
+            *status = PIC_POISSON_ENONFINITE;
+            break;
+        }
+        if (stop.done(rel)) {
+            *status = PIC_POISSON_OK;
+            break;
+        }
+        if (cycles >= P.d.max_cycles) {
+            *status = PIC_POISSON_ENOTCONVERGED;
+            break;
+        }
+        if (L == 1) {
+            RUN(R, PIC_POISSON_PHASE_COARSE, launch_coarse(S[0], P.cf, P.stream));
+            account_coarse(R, S[0]);
+            ++cycles;
+        } else {
+            for (int c = 0; c < P.d.inner_cycles; ++c) {
+                rc = smooth_level(R, S[0], pre, c == 0 && pre > 0, PIC_POISSON_PHASE_SMOOTH);
+                if (rc) return rc;
+                RUN(R, PIC_POISSON_PHASE_RESTRICT,
+                    launch_residual_restrict(S[0], S[1], P.d.ntheta, pre > 0, restrict_init(0, L, pre),
+                                             (double *)nullptr, (int *)nullptr, P.stream));
+                account_restrict(R, S[0], pre > 0, restrict_init(0, L, pre), false);
+                rc = descend_ascend(R, S, P.cf, 0);
+                if (rc) return rc;
+                ++cycles;
+            }
+        }
+        RUN(R, PIC_POISSON_PHASE_DEFECT, launch_update(D, S[0], 1.0 / sigma, P.stream));
+        R.account(PIC_POISSON_PHASE_DEFECT, 2.0 * vbytes(D) + vbytes(S[0]), 4.0 * ventries(D));
+        ++outer;
+        sigma = pow2_scale(nn[1] / 2.0, count);
+    }
+    if (info) {
+        info->cycles = cycles;
+        info->outer_iterations = outer;
+        info->rel_res = rel;
+    }
+    return PIC_POISSON_OK;
+}
+
 int solve_dev(pic_poisson_plan_s &P, const double *rho, double *phi, double tol, pic_poisson_info *info) {
     Runner R(P, info);
     const pic_poisson_desc &d = P.d;
     const LevelHost &h0 = P.lv[0];
     LevelDev<double> &F = P.dl[0];
+    const bool mixed = d.precision == PIC_POISSON_MIXED;
     const size_t n0 = (size_t)h0.nr * h0.nz * P.nm;
     int nb = 0;
     RUN(R, PIC_POISSON_PHASE_FORWARD,
-        launch_forward(rho, F.b, h0.nr, d.ntheta, h0.nz, P.fft, P.s0, P.bD0, P.partials, &nb, P.stream));
+        launch_forward(rho, F.b, h0.nr, d.ntheta, h0.nz, P.fft, P.s0, P.bD0, P.partials, &nb,
+                       mixed ? (double2 *)nullptr : F.bh, F.invd, F.ncls, P.stream));
+    const double X = (double)h0.nr * h0.nz * d.ntheta * sizeof(double);
+    const double columns = (double)h0.nr * h0.nz;
+    R.account(PIC_POISSON_PHASE_FORWARD, X + (mixed ? 1.0 : 2.0) * vbytes(F), columns * fft_flops(d.ntheta));
     RUN(R, PIC_POISSON_PHASE_NORM, launch_sum(P.partials, nb, P.dnorm, P.stream));
     const bool guess = d.flags & PIC_POISSON_USE_INITIAL_GUESS;
     if (guess) {
         RUN(R, PIC_POISSON_PHASE_FORWARD,
             launch_forward(phi, F.u, h0.nr, d.ntheta, h0.nz, P.fft, (const double *)nullptr,
-                           (const double *)nullptr, (double *)nullptr, (int *)nullptr, P.stream));
+                           (const double *)nullptr, (double *)nullptr, (int *)nullptr, (double2 *)nullptr,
+                           (const double *)nullptr, 0, P.stream));
+        R.account(PIC_POISSON_PHASE_FORWARD, X + vbytes(F), columns * fft_flops(d.ntheta));
     } else {
         PP_CUDA(cudaMemsetAsync(F.u, 0, n0 * sizeof(double2), P.stream));
     }
@@ -582,17 +754,21 @@ int solve_dev(pic_poisson_plan_s &P, const double *rho, double *phi, double tol,
         if (guess) {
             RUN(R, PIC_POISSON_PHASE_RESTRICT,
                 launch_residual(F, (double2 *)nullptr, d.ntheta, P.partials, &nb, P.stream));
+            R.account(PIC_POISSON_PHASE_RESTRICT, 2.0 * vbytes(F), 22.0 * ventries(F));
             RUN(R, PIC_POISSON_PHASE_NORM, launch_sum(P.partials, nb, P.dnorm + 1, P.stream));
             double r2[2];
             rc = read_norms(P, 2, r2);
             if (rc) return rc;
             if (info) info->rel_res0 = std::sqrt(r2[1] / bnorm2);
         }
-        rc = mg_fp64(R, tol, bnorm2, info, &status);
+        rc = mixed ? mg_mixed(R, tol, bnorm2, info, &status) : mg_fp64(R, tol, bnorm2, info, &status);
         if (rc) return rc;
     }
     if (status != PIC_POISSON_ENONFINITE)
+    {
         RUN(R, PIC_POISSON_PHASE_INVERSE, launch_inverse(F.u, phi, h0.nr, d.ntheta, h0.nz, P.fft, P.stream));
+        R.account(PIC_POISSON_PHASE_INVERSE, X + vbytes(F), columns * fft_flops(d.ntheta));
+    }
     rc = R.finish();
     if (rc) return rc;
     if (status == PIC_POISSON_ENONFINITE) set_error("non-finite right-hand side or residual");
@@ -793,7 +969,7 @@ int pic_poisson_forward(pic_poisson_plan_t plan, const double *rho_dev, double *
     }
     const pic_poisson_plan_s &P = *plan;
     cudaError_t err = launch_forward(rho_dev, (double2 *)bhat_dev, P.d.nr, P.d.ntheta, P.d.nz, P.fft, P.s0,
-                                     P.bD0, nullptr, nullptr, P.stream);
+                                     P.bD0, nullptr, nullptr, nullptr, nullptr, 0, P.stream);
     if (err != cudaSuccess) {
         set_error("forward transform launch failed: %s", cudaGetErrorString(err));
         return PIC_POISSON_ECUDA;

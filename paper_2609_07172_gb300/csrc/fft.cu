@@ -79,7 +79,8 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 __global__ void __launch_bounds__(FFT_THREADS)
 k_forward(const double *__restrict__ rho, double2 *__restrict__ bhat, int nr, int nt, int nz,
           const double2 *__restrict__ tw, const double2 *__restrict__ tw2, const double *__restrict__ s,
-          const double *__restrict__ bD, double *__restrict__ partials, int log2M) {
+          const double *__restrict__ bD, double *__restrict__ partials, int log2M, double2 *__restrict__ bh,
+          const double *__restrict__ invd, int ncls) {
     extern __shared__ double2 sm[];
     const int M = nt >> 1, nm = M + 1;
     double2 *buf = sm;              // [M][LD]
@@ -133,6 +134,17 @@ k_forward(const double *__restrict__ rho, double2 *__restrict__ bhat, int nr, in
     const int ncols = min(TI, nr - i0);
     double2 *dst = bhat + ((size_t)k * nr + i0) * nm;
     for (int f = threadIdx.x; f < ncols * nm; f += blockDim.x) dst[f] = outb[f];
+    if (bh) {
+        // b_hat = b / diag for the smoother (row class of plane k, cells i0.., all modes)
+        const int cls = k == 0 ? 0 : (k == nz - 1 ? ncls - 1 : 1);
+        const double *inv = invd + ((size_t)cls * nr + i0) * nm;
+        double2 *dh = bh + ((size_t)k * nr + i0) * nm;
+        for (int f = threadIdx.x; f < ncols * nm; f += blockDim.x) {
+            const double2 x = outb[f];
+            const double v = inv[f];
+            dh[f] = make_double2(x.x * v, x.y * v);
+        }
+    }
     if (partials) {
         const double tot = block_sum(acc, red);
         if (threadIdx.x == 0) partials[blockIdx.x] = tot;
@@ -201,13 +213,15 @@ size_t fft_smem(int nt) {
 }  // namespace
 
 cudaError_t launch_forward(const double *rho, double2 *bhat, int nr, int nt, int nz, const FFTDev &f,
-                           const double *s, const double *bD, double *partials, int *nblocks, cudaStream_t st) {
+                           const double *s, const double *bD, double *partials, int *nblocks, double2 *bh,
+                           const double *invd, int ncls, cudaStream_t st) {
     const int tiles = (nr + TI - 1) / TI;
     const int blocks = nz * tiles;
     const size_t smem = fft_smem(nt);
     cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_forward<<<blocks, FFT_THREADS, smem, st>>>(rho, bhat, nr, nt, nz, (const double2 *)f.tw,
-                                                 (const double2 *)f.tw2, s, bD, partials, ilog2(nt / 2));
+                                                 (const double2 *)f.tw2, s, bD, partials, ilog2(nt / 2), bh,
+                                                 invd, ncls);
     if (nblocks) *nblocks = blocks;
     return cudaGetLastError();
 }

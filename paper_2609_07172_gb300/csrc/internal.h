@@ -57,14 +57,17 @@ struct LevelHost {
     std::vector<double> cw, ce, cz, d0r, mu;   // per radial index
     std::vector<double> tz;       // per class
     std::vector<double> invd, diag;             // [ncls][nr][nm]
+    std::vector<double> hw, he, hz;             // [ncls][nr][nm]: cw, ce, cz divided by diag
 };
 
 template <class T> struct LevelDev {
     int nr, nz, nm, ncls;
     const T *cw, *ce, *cz;        // [nr]
     const T *invd, *diag;         // [ncls][nr][nm]
+    const T *hw, *he, *hz;        // [ncls][nr][nm] off-diagonal conductances / diag
     V2<T> *u;                     // iterate / correction, [nz][nr][nm]
     V2<T> *b;                     // right-hand side, [nz][nr][nm]
+    V2<T> *bh;                    // right-hand side / diag, [nz][nr][nm]
 };
 
 // Coarsest level: separable direct solve (z eigenbasis, tridiagonal in r).
@@ -84,25 +87,31 @@ struct FFTDev {
     const double *tw2;            // [M+1] e^{-2 pi i m / N_theta}
 };
 
+// bh (may be null): also write bhat / diag using the level-0 table invd [ncls][nr][nm].
 cudaError_t launch_forward(const double *rho, double2 *bhat, int nr, int nt, int nz, const FFTDev &f,
                            const double *s, const double *bD, double *partials, int *nblocks,
-                           cudaStream_t st);
+                           double2 *bh, const double *invd, int ncls, cudaStream_t st);
 cudaError_t launch_inverse(const double2 *uhat, double *phi, int nr, int nt, int nz, const FFTDev &f,
                            cudaStream_t st);
 
 template <class T>
 cudaError_t launch_smooth(const LevelDev<T> &L, int color, cudaStream_t st);
+// red_only: residual of the red fine cells only (valid right after a black half-sweep).
+// init: 0 = coarse b only; 1 = also b_hat and u = 0; 2 = also b_hat and u = (red ? b_hat : 0).
 template <class T>
-cudaError_t launch_residual_restrict(const LevelDev<T> &L, const LevelDev<T> &C, int nt, double *partials,
-                                     int *nblocks, cudaStream_t st);
+cudaError_t launch_residual_restrict(const LevelDev<T> &L, const LevelDev<T> &C, int nt, bool red_only, int init,
+                                     double *partials, int *nblocks, cudaStream_t st);
 template <class T>
 cudaError_t launch_residual(const LevelDev<T> &L, V2<T> *r, int nt, double *partials, int *nblocks,
                             cudaStream_t st);
 template <class T>
-cudaError_t launch_prolong(const LevelDev<T> &L, const LevelDev<T> &C, cudaStream_t st);
+cudaError_t launch_prolong(const LevelDev<T> &L, const LevelDev<T> &C, bool black_only, cudaStream_t st);
 template <class T>
 cudaError_t launch_coarse(const LevelDev<T> &L, const CoarseDev<T> &C, cudaStream_t st);
 
+cudaError_t launch_defect(const LevelDev<double> &D, const LevelDev<float> &S, double sigma, int nt, bool init_red,
+                          double *partials, int *nblocks, cudaStream_t st);
+cudaError_t launch_update(const LevelDev<double> &D, const LevelDev<float> &S, double inv_sigma, cudaStream_t st);
 cudaError_t launch_sum(const double *partials, int n, double *out, cudaStream_t st);
 
 cudaError_t measure_fma(cudaStream_t st, double *fp64_gflops, double *fp32_gflops);

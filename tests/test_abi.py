@@ -40,9 +40,9 @@ def test_query_hierarchy_paper_grid():
     assert q["nr"] == [512, 256, 128, 64, 32]
     assert q["nz"] == [400, 200, 100, 50, 25]
     assert q["n_modes"] == 65
-    # two complex FP64 vectors on every level dominate the workspace
+    # three complex FP64 vectors (u, b, b / diag) on every level dominate the workspace
     v0 = 512 * 400 * 65 * 16
-    assert 2 * v0 < q["workspace_bytes"] < 2 * v0 * 1.5
+    assert 3 * v0 < q["workspace_bytes"] < 3 * v0 * 1.5
 
 
 def test_query_mixed_has_fp32_levels():

@@ -102,6 +102,21 @@ def test_c0_discrete_manufactured():
     assert rel_l2(phi.cpu().numpy(), phi_ex) <= FP64_TOL
 
 
+@pytest.mark.parametrize("sweeps", [(1, 1), (0, 2), (2, 0), (3, 1), (1, 0), (2, 2)])
+def test_sweep_schedules_match_oracle(sweeps):
+    """Every smoothing schedule (including the red-only residual, black-only
+    prolongation and fused first-red variants and their full counterparts)
+    converges to the oracle's solution."""
+    p = with_bias_walls(W.annulus(64, 32, 48))
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=12)
+    ref, _ = oracle.solve3d(g, rho, tol=1e-15)
+    with Plan(p, pre_sweeps=sweeps[0], post_sweeps=sweeps[1]) as plan:
+        phi, info = plan.solve(dev(rho), tol=0.0)
+    assert info["status"] == B.OK
+    assert rel_l2(phi.cpu().numpy(), ref) <= FP64_TOL, info
+
+
 @pytest.mark.parametrize("tol", [1e-6, 1e-10])
 def test_stop_at_tolerance_reports_true_residual(tol):
     p = with_bias_walls(W.annulus(64, 32, 48))
