@@ -59,7 +59,10 @@ extern "C" {
 
 /* flags */
 #define PIC_POISSON_USE_INITIAL_GUESS 1u  /* phi_dev is read as the initial iterate */
-#define PIC_POISSON_PROFILE 2u            /* time every kernel class with CUDA events */
+#define PIC_POISSON_PROFILE 2u            /* time every kernel class with CUDA events (host-driven loop) */
+#define PIC_POISSON_GRAPH 4u              /* run each solve as one CUDA graph: the convergence loop is a
+                                             device-side while node (captured on the first solve; ignored
+                                             together with PIC_POISSON_PROFILE) */
 
 /* kernel classes, indices into pic_poisson_info.ms_phase / launches_phase */
 #define PIC_POISSON_PHASE_FORWARD 0   /* azimuthal rFFT + right-hand side */
@@ -74,6 +77,7 @@ extern "C" {
 #define PIC_POISSON_NPHASE 9
 
 #define PIC_POISSON_MAX_LEVELS 16
+#define PIC_POISSON_MAX_BATCH 64      /* problems per batched plan */
 
 typedef struct pic_poisson_plan_s *pic_poisson_plan_t;
 
@@ -100,7 +104,8 @@ typedef struct {
     int cycles;                /* coarse-grid corrections applied */
     int outer_iterations;      /* FP64 defect corrections (mixed precision) */
     int launches;              /* kernels this call launched */
-    double rel_res0;           /* ||b - A phi_0|| / ||b|| of the initial iterate */
+    double rel_res0;           /* relative residual at the first convergence test: of the initial iterate
+                                  (mixed) or after the first pre-smoothing (FP64) */
     double rel_res;            /* ||b - A phi|| / ||b|| of the returned iterate (3-D system, Parseval) */
     double ms_phase[PIC_POISSON_NPHASE];   /* device ms per kernel class (PROFILE flag) */
     int launches_phase[PIC_POISSON_NPHASE];/* launches per kernel class */
@@ -143,6 +148,15 @@ int pic_poisson_cell_coeffs(const pic_poisson_desc *desc, int i, int k, double *
  */
 int pic_poisson_plan(const pic_poisson_desc *desc, void *stream, pic_poisson_plan_t *out);
 
+/*
+ * Build one plan for n independent problems (1 <= n <= PIC_POISSON_MAX_BATCH)
+ * of different sizes and azimuthal resolutions.  Every kernel launch of a
+ * solve covers all problems at once (per launch, each problem owns a range of
+ * blocks), so n problems cost one launch per kernel and level, not n.  The
+ * problems must share precision, max_cycles, sweeps, inner_cycles and flags.
+ */
+int pic_poisson_plan_batch(const pic_poisson_desc *descs, int n, void *stream, pic_poisson_plan_t *out);
+
 /* Replace the plan's stream (later calls enqueue there). */
 int pic_poisson_set_stream(pic_poisson_plan_t plan, void *stream);
 
@@ -152,11 +166,26 @@ int pic_poisson_set_stream(pic_poisson_plan_t plan, void *stream);
  * three-dimensional system, ||b - A phi||_2 / ||b||_2, is <= tol (tol <= 0:
  * until the residual stops decreasing, the rounding floor).  The residual is
  * measured in mode space with Parseval weights 1 (m = 0, N/2) and 2 (others).
- * Synchronises the plan's stream once per cycle to test convergence.
+ * The convergence test runs on the device; without PIC_POISSON_GRAPH the host
+ * reads its flag after every test (one small copy and stream synchronisation
+ * per cycle), with it the whole solve is one graph launch.  For a plan with
+ * several problems use pic_poisson_solve_batch (this call returns EINVAL).
  * rho_dev and phi_dev may not alias.  `info` may be NULL.
  */
 int pic_poisson_solve(pic_poisson_plan_t plan, const double *rho_dev, double *phi_dev, double tol,
                       pic_poisson_info *info);
+
+/*
+ * Solve every problem of a batched plan: rho_dev[p] -> phi_dev[p] (host
+ * arrays of n device pointers, layouts as for pic_poisson_solve).  Iterates
+ * until every problem meets tol (problems that already did keep being
+ * iterated, so each returned phi has at least the reported accuracy).  infos
+ * (n entries, may be NULL): per-problem status, cycles and residuals; the
+ * timing, byte and launch counters are those of the whole batched solve.
+ * Returns ENONFINITE if any problem has it, else ENOTCONVERGED if any, else OK.
+ */
+int pic_poisson_solve_batch(pic_poisson_plan_t plan, const double *const *rho_dev, double *const *phi_dev,
+                            double tol, pic_poisson_info *infos);
 
 /*
  * As pic_poisson_solve with host buffers (pinned or pageable): copies rho_host
@@ -220,7 +249,10 @@ int pic_poisson_mode_residual_noalloc(const pic_poisson_desc *desc, const double
                                       const double *bhat_dev, double *rhat_dev, double *rel_res_dev,
                                       void *stream);
 
-/* Release everything the plan owns.  NULL is accepted. */
+/* Release everything the plan owns.  NULL is accepted.
+ * The stage calls pic_poisson_forward, pic_poisson_inverse,
+ * pic_poisson_mode_residual and pic_poisson_solve_host need a single-problem
+ * plan (EINVAL otherwise). */
 int pic_poisson_destroy(pic_poisson_plan_t plan);
 
 /* Description of the most recent failure on this thread ("" if none). */

@@ -14,13 +14,15 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE = 0, 1, 2, 3, 4, 5
 FP64, MIXED = 0, 1
-USE_INITIAL_GUESS, PROFILE = 1, 2
+USE_INITIAL_GUESS, PROFILE, GRAPH = 1, 2, 4
+MAX_BATCH = 64
 PHASES = ("forward", "smooth", "smooth_coarse", "restrict", "coarse", "prolong", "norm", "inverse", "defect")
 MAX_LEVELS = 16
 NPHASE = len(PHASES)
 
 EXPORTS = (
-    "pic_poisson_query", "pic_poisson_cell_coeffs", "pic_poisson_plan", "pic_poisson_set_stream",
+    "pic_poisson_query", "pic_poisson_cell_coeffs", "pic_poisson_plan", "pic_poisson_plan_batch",
+    "pic_poisson_set_stream", "pic_poisson_solve_batch",
     "pic_poisson_solve", "pic_poisson_solve_host", "pic_poisson_forward", "pic_poisson_inverse",
     "pic_poisson_mode_residual", "pic_poisson_destroy", "pic_poisson_last_error",
     "pic_poisson_measure_fma_peaks", "pic_poisson_mode_residual_noalloc",
@@ -103,6 +105,8 @@ def load(build_if_missing: bool = True):
         "pic_poisson_query": ([vp, vp], ip),
         "pic_poisson_cell_coeffs": ([vp, ip, ip, vp], ip),
         "pic_poisson_plan": ([vp, vp, vp], ip),
+        "pic_poisson_plan_batch": ([vp, ip, vp, vp], ip),
+        "pic_poisson_solve_batch": ([vp, vp, vp, dp, vp], ip),
         "pic_poisson_set_stream": ([vp, vp], ip),
         "pic_poisson_solve": ([vp, vp, vp, dp, vp], ip),
         "pic_poisson_solve_host": ([vp, vp, vp, dp, vp], ip),
@@ -195,10 +199,11 @@ class Plan:
     """A solver plan for one problem (wraps pic_poisson_plan / solve / destroy)."""
 
     def __init__(self, problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
-                 profile=False, initial_guess=False, stream=None, inner_cycles=0):
+                 profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False):
         import torch
         self.problem = problem
-        flags = (PROFILE if profile else 0) | (USE_INITIAL_GUESS if initial_guess else 0)
+        flags = ((PROFILE if profile else 0) | (USE_INITIAL_GUESS if initial_guess else 0)
+                 | (GRAPH if graph else 0))
         self._desc, self._keep = make_desc(problem, precision, max_cycles, pre_sweeps, post_sweeps, flags,
                                            inner_cycles)
         self.stream = torch.cuda.current_stream() if stream is None else stream
@@ -280,3 +285,58 @@ class Plan:
             self._plan, _dev_ptr(uhat, self.mode_shape, "uhat"), _dev_ptr(bhat, self.mode_shape, "bhat"),
             _dev_ptr(r, self.mode_shape, "rhat") if want_r else None, ctypes.byref(rel)))
         return r, rel.value
+
+
+class BatchPlan:
+    """One plan for several independent problems (wraps pic_poisson_plan_batch / solve_batch)."""
+
+    def __init__(self, problems, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
+                 profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False):
+        import torch
+        self.problems = list(problems)
+        n = len(self.problems)
+        if not 1 <= n <= MAX_BATCH:
+            raise ValueError(f"batch of {n} problems; 1..{MAX_BATCH} supported")
+        flags = ((PROFILE if profile else 0) | (USE_INITIAL_GUESS if initial_guess else 0)
+                 | (GRAPH if graph else 0))
+        self._descs = (Desc * n)()
+        self._keep = []
+        for i, p in enumerate(self.problems):
+            d, keep = make_desc(p, precision, max_cycles, pre_sweeps, post_sweeps, flags, inner_cycles)
+            self._descs[i] = d
+            self._keep.extend(keep)
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        self._plan = ctypes.c_void_p()
+        _check(load().pic_poisson_plan_batch(self._descs, n, ctypes.c_void_p(self.stream.cuda_stream),
+                                             ctypes.byref(self._plan)))
+        self.shapes = [(p.nz, p.ntheta, p.nr) for p in self.problems]
+
+    def close(self):
+        if self._plan:
+            load().pic_poisson_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, rhos, phis=None, tol=1e-10):
+        """Solve all problems; returns (phis, [info dicts]).  Raises except for OK / ENOTCONVERGED."""
+        import torch
+        n = len(self.problems)
+        if phis is None:
+            phis = [torch.empty(sh, dtype=torch.float64, device=r.device) for sh, r in zip(self.shapes, rhos)]
+        rp = (ctypes.c_void_p * n)(*[_dev_ptr(r, sh, "rho").value for r, sh in zip(rhos, self.shapes)])
+        fp = (ctypes.c_void_p * n)(*[_dev_ptr(f, sh, "phi").value for f, sh in zip(phis, self.shapes)])
+        infos = (Info * n)()
+        st = load().pic_poisson_solve_batch(self._plan, rp, fp, float(tol), infos)
+        _check(st, allow=(OK, ENOTCONVERGED))
+        return phis, [i.as_dict() for i in infos]

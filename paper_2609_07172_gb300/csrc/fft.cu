@@ -6,21 +6,22 @@
 // Inverse (Sec. 3.1, inverse transform, no scale), with conjugate symmetry:
 //   phi_j = sum_{m=0}^{N-1} phihat_m e^{2 pi i m j / N}
 //
-// Each CTA owns one axial plane k and TI = 32 consecutive radial columns; lane
-// l of every warp works on column i0 + l, so global loads of rho (r fastest)
-// and shared-memory accesses are contiguous across a warp.  A real sequence of
-// length N is packed as z_n = x_2n + i x_2n+1 (n < M = N/2), transformed by an
-// in-place radix-2 decimation-in-time FFT of length M in shared memory (bit-
-// reversed load), and unpacked into the N/2+1 half-spectrum.  The CTA's output
-// is the contiguous mode-layout block of cells (k, i0 .. i0+TI-1), staged in
-// shared memory and stored with coalesced 16-byte writes.
+// Each CTA owns one axial plane k of one problem and TI = 32 consecutive radial
+// columns; lane l of every warp works on column i0 + l, so global loads of rho
+// (r fastest) and shared-memory accesses are contiguous across a warp.  A real
+// sequence of length N is packed as z_n = x_2n + i x_2n+1 (n < M = N/2),
+// transformed by an in-place radix-2 decimation-in-time FFT of length M in
+// shared memory (bit-reversed load), and unpacked into the N/2+1 half-spectrum.
+// The CTA's output is the contiguous mode-layout block of cells
+// (k, i0 .. i0+TI-1), staged in shared memory and stored with coalesced writes.
+// Problems of a batch may differ in size and N_theta; the dynamic shared
+// memory is sized for the largest.
 #include "internal.h"
 
 namespace pp {
 namespace {
 
-constexpr int TI = 32;
-constexpr int FFT_THREADS = 256;
+constexpr int TI = FFT_TI;
 constexpr int LD = TI + 1;   // padded row of the transform buffer (conflict-free 16-byte lanes)
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -34,8 +35,19 @@ __device__ __forceinline__ int bitrev(int n, int log2M) {
     return log2M == 0 ? 0 : (int)(__brev((unsigned)n) >> (32 - log2M));
 }
 
+__device__ __forceinline__ int find_problem(const unsigned *__restrict__ start, int n, unsigned blk) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (start[mid] <= blk) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // In-place radix-2 DIT FFT of length M on buf[M][LD] (bit-reversed input).
-// inverse: conjugated twiddles (e^{+2 pi i t / M}).
+// INVERSE: conjugated twiddles (e^{+2 pi i t / M}).  Twiddles w = 1 (pos = 0)
+// and w = -i / +i (pos = h/2) need no multiplication.
 template <bool INVERSE>
 __device__ __forceinline__ void fft_stages(double2 *buf, const double2 *__restrict__ tw, int M, int lane, int warp,
                                            int nw) {
@@ -52,6 +64,8 @@ __device__ __forceinline__ void fft_stages(double2 *buf, const double2 *__restri
             double2 t;
             if (pos == 0) {
                 t = zb;
+            } else if (2 * pos == h) {
+                t = INVERSE ? make_double2(-zb.y, zb.x) : make_double2(zb.y, -zb.x);
             } else {
                 const double2 w = tw[pos * stride];
                 t = INVERSE ? cmulc(w, zb) : cmul(w, zb);
@@ -76,38 +90,39 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     return s;
 }
 
-__global__ void __launch_bounds__(FFT_THREADS)
-k_forward(const double *__restrict__ rho, double2 *__restrict__ bhat, int nr, int nt, int nz,
-          const double2 *__restrict__ tw, const double2 *__restrict__ tw2, const double *__restrict__ s,
-          const double *__restrict__ bD, double *__restrict__ partials, int log2M, double2 *__restrict__ bh,
-          const double *__restrict__ invd, int ncls) {
+__global__ void __launch_bounds__(FFT_THREADS) k_forward(const FFTTab *__restrict__ tab, double *__restrict__ partials) {
     extern __shared__ double2 sm[];
+    __shared__ double red[FFT_THREADS / 32];
+    const int pr = find_problem(tab->start, tab->n, blockIdx.x);
+    const FFTProb P = tab->p[pr];
+    const int nr = P.nr, nt = P.nt, nz = P.nz;
     const int M = nt >> 1, nm = M + 1;
     double2 *buf = sm;              // [M][LD]
     double2 *outb = sm + M * LD;    // [TI][nm]
-    __shared__ double red[FFT_THREADS / 32];
 
     const int tiles = (nr + TI - 1) / TI;
-    const int k = blockIdx.x / tiles;
-    const int i0 = (blockIdx.x - k * tiles) * TI;
+    const int lb = (int)(blockIdx.x - tab->start[pr]);
+    const int k = lb / tiles;
+    const int i0 = (lb - k * tiles) * TI;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int i = i0 + lane;
     const bool valid = i < nr;
 
-    const double *src = rho + (size_t)k * nt * nr + i;
+    const double *src = P.rho + (size_t)k * nt * nr + i;
     for (int n = warp; n < M; n += nw) {
         double a = 0.0, b = 0.0;
         if (valid) {
             a = src[(size_t)(2 * n) * nr];
             b = src[(size_t)(2 * n + 1) * nr];
         }
-        buf[bitrev(n, log2M) * LD + lane] = make_double2(a, b);
+        buf[bitrev(n, P.log2M) * LD + lane] = make_double2(a, b);
     }
     __syncthreads();
-    fft_stages<false>(buf, tw, M, lane, warp, nw);
+    fft_stages<false>(buf, (const double2 *)P.tw, M, lane, warp, nw);
 
     // Unpack: X_m = 1/2 [ (Z_m + conj Z_{M-m}) - i W^m (Z_m - conj Z_{M-m}) ], W = e^{-2 pi i / N}
-    const double scale = (s ? s[valid ? i : 0] : 1.0) * (0.5 / (double)nt);
+    const double2 *tw2 = (const double2 *)P.tw2;
+    const double scale = (P.s ? P.s[valid ? i : 0] : 1.0) * (0.5 / (double)nt);
     double acc = 0.0;
     for (int m = warp; m <= M; m += nw) {
         const double2 A = buf[(m == M ? 0 : m) * LD + lane];
@@ -123,7 +138,7 @@ k_forward(const double *__restrict__ rho, double2 *__restrict__ bhat, int nr, in
             const double2 t = cmul(tw2[m], mid);
             x = make_double2((S.x + t.x) * scale, (S.y + t.y) * scale);
         }
-        if (m == 0 && bD && valid) x.x += bD[(size_t)k * nr + i];
+        if (m == 0 && P.bD && valid) x.x += P.bD[(size_t)k * nr + i];
         if (valid && partials) {
             const double w = (m == 0 || m == M) ? 1.0 : 2.0;
             acc += w * (x.x * x.x + x.y * x.y);
@@ -132,13 +147,13 @@ k_forward(const double *__restrict__ rho, double2 *__restrict__ bhat, int nr, in
     }
     __syncthreads();
     const int ncols = min(TI, nr - i0);
-    double2 *dst = bhat + ((size_t)k * nr + i0) * nm;
+    double2 *dst = P.b + ((size_t)k * nr + i0) * nm;
     for (int f = threadIdx.x; f < ncols * nm; f += blockDim.x) dst[f] = outb[f];
-    if (bh) {
+    if (P.bh && P.invd) {
         // b_hat = b / diag for the smoother (row class of plane k, cells i0.., all modes)
-        const int cls = k == 0 ? 0 : (k == nz - 1 ? ncls - 1 : 1);
-        const double *inv = invd + ((size_t)cls * nr + i0) * nm;
-        double2 *dh = bh + ((size_t)k * nr + i0) * nm;
+        const int cls = k == 0 ? 0 : (k == nz - 1 ? P.ncls - 1 : 1);
+        const double *inv = P.invd + ((size_t)cls * nr + i0) * nm;
+        double2 *dh = P.bh + ((size_t)k * nr + i0) * nm;
         for (int f = threadIdx.x; f < ncols * nm; f += blockDim.x) {
             const double2 x = outb[f];
             const double v = inv[f];
@@ -151,29 +166,32 @@ k_forward(const double *__restrict__ rho, double2 *__restrict__ bhat, int nr, in
     }
 }
 
-__global__ void __launch_bounds__(FFT_THREADS)
-k_inverse(const double2 *__restrict__ uhat, double *__restrict__ phi, int nr, int nt, int nz,
-          const double2 *__restrict__ tw, const double2 *__restrict__ tw2, int log2M) {
+__global__ void __launch_bounds__(FFT_THREADS) k_inverse(const FFTTab *__restrict__ tab) {
     extern __shared__ double2 sm[];
+    const int pr = find_problem(tab->start, tab->n, blockIdx.x);
+    const FFTProb P = tab->p[pr];
+    const int nr = P.nr, nt = P.nt;
     const int M = nt >> 1, nm = M + 1;
     double2 *buf = sm;              // [M][LD]
     double2 *inb = sm + M * LD;     // [TI][nm]
 
     const int tiles = (nr + TI - 1) / TI;
-    const int k = blockIdx.x / tiles;
-    const int i0 = (blockIdx.x - k * tiles) * TI;
+    const int lb = (int)(blockIdx.x - tab->start[pr]);
+    const int k = lb / tiles;
+    const int i0 = (lb - k * tiles) * TI;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int i = i0 + lane;
     const bool valid = i < nr;
     const int ncols = min(TI, nr - i0);
 
-    const double2 *src = uhat + ((size_t)k * nr + i0) * nm;
+    const double2 *src = P.uhat + ((size_t)k * nr + i0) * nm;
     for (int f = threadIdx.x; f < TI * nm; f += blockDim.x)
         inb[f] = f < ncols * nm ? src[f] : make_double2(0.0, 0.0);
     __syncthreads();
 
     // Pack: Z_m = (X_m + conj X_{M-m}) + i w^m (X_m - conj X_{M-m}), w = e^{+2 pi i / N};
     // X_0 and X_M enter through their real parts only.
+    const double2 *tw2 = (const double2 *)P.tw2;
     for (int m = warp; m < M; m += nw) {
         double2 A = inb[lane * nm + m];
         double2 B = inb[lane * nm + (M - m)];
@@ -184,13 +202,13 @@ k_inverse(const double2 *__restrict__ uhat, double *__restrict__ phi, int nr, in
         const double2 S = make_double2(A.x + B.x, A.y - B.y);   // X_m + conj X_{M-m}
         const double2 D = make_double2(A.x - B.x, A.y + B.y);   // X_m - conj X_{M-m}
         const double2 t = cmulc(tw2[m], D);                     // w^m D
-        buf[bitrev(m, log2M) * LD + lane] = make_double2(S.x - t.y, S.y + t.x);   // S + i t
+        buf[bitrev(m, P.log2M) * LD + lane] = make_double2(S.x - t.y, S.y + t.x);   // S + i t
     }
     __syncthreads();
-    fft_stages<true>(buf, tw, M, lane, warp, nw);
+    fft_stages<true>(buf, (const double2 *)P.tw, M, lane, warp, nw);
 
     if (valid) {
-        double *dst = phi + (size_t)k * nt * nr + i;
+        double *dst = P.phi + (size_t)k * nt * nr + i;
         for (int n = warp; n < M; n += nw) {
             const double2 z = buf[n * LD + lane];
             dst[(size_t)(2 * n) * nr] = z.x;
@@ -199,41 +217,24 @@ k_inverse(const double2 *__restrict__ uhat, double *__restrict__ phi, int nr, in
     }
 }
 
-int ilog2(int v) {
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return l;
-}
+}  // namespace
 
-size_t fft_smem(int nt) {
+size_t fft_smem_bytes(int nt) {
     const int M = nt / 2, nm = M + 1;
     return (size_t)(M * LD + TI * nm) * sizeof(double2);
 }
 
-}  // namespace
-
-cudaError_t launch_forward(const double *rho, double2 *bhat, int nr, int nt, int nz, const FFTDev &f,
-                           const double *s, const double *bD, double *partials, int *nblocks, double2 *bh,
-                           const double *invd, int ncls, cudaStream_t st) {
-    const int tiles = (nr + TI - 1) / TI;
-    const int blocks = nz * tiles;
-    const size_t smem = fft_smem(nt);
-    cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_forward<<<blocks, FFT_THREADS, smem, st>>>(rho, bhat, nr, nt, nz, (const double2 *)f.tw,
-                                                 (const double2 *)f.tw2, s, bD, partials, ilog2(nt / 2), bh,
-                                                 invd, ncls);
-    if (nblocks) *nblocks = blocks;
+cudaError_t launch_forward(const FFTTab *tab, unsigned grid, size_t smem, double *partials, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_forward<<<grid, FFT_THREADS, smem, st>>>(tab, partials);
     return cudaGetLastError();
 }
 
-cudaError_t launch_inverse(const double2 *uhat, double *phi, int nr, int nt, int nz, const FFTDev &f,
-                           cudaStream_t st) {
-    const int tiles = (nr + TI - 1) / TI;
-    const int blocks = nz * tiles;
-    const size_t smem = fft_smem(nt);
-    cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_inverse<<<blocks, FFT_THREADS, smem, st>>>(uhat, phi, nr, nt, nz, (const double2 *)f.tw,
-                                                 (const double2 *)f.tw2, ilog2(nt / 2));
+cudaError_t launch_inverse(const FFTTab *tab, unsigned grid, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_inverse<<<grid, FFT_THREADS, smem, st>>>(tab);
     return cudaGetLastError();
 }
 

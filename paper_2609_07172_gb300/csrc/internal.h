@@ -26,21 +26,13 @@ void clear_error();
         }                                                                               \
     } while (0)
 
-#define PP_LAUNCH_CHECK()                                                               \
-    do {                                                                                \
-        cudaError_t e_ = cudaGetLastError();                                            \
-        if (e_ != cudaSuccess) {                                                        \
-            ::pp::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), \
-                            __FILE__, __LINE__);                                        \
-            return PIC_POISSON_ECUDA;                                                   \
-        }                                                                               \
-    } while (0)
-
 // ------------------------------------------------------------------ complex vector types
 template <class T> struct V2t;
 template <> struct V2t<double> { using type = double2; };
 template <> struct V2t<float> { using type = float2; };
 template <class T> using V2 = typename V2t<T>::type;
+
+constexpr int kMaxBatch = PIC_POISSON_MAX_BATCH;
 
 // ------------------------------------------------------------------ one multigrid level
 // Coefficients of A_m on a uniform level (appendix Eqs. interior_face_conductances,
@@ -52,7 +44,7 @@ template <class T> using V2 = typename V2t<T>::type;
 // a half-distance Dirichlet face of conductance 2 cz) instead of 2.
 struct LevelHost {
     int nr = 0, nz = 0;
-    double r0 = 0, dr = 0, z0 = 0, dz = 0;
+    double dr = 0, dz = 0;
     int ncls = 0;                 // distinct axial row classes: min(nz, 3)
     std::vector<double> cw, ce, cz, d0r, mu;   // per radial index
     std::vector<double> tz;       // per class
@@ -60,8 +52,11 @@ struct LevelHost {
     std::vector<double> hw, he, hz;             // [ncls][nr][nm]: cw, ce, cz divided by diag
 };
 
+// One level of one problem, as the kernels see it.
 template <class T> struct LevelDev {
     int nr, nz, nm, ncls;
+    int nt;                       // azimuthal cells (Parseval weights of the norms)
+    int init;                     // what a restriction into the next level writes (see launch_residual_restrict)
     const T *cw, *ce, *cz;        // [nr]
     const T *invd, *diag;         // [ncls][nr][nm]
     const T *hw, *he, *hz;        // [ncls][nr][nm] off-diagonal conductances / diag
@@ -79,41 +74,125 @@ template <class T> struct CoarseDev {
     const T *cpr;                 // [nm][nz][nr] upper multipliers of the Thomas factorisation
 };
 
-// ------------------------------------------------------------------ kernels (launchers)
-// All launchers enqueue on `st` and return cudaGetLastError().
-struct FFTDev {
-    int nt;                       // N_theta
-    const double *tw;             // [max(M/2,1)] e^{-2 pi i t / M}, M = N_theta/2, as (cos, sin) pairs
-    const double *tw2;            // [M+1] e^{-2 pi i m / N_theta}
+// Work of one launch over a batch of problems: problem p owns the blocks
+// [start[p], start[p+1]) of the grid; f / c are its fine / coarse level views.
+template <class T> struct LaunchTab {
+    int n;
+    unsigned start[kMaxBatch + 1];
+    LevelDev<T> f[kMaxBatch];
+    LevelDev<T> c[kMaxBatch];
 };
 
-// bh (may be null): also write bhat / diag using the level-0 table invd [ncls][nr][nm].
-cudaError_t launch_forward(const double *rho, double2 *bhat, int nr, int nt, int nz, const FFTDev &f,
-                           const double *s, const double *bD, double *partials, int *nblocks,
-                           double2 *bh, const double *invd, int ncls, cudaStream_t st);
-cudaError_t launch_inverse(const double2 *uhat, double *phi, int nr, int nt, int nz, const FFTDev &f,
-                           cudaStream_t st);
+template <class T> struct CoarseTab {
+    int n;
+    unsigned start[kMaxBatch + 1];
+    LevelDev<T> f[kMaxBatch];
+    CoarseDev<T> c[kMaxBatch];
+    size_t smem;                  // dynamic shared memory of the largest problem
+};
+
+struct DefectTab {                // mixed precision: FP64 level 0 and FP32 level 0 of each problem
+    int n;
+    unsigned start[kMaxBatch + 1];
+    LevelDev<double> d[kMaxBatch];
+    LevelDev<float> s[kMaxBatch];
+    int init_red[kMaxBatch];
+};
+
+// Azimuthal transforms of one problem's finest level.
+struct FFTProb {
+    int nr, nt, nz, nm, ncls, log2M;
+    const double *tw;             // [max(M/2,1)] e^{-2 pi i t / M}, M = nt / 2, as (cos, sin) pairs
+    const double *tw2;            // [M+1] e^{-2 pi i m / nt}
+    const double *s;              // [nr] s_i (Eq. mode_rhs); null: plain 1/N transform
+    const double *bD;             // [nz][nr] Dirichlet right-hand side; may be null
+    const double *invd;           // level-0 inverse diagonal [ncls][nr][nm]; null: no b_hat
+    double2 *b;                   // mode-layout output of the forward transform
+    double2 *bh;                  // b / diag (may be null)
+    const double2 *uhat;          // mode-layout input of the inverse transform
+    const double *rho;            // (nz, nt, nr) input of the forward transform
+    double *phi;                  // (nz, nt, nr) output of the inverse transform
+};
+
+struct FFTTab {
+    int n;
+    unsigned start[kMaxBatch + 1];
+    FFTProb p[kMaxBatch];
+    size_t smem;
+};
+
+// Device-side state of the convergence loop (one per plan).
+struct Ctrl {
+    double tol;                   // per solve
+    int max_cycles;               // per solve
+    int inc;                      // cycles added by one pass of the loop body
+    int cycles;                   // V-cycles applied so far
+    int cont;                     // 1 while some problem is still iterating
+    int n;                        // problems
+    int scaled;                   // residual partials are of the sigma-scaled residual (mixed)
+    double bnorm2[kMaxBatch];     // Parseval-weighted ||b||^2
+    double rel[kMaxBatch];        // latest relative residual
+    double best[kMaxBatch];       // best relative residual (floor detection)
+    double sigma_used[kMaxBatch]; // mixed: scale of the correction problem being solved
+    double inv_sigma_used[kMaxBatch];
+    double sigma_next[kMaxBatch]; // mixed: scale for the next defect
+    double count[kMaxBatch];      // cells of the 3-D grid (scale normalisation)
+    double rel_first[kMaxBatch];  // relative residual at the first convergence test
+    int stall[kMaxBatch];
+    int status[kMaxBatch];
+    int done[kMaxBatch];
+    int done_cycles[kMaxBatch];
+    unsigned rbegin[kMaxBatch];   // residual-norm partials of problem p: [rbegin, rend)
+    unsigned rend[kMaxBatch];
+};
+
+// ------------------------------------------------------------------ launchers
+// All launchers enqueue on `st` and return cudaGetLastError().  `grid` is the
+// table's total block count (start[n]); tables live in device memory.
+cudaError_t launch_forward(const FFTTab *tab, unsigned grid, size_t smem, double *partials, cudaStream_t st);
+cudaError_t launch_inverse(const FFTTab *tab, unsigned grid, size_t smem, cudaStream_t st);
 
 template <class T>
-cudaError_t launch_smooth(const LevelDev<T> &L, int color, cudaStream_t st);
+cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, cudaStream_t st);
 // red_only: residual of the red fine cells only (valid right after a black half-sweep).
-// init: 0 = coarse b only; 1 = also b_hat and u = 0; 2 = also b_hat and u = (red ? b_hat : 0).
+// Per problem, f.init selects what is written into the coarse level c: 0 = b only
+// (coarsest, solved directly); 1 = also b_hat and u = 0; 2 = also b_hat and
+// u = (red ? b_hat : 0), the first red half-sweep from zero.
 template <class T>
-cudaError_t launch_residual_restrict(const LevelDev<T> &L, const LevelDev<T> &C, int nt, bool red_only, int init,
-                                     double *partials, int *nblocks, cudaStream_t st);
+cudaError_t launch_residual_restrict(const LaunchTab<T> *tab, unsigned grid, bool red_only, double *partials,
+                                     cudaStream_t st);
+// r = b - A_m u on level f of every problem (r_out: optional per-problem output
+// in c[p].u), Parseval-weighted norms of r and b into partials[block] and
+// partials[partial_stride + block].
 template <class T>
-cudaError_t launch_residual(const LevelDev<T> &L, V2<T> *r, int nt, double *partials, int *nblocks,
-                            cudaStream_t st);
+cudaError_t launch_residual(const LaunchTab<T> *tab, unsigned grid, bool write_r, double *partials,
+                            unsigned partial_stride, cudaStream_t st);
 template <class T>
-cudaError_t launch_prolong(const LevelDev<T> &L, const LevelDev<T> &C, bool black_only, cudaStream_t st);
+cudaError_t launch_prolong(const LaunchTab<T> *tab, unsigned grid, bool black_only, cudaStream_t st);
 template <class T>
-cudaError_t launch_coarse(const LevelDev<T> &L, const CoarseDev<T> &C, cudaStream_t st);
+cudaError_t launch_coarse(const CoarseTab<T> *tab, unsigned grid, size_t smem, cudaStream_t st);
 
-cudaError_t launch_defect(const LevelDev<double> &D, const LevelDev<float> &S, double sigma, int nt, bool init_red,
-                          double *partials, int *nblocks, cudaStream_t st);
-cudaError_t launch_update(const LevelDev<double> &D, const LevelDev<float> &S, double inv_sigma, cudaStream_t st);
+cudaError_t launch_defect(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, double *partials, cudaStream_t st);
+cudaError_t launch_update(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, cudaStream_t st);
+
+// Sums of the forward transform's partials per problem -> ctrl->bnorm2; initial
+// scale of the mixed correction problem.
+cudaError_t launch_bnorm(Ctrl *ctrl, const FFTTab *fft, const double *partials, cudaStream_t st);
+// Convergence test: per-problem residual norms from partials, stop rule,
+// cycle count (+inc when counting), graph conditional (when use_handle).
+cudaError_t launch_check(Ctrl *ctrl, const double *partials, int counting, cudaGraphConditionalHandle handle,
+                         int use_handle, cudaStream_t st);
+// Plain sum of n partials into *out (single problem helpers).
 cudaError_t launch_sum(const double *partials, int n, double *out, cudaStream_t st);
 
 cudaError_t measure_fma(cudaStream_t st, double *fp64_gflops, double *fp32_gflops);
+
+// Threads per block of the multigrid kernels and the block count a launch
+// over `entries` work items of one problem needs.
+constexpr int MG_THREADS = 256;
+inline unsigned mg_blocks(size_t entries) { return (unsigned)((entries + MG_THREADS - 1) / MG_THREADS); }
+constexpr int FFT_TI = 32;        // radial columns per transform CTA
+constexpr int FFT_THREADS = 256;
+size_t fft_smem_bytes(int nt);
 
 }  // namespace pp

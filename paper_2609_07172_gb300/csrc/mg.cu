@@ -1,5 +1,6 @@
-// Mode-batched matrix-free multigrid kernels (steps a-3 .. a-7) and the
-// FP64 defect / update kernels of the mixed-precision form.
+// Mode-batched matrix-free multigrid kernels (steps a-3 .. a-7), the FP64
+// defect / update kernels of the mixed-precision form, and the device-side
+// convergence test.
 //
 // Every kernel works on the cell-major, mode-fast layout of Eq. mode_fast_layout
 // (entry (k, i, m) at (k*nr + i)*nm + m, unpadded): consecutive threads take
@@ -7,6 +8,11 @@
 // and store of a warp is contiguous.  Only the diagonal shift lambda_m mu of
 // A_m depends on the mode (Eq. shifted_operator_family); it enters through
 // per-level tables indexed (row class, i, m).
+//
+// One launch serves a batch of independent problems of different sizes (and
+// different azimuthal mode counts): problem p owns a contiguous range of
+// blocks, found by a binary search over the launch table; every block belongs
+// to one problem, so per-block norm partials never mix problems.
 //
 // On GB300 FP64 runs at 1/64 of the FP32 rate, so the FP64 kernels are bound
 // by FP64 instructions, and every kernel here is arranged to issue as few as
@@ -24,8 +30,6 @@
 
 namespace pp {
 namespace {
-
-constexpr int MG_THREADS = 256;
 
 template <class T> __device__ __forceinline__ V2<T> mk(T x, T y);
 template <> __device__ __forceinline__ double2 mk<double>(double x, double y) { return make_double2(x, y); }
@@ -53,6 +57,22 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     if (threadIdx.x == 0)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
     return s;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Problem owning block `blk`: the last p with start[p] <= blk.
+__device__ __forceinline__ int find_problem(const unsigned *__restrict__ start, int n, unsigned blk) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (start[mid] <= blk) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // (k, i) of the c-th cell of colour `color` ((i + k) % 2 == color) on a level
@@ -84,16 +104,18 @@ __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i,
 //   u_q <- (b_q + sum_q' G_qq' u_q') / (D0_q + lambda_m mu_q)
 // written as u = b_hat + h_z (u_S + u_N) + h_w u_W + h_e u_E with h = G / diag.
 template <class T>
-__global__ void __launch_bounds__(MG_THREADS) k_smooth(const LevelDev<T> L, int color, unsigned total) {
-    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= total) return;
+__global__ void __launch_bounds__(MG_THREADS) k_smooth(const LaunchTab<T> *__restrict__ tab, int color) {
+    const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    const LevelDev<T> L = tab->f[p];
+    const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
     const unsigned nm = L.nm;
+    if (e >= (unsigned)L.nz * (unsigned)(L.nr >> 1) * nm) return;
     const unsigned c = e / nm;
     const int m = (int)(e - c * nm);
     int k, i;
     colour_cell(c, L.nr, color, k, i);
     const size_t idx = ((size_t)k * L.nr + i) * nm + m;
-    const size_t tab = ((size_t)row_class(k, L.nz, L.ncls) * L.nr + i) * nm + m;
+    const size_t tb = ((size_t)row_class(k, L.nz, L.ncls) * L.nr + i) * nm + m;
     const size_t rowstride = (size_t)L.nr * nm;
     V2<T> s = mk<T>(0, 0);
     if (k > 0) s = L.u[idx - rowstride];
@@ -101,28 +123,27 @@ __global__ void __launch_bounds__(MG_THREADS) k_smooth(const LevelDev<T> L, int 
         const V2<T> n = L.u[idx + rowstride];
         s = (k > 0) ? mk<T>(s.x + n.x, s.y + n.y) : n;
     }
-    V2<T> acc = fma2<T>(L.hz[tab], s, L.bh[idx]);
-    if (i > 0) acc = fma2<T>(L.hw[tab], L.u[idx - nm], acc);
-    if (i < L.nr - 1) acc = fma2<T>(L.he[tab], L.u[idx + nm], acc);
+    V2<T> acc = fma2<T>(L.hz[tb], s, L.bh[idx]);
+    if (i > 0) acc = fma2<T>(L.hw[tb], L.u[idx - nm], acc);
+    if (i < L.nr - 1) acc = fma2<T>(L.he[tb], L.u[idx + nm], acc);
     L.u[idx] = acc;
 }
 
 // Residual of the fine cells of each coarse cell, summed into the coarse
 // right-hand side (finite-volume restriction: a residual is a cell integral),
-// with optional Parseval-weighted squared-norm partials.
-//  RED_ONLY: only the two red fine cells (after a black half-sweep the black
-//            residuals vanish); otherwise all four.
-//  INIT: 0 = write coarse b only (coarsest level, solved directly);
-//        1 = also b_hat = b / diag and u = 0;
-//        2 = also b_hat and u = (red ? b_hat : 0), i.e. the first red
-//            half-sweep from a zero iterate.
-template <class T, bool RED_ONLY, int INIT>
+// with optional Parseval-weighted squared-norm partials.  RED_ONLY: only the
+// two red fine cells (after a black half-sweep the black residuals vanish).
+// F.init selects what else the coarse level receives (see internal.h).
+template <class T, bool RED_ONLY>
 __global__ void __launch_bounds__(MG_THREADS)
-k_residual_restrict(const LevelDev<T> F, const LevelDev<T> C, int nt, double *__restrict__ partials, unsigned total) {
+k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ partials) {
     __shared__ double red[MG_THREADS / 32];
-    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    const LevelDev<T> F = tab->f[p];
+    const LevelDev<T> C = tab->c[p];
+    const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
     double acc = 0.0;
-    if (e < total) {
+    if (e < (unsigned)C.nz * (unsigned)C.nr * (unsigned)C.nm) {
         const unsigned nm = C.nm;
         const unsigned cc = e / nm;
         const int m = (int)(e - cc * nm);
@@ -143,13 +164,13 @@ k_residual_restrict(const LevelDev<T> F, const LevelDev<T> C, int nt, double *__
             }
         }
         C.b[e] = sum;
-        if (INIT > 0) {
+        if (F.init > 0) {
             const T inv = C.invd[((size_t)row_class(K, C.nz, C.ncls) * C.nr + I) * nm + m];
             const V2<T> bh = mk<T>(sum.x * inv, sum.y * inv);
             C.bh[e] = bh;
-            C.u[e] = (INIT == 2 && ((K + I) & 1) == 0) ? bh : mk<T>(0, 0);
+            C.u[e] = (F.init == 2 && ((K + I) & 1) == 0) ? bh : mk<T>(0, 0);
         }
-        if (partials) acc *= parseval_w(m, nt);
+        if (partials) acc *= parseval_w(m, F.nt);
     }
     if (partials) {
         const double tot = block_sum(acc, red);
@@ -157,32 +178,37 @@ k_residual_restrict(const LevelDev<T> F, const LevelDev<T> C, int nt, double *__
     }
 }
 
-// r = b - A_m u on one level (r may be null), with Parseval-weighted squared
-// norms of r and b in partials[0..nblocks) and partials[nblocks..2 nblocks).
+// r = b - A_m u on level f (r written to c.u when write_r), Parseval-weighted
+// squared norms of r into partials[block] and, when stride > 0, of b into
+// partials[stride + block].
 template <class T>
 __global__ void __launch_bounds__(MG_THREADS)
-k_residual(const LevelDev<T> L, V2<T> *__restrict__ r_out, int nt, double *__restrict__ partials, unsigned total) {
+k_residual(const LaunchTab<T> *__restrict__ tab, int write_r, double *__restrict__ partials, unsigned stride) {
     __shared__ double red[MG_THREADS / 32];
-    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    const LevelDev<T> L = tab->f[p];
+    const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
     double ar = 0.0, ab = 0.0;
-    if (e < total) {
+    if (e < (unsigned)L.nz * (unsigned)L.nr * (unsigned)L.nm) {
         const unsigned nm = L.nm;
         const unsigned c = e / nm;
         const int m = (int)(e - c * nm);
         const int k = (int)(c / (unsigned)L.nr);
         const int i = (int)(c - (unsigned)k * L.nr);
         const V2<T> r = residual_at(L, k, i, m, e);
-        if (r_out) r_out[e] = r;
+        if (write_r) tab->c[p].u[e] = r;
         const V2<T> b = L.b[e];
-        const double w = parseval_w(m, nt);
+        const double w = parseval_w(m, L.nt);
         ar = w * ((double)r.x * r.x + (double)r.y * r.y);
         ab = w * ((double)b.x * b.x + (double)b.y * b.y);
     }
     if (partials) {
         const double tr = block_sum(ar, red);
         if (threadIdx.x == 0) partials[blockIdx.x] = tr;
-        const double tb = block_sum(ab, red);
-        if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = tb;
+        if (stride) {
+            const double tb = block_sum(ab, red);
+            if (threadIdx.x == 0) partials[stride + blockIdx.x] = tb;
+        }
     }
 }
 
@@ -192,10 +218,14 @@ k_residual(const LevelDev<T> L, V2<T> *__restrict__ r_out, int nt, double *__res
 // (the correction vanishes on the Dirichlet face).  BLACK_ONLY: only black
 // fine cells (the red half-sweep that follows overwrites the red ones).
 template <class T, bool BLACK_ONLY>
-__global__ void __launch_bounds__(MG_THREADS) k_prolong(const LevelDev<T> F, const LevelDev<T> C, unsigned total) {
-    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= total) return;
+__global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__restrict__ tab) {
+    const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    const LevelDev<T> F = tab->f[p];
+    const LevelDev<T> C = tab->c[p];
+    const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
     const unsigned nm = F.nm;
+    const unsigned total = (unsigned)F.nz * (unsigned)(BLACK_ONLY ? (F.nr >> 1) : F.nr) * nm;
+    if (e >= total) return;
     const unsigned c = e / nm;
     const int m = (int)(e - c * nm);
     int k, i;
@@ -224,61 +254,72 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LevelDev<T> F, con
     F.u[idx] = u;
 }
 
-// Mixed precision, FP64 defect: r = b - A_m x on the FP64 level-0 view D
-// (all cells), Parseval-weighted ||r||^2 partials, and the FP32 level-0
-// right-hand side of the correction equation, scaled by sigma (a power of two,
-// exact): b32 = r * sigma, b_hat32 = b32 / diag, u32 = (red ? b_hat32 : 0) --
-// the first red half-sweep of the FP32 V-cycle from a zero correction
-// (INIT_RED) -- or u32 = 0.
-template <bool INIT_RED>
+// Mixed precision, FP64 defect: r = b - A_m x on the FP64 level 0 (all cells)
+// and the FP32 level-0 right-hand side of the correction equation, scaled by
+// sigma (a power of two, exact): b32 = r sigma, b_hat32 = b32 / diag and
+// u32 = (red ? b_hat32 : 0) -- the first red half-sweep of the FP32 V-cycle
+// from a zero correction -- or u32 = 0.  The squared norm of the scaled
+// residual is accumulated in FP32 per entry (it only decides convergence).
 __global__ void __launch_bounds__(MG_THREADS)
-k_defect(const LevelDev<double> D, const LevelDev<float> S, double sigma, int nt, double *__restrict__ partials,
-         unsigned total) {
+k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, double *__restrict__ partials) {
     __shared__ double red[MG_THREADS / 32];
-    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    const LevelDev<double> D = tab->d[p];
+    const LevelDev<float> S = tab->s[p];
+    const int init_red = tab->init_red[p];
+    const double sigma = ctrl->sigma_next[p];
+    const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
     double acc = 0.0;
-    if (e < total) {
+    if (e < (unsigned)D.nz * (unsigned)D.nr * (unsigned)D.nm) {
         const unsigned nm = D.nm;
         const unsigned c = e / nm;
         const int m = (int)(e - c * nm);
         const int k = (int)(c / (unsigned)D.nr);
         const int i = (int)(c - (unsigned)k * D.nr);
         const double2 r = residual_at(D, k, i, m, e);
-        acc = parseval_w(m, nt) * (r.x * r.x + r.y * r.y);
         const float2 b32 = make_float2((float)(r.x * sigma), (float)(r.y * sigma));
+        const float w = (m == 0 || 2 * m == D.nt) ? 1.f : 2.f;
+        acc = (double)(w * fmaf(b32.x, b32.x, b32.y * b32.y));
         const float inv = S.invd[((size_t)row_class(k, S.nz, S.ncls) * S.nr + i) * nm + m];
         const float2 bh = make_float2(b32.x * inv, b32.y * inv);
         S.b[e] = b32;
         S.bh[e] = bh;
-        S.u[e] = (INIT_RED && ((k + i) & 1) == 0) ? bh : make_float2(0.f, 0.f);
+        S.u[e] = (init_red && ((k + i) & 1) == 0) ? bh : make_float2(0.f, 0.f);
     }
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
-// Mixed precision, FP64 update: x += e32 / sigma.
-__global__ void __launch_bounds__(MG_THREADS)
-k_update(const LevelDev<double> D, const LevelDev<float> S, double inv_sigma, unsigned total) {
-    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= total) return;
+// Mixed precision, FP64 update: x += e32 / sigma (the scale of the correction
+// problem just solved; 1/sigma is an exact power of two).
+__global__ void __launch_bounds__(MG_THREADS) k_update(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl) {
+    const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    const LevelDev<double> D = tab->d[p];
+    const LevelDev<float> S = tab->s[p];
+    const double inv = ctrl->inv_sigma_used[p];
+    const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
+    if (e >= (unsigned)D.nz * (unsigned)D.nr * (unsigned)D.nm) return;
     const float2 c = S.u[e];
     double2 x = D.u[e];
-    x.x = fma((double)c.x, inv_sigma, x.x);
-    x.y = fma((double)c.y, inv_sigma, x.y);
+    x.x = fma((double)c.x, inv, x.x);
+    x.y = fma((double)c.y, inv, x.y);
     D.u[e] = x;
 }
 
-// Coarsest level, exact separable solve, one CTA per mode.  On a uniform
-// level A_m = I_z (x) K_m + T_z (x) diag(cz) with K_m the radial tridiagonal
-// operator (diagonal D0r + lambda_m mu) and T_z = tridiag(-1, tz_k, -1).
+// Coarsest level, exact separable solve, one CTA per (problem, mode).  On a
+// uniform level A_m = I_z (x) K_m + T_z (x) diag(cz) with K_m the radial
+// tridiagonal operator (diagonal D0r + lambda_m mu) and T_z = tridiag(-1, tz_k, -1).
 // T_z = V Lambda V^T (V given), so for each axial eigenvector j the system is
 // tridiagonal in r: (K_m + Lambda_j diag(cz)) w_j = (V^T b)_j, factorised at
 // plan time (Thomas: inverse pivots piv, multipliers cpr).  u = V w.
 template <class T>
-__global__ void __launch_bounds__(MG_THREADS) k_coarse(const LevelDev<T> L, const CoarseDev<T> D) {
+__global__ void __launch_bounds__(MG_THREADS) k_coarse(const CoarseTab<T> *__restrict__ tab) {
     extern __shared__ unsigned char smraw[];
+    const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    const LevelDev<T> L = tab->f[p];
+    const CoarseDev<T> D = tab->c[p];
     const int nr = D.nr, nz = D.nz, nm = D.nm;
-    const int m = blockIdx.x;
+    const int m = (int)(blockIdx.x - tab->start[p]);
     V2<T> *bs = (V2<T> *)smraw;              // [nz][nr]
     V2<T> *ws = bs + (size_t)nz * nr;        // [nz][nr]
     T *Vs = (T *)(ws + (size_t)nz * nr);     // [nz][nz]
@@ -332,6 +373,104 @@ __global__ void __launch_bounds__(MG_THREADS) k_coarse(const LevelDev<T> L, cons
     }
 }
 
+// Power of two closest to 1 / sqrt(mean square): scales an FP32 correction
+// problem to O(1) values without any rounding from the scale itself.
+__device__ double pow2_scale(double sumsq, double count) {
+    const double rms = sqrt(sumsq / fmax(count, 1.0));
+    if (!(rms > 0.0) || isinf(rms) || isnan(rms)) return 1.0;
+    int ex = 0;
+    frexp(rms, &ex);
+    return ldexp(1.0, -ex);
+}
+
+// ||b||^2 per problem from the forward transform's block partials (one warp
+// per problem, fixed summation order), and the first correction scale.
+__global__ void __launch_bounds__(256) k_bnorm(Ctrl *__restrict__ ctrl, const FFTTab *__restrict__ fft,
+                                               const double *__restrict__ partials) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int p = warp; p < fft->n; p += nw) {
+        double s = 0.0;
+        for (unsigned b = fft->start[p] + lane; b < fft->start[p + 1]; b += 32) s += partials[b];
+        s = warp_sum(s);
+        if (lane == 0) {
+            ctrl->bnorm2[p] = s;
+            ctrl->sigma_next[p] = pow2_scale(s, ctrl->count[p]);
+        }
+    }
+}
+
+// Device-side convergence test after a residual evaluation.  Per problem: the
+// Parseval-weighted ||r||^2 from its block partials (mixed precision: of the
+// residual scaled by sigma), rel = ||r|| / ||b||, and the stop rule: tol > 0
+// stops at rel <= tol; tol <= 0 stops once rel has not halved for two
+// evaluations (the rounding floor); non-finite stops with ENONFINITE; the
+// cycle cap with ENOTCONVERGED.  Problems that stopped keep being iterated
+// (their rel keeps describing the returned iterate) until all have stopped.
+// counting: add ctrl->inc to the cycle count first (evaluations after a pass
+// of the loop body).  When use_handle, sets the graph's while-condition.
+__global__ void __launch_bounds__(256) k_check(Ctrl *__restrict__ ctrl, const double *__restrict__ partials,
+                                               int counting, cudaGraphConditionalHandle handle, int use_handle) {
+    __shared__ int s_cycles, s_any;
+    if (threadIdx.x == 0) {
+        s_cycles = ctrl->cycles + (counting ? ctrl->inc : 0);
+        s_any = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double tol = ctrl->tol;
+    for (int p = warp; p < ctrl->n; p += nw) {
+        double s = 0.0;
+        for (unsigned b = ctrl->rbegin[p] + lane; b < ctrl->rend[p]; b += 32) s += partials[b];
+        s = warp_sum(s);
+        if (lane == 0) {
+            double rr2 = s;
+            if (ctrl->scaled) {
+                const double su = ctrl->sigma_next[p];
+                ctrl->sigma_used[p] = su;
+                ctrl->inv_sigma_used[p] = 1.0 / su;
+                rr2 = rr2 / (su * su);
+                ctrl->sigma_next[p] = pow2_scale(rr2, ctrl->count[p]);
+            }
+            const double bb = ctrl->bnorm2[p];
+            const double rel = bb > 0.0 ? sqrt(rr2 / bb) : sqrt(rr2);
+            ctrl->rel[p] = rel;
+            if (!counting) ctrl->rel_first[p] = rel;
+            if (!ctrl->done[p]) {
+                int stop = 0, status = PIC_POISSON_OK;
+                if (isnan(rel) || isinf(rel)) {
+                    stop = 1;
+                    status = PIC_POISSON_ENONFINITE;
+                } else if (tol > 0.0) {
+                    stop = rel <= tol;
+                } else if (rel < 0.5 * ctrl->best[p]) {
+                    ctrl->best[p] = rel;
+                    ctrl->stall[p] = 0;
+                } else {
+                    ctrl->best[p] = fmin(ctrl->best[p], rel);
+                    stop = ++ctrl->stall[p] >= 2;
+                }
+                if (!stop && s_cycles >= ctrl->max_cycles) {
+                    stop = 1;
+                    status = PIC_POISSON_ENOTCONVERGED;
+                }
+                if (stop) {
+                    ctrl->done[p] = 1;
+                    ctrl->status[p] = status;
+                    ctrl->done_cycles[p] = s_cycles;
+                } else {
+                    atomicOr(&s_any, 1);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctrl->cycles = s_cycles;
+        ctrl->cont = s_any;
+        if (use_handle) cudaGraphSetConditional(handle, s_any ? 1u : 0u);
+    }
+}
+
 // Deterministic single-CTA sum of n partials (fixed order per thread, fixed tree).
 __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ p, int n, double *__restrict__ out) {
     __shared__ double red[32];
@@ -341,76 +480,62 @@ __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ p, int 
     if (threadIdx.x == 0) *out = t;
 }
 
-inline unsigned nblk(unsigned total) { return (total + MG_THREADS - 1) / MG_THREADS; }
-
 }  // namespace
 
 template <class T>
-cudaError_t launch_smooth(const LevelDev<T> &L, int color, cudaStream_t st) {
-    const unsigned total = (unsigned)L.nz * (unsigned)(L.nr / 2) * (unsigned)L.nm;
-    k_smooth<T><<<nblk(total), MG_THREADS, 0, st>>>(L, color, total);
+cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, cudaStream_t st) {
+    k_smooth<T><<<grid, MG_THREADS, 0, st>>>(tab, color);
     return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_residual_restrict(const LevelDev<T> &L, const LevelDev<T> &C, int nt, bool red_only, int init,
-                                     double *partials, int *nblocks, cudaStream_t st) {
-    const unsigned total = (unsigned)C.nz * (unsigned)C.nr * (unsigned)C.nm;
-    const unsigned nb = nblk(total);
-    if (red_only) {
-        if (init == 0) k_residual_restrict<T, true, 0><<<nb, MG_THREADS, 0, st>>>(L, C, nt, partials, total);
-        else if (init == 1) k_residual_restrict<T, true, 1><<<nb, MG_THREADS, 0, st>>>(L, C, nt, partials, total);
-        else k_residual_restrict<T, true, 2><<<nb, MG_THREADS, 0, st>>>(L, C, nt, partials, total);
-    } else {
-        if (init == 0) k_residual_restrict<T, false, 0><<<nb, MG_THREADS, 0, st>>>(L, C, nt, partials, total);
-        else if (init == 1) k_residual_restrict<T, false, 1><<<nb, MG_THREADS, 0, st>>>(L, C, nt, partials, total);
-        else k_residual_restrict<T, false, 2><<<nb, MG_THREADS, 0, st>>>(L, C, nt, partials, total);
-    }
-    if (nblocks) *nblocks = (int)nb;
+cudaError_t launch_residual_restrict(const LaunchTab<T> *tab, unsigned grid, bool red_only, double *partials,
+                                     cudaStream_t st) {
+    if (red_only) k_residual_restrict<T, true><<<grid, MG_THREADS, 0, st>>>(tab, partials);
+    else k_residual_restrict<T, false><<<grid, MG_THREADS, 0, st>>>(tab, partials);
     return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_residual(const LevelDev<T> &L, V2<T> *r, int nt, double *partials, int *nblocks,
-                            cudaStream_t st) {
-    const unsigned total = (unsigned)L.nz * (unsigned)L.nr * (unsigned)L.nm;
-    k_residual<T><<<nblk(total), MG_THREADS, 0, st>>>(L, r, nt, partials, total);
-    if (nblocks) *nblocks = (int)nblk(total);
+cudaError_t launch_residual(const LaunchTab<T> *tab, unsigned grid, bool write_r, double *partials,
+                            unsigned partial_stride, cudaStream_t st) {
+    k_residual<T><<<grid, MG_THREADS, 0, st>>>(tab, write_r ? 1 : 0, partials, partial_stride);
     return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_prolong(const LevelDev<T> &L, const LevelDev<T> &C, bool black_only, cudaStream_t st) {
-    if (black_only) {
-        const unsigned total = (unsigned)L.nz * (unsigned)(L.nr / 2) * (unsigned)L.nm;
-        k_prolong<T, true><<<nblk(total), MG_THREADS, 0, st>>>(L, C, total);
-    } else {
-        const unsigned total = (unsigned)L.nz * (unsigned)L.nr * (unsigned)L.nm;
-        k_prolong<T, false><<<nblk(total), MG_THREADS, 0, st>>>(L, C, total);
-    }
+cudaError_t launch_prolong(const LaunchTab<T> *tab, unsigned grid, bool black_only, cudaStream_t st) {
+    if (black_only) k_prolong<T, true><<<grid, MG_THREADS, 0, st>>>(tab);
+    else k_prolong<T, false><<<grid, MG_THREADS, 0, st>>>(tab);
     return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_coarse(const LevelDev<T> &L, const CoarseDev<T> &C, cudaStream_t st) {
-    const size_t smem = (size_t)2 * C.nr * C.nz * sizeof(V2<T>) + (size_t)C.nz * C.nz * sizeof(T);
-    cudaFuncSetAttribute(k_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_coarse<T><<<C.nm, MG_THREADS, smem, st>>>(L, C);
+cudaError_t launch_coarse(const CoarseTab<T> *tab, unsigned grid, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_coarse<T><<<grid, MG_THREADS, smem, st>>>(tab);
     return cudaGetLastError();
 }
 
-cudaError_t launch_defect(const LevelDev<double> &D, const LevelDev<float> &S, double sigma, int nt, bool init_red,
-                          double *partials, int *nblocks, cudaStream_t st) {
-    const unsigned total = (unsigned)D.nz * (unsigned)D.nr * (unsigned)D.nm;
-    if (init_red) k_defect<true><<<nblk(total), MG_THREADS, 0, st>>>(D, S, sigma, nt, partials, total);
-    else k_defect<false><<<nblk(total), MG_THREADS, 0, st>>>(D, S, sigma, nt, partials, total);
-    if (nblocks) *nblocks = (int)nblk(total);
+cudaError_t launch_defect(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, double *partials, cudaStream_t st) {
+    k_defect<<<grid, MG_THREADS, 0, st>>>(tab, ctrl, partials);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(const LevelDev<double> &D, const LevelDev<float> &S, double inv_sigma, cudaStream_t st) {
-    const unsigned total = (unsigned)D.nz * (unsigned)D.nr * (unsigned)D.nm;
-    k_update<<<nblk(total), MG_THREADS, 0, st>>>(D, S, inv_sigma, total);
+cudaError_t launch_update(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, cudaStream_t st) {
+    k_update<<<grid, MG_THREADS, 0, st>>>(tab, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bnorm(Ctrl *ctrl, const FFTTab *fft, const double *partials, cudaStream_t st) {
+    k_bnorm<<<1, 256, 0, st>>>(ctrl, fft, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check(Ctrl *ctrl, const double *partials, int counting, cudaGraphConditionalHandle handle,
+                         int use_handle, cudaStream_t st) {
+    k_check<<<1, 256, 0, st>>>(ctrl, partials, counting, handle, use_handle);
     return cudaGetLastError();
 }
 
@@ -419,13 +544,14 @@ cudaError_t launch_sum(const double *partials, int n, double *out, cudaStream_t 
     return cudaGetLastError();
 }
 
-#define PP_INST(T)                                                                                          \
-    template cudaError_t launch_smooth<T>(const LevelDev<T> &, int, cudaStream_t);                          \
-    template cudaError_t launch_residual_restrict<T>(const LevelDev<T> &, const LevelDev<T> &, int, bool, int, \
-                                                     double *, int *, cudaStream_t);                        \
-    template cudaError_t launch_residual<T>(const LevelDev<T> &, V2<T> *, int, double *, int *, cudaStream_t); \
-    template cudaError_t launch_prolong<T>(const LevelDev<T> &, const LevelDev<T> &, bool, cudaStream_t);   \
-    template cudaError_t launch_coarse<T>(const LevelDev<T> &, const CoarseDev<T> &, cudaStream_t);
+#define PP_INST(T)                                                                                         \
+    template cudaError_t launch_smooth<T>(const LaunchTab<T> *, unsigned, int, cudaStream_t);              \
+    template cudaError_t launch_residual_restrict<T>(const LaunchTab<T> *, unsigned, bool, double *,       \
+                                                     cudaStream_t);                                        \
+    template cudaError_t launch_residual<T>(const LaunchTab<T> *, unsigned, bool, double *, unsigned,      \
+                                            cudaStream_t);                                                 \
+    template cudaError_t launch_prolong<T>(const LaunchTab<T> *, unsigned, bool, cudaStream_t);            \
+    template cudaError_t launch_coarse<T>(const CoarseTab<T> *, unsigned, size_t, cudaStream_t);
 PP_INST(double)
 PP_INST(float)
 #undef PP_INST

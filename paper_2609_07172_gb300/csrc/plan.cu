@@ -1,0 +1,753 @@
+// Plan construction: descriptor validation, multigrid hierarchy, per-level
+// coefficient tables (step a-2), coarsest-level factors, device workspace and
+// the launch tables that let one kernel launch serve a batch of problems.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "plan.h"
+
+namespace pp {
+
+static thread_local char g_err[512];
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+const char *last_error_text() { return g_err; }
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kEps0 = 8.8541878128e-12;   // F/m, CODATA 2018
+constexpr int kMaxNtheta = 256;
+constexpr int kMaxCoarseCells = 4096;
+constexpr int kMaxCoarseNz = 64;
+constexpr unsigned kKnownFlags = PIC_POISSON_USE_INITIAL_GUESS | PIC_POISSON_PROFILE | PIC_POISSON_GRAPH;
+
+int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
+    if (!in) {
+        set_error("desc is NULL");
+        return PIC_POISSON_EINVAL;
+    }
+    *d = *in;
+    if (d->theta_span <= 0) d->theta_span = 2.0 * kPi;
+    if (d->eps0 <= 0) d->eps0 = kEps0;
+    if (d->max_cycles <= 0) d->max_cycles = 200;
+    if (d->pre_sweeps < 0) d->pre_sweeps = 2;
+    if (d->post_sweeps < 0) d->post_sweeps = 2;
+    if (d->inner_cycles <= 0) d->inner_cycles = 2;
+    if (d->nr < 1 || d->nz < 1) {
+        set_error("nr and nz must be >= 1 (got %d, %d)", d->nr, d->nz);
+        return PIC_POISSON_EINVAL;
+    }
+    if (d->ntheta < 2 || d->ntheta > kMaxNtheta || (d->ntheta & (d->ntheta - 1))) {
+        set_error("ntheta must be a power of two in [2, %d] (got %d)", kMaxNtheta, d->ntheta);
+        return PIC_POISSON_EINVAL;
+    }
+    if (!(d->r_in > 0) || !(d->r_out > d->r_in) || !(d->z1 > d->z0) || !std::isfinite(d->r_out) ||
+        !std::isfinite(d->z0) || !std::isfinite(d->z1)) {
+        set_error("need 0 < r_in < r_out and z0 < z1 (finite)");
+        return PIC_POISSON_EINVAL;
+    }
+    if (d->precision != PIC_POISSON_FP64 && d->precision != PIC_POISSON_MIXED) {
+        set_error("precision must be PIC_POISSON_FP64 or PIC_POISSON_MIXED");
+        return PIC_POISSON_EINVAL;
+    }
+    if (d->pre_sweeps + d->post_sweeps == 0 || d->pre_sweeps > 64 || d->post_sweeps > 64 || d->inner_cycles > 64) {
+        set_error("need 0 < pre_sweeps + post_sweeps, sweeps <= 64, inner_cycles <= 64");
+        return PIC_POISSON_EINVAL;
+    }
+    if (d->flags & ~kKnownFlags) {
+        set_error("unknown flag bits 0x%x", d->flags & ~kKnownFlags);
+        return PIC_POISSON_EINVAL;
+    }
+    const double n = (double)d->nr * d->nz * (d->ntheta / 2 + 1);
+    if (n > 2.0e9) {
+        set_error("too many mode entries (nr*nz*(ntheta/2+1) = %.0f > 2e9)", n);
+        return PIC_POISSON_EINVAL;
+    }
+    return PIC_POISSON_OK;
+}
+
+// 2:1 coarsening while both counts are even and at least 8.
+int hierarchy(const pic_poisson_desc &d, int *nr, int *nz, int *levels) {
+    int L = 1, r = d.nr, z = d.nz;
+    nr[0] = r;
+    nz[0] = z;
+    while (L < PIC_POISSON_MAX_LEVELS && r % 2 == 0 && z % 2 == 0 && r >= 8 && z >= 8) {
+        r /= 2;
+        z /= 2;
+        nr[L] = r;
+        nz[L] = z;
+        ++L;
+    }
+    *levels = L;
+    if (z > kMaxCoarseNz || (long)r * z > kMaxCoarseCells) {
+        set_error("coarsest level %d x %d (r x z) exceeds the direct-solve limit (nz <= %d, cells <= %d); "
+                  "use cell counts with more factors of two",
+                  r, z, kMaxCoarseNz, kMaxCoarseCells);
+        return PIC_POISSON_EINVAL;
+    }
+    return PIC_POISSON_OK;
+}
+
+double wall_rin(const pic_poisson_desc &d, int k) { return d.phi_r_in_z ? d.phi_r_in_z[k] : d.phi_r_in; }
+double wall_rout(const pic_poisson_desc &d, int k) { return d.phi_r_out_z ? d.phi_r_out_z[k] : d.phi_r_out; }
+
+// Exact discrete azimuthal eigenvalue, Eq. discrete_azimuthal_eigenvalue.
+double lambda_m(const pic_poisson_desc &d, int m) {
+    const double da = d.theta_span / d.ntheta;
+    const double s = std::sin(kPi * m / d.ntheta);
+    return 4.0 / (da * da) * s * s;
+}
+
+// Coefficients of one uniform level (appendix Eqs. interior_face_conductances,
+// dirichlet_face_conductances, mode_mass_coefficient), rediscretised on the
+// level's own cells.
+void build_level(const pic_poisson_desc &d, int nr, int nz, int nm, LevelHost &h) {
+    h.nr = nr;
+    h.nz = nz;
+    h.dr = (d.r_out - d.r_in) / nr;
+    h.dz = (d.z1 - d.z0) / nz;
+    const double dr = h.dr, dz = h.dz;
+    h.cw.assign(nr, 0.0);
+    h.ce.assign(nr, 0.0);
+    h.cz.assign(nr, 0.0);
+    h.d0r.assign(nr, 0.0);
+    h.mu.assign(nr, 0.0);
+    for (int i = 0; i < nr; ++i) {
+        const double rm = d.r_in + i * dr, rp = d.r_in + (i + 1) * dr, rc = d.r_in + (i + 0.5) * dr;
+        const double gw = (i > 0) ? rm * dz / dr : rm * dz / (0.5 * dr);
+        const double ge = (i < nr - 1) ? rp * dz / dr : rp * dz / (0.5 * dr);
+        h.cw[i] = (i > 0) ? gw : 0.0;
+        h.ce[i] = (i < nr - 1) ? ge : 0.0;
+        h.d0r[i] = gw + ge;
+        h.cz[i] = rc * dr / dz;
+        h.mu[i] = dr * dz / rc;
+    }
+    h.ncls = std::min(nz, 3);
+    if (nz == 1) h.tz = {4.0};
+    else if (nz == 2) h.tz = {3.0, 3.0};
+    else h.tz = {3.0, 2.0, 3.0};
+    const size_t nt = (size_t)h.ncls * nr * nm;
+    h.diag.assign(nt, 0.0);
+    h.invd.assign(nt, 0.0);
+    h.hw.assign(nt, 0.0);
+    h.he.assign(nt, 0.0);
+    h.hz.assign(nt, 0.0);
+    for (int c = 0; c < h.ncls; ++c)
+        for (int i = 0; i < nr; ++i)
+            for (int m = 0; m < nm; ++m) {
+                const size_t t = ((size_t)c * nr + i) * nm + m;
+                const double dg = h.d0r[i] + h.tz[c] * h.cz[i] + lambda_m(d, m) * h.mu[i];
+                h.diag[t] = dg;
+                h.invd[t] = 1.0 / dg;
+                h.hw[t] = h.cw[i] / dg;
+                h.he[t] = h.ce[i] / dg;
+                h.hz[t] = h.cz[i] / dg;
+            }
+}
+
+// Coarsest-level factors: axial eigenbasis (closed form for the uniform
+// cell-centred Dirichlet operator: V_kj ~ sin(pi (j+1)(k+1/2)/nz), eigenvalue
+// 4 sin^2(pi (j+1) / (2 nz))) and the Thomas factorisation of the radial
+// tridiagonal system of every (mode, axial eigenvector).
+void coarse_factors(const ProblemPlan &pp_, std::vector<double> &V, std::vector<double> &e, std::vector<double> &piv,
+                    std::vector<double> &cpr) {
+    const LevelHost &h = pp_.lv[pp_.L - 1];
+    const int nr = h.nr, nz = h.nz, nm = pp_.nm;
+    V.assign((size_t)nz * nz, 0.0);
+    std::vector<double> lam_z(nz);
+    for (int j = 0; j < nz; ++j) {
+        const int p = j + 1;
+        const double nrm = (p < nz) ? std::sqrt(2.0 / nz) : std::sqrt(1.0 / nz);
+        for (int k = 0; k < nz; ++k) V[(size_t)k * nz + j] = nrm * std::sin(kPi * p * (k + 0.5) / nz);
+        const double s = std::sin(kPi * p / (2.0 * nz));
+        lam_z[j] = 4.0 * s * s;
+    }
+    e.assign(nr, 0.0);
+    for (int i = 0; i + 1 < nr; ++i) e[i] = -h.ce[i];
+    piv.assign((size_t)nm * nz * nr, 0.0);
+    cpr.assign((size_t)nm * nz * nr, 0.0);
+    for (int m = 0; m < nm; ++m) {
+        const double lm = lambda_m(pp_.d, m);
+        for (int j = 0; j < nz; ++j) {
+            double *pv = &piv[((size_t)m * nz + j) * nr];
+            double *cp = &cpr[((size_t)m * nz + j) * nr];
+            double prev_c = 0.0;
+            for (int i = 0; i < nr; ++i) {
+                const double di = h.d0r[i] + lm * h.mu[i] + lam_z[j] * h.cz[i];
+                const double den = di - (i > 0 ? e[i - 1] * prev_c : 0.0);
+                pv[i] = 1.0 / den;
+                cp[i] = (i + 1 < nr) ? e[i] * pv[i] : 0.0;
+                prev_c = cp[i];
+            }
+        }
+    }
+}
+
+// Bump allocator over one device allocation (sizing pass when base == nullptr).
+struct Carver {
+    char *base = nullptr;
+    size_t off = 0;
+    template <class T> T *take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+int setup_problem(ProblemPlan &q, const pic_poisson_desc &d) {
+    q.d = d;
+    if (d.phi_r_in_z) {
+        q.rin_z.assign(d.phi_r_in_z, d.phi_r_in_z + d.nz);
+        q.d.phi_r_in_z = q.rin_z.data();
+    }
+    if (d.phi_r_out_z) {
+        q.rout_z.assign(d.phi_r_out_z, d.phi_r_out_z + d.nz);
+        q.d.phi_r_out_z = q.rout_z.data();
+    }
+    int nr[PIC_POISSON_MAX_LEVELS], nz[PIC_POISSON_MAX_LEVELS];
+    int rc = hierarchy(q.d, nr, nz, &q.L);
+    if (rc) return rc;
+    q.nm = d.ntheta / 2 + 1;
+    q.lv.resize(q.L);
+    for (int l = 0; l < q.L; ++l) build_level(q.d, nr[l], nz[l], q.nm, q.lv[l]);
+    return PIC_POISSON_OK;
+}
+
+template <class T, class V> void carve_level(const LevelHost &h, int nm, int nt, Carver &c, LevelDev<T> &v) {
+    v.nr = h.nr;
+    v.nz = h.nz;
+    v.nm = nm;
+    v.ncls = h.ncls;
+    v.nt = nt;
+    v.init = 0;
+    const size_t n = (size_t)h.nr * h.nz * nm, ntab = (size_t)h.ncls * h.nr * nm;
+    v.u = c.take<V>(n);
+    v.b = c.take<V>(n);
+    v.bh = c.take<V>(n);
+    v.cw = c.take<T>(h.nr);
+    v.ce = c.take<T>(h.nr);
+    v.cz = c.take<T>(h.nr);
+    v.invd = c.take<T>(ntab);
+    v.diag = c.take<T>(ntab);
+    v.hw = c.take<T>(ntab);
+    v.he = c.take<T>(ntab);
+    v.hz = c.take<T>(ntab);
+}
+
+template <class T> void carve_coarse(const ProblemPlan &q, Carver &c, CoarseDev<T> &cd) {
+    const LevelHost &h = q.lv[q.L - 1];
+    const size_t nf = (size_t)q.nm * h.nz * h.nr;
+    cd.nr = h.nr;
+    cd.nz = h.nz;
+    cd.nm = q.nm;
+    cd.V = c.take<T>((size_t)h.nz * h.nz);
+    cd.e = c.take<T>(h.nr);
+    cd.piv = c.take<T>(nf);
+    cd.cpr = c.take<T>(nf);
+}
+
+template <class T> void carve_hier(pic_poisson_plan_s &P, Carver &c, Hier<T> &H) {
+    const int nl = std::max(P.Lmax - 1, 0);
+    H.smooth.assign(nl, nullptr);
+    H.restr.assign(nl, nullptr);
+    H.prolong.assign(nl, nullptr);
+    for (int l = 0; l < nl; ++l) {
+        H.smooth[l] = c.take<LaunchTab<T>>(1);
+        H.restr[l] = c.take<LaunchTab<T>>(1);
+        H.prolong[l] = c.take<LaunchTab<T>>(1);
+    }
+    H.coarse = c.take<CoarseTab<T>>(1);
+}
+
+// Lay out (or size) the whole device workspace.
+void carve(pic_poisson_plan_s &P, Carver &c) {
+    const bool mixed = P.shared.precision == PIC_POISSON_MIXED;
+    size_t g_restr0 = 0, g_single = 0, g_defect = 0, g_fft = 0, g_api = 0;
+    for (int p = 0; p < P.n; ++p) {
+        ProblemPlan &q = P.pr[p];
+        const int nt = q.d.ntheta;
+        q.dl.assign(mixed ? 1 : q.L, LevelDev<double>{});
+        q.fl.assign(mixed ? q.L : 0, LevelDev<float>{});
+        for (int l = 0; l < (int)q.dl.size(); ++l) carve_level<double, double2>(q.lv[l], q.nm, nt, c, q.dl[l]);
+        for (int l = 0; l < (int)q.fl.size(); ++l) carve_level<float, float2>(q.lv[l], q.nm, nt, c, q.fl[l]);
+        if (mixed) carve_coarse(q, c, q.cf);
+        else carve_coarse(q, c, q.cd);
+        const int M = nt / 2;
+        q.tw = (const double *)c.take<double2>(std::max(M / 2, 1));
+        q.tw2 = (const double *)c.take<double2>(M + 1);
+        q.s0 = c.take<double>(q.lv[0].nr);
+        q.bD0 = c.take<double>((size_t)q.lv[0].nr * q.lv[0].nz);
+        const LevelHost &h0 = q.lv[0];
+        const size_t n0 = (size_t)h0.nr * h0.nz * q.nm;
+        g_fft += (size_t)h0.nz * ((h0.nr + FFT_TI - 1) / FFT_TI);
+        if (q.L > 1) g_restr0 += mg_blocks((size_t)q.lv[1].nr * q.lv[1].nz * q.nm);
+        else g_single += mg_blocks(n0);
+        g_defect += mg_blocks(n0);
+        if (p == 0) g_api = mg_blocks(n0);
+    }
+    P.fwd = c.take<FFTTab>(1);
+    P.guess = c.take<FFTTab>(1);
+    P.inv = c.take<FFTTab>(1);
+    P.api_fft = c.take<FFTTab>(1);
+    if (mixed) carve_hier(P, c, P.h32);
+    else carve_hier(P, c, P.h64);
+    P.res_single = c.take<LaunchTab<double>>(1);
+    P.api_res = c.take<LaunchTab<double>>(1);
+    P.defect = c.take<DefectTab>(1);
+    P.ctrl = c.take<Ctrl>(1);
+    P.npartials = std::max(std::max(g_restr0 + g_single, g_defect), 2 * g_api) + 64;
+    P.npartials_fwd = g_fft + 64;
+    P.partials = c.take<double>(P.npartials);
+    P.partials_fwd = c.take<double>(P.npartials_fwd);
+    P.dsum = c.take<double>(8);
+}
+
+template <class T> void to_dev(const std::vector<double> &src, const T *dst, cudaStream_t st, cudaError_t &err) {
+    if (err != cudaSuccess || src.empty()) return;
+    std::vector<T> conv(src.begin(), src.end());
+    err = cudaMemcpyAsync((void *)dst, conv.data(), conv.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+}
+
+template <class X> void blob_to_dev(const X &src, X *dst, cudaStream_t st, cudaError_t &err) {
+    if (err != cudaSuccess || !dst) return;
+    err = cudaMemcpyAsync(dst, &src, sizeof(X), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+}
+
+template <class T> void upload_level(const LevelHost &h, const LevelDev<T> &v, cudaStream_t st, cudaError_t &err) {
+    to_dev(h.cw, v.cw, st, err);
+    to_dev(h.ce, v.ce, st, err);
+    to_dev(h.cz, v.cz, st, err);
+    to_dev(h.invd, v.invd, st, err);
+    to_dev(h.diag, v.diag, st, err);
+    to_dev(h.hw, v.hw, st, err);
+    to_dev(h.he, v.he, st, err);
+    to_dev(h.hz, v.hz, st, err);
+}
+
+// Launch tables of one precision's hierarchy.  views(q) is problem q's level list.
+template <class T, class Views, class Coarse>
+void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, cudaStream_t st, cudaError_t &err) {
+    const int nl = std::max(P.Lmax - 1, 0);
+    const int pre = P.shared.pre_sweeps, post = P.shared.post_sweeps;
+    H.g_smooth.assign(nl, 0);
+    H.g_restr.assign(nl, 0);
+    H.g_prolong.assign(nl, 0);
+    for (int l = 0; l < nl; ++l) {
+        LaunchTab<T> ts{}, tr{}, tp{};
+        for (int p = 0; p < P.n; ++p) {
+            const ProblemPlan &q = P.pr[p];
+            if (l >= q.L - 1) continue;
+            const std::vector<LevelDev<T>> &v = views(q);
+            LevelDev<T> f = v[l];
+            f.init = (l + 1 == q.L - 1) ? 0 : (pre > 0 ? 2 : 1);
+            const size_t half = (size_t)f.nz * (f.nr / 2) * f.nm, full = (size_t)f.nz * f.nr * f.nm;
+            const size_t coarse_n = (size_t)v[l + 1].nz * v[l + 1].nr * f.nm;
+            ts.f[ts.n] = f;
+            ts.start[ts.n + 1] = ts.start[ts.n] + mg_blocks(half);
+            ++ts.n;
+            tr.f[tr.n] = f;
+            tr.c[tr.n] = v[l + 1];
+            tr.start[tr.n + 1] = tr.start[tr.n] + mg_blocks(coarse_n);
+            ++tr.n;
+            tp.f[tp.n] = f;
+            tp.c[tp.n] = v[l + 1];
+            tp.start[tp.n + 1] = tp.start[tp.n] + mg_blocks(post > 0 ? half : full);
+            ++tp.n;
+        }
+        H.g_smooth[l] = ts.start[ts.n];
+        H.g_restr[l] = tr.start[tr.n];
+        H.g_prolong[l] = tp.start[tp.n];
+        if (ts.n == 0) {
+            H.smooth[l] = H.restr[l] = H.prolong[l] = nullptr;
+            continue;
+        }
+        blob_to_dev(ts, H.smooth[l], st, err);
+        blob_to_dev(tr, H.restr[l], st, err);
+        blob_to_dev(tp, H.prolong[l], st, err);
+    }
+    CoarseTab<T> tc{};
+    for (int p = 0; p < P.n; ++p) {
+        const ProblemPlan &q = P.pr[p];
+        const CoarseDev<T> &cd = coarse(q);
+        tc.f[tc.n] = views(q)[q.L - 1];
+        tc.c[tc.n] = cd;
+        tc.start[tc.n + 1] = tc.start[tc.n] + (unsigned)q.nm;
+        tc.smem = std::max(tc.smem, (size_t)2 * cd.nr * cd.nz * sizeof(V2<T>) + (size_t)cd.nz * cd.nz * sizeof(T));
+        ++tc.n;
+    }
+    H.g_coarse = tc.start[tc.n];
+    H.smem_coarse = tc.smem;
+    blob_to_dev(tc, H.coarse, st, err);
+}
+
+int upload(pic_poisson_plan_s &P) {
+    cudaError_t err = cudaSuccess;
+    const cudaStream_t st = P.stream;
+    const bool mixed = P.shared.precision == PIC_POISSON_MIXED;
+    for (int p = 0; p < P.n; ++p) {
+        ProblemPlan &q = P.pr[p];
+        for (size_t l = 0; l < q.dl.size(); ++l) upload_level(q.lv[l], q.dl[l], st, err);
+        for (size_t l = 0; l < q.fl.size(); ++l) upload_level(q.lv[l], q.fl[l], st, err);
+        std::vector<double> V, e, piv, cpr;
+        coarse_factors(q, V, e, piv, cpr);
+        if (!mixed) {
+            to_dev(V, q.cd.V, st, err);
+            to_dev(e, q.cd.e, st, err);
+            to_dev(piv, q.cd.piv, st, err);
+            to_dev(cpr, q.cd.cpr, st, err);
+        } else {
+            to_dev(V, q.cf.V, st, err);
+            to_dev(e, q.cf.e, st, err);
+            to_dev(piv, q.cf.piv, st, err);
+            to_dev(cpr, q.cf.cpr, st, err);
+        }
+        const int nt = q.d.ntheta, M = nt / 2;
+        std::vector<double> tw(2 * std::max(M / 2, 1), 0.0), tw2(2 * (M + 1), 0.0);
+        for (int t = 0; t < M / 2; ++t) {
+            tw[2 * t] = std::cos(2.0 * kPi * t / M);
+            tw[2 * t + 1] = -std::sin(2.0 * kPi * t / M);
+        }
+        if (M / 2 == 0) tw[0] = 1.0;
+        for (int m = 0; m <= M; ++m) {
+            tw2[2 * m] = std::cos(2.0 * kPi * m / nt);
+            tw2[2 * m + 1] = -std::sin(2.0 * kPi * m / nt);
+        }
+        to_dev(tw, q.tw, st, err);
+        to_dev(tw2, q.tw2, st, err);
+        // level-0 right-hand-side factors: s_i (Eq. mode_rhs) and b^D (Eq. boundary_rhs_appendix)
+        const LevelHost &h = q.lv[0];
+        std::vector<double> s(h.nr), bD((size_t)h.nr * h.nz, 0.0);
+        for (int i = 0; i < h.nr; ++i) {
+            const double rc = q.d.r_in + (i + 0.5) * h.dr;
+            s[i] = rc * h.dr * h.dz / q.d.eps0;
+        }
+        for (int k = 0; k < h.nz; ++k)
+            for (int i = 0; i < h.nr; ++i) {
+                double v = 0.0;
+                const double rm = q.d.r_in + i * h.dr, rp = q.d.r_in + (i + 1) * h.dr;
+                if (i == 0) v += rm * h.dz / (0.5 * h.dr) * wall_rin(q.d, k);
+                if (i == h.nr - 1) v += rp * h.dz / (0.5 * h.dr) * wall_rout(q.d, k);
+                if (k == 0) v += 2.0 * h.cz[i] * q.d.phi_z0;
+                if (k == h.nz - 1) v += 2.0 * h.cz[i] * q.d.phi_z1;
+                bD[(size_t)k * h.nr + i] = v;
+            }
+        to_dev(s, q.s0, st, err);
+        to_dev(bD, q.bD0, st, err);
+    }
+
+    // transforms
+    FFTTab &F = P.h_fwd, &G = P.h_guess, &I = P.h_inv;
+    F = FFTTab{};
+    G = FFTTab{};
+    I = FFTTab{};
+    size_t smem = 0;
+    for (int p = 0; p < P.n; ++p) {
+        const ProblemPlan &q = P.pr[p];
+        const LevelDev<double> &d0 = q.dl[0];
+        FFTProb fp{};
+        fp.nr = d0.nr;
+        fp.nt = q.d.ntheta;
+        fp.nz = d0.nz;
+        fp.nm = q.nm;
+        fp.ncls = d0.ncls;
+        int lg = 0;
+        while ((1 << lg) < q.d.ntheta / 2) ++lg;
+        fp.log2M = lg;
+        fp.tw = q.tw;
+        fp.tw2 = q.tw2;
+        FFTProb f = fp, g = fp, iv = fp;
+        f.s = q.s0;
+        f.bD = q.bD0;
+        f.invd = mixed ? nullptr : d0.invd;
+        f.b = d0.b;
+        f.bh = mixed ? nullptr : d0.bh;
+        g.b = d0.u;                         // initial guess: plain 1/N transform of phi into u
+        iv.uhat = d0.u;
+        const unsigned blocks = (unsigned)(d0.nz * ((d0.nr + FFT_TI - 1) / FFT_TI));
+        F.p[p] = f;
+        G.p[p] = g;
+        I.p[p] = iv;
+        F.start[p + 1] = G.start[p + 1] = I.start[p + 1] = F.start[p] + blocks;
+        smem = std::max(smem, fft_smem_bytes(q.d.ntheta));
+    }
+    F.n = G.n = I.n = P.n;
+    F.smem = G.smem = I.smem = smem;
+    P.g_fft = F.start[P.n];
+    P.smem_fft = smem;
+    blob_to_dev(F, P.fwd, st, err);
+    blob_to_dev(G, P.guess, st, err);
+    blob_to_dev(I, P.inv, st, err);
+
+    // hierarchy tables
+    if (mixed) {
+        build_hier<float>(P, P.h32, [](const ProblemPlan &q) -> const std::vector<LevelDev<float>> & { return q.fl; },
+                          [](const ProblemPlan &q) -> const CoarseDev<float> & { return q.cf; }, st, err);
+    } else {
+        build_hier<double>(P, P.h64, [](const ProblemPlan &q) -> const std::vector<LevelDev<double>> & { return q.dl; },
+                           [](const ProblemPlan &q) -> const CoarseDev<double> & { return q.cd; }, st, err);
+    }
+
+    // single-level problems' residual norms; defect table; stage-call table
+    LaunchTab<double> rs{};
+    DefectTab dt{};
+    for (int p = 0; p < P.n; ++p) {
+        const ProblemPlan &q = P.pr[p];
+        const size_t n0 = (size_t)q.lv[0].nr * q.lv[0].nz * q.nm;
+        if (q.L == 1) {
+            rs.f[rs.n] = q.dl[0];
+            rs.start[rs.n + 1] = rs.start[rs.n] + mg_blocks(n0);
+            ++rs.n;
+        }
+        if (mixed) {
+            dt.d[dt.n] = q.dl[0];
+            dt.s[dt.n] = q.fl[0];
+            dt.init_red[dt.n] = (q.L > 1 && P.shared.pre_sweeps > 0) ? 1 : 0;
+            dt.start[dt.n + 1] = dt.start[dt.n] + mg_blocks(n0);
+            ++dt.n;
+        }
+    }
+    P.g_res_single = rs.start[rs.n];
+    P.g_defect = dt.start[dt.n];
+    blob_to_dev(rs, P.res_single, st, err);
+    blob_to_dev(dt, P.defect, st, err);
+    P.h_api_res = LaunchTab<double>{};
+    P.h_api_res.n = 1;
+    P.h_api_res.f[0] = P.pr[0].dl[0];
+    P.g_api_res = mg_blocks((size_t)P.pr[0].lv[0].nr * P.pr[0].lv[0].nz * P.pr[0].nm);
+    P.h_api_res.start[1] = P.g_api_res;
+
+    // per-problem ranges of the residual-norm partials and control state
+    Ctrl &C = P.hctrl;
+    C = Ctrl{};
+    C.n = P.n;
+    C.scaled = mixed ? 1 : 0;
+    C.inc = mixed ? P.shared.inner_cycles : 1;
+    const unsigned g_restr0 = (!mixed && P.Lmax > 1) ? P.h64.g_restr[0] : 0;
+    P.res_single_offset = g_restr0;
+    unsigned b0 = 0;
+    int is = 0;
+    for (int p = 0; p < P.n; ++p) {
+        const ProblemPlan &q = P.pr[p];
+        C.count[p] = (double)q.lv[0].nr * q.lv[0].nz * q.d.ntheta;
+        if (mixed) {
+            C.rbegin[p] = dt.start[p];
+            C.rend[p] = dt.start[p + 1];
+        } else if (q.L > 1) {
+            // the level-0 restriction table lists the multi-level problems in order
+            const unsigned nb = mg_blocks((size_t)q.lv[1].nr * q.lv[1].nz * q.nm);
+            C.rbegin[p] = b0;
+            C.rend[p] = b0 + nb;
+            b0 += nb;
+        } else {
+            C.rbegin[p] = g_restr0 + rs.start[is];
+            C.rend[p] = g_restr0 + rs.start[is + 1];
+            ++is;
+        }
+    }
+    if (err != cudaSuccess) {
+        set_error("uploading plan tables failed: %s", cudaGetErrorString(err));
+        return PIC_POISSON_ECUDA;
+    }
+    return PIC_POISSON_OK;
+}
+
+int same_settings(const pic_poisson_desc &a, const pic_poisson_desc &b) {
+    return a.precision == b.precision && a.max_cycles == b.max_cycles && a.pre_sweeps == b.pre_sweeps &&
+           a.post_sweeps == b.post_sweeps && a.inner_cycles == b.inner_cycles && a.flags == b.flags;
+}
+
+int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
+    if (n < 1 || n > kMaxBatch) {
+        set_error("batch size %d outside [1, %d]", n, kMaxBatch);
+        return PIC_POISSON_EINVAL;
+    }
+    P.n = n;
+    P.pr.resize(n);
+    for (int p = 0; p < n; ++p) {
+        pic_poisson_desc d;
+        int rc = resolve(&descs[p], &d);
+        if (rc) return rc;
+        if (p == 0) P.shared = d;
+        else if (!same_settings(P.shared, d)) {
+            set_error("problem %d: precision, max_cycles, sweeps, inner_cycles and flags must match problem 0", p);
+            return PIC_POISSON_EINVAL;
+        }
+        rc = setup_problem(P.pr[p], d);
+        if (rc) return rc;
+        P.Lmax = std::max(P.Lmax, P.pr[p].L);
+    }
+    return PIC_POISSON_OK;
+}
+
+}  // namespace
+
+int plan_enter(pic_poisson_plan_s *P) {
+    clear_error();
+    if (!P) {
+        set_error("plan is NULL");
+        return PIC_POISSON_EINVAL;
+    }
+    PP_CUDA(cudaSetDevice(P->device));
+    return PIC_POISSON_OK;
+}
+
+}  // namespace pp
+
+using namespace pp;
+
+extern "C" {
+
+const char *pic_poisson_last_error(void) { return pp::last_error_text(); }
+
+int pic_poisson_query(const pic_poisson_desc *desc, pic_poisson_layout *out) {
+    clear_error();
+    pic_poisson_plan_s P;
+    int rc = setup_plan(P, desc, 1);
+    if (rc) return rc;
+    if (out) {
+        memset(out, 0, sizeof *out);
+        out->levels = P.pr[0].L;
+        for (int l = 0; l < P.pr[0].L; ++l) {
+            out->nr[l] = P.pr[0].lv[l].nr;
+            out->nz[l] = P.pr[0].lv[l].nz;
+        }
+        out->n_modes = P.pr[0].nm;
+        Carver c;
+        carve(P, c);
+        out->workspace_bytes = c.off;
+    }
+    return PIC_POISSON_OK;
+}
+
+int pic_poisson_cell_coeffs(const pic_poisson_desc *desc, int i, int k, double *out) {
+    clear_error();
+    pic_poisson_desc d;
+    int rc = resolve(desc, &d);
+    if (rc) return rc;
+    if (!out || i < 0 || i >= d.nr || k < 0 || k >= d.nz) {
+        set_error("cell (%d, %d) outside the %d x %d grid or out is NULL", i, k, d.nr, d.nz);
+        return PIC_POISSON_EINVAL;
+    }
+    LevelHost h;
+    build_level(d, d.nr, d.nz, 1, h);
+    const bool dw = i == 0, de = i == d.nr - 1, ds = k == 0, dn = k == d.nz - 1;
+    const double rm = d.r_in + i * h.dr, rp = d.r_in + (i + 1) * h.dr;
+    out[0] = dw ? rm * h.dz / (0.5 * h.dr) : h.cw[i];
+    out[1] = de ? rp * h.dz / (0.5 * h.dr) : h.ce[i];
+    out[2] = ds ? 2.0 * h.cz[i] : h.cz[i];
+    out[3] = dn ? 2.0 * h.cz[i] : h.cz[i];
+    out[4] = dw;
+    out[5] = de;
+    out[6] = ds;
+    out[7] = dn;
+    out[8] = h.mu[i];
+    const double rc_ = d.r_in + (i + 0.5) * h.dr;
+    out[9] = rc_ * h.dr * h.dz / d.eps0;
+    const int tzc = d.nz == 1 ? 4 : ((k == 0 || k == d.nz - 1) ? 3 : 2);
+    out[10] = h.d0r[i] + tzc * h.cz[i];
+    double bd = 0.0;
+    if (dw) bd += out[0] * (d.phi_r_in_z ? d.phi_r_in_z[k] : d.phi_r_in);
+    if (de) bd += out[1] * (d.phi_r_out_z ? d.phi_r_out_z[k] : d.phi_r_out);
+    if (ds) bd += out[2] * d.phi_z0;
+    if (dn) bd += out[3] * d.phi_z1;
+    out[11] = bd;
+    return PIC_POISSON_OK;
+}
+
+int pic_poisson_plan_batch(const pic_poisson_desc *descs, int n, void *stream, pic_poisson_plan_t *out) {
+    clear_error();
+    if (!out || !descs) {
+        set_error("descs and out must be non-NULL");
+        return PIC_POISSON_EINVAL;
+    }
+    *out = nullptr;
+    pic_poisson_plan_s *P = new (std::nothrow) pic_poisson_plan_s;
+    if (!P) {
+        set_error("host allocation failed");
+        return PIC_POISSON_ENOMEM;
+    }
+    int rc = setup_plan(*P, descs, n);
+    if (rc) {
+        delete P;
+        return rc;
+    }
+    P->stream = (cudaStream_t)stream;
+    cudaError_t err = cudaGetDevice(&P->device);
+    if (err != cudaSuccess) {
+        set_error("cudaGetDevice: %s", cudaGetErrorString(err));
+        delete P;
+        return PIC_POISSON_ECUDA;
+    }
+    Carver c;
+    carve(*P, c);
+    P->arena_bytes = c.off;
+    err = cudaMalloc(&P->arena, P->arena_bytes);
+    if (err != cudaSuccess) {
+        set_error("cudaMalloc(%zu) failed: %s", P->arena_bytes, cudaGetErrorString(err));
+        cudaGetLastError();
+        delete P;
+        return PIC_POISSON_ENOMEM;
+    }
+    c = Carver{(char *)P->arena, 0};
+    carve(*P, c);
+    err = cudaMallocHost(&P->hctrl_out, sizeof(Ctrl));
+    if (err == cudaSuccess) err = cudaMallocHost(&P->hsum, 8 * sizeof(double));
+    if (err != cudaSuccess) {
+        set_error("cudaMallocHost failed: %s", cudaGetErrorString(err));
+        pic_poisson_destroy(P);
+        return PIC_POISSON_ENOMEM;
+    }
+    rc = upload(*P);
+    if (rc) {
+        pic_poisson_destroy(P);
+        return rc;
+    }
+    *out = P;
+    return PIC_POISSON_OK;
+}
+
+int pic_poisson_plan(const pic_poisson_desc *desc, void *stream, pic_poisson_plan_t *out) {
+    return pic_poisson_plan_batch(desc, 1, stream, out);
+}
+
+int pic_poisson_set_stream(pic_poisson_plan_t plan, void *stream) {
+    int rc = plan_enter(plan);
+    if (rc) return rc;
+    plan->stream = (cudaStream_t)stream;
+    return PIC_POISSON_OK;
+}
+
+int pic_poisson_destroy(pic_poisson_plan_t plan) {
+    if (!plan) return PIC_POISSON_OK;
+    cudaSetDevice(plan->device);
+    if (plan->stream) cudaStreamSynchronize(plan->stream);
+    else cudaDeviceSynchronize();
+    if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->cap0) cudaStreamDestroy(plan->cap0);
+    if (plan->cap1) cudaStreamDestroy(plan->cap1);
+    for (cudaEvent_t e : plan->evs) cudaEventDestroy(e);
+    if (plan->arena) cudaFree(plan->arena);
+    if (plan->hctrl_out) cudaFreeHost(plan->hctrl_out);
+    if (plan->hsum) cudaFreeHost(plan->hsum);
+    if (plan->stage_rho) cudaFree(plan->stage_rho);
+    if (plan->stage_phi) cudaFree(plan->stage_phi);
+    delete plan;
+    return PIC_POISSON_OK;
+}
+
+}  // extern "C"

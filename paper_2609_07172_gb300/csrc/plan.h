@@ -1,0 +1,89 @@
+// The plan: host-side description of a batch of problems, its device
+// workspace, the launch tables of every kernel, and the captured graph.
+#pragma once
+
+#include "internal.h"
+
+namespace pp {
+
+struct ProblemPlan {
+    pic_poisson_desc d{};                       // resolved descriptor (wall arrays point below)
+    std::vector<double> rin_z, rout_z;
+    int L = 0, nm = 0;
+    std::vector<LevelHost> lv;
+    std::vector<LevelDev<double>> dl;           // FP64 levels (all for FP64 plans, level 0 for mixed)
+    std::vector<LevelDev<float>> fl;            // FP32 levels (mixed)
+    CoarseDev<double> cd{};
+    CoarseDev<float> cf{};
+    const double *tw = nullptr, *tw2 = nullptr; // FFT twiddles
+    double *s0 = nullptr, *bD0 = nullptr;       // level-0 right-hand-side factors
+};
+
+// Launch tables of one precision's hierarchy, per level l = 0 .. Lmax-2
+// (problems that have a level below l), plus the coarsest-level solve.
+template <class T> struct Hier {
+    std::vector<LaunchTab<T> *> smooth, restr, prolong;   // device tables (null when no problem takes part)
+    std::vector<unsigned> g_smooth, g_restr, g_prolong;   // grids
+    CoarseTab<T> *coarse = nullptr;
+    unsigned g_coarse = 0;
+    size_t smem_coarse = 0;
+};
+
+// Algorithmic traffic / arithmetic / launches recorded per kernel class.
+struct Tally {
+    double bytes[PIC_POISSON_NPHASE] = {0}, flops[PIC_POISSON_NPHASE] = {0};
+    int launches[PIC_POISSON_NPHASE] = {0};
+};
+
+}  // namespace pp
+
+struct pic_poisson_plan_s {
+    int n = 0;
+    std::vector<pp::ProblemPlan> pr;
+    pic_poisson_desc shared{};                  // settings common to the batch (descs[0])
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap0 = nullptr, cap1 = nullptr;// capture streams (graph construction)
+    int Lmax = 0;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+
+    // launch tables (device) and their grids
+    pp::FFTTab *fwd = nullptr, *guess = nullptr, *inv = nullptr, *api_fft = nullptr;
+    unsigned g_fft = 0;
+    size_t smem_fft = 0;
+    pp::FFTTab h_fwd{}, h_guess{}, h_inv{};     // host copies (rho / phi pointers patched per solve)
+    pp::Hier<double> h64;
+    pp::Hier<float> h32;
+    pp::LaunchTab<double> *res_single = nullptr;// FP64 residual norms of single-level problems
+    unsigned g_res_single = 0;
+    unsigned res_single_offset = 0;             // their place in the partials buffer
+    pp::LaunchTab<double> *api_res = nullptr;   // mode-residual stage call (problem 0)
+    pp::LaunchTab<double> h_api_res{};
+    unsigned g_api_res = 0;
+    pp::DefectTab *defect = nullptr;
+    unsigned g_defect = 0;
+
+    pp::Ctrl *ctrl = nullptr;                   // device
+    pp::Ctrl hctrl{};                           // per-solve initial state
+    pp::Ctrl *hctrl_out = nullptr;              // pinned, results
+    double *partials = nullptr, *partials_fwd = nullptr;
+    size_t npartials = 0, npartials_fwd = 0;
+    double *dsum = nullptr, *hsum = nullptr;    // small device / pinned scratch for stage calls
+
+    // graph of the whole solve (PIC_POISSON_GRAPH)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphConditionalHandle handle{};
+    pp::Tally seg[3];                           // prologue, loop body, epilogue (recorded at capture)
+
+    std::vector<cudaEvent_t> evs;               // PROFILE events
+    double *stage_rho = nullptr, *stage_phi = nullptr;   // pic_poisson_solve_host staging
+    const double *last_rho[pp::kMaxBatch] = {};
+    double *last_phi[pp::kMaxBatch] = {};
+    bool io_valid = false;
+};
+
+namespace pp {
+int plan_enter(pic_poisson_plan_s *P);
+}

@@ -116,3 +116,19 @@ def test_cell_coeffs_match_oracle_everywhere():
 def test_cell_coeffs_rejects_outside():
     with pytest.raises(B.PicPoissonError):
         B.cell_coeffs(W.c0_problem(), 32, 0)
+
+
+def test_batch_plan_rejects_mismatched_settings_before_touching_the_gpu():
+    a, ka = B.make_desc(W.c0_problem())
+    b, kb = B.make_desc(W.annulus(16, 8, 16), pre_sweeps=1)
+    descs = (B.Desc * 2)(a, b)
+    out = ctypes.c_void_p()
+    assert B.load().pic_poisson_plan_batch(descs, 2, None, ctypes.byref(out)) == B.EINVAL
+    assert "must match problem 0" in B.last_error()
+    assert B.load().pic_poisson_plan_batch(descs, 0, None, ctypes.byref(out)) == B.EINVAL
+    assert B.load().pic_poisson_plan_batch(descs, 65, None, ctypes.byref(out)) == B.EINVAL
+
+
+def test_unknown_flags_rejected():
+    d, _ = B.make_desc(W.c0_problem(), flags=64)
+    assert B.load().pic_poisson_query(ctypes.byref(d), None) == B.EINVAL

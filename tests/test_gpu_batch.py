@@ -1,0 +1,116 @@
+"""Batched uneven problems, the CUDA-graph solve and previous-step guesses (GPU).
+
+One plan holds problems of different sizes, azimuthal resolutions and
+multigrid depths (including a single-level one); every kernel launch covers
+all of them.  Each problem's potential is compared with the FP64 oracle at the
+rounding floor.  The graph path (device-side while loop) must reproduce the
+host-driven loop bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import narrow_span, rel_l2, small_rin, with_bias_walls
+from paper_2609_07172_gb300 import FP64, MIXED, BatchPlan, Plan, binding as B, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {FP64: 1e-12, MIXED: 1e-10}
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def uneven_problems():
+    dims = [(32, 16, 32), (40, 8, 24), (64, 32, 48), (15, 4, 9), (48, 2, 16), (96, 16, 40), (128, 64, 64),
+            (64, 128, 32)]
+    return [with_bias_walls(W.annulus(*d)) for d in dims] + [narrow_span(), small_rin()]
+
+
+@pytest.fixture(scope="module")
+def uneven_refs():
+    probs = uneven_problems()
+    rhos = [W.rho_plasma(p, seed=20 + i) for i, p in enumerate(probs)]
+    refs = [oracle.solve3d(oracle.grid_from_problem(p), r, tol=1e-15)[0] for p, r in zip(probs, rhos)]
+    return probs, rhos, refs
+
+
+@pytest.mark.parametrize("graph", [False, True], ids=["hostloop", "graph"])
+@pytest.mark.parametrize("precision", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_uneven_batch_matches_oracle(uneven_refs, precision, graph):
+    probs, rhos, refs = uneven_refs
+    with BatchPlan(probs, precision=precision, graph=graph) as bp:
+        phis, infos = bp.solve([dev(r) for r in rhos], tol=0.0)
+    for p, rho, ref, phi, info in zip(probs, rhos, refs, phis, infos):
+        got = phi.cpu().numpy()
+        assert info["status"] == B.OK, info
+        assert rel_l2(got, ref) <= TOL[precision], (p.shape, info)
+        assert oracle.relres(oracle.grid_from_problem(p), rho, got) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_graph_equals_host_loop_bitwise(precision):
+    p = with_bias_walls(W.annulus(64, 32, 48))
+    rho = dev(W.rho_plasma(p, seed=31))
+    with Plan(p, precision=precision) as a, Plan(p, precision=precision, graph=True) as g:
+        pa, ia = a.solve(rho, tol=1e-10)
+        pg, ig = g.solve(rho, tol=1e-10)
+    assert ia["cycles"] == ig["cycles"] and ia["status"] == ig["status"] == B.OK
+    assert ia["rel_res"] == ig["rel_res"]
+    assert torch.equal(pa, pg)
+    assert ia["bytes_phase"] == ig["bytes_phase"] and ia["launches"] == ig["launches"]
+
+
+def test_graph_reused_with_new_buffers_and_tolerances():
+    p = W.annulus(96, 16, 40)
+    with Plan(p) as a, Plan(p, graph=True) as g:
+        for seed, tol in ((1, 1e-6), (2, 1e-10), (3, 1e-8)):
+            rho = dev(W.rho_plasma(p, seed=seed))
+            pa, ia = a.solve(rho, tol=tol)
+            pg, ig = g.solve(rho, tol=tol)          # fresh output tensor each time
+            assert ia["cycles"] == ig["cycles"] and torch.equal(pa, pg)
+            assert ig["rel_res"] <= tol
+
+
+def test_batch_stops_when_every_problem_meets_tol():
+    probs = [W.annulus(64, 16, 64), W.annulus(128, 32, 100), W.annulus(32, 8, 32)]
+    rhos = [W.rho_plasma(p, seed=40 + i) for i, p in enumerate(probs)]
+    with BatchPlan(probs, graph=True) as bp:
+        phis, infos = bp.solve([dev(r) for r in rhos], tol=1e-9)
+    for p, rho, phi, info in zip(probs, rhos, phis, infos):
+        assert info["status"] == B.OK and info["rel_res"] <= 1e-9
+        true = oracle.relres(oracle.grid_from_problem(p), rho, phi.cpu().numpy())
+        assert true == pytest.approx(info["rel_res"], rel=1e-6, abs=1e-14)
+
+
+def test_batch_not_converged_and_nonfinite_are_per_problem():
+    probs = [W.annulus(64, 16, 64), W.annulus(32, 8, 32)]
+    rho0 = W.rho_plasma(probs[0], seed=1)
+    rho1 = W.rho_plasma(probs[1], seed=2)
+    rho1[0, 0, 0] = np.nan
+    with BatchPlan(probs, max_cycles=3) as bp:
+        with pytest.raises(B.PicPoissonError) as ei:
+            bp.solve([dev(rho0), dev(rho1)], tol=1e-14)
+    assert ei.value.status == B.ENONFINITE
+
+
+def test_previous_step_guess_sequence():
+    """Drifting m = 8 wave solved back to back; the previous potential as the
+    initial guess needs fewer cycles than a zero guess, at the same accuracy."""
+    p = W.annulus(64, 32, 48)
+    g = oracle.grid_from_problem(p)
+    phi_prev = None
+    with Plan(p, graph=True) as zero, Plan(p, graph=True, initial_guess=True) as warm:
+        for t in range(4):
+            rho_np = W.drifting_rho(p, t)
+            rho = dev(rho_np)
+            pz, iz = zero.solve(rho, tol=1e-10)
+            if phi_prev is None:
+                phi_prev = pz.clone()
+                continue
+            pw, iw = warm.solve(rho, phi_prev, tol=1e-10)
+            assert iw["status"] == B.OK and iw["cycles"] <= iz["cycles"]
+            assert oracle.relres(g, rho_np, pw.cpu().numpy()) <= 1.0001e-10
+            phi_prev = pw.clone()
