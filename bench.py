@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other precision form")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 24-problem uneven batch")
+    ap.add_argument("--no-sequence", action="store_true", help="skip the drifting-wave sequence")
+    ap.add_argument("--sequence-steps", type=int, default=200)
+    ap.add_argument("--tune-cache", default=None, help="JSON file caching autotuner results")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NR", "NTHETA", "NZ"), default=None,
                     help="override the 512 128 400 grid (profiling of smaller cases)")
     return ap.parse_args()
@@ -326,6 +330,15 @@ def run_ours(args):
     ref_phi = phi.clone()
     plan.close()
 
+    # ---- the same solves as one CUDA graph each (device-side convergence loop)
+    gplan = Plan(p, precision=prec, graph=True)
+    ms_g, infos_g, _ = time_form(gplan, rhos, phi, args.steps, args.warmup, args.tol, world, dist)
+    line["graph"] = {"ms_per_solve": ms_g / args.steps,
+                     "cycles_median": statistics.median([i["cycles"] for i in infos_g]),
+                     "note": "PIC_POISSON_GRAPH: whole solve one graph launch, convergence loop a device-side "
+                             "while node; same kernels and cycles as the headline host-driven loop"}
+    gplan.close()
+
     # ---- the other form on the same GPU and inputs (mixed FP32/FP64 when the headline is FP64)
     if not args.no_forms:
         other = MIXED if prec == FP64 else FP64
@@ -354,6 +367,11 @@ def run_ours(args):
             "hbm_roofline_solve": {"achieved_gbs": gbs2, "peak_gbs": hbm_peak, "frac": gbs2 / hbm_peak}}}
         plan2.close()
 
+    if not args.no_batch:
+        line["batch_uneven"] = run_batch(args, dev)
+    if not args.no_sequence:
+        line["sequence"] = run_sequence(args, dev, p)
+
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         ms, det = oracle_sample()
         line["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": det["threads"], "kind": "oracle",
@@ -364,6 +382,97 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batch(args, dev):
+    """24 independent problems of uneven sizes (seed 3) in one batched, autotuned,
+    graph-captured plan vs one graph-captured plan per problem."""
+    import torch
+    from paper_2609_07172_gb300 import FP64, BatchPlan, Plan, autotune
+    from paper_2609_07172_gb300 import workloads as W
+    probs = W.uneven_batch(3)
+    problems = [p for p, _ in probs]
+    rhos = [torch.from_numpy(W.rho_plasma(p, s)).to(dev) for p, s in probs]
+    tuned = autotune(problems, rhos, tol=args.tol, precision=FP64, graph=True, repeats=2, cache=args.tune_cache)
+    kw = {k: tuned[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads")}
+    bp = BatchPlan(problems, graph=True, **kw)
+    phis = [torch.empty_like(r) for r in rhos]
+    for _ in range(2):
+        bp.solve(rhos, phis, tol=args.tol)
+    steps = max(3, args.steps // 8)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        _, infos = bp.solve(rhos, phis, tol=args.tol)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / steps
+    launches = infos[0]["launches"]
+    bp.close()
+    plans = [Plan(q, graph=True, **kw) for q in problems]
+    for pl, r, f in zip(plans, rhos, phis):
+        pl.solve(r, f, tol=args.tol)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        for pl, r, f in zip(plans, rhos, phis):
+            pl.solve(r, f, tol=args.tol)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_each = e0.elapsed_time(e1) / steps
+    for pl in plans:
+        pl.close()
+    return {"workload": "24 problems, N_r in {64..512}, N_theta in {16..128}, N_z in {64,200,400} (seed 3), "
+                        "FP64, rel-res %g" % args.tol,
+            "cells_total": int(sum(q.nr * q.ntheta * q.nz for q in problems)),
+            "ms_per_batch": ms_batch, "ms_one_plan_per_problem": ms_each, "steps": steps,
+            "cycles": infos[0]["cycles"], "rel_res_max": max(i["rel_res"] for i in infos),
+            "launches_per_batch": launches, "autotuned": dict(kw, ms=tuned.get("ms")),
+            "autotune_candidates": len(tuned.get("tried", [])) or None}
+
+
+def run_sequence(args, dev, p):
+    """Drifting m = 8 wave (one azimuthal cell per step) at the headline grid,
+    solved back to back with the previous step's potential as initial guess,
+    against the zero initial guess, both graph-captured."""
+    import torch
+    from paper_2609_07172_gb300 import FP64, MIXED, Plan
+    from paper_2609_07172_gb300 import workloads as W
+    out = {"workload": "%dx%dx%d drifting m=8 wave, %d steps, GPU-drawn Poisson counts (seeded)"
+                       % (p.nr, p.ntheta, p.nz, args.sequence_steps), "tol": args.tol}
+    for name, prec in (("fp64", FP64), ("mixed", MIXED)):
+        warm = Plan(p, precision=prec, graph=True, initial_guess=True)
+        zero = Plan(p, precision=prec, graph=True)
+        phi = torch.zeros(p.shape, dtype=torch.float64, device=dev)
+        tmp = torch.empty_like(phi)
+        ms_w = ms_z = 0.0
+        cyc_w, cyc_z = [], []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for t in range(args.sequence_steps):
+            rho = W.drifting_rho_torch(p, t, device=dev)
+            torch.cuda.synchronize()
+            e0.record()
+            _, iw = warm.solve(rho, phi, tol=args.tol)
+            e1.record()
+            torch.cuda.synchronize()
+            if t > 0:
+                ms_w += e0.elapsed_time(e1)
+                cyc_w.append(iw["cycles"])
+            if t % 20 == 1:                      # zero-guess reference on a sample of steps
+                e0.record()
+                _, iz = zero.solve(rho, tmp, tol=args.tol)
+                e1.record()
+                torch.cuda.synchronize()
+                ms_z += e0.elapsed_time(e1)
+                cyc_z.append(iz["cycles"])
+        n = args.sequence_steps - 1
+        out[name] = {"ms_per_step_prev_guess": ms_w / n, "cycles_per_step_prev_guess": sum(cyc_w) / n,
+                     "ms_per_step_zero_guess": ms_z / len(cyc_z), "cycles_per_step_zero_guess":
+                         sum(cyc_z) / len(cyc_z), "zero_guess_sampled_steps": len(cyc_z)}
+        warm.close()
+        zero.close()
+    return out
 
 
 def main():

@@ -96,6 +96,7 @@ typedef struct {
     int pre_sweeps;            /* red-black sweeps before restriction; < 0 selects 2 */
     int post_sweeps;           /* red-black sweeps after prolongation; < 0 selects 2 */
     int inner_cycles;          /* mixed precision: FP32 V-cycles per FP64 defect correction; <= 0 selects 2 */
+    int smooth_threads;        /* threads per block of the smoother: 64, 128, 256 or 512; <= 0 selects 256 */
     unsigned flags;            /* PIC_POISSON_* flags */
 } pic_poisson_desc;
 
@@ -112,6 +113,19 @@ typedef struct {
     double bytes_phase[PIC_POISSON_NPHASE];/* algorithmic (compulsory) DRAM bytes per kernel class */
     double flops_phase[PIC_POISSON_NPHASE];/* algorithmic floating-point operations per kernel class */
 } pic_poisson_info;
+
+#define PIC_POISSON_MAX_TUNE 64
+
+typedef struct {
+    int pre_sweeps, post_sweeps;           /* best smoothing schedule */
+    int inner_cycles;                      /* best FP32 V-cycles per defect correction (mixed) */
+    int smooth_threads;                    /* best smoother block size */
+    double ms;                             /* its median wall time per solve call */
+    int tried;                             /* candidates timed (entries below) */
+    double ms_tried[PIC_POISSON_MAX_TUNE];
+    int pre_tried[PIC_POISSON_MAX_TUNE], post_tried[PIC_POISSON_MAX_TUNE];
+    int inner_tried[PIC_POISSON_MAX_TUNE], threads_tried[PIC_POISSON_MAX_TUNE];
+} pic_poisson_tuning;
 
 typedef struct {
     int levels;                            /* multigrid levels (1 = direct solve only) */
@@ -186,6 +200,22 @@ int pic_poisson_solve(pic_poisson_plan_t plan, const double *rho_dev, double *ph
  */
 int pic_poisson_solve_batch(pic_poisson_plan_t plan, const double *const *rho_dev, double *const *phi_dev,
                             double tol, pic_poisson_info *infos);
+
+/*
+ * Autotuner: choose pre/post sweeps, inner_cycles (mixed precision) and
+ * smooth_threads for the problems `descs` (as for pic_poisson_plan_batch) by
+ * timing complete solves of rho_dev[p] -> phi_dev[p] to `tol` (> 0).  Stage 1
+ * times the schedules (1,1) (2,1) (1,2) (2,2) (3,2) (2,3) (3,3), and for mixed
+ * precision 1 to 4 inner cycles each, at 256 threads; stage 2 times 64, 128
+ * and 512 threads for the winner.  Each candidate builds its own plan, runs
+ * one untimed solve and `repeats` (1..16) timed ones; the score is the median
+ * wall time of the solve call.  Results in *out; phi_dev is overwritten.
+ * This is a project addition for choosing kernel schedules; the paper does
+ * not specify its multigrid schedule.
+ */
+int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const double *const *rho_dev,
+                         double *const *phi_dev, double tol, void *stream, int repeats,
+                         pic_poisson_tuning *out);
 
 /*
  * As pic_poisson_solve with host buffers (pinned or pageable): copies rho_host

@@ -25,7 +25,7 @@ EXPORTS = (
     "pic_poisson_set_stream", "pic_poisson_solve_batch",
     "pic_poisson_solve", "pic_poisson_solve_host", "pic_poisson_forward", "pic_poisson_inverse",
     "pic_poisson_mode_residual", "pic_poisson_destroy", "pic_poisson_last_error",
-    "pic_poisson_measure_fma_peaks", "pic_poisson_mode_residual_noalloc",
+    "pic_poisson_measure_fma_peaks", "pic_poisson_mode_residual_noalloc", "pic_poisson_autotune",
 )
 
 
@@ -47,7 +47,7 @@ class Desc(ctypes.Structure):
         ("eps0", ctypes.c_double),
         ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
         ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int),
-        ("inner_cycles", ctypes.c_int), ("flags", ctypes.c_uint),
+        ("inner_cycles", ctypes.c_int), ("smooth_threads", ctypes.c_int), ("flags", ctypes.c_uint),
     ]
 
 
@@ -69,6 +69,19 @@ class Info(ctypes.Structure):
             "bytes_phase": {p: self.bytes_phase[i] for i, p in enumerate(PHASES)},
             "flops_phase": {p: self.flops_phase[i] for i, p in enumerate(PHASES)},
         }
+
+
+MAX_TUNE = 64
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [
+        ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int), ("inner_cycles", ctypes.c_int),
+        ("smooth_threads", ctypes.c_int), ("ms", ctypes.c_double), ("tried", ctypes.c_int),
+        ("ms_tried", ctypes.c_double * MAX_TUNE), ("pre_tried", ctypes.c_int * MAX_TUNE),
+        ("post_tried", ctypes.c_int * MAX_TUNE), ("inner_tried", ctypes.c_int * MAX_TUNE),
+        ("threads_tried", ctypes.c_int * MAX_TUNE),
+    ]
 
 
 class Layout(ctypes.Structure):
@@ -117,6 +130,7 @@ def load(build_if_missing: bool = True):
         "pic_poisson_last_error": ([], ctypes.c_char_p),
         "pic_poisson_measure_fma_peaks": ([vp, vp, vp], ip),
         "pic_poisson_mode_residual_noalloc": ([vp, vp, vp, vp, vp, vp], ip),
+        "pic_poisson_autotune": ([vp, ip, vp, vp, dp, vp, ip, vp], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -136,7 +150,8 @@ def _check(status, allow=(OK,)):
     return status
 
 
-def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1, flags=0, inner_cycles=0):
+def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1, flags=0, inner_cycles=0,
+              smooth_threads=0):
     """Descriptor for a workloads.Problem; returns (Desc, keep-alive buffers)."""
     keep = []
     d = Desc()
@@ -157,6 +172,7 @@ def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=
     d.pre_sweeps = pre_sweeps
     d.post_sweeps = post_sweeps
     d.inner_cycles = inner_cycles
+    d.smooth_threads = smooth_threads
     d.flags = flags
     return d, keep
 
@@ -199,13 +215,14 @@ class Plan:
     """A solver plan for one problem (wraps pic_poisson_plan / solve / destroy)."""
 
     def __init__(self, problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
-                 profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False):
+                 profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False,
+                 smooth_threads=0):
         import torch
         self.problem = problem
         flags = ((PROFILE if profile else 0) | (USE_INITIAL_GUESS if initial_guess else 0)
                  | (GRAPH if graph else 0))
         self._desc, self._keep = make_desc(problem, precision, max_cycles, pre_sweeps, post_sweeps, flags,
-                                           inner_cycles)
+                                           inner_cycles, smooth_threads)
         self.stream = torch.cuda.current_stream() if stream is None else stream
         self._plan = ctypes.c_void_p()
         _check(load().pic_poisson_plan(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
@@ -291,7 +308,8 @@ class BatchPlan:
     """One plan for several independent problems (wraps pic_poisson_plan_batch / solve_batch)."""
 
     def __init__(self, problems, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
-                 profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False):
+                 profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False,
+                 smooth_threads=0):
         import torch
         self.problems = list(problems)
         n = len(self.problems)
@@ -302,7 +320,8 @@ class BatchPlan:
         self._descs = (Desc * n)()
         self._keep = []
         for i, p in enumerate(self.problems):
-            d, keep = make_desc(p, precision, max_cycles, pre_sweeps, post_sweeps, flags, inner_cycles)
+            d, keep = make_desc(p, precision, max_cycles, pre_sweeps, post_sweeps, flags, inner_cycles,
+                                smooth_threads)
             self._descs[i] = d
             self._keep.extend(keep)
         self.stream = torch.cuda.current_stream() if stream is None else stream
@@ -340,3 +359,49 @@ class BatchPlan:
         st = load().pic_poisson_solve_batch(self._plan, rp, fp, float(tol), infos)
         _check(st, allow=(OK, ENOTCONVERGED))
         return phis, [i.as_dict() for i in infos]
+
+
+def autotune(problems, rhos, tol=1e-10, precision=FP64, graph=False, repeats=3, cache=None):
+    """Tuned solver settings for `problems` (pic_poisson_autotune), as Plan keyword arguments.
+
+    cache: optional JSON file; results are stored under a key made of the
+    problem sizes, precision, graph flag and tolerance and reused when present.
+    """
+    import json
+    import os
+    import torch
+    problems = list(problems)
+    key = "|".join("%dx%dx%d" % (p.nr, p.ntheta, p.nz) for p in problems) + "|%d|%d|%g" % (precision, graph, tol)
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+        if key in table:
+            return table[key]["best"]
+    n = len(problems)
+    descs = (Desc * n)()
+    keep = []
+    for i, p in enumerate(problems):
+        d, k = make_desc(p, precision, 0, -1, -1, GRAPH if graph else 0)
+        descs[i] = d
+        keep.extend(k)
+    shapes = [(p.nz, p.ntheta, p.nr) for p in problems]
+    phis = [torch.empty(sh, dtype=torch.float64, device=r.device) for sh, r in zip(shapes, rhos)]
+    rp = (ctypes.c_void_p * n)(*[_dev_ptr(r, sh, "rho").value for r, sh in zip(rhos, shapes)])
+    fp = (ctypes.c_void_p * n)(*[_dev_ptr(f, sh, "phi").value for f, sh in zip(phis, shapes)])
+    out = Tuning()
+    st = torch.cuda.current_stream().cuda_stream
+    _check(load().pic_poisson_autotune(descs, n, rp, fp, float(tol), ctypes.c_void_p(st), int(repeats),
+                                       ctypes.byref(out)))
+    best = {"pre_sweeps": out.pre_sweeps, "post_sweeps": out.post_sweeps, "inner_cycles": out.inner_cycles,
+            "smooth_threads": out.smooth_threads}
+    tried = [{"pre": out.pre_tried[i], "post": out.post_tried[i], "inner": out.inner_tried[i],
+              "threads": out.threads_tried[i], "ms": out.ms_tried[i]} for i in range(out.tried)]
+    if cache:
+        table = {}
+        if os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+        table[key] = {"best": best, "ms": out.ms, "tried": tried}
+        with open(cache, "w") as f:
+            json.dump(table, f, indent=1)
+    return dict(best, ms=out.ms, tried=tried)

@@ -152,8 +152,10 @@ struct Ctrl {
 cudaError_t launch_forward(const FFTTab *tab, unsigned grid, size_t smem, double *partials, cudaStream_t st);
 cudaError_t launch_inverse(const FFTTab *tab, unsigned grid, size_t smem, cudaStream_t st);
 
+// threads: block size of the smoother (64, 128, 256 or 512; the table's block
+// ranges must have been computed with the same size).
 template <class T>
-cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, cudaStream_t st);
+cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, int threads, cudaStream_t st);
 // red_only: residual of the red fine cells only (valid right after a black half-sweep).
 // Per problem, f.init selects what is written into the coarse level c: 0 = b only
 // (coarsest, solved directly); 1 = also b_hat and u = 0; 2 = also b_hat and
@@ -190,7 +192,9 @@ cudaError_t measure_fma(cudaStream_t st, double *fp64_gflops, double *fp32_gflop
 // Threads per block of the multigrid kernels and the block count a launch
 // over `entries` work items of one problem needs.
 constexpr int MG_THREADS = 256;
-inline unsigned mg_blocks(size_t entries) { return (unsigned)((entries + MG_THREADS - 1) / MG_THREADS); }
+inline unsigned mg_blocks(size_t entries, int threads = MG_THREADS) {
+    return (unsigned)((entries + threads - 1) / threads);
+}
 constexpr int FFT_TI = 32;        // radial columns per transform CTA
 constexpr int FFT_THREADS = 256;
 size_t fft_smem_bytes(int nt);

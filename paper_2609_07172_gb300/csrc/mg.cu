@@ -103,8 +103,8 @@ __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i,
 // One red-black Gauss-Seidel half-sweep over the cells of one colour:
 //   u_q <- (b_q + sum_q' G_qq' u_q') / (D0_q + lambda_m mu_q)
 // written as u = b_hat + h_z (u_S + u_N) + h_w u_W + h_e u_E with h = G / diag.
-template <class T>
-__global__ void __launch_bounds__(MG_THREADS) k_smooth(const LaunchTab<T> *__restrict__ tab, int color) {
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) k_smooth(const LaunchTab<T> *__restrict__ tab, int color) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     const LevelDev<T> L = tab->f[p];
     const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
@@ -149,13 +149,16 @@ k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ p
         const int m = (int)(e - cc * nm);
         const int K = (int)(cc / (unsigned)C.nr);
         const int I = (int)(cc - (unsigned)K * C.nr);
+        // coarsening factors of this level pair (semi-coarsening keeps one direction)
+        const int fz = F.nz == C.nz ? 1 : 2, fr = F.nr == C.nr ? 1 : 2;
         V2<T> sum = mk<T>(0, 0);
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
 #pragma unroll
             for (int bb = 0; bb < 2; ++bb) {
-                if (RED_ONLY && a != bb) continue;
-                const int k = 2 * K + a, i = 2 * I + bb;
+                if (a >= fz || bb >= fr) continue;
+                const int k = fz * K + a, i = fr * I + bb;
+                if (RED_ONLY && ((k + i) & 1)) continue;
                 const size_t idx = ((size_t)k * F.nr + i) * nm + m;
                 const V2<T> r = residual_at(F, k, i, m, idx);
                 sum.x += r.x;
@@ -212,11 +215,13 @@ k_residual(const LaunchTab<T> *__restrict__ tab, int write_r, double *__restrict
     }
 }
 
-// Bilinear cell-centred prolongation of the coarse correction and update
-// u += P e.  Weights 9/16, 3/16, 3/16, 1/16 from the four nearest coarse
-// centres; beyond a wall the coarse value is reflected with a sign change
-// (the correction vanishes on the Dirichlet face).  BLACK_ONLY: only black
-// fine cells (the red half-sweep that follows overwrites the red ones).
+// Cell-centred prolongation of the coarse correction and update u += P e:
+// bilinear (weights 9/16, 3/16, 3/16, 1/16 from the four nearest coarse
+// centres) after 2:1 coarsening in both directions, linear (3/4, 1/4) along
+// the coarsened direction after semi-coarsening.  Beyond a wall the coarse
+// value is reflected with a sign change (the correction vanishes on the
+// Dirichlet face).  BLACK_ONLY: only black fine cells (the red half-sweep that
+// follows overwrites the red ones).
 template <class T, bool BLACK_ONLY>
 __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__restrict__ tab) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
@@ -236,7 +241,8 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
         i = (int)(c - (unsigned)k * F.nr);
     }
     const size_t idx = ((size_t)k * F.nr + i) * nm + m;
-    const int K = k >> 1, I = i >> 1;
+    const bool cz2 = F.nz != C.nz, cr2 = F.nr != C.nr;
+    const int K = cz2 ? (k >> 1) : k, I = cr2 ? (i >> 1) : i;
     const int K2 = K + ((k & 1) ? 1 : -1);
     const int I2 = I + ((i & 1) ? 1 : -1);
     const bool kin = K2 >= 0 && K2 < C.nz;
@@ -244,13 +250,21 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
     const int Kx = kin ? K2 : K, Ix = iin ? I2 : I;
     const T sk = kin ? T(1) : T(-1), si = iin ? T(1) : T(-1);
     const V2<T> c0 = C.u[((size_t)K * C.nr + I) * nm + m];
-    const V2<T> c1 = C.u[((size_t)K * C.nr + Ix) * nm + m];
-    const V2<T> c2 = C.u[((size_t)Kx * C.nr + I) * nm + m];
-    const V2<T> c3 = C.u[((size_t)Kx * C.nr + Ix) * nm + m];
-    const T w1 = T(0.1875) * si, w2 = T(0.1875) * sk, w3 = T(0.0625) * si * sk;
     V2<T> u = F.u[idx];
-    u.x += fma(w3, c3.x, fma(w2, c2.x, fma(w1, c1.x, T(0.5625) * c0.x)));
-    u.y += fma(w3, c3.y, fma(w2, c2.y, fma(w1, c1.y, T(0.5625) * c0.y)));
+    if (cz2 && cr2) {
+        const V2<T> c1 = C.u[((size_t)K * C.nr + Ix) * nm + m];
+        const V2<T> c2 = C.u[((size_t)Kx * C.nr + I) * nm + m];
+        const V2<T> c3 = C.u[((size_t)Kx * C.nr + Ix) * nm + m];
+        const T w1 = T(0.1875) * si, w2 = T(0.1875) * sk, w3 = T(0.0625) * si * sk;
+        u.x += fma(w3, c3.x, fma(w2, c2.x, fma(w1, c1.x, T(0.5625) * c0.x)));
+        u.y += fma(w3, c3.y, fma(w2, c2.y, fma(w1, c1.y, T(0.5625) * c0.y)));
+    } else {
+        // linear along the coarsened direction
+        const V2<T> c1 = cz2 ? C.u[((size_t)Kx * C.nr + I) * nm + m] : C.u[((size_t)K * C.nr + Ix) * nm + m];
+        const T w1 = T(0.25) * (cz2 ? sk : si);
+        u.x += fma(w1, c1.x, T(0.75) * c0.x);
+        u.y += fma(w1, c1.y, T(0.75) * c0.y);
+    }
     F.u[idx] = u;
 }
 
@@ -383,19 +397,43 @@ __device__ double pow2_scale(double sumsq, double count) {
     return ldexp(1.0, -ex);
 }
 
-// ||b||^2 per problem from the forward transform's block partials (one warp
-// per problem, fixed summation order), and the first correction scale.
-__global__ void __launch_bounds__(256) k_bnorm(Ctrl *__restrict__ ctrl, const FFTTab *__restrict__ fft,
-                                               const double *__restrict__ partials) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int p = warp; p < fft->n; p += nw) {
+// Deterministic sums of per-problem ranges of block partials by one CTA:
+// with n problems and W warps, problem p is summed by the warps w = p, p + n,
+// ... (each lane a fixed strided subset, then a fixed shuffle tree), and the
+// group's warp sums are added in warp order.  Result in out[p].
+__device__ void range_sums(const double *__restrict__ partials, const unsigned *__restrict__ begin,
+                           const unsigned *__restrict__ end, int n, double *out, double *wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+    for (int base = 0; base < n; base += W) {
+        const int cnt = min(n - base, W);
+        const int p = base + warp % cnt, g = W / cnt, rank = warp / cnt;
         double s = 0.0;
-        for (unsigned b = fft->start[p] + lane; b < fft->start[p + 1]; b += 32) s += partials[b];
-        s = warp_sum(s);
-        if (lane == 0) {
-            ctrl->bnorm2[p] = s;
-            ctrl->sigma_next[p] = pow2_scale(s, ctrl->count[p]);
+        if (rank < g) {
+            const unsigned b0 = begin[p], b1 = end[p];
+            for (unsigned b = b0 + rank * 32 + lane; b < b1; b += 32u * g) s += partials[b];
         }
+        s = warp_sum(s);
+        if (lane == 0) wsum[warp] = (rank < g) ? s : 0.0;
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            double t = 0.0;
+            for (int r = 0; r < g; ++r) t += wsum[r * cnt + threadIdx.x];
+            out[base + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// ||b||^2 per problem from the forward transform's block partials, and the
+// first correction scale.
+__global__ void __launch_bounds__(1024) k_bnorm(Ctrl *__restrict__ ctrl, const FFTTab *__restrict__ fft,
+                                                const double *__restrict__ partials) {
+    __shared__ double wsum[32];
+    __shared__ double sums[kMaxBatch];
+    range_sums(partials, fft->start, fft->start + 1, fft->n, sums, wsum);
+    for (int p = threadIdx.x; p < fft->n; p += blockDim.x) {
+        ctrl->bnorm2[p] = sums[p];
+        ctrl->sigma_next[p] = pow2_scale(sums[p], ctrl->count[p]);
     }
 }
 
@@ -408,64 +446,58 @@ __global__ void __launch_bounds__(256) k_bnorm(Ctrl *__restrict__ ctrl, const FF
 // (their rel keeps describing the returned iterate) until all have stopped.
 // counting: add ctrl->inc to the cycle count first (evaluations after a pass
 // of the loop body).  When use_handle, sets the graph's while-condition.
-__global__ void __launch_bounds__(256) k_check(Ctrl *__restrict__ ctrl, const double *__restrict__ partials,
-                                               int counting, cudaGraphConditionalHandle handle, int use_handle) {
-    __shared__ int s_cycles, s_any;
-    if (threadIdx.x == 0) {
-        s_cycles = ctrl->cycles + (counting ? ctrl->inc : 0);
-        s_any = 0;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__global__ void __launch_bounds__(1024) k_check(Ctrl *__restrict__ ctrl, const double *__restrict__ partials,
+                                                int counting, cudaGraphConditionalHandle handle, int use_handle) {
+    __shared__ double wsum[32];
+    __shared__ double sums[kMaxBatch];
+    __shared__ int s_any;
+    const int cycles = ctrl->cycles + (counting ? ctrl->inc : 0);
+    if (threadIdx.x == 0) s_any = 0;
+    range_sums(partials, ctrl->rbegin, ctrl->rend, ctrl->n, sums, wsum);
     const double tol = ctrl->tol;
-    for (int p = warp; p < ctrl->n; p += nw) {
-        double s = 0.0;
-        for (unsigned b = ctrl->rbegin[p] + lane; b < ctrl->rend[p]; b += 32) s += partials[b];
-        s = warp_sum(s);
-        if (lane == 0) {
-            double rr2 = s;
-            if (ctrl->scaled) {
-                const double su = ctrl->sigma_next[p];
-                ctrl->sigma_used[p] = su;
-                ctrl->inv_sigma_used[p] = 1.0 / su;
-                rr2 = rr2 / (su * su);
-                ctrl->sigma_next[p] = pow2_scale(rr2, ctrl->count[p]);
+    for (int p = threadIdx.x; p < ctrl->n; p += blockDim.x) {
+        double rr2 = sums[p];
+        if (ctrl->scaled) {
+            const double su = ctrl->sigma_next[p];
+            ctrl->sigma_used[p] = su;
+            ctrl->inv_sigma_used[p] = 1.0 / su;
+            rr2 = rr2 / (su * su);
+            ctrl->sigma_next[p] = pow2_scale(rr2, ctrl->count[p]);
+        }
+        const double bb = ctrl->bnorm2[p];
+        const double rel = bb > 0.0 ? sqrt(rr2 / bb) : sqrt(rr2);
+        ctrl->rel[p] = rel;
+        if (!counting) ctrl->rel_first[p] = rel;
+        if (!ctrl->done[p]) {
+            int stop = 0, status = PIC_POISSON_OK;
+            if (isnan(rel) || isinf(rel)) {
+                stop = 1;
+                status = PIC_POISSON_ENONFINITE;
+            } else if (tol > 0.0) {
+                stop = rel <= tol;
+            } else if (rel < 0.5 * ctrl->best[p]) {
+                ctrl->best[p] = rel;
+                ctrl->stall[p] = 0;
+            } else {
+                ctrl->best[p] = fmin(ctrl->best[p], rel);
+                stop = ++ctrl->stall[p] >= 2;
             }
-            const double bb = ctrl->bnorm2[p];
-            const double rel = bb > 0.0 ? sqrt(rr2 / bb) : sqrt(rr2);
-            ctrl->rel[p] = rel;
-            if (!counting) ctrl->rel_first[p] = rel;
-            if (!ctrl->done[p]) {
-                int stop = 0, status = PIC_POISSON_OK;
-                if (isnan(rel) || isinf(rel)) {
-                    stop = 1;
-                    status = PIC_POISSON_ENONFINITE;
-                } else if (tol > 0.0) {
-                    stop = rel <= tol;
-                } else if (rel < 0.5 * ctrl->best[p]) {
-                    ctrl->best[p] = rel;
-                    ctrl->stall[p] = 0;
-                } else {
-                    ctrl->best[p] = fmin(ctrl->best[p], rel);
-                    stop = ++ctrl->stall[p] >= 2;
-                }
-                if (!stop && s_cycles >= ctrl->max_cycles) {
-                    stop = 1;
-                    status = PIC_POISSON_ENOTCONVERGED;
-                }
-                if (stop) {
-                    ctrl->done[p] = 1;
-                    ctrl->status[p] = status;
-                    ctrl->done_cycles[p] = s_cycles;
-                } else {
-                    atomicOr(&s_any, 1);
-                }
+            if (!stop && cycles >= ctrl->max_cycles) {
+                stop = 1;
+                status = PIC_POISSON_ENOTCONVERGED;
+            }
+            if (stop) {
+                ctrl->done[p] = 1;
+                ctrl->status[p] = status;
+                ctrl->done_cycles[p] = cycles;
+            } else {
+                atomicOr(&s_any, 1);
             }
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        ctrl->cycles = s_cycles;
+        ctrl->cycles = cycles;
         ctrl->cont = s_any;
         if (use_handle) cudaGraphSetConditional(handle, s_any ? 1u : 0u);
     }
@@ -483,8 +515,13 @@ __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ p, int 
 }  // namespace
 
 template <class T>
-cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, cudaStream_t st) {
-    k_smooth<T><<<grid, MG_THREADS, 0, st>>>(tab, color);
+cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, int threads, cudaStream_t st) {
+    switch (threads) {
+    case 64: k_smooth<T, 64><<<grid, 64, 0, st>>>(tab, color); break;
+    case 128: k_smooth<T, 128><<<grid, 128, 0, st>>>(tab, color); break;
+    case 512: k_smooth<T, 512><<<grid, 512, 0, st>>>(tab, color); break;
+    default: k_smooth<T, 256><<<grid, 256, 0, st>>>(tab, color); break;
+    }
     return cudaGetLastError();
 }
 
@@ -529,13 +566,13 @@ cudaError_t launch_update(const DefectTab *tab, unsigned grid, const Ctrl *ctrl,
 }
 
 cudaError_t launch_bnorm(Ctrl *ctrl, const FFTTab *fft, const double *partials, cudaStream_t st) {
-    k_bnorm<<<1, 256, 0, st>>>(ctrl, fft, partials);
+    k_bnorm<<<1, 1024, 0, st>>>(ctrl, fft, partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_check(Ctrl *ctrl, const double *partials, int counting, cudaGraphConditionalHandle handle,
                          int use_handle, cudaStream_t st) {
-    k_check<<<1, 256, 0, st>>>(ctrl, partials, counting, handle, use_handle);
+    k_check<<<1, 1024, 0, st>>>(ctrl, partials, counting, handle, use_handle);
     return cudaGetLastError();
 }
 
@@ -545,7 +582,7 @@ cudaError_t launch_sum(const double *partials, int n, double *out, cudaStream_t 
 }
 
 #define PP_INST(T)                                                                                         \
-    template cudaError_t launch_smooth<T>(const LaunchTab<T> *, unsigned, int, cudaStream_t);              \
+    template cudaError_t launch_smooth<T>(const LaunchTab<T> *, unsigned, int, int, cudaStream_t);         \
     template cudaError_t launch_residual_restrict<T>(const LaunchTab<T> *, unsigned, bool, double *,       \
                                                      cudaStream_t);                                        \
     template cudaError_t launch_residual<T>(const LaunchTab<T> *, unsigned, bool, double *, unsigned,      \

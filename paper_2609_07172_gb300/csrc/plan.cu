@@ -44,6 +44,11 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
     if (d->pre_sweeps < 0) d->pre_sweeps = 2;
     if (d->post_sweeps < 0) d->post_sweeps = 2;
     if (d->inner_cycles <= 0) d->inner_cycles = 2;
+    if (d->smooth_threads <= 0) d->smooth_threads = MG_THREADS;
+    if (d->smooth_threads != 64 && d->smooth_threads != 128 && d->smooth_threads != 256 && d->smooth_threads != 512) {
+        set_error("smooth_threads must be 64, 128, 256 or 512 (got %d)", d->smooth_threads);
+        return PIC_POISSON_EINVAL;
+    }
     if (d->nr < 1 || d->nz < 1) {
         set_error("nr and nz must be >= 1 (got %d, %d)", d->nr, d->nz);
         return PIC_POISSON_EINVAL;
@@ -77,14 +82,35 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
     return PIC_POISSON_OK;
 }
 
-// 2:1 coarsening while both counts are even and at least 8.
+// Coarsening that keeps coarse cells near-isotropic (the point smoother only
+// smooths well when neither direction's coupling dominates: G_z / G_r =
+// (dr / dz)^2).  From a level with cell aspect dr / dz: above sqrt(2) halve
+// only N_z, below 1/sqrt(2) halve only N_r, otherwise halve both; a halved
+// count must be even and at least 8, and the level being coarsened needs an
+// even N_r (it is smoothed red-black).  Stop when the preferred step is not
+// possible; the coarsest level is solved directly.
 int hierarchy(const pic_poisson_desc &d, int *nr, int *nz, int *levels) {
     int L = 1, r = d.nr, z = d.nz;
     nr[0] = r;
     nz[0] = z;
-    while (L < PIC_POISSON_MAX_LEVELS && r % 2 == 0 && z % 2 == 0 && r >= 8 && z >= 8) {
-        r /= 2;
-        z /= 2;
+    const double Lr = d.r_out - d.r_in, Lz = d.z1 - d.z0, s2 = std::sqrt(2.0);
+    while (L < PIC_POISSON_MAX_LEVELS && r % 2 == 0) {
+        const double aspect = (Lr / r) / (Lz / z);
+        const bool can_r = r >= 8, can_z = z % 2 == 0 && z >= 8;
+        int r2 = r, z2 = z;
+        if (aspect > s2) {
+            if (!can_z) break;
+            z2 = z / 2;
+        } else if (aspect < 1.0 / s2) {
+            if (!can_r) break;
+            r2 = r / 2;
+        } else {
+            if (!(can_r && can_z)) break;
+            r2 = r / 2;
+            z2 = z / 2;
+        }
+        r = r2;
+        z = z2;
         nr[L] = r;
         nz[L] = z;
         ++L;
@@ -357,7 +383,7 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
             const size_t half = (size_t)f.nz * (f.nr / 2) * f.nm, full = (size_t)f.nz * f.nr * f.nm;
             const size_t coarse_n = (size_t)v[l + 1].nz * v[l + 1].nr * f.nm;
             ts.f[ts.n] = f;
-            ts.start[ts.n + 1] = ts.start[ts.n] + mg_blocks(half);
+            ts.start[ts.n + 1] = ts.start[ts.n] + mg_blocks(half, P.shared.smooth_threads);
             ++ts.n;
             tr.f[tr.n] = f;
             tr.c[tr.n] = v[l + 1];
@@ -567,7 +593,8 @@ int upload(pic_poisson_plan_s &P) {
 
 int same_settings(const pic_poisson_desc &a, const pic_poisson_desc &b) {
     return a.precision == b.precision && a.max_cycles == b.max_cycles && a.pre_sweeps == b.pre_sweeps &&
-           a.post_sweeps == b.post_sweeps && a.inner_cycles == b.inner_cycles && a.flags == b.flags;
+           a.post_sweeps == b.post_sweeps && a.inner_cycles == b.inner_cycles && a.flags == b.flags &&
+           a.smooth_threads == b.smooth_threads;
 }
 
 int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
@@ -583,7 +610,8 @@ int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
         if (rc) return rc;
         if (p == 0) P.shared = d;
         else if (!same_settings(P.shared, d)) {
-            set_error("problem %d: precision, max_cycles, sweeps, inner_cycles and flags must match problem 0", p);
+            set_error("problem %d: precision, max_cycles, sweeps, inner_cycles, smooth_threads and flags must match "
+                      "problem 0", p);
             return PIC_POISSON_EINVAL;
         }
         rc = setup_problem(P.pr[p], d);

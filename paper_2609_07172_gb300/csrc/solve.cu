@@ -122,7 +122,7 @@ int smooth_level(Runner &R, const Hier<T> &H, int l, int sweeps, bool skip_first
     const double n = level_entries<T>(R.P, l);
     for (int s = 0; s < sweeps; ++s) {
         for (int color = (s == 0 && skip_first_red) ? 1 : 0; color < 2; ++color) {
-            RUN(R, ph, launch_smooth(H.smooth[l], H.g_smooth[l], color, R.st));
+            RUN(R, ph, launch_smooth(H.smooth[l], H.g_smooth[l], color, R.P.shared.smooth_threads, R.st));
             R.account(ph, 1.5 * n * sizeof(V2<T>), 14.0 * 0.5 * n);
         }
     }

@@ -164,3 +164,38 @@ def drifting_rho(p: Problem, t: int, base_seed: int = 3) -> np.ndarray:
     """Step ``t`` of a drifting-wave sequence: the m = 8 wave advanced by t cells."""
     da = p.theta_span / p.ntheta
     return rho_plasma(p, [base_seed, t], wave_phase=t * da)
+
+
+def rho_plasma_torch(p: Problem, seed: int, wave_phase: float = 0.0, device="cuda", mean_count: float = 27.0,
+                     weight: float = 1e8, wave_m: int = 8, wave_amp: float = 0.05, profile_centre: float = 0.5,
+                     profile_width: float = 0.15):
+    """The rho_plasma recipe drawn on the GPU with a seeded torch generator.
+
+    Same distribution as :func:`rho_plasma` (not the same samples: torch's
+    generator replaces numpy's).  Used for long sequences of full-size inputs
+    whose host-side generation would dominate a benchmark.
+    """
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    L = p.z1 - p.z0
+    z = torch.as_tensor(p.z_centres() - p.z0, device=device)
+    G = torch.exp(-((z - profile_centre * L) ** 2) / (2.0 * (profile_width * L) ** 2))
+    gz = G / G.mean()
+    th = torch.as_tensor(p.theta_centres(), device=device)
+    lam_e = (mean_count * gz)[:, None, None].expand(p.nz, p.ntheta, p.nr).contiguous()
+    wave = 1.0 + wave_amp * torch.cos(wave_m * (th - wave_phase))
+    lam_i = lam_e * wave[None, :, None]
+    n_i = torch.poisson(lam_i, generator=g)
+    n_e = torch.poisson(lam_e, generator=g)
+    dr = (p.r_out - p.r_in) / p.nr
+    dz = L / p.nz
+    da = p.theta_span / p.ntheta
+    vol = torch.as_tensor(p.r_centres() * dr * da * dz, device=device)
+    return (E_CHARGE * weight) * (n_i - n_e) / vol[None, None, :]
+
+
+def drifting_rho_torch(p: Problem, t: int, base_seed: int = 3, device="cuda"):
+    """GPU-drawn step ``t`` of the drifting-wave sequence (see :func:`drifting_rho`)."""
+    da = p.theta_span / p.ntheta
+    return rho_plasma_torch(p, base_seed * 1_000_003 + t, wave_phase=t * da, device=device)

@@ -25,7 +25,7 @@ def dev(x):
 
 def uneven_problems():
     dims = [(32, 16, 32), (40, 8, 24), (64, 32, 48), (15, 4, 9), (48, 2, 16), (96, 16, 40), (128, 64, 64),
-            (64, 128, 32)]
+            (64, 128, 32), (32, 8, 200), (128, 4, 16)]
     return [with_bias_walls(W.annulus(*d)) for d in dims] + [narrow_span(), small_rin()]
 
 
@@ -114,3 +114,37 @@ def test_previous_step_guess_sequence():
             assert iw["status"] == B.OK and iw["cycles"] <= iz["cycles"]
             assert oracle.relres(g, rho_np, pw.cpu().numpy()) <= 1.0001e-10
             phi_prev = pw.clone()
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_autotune_picks_a_working_schedule(precision, tmp_path):
+    from paper_2609_07172_gb300 import autotune
+    p = W.annulus(64, 16, 64)
+    rho = dev(W.rho_plasma(p, seed=50))
+    cache = str(tmp_path / "tune.json")
+    best = autotune([p], [rho], tol=1e-10, precision=precision, graph=True, repeats=1, cache=cache)
+    n_sched = 7 * (4 if precision == MIXED else 1)
+    assert len(best["tried"]) == n_sched + 3
+    assert best["smooth_threads"] in (64, 128, 256, 512)
+    assert best["ms"] == min(t["ms"] for t in best["tried"])
+    again = autotune([p], [rho], tol=1e-10, precision=precision, graph=True, cache=cache)   # cached
+    assert {k: again[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads")} == \
+           {k: best[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads")}
+    kw = {k: best[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads")}
+    with Plan(p, precision=precision, graph=True, **kw) as plan:
+        phi, info = plan.solve(rho, tol=1e-10)
+    assert info["status"] == B.OK and info["rel_res"] <= 1e-10
+
+
+def test_gpu_generator_matches_recipe_statistics():
+    """The GPU-drawn charge density follows the same recipe as the host one."""
+    p = W.annulus(128, 32, 100)
+    a = W.rho_plasma(p, seed=1)
+    b = W.rho_plasma_torch(p, seed=1).cpu().numpy()
+    assert b.shape == a.shape
+    # per-plane means and the m = 8 azimuthal wave amplitude agree statistically
+    pa, pb = a.mean(axis=(1, 2)), b.mean(axis=(1, 2))
+    assert np.abs(pa - pb).max() < 6 * a.std() / np.sqrt(p.ntheta * p.nr)
+    wa = np.abs(np.fft.rfft(a.mean(axis=(0, 2)))[8])
+    wb = np.abs(np.fft.rfft(b.mean(axis=(0, 2)))[8])
+    assert wb == pytest.approx(wa, rel=0.2)

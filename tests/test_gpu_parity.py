@@ -30,6 +30,9 @@ def problems():
         out.append(pytest.param(with_bias_walls(W.annulus(nr, nt, nz)), id=f"annulus{nr}x{nt}x{nz}"))
     out.append(pytest.param(narrow_span(), id="narrow_span"))
     out.append(pytest.param(small_rin(), id="small_rin"))
+    # strongly anisotropic cells: z-only and r-only semi-coarsening
+    out.append(pytest.param(W.annulus(64, 8, 400), id="aniso_z"))
+    out.append(pytest.param(W.annulus(256, 8, 32), id="aniso_r"))
     return out
 
 
@@ -192,3 +195,14 @@ def test_profile_counts_launches():
     assert lp["forward"] == 1 and lp["inverse"] == 1
     assert lp["smooth"] > 0 and ms["smooth"] > 0
     assert info["launches"] == sum(lp.values())
+
+
+@pytest.mark.parametrize("dims", [(64, 16, 400), (512, 16, 64), (512, 128, 400)])
+def test_convergence_rate_independent_of_cell_aspect(dims):
+    """Semi-coarsening keeps coarse cells near-isotropic, so strongly
+    anisotropic grids converge in about as many cycles as the paper's grid."""
+    p = W.annulus(*dims)
+    rho = W.rho_plasma(p, seed=3)
+    with Plan(p) as plan:
+        _, info = plan.solve(dev(rho), tol=1e-10)
+    assert info["status"] == B.OK and info["cycles"] <= 12, info["cycles"]
