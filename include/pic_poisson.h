@@ -218,6 +218,25 @@ int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const double *con
                          pic_poisson_tuning *out);
 
 /*
+ * As pic_poisson_solve, starting from the mode-layout iterate uhat_guess_dev
+ * (e.g. a previous solution from pic_poisson_get_modes, or a learned guess)
+ * instead of zero or the transform of phi.  Single-problem plans.
+ */
+int pic_poisson_solve_modes(pic_poisson_plan_t plan, const double *rho_dev, const double *uhat_guess_dev,
+                            double *phi_dev, double tol, pic_poisson_info *info);
+
+/*
+ * uhat_dev (mode layout) = (1/N_theta) DFT of phi_dev along theta
+ * (Eq. azimuthal_dft, without the s_q factor or Dirichlet term of
+ * pic_poisson_forward): the mode coefficients of a potential.
+ */
+int pic_poisson_analyze(pic_poisson_plan_t plan, const double *phi_dev, double *uhat_dev);
+
+/* uhat_dev (mode layout) = the mode-space iterate of the last solve (its
+ * converged phi_hat), copied on the plan's stream. */
+int pic_poisson_get_modes(pic_poisson_plan_t plan, double *uhat_dev);
+
+/*
  * As pic_poisson_solve with host buffers (pinned or pageable): copies rho_host
  * to the device, solves, copies phi back; returns after phi_host is written.
  * The device staging buffers are part of the plan's workspace (allocated on

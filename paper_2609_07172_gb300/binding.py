@@ -26,6 +26,7 @@ EXPORTS = (
     "pic_poisson_solve", "pic_poisson_solve_host", "pic_poisson_forward", "pic_poisson_inverse",
     "pic_poisson_mode_residual", "pic_poisson_destroy", "pic_poisson_last_error",
     "pic_poisson_measure_fma_peaks", "pic_poisson_mode_residual_noalloc", "pic_poisson_autotune",
+    "pic_poisson_solve_modes", "pic_poisson_analyze", "pic_poisson_get_modes",
 )
 
 
@@ -131,6 +132,9 @@ def load(build_if_missing: bool = True):
         "pic_poisson_measure_fma_peaks": ([vp, vp, vp], ip),
         "pic_poisson_mode_residual_noalloc": ([vp, vp, vp, vp, vp, vp], ip),
         "pic_poisson_autotune": ([vp, ip, vp, vp, dp, vp, ip, vp], ip),
+        "pic_poisson_solve_modes": ([vp, vp, vp, vp, dp, vp], ip),
+        "pic_poisson_analyze": ([vp, vp, vp], ip),
+        "pic_poisson_get_modes": ([vp, vp], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -277,6 +281,35 @@ class Plan:
                                            ctypes.c_void_p(phi_host.data_ptr()), float(tol), ctypes.byref(info))
         _check(st, allow=(OK, ENOTCONVERGED))
         return info.as_dict()
+
+    def solve_modes(self, rho, uhat_guess, phi=None, tol=1e-10):
+        """Solve starting from a mode-layout initial iterate; returns (phi, info)."""
+        import torch
+        if phi is None:
+            phi = torch.empty(self.shape, dtype=torch.float64, device=rho.device)
+        info = Info()
+        st = load().pic_poisson_solve_modes(self._plan, _dev_ptr(rho, self.shape, "rho"),
+                                            _dev_ptr(uhat_guess, self.mode_shape, "uhat_guess"),
+                                            _dev_ptr(phi, self.shape, "phi"), float(tol), ctypes.byref(info))
+        _check(st, allow=(OK, ENOTCONVERGED))
+        return phi, info.as_dict()
+
+    def analyze(self, phi, uhat=None):
+        """Mode coefficients (1/N DFT) of a potential."""
+        import torch
+        if uhat is None:
+            uhat = torch.empty(self.mode_shape, dtype=torch.float64, device=phi.device)
+        _check(load().pic_poisson_analyze(self._plan, _dev_ptr(phi, self.shape, "phi"),
+                                          _dev_ptr(uhat, self.mode_shape, "uhat")))
+        return uhat
+
+    def get_modes(self, uhat=None):
+        """The mode-space iterate of the last solve."""
+        import torch
+        if uhat is None:
+            uhat = torch.empty(self.mode_shape, dtype=torch.float64, device="cuda")
+        _check(load().pic_poisson_get_modes(self._plan, _dev_ptr(uhat, self.mode_shape, "uhat")))
+        return uhat
 
     def forward(self, rho, bhat=None):
         import torch

@@ -217,7 +217,27 @@ __global__ void __launch_bounds__(FFT_THREADS) k_inverse(const FFTTab *__restric
     }
 }
 
+// Mode-layout initial iterate: b = guess, each CTA copying the cells of its
+// plane k and radial tile (the same block ranges as the transforms).
+__global__ void __launch_bounds__(FFT_THREADS) k_copy_guess(const FFTTab *__restrict__ tab) {
+    const int pr = find_problem(tab->start, tab->n, blockIdx.x);
+    const FFTProb P = tab->p[pr];
+    const int nm = P.nt / 2 + 1;
+    const int tiles = (P.nr + TI - 1) / TI;
+    const int lb = (int)(blockIdx.x - tab->start[pr]);
+    const int k = lb / tiles;
+    const int i0 = (lb - k * tiles) * TI;
+    const int ncols = min(TI, P.nr - i0);
+    const size_t off = ((size_t)k * P.nr + i0) * nm;
+    for (int f = threadIdx.x; f < ncols * nm; f += blockDim.x) P.b[off + f] = P.guess[off + f];
+}
+
 }  // namespace
+
+cudaError_t launch_copy_guess(const FFTTab *tab, unsigned grid, cudaStream_t st) {
+    k_copy_guess<<<grid, FFT_THREADS, 0, st>>>(tab);
+    return cudaGetLastError();
+}
 
 size_t fft_smem_bytes(int nt) {
     const int M = nt / 2, nm = M + 1;

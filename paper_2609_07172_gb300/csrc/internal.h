@@ -112,6 +112,7 @@ struct FFTProb {
     const double2 *uhat;          // mode-layout input of the inverse transform
     const double *rho;            // (nz, nt, nr) input of the forward transform
     double *phi;                  // (nz, nt, nr) output of the inverse transform
+    const double2 *guess;         // mode-layout initial iterate copied into b (mode-space guesses)
 };
 
 struct FFTTab {
@@ -151,6 +152,8 @@ struct Ctrl {
 // table's total block count (start[n]); tables live in device memory.
 cudaError_t launch_forward(const FFTTab *tab, unsigned grid, size_t smem, double *partials, cudaStream_t st);
 cudaError_t launch_inverse(const FFTTab *tab, unsigned grid, size_t smem, cudaStream_t st);
+// b = guess for every problem of the table (mode-layout initial iterates).
+cudaError_t launch_copy_guess(const FFTTab *tab, unsigned grid, cudaStream_t st);
 
 // threads: block size of the smoother (64, 128, 256 or 512; the table's block
 // ranges must have been computed with the same size).

@@ -764,8 +764,10 @@ int pic_poisson_destroy(pic_poisson_plan_t plan) {
     cudaSetDevice(plan->device);
     if (plan->stream) cudaStreamSynchronize(plan->stream);
     else cudaDeviceSynchronize();
-    if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
-    if (plan->graph) cudaGraphDestroy(plan->graph);
+    for (int v = 0; v < 2; ++v) {
+        if (plan->gexec[v]) cudaGraphExecDestroy(plan->gexec[v]);
+        if (plan->graph[v]) cudaGraphDestroy(plan->graph[v]);
+    }
     if (plan->cap0) cudaStreamDestroy(plan->cap0);
     if (plan->cap1) cudaStreamDestroy(plan->cap1);
     for (cudaEvent_t e : plan->evs) cudaEventDestroy(e);

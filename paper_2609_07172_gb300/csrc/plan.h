@@ -71,11 +71,13 @@ struct pic_poisson_plan_s {
     size_t npartials = 0, npartials_fwd = 0;
     double *dsum = nullptr, *hsum = nullptr;    // small device / pinned scratch for stage calls
 
-    // graph of the whole solve (PIC_POISSON_GRAPH)
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    // graphs of the whole solve (PIC_POISSON_GRAPH); [0]: initial iterate per
+    // the plan's flags, [1]: mode-layout initial iterate
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaGraphConditionalHandle handle{};
-    pp::Tally seg[3];                           // prologue, loop body, epilogue (recorded at capture)
+    pp::Tally seg[2][3];                        // prologue, loop body, epilogue (recorded at capture)
+    const double *last_guess[pp::kMaxBatch] = {};
 
     std::vector<cudaEvent_t> evs;               // PROFILE events
     double *stage_rho = nullptr, *stage_phi = nullptr;   // pic_poisson_solve_host staging

@@ -199,18 +199,21 @@ int mixed_defect_and_check(Runner &R, int counting) {
 
 // Forward transform + right-hand side, ||b||, initial iterate, first
 // evaluation of the residual and the first convergence test.
-int enqueue_prologue(Runner &R) {
+// guess: 0 = zero initial iterate, 1 = transform of phi, 2 = mode-layout iterate.
+int enqueue_prologue(Runner &R, int guess) {
     pic_poisson_plan_s &P = R.P;
     const bool mixed = P.shared.precision == PIC_POISSON_MIXED;
-    const bool guess = P.shared.flags & PIC_POISSON_USE_INITIAL_GUESS;
     double x3 = 0;
     const double ff = fft_flops_all(P, &x3), n0 = level0_entries(P, 0);
     RUN(R, PIC_POISSON_PHASE_FORWARD, launch_forward(P.fwd, P.g_fft, P.smem_fft, P.partials_fwd, R.st));
     R.account(PIC_POISSON_PHASE_FORWARD, x3 + (mixed ? 1.0 : 2.0) * n0 * sizeof(double2), ff);
     RUN(R, PIC_POISSON_PHASE_NORM, launch_bnorm(P.ctrl, P.fwd, P.partials_fwd, R.st));
-    if (guess) {
+    if (guess == 1) {
         RUN(R, PIC_POISSON_PHASE_FORWARD, launch_forward(P.guess, P.g_fft, P.smem_fft, nullptr, R.st));
         R.account(PIC_POISSON_PHASE_FORWARD, x3 + n0 * sizeof(double2), ff);
+    } else if (guess == 2) {
+        RUN(R, PIC_POISSON_PHASE_FORWARD, launch_copy_guess(P.guess, P.g_fft, R.st));
+        R.account(PIC_POISSON_PHASE_FORWARD, 2.0 * n0 * sizeof(double2), 0.0);
     } else {
         for (const ProblemPlan &q : P.pr) {
             const size_t n = (size_t)q.lv[0].nr * q.lv[0].nz * q.nm;
@@ -267,16 +270,21 @@ int enqueue_epilogue(Runner &R) {
 }
 
 // ---------------------------------------------------------------- per-solve inputs
-int set_io(pic_poisson_plan_s &P, const double *const *rho, double *const *phi, double tol) {
+int set_io(pic_poisson_plan_s &P, const double *const *rho, double *const *phi, const double *const *guess,
+           double tol) {
     bool changed = !P.io_valid;
-    for (int p = 0; p < P.n; ++p) changed = changed || P.last_rho[p] != rho[p] || P.last_phi[p] != phi[p];
+    for (int p = 0; p < P.n; ++p)
+        changed = changed || P.last_rho[p] != rho[p] || P.last_phi[p] != phi[p] ||
+                  P.last_guess[p] != (guess ? guess[p] : nullptr);
     if (changed) {
         for (int p = 0; p < P.n; ++p) {
             P.h_fwd.p[p].rho = rho[p];
             P.h_guess.p[p].rho = phi[p];
+            P.h_guess.p[p].guess = (const double2 *)(guess ? guess[p] : nullptr);
             P.h_inv.p[p].phi = phi[p];
             P.last_rho[p] = rho[p];
             P.last_phi[p] = phi[p];
+            P.last_guess[p] = guess ? guess[p] : nullptr;
         }
         PP_CUDA(cudaMemcpyAsync(P.fwd, &P.h_fwd, sizeof(FFTTab), cudaMemcpyHostToDevice, P.stream));
         PP_CUDA(cudaMemcpyAsync(P.guess, &P.h_guess, sizeof(FFTTab), cudaMemcpyHostToDevice, P.stream));
@@ -311,10 +319,10 @@ int read_cont(pic_poisson_plan_s &P, int *cont) {
 }
 
 // ---------------------------------------------------------------- drivers
-int run_host_loop(pic_poisson_plan_s &P, Tally &tally, double *ms) {
+int run_host_loop(pic_poisson_plan_s &P, int guess, Tally &tally, double *ms) {
     const bool prof = P.shared.flags & PIC_POISSON_PROFILE;
     Runner R(P, P.stream, prof, false, tally);
-    int rc = enqueue_prologue(R);
+    int rc = enqueue_prologue(R, guess);
     if (rc) return rc;
     int cont = 0;
     rc = read_cont(P, &cont);
@@ -330,10 +338,11 @@ int run_host_loop(pic_poisson_plan_s &P, Tally &tally, double *ms) {
     return R.event_times(ms);
 }
 
-int capture_graph(pic_poisson_plan_s &P) {
+int capture_graph(pic_poisson_plan_s &P, int guess) {
+    const int v = guess == 2 ? 1 : 0;
     if (!P.cap0) PP_CUDA(cudaStreamCreateWithFlags(&P.cap0, cudaStreamNonBlocking));
     if (!P.cap1) PP_CUDA(cudaStreamCreateWithFlags(&P.cap1, cudaStreamNonBlocking));
-    for (Tally &t : P.seg) t = Tally{};
+    for (Tally &t : P.seg[v]) t = Tally{};
     const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
     cudaGraph_t graph = nullptr;
     bool body_open = false;
@@ -355,8 +364,8 @@ int capture_graph(pic_poisson_plan_s &P) {
         set_error("graph conditional handle creation failed");
         return fail(PIC_POISSON_ECUDA);
     }
-    Runner R0(P, P.cap0, false, true, P.seg[0]);
-    int rc = enqueue_prologue(R0);
+    Runner R0(P, P.cap0, false, true, P.seg[v][0]);
+    int rc = enqueue_prologue(R0, guess);
     if (rc) return fail(rc);
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
@@ -382,7 +391,7 @@ int capture_graph(pic_poisson_plan_s &P) {
         return fail(PIC_POISSON_ECUDA);
     }
     body_open = true;
-    Runner R1(P, P.cap1, false, true, P.seg[1]);
+    Runner R1(P, P.cap1, false, true, P.seg[v][1]);
     rc = enqueue_body(R1);
     if (rc) return fail(rc);
     body_open = false;
@@ -390,7 +399,7 @@ int capture_graph(pic_poisson_plan_s &P) {
         set_error("capturing the loop body failed");
         return fail(PIC_POISSON_ECUDA);
     }
-    Runner R2(P, P.cap0, false, false, P.seg[2]);
+    Runner R2(P, P.cap0, false, false, P.seg[v][2]);
     rc = enqueue_epilogue(R2);
     if (rc) return fail(rc);
     cudaError_t err = cudaStreamEndCapture(P.cap0, &graph);
@@ -399,34 +408,36 @@ int capture_graph(pic_poisson_plan_s &P) {
         cudaGetLastError();
         return PIC_POISSON_ECUDA;
     }
-    P.graph = graph;
-    err = cudaGraphInstantiate(&P.gexec, P.graph, 0);
+    P.graph[v] = graph;
+    err = cudaGraphInstantiate(&P.gexec[v], P.graph[v], 0);
     if (err != cudaSuccess) {
         set_error("cudaGraphInstantiate failed: %s", cudaGetErrorString(err));
         cudaGetLastError();
-        cudaGraphDestroy(P.graph);
-        P.graph = nullptr;
-        P.gexec = nullptr;
+        cudaGraphDestroy(P.graph[v]);
+        P.graph[v] = nullptr;
+        P.gexec[v] = nullptr;
         return PIC_POISSON_ECUDA;
     }
     return PIC_POISSON_OK;
 }
 
 int solve_batch(pic_poisson_plan_s &P, const double *const *rho, double *const *phi, double tol,
-                pic_poisson_info *infos) {
-    int rc = set_io(P, rho, phi, tol);
+                pic_poisson_info *infos, const double *const *guess_modes = nullptr) {
+    int rc = set_io(P, rho, phi, guess_modes, tol);
     if (rc) return rc;
     Tally tally;
     double ms[PIC_POISSON_NPHASE] = {0};
+    const int guess = guess_modes ? 2 : ((P.shared.flags & PIC_POISSON_USE_INITIAL_GUESS) ? 1 : 0);
+    const int v = guess == 2 ? 1 : 0;
     const bool graph = (P.shared.flags & PIC_POISSON_GRAPH) && !(P.shared.flags & PIC_POISSON_PROFILE);
     if (graph) {
-        if (!P.gexec) {
-            rc = capture_graph(P);
+        if (!P.gexec[v]) {
+            rc = capture_graph(P, guess);
             if (rc) return rc;
         }
-        PP_CUDA(cudaGraphLaunch(P.gexec, P.stream));
+        PP_CUDA(cudaGraphLaunch(P.gexec[v], P.stream));
     } else {
-        rc = run_host_loop(P, tally, ms);
+        rc = run_host_loop(P, guess, tally, ms);
         if (rc) return rc;
     }
     PP_CUDA(cudaMemcpyAsync(P.hctrl_out, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, P.stream));
@@ -436,9 +447,10 @@ int solve_batch(pic_poisson_plan_s &P, const double *const *rho, double *const *
     if (graph) {
         const int passes = C.cycles / inc;
         for (int ph = 0; ph < PIC_POISSON_NPHASE; ++ph) {
-            tally.bytes[ph] = P.seg[0].bytes[ph] + passes * P.seg[1].bytes[ph] + P.seg[2].bytes[ph];
-            tally.flops[ph] = P.seg[0].flops[ph] + passes * P.seg[1].flops[ph] + P.seg[2].flops[ph];
-            tally.launches[ph] = P.seg[0].launches[ph] + passes * P.seg[1].launches[ph] + P.seg[2].launches[ph];
+            const Tally *sg = P.seg[v];
+            tally.bytes[ph] = sg[0].bytes[ph] + passes * sg[1].bytes[ph] + sg[2].bytes[ph];
+            tally.flops[ph] = sg[0].flops[ph] + passes * sg[1].flops[ph] + sg[2].flops[ph];
+            tally.launches[ph] = sg[0].launches[ph] + passes * sg[1].launches[ph] + sg[2].launches[ph];
         }
     }
     int worst = PIC_POISSON_OK;
@@ -613,6 +625,52 @@ int pic_poisson_mode_residual(pic_poisson_plan_t plan, const double *uhat_dev, c
         PP_CUDA(cudaStreamSynchronize(P.stream));
         *rel_res = P.hsum[1] > 0 ? std::sqrt(P.hsum[0] / P.hsum[1]) : std::sqrt(P.hsum[0]);
     }
+    return PIC_POISSON_OK;
+}
+
+int pic_poisson_solve_modes(pic_poisson_plan_t plan, const double *rho_dev, const double *uhat_guess_dev,
+                            double *phi_dev, double tol, pic_poisson_info *info) {
+    int rc = plan_enter(plan);
+    if (rc) return rc;
+    rc = single_only(*plan, "pic_poisson_solve_modes");
+    if (rc) return rc;
+    if (!rho_dev || !phi_dev || !uhat_guess_dev || (const void *)rho_dev == (const void *)phi_dev || std::isnan(tol)) {
+        set_error("rho_dev, uhat_guess_dev and phi_dev must be non-NULL (rho != phi) and tol a number");
+        return PIC_POISSON_EINVAL;
+    }
+    return solve_batch(*plan, &rho_dev, &phi_dev, tol, info, &uhat_guess_dev);
+}
+
+int pic_poisson_analyze(pic_poisson_plan_t plan, const double *phi_dev, double *uhat_dev) {
+    int rc = plan_enter(plan);
+    if (rc) return rc;
+    rc = single_only(*plan, "pic_poisson_analyze");
+    if (rc) return rc;
+    if (!phi_dev || !uhat_dev) {
+        set_error("NULL pointer");
+        return PIC_POISSON_EINVAL;
+    }
+    pic_poisson_plan_s &P = *plan;
+    FFTTab t = P.h_guess;
+    t.p[0].rho = phi_dev;
+    t.p[0].b = (double2 *)uhat_dev;
+    PP_CUDA(cudaMemcpyAsync(P.api_fft, &t, sizeof t, cudaMemcpyHostToDevice, P.stream));
+    PP_CUDA(launch_forward(P.api_fft, P.g_fft, P.smem_fft, nullptr, P.stream));
+    return PIC_POISSON_OK;
+}
+
+int pic_poisson_get_modes(pic_poisson_plan_t plan, double *uhat_dev) {
+    int rc = plan_enter(plan);
+    if (rc) return rc;
+    rc = single_only(*plan, "pic_poisson_get_modes");
+    if (rc) return rc;
+    if (!uhat_dev) {
+        set_error("NULL pointer");
+        return PIC_POISSON_EINVAL;
+    }
+    const ProblemPlan &q = plan->pr[0];
+    const size_t n = (size_t)q.lv[0].nr * q.lv[0].nz * q.nm;
+    PP_CUDA(cudaMemcpyAsync(uhat_dev, q.dl[0].u, n * sizeof(double2), cudaMemcpyDeviceToDevice, plan->stream));
     return PIC_POISSON_OK;
 }
 
