@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-sequence", action="store_true", help="skip the drifting-wave sequence")
     ap.add_argument("--sequence-steps", type=int, default=200)
     ap.add_argument("--tune-cache", default=None, help="JSON file caching autotuner results")
+    ap.add_argument("--learned", action="store_true", help="train and evaluate the learned warm start (~2 min)")
+    ap.add_argument("--learned-steps", type=int, default=40, help="evaluation steps of the learned warm start")
+    ap.add_argument("--learned-epochs", type=int, default=8)
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NR", "NTHETA", "NZ"), default=None,
                     help="override the 512 128 400 grid (profiling of smaller cases)")
     return ap.parse_args()
@@ -371,6 +374,8 @@ def run_ours(args):
         line["batch_uneven"] = run_batch(args, dev)
     if not args.no_sequence:
         line["sequence"] = run_sequence(args, dev, p)
+    if args.learned:
+        line["learned_warm_start"] = run_learned(args, dev, p)
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         ms, det = oracle_sample()
@@ -473,6 +478,55 @@ def run_sequence(args, dev, p):
         warm.close()
         zero.close()
     return out
+
+
+def run_learned(args, dev, p):
+    """Learned warm start: train the U-Net on 3000 (residual, correction) pairs from
+    plain solves of a 256x64x200 drifting-wave sequence (seed 7), then solve the
+    drifting sequence at the headline grid from the learned guess vs the
+    previous-step guess (inference, extra transform and step included)."""
+    import torch
+    from paper_2609_07172_gb300 import learned as LW, workloads as W
+    from paper_2609_07172_gb300.unet import UNet
+    t0 = time.perf_counter()
+    pt = W.annulus(256, 64, 200)
+    steps = -(-3000 // pt.n_modes)
+    X, Y, gain = LW.training_pairs(pt, steps=steps, seed=7, limit=3000)
+    t_data = time.perf_counter() - t0
+    net = UNet(seed=0)
+    t0 = time.perf_counter()
+    losses = LW.train(net, X, Y, epochs=args.learned_epochs, batch=16, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del X, Y
+    res = LW.evaluate_sequence(net, gain, p, steps=args.learned_steps, tol=args.tol, coarse=True, gpu_inputs=True,
+                               seed=3)
+    # inference alone (pack, U-Net, unpack, prolongation, minimal-residual step)
+    plan = None
+    from paper_2609_07172_gb300 import Plan
+    plan = Plan(p, graph=True)
+    ws = LW.WarmStart(net, gain, p, plan)
+    rho = W.drifting_rho_torch(p, 0)
+    bhat = plan.forward(rho)
+    u = torch.zeros(plan.mode_shape, dtype=torch.float64, device=dev)
+    ws.guess(bhat, u)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(5):
+        ws.guess(bhat, u)
+    e1.record()
+    torch.cuda.synchronize()
+    inf_ms = e0.elapsed_time(e1) / 5
+    plan.close()
+    return {"train": {"grid": "256x64x200 drifting m=8 wave, seed 7", "pairs": 3000, "params": net.n_params(),
+                      "epochs": args.learned_epochs, "batch": 16, "data_s": t_data, "train_s": t_train,
+                      "loss_epoch_mean": losses},
+            "eval": {k: v for k, v in res.items() if k != "records"},
+            "warm_start_ms": inf_ms,
+            "note": "learned = forward transform + residual of the previous iterate + U-Net on the 2:1 restricted "
+                    "residual (65 modes at 256x200) + prolongation + minimal-residual step, then the solve; "
+                    "prev = solve from the previous-step modes; both graph-captured FP64 to rel-res %g" % args.tol}
 
 
 def main():

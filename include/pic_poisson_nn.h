@@ -105,7 +105,7 @@ int pic_nn_prolong2(const double *c, int nr, int nz, int nm, double *f, void *st
  * the entries; alpha = 0 when <b, b> = 0); with b = -A d and sign = -1 this is
  * the step that minimises ||r - alpha A d||, so the result's residual is never
  * larger than r's.  *alpha (device, may be NULL) receives the step.
- * scratch: 1026 doubles.
+ * scratch: 1027 doubles.
  */
 int pic_nn_minres_step(const double *x, const double *d, const double *r, const double *b, long entries, int nm,
                        int nt, double sign, double *scratch, double *out, double *alpha, void *stream);

@@ -465,27 +465,45 @@ __global__ void __launch_bounds__(256) k_dots(const double2 *__restrict__ a, con
     }
 }
 
-__global__ void k_dots_final(const double *__restrict__ part, int nb, double *__restrict__ out) {
-    if (threadIdx.x != 0) return;
+// Sums of the dot partials (one CTA, fixed order) and the step
+// alpha = sign <r, b> / <b, b> (0 when <b, b> = 0 or not finite): out[0..2].
+__global__ void __launch_bounds__(512) k_dots_final(const double *__restrict__ part, int nb, double sign,
+                                                    double *__restrict__ out, double *__restrict__ alpha_out) {
+    __shared__ double r1[16], r2[16];
     double s1 = 0.0, s2 = 0.0;
-    for (int b = 0; b < nb; ++b) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         s1 += part[2 * b];
         s2 += part[2 * b + 1];
     }
-    out[0] = s1;
-    out[1] = s2;
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        r1[threadIdx.x >> 5] = s1;
+        r2[threadIdx.x >> 5] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t1 += r1[w];
+            t2 += r2[w];
+        }
+        const double al = (t2 > 0.0 && isfinite(t1)) ? sign * t1 / t2 : 0.0;
+        out[0] = t1;
+        out[1] = t2;
+        out[2] = al;
+        if (alpha_out) *alpha_out = al;
+    }
 }
 
-// out = x + alpha d with alpha = sign * dots[0] / dots[1] (0 when dots[1] = 0):
-// the minimal-residual step along d when b = -A d is the field of dots.
+// out = x + alpha d with the step computed by k_dots_final.
 __global__ void k_axpy_alpha(const double2 *__restrict__ x, const double2 *__restrict__ d,
-                             const double *__restrict__ dots, double sign, long n, double2 *__restrict__ out,
-                             double *__restrict__ alpha_out) {
+                             const double *__restrict__ dots, long n, double2 *__restrict__ out) {
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const double den = dots[1];
-    const double al = (den > 0.0 && isfinite(dots[0])) ? sign * dots[0] / den : 0.0;
-    if (e == 0 && alpha_out) *alpha_out = al;
     if (e >= n) return;
+    const double al = dots[2];
     const double2 a = x[e], b = d[e];
     out[e] = make_double2(fma(al, b.x, a.x), fma(al, b.y, a.y));
 }
@@ -679,9 +697,9 @@ int pic_nn_minres_step(const double *x, const double *d, const double *r, const 
     const cudaStream_t st = (cudaStream_t)stream;
     const int nb = 512;
     k_dots<<<nb, 256, 0, st>>>((const double2 *)r, (const double2 *)b, entries, nm, nt, scratch);
-    k_dots_final<<<1, 32, 0, st>>>(scratch, nb, scratch + 2 * nb);
-    k_axpy_alpha<<<grid1(entries), 256, 0, st>>>((const double2 *)x, (const double2 *)d, scratch + 2 * nb, sign,
-                                                 entries, (double2 *)out, alpha);
+    k_dots_final<<<1, 512, 0, st>>>(scratch, nb, sign, scratch + 2 * nb, alpha);
+    k_axpy_alpha<<<grid1(entries), 256, 0, st>>>((const double2 *)x, (const double2 *)d, scratch + 2 * nb, entries,
+                                                 (double2 *)out);
     NN_CHECK();
     return PIC_POISSON_OK;
 }

@@ -67,8 +67,10 @@ class Packer:
 def training_pairs(p, steps, seed=7, limit=None, tol=1e-11):
     """Pairs (network input, normalised correction) from plain FP64 solves of the
     drifting-wave sequence on problem p (`steps` steps, N_theta/2+1 modes each).
-    Returns X (BF16 [n, nz, nr, 16]), Y (FP32 [n, nz, nr, 2]) and the gain g
-    with Y = correction / (g * rms(residual))."""
+    Returns X (BF16 [n, nz, nr, 16]), Y (FP32 [n, nz, nr, 2]) and a gain.
+    Each target is the correction scaled to unit RMS: the network learns the
+    direction of the correction; its length is set at use by the
+    minimal-residual step, so the returned gain is 1."""
     dev = torch.device("cuda")
     pk = Packer(p)
     nm = pk.nm
@@ -85,20 +87,21 @@ def training_pairs(p, steps, seed=7, limit=None, tol=1e-11):
             x, rms_r = pk.pack(r)
             xs.append(x.clone())
             rr.append(rms_r.clone())
-            es.append(e.permute(2, 0, 1, 3).contiguous().float() / rms_r.view(nm, 1, 1, 1))
+            em = e.permute(2, 0, 1, 3).contiguous()
+            rms_e = em.pow(2).mean(dim=(1, 2, 3)).sqrt().clamp_min(1e-300)
+            es.append((em / rms_e.view(nm, 1, 1, 1)).float())
             uprev = u
     X = torch.cat(xs)
-    Yraw = torch.cat(es)
-    ratio = Yraw.pow(2).mean(dim=(1, 2, 3)).sqrt()
-    gain = float(ratio.median())
-    Y = Yraw / gain
+    Y = torch.cat(es)
+    gain = 1.0
     if limit:
         X, Y = X[:limit], Y[:limit]
     return X.contiguous(), Y.contiguous(), gain
 
 
-def train(net, X, Y, epochs=20, batch=16, lr=2e-3, seed=0, log=None):
-    """Adam on MSE with random sign flips (the correction is odd in the residual)."""
+def train(net, X, Y, epochs=20, batch=16, lr=1e-3, seed=0, log=None):
+    """Adam on MSE with random sign flips (the correction is odd in the residual);
+    returns the mean loss of every epoch."""
     g = torch.Generator(device="cpu").manual_seed(seed)
     n = X.shape[0]
     steps = max(1, n // batch) * epochs
@@ -106,6 +109,7 @@ def train(net, X, Y, epochs=20, batch=16, lr=2e-3, seed=0, log=None):
     t0 = time.time()
     k = 0
     for ep in range(epochs):
+        ep_losses = []
         perm = torch.randperm(n, generator=g)
         for s in range(n // batch):
             idx = perm[s * batch:(s + 1) * batch].to(X.device)
@@ -118,10 +122,10 @@ def train(net, X, Y, epochs=20, batch=16, lr=2e-3, seed=0, log=None):
             cur = lr * 0.5 * (1.0 + math.cos(math.pi * k / steps))
             net.adam(cur)
             k += 1
-            if s % 20 == 0:
-                losses.append(float(loss.item()))
+            ep_losses.append(loss.clone())
+        losses.append(float(torch.stack(ep_losses).mean().item()))
         if log:
-            log(f"epoch {ep}: loss {losses[-1]:.4f} ({time.time() - t0:.1f} s)")
+            log(f"epoch {ep}: mean loss {losses[-1]:.4f} ({time.time() - t0:.1f} s)")
     return losses
 
 
