@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("fp64", "mixed"), default="fp64")
-    ap.add_argument("--seeds", type=int, default=4)
+    ap.add_argument("--seeds", type=int, default=10)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--sequence-steps", type=int, default=200)
     ap.add_argument("--tune-cache", default=None, help="JSON file caching autotuner results")
     ap.add_argument("--learned", action="store_true", help="train and evaluate the learned warm start (~2 min)")
-    ap.add_argument("--learned-steps", type=int, default=40, help="evaluation steps of the learned warm start")
+    ap.add_argument("--no-tune", action="store_true", help="default schedule instead of the autotuner's")
+    ap.add_argument("--learned-steps", type=int, default=200, help="evaluation steps of the learned warm start")
     ap.add_argument("--learned-epochs", type=int, default=8)
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NR", "NTHETA", "NZ"), default=None,
                     help="override the 512 128 400 grid (profiling of smaller cases)")
@@ -206,19 +207,27 @@ def time_form(plan, rhos, phi, steps, warmup, tol, world, dist, sampler=None):
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     infos = []
-    e0.record(plan.stream)
+    ev[0].record(plan.stream)
     for k in range(steps):
         _, info = plan.solve(rhos[k % len(rhos)], phi, tol=tol)
         infos.append(info)
-    e1.record(plan.stream)
+        ev[k + 1].record(plan.stream)
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
     if world > 1:
         dist.barrier()
-    return e0.elapsed_time(e1), infos, clocks
+    # per-solve times (each solve returns its info, so the steps do not overlap)
+    for k, info in enumerate(infos):
+        info["ms_event"] = ev[k].elapsed_time(ev[k + 1])
+    return ev[0].elapsed_time(ev[-1]), infos, clocks
+
+
+def percentiles(infos):
+    xs = sorted(i["ms_event"] for i in infos)
+    q = lambda f: xs[min(len(xs) - 1, int(round(f * (len(xs) - 1))))]
+    return {"p10": q(0.1), "p50": q(0.5), "p90": q(0.9)}
 
 
 def roofline(infos, prec_fp64, fp64_tflops, hbm_peak, hbm_src, traffic):
@@ -275,7 +284,19 @@ def run_ours(args):
     hbm_peak, hbm_src = measured_peaks()
     tag = "%dx%dx%d" % (p.nr, p.ntheta, p.nz)
 
-    plan = Plan(p, precision=prec, profile=True)
+    # schedule (sweeps, FP32 inner cycles, smoother block size) picked by the
+    # autotuner on this problem, outside the timed region (cached with --tune-cache)
+    def tuned_kw(precision):
+        if args.no_tune:
+            return {}, None
+        from paper_2609_07172_gb300 import autotune
+        t = autotune([p], [rhos[0]], tol=args.tol, precision=precision, graph=True, repeats=2,
+                     cache=args.tune_cache)
+        return {k: t[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads")}, t
+
+    kw, tuned = tuned_kw(prec)
+    # headline: each solve one CUDA graph (device-side convergence loop)
+    plan = Plan(p, precision=prec, graph=True, **kw)
     ms_total, infos, clocks = time_form(plan, rhos, phi, args.steps, args.warmup, args.tol, world, dist,
                                         ClockSampler(local))
     if world > 1:
@@ -287,29 +308,44 @@ def run_ours(args):
     cycles = [i["cycles"] for i in infos]
     by = sum_phase(infos, "bytes_phase")
     solve_gbs = sum(by.values()) / len(infos) / (ms_local * 1e-3) / 1e9
-    ms_ph = sum_phase(infos, "ms_phase")
-    traffic = traffic_from_profile("smooth_%s_%s.md" % (args.precision, tag))
+    # profiled pass: the same solves through the host-driven loop with CUDA events
+    # around every launch, for per-kernel-class times and the roofline
+    pplan = Plan(p, precision=prec, profile=True, **kw)
+    ms_prof, pinfos, _ = time_form(pplan, rhos, phi, args.steps, 2, args.tol, world, dist)
+    pplan.close()
+    ms_ph = sum_phase(pinfos, "ms_phase")
+    # DRAM bytes of a level-0 half-sweep at 512x128x400 (ncu, scaled from 512x128x200 where valid)
+    traffic = traffic_from_profile("smooth_%s_512x128x200.md" % args.precision) if tag == "512x128x400" else None
+    sched = {"pre_sweeps": kw.get("pre_sweeps", 2), "post_sweeps": kw.get("post_sweeps", 2),
+             "inner_cycles": kw.get("inner_cycles", 2), "smooth_threads": kw.get("smooth_threads", 256)}
 
     line = {"metric": METRIC, "value": ms_per_solve, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_local, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == FP64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": "annulus %s, %d azimuthal modes, %s batched GMG V(2,2), rho seeds %s "
+            "config": {"workload": "annulus %s, %d azimuthal modes, %s batched GMG, rho seeds %s "
                                    "(Poisson counts, mean 27, m=8 wave)" % (tag, p.n_modes, args.precision, seeds),
                        "grid_nr_ntheta_nz": [p.nr, p.ntheta, p.nz], "tol": args.tol, "levels": q["levels"],
+                       "schedule": sched, "driver": "one CUDA graph per solve (PIC_POISSON_GRAPH)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (rho 209.7 MB, mode vector 213 MB per step)"},
             "status": sorted({i["status"] for i in infos}),
             "cycles": {"min": min(cycles), "max": max(cycles), "median": statistics.median(cycles)},
+            "ms_per_solve_percentiles": percentiles(infos),
             "rel_res_max": max(i["rel_res"] for i in infos),
             "gpu_launches": int(sum(i["launches"] for i in infos)),
-            "phase_ms_per_solve": {k: v / len(infos) for k, v in ms_ph.items()},
-            "roofline": roofline(infos, prec == FP64, fp64_gflops / 1e3, hbm_peak, hbm_src, traffic),
+            "phase_ms_per_solve": {k: v / len(pinfos) for k, v in ms_ph.items()},
+            "roofline": dict(roofline(pinfos, prec == FP64, fp64_gflops / 1e3, hbm_peak, hbm_src, traffic),
+                             timed_region="profiled pass: the same %d solves through the host-driven loop with "
+                                          "CUDA events around every launch" % args.steps),
             "hbm_roofline_solve": {"achieved_gbs": solve_gbs, "peak_gbs": hbm_peak, "frac": solve_gbs / hbm_peak,
                                    "algorithmic_bytes_per_solve": sum(by.values()) / len(infos),
                                    "peak_source": hbm_src},
             "fma_peaks_gflops": {"fp64": fp64_gflops, "fp32": fp32_gflops},
-            "clocks": clocks}
+            "clocks": clocks,
+            "host_loop_profiled_ms_per_solve": ms_prof / args.steps}
+    if tuned:
+        line["autotune"] = {"candidates": len(tuned.get("tried", [])), "best_ms": tuned.get("ms")}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     if not args.no_e2e:
@@ -333,42 +369,37 @@ def run_ours(args):
     ref_phi = phi.clone()
     plan.close()
 
-    # ---- the same solves as one CUDA graph each (device-side convergence loop)
-    gplan = Plan(p, precision=prec, graph=True)
-    ms_g, infos_g, _ = time_form(gplan, rhos, phi, args.steps, args.warmup, args.tol, world, dist)
-    line["graph"] = {"ms_per_solve": ms_g / args.steps,
-                     "cycles_median": statistics.median([i["cycles"] for i in infos_g]),
-                     "note": "PIC_POISSON_GRAPH: whole solve one graph launch, convergence loop a device-side "
-                             "while node; same kernels and cycles as the headline host-driven loop"}
-    gplan.close()
-
     # ---- the other form on the same GPU and inputs (mixed FP32/FP64 when the headline is FP64)
     if not args.no_forms:
         other = MIXED if prec == FP64 else FP64
         name = "mixed" if other == MIXED else "fp64"
-        plan2 = Plan(p, precision=other, profile=True)
+        kw2, _ = tuned_kw(other)
+        plan2 = Plan(p, precision=other, graph=True, **kw2)
         steps2 = max(4, args.steps // 2)
         phi2 = torch.empty_like(phi)
         ms2, infos2, _ = time_form(plan2, rhos, phi2, steps2, 2, args.tol, world, dist)
-        # same input as the last headline step
         plan2.solve(rhos[(args.steps - 1) % len(rhos)], phi2, tol=args.tol)
         torch.cuda.synchronize()
         diff = float(torch.linalg.vector_norm(phi2 - ref_phi) / torch.linalg.vector_norm(ref_phi))
+        plan2.close()
+        pplan2 = Plan(p, precision=other, profile=True, **kw2)
+        _, pinfos2, _ = time_form(pplan2, rhos, phi2, steps2, 1, args.tol, world, dist)
+        pplan2.close()
         by2 = sum_phase(infos2, "bytes_phase")
         ms2_solve = ms2 / steps2
         gbs2 = sum(by2.values()) / len(infos2) / (ms2_solve * 1e-3) / 1e9
         c2 = [i["cycles"] for i in infos2]
         line["forms"] = {name: {
-            "ms_per_solve": ms2_solve, "steps": steps2, "dtype": "f32+f64" if other == MIXED else "f64",
-            "cycles_median": statistics.median(c2),
+            "ms_per_solve": ms2_solve, "steps": steps2, "ms_per_solve_percentiles": percentiles(infos2), "dtype": "f32+f64" if other == MIXED else "f64",
+            "schedule": kw2 or "defaults", "cycles_median": statistics.median(c2),
             "outer_iterations_median": statistics.median([i["outer_iterations"] for i in infos2]),
             "rel_res_max": max(i["rel_res"] for i in infos2),
             "rel_l2_vs_headline_phi": diff,
-            "phase_ms_per_solve": {k: v / len(infos2) for k, v in sum_phase(infos2, "ms_phase").items()},
-            "roofline": roofline(infos2, other == FP64, fp64_gflops / 1e3, hbm_peak, hbm_src,
-                                 traffic_from_profile("smooth_%s_%s.md" % (name, tag))),
+            "phase_ms_per_solve": {k: v / len(pinfos2) for k, v in sum_phase(pinfos2, "ms_phase").items()},
+            "roofline": roofline(pinfos2, other == FP64, fp64_gflops / 1e3, hbm_peak, hbm_src,
+                                 traffic_from_profile("smooth_%s_512x128x200.md" % name)
+                                 if tag == "512x128x400" else None),
             "hbm_roofline_solve": {"achieved_gbs": gbs2, "peak_gbs": hbm_peak, "frac": gbs2 / hbm_peak}}}
-        plan2.close()
 
     if not args.no_batch:
         line["batch_uneven"] = run_batch(args, dev)

@@ -16,6 +16,17 @@
 // (k, i0 .. i0+TI-1), staged in shared memory and stored with coalesced writes.
 // Problems of a batch may differ in size and N_theta; the dynamic shared
 // memory is sized for the largest.
+//
+// FP64 runs at 1/64 of the FP32 rate on this GPU, so the transforms are bound
+// by FP64 instructions and are written to issue few of them:
+//  * a butterfly top +- w bot with w = a (1 + i b) (or a (b + i)) costs six
+//    multiply-adds: u = bot + i b bot (two), top +- a u (four) -- instead of a
+//    four-operation complex product and four additions;
+//  * twiddles 1 and -i (+i inverse) need additions only;
+//  * each thread applies two consecutive radix-2 stages to four values held
+//    in registers, halving the shared-memory round trips and barriers;
+//  * the unpack (pack) of the real transform treats modes m and M - m
+//    together, sharing one twiddle product.
 #include "internal.h"
 
 namespace pp {
@@ -23,13 +34,6 @@ namespace {
 
 constexpr int TI = FFT_TI;
 constexpr int LD = TI + 1;   // padded row of the transform buffer (conflict-free 16-byte lanes)
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {   // conj(a) * b
-    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
-}
 
 __device__ __forceinline__ int bitrev(int n, int log2M) {
     return log2M == 0 ? 0 : (int)(__brev((unsigned)n) >> (32 - log2M));
@@ -45,33 +49,71 @@ __device__ __forceinline__ int find_problem(const unsigned *__restrict__ start, 
     return lo;
 }
 
-// In-place radix-2 DIT FFT of length M on buf[M][LD] (bit-reversed input).
-// INVERSE: conjugated twiddles (e^{+2 pi i t / M}).  Twiddles w = 1 (pos = 0)
-// and w = -i / +i (pos = h/2) need no multiplication.
+// u with w z = a u for the twiddle entry (a, b) of e^{-2 pi i t / n}
+// (INVERSE: of its conjugate).  first: the entry's form (tw_first_form).
 template <bool INVERSE>
-__device__ __forceinline__ void fft_stages(double2 *buf, const double2 *__restrict__ tw, int M, int lane, int warp,
-                                           int nw) {
-    const int half = M >> 1;
-    int log2h = 0;
-    for (int h = 1; h < M; h <<= 1, ++log2h) {
-        const int stride = half >> log2h;           // twiddle index step: M / (2h)
-        for (int bi = warp; bi < half; bi += nw) {
-            const int pos = bi & (h - 1);
-            const int top = ((bi >> log2h) << (log2h + 1)) + pos;
-            const int bot = top + h;
-            const double2 zt = buf[top * LD + lane];
-            const double2 zb = buf[bot * LD + lane];
-            double2 t;
-            if (pos == 0) {
-                t = zb;
-            } else if (2 * pos == h) {
-                t = INVERSE ? make_double2(-zb.y, zb.x) : make_double2(zb.y, -zb.x);
-            } else {
-                const double2 w = tw[pos * stride];
-                t = INVERSE ? cmulc(w, zb) : cmul(w, zb);
-            }
-            buf[top * LD + lane] = make_double2(zt.x + t.x, zt.y + t.y);
-            buf[bot * LD + lane] = make_double2(zt.x - t.x, zt.y - t.y);
+__device__ __forceinline__ double2 tw_reduce(double b, bool first, double2 z) {
+    if (first) {   // w = a (1 + i b)
+        return INVERSE ? make_double2(fma(b, z.y, z.x), fma(-b, z.x, z.y))
+                       : make_double2(fma(-b, z.y, z.x), fma(b, z.x, z.y));
+    }
+    // w = a (b + i)
+    return INVERSE ? make_double2(fma(b, z.x, z.y), fma(b, z.y, -z.x)) : make_double2(fma(b, z.x, -z.y), fma(b, z.y, z.x));
+}
+
+// Radix-2 butterfly (top, bot) <- (top + w bot, top - w bot), w = e^{-+2 pi i t / M}.
+template <bool INVERSE>
+__device__ __forceinline__ void bfly(double2 &top, double2 &bot, int t, int M, const double2 *__restrict__ tw) {
+    if (t == 0) {
+        const double2 x = top;
+        top = make_double2(x.x + bot.x, x.y + bot.y);
+        bot = make_double2(x.x - bot.x, x.y - bot.y);
+    } else if (4 * t == M) {   // w = -i (+i inverse)
+        const double2 x = top, y = INVERSE ? make_double2(-bot.y, bot.x) : make_double2(bot.y, -bot.x);
+        top = make_double2(x.x + y.x, x.y + y.y);
+        bot = make_double2(x.x - y.x, x.y - y.y);
+    } else {
+        const double2 ab = tw[t];
+        const double2 u = tw_reduce<INVERSE>(ab.y, tw_first_form(t, M), bot);
+        const double2 x = top;
+        top = make_double2(fma(ab.x, u.x, x.x), fma(ab.x, u.y, x.y));
+        bot = make_double2(fma(-ab.x, u.x, x.x), fma(-ab.x, u.y, x.y));
+    }
+}
+
+// In-place radix-2 DIT FFT of length M on buf[M][LD] (bit-reversed input),
+// two stages (h, 2h) per pass on four values per thread, a single first
+// stage when log2 M is odd.  INVERSE: conjugated twiddles.
+template <bool INVERSE>
+__device__ __forceinline__ void fft_stages(double2 *buf, const double2 *__restrict__ tw, int M, int log2M, int lane,
+                                           int warp, int nw) {
+    int h = 1;
+    if (log2M & 1) {   // stage h = 1: twiddle 1 only
+        for (int q = warp; q < (M >> 1); q += nw) {
+            double2 a = buf[(2 * q) * LD + lane], b = buf[(2 * q + 1) * LD + lane];
+            bfly<INVERSE>(a, b, 0, M, tw);
+            buf[(2 * q) * LD + lane] = a;
+            buf[(2 * q + 1) * LD + lane] = b;
+        }
+        __syncthreads();
+        h = 2;
+    }
+    for (; 4 * h <= M; h <<= 2) {
+        for (int q = warp; q < (M >> 2); q += nw) {
+            const int p = q & (h - 1);
+            const int g = (q - p) << 2;   // (q / h) * 4h
+            double2 *x = buf + (g + p) * LD + lane;
+            double2 a0 = x[0], a1 = x[h * LD], a2 = x[2 * h * LD], a3 = x[3 * h * LD];
+            const int t1 = p * (M / (2 * h));          // W_{2h}^p
+            bfly<INVERSE>(a0, a1, t1, M, tw);
+            bfly<INVERSE>(a2, a3, t1, M, tw);
+            const int t2 = p * (M / (4 * h));          // W_{4h}^p and W_{4h}^{p+h}
+            bfly<INVERSE>(a0, a2, t2, M, tw);
+            bfly<INVERSE>(a1, a3, t2 + (M >> 2), M, tw);
+            x[0] = a0;
+            x[h * LD] = a1;
+            x[2 * h * LD] = a2;
+            x[3 * h * LD] = a3;
         }
         __syncthreads();
     }
@@ -118,32 +160,41 @@ __global__ void __launch_bounds__(FFT_THREADS) k_forward(const FFTTab *__restric
         buf[bitrev(n, P.log2M) * LD + lane] = make_double2(a, b);
     }
     __syncthreads();
-    fft_stages<false>(buf, (const double2 *)P.tw, M, lane, warp, nw);
+    fft_stages<false>(buf, (const double2 *)P.tw, M, P.log2M, lane, warp, nw);
 
-    // Unpack: X_m = 1/2 [ (Z_m + conj Z_{M-m}) - i W^m (Z_m - conj Z_{M-m}) ], W = e^{-2 pi i / N}
+    // Unpack, modes m and M - m together (W = e^{-2 pi i / N}, hs = s_i / (2N)):
+    //   S = Z_m + conj Z_{M-m},  D = Z_m - conj Z_{M-m},  T = W^m D,
+    //   X_m = hs (S - i T),  X_{M-m} = hs conj(S + i T);
+    // X_0 = 2 hs (Re Z_0 + Im Z_0), X_M = 2 hs (Re Z_0 - Im Z_0), both exactly real.
     const double2 *tw2 = (const double2 *)P.tw2;
-    const double scale = (P.s ? P.s[valid ? i : 0] : 1.0) * (0.5 / (double)nt);
-    double acc = 0.0;
-    for (int m = warp; m <= M; m += nw) {
-        const double2 A = buf[(m == M ? 0 : m) * LD + lane];
-        const double2 Bc = buf[(m == 0 ? 0 : M - m) * LD + lane];
-        double2 x;
-        if (m == 0 || m == M) {
-            // Z_0 carries X_0 = Re + Im and X_M = Re - Im; both exactly real
-            x = make_double2((m == 0 ? (A.x + A.y) : (A.x - A.y)) * (2.0 * scale), 0.0);
-        } else {
-            const double2 S = make_double2(A.x + Bc.x, A.y - Bc.y);        // Z_m + conj Z_{M-m}
-            const double2 D = make_double2(A.x - Bc.x, A.y + Bc.y);        // Z_m - conj Z_{M-m}
-            const double2 mid = make_double2(D.y, -D.x);                    // -i D
-            const double2 t = cmul(tw2[m], mid);
-            x = make_double2((S.x + t.x) * scale, (S.y + t.y) * scale);
+    const double hs = (P.s ? P.s[valid ? i : 0] : 1.0) * (0.5 / (double)nt);
+    double acc_in = 0.0, acc_edge = 0.0;   // Parseval weight 2 (0 < m < M) and 1 (m = 0, M)
+    double2 *ob = outb + lane * nm;
+    for (int m = warp; 2 * m <= M; m += nw) {
+        if (m == 0) {
+            const double2 z = buf[lane];
+            double x0 = (z.x + z.y) * (2.0 * hs);
+            const double xM = (z.x - z.y) * (2.0 * hs);
+            if (P.bD && valid) x0 += P.bD[(size_t)k * nr + i];
+            acc_edge = fma(x0, x0, fma(xM, xM, acc_edge));
+            ob[0] = make_double2(x0, 0.0);
+            ob[M] = make_double2(xM, 0.0);
+            continue;
         }
-        if (m == 0 && P.bD && valid) x.x += P.bD[(size_t)k * nr + i];
-        if (valid && partials) {
-            const double w = (m == 0 || m == M) ? 1.0 : 2.0;
-            acc += w * (x.x * x.x + x.y * x.y);
+        const double2 A = buf[m * LD + lane], B = buf[(M - m) * LD + lane];
+        const double2 S = make_double2(hs * (A.x + B.x), hs * (A.y - B.y));
+        const double2 D = make_double2(A.x - B.x, A.y + B.y);
+        const double2 ab = tw2[m];
+        const double2 u = tw_reduce<false>(ab.y, tw_first_form(m, nt), D);   // T = ab.x u
+        const double g = hs * ab.x;
+        const double2 xm = make_double2(fma(g, u.y, S.x), fma(-g, u.x, S.y));
+        const double2 xp = make_double2(fma(-g, u.y, S.x), -fma(g, u.x, S.y));
+        ob[m] = xm;
+        acc_in = fma(xm.x, xm.x, fma(xm.y, xm.y, acc_in));
+        if (2 * m != M) {
+            ob[M - m] = xp;
+            acc_in = fma(xp.x, xp.x, fma(xp.y, xp.y, acc_in));
         }
-        outb[lane * nm + m] = x;
     }
     __syncthreads();
     const int ncols = min(TI, nr - i0);
@@ -161,7 +212,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_forward(const FFTTab *__restric
         }
     }
     if (partials) {
-        const double tot = block_sum(acc, red);
+        const double tot = block_sum(valid ? fma(2.0, acc_in, acc_edge) : 0.0, red);
         if (threadIdx.x == 0) partials[blockIdx.x] = tot;
     }
 }
@@ -189,23 +240,29 @@ __global__ void __launch_bounds__(FFT_THREADS) k_inverse(const FFTTab *__restric
         inb[f] = f < ncols * nm ? src[f] : make_double2(0.0, 0.0);
     __syncthreads();
 
-    // Pack: Z_m = (X_m + conj X_{M-m}) + i w^m (X_m - conj X_{M-m}), w = e^{+2 pi i / N};
-    // X_0 and X_M enter through their real parts only.
+    // Pack, modes m and M - m together (w = e^{+2 pi i / N}):
+    //   S = X_m + conj X_{M-m},  D = X_m - conj X_{M-m},  T = w^m D,
+    //   Z_m = S + i T,  Z_{M-m} = conj(S - i T);
+    // X_0 and X_M enter through their real parts only: Z_0 = (X_0 + X_M) + i (X_0 - X_M).
     const double2 *tw2 = (const double2 *)P.tw2;
-    for (int m = warp; m < M; m += nw) {
-        double2 A = inb[lane * nm + m];
-        double2 B = inb[lane * nm + (M - m)];
+    const double2 *ib = inb + lane * nm;
+    for (int m = warp; 2 * m <= M; m += nw) {
         if (m == 0) {
-            A.y = 0.0;
-            B.y = 0.0;
+            const double a = ib[0].x, b = ib[M].x;
+            buf[lane] = make_double2(a + b, a - b);
+            continue;
         }
-        const double2 S = make_double2(A.x + B.x, A.y - B.y);   // X_m + conj X_{M-m}
-        const double2 D = make_double2(A.x - B.x, A.y + B.y);   // X_m - conj X_{M-m}
-        const double2 t = cmulc(tw2[m], D);                     // w^m D
-        buf[bitrev(m, P.log2M) * LD + lane] = make_double2(S.x - t.y, S.y + t.x);   // S + i t
+        const double2 A = ib[m], B = ib[M - m];
+        const double2 S = make_double2(A.x + B.x, A.y - B.y);
+        const double2 D = make_double2(A.x - B.x, A.y + B.y);
+        const double2 ab = tw2[m];
+        const double2 u = tw_reduce<true>(ab.y, tw_first_form(m, nt), D);   // T = ab.x u
+        buf[bitrev(m, P.log2M) * LD + lane] = make_double2(fma(-ab.x, u.y, S.x), fma(ab.x, u.x, S.y));
+        if (2 * m != M)
+            buf[bitrev(M - m, P.log2M) * LD + lane] = make_double2(fma(ab.x, u.y, S.x), fma(ab.x, u.x, -S.y));
     }
     __syncthreads();
-    fft_stages<true>(buf, (const double2 *)P.tw, M, lane, warp, nw);
+    fft_stages<true>(buf, (const double2 *)P.tw, M, P.log2M, lane, warp, nw);
 
     if (valid) {
         double *dst = P.phi + (size_t)k * nt * nr + i;

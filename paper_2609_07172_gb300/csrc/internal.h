@@ -57,6 +57,7 @@ template <class T> struct LevelDev {
     int nr, nz, nm, ncls;
     int nt;                       // azimuthal cells (Parseval weights of the norms)
     int init;                     // what a restriction into the next level writes (see launch_residual_restrict)
+    int strip;                    // smoother: rows of one parity updated per thread (1, 2, 4 or 8)
     const T *cw, *ce, *cz;        // [nr]
     const T *invd, *diag;         // [ncls][nr][nm]
     const T *hw, *he, *hz;        // [ncls][nr][nm] off-diagonal conductances / diag
@@ -102,8 +103,8 @@ struct DefectTab {                // mixed precision: FP64 level 0 and FP32 leve
 // Azimuthal transforms of one problem's finest level.
 struct FFTProb {
     int nr, nt, nz, nm, ncls, log2M;
-    const double *tw;             // [max(M/2,1)] e^{-2 pi i t / M}, M = nt / 2, as (cos, sin) pairs
-    const double *tw2;            // [M+1] e^{-2 pi i m / nt}
+    const double *tw;             // [max(M/2,1)] e^{-2 pi i t / M}, M = nt / 2, as (scale, ratio) pairs
+    const double *tw2;            // [M+1] e^{-2 pi i m / nt}, same form (see tw_first_form)
     const double *s;              // [nr] s_i (Eq. mode_rhs); null: plain 1/N transform
     const double *bD;             // [nz][nr] Dirichlet right-hand side; may be null
     const double *invd;           // level-0 inverse diagonal [ncls][nr][nm]; null: no b_hat
@@ -198,8 +199,24 @@ constexpr int MG_THREADS = 256;
 inline unsigned mg_blocks(size_t entries, int threads = MG_THREADS) {
     return (unsigned)((entries + threads - 1) / threads);
 }
+// Blocks of one smoother launch over a level (see k_smooth): rows of each
+// parity in strips of `strip`, and per strip the (nr/2) * nm entries of one
+// colour of a row.
+inline unsigned smooth_blocks(int nr, int nz, int nm, int strip, int threads) {
+    const size_t w = (size_t)(nr / 2) * nm;
+    const unsigned bx = (unsigned)((w + threads - 1) / threads);
+    const unsigned s0 = (unsigned)(((nz + 1) / 2 + strip - 1) / strip), s1 = (unsigned)((nz / 2 + strip - 1) / strip);
+    return (s0 + s1) * bx;
+}
 constexpr int FFT_TI = 32;        // radial columns per transform CTA
 constexpr int FFT_THREADS = 256;
 size_t fft_smem_bytes(int nt);
+
+// Twiddle tables of the transforms hold e^{-2 pi i t / n} = c - i s as a
+// scale and a ratio, w = a (1 + i b) when |c| >= |s| (a = c, b = -s / c) and
+// w = a (b + i) otherwise (a = -s, b = -c / s), so that a complex product
+// w z costs two multiply-adds plus the scale, which folds into the butterfly's
+// own multiply-adds.  This picks the first form (|b| <= 1 either way).
+__host__ __device__ inline bool tw_first_form(int t, int n) { return 8 * t <= n || 8 * t >= 3 * n; }
 
 }  // namespace pp

@@ -103,30 +103,58 @@ __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i,
 // One red-black Gauss-Seidel half-sweep over the cells of one colour:
 //   u_q <- (b_q + sum_q' G_qq' u_q') / (D0_q + lambda_m mu_q)
 // written as u = b_hat + h_z (u_S + u_N) + h_w u_W + h_e u_E with h = G / diag.
+// Cells of one colour in rows of one parity share their radial index, so a
+// thread owns one (radial cell, mode) and walks a strip of L.strip rows of
+// that parity (k, k+2, ...): the north neighbour of row k is the south
+// neighbour of row k+2 and stays in a register, the interior rows share one
+// set of coefficients, and the index arithmetic is done once per strip.
+// Consecutive threads take consecutive modes of a cell, so every load and
+// store of a warp is contiguous.  Blocks: per parity, strips of rows; per
+// strip, ceil((nr/2) nm / NT) blocks (smooth_blocks).
 template <class T, int NT>
 __global__ void __launch_bounds__(NT) k_smooth(const LaunchTab<T> *__restrict__ tab, int color) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     const LevelDev<T> L = tab->f[p];
-    const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
     const unsigned nm = L.nm;
-    if (e >= (unsigned)L.nz * (unsigned)(L.nr >> 1) * nm) return;
-    const unsigned c = e / nm;
-    const int m = (int)(e - c * nm);
-    int k, i;
-    colour_cell(c, L.nr, color, k, i);
-    const size_t idx = ((size_t)k * L.nr + i) * nm + m;
-    const size_t tb = ((size_t)row_class(k, L.nz, L.ncls) * L.nr + i) * nm + m;
+    const unsigned w = (unsigned)(L.nr >> 1) * nm;
+    const unsigned bx = (w + NT - 1) / NT;
+    const unsigned lb = blockIdx.x - tab->start[p];
+    const unsigned g = lb / bx;
+    const unsigned x = (lb - g * bx) * NT + threadIdx.x;
+    if (x >= w) return;
+    const unsigned s0 = ((unsigned)(L.nz + 1) / 2 + L.strip - 1) / L.strip;
+    const int par = g < s0 ? 0 : 1;
+    const int k0 = par + 2 * (int)(g < s0 ? g : g - s0) * L.strip;
+    const unsigned j = x / nm;
+    const int m = (int)(x - j * nm);
+    const int i = 2 * (int)j + ((par + color) & 1);
     const size_t rowstride = (size_t)L.nr * nm;
-    V2<T> s = mk<T>(0, 0);
-    if (k > 0) s = L.u[idx - rowstride];
-    if (k < L.nz - 1) {
-        const V2<T> n = L.u[idx + rowstride];
-        s = (k > 0) ? mk<T>(s.x + n.x, s.y + n.y) : n;
+    const size_t plane = (size_t)L.nr * nm;            // one row of cells, all modes
+    const size_t tcol = (size_t)i * nm + m;            // (i, m) within a coefficient class
+    const size_t t1 = (L.ncls > 1 ? plane : 0) + tcol;   // interior class (class 1)
+    const T hz1 = L.hz[t1], hw1 = L.hw[t1], he1 = L.he[t1];
+    size_t idx = (size_t)k0 * rowstride + tcol;
+    V2<T> south = k0 > 0 ? L.u[idx - rowstride] : mk<T>(0, 0);
+    const int kend = min(L.nz, k0 + 2 * L.strip);
+    for (int k = k0; k < kend; k += 2, idx += 2 * rowstride) {
+        const bool has_n = k < L.nz - 1;
+        const V2<T> north = has_n ? L.u[idx + rowstride] : mk<T>(0, 0);
+        V2<T> s;
+        if (k > 0 && has_n) s = mk<T>(south.x + north.x, south.y + north.y);
+        else s = k > 0 ? south : north;
+        T hz = hz1, hw = hw1, he = he1;
+        if (k == 0 || !has_n) {   // boundary rows have their own coefficient class
+            const size_t tb = (size_t)row_class(k, L.nz, L.ncls) * plane + tcol;
+            hz = L.hz[tb];
+            hw = L.hw[tb];
+            he = L.he[tb];
+        }
+        V2<T> acc = fma2<T>(hz, s, L.bh[idx]);
+        if (i > 0) acc = fma2<T>(hw, L.u[idx - nm], acc);
+        if (i < L.nr - 1) acc = fma2<T>(he, L.u[idx + nm], acc);
+        L.u[idx] = acc;
+        south = north;
     }
-    V2<T> acc = fma2<T>(L.hz[tb], s, L.bh[idx]);
-    if (i > 0) acc = fma2<T>(L.hw[tb], L.u[idx - nm], acc);
-    if (i < L.nr - 1) acc = fma2<T>(L.he[tb], L.u[idx + nm], acc);
-    L.u[idx] = acc;
 }
 
 // Residual of the fine cells of each coarse cell, summed into the coarse
@@ -152,18 +180,27 @@ k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ p
         // coarsening factors of this level pair (semi-coarsening keeps one direction)
         const int fz = F.nz == C.nz ? 1 : 2, fr = F.nr == C.nr ? 1 : 2;
         V2<T> sum = mk<T>(0, 0);
+        auto add = [&](int k, int i, bool first) {
+            const V2<T> r = residual_at(F, k, i, m, ((size_t)k * F.nr + i) * nm + m);
+            sum = first ? r : mk<T>(sum.x + r.x, sum.y + r.y);
+            if (partials) acc = fma((double)r.y, (double)r.y, fma((double)r.x, (double)r.x, acc));
+        };
+        if (RED_ONLY && fz == 2 && fr == 2) {
+            // the red cells of a 2x2 block are its (0,0) and (1,1) corners
+            add(2 * K, 2 * I, true);
+            add(2 * K + 1, 2 * I + 1, false);
+        } else {
+            bool first = true;
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
+            for (int a = 0; a < 2; ++a) {
 #pragma unroll
-            for (int bb = 0; bb < 2; ++bb) {
-                if (a >= fz || bb >= fr) continue;
-                const int k = fz * K + a, i = fr * I + bb;
-                if (RED_ONLY && ((k + i) & 1)) continue;
-                const size_t idx = ((size_t)k * F.nr + i) * nm + m;
-                const V2<T> r = residual_at(F, k, i, m, idx);
-                sum.x += r.x;
-                sum.y += r.y;
-                if (partials) acc += (double)r.x * r.x + (double)r.y * r.y;
+                for (int bb = 0; bb < 2; ++bb) {
+                    if (a >= fz || bb >= fr) continue;
+                    const int k = fz * K + a, i = fr * I + bb;
+                    if (RED_ONLY && ((k + i) & 1)) continue;
+                    add(k, i, first);
+                    first = false;
+                }
             }
         }
         C.b[e] = sum;
@@ -248,25 +285,63 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
     const bool kin = K2 >= 0 && K2 < C.nz;
     const bool iin = I2 >= 0 && I2 < C.nr;
     const int Kx = kin ? K2 : K, Ix = iin ? I2 : I;
-    const T sk = kin ? T(1) : T(-1), si = iin ? T(1) : T(-1);
     const V2<T> c0 = C.u[((size_t)K * C.nr + I) * nm + m];
     V2<T> u = F.u[idx];
     if (cz2 && cr2) {
         const V2<T> c1 = C.u[((size_t)K * C.nr + Ix) * nm + m];
         const V2<T> c2 = C.u[((size_t)Kx * C.nr + I) * nm + m];
         const V2<T> c3 = C.u[((size_t)Kx * C.nr + Ix) * nm + m];
-        const T w1 = T(0.1875) * si, w2 = T(0.1875) * sk, w3 = T(0.0625) * si * sk;
-        u.x += fma(w3, c3.x, fma(w2, c2.x, fma(w1, c1.x, T(0.5625) * c0.x)));
-        u.y += fma(w3, c3.y, fma(w2, c2.y, fma(w1, c1.y, T(0.5625) * c0.y)));
+        // signed weights by selection (no FP64 multiply), four multiply-adds per part
+        const T w1 = iin ? T(0.1875) : T(-0.1875), w2 = kin ? T(0.1875) : T(-0.1875);
+        const T w3 = iin == kin ? T(0.0625) : T(-0.0625);
+        u.x = fma(w3, c3.x, fma(w2, c2.x, fma(w1, c1.x, fma(T(0.5625), c0.x, u.x))));
+        u.y = fma(w3, c3.y, fma(w2, c2.y, fma(w1, c1.y, fma(T(0.5625), c0.y, u.y))));
     } else {
         // linear along the coarsened direction
         const V2<T> c1 = cz2 ? C.u[((size_t)Kx * C.nr + I) * nm + m] : C.u[((size_t)K * C.nr + Ix) * nm + m];
-        const T w1 = T(0.25) * (cz2 ? sk : si);
-        u.x += fma(w1, c1.x, T(0.75) * c0.x);
-        u.y += fma(w1, c1.y, T(0.75) * c0.y);
+        const T w1 = (cz2 ? kin : iin) ? T(0.25) : T(-0.25);
+        u.x = fma(w1, c1.x, fma(T(0.75), c0.x, u.x));
+        u.y = fma(w1, c1.y, fma(T(0.75), c0.y, u.y));
     }
     F.u[idx] = u;
 }
+
+// Conversions between binary64 and binary32 with a power-of-two scale 2^s,
+// done on the IEEE-754 bit patterns with integer instructions: on this GPU the
+// FP64 unit's conversions cost several FP64 instruction slots each, and the
+// FP64 unit is what bounds the defect and update kernels.
+//   to binary32: the 52-bit mantissa is cut to 23 bits and rounded to nearest
+//   (ties away from zero; a carry moves into the exponent, up to infinity);
+//   results below the binary32 normal range become signed zero, above it
+//   infinity; infinities stay infinite and NaN stays NaN.
+//   to binary64: exact for normal binary32 values; binary32 subnormals become
+//   signed zero.
+__device__ __forceinline__ float f64_to_f32_pow2(double x, int s) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const unsigned m = hi & 0xfffffu;
+    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | ((m | lo) ? 0x400000u : 0u));
+    const int ef = e - 1023 + 127 + s;
+    if (e == 0 || ef <= 0) return __uint_as_float(sign);
+    if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
+    const unsigned bits = (((unsigned)ef << 23) | (m << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
+    return __uint_as_float(sign | bits);
+}
+__device__ __forceinline__ double f32_to_f64_pow2(float f, int s) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u;
+    const int e = (int)((b >> 23) & 0xffu);
+    const unsigned m = b & 0x7fffffu;
+    if (e == 0) return __hiloint2double((int)sign, 0);
+    if (e == 0xff) return __hiloint2double((int)(sign | 0x7ff00000u | (m ? 0x80000u : 0u)), 0);
+    const int ed = e - 127 + 1023 + s;
+    if (ed <= 0) return __hiloint2double((int)sign, 0);
+    if (ed >= 0x7ff) return __hiloint2double((int)(sign | 0x7ff00000u), 0);
+    return __hiloint2double((int)(sign | ((unsigned)ed << 20) | (m >> 3)), (int)(m << 29));
+}
+// Exponent s of a positive power of two 2^s held in a double.
+__device__ __forceinline__ int pow2_exponent(double v) { return ((__double2hiint(v) >> 20) & 0x7ff) - 1023; }
 
 // Mixed precision, FP64 defect: r = b - A_m x on the FP64 level 0 (all cells)
 // and the FP32 level-0 right-hand side of the correction equation, scaled by
@@ -281,7 +356,7 @@ k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, doubl
     const LevelDev<double> D = tab->d[p];
     const LevelDev<float> S = tab->s[p];
     const int init_red = tab->init_red[p];
-    const double sigma = ctrl->sigma_next[p];
+    const int ls = pow2_exponent(ctrl->sigma_next[p]);
     const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
     double acc = 0.0;
     if (e < (unsigned)D.nz * (unsigned)D.nr * (unsigned)D.nm) {
@@ -291,9 +366,9 @@ k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, doubl
         const int k = (int)(c / (unsigned)D.nr);
         const int i = (int)(c - (unsigned)k * D.nr);
         const double2 r = residual_at(D, k, i, m, e);
-        const float2 b32 = make_float2((float)(r.x * sigma), (float)(r.y * sigma));
+        const float2 b32 = make_float2(f64_to_f32_pow2(r.x, ls), f64_to_f32_pow2(r.y, ls));
         const float w = (m == 0 || 2 * m == D.nt) ? 1.f : 2.f;
-        acc = (double)(w * fmaf(b32.x, b32.x, b32.y * b32.y));
+        acc = f32_to_f64_pow2(w * fmaf(b32.x, b32.x, b32.y * b32.y), 0);
         const float inv = S.invd[((size_t)row_class(k, S.nz, S.ncls) * S.nr + i) * nm + m];
         const float2 bh = make_float2(b32.x * inv, b32.y * inv);
         S.b[e] = b32;
@@ -310,22 +385,30 @@ __global__ void __launch_bounds__(MG_THREADS) k_update(const DefectTab *__restri
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     const LevelDev<double> D = tab->d[p];
     const LevelDev<float> S = tab->s[p];
-    const double inv = ctrl->inv_sigma_used[p];
+    const int ls = pow2_exponent(ctrl->inv_sigma_used[p]);
     const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
     if (e >= (unsigned)D.nz * (unsigned)D.nr * (unsigned)D.nm) return;
     const float2 c = S.u[e];
     double2 x = D.u[e];
-    x.x = fma((double)c.x, inv, x.x);
-    x.y = fma((double)c.y, inv, x.y);
+    x.x += f32_to_f64_pow2(c.x, ls);
+    x.y += f32_to_f64_pow2(c.y, ls);
     D.u[e] = x;
 }
 
-// Coarsest level, exact separable solve, one CTA per (problem, mode).  On a
-// uniform level A_m = I_z (x) K_m + T_z (x) diag(cz) with K_m the radial
-// tridiagonal operator (diagonal D0r + lambda_m mu) and T_z = tridiag(-1, tz_k, -1).
-// T_z = V Lambda V^T (V given), so for each axial eigenvector j the system is
+// Coarsest level, exact separable solve, one CTA per (problem, mode, real or
+// imaginary part).  On a uniform level A_m = I_z (x) K_m + T_z (x) diag(cz)
+// with K_m the radial tridiagonal operator (diagonal D0r + lambda_m mu) and
+// T_z = tridiag(-1, 2, -1) with 3 in both corners (Dirichlet faces at half a
+// cell).  T_z = V Lambda V^T with the DST-II basis V[k][j] = c_j
+// sin(pi (j+1)(k+1/2)/nz), so for each axial eigenvector j the system is
 // tridiagonal in r: (K_m + Lambda_j diag(cz)) w_j = (V^T b)_j, factorised at
-// plan time (Thomas: inverse pivots piv, multipliers cpr).  u = V w.
+// plan time (Thomas: inverse pivots piv, multipliers cpr), and u = V w.
+// The basis is mirror-symmetric, V[nz-1-k][j] = (-1)^j V[k][j], so both
+// transforms fold the axial index: with P_k = b_k + b_(nz-1-k) and
+// Q_k = b_k - b_(nz-1-k), (V^T b)_j sums V[k][j] P_k (even j) or V[k][j] Q_k
+// (odd j) over the first half only, and u_k, u_(nz-1-k) = E_k +- O_k with E, O
+// the sums over even and odd j -- half the FP64 multiply-adds of the plain
+// products.  Only rows k < ceil(nz/2) of V are read.
 template <class T>
 __global__ void __launch_bounds__(MG_THREADS) k_coarse(const CoarseTab<T> *__restrict__ tab) {
     extern __shared__ unsigned char smraw[];
@@ -333,57 +416,66 @@ __global__ void __launch_bounds__(MG_THREADS) k_coarse(const CoarseTab<T> *__res
     const LevelDev<T> L = tab->f[p];
     const CoarseDev<T> D = tab->c[p];
     const int nr = D.nr, nz = D.nz, nm = D.nm;
-    const int m = (int)(blockIdx.x - tab->start[p]);
-    V2<T> *bs = (V2<T> *)smraw;              // [nz][nr]
-    V2<T> *ws = bs + (size_t)nz * nr;        // [nz][nr]
-    T *Vs = (T *)(ws + (size_t)nz * nr);     // [nz][nz]
-    const int n = nr * nz;
-    for (int f = threadIdx.x; f < n; f += blockDim.x) bs[f] = L.b[(size_t)f * nm + m];
-    for (int f = threadIdx.x; f < nz * nz; f += blockDim.x) Vs[f] = D.V[f];
+    const int lb = (int)(blockIdx.x - tab->start[p]);
+    const int m = lb >> 1, comp = lb & 1;
+    const int h = nz >> 1, hz = nz - h;      // mirror pairs, rows with k <= nz-1-k
+    T *bs = (T *)smraw;                      // [nz][nr]: b, then P (rows < hz) and Q (row nz-1-k)
+    const int lw = nr + 1;                   // padded rows: the Thomas threads walk rows
+    T *ws = bs + (size_t)nz * nr;            // [nz][lw]
+    T *Vs = ws + (size_t)nz * lw;            // [hz][nz]
+    const T *bg = (const T *)L.b + comp;
+    for (int f = threadIdx.x; f < nz * nr; f += blockDim.x) bs[f] = bg[2 * ((size_t)f * nm + m)];
+    for (int f = threadIdx.x; f < hz * nz; f += blockDim.x) Vs[f] = D.V[f];
     __syncthreads();
-    // w[j][i] = sum_k V[k][j] b[k][i]
-    for (int f = threadIdx.x; f < n; f += blockDim.x) {
-        const int j = f / nr, i = f - j * nr;
-        T ax = 0, ay = 0;
-        for (int k = 0; k < nz; ++k) {
-            const T v = Vs[k * nz + j];
-            const V2<T> b = bs[k * nr + i];
-            ax = fma(v, b.x, ax);
-            ay = fma(v, b.y, ay);
-        }
-        ws[f] = mk<T>(ax, ay);
+    for (int f = threadIdx.x; f < h * nr; f += blockDim.x) {
+        const int k = f / nr, i = f - k * nr;
+        const T lo = bs[k * nr + i], hi = bs[(nz - 1 - k) * nr + i];
+        bs[k * nr + i] = lo + hi;
+        bs[(nz - 1 - k) * nr + i] = lo - hi;
     }
     __syncthreads();
-    // tridiagonal solves along r, one thread per (j, component)
-    for (int t = threadIdx.x; t < 2 * nz; t += blockDim.x) {
-        const int j = t >> 1, comp = t & 1;
+    // w[j][i] = sum_k V[k][j] b[k][i], folded
+    for (int f = threadIdx.x; f < nz * nr; f += blockDim.x) {
+        const int j = f / nr, i = f - j * nr;
+        T a = 0;
+        if ((j & 1) == 0) {
+            for (int k = 0; k < hz; ++k) a = fma(Vs[k * nz + j], bs[k * nr + i], a);
+        } else {
+            for (int k = 0; k < h; ++k) a = fma(Vs[k * nz + j], bs[(nz - 1 - k) * nr + i], a);
+        }
+        ws[j * lw + i] = a;
+    }
+    __syncthreads();
+    // tridiagonal solves along r, one thread per axial eigenvector j
+    for (int j = threadIdx.x; j < nz; j += blockDim.x) {
         const T *piv = D.piv + ((size_t)m * nz + j) * nr;
         const T *cpr = D.cpr + ((size_t)m * nz + j) * nr;
-        T *row = ((T *)(ws + (size_t)j * nr)) + comp;   // stride 2
+        T *row = ws + (size_t)j * lw;
         T y = row[0] * piv[0];
         row[0] = y;
         for (int i = 1; i < nr; ++i) {
-            y = (row[2 * i] - D.e[i - 1] * y) * piv[i];
-            row[2 * i] = y;
+            y = (row[i] - D.e[i - 1] * y) * piv[i];
+            row[i] = y;
         }
         T x = y;
         for (int i = nr - 2; i >= 0; --i) {
-            x = row[2 * i] - cpr[i] * x;
-            row[2 * i] = x;
+            x = row[i] - cpr[i] * x;
+            row[i] = x;
         }
     }
     __syncthreads();
-    // u[k][i] = sum_j V[k][j] w[j][i]
-    for (int f = threadIdx.x; f < n; f += blockDim.x) {
+    // u[k][i] = sum_j V[k][j] w[j][i] = E +- O for the mirror pair (k, nz-1-k)
+    T *ug = (T *)L.u + comp;
+    for (int f = threadIdx.x; f < hz * nr; f += blockDim.x) {
         const int k = f / nr, i = f - k * nr;
-        T ax = 0, ay = 0;
-        for (int j = 0; j < nz; ++j) {
-            const T v = Vs[k * nz + j];
-            const V2<T> w = ws[j * nr + i];
-            ax = fma(v, w.x, ax);
-            ay = fma(v, w.y, ay);
+        T e = 0, o = 0;
+        for (int j = 0; j + 1 < nz; j += 2) {
+            e = fma(Vs[k * nz + j], ws[j * lw + i], e);
+            o = fma(Vs[k * nz + j + 1], ws[(j + 1) * lw + i], o);
         }
-        L.u[(size_t)f * nm + m] = mk<T>(ax, ay);
+        if (nz & 1) e = fma(Vs[k * nz + nz - 1], ws[(nz - 1) * lw + i], e);
+        ug[2 * ((size_t)(k * nr + i) * nm + m)] = e + o;
+        if (nz - 1 - k != k) ug[2 * ((size_t)((nz - 1 - k) * nr + i) * nm + m)] = e - o;
     }
 }
 

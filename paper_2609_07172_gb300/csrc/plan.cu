@@ -374,6 +374,16 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
     H.g_prolong.assign(nl, 0);
     for (int l = 0; l < nl; ++l) {
         LaunchTab<T> ts{}, tr{}, tp{};
+        // smoother strip: enough rows per thread to amortise its index work
+        // while the launch still fills the GPU (~2 full waves of 152 SMs x
+        // 2048 threads before the strip grows)
+        double updates = 0;
+        for (int p = 0; p < P.n; ++p) {
+            const ProblemPlan &q = P.pr[p];
+            if (l < q.L - 1) updates += (double)views(q)[l].nz * (views(q)[l].nr / 2) * views(q)[l].nm;
+        }
+        int strip = 1;
+        while (strip < 8 && updates / (2.0 * strip) >= 2.0 * 152 * 2048) strip <<= 1;
         for (int p = 0; p < P.n; ++p) {
             const ProblemPlan &q = P.pr[p];
             if (l >= q.L - 1) continue;
@@ -383,7 +393,8 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
             const size_t half = (size_t)f.nz * (f.nr / 2) * f.nm, full = (size_t)f.nz * f.nr * f.nm;
             const size_t coarse_n = (size_t)v[l + 1].nz * v[l + 1].nr * f.nm;
             ts.f[ts.n] = f;
-            ts.start[ts.n + 1] = ts.start[ts.n] + mg_blocks(half, P.shared.smooth_threads);
+            ts.f[ts.n].strip = strip;
+            ts.start[ts.n + 1] = ts.start[ts.n] + smooth_blocks(f.nr, f.nz, f.nm, strip, P.shared.smooth_threads);
             ++ts.n;
             tr.f[tr.n] = f;
             tr.c[tr.n] = v[l + 1];
@@ -411,8 +422,9 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
         const CoarseDev<T> &cd = coarse(q);
         tc.f[tc.n] = views(q)[q.L - 1];
         tc.c[tc.n] = cd;
-        tc.start[tc.n + 1] = tc.start[tc.n] + (unsigned)q.nm;
-        tc.smem = std::max(tc.smem, (size_t)2 * cd.nr * cd.nz * sizeof(V2<T>) + (size_t)cd.nz * cd.nz * sizeof(T));
+        tc.start[tc.n + 1] = tc.start[tc.n] + 2u * (unsigned)q.nm;   // (mode, real / imaginary part)
+        tc.smem = std::max(tc.smem, ((size_t)cd.nr * cd.nz + (size_t)(cd.nr + 1) * cd.nz +
+                                     (size_t)(cd.nz - cd.nz / 2) * cd.nz) * sizeof(T));
         ++tc.n;
     }
     H.g_coarse = tc.start[tc.n];
@@ -443,15 +455,19 @@ int upload(pic_poisson_plan_s &P) {
         }
         const int nt = q.d.ntheta, M = nt / 2;
         std::vector<double> tw(2 * std::max(M / 2, 1), 0.0), tw2(2 * (M + 1), 0.0);
-        for (int t = 0; t < M / 2; ++t) {
-            tw[2 * t] = std::cos(2.0 * kPi * t / M);
-            tw[2 * t + 1] = -std::sin(2.0 * kPi * t / M);
-        }
+        auto scale_ratio = [](double *out, int t, int n) {   // e^{-2 pi i t / n} as (a, b)
+            const double c = std::cos(2.0 * kPi * t / n), sn = std::sin(2.0 * kPi * t / n);
+            if (tw_first_form(t, n)) {
+                out[0] = c;
+                out[1] = -sn / c;
+            } else {
+                out[0] = -sn;
+                out[1] = -c / sn;
+            }
+        };
+        for (int t = 0; t < M / 2; ++t) scale_ratio(&tw[2 * t], t, M);
         if (M / 2 == 0) tw[0] = 1.0;
-        for (int m = 0; m <= M; ++m) {
-            tw2[2 * m] = std::cos(2.0 * kPi * m / nt);
-            tw2[2 * m + 1] = -std::sin(2.0 * kPi * m / nt);
-        }
+        for (int m = 0; m <= M; ++m) scale_ratio(&tw2[2 * m], m, nt);
         to_dev(tw, q.tw, st, err);
         to_dev(tw2, q.tw2, st, err);
         // level-0 right-hand-side factors: s_i (Eq. mode_rhs) and b^D (Eq. boundary_rhs_appendix)

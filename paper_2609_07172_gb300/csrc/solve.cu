@@ -88,7 +88,7 @@ double coarse_entries(const pic_poisson_plan_s &P, double *flops_per) {
         const LevelHost &h = q.lv[q.L - 1];
         const double e = (double)h.nr * h.nz * q.nm;
         n += e;
-        f += e * (16.0 * h.nz + 20.0);
+        f += e * (4.0 * h.nz + 12.0);   // folded axial transforms (2 nz FMA) + Thomas, two parts
     }
     *flops_per = f;
     return n;
