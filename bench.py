@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--tune-cache", default=None, help="JSON file caching autotuner results")
     ap.add_argument("--learned", action="store_true", help="train and evaluate the learned warm start (~2 min)")
     ap.add_argument("--no-tune", action="store_true", help="default schedule instead of the autotuner's")
+    ap.add_argument("--schedule", default=None,
+                    help='JSON of Plan settings used instead of the autotuner\'s for every form, e.g. '
+                         '\'{"smooth_strip": 2, "omega": 1.2}\'')
     ap.add_argument("--learned-steps", type=int, default=200, help="evaluation steps of the learned warm start")
     ap.add_argument("--learned-epochs", type=int, default=8)
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NR", "NTHETA", "NZ"), default=None,
@@ -195,6 +198,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(value, world, dist, device):
+    """The largest of the ranks' values (each rank's own when world == 1)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_solve(ms_total_max, steps, world):
+    """Whole-job time per solve: `world` replicas each solved `steps` problems
+    in at most `ms_total_max` (the slowest rank's time)."""
+    return ms_total_max / (steps * world)
+
+
 # ------------------------------------------------------------------ GPU arm
 def time_form(plan, rhos, phi, steps, warmup, tol, world, dist, sampler=None):
     """Warm up, then time `steps` solves on the plan's stream; returns (ms total, infos, clocks)."""
@@ -287,24 +307,24 @@ def run_ours(args):
     # schedule (sweeps, FP32 inner cycles, smoother block size) picked by the
     # autotuner on this problem, outside the timed region (cached with --tune-cache)
     def tuned_kw(precision):
+        if args.schedule:
+            return json.loads(args.schedule), None
         if args.no_tune:
             return {}, None
         from paper_2609_07172_gb300 import autotune
         t = autotune([p], [rhos[0]], tol=args.tol, precision=precision, graph=True, repeats=2,
                      cache=args.tune_cache)
-        return {k: t[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads")}, t
+        return {k: t[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads", "smooth_strip",
+                                  "omega") if k in t}, t
 
     kw, tuned = tuned_kw(prec)
     # headline: each solve one CUDA graph (device-side convergence loop)
     plan = Plan(p, precision=prec, graph=True, **kw)
     ms_total, infos, clocks = time_form(plan, rhos, phi, args.steps, args.warmup, args.tol, world, dist,
                                         ClockSampler(local))
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world, dist, dev)
     ms_local = ms_total / args.steps
-    ms_per_solve = ms_total / (args.steps * world)
+    ms_per_solve = job_ms_per_solve(ms_total, args.steps, world)
     cycles = [i["cycles"] for i in infos]
     by = sum_phase(infos, "bytes_phase")
     solve_gbs = sum(by.values()) / len(infos) / (ms_local * 1e-3) / 1e9
@@ -317,7 +337,8 @@ def run_ours(args):
     # DRAM bytes of a level-0 half-sweep at 512x128x400 (ncu, scaled from 512x128x200 where valid)
     traffic = traffic_from_profile("smooth_%s_512x128x200.md" % args.precision) if tag == "512x128x400" else None
     sched = {"pre_sweeps": kw.get("pre_sweeps", 2), "post_sweeps": kw.get("post_sweeps", 2),
-             "inner_cycles": kw.get("inner_cycles", 2), "smooth_threads": kw.get("smooth_threads", 256)}
+             "inner_cycles": kw.get("inner_cycles", 2), "smooth_threads": kw.get("smooth_threads", 256),
+             "smooth_strip": kw.get("smooth_strip", 0), "omega": kw.get("omega", 1.0)}
 
     line = {"metric": METRIC, "value": ms_per_solve, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_local, "higher_is_better": False, "scaling": "weak",
@@ -358,11 +379,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for k in range(ne):
             plan.solve_host(rho_h[k % len(rho_h)], phi_h, tol=args.tol)
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / ne
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item()) / world
+        e2e_ms = job_ms_per_solve(max_over_ranks((time.perf_counter() - t0) * 1e3, world, dist, dev), ne, world)
         nbytes = p.nr * p.ntheta * p.nz * 8
         line["e2e"] = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                        "steps": ne, "api": "pic_poisson_solve_host (pinned host buffers)"}
@@ -430,7 +447,8 @@ def run_batch(args, dev):
     problems = [p for p, _ in probs]
     rhos = [torch.from_numpy(W.rho_plasma(p, s)).to(dev) for p, s in probs]
     tuned = autotune(problems, rhos, tol=args.tol, precision=FP64, graph=True, repeats=2, cache=args.tune_cache)
-    kw = {k: tuned[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads")}
+    kw = {k: tuned[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads", "smooth_strip",
+                                "omega") if k in tuned}
     bp = BatchPlan(problems, graph=True, **kw)
     phis = [torch.empty_like(r) for r in rhos]
     for _ in range(2):

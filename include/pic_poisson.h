@@ -97,6 +97,10 @@ typedef struct {
     int post_sweeps;           /* red-black sweeps after prolongation; < 0 selects 2 */
     int inner_cycles;          /* mixed precision: FP32 V-cycles per FP64 defect correction; <= 0 selects 2 */
     int smooth_threads;        /* threads per block of the smoother: 64, 128, 256 or 512; <= 0 selects 256 */
+    int smooth_strip;          /* smoother work per thread: <= 0 one entry; 1, 2 or 4: that many rows of one
+                                  parity at one (radial cell, mode), loads of the strip issued together */
+    double omega;              /* over-relaxation of the red-black smoother, u <- u + omega (u_GS - u),
+                                  0 < omega < 2; <= 0 selects 1 (plain Gauss-Seidel) */
     unsigned flags;            /* PIC_POISSON_* flags */
 } pic_poisson_desc;
 
@@ -120,11 +124,15 @@ typedef struct {
     int pre_sweeps, post_sweeps;           /* best smoothing schedule */
     int inner_cycles;                      /* best FP32 V-cycles per defect correction (mixed) */
     int smooth_threads;                    /* best smoother block size */
+    int smooth_strip;                      /* best smoother strip (0: one entry per thread) */
+    double omega;                          /* best over-relaxation factor */
     double ms;                             /* its median wall time per solve call */
     int tried;                             /* candidates timed (entries below) */
     double ms_tried[PIC_POISSON_MAX_TUNE];
     int pre_tried[PIC_POISSON_MAX_TUNE], post_tried[PIC_POISSON_MAX_TUNE];
     int inner_tried[PIC_POISSON_MAX_TUNE], threads_tried[PIC_POISSON_MAX_TUNE];
+    int strip_tried[PIC_POISSON_MAX_TUNE];
+    double omega_tried[PIC_POISSON_MAX_TUNE];
 } pic_poisson_tuning;
 
 typedef struct {
@@ -202,12 +210,16 @@ int pic_poisson_solve_batch(pic_poisson_plan_t plan, const double *const *rho_de
                             double tol, pic_poisson_info *infos);
 
 /*
- * Autotuner: choose pre/post sweeps, inner_cycles (mixed precision) and
- * smooth_threads for the problems `descs` (as for pic_poisson_plan_batch) by
- * timing complete solves of rho_dev[p] -> phi_dev[p] to `tol` (> 0).  Stage 1
- * times the schedules (1,1) (2,1) (1,2) (2,2) (3,2) (2,3) (3,3), and for mixed
- * precision 1 to 4 inner cycles each, at 256 threads; stage 2 times 64, 128
- * and 512 threads for the winner.  Each candidate builds its own plan, runs
+ * Autotuner: choose pre/post sweeps, inner_cycles (mixed precision),
+ * smooth_threads and smooth_strip for the problems `descs` (as for
+ * pic_poisson_plan_batch) by timing complete solves of rho_dev[p] -> phi_dev[p]
+ * to `tol` (> 0).  Stage 1 times the schedules (1,1) (2,1) (1,2) (2,2) (3,2)
+ * (2,3) (3,3), and for mixed precision 1 to 4 inner cycles each, at 256
+ * threads and one entry per thread; stage 2 times 64, 128 and 512 threads for
+ * the winner; stage 3 strips of 2 and 4 rows at the best block size; stage 4
+ * over-relaxation omega = 1.1, 1.2, 1.3 with the schedules (1,1), (1,2),
+ * (2,1), (2,2) at the best block size, strip and inner cycles.  Each
+ * candidate builds its own plan, runs
  * one untimed solve and `repeats` (1..16) timed ones; the score is the median
  * wall time of the solve call.  Results in *out; phi_dev is overwritten.
  * This is a project addition for choosing kernel schedules; the paper does

@@ -48,7 +48,8 @@ class Desc(ctypes.Structure):
         ("eps0", ctypes.c_double),
         ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
         ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int),
-        ("inner_cycles", ctypes.c_int), ("smooth_threads", ctypes.c_int), ("flags", ctypes.c_uint),
+        ("inner_cycles", ctypes.c_int), ("smooth_threads", ctypes.c_int), ("smooth_strip", ctypes.c_int),
+        ("omega", ctypes.c_double), ("flags", ctypes.c_uint),
     ]
 
 
@@ -78,10 +79,11 @@ MAX_TUNE = 64
 class Tuning(ctypes.Structure):
     _fields_ = [
         ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-        ("smooth_threads", ctypes.c_int), ("ms", ctypes.c_double), ("tried", ctypes.c_int),
-        ("ms_tried", ctypes.c_double * MAX_TUNE), ("pre_tried", ctypes.c_int * MAX_TUNE),
-        ("post_tried", ctypes.c_int * MAX_TUNE), ("inner_tried", ctypes.c_int * MAX_TUNE),
-        ("threads_tried", ctypes.c_int * MAX_TUNE),
+        ("smooth_threads", ctypes.c_int), ("smooth_strip", ctypes.c_int), ("omega", ctypes.c_double),
+        ("ms", ctypes.c_double), ("tried", ctypes.c_int), ("ms_tried", ctypes.c_double * MAX_TUNE),
+        ("pre_tried", ctypes.c_int * MAX_TUNE), ("post_tried", ctypes.c_int * MAX_TUNE),
+        ("inner_tried", ctypes.c_int * MAX_TUNE), ("threads_tried", ctypes.c_int * MAX_TUNE),
+        ("strip_tried", ctypes.c_int * MAX_TUNE), ("omega_tried", ctypes.c_double * MAX_TUNE),
     ]
 
 
@@ -155,7 +157,7 @@ def _check(status, allow=(OK,)):
 
 
 def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1, flags=0, inner_cycles=0,
-              smooth_threads=0):
+              smooth_threads=0, smooth_strip=0, omega=0.0):
     """Descriptor for a workloads.Problem; returns (Desc, keep-alive buffers)."""
     keep = []
     d = Desc()
@@ -177,6 +179,8 @@ def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=
     d.post_sweeps = post_sweeps
     d.inner_cycles = inner_cycles
     d.smooth_threads = smooth_threads
+    d.smooth_strip = smooth_strip
+    d.omega = omega
     d.flags = flags
     return d, keep
 
@@ -220,13 +224,13 @@ class Plan:
 
     def __init__(self, problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
                  profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False,
-                 smooth_threads=0):
+                 smooth_threads=0, smooth_strip=0, omega=0.0):
         import torch
         self.problem = problem
         flags = ((PROFILE if profile else 0) | (USE_INITIAL_GUESS if initial_guess else 0)
                  | (GRAPH if graph else 0))
         self._desc, self._keep = make_desc(problem, precision, max_cycles, pre_sweeps, post_sweeps, flags,
-                                           inner_cycles, smooth_threads)
+                                           inner_cycles, smooth_threads, smooth_strip, omega)
         self.stream = torch.cuda.current_stream() if stream is None else stream
         self._plan = ctypes.c_void_p()
         _check(load().pic_poisson_plan(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
@@ -342,7 +346,7 @@ class BatchPlan:
 
     def __init__(self, problems, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
                  profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False,
-                 smooth_threads=0):
+                 smooth_threads=0, smooth_strip=0, omega=0.0):
         import torch
         self.problems = list(problems)
         n = len(self.problems)
@@ -354,7 +358,7 @@ class BatchPlan:
         self._keep = []
         for i, p in enumerate(self.problems):
             d, keep = make_desc(p, precision, max_cycles, pre_sweeps, post_sweeps, flags, inner_cycles,
-                                smooth_threads)
+                                smooth_threads, smooth_strip, omega)
             self._descs[i] = d
             self._keep.extend(keep)
         self.stream = torch.cuda.current_stream() if stream is None else stream
@@ -426,9 +430,11 @@ def autotune(problems, rhos, tol=1e-10, precision=FP64, graph=False, repeats=3, 
     _check(load().pic_poisson_autotune(descs, n, rp, fp, float(tol), ctypes.c_void_p(st), int(repeats),
                                        ctypes.byref(out)))
     best = {"pre_sweeps": out.pre_sweeps, "post_sweeps": out.post_sweeps, "inner_cycles": out.inner_cycles,
-            "smooth_threads": out.smooth_threads}
+            "smooth_threads": out.smooth_threads, "smooth_strip": out.smooth_strip, "omega": out.omega}
     tried = [{"pre": out.pre_tried[i], "post": out.post_tried[i], "inner": out.inner_tried[i],
-              "threads": out.threads_tried[i], "ms": out.ms_tried[i]} for i in range(out.tried)]
+              "threads": out.threads_tried[i], "strip": out.strip_tried[i], "omega": out.omega_tried[i],
+              "ms": out.ms_tried[i]}
+             for i in range(out.tried)]
     if cache:
         table = {}
         if os.path.exists(cache):

@@ -19,10 +19,12 @@
 //
 // FP64 runs at 1/64 of the FP32 rate on this GPU, so the transforms are bound
 // by FP64 instructions and are written to issue few of them:
-//  * a butterfly top +- w bot with w = a (1 + i b) (or a (b + i)) costs six
-//    multiply-adds: u = bot + i b bot (two), top +- a u (four) -- instead of a
-//    four-operation complex product and four additions;
-//  * twiddles 1 and -i (+i inverse) need additions only;
+//  * a butterfly top +- w bot with w = rho a (1 + i b) (see tw_rot) costs six
+//    multiply-adds: u = bot + i b bot (two), top +- a rho u (four) -- instead
+//    of a four-operation complex product and four additions; rho is applied
+//    with integer instructions, so no FP64 instruction depends on a branch;
+//  * the first stages, whose twiddles are 1 and -i (+i inverse), are
+//    additions only;
 //  * each thread applies two consecutive radix-2 stages to four values held
 //    in registers, halving the shared-memory round trips and barriers;
 //  * the unpack (pack) of the real transform treats modes m and M - m
@@ -49,55 +51,71 @@ __device__ __forceinline__ int find_problem(const unsigned *__restrict__ start, 
     return lo;
 }
 
-// u with w z = a u for the twiddle entry (a, b) of e^{-2 pi i t / n}
-// (INVERSE: of its conjugate).  first: the entry's form (tw_first_form).
+// -x when c (sign bit flipped with an integer instruction).
+__device__ __forceinline__ double flip_if(double x, bool c) {
+    return __hiloint2double(__double2hiint(x) ^ (c ? (int)0x80000000 : 0), __double2loint(x));
+}
+
+// v with w z = a v for the twiddle entry ab = (a, b) of w (INVERSE: of
+// conj w); rot: the entry's rotation flag (tw_rot).
 template <bool INVERSE>
-__device__ __forceinline__ double2 tw_reduce(double b, bool first, double2 z) {
-    if (first) {   // w = a (1 + i b)
-        return INVERSE ? make_double2(fma(b, z.y, z.x), fma(-b, z.x, z.y))
-                       : make_double2(fma(-b, z.y, z.x), fma(b, z.x, z.y));
-    }
-    // w = a (b + i)
-    return INVERSE ? make_double2(fma(b, z.x, z.y), fma(b, z.y, -z.x)) : make_double2(fma(b, z.x, -z.y), fma(b, z.y, z.x));
+__device__ __forceinline__ double2 tw_v(double2 ab, bool rot, double2 z) {
+    const double b = INVERSE ? -ab.y : ab.y;
+    const double ux = fma(-b, z.y, z.x), uy = fma(b, z.x, z.y);   // u = z + i b z
+    // rho u with rho = -i (forward) or +i (inverse) when rot, 1 otherwise
+    const double vx = rot ? uy : ux, vy = rot ? ux : uy;
+    return make_double2(flip_if(vx, rot && INVERSE), flip_if(vy, rot && !INVERSE));
 }
 
 // Radix-2 butterfly (top, bot) <- (top + w bot, top - w bot), w = e^{-+2 pi i t / M}.
 template <bool INVERSE>
 __device__ __forceinline__ void bfly(double2 &top, double2 &bot, int t, int M, const double2 *__restrict__ tw) {
-    if (t == 0) {
-        const double2 x = top;
-        top = make_double2(x.x + bot.x, x.y + bot.y);
-        bot = make_double2(x.x - bot.x, x.y - bot.y);
-    } else if (4 * t == M) {   // w = -i (+i inverse)
-        const double2 x = top, y = INVERSE ? make_double2(-bot.y, bot.x) : make_double2(bot.y, -bot.x);
-        top = make_double2(x.x + y.x, x.y + y.y);
-        bot = make_double2(x.x - y.x, x.y - y.y);
-    } else {
-        const double2 ab = tw[t];
-        const double2 u = tw_reduce<INVERSE>(ab.y, tw_first_form(t, M), bot);
-        const double2 x = top;
-        top = make_double2(fma(ab.x, u.x, x.x), fma(ab.x, u.y, x.y));
-        bot = make_double2(fma(-ab.x, u.x, x.x), fma(-ab.x, u.y, x.y));
-    }
+    const double2 ab = tw[t];
+    const double2 v = tw_v<INVERSE>(ab, tw_rot(t, M), bot);
+    const double2 x = top;
+    top = make_double2(fma(ab.x, v.x, x.x), fma(ab.x, v.y, x.y));
+    bot = make_double2(fma(-ab.x, v.x, x.x), fma(-ab.x, v.y, x.y));
+}
+
+__device__ __forceinline__ void add_sub(double2 &a, double2 &b) {
+    const double2 x = a;
+    a = make_double2(x.x + b.x, x.y + b.y);
+    b = make_double2(x.x - b.x, x.y - b.y);
 }
 
 // In-place radix-2 DIT FFT of length M on buf[M][LD] (bit-reversed input),
-// two stages (h, 2h) per pass on four values per thread, a single first
-// stage when log2 M is odd.  INVERSE: conjugated twiddles.
+// two stages (h, 2h) per pass on four values per thread.  The first pass
+// (or the first single stage when log2 M is odd) has twiddles 1 and -i only
+// and is done with additions.  INVERSE: conjugated twiddles.
 template <bool INVERSE>
 __device__ __forceinline__ void fft_stages(double2 *buf, const double2 *__restrict__ tw, int M, int log2M, int lane,
                                            int warp, int nw) {
-    int h = 1;
-    if (log2M & 1) {   // stage h = 1: twiddle 1 only
+    int h;
+    if (log2M & 1) {   // single stage h = 1
         for (int q = warp; q < (M >> 1); q += nw) {
             double2 a = buf[(2 * q) * LD + lane], b = buf[(2 * q + 1) * LD + lane];
-            bfly<INVERSE>(a, b, 0, M, tw);
+            add_sub(a, b);
             buf[(2 * q) * LD + lane] = a;
             buf[(2 * q + 1) * LD + lane] = b;
         }
-        __syncthreads();
         h = 2;
+    } else {           // stages 1 and 2: four-point DFTs
+        for (int q = warp; q < (M >> 2); q += nw) {
+            double2 *x = buf + 4 * q * LD + lane;
+            double2 a0 = x[0], a1 = x[LD], a2 = x[2 * LD], a3 = x[3 * LD];
+            add_sub(a0, a1);
+            add_sub(a2, a3);
+            add_sub(a0, a2);
+            a3 = INVERSE ? make_double2(-a3.y, a3.x) : make_double2(a3.y, -a3.x);   // w = -i (+i)
+            add_sub(a1, a3);
+            x[0] = a0;
+            x[LD] = a1;
+            x[2 * LD] = a2;
+            x[3 * LD] = a3;
+        }
+        h = 4;
     }
+    __syncthreads();
     for (; 4 * h <= M; h <<= 2) {
         for (int q = warp; q < (M >> 2); q += nw) {
             const int p = q & (h - 1);
@@ -167,34 +185,37 @@ __global__ void __launch_bounds__(FFT_THREADS) k_forward(const FFTTab *__restric
     //   X_m = hs (S - i T),  X_{M-m} = hs conj(S + i T);
     // X_0 = 2 hs (Re Z_0 + Im Z_0), X_M = 2 hs (Re Z_0 - Im Z_0), both exactly real.
     const double2 *tw2 = (const double2 *)P.tw2;
-    const double hs = (P.s ? P.s[valid ? i : 0] : 1.0) * (0.5 / (double)nt);
+    const double hs = (P.s ? P.s[valid ? i : 0] : 1.0) * P.half_inv_n;
     double acc_in = 0.0, acc_edge = 0.0;   // Parseval weight 2 (0 < m < M) and 1 (m = 0, M)
     double2 *ob = outb + lane * nm;
-    for (int m = warp; 2 * m <= M; m += nw) {
-        if (m == 0) {
-            const double2 z = buf[lane];
-            double x0 = (z.x + z.y) * (2.0 * hs);
-            const double xM = (z.x - z.y) * (2.0 * hs);
-            if (P.bD && valid) x0 += P.bD[(size_t)k * nr + i];
-            acc_edge = fma(x0, x0, fma(xM, xM, acc_edge));
-            ob[0] = make_double2(x0, 0.0);
-            ob[M] = make_double2(xM, 0.0);
-            continue;
-        }
+    for (int m = 1 + warp; 2 * m < M; m += nw) {
         const double2 A = buf[m * LD + lane], B = buf[(M - m) * LD + lane];
         const double2 S = make_double2(hs * (A.x + B.x), hs * (A.y - B.y));
         const double2 D = make_double2(A.x - B.x, A.y + B.y);
         const double2 ab = tw2[m];
-        const double2 u = tw_reduce<false>(ab.y, tw_first_form(m, nt), D);   // T = ab.x u
+        const double2 v = tw_v<false>(ab, tw_rot(m, nt), D);   // T = ab.x v
         const double g = hs * ab.x;
-        const double2 xm = make_double2(fma(g, u.y, S.x), fma(-g, u.x, S.y));
-        const double2 xp = make_double2(fma(-g, u.y, S.x), -fma(g, u.x, S.y));
+        const double2 xm = make_double2(fma(g, v.y, S.x), fma(-g, v.x, S.y));
+        const double2 xp = make_double2(fma(-g, v.y, S.x), -fma(g, v.x, S.y));
         ob[m] = xm;
+        ob[M - m] = xp;
         acc_in = fma(xm.x, xm.x, fma(xm.y, xm.y, acc_in));
-        if (2 * m != M) {
-            ob[M - m] = xp;
-            acc_in = fma(xp.x, xp.x, fma(xp.y, xp.y, acc_in));
-        }
+        acc_in = fma(xp.x, xp.x, fma(xp.y, xp.y, acc_in));
+    }
+    if (warp == 0) {
+        const double2 z = buf[lane];
+        double x0 = (z.x + z.y) * (2.0 * hs);
+        const double xM = (z.x - z.y) * (2.0 * hs);
+        if (P.bD && valid) x0 += P.bD[(size_t)k * nr + i];
+        acc_edge = fma(x0, x0, fma(xM, xM, acc_edge));
+        ob[0] = make_double2(x0, 0.0);
+        ob[M] = make_double2(xM, 0.0);
+    }
+    if (M >= 2 && warp == nw - 1) {   // m = M/2 pairs with itself: X = 2 hs conj Z
+        const double2 z = buf[(M >> 1) * LD + lane];
+        const double2 x = make_double2((2.0 * hs) * z.x, -(2.0 * hs) * z.y);
+        ob[M >> 1] = x;
+        acc_in = fma(x.x, x.x, fma(x.y, x.y, acc_in));
     }
     __syncthreads();
     const int ncols = min(TI, nr - i0);
@@ -246,20 +267,22 @@ __global__ void __launch_bounds__(FFT_THREADS) k_inverse(const FFTTab *__restric
     // X_0 and X_M enter through their real parts only: Z_0 = (X_0 + X_M) + i (X_0 - X_M).
     const double2 *tw2 = (const double2 *)P.tw2;
     const double2 *ib = inb + lane * nm;
-    for (int m = warp; 2 * m <= M; m += nw) {
-        if (m == 0) {
-            const double a = ib[0].x, b = ib[M].x;
-            buf[lane] = make_double2(a + b, a - b);
-            continue;
-        }
+    for (int m = 1 + warp; 2 * m < M; m += nw) {
         const double2 A = ib[m], B = ib[M - m];
         const double2 S = make_double2(A.x + B.x, A.y - B.y);
         const double2 D = make_double2(A.x - B.x, A.y + B.y);
         const double2 ab = tw2[m];
-        const double2 u = tw_reduce<true>(ab.y, tw_first_form(m, nt), D);   // T = ab.x u
-        buf[bitrev(m, P.log2M) * LD + lane] = make_double2(fma(-ab.x, u.y, S.x), fma(ab.x, u.x, S.y));
-        if (2 * m != M)
-            buf[bitrev(M - m, P.log2M) * LD + lane] = make_double2(fma(ab.x, u.y, S.x), fma(ab.x, u.x, -S.y));
+        const double2 v = tw_v<true>(ab, tw_rot(m, nt), D);   // T = ab.x v
+        buf[bitrev(m, P.log2M) * LD + lane] = make_double2(fma(-ab.x, v.y, S.x), fma(ab.x, v.x, S.y));
+        buf[bitrev(M - m, P.log2M) * LD + lane] = make_double2(fma(ab.x, v.y, S.x), fma(ab.x, v.x, -S.y));
+    }
+    if (warp == 0) {
+        const double a = ib[0].x, b = ib[M].x;
+        buf[lane] = make_double2(a + b, a - b);
+    }
+    if (M >= 2 && warp == nw - 1) {   // m = M/2 pairs with itself: Z = 2 conj X
+        const double2 x = ib[M >> 1];
+        buf[bitrev(M >> 1, P.log2M) * LD + lane] = make_double2(x.x + x.x, -(x.y + x.y));
     }
     __syncthreads();
     fft_stages<true>(buf, (const double2 *)P.tw, M, P.log2M, lane, warp, nw);

@@ -57,10 +57,11 @@ template <class T> struct LevelDev {
     int nr, nz, nm, ncls;
     int nt;                       // azimuthal cells (Parseval weights of the norms)
     int init;                     // what a restriction into the next level writes (see launch_residual_restrict)
-    int strip;                    // smoother: rows of one parity updated per thread (1, 2, 4 or 8)
+    int strip;                    // smoother: rows of one parity updated per thread (1, 2 or 4; 0: one entry)
+    T relax;                      // 1 - omega (over-relaxed smoother; the h tables and invd carry omega)
     const T *cw, *ce, *cz;        // [nr]
-    const T *invd, *diag;         // [ncls][nr][nm]
-    const T *hw, *he, *hz;        // [ncls][nr][nm] off-diagonal conductances / diag
+    const T *invd, *diag;         // [ncls][nr][nm]: omega / diag, diag
+    const T *hw, *he, *hz;        // [ncls][nr][nm] omega * off-diagonal conductances / diag
     V2<T> *u;                     // iterate / correction, [nz][nr][nm]
     V2<T> *b;                     // right-hand side, [nz][nr][nm]
     V2<T> *bh;                    // right-hand side / diag, [nz][nr][nm]
@@ -104,7 +105,8 @@ struct DefectTab {                // mixed precision: FP64 level 0 and FP32 leve
 struct FFTProb {
     int nr, nt, nz, nm, ncls, log2M;
     const double *tw;             // [max(M/2,1)] e^{-2 pi i t / M}, M = nt / 2, as (scale, ratio) pairs
-    const double *tw2;            // [M+1] e^{-2 pi i m / nt}, same form (see tw_first_form)
+    const double *tw2;            // [M+1] e^{-2 pi i m / nt}, same form (see tw_rot)
+    double half_inv_n;            // 1 / (2 nt)
     const double *s;              // [nr] s_i (Eq. mode_rhs); null: plain 1/N transform
     const double *bD;             // [nz][nr] Dirichlet right-hand side; may be null
     const double *invd;           // level-0 inverse diagonal [ncls][nr][nm]; null: no b_hat
@@ -158,8 +160,10 @@ cudaError_t launch_copy_guess(const FFTTab *tab, unsigned grid, cudaStream_t st)
 
 // threads: block size of the smoother (64, 128, 256 or 512; the table's block
 // ranges must have been computed with the same size).
+// strip: see pic_poisson_desc.smooth_strip; sor: over-relaxed update (omega != 1).
 template <class T>
-cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, int threads, cudaStream_t st);
+cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, int threads, int strip, bool sor,
+                          cudaStream_t st);
 // red_only: residual of the red fine cells only (valid right after a black half-sweep).
 // Per problem, f.init selects what is written into the coarse level c: 0 = b only
 // (coarsest, solved directly); 1 = also b_hat and u = 0; 2 = also b_hat and
@@ -178,7 +182,9 @@ cudaError_t launch_prolong(const LaunchTab<T> *tab, unsigned grid, bool black_on
 template <class T>
 cudaError_t launch_coarse(const CoarseTab<T> *tab, unsigned grid, size_t smem, cudaStream_t st);
 
-cudaError_t launch_defect(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, double *partials, cudaStream_t st);
+// zero_x: the FP64 iterate is zero (r = b; the kernel also writes x = 0).
+cudaError_t launch_defect(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, double *partials, bool zero_x,
+                          cudaStream_t st);
 cudaError_t launch_update(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, cudaStream_t st);
 
 // Sums of the forward transform's partials per problem -> ctrl->bnorm2; initial
@@ -212,11 +218,13 @@ constexpr int FFT_TI = 32;        // radial columns per transform CTA
 constexpr int FFT_THREADS = 256;
 size_t fft_smem_bytes(int nt);
 
-// Twiddle tables of the transforms hold e^{-2 pi i t / n} = c - i s as a
-// scale and a ratio, w = a (1 + i b) when |c| >= |s| (a = c, b = -s / c) and
-// w = a (b + i) otherwise (a = -s, b = -c / s), so that a complex product
-// w z costs two multiply-adds plus the scale, which folds into the butterfly's
-// own multiply-adds.  This picks the first form (|b| <= 1 either way).
-__host__ __device__ inline bool tw_first_form(int t, int n) { return 8 * t <= n || 8 * t >= 3 * n; }
+// Twiddle tables of the transforms hold w = e^{-i theta}, theta = 2 pi t / n,
+// as a scale and a ratio: w = rho a (1 + i b) with a = cos theta', b =
+// -tan theta', theta' = theta - rot pi/2 and rho = (-i)^rot, where rot = 1
+// for theta in (pi/4, 3 pi/4) keeps |b| <= 1.  A complex product w z then
+// costs two multiply-adds, u = z + i b z, plus the scale a, which folds into
+// the butterfly's own multiply-adds; the factor rho is a swap of the parts
+// of u and a sign, done with integer instructions.
+__host__ __device__ inline bool tw_rot(int t, int n) { return !(8 * t <= n || 8 * t >= 3 * n); }
 
 }  // namespace pp

@@ -104,56 +104,98 @@ __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i,
 //   u_q <- (b_q + sum_q' G_qq' u_q') / (D0_q + lambda_m mu_q)
 // written as u = b_hat + h_z (u_S + u_N) + h_w u_W + h_e u_E with h = G / diag.
 // Cells of one colour in rows of one parity share their radial index, so a
-// thread owns one (radial cell, mode) and walks a strip of L.strip rows of
-// that parity (k, k+2, ...): the north neighbour of row k is the south
-// neighbour of row k+2 and stays in a register, the interior rows share one
-// set of coefficients, and the index arithmetic is done once per strip.
-// Consecutive threads take consecutive modes of a cell, so every load and
-// store of a warp is contiguous.  Blocks: per parity, strips of rows; per
-// strip, ceil((nr/2) nm / NT) blocks (smooth_blocks).
-template <class T, int NT>
+// thread owns one (radial cell, mode) and updates a strip of S rows of that
+// parity (k, k+2, ...): the north neighbour of row k is the south neighbour
+// of row k+2, the interior rows share one set of coefficients, and the index
+// arithmetic is done once per strip.  All loads of the strip are issued before
+// its first store -- the launch reads only the other colour and b_hat, which
+// it does not write -- so they are in flight together.  Consecutive threads
+// take consecutive modes of a cell: every load and store of a warp is
+// contiguous.  Blocks: per parity, strips of rows; per strip,
+// ceil((nr/2) nm / NT) blocks (smooth_blocks).
+// S = 0: one entry per thread, consecutive threads over the cells of one
+// colour in cell-major, mode-fast order (blocks: mg_blocks of the entries).
+// SOR: over-relaxation u <- (1 - omega) u + omega u_GS, the tables carrying
+// omega (one more load and multiply-add per component); otherwise omega = 1.
+template <class T, int NT, int S, bool SOR>
 __global__ void __launch_bounds__(NT) k_smooth(const LaunchTab<T> *__restrict__ tab, int color) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     const LevelDev<T> L = tab->f[p];
     const unsigned nm = L.nm;
-    const unsigned w = (unsigned)(L.nr >> 1) * nm;
-    const unsigned bx = (w + NT - 1) / NT;
-    const unsigned lb = blockIdx.x - tab->start[p];
-    const unsigned g = lb / bx;
-    const unsigned x = (lb - g * bx) * NT + threadIdx.x;
-    if (x >= w) return;
-    const unsigned s0 = ((unsigned)(L.nz + 1) / 2 + L.strip - 1) / L.strip;
-    const int par = g < s0 ? 0 : 1;
-    const int k0 = par + 2 * (int)(g < s0 ? g : g - s0) * L.strip;
-    const unsigned j = x / nm;
-    const int m = (int)(x - j * nm);
-    const int i = 2 * (int)j + ((par + color) & 1);
-    const size_t rowstride = (size_t)L.nr * nm;
-    const size_t plane = (size_t)L.nr * nm;            // one row of cells, all modes
-    const size_t tcol = (size_t)i * nm + m;            // (i, m) within a coefficient class
-    const size_t t1 = (L.ncls > 1 ? plane : 0) + tcol;   // interior class (class 1)
-    const T hz1 = L.hz[t1], hw1 = L.hw[t1], he1 = L.he[t1];
-    size_t idx = (size_t)k0 * rowstride + tcol;
-    V2<T> south = k0 > 0 ? L.u[idx - rowstride] : mk<T>(0, 0);
-    const int kend = min(L.nz, k0 + 2 * L.strip);
-    for (int k = k0; k < kend; k += 2, idx += 2 * rowstride) {
-        const bool has_n = k < L.nz - 1;
-        const V2<T> north = has_n ? L.u[idx + rowstride] : mk<T>(0, 0);
-        V2<T> s;
-        if (k > 0 && has_n) s = mk<T>(south.x + north.x, south.y + north.y);
-        else s = k > 0 ? south : north;
-        T hz = hz1, hw = hw1, he = he1;
-        if (k == 0 || !has_n) {   // boundary rows have their own coefficient class
-            const size_t tb = (size_t)row_class(k, L.nz, L.ncls) * plane + tcol;
-            hz = L.hz[tb];
-            hw = L.hw[tb];
-            he = L.he[tb];
+    if constexpr (S == 0) {
+        const unsigned e = (blockIdx.x - tab->start[p]) * NT + threadIdx.x;
+        if (e >= (unsigned)L.nz * (unsigned)(L.nr >> 1) * nm) return;
+        const unsigned c = e / nm;
+        const int m = (int)(e - c * nm);
+        int k, i;
+        colour_cell(c, L.nr, color, k, i);
+        const size_t idx = ((size_t)k * L.nr + i) * nm + m;
+        const size_t tb = ((size_t)row_class(k, L.nz, L.ncls) * L.nr + i) * nm + m;
+        const size_t rowstride = (size_t)L.nr * nm;
+        V2<T> s = mk<T>(0, 0);
+        if (k > 0) s = L.u[idx - rowstride];
+        if (k < L.nz - 1) {
+            const V2<T> n = L.u[idx + rowstride];
+            s = (k > 0) ? mk<T>(s.x + n.x, s.y + n.y) : n;
         }
-        V2<T> acc = fma2<T>(hz, s, L.bh[idx]);
-        if (i > 0) acc = fma2<T>(hw, L.u[idx - nm], acc);
-        if (i < L.nr - 1) acc = fma2<T>(he, L.u[idx + nm], acc);
+        V2<T> acc = fma2<T>(L.hz[tb], s, L.bh[idx]);
+        if (i > 0) acc = fma2<T>(L.hw[tb], L.u[idx - nm], acc);
+        if (i < L.nr - 1) acc = fma2<T>(L.he[tb], L.u[idx + nm], acc);
+        if (SOR) acc = fma2<T>(L.relax, L.u[idx], acc);
         L.u[idx] = acc;
-        south = north;
+    } else {
+        const unsigned w = (unsigned)(L.nr >> 1) * nm;
+        const unsigned bx = (w + NT - 1) / NT;
+        const unsigned lb = blockIdx.x - tab->start[p];
+        const unsigned g = lb / bx;
+        const unsigned x = (lb - g * bx) * NT + threadIdx.x;
+        if (x >= w) return;
+        const unsigned s0 = ((unsigned)(L.nz + 1) / 2 + S - 1) / S;
+        const int par = g < s0 ? 0 : 1;
+        const int k0 = par + 2 * (int)(g < s0 ? g : g - s0) * S;
+        const unsigned j = x / nm;
+        const int m = (int)(x - j * nm);
+        const int i = 2 * (int)j + ((par + color) & 1);
+        const size_t rs = (size_t)L.nr * nm;                 // one row of cells, all modes
+        const size_t tcol = (size_t)i * nm + m;              // (i, m) within a row / a coefficient class
+        const size_t t1 = (L.ncls > 1 ? rs : 0) + tcol;      // interior coefficient class
+        const T hz1 = __ldg(L.hz + t1), hw1 = __ldg(L.hw + t1), he1 = __ldg(L.he + t1);
+        const V2<T> zero = mk<T>(0, 0);
+        const size_t idx0 = (size_t)k0 * rs + tcol;
+        V2<T> south = k0 > 0 ? __ldg(L.u + idx0 - rs) : zero;
+        V2<T> vn[S], vw[S], ve[S], vb[S], vo[S];
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            const int k = k0 + 2 * t;
+            const size_t idx = idx0 + (size_t)(2 * t) * rs;
+            vn[t] = vw[t] = ve[t] = vb[t] = vo[t] = zero;
+            if (k < L.nz) {
+                if (k < L.nz - 1) vn[t] = __ldg(L.u + idx + rs);
+                if (i > 0) vw[t] = __ldg(L.u + idx - nm);
+                if (i < L.nr - 1) ve[t] = __ldg(L.u + idx + nm);
+                vb[t] = __ldg(L.bh + idx);
+                if (SOR) vo[t] = L.u[idx];   // this colour: written below, so not through the read-only path
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            const int k = k0 + 2 * t;
+            if (k >= L.nz) break;
+            T hz = hz1, hw = hw1, he = he1;
+            if (k == 0 || k == L.nz - 1) {   // boundary rows have their own coefficient class
+                const size_t tb = (size_t)row_class(k, L.nz, L.ncls) * rs + tcol;
+                hz = L.hz[tb];
+                hw = L.hw[tb];
+                he = L.he[tb];
+            }
+            const V2<T> s = mk<T>(south.x + vn[t].x, south.y + vn[t].y);   // absent neighbours are zero
+            V2<T> acc = fma2<T>(hz, s, vb[t]);
+            if (i > 0) acc = fma2<T>(hw, vw[t], acc);
+            if (i < L.nr - 1) acc = fma2<T>(he, ve[t], acc);
+            if (SOR) acc = fma2<T>(L.relax, vo[t], acc);
+            L.u[idx0 + (size_t)(2 * t) * rs] = acc;
+            south = vn[t];
+        }
     }
 }
 
@@ -179,29 +221,38 @@ k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ p
         const int I = (int)(cc - (unsigned)K * C.nr);
         // coarsening factors of this level pair (semi-coarsening keeps one direction)
         const int fz = F.nz == C.nz ? 1 : 2, fr = F.nr == C.nr ? 1 : 2;
-        V2<T> sum = mk<T>(0, 0);
-        auto add = [&](int k, int i, bool first) {
+        // fine cells that carry a residual, c < nc: RED_ONLY keeps the red ones
+        // (k + i even) -- the (0,0) and (1,1) corners of a 2x2 block, one cell
+        // of a 2x1 pair -- otherwise all fz * fr cells
+        const int nc = RED_ONLY ? (fz == 2 && fr == 2 ? 2 : 1) : fz * fr;
+        auto cell = [&](int c, int &k, int &i) {
+            if (RED_ONLY) {
+                k = fz * K + (fz == 2 ? (fr == 2 ? c : (I & 1)) : 0);
+                i = fr * I + (fr == 2 ? (fz == 2 ? c : (K & 1)) : 0);
+            } else {
+                k = fz * K + (fr == 2 ? (c >> 1) : c);
+                i = fr * I + (fr == 2 ? (c & 1) : 0);
+            }
+        };
+        int k, i;
+        cell(0, k, i);
+        V2<T> sum = residual_at(F, k, i, m, ((size_t)k * F.nr + i) * nm + m);
+        if (partials) acc = fma((double)sum.y, (double)sum.y, (double)sum.x * (double)sum.x);
+        auto more = [&](int c) {
+            cell(c, k, i);
             const V2<T> r = residual_at(F, k, i, m, ((size_t)k * F.nr + i) * nm + m);
-            sum = first ? r : mk<T>(sum.x + r.x, sum.y + r.y);
+            sum = mk<T>(sum.x + r.x, sum.y + r.y);
             if (partials) acc = fma((double)r.y, (double)r.y, fma((double)r.x, (double)r.x, acc));
         };
-        if (RED_ONLY && fz == 2 && fr == 2) {
-            // the red cells of a 2x2 block are its (0,0) and (1,1) corners
-            add(2 * K, 2 * I, true);
-            add(2 * K + 1, 2 * I + 1, false);
+        if constexpr (sizeof(T) == sizeof(double)) {
+            // a loop, not a predicated unroll: FP64 work only for the cells that exist
+#pragma unroll 1
+            for (int c = 1; c < nc; ++c) more(c);
         } else {
-            bool first = true;
+            // FP32 is bound by load latency: unrolled, all loads in flight together
 #pragma unroll
-            for (int a = 0; a < 2; ++a) {
-#pragma unroll
-                for (int bb = 0; bb < 2; ++bb) {
-                    if (a >= fz || bb >= fr) continue;
-                    const int k = fz * K + a, i = fr * I + bb;
-                    if (RED_ONLY && ((k + i) & 1)) continue;
-                    add(k, i, first);
-                    first = false;
-                }
-            }
+            for (int c = 1; c < 4; ++c)
+                if (c < nc) more(c);
         }
         C.b[e] = sum;
         if (F.init > 0) {
@@ -349,6 +400,10 @@ __device__ __forceinline__ int pow2_exponent(double v) { return ((__double2hiint
 // u32 = (red ? b_hat32 : 0) -- the first red half-sweep of the FP32 V-cycle
 // from a zero correction -- or u32 = 0.  The squared norm of the scaled
 // residual is accumulated in FP32 per entry (it only decides convergence).
+// ZERO_X: the iterate is zero (first defect of a solve from a zero initial
+// guess), so r = b and the kernel also writes x = 0 -- a memory pass, no FP64
+// stencil.
+template <bool ZERO_X>
 __global__ void __launch_bounds__(MG_THREADS)
 k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, double *__restrict__ partials) {
     __shared__ double red[MG_THREADS / 32];
@@ -365,7 +420,13 @@ k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, doubl
         const int m = (int)(e - c * nm);
         const int k = (int)(c / (unsigned)D.nr);
         const int i = (int)(c - (unsigned)k * D.nr);
-        const double2 r = residual_at(D, k, i, m, e);
+        double2 r;
+        if (ZERO_X) {
+            r = D.b[e];
+            D.u[e] = make_double2(0.0, 0.0);
+        } else {
+            r = residual_at(D, k, i, m, e);
+        }
         const float2 b32 = make_float2(f64_to_f32_pow2(r.x, ls), f64_to_f32_pow2(r.y, ls));
         const float w = (m == 0 || 2 * m == D.nt) ? 1.f : 2.f;
         acc = f32_to_f64_pow2(w * fmaf(b32.x, b32.x, b32.y * b32.y), 0);
@@ -606,15 +667,34 @@ __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ p, int 
 
 }  // namespace
 
-template <class T>
-cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, int threads, cudaStream_t st) {
+template <class T, int S, bool SOR>
+void launch_smooth_s(const LaunchTab<T> *tab, unsigned grid, int color, int threads, cudaStream_t st) {
     switch (threads) {
-    case 64: k_smooth<T, 64><<<grid, 64, 0, st>>>(tab, color); break;
-    case 128: k_smooth<T, 128><<<grid, 128, 0, st>>>(tab, color); break;
-    case 512: k_smooth<T, 512><<<grid, 512, 0, st>>>(tab, color); break;
-    default: k_smooth<T, 256><<<grid, 256, 0, st>>>(tab, color); break;
+    case 64: k_smooth<T, 64, S, SOR><<<grid, 64, 0, st>>>(tab, color); break;
+    case 128: k_smooth<T, 128, S, SOR><<<grid, 128, 0, st>>>(tab, color); break;
+    case 512: k_smooth<T, 512, S, SOR><<<grid, 512, 0, st>>>(tab, color); break;
+    default: k_smooth<T, 256, S, SOR><<<grid, 256, 0, st>>>(tab, color); break;
+    }
+}
+
+template <class T, bool SOR>
+cudaError_t launch_smooth_r(const LaunchTab<T> *tab, unsigned grid, int color, int threads, int strip,
+                            cudaStream_t st) {
+    switch (strip) {
+    case 0: launch_smooth_s<T, 0, SOR>(tab, grid, color, threads, st); break;
+    case 1: launch_smooth_s<T, 1, SOR>(tab, grid, color, threads, st); break;
+    case 2: launch_smooth_s<T, 2, SOR>(tab, grid, color, threads, st); break;
+    case 4: launch_smooth_s<T, 4, SOR>(tab, grid, color, threads, st); break;
+    default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, int threads, int strip, bool sor,
+                          cudaStream_t st) {
+    return sor ? launch_smooth_r<T, true>(tab, grid, color, threads, strip, st)
+               : launch_smooth_r<T, false>(tab, grid, color, threads, strip, st);
 }
 
 template <class T>
@@ -647,8 +727,10 @@ cudaError_t launch_coarse(const CoarseTab<T> *tab, unsigned grid, size_t smem, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_defect(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, double *partials, cudaStream_t st) {
-    k_defect<<<grid, MG_THREADS, 0, st>>>(tab, ctrl, partials);
+cudaError_t launch_defect(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, double *partials, bool zero_x,
+                          cudaStream_t st) {
+    if (zero_x) k_defect<true><<<grid, MG_THREADS, 0, st>>>(tab, ctrl, partials);
+    else k_defect<false><<<grid, MG_THREADS, 0, st>>>(tab, ctrl, partials);
     return cudaGetLastError();
 }
 
@@ -674,7 +756,7 @@ cudaError_t launch_sum(const double *partials, int n, double *out, cudaStream_t 
 }
 
 #define PP_INST(T)                                                                                         \
-    template cudaError_t launch_smooth<T>(const LaunchTab<T> *, unsigned, int, int, cudaStream_t);         \
+    template cudaError_t launch_smooth<T>(const LaunchTab<T> *, unsigned, int, int, int, bool, cudaStream_t); \
     template cudaError_t launch_residual_restrict<T>(const LaunchTab<T> *, unsigned, bool, double *,       \
                                                      cudaStream_t);                                        \
     template cudaError_t launch_residual<T>(const LaunchTab<T> *, unsigned, bool, double *, unsigned,      \

@@ -45,6 +45,16 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
     if (d->post_sweeps < 0) d->post_sweeps = 2;
     if (d->inner_cycles <= 0) d->inner_cycles = 2;
     if (d->smooth_threads <= 0) d->smooth_threads = MG_THREADS;
+    if (d->smooth_strip < 0) d->smooth_strip = 0;
+    if (d->omega <= 0) d->omega = 1.0;
+    if (!(d->omega < 2.0)) {
+        set_error("omega must be in (0, 2) (got %g)", d->omega);
+        return PIC_POISSON_EINVAL;
+    }
+    if (d->smooth_strip != 0 && d->smooth_strip != 1 && d->smooth_strip != 2 && d->smooth_strip != 4) {
+        set_error("smooth_strip must be <= 0, 1, 2 or 4 (got %d)", d->smooth_strip);
+        return PIC_POISSON_EINVAL;
+    }
     if (d->smooth_threads != 64 && d->smooth_threads != 128 && d->smooth_threads != 256 && d->smooth_threads != 512) {
         set_error("smooth_threads must be 64, 128, 256 or 512 (got %d)", d->smooth_threads);
         return PIC_POISSON_EINVAL;
@@ -174,11 +184,15 @@ void build_level(const pic_poisson_desc &d, int nr, int nz, int nm, LevelHost &h
             for (int m = 0; m < nm; ++m) {
                 const size_t t = ((size_t)c * nr + i) * nm + m;
                 const double dg = h.d0r[i] + h.tz[c] * h.cz[i] + lambda_m(d, m) * h.mu[i];
+                // smoother tables carry the over-relaxation factor: with
+                // omega b / diag and omega G / diag the update is
+                // u <- (1 - omega) u + (omega b_hat + sum omega h u)
+                const double w = d.omega > 0 ? d.omega : 1.0;
                 h.diag[t] = dg;
-                h.invd[t] = 1.0 / dg;
-                h.hw[t] = h.cw[i] / dg;
-                h.he[t] = h.ce[i] / dg;
-                h.hz[t] = h.cz[i] / dg;
+                h.invd[t] = w / dg;
+                h.hw[t] = w * h.cw[i] / dg;
+                h.he[t] = w * h.ce[i] / dg;
+                h.hz[t] = w * h.cz[i] / dg;
             }
 }
 
@@ -306,8 +320,14 @@ void carve(pic_poisson_plan_s &P, Carver &c) {
         const int nt = q.d.ntheta;
         q.dl.assign(mixed ? 1 : q.L, LevelDev<double>{});
         q.fl.assign(mixed ? q.L : 0, LevelDev<float>{});
-        for (int l = 0; l < (int)q.dl.size(); ++l) carve_level<double, double2>(q.lv[l], q.nm, nt, c, q.dl[l]);
-        for (int l = 0; l < (int)q.fl.size(); ++l) carve_level<float, float2>(q.lv[l], q.nm, nt, c, q.fl[l]);
+        for (int l = 0; l < (int)q.dl.size(); ++l) {
+            carve_level<double, double2>(q.lv[l], q.nm, nt, c, q.dl[l]);
+            q.dl[l].relax = 1.0 - q.d.omega;
+        }
+        for (int l = 0; l < (int)q.fl.size(); ++l) {
+            carve_level<float, float2>(q.lv[l], q.nm, nt, c, q.fl[l]);
+            q.fl[l].relax = (float)(1.0 - q.d.omega);
+        }
         if (mixed) carve_coarse(q, c, q.cf);
         else carve_coarse(q, c, q.cd);
         const int M = nt / 2;
@@ -372,18 +392,17 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
     H.g_smooth.assign(nl, 0);
     H.g_restr.assign(nl, 0);
     H.g_prolong.assign(nl, 0);
+    H.strip.assign(nl, 1);
     for (int l = 0; l < nl; ++l) {
         LaunchTab<T> ts{}, tr{}, tp{};
-        // smoother strip: enough rows per thread to amortise its index work
-        // while the launch still fills the GPU (~2 full waves of 152 SMs x
-        // 2048 threads before the strip grows)
-        double updates = 0;
-        for (int p = 0; p < P.n; ++p) {
-            const ProblemPlan &q = P.pr[p];
-            if (l < q.L - 1) updates += (double)views(q)[l].nz * (views(q)[l].nr / 2) * views(q)[l].nm;
-        }
-        int strip = 1;
-        while (strip < 8 && updates / (2.0 * strip) >= 2.0 * 152 * 2048) strip <<= 1;
+        // smoother strip (0: one entry per thread); a strip longer than the
+        // level's rows of one parity is cut to the next power of two that fits
+        int strip = P.shared.smooth_strip;
+        int zmax = 0;
+        for (int p = 0; p < P.n; ++p)
+            if (l < P.pr[p].L - 1) zmax = std::max(zmax, (views(P.pr[p])[l].nz + 1) / 2);
+        while (strip > 1 && strip > zmax) strip >>= 1;
+        H.strip[l] = strip;
         for (int p = 0; p < P.n; ++p) {
             const ProblemPlan &q = P.pr[p];
             if (l >= q.L - 1) continue;
@@ -394,7 +413,9 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
             const size_t coarse_n = (size_t)v[l + 1].nz * v[l + 1].nr * f.nm;
             ts.f[ts.n] = f;
             ts.f[ts.n].strip = strip;
-            ts.start[ts.n + 1] = ts.start[ts.n] + smooth_blocks(f.nr, f.nz, f.nm, strip, P.shared.smooth_threads);
+            ts.start[ts.n + 1] = ts.start[ts.n] + (strip == 0 ? mg_blocks(half, P.shared.smooth_threads)
+                                                             : smooth_blocks(f.nr, f.nz, f.nm, strip,
+                                                                             P.shared.smooth_threads));
             ++ts.n;
             tr.f[tr.n] = f;
             tr.c[tr.n] = v[l + 1];
@@ -402,7 +423,7 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
             ++tr.n;
             tp.f[tp.n] = f;
             tp.c[tp.n] = v[l + 1];
-            tp.start[tp.n + 1] = tp.start[tp.n] + mg_blocks(post > 0 ? half : full);
+            tp.start[tp.n + 1] = tp.start[tp.n] + mg_blocks(post > 0 && P.shared.omega == 1.0 ? half : full);
             ++tp.n;
         }
         H.g_smooth[l] = ts.start[ts.n];
@@ -455,15 +476,10 @@ int upload(pic_poisson_plan_s &P) {
         }
         const int nt = q.d.ntheta, M = nt / 2;
         std::vector<double> tw(2 * std::max(M / 2, 1), 0.0), tw2(2 * (M + 1), 0.0);
-        auto scale_ratio = [](double *out, int t, int n) {   // e^{-2 pi i t / n} as (a, b)
-            const double c = std::cos(2.0 * kPi * t / n), sn = std::sin(2.0 * kPi * t / n);
-            if (tw_first_form(t, n)) {
-                out[0] = c;
-                out[1] = -sn / c;
-            } else {
-                out[0] = -sn;
-                out[1] = -c / sn;
-            }
+        auto scale_ratio = [](double *out, int t, int n) {   // e^{-2 pi i t / n} as (a, b), see tw_rot
+            const double th = 2.0 * kPi * t / n - (tw_rot(t, n) ? 0.5 * kPi : 0.0);
+            out[0] = std::cos(th);
+            out[1] = -std::tan(th);
         };
         for (int t = 0; t < M / 2; ++t) scale_ratio(&tw[2 * t], t, M);
         if (M / 2 == 0) tw[0] = 1.0;
@@ -511,6 +527,7 @@ int upload(pic_poisson_plan_s &P) {
         fp.log2M = lg;
         fp.tw = q.tw;
         fp.tw2 = q.tw2;
+        fp.half_inv_n = 0.5 / q.d.ntheta;
         FFTProb f = fp, g = fp, iv = fp;
         f.s = q.s0;
         f.bD = q.bD0;
@@ -610,7 +627,7 @@ int upload(pic_poisson_plan_s &P) {
 int same_settings(const pic_poisson_desc &a, const pic_poisson_desc &b) {
     return a.precision == b.precision && a.max_cycles == b.max_cycles && a.pre_sweeps == b.pre_sweeps &&
            a.post_sweeps == b.post_sweeps && a.inner_cycles == b.inner_cycles && a.flags == b.flags &&
-           a.smooth_threads == b.smooth_threads;
+           a.smooth_threads == b.smooth_threads && a.smooth_strip == b.smooth_strip && a.omega == b.omega;
 }
 
 int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
@@ -626,7 +643,8 @@ int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
         if (rc) return rc;
         if (p == 0) P.shared = d;
         else if (!same_settings(P.shared, d)) {
-            set_error("problem %d: precision, max_cycles, sweeps, inner_cycles, smooth_threads and flags must match "
+            set_error("problem %d: precision, max_cycles, sweeps, inner_cycles, smooth_threads, smooth_strip, omega "
+                      "and flags must match "
                       "problem 0", p);
             return PIC_POISSON_EINVAL;
         }

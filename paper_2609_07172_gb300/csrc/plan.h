@@ -24,6 +24,7 @@ struct ProblemPlan {
 template <class T> struct Hier {
     std::vector<LaunchTab<T> *> smooth, restr, prolong;   // device tables (null when no problem takes part)
     std::vector<unsigned> g_smooth, g_restr, g_prolong;   // grids
+    std::vector<int> strip;                               // smoother strip per level
     CoarseTab<T> *coarse = nullptr;
     unsigned g_coarse = 0;
     size_t smem_coarse = 0;

@@ -114,7 +114,8 @@ double fft_flops_all(const pic_poisson_plan_s &P, double *bytes3d) {
 // `sweeps` red-black sweeps on level l of every problem that is smoothed
 // there.  skip_first_red: the first sweep starts at its black half, because
 // the kernel that initialised the level already performed the red half-sweep
-// from a zero iterate.  Half-sweep: 1.5 V, 14 flops per updated complex entry.
+// from a zero iterate.  Half-sweep: 1.5 V, 14 flops per updated complex entry
+// (over-relaxed: 2 V, 18 flops -- the cell's own value is read and weighted).
 template <class T>
 int smooth_level(Runner &R, const Hier<T> &H, int l, int sweeps, bool skip_first_red) {
     if (!H.smooth[l]) return PIC_POISSON_OK;
@@ -122,8 +123,10 @@ int smooth_level(Runner &R, const Hier<T> &H, int l, int sweeps, bool skip_first
     const double n = level_entries<T>(R.P, l);
     for (int s = 0; s < sweeps; ++s) {
         for (int color = (s == 0 && skip_first_red) ? 1 : 0; color < 2; ++color) {
-            RUN(R, ph, launch_smooth(H.smooth[l], H.g_smooth[l], color, R.P.shared.smooth_threads, R.st));
-            R.account(ph, 1.5 * n * sizeof(V2<T>), 14.0 * 0.5 * n);
+            const bool sor = R.P.shared.omega != 1.0;
+            RUN(R, ph, launch_smooth(H.smooth[l], H.g_smooth[l], color, R.P.shared.smooth_threads, H.strip[l], sor,
+                                     R.st));
+            R.account(ph, (sor ? 2.0 : 1.5) * n * sizeof(V2<T>), (sor ? 18.0 : 14.0) * 0.5 * n);
         }
     }
     return PIC_POISSON_OK;
@@ -135,7 +138,9 @@ int smooth_level(Runner &R, const Hier<T> &H, int l, int sweeps, bool skip_first
 template <class T>
 int restrict_level(Runner &R, const Hier<T> &H, int l, double *partials) {
     if (!H.restr[l]) return PIC_POISSON_OK;
-    const bool red_only = R.P.shared.pre_sweeps > 0;
+    // after a Gauss-Seidel black half-sweep the black residuals vanish; an
+    // over-relaxed one leaves them nonzero, so then every cell is evaluated
+    const bool red_only = R.P.shared.pre_sweeps > 0 && R.P.shared.omega == 1.0;
     RUN(R, PIC_POISSON_PHASE_RESTRICT, launch_residual_restrict(H.restr[l], H.g_restr[l], red_only, partials, R.st));
     const double n = level_entries<T>(R.P, l), frac = red_only ? 0.5 : 1.0;
     R.account(PIC_POISSON_PHASE_RESTRICT, n * sizeof(V2<T>) * (1.0 + frac + 0.75),
@@ -162,8 +167,11 @@ int descend_ascend(Runner &R, const Hier<T> &H) {
     R.account(PIC_POISSON_PHASE_COARSE, 2.0 * cn * sizeof(V2<T>) + cn * 2 * sizeof(T), cf);
     for (int l = nl - 1; l >= 0; --l) {
         if (!H.prolong[l]) continue;
-        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_prolong(H.prolong[l], H.g_prolong[l], post > 0, R.st));
-        const double n = level_entries<T>(P, l), frac = post > 0 ? 0.5 : 1.0;
+        // the red half-sweep that follows overwrites the red cells unread
+        // (Gauss-Seidel only: an over-relaxed update reads the old value)
+        const bool black_only = post > 0 && P.shared.omega == 1.0;
+        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_prolong(H.prolong[l], H.g_prolong[l], black_only, R.st));
+        const double n = level_entries<T>(P, l), frac = black_only ? 0.5 : 1.0;
         R.account(PIC_POISSON_PHASE_PROLONG, n * sizeof(V2<T>) * (0.25 + 2.0 * frac), 16.0 * frac * n);
         int rc = smooth_level(R, H, l, post, false);
         if (rc) return rc;
@@ -188,11 +196,11 @@ int fp64_residual_and_check(Runner &R, int counting) {
     return PIC_POISSON_OK;
 }
 
-int mixed_defect_and_check(Runner &R, int counting) {
+int mixed_defect_and_check(Runner &R, int counting, bool zero_x = false) {
     pic_poisson_plan_s &P = R.P;
-    RUN(R, PIC_POISSON_PHASE_DEFECT, launch_defect(P.defect, P.g_defect, P.ctrl, P.partials, R.st));
+    RUN(R, PIC_POISSON_PHASE_DEFECT, launch_defect(P.defect, P.g_defect, P.ctrl, P.partials, zero_x, R.st));
     const double n = level0_entries(P, 0);
-    R.account(PIC_POISSON_PHASE_DEFECT, n * (2.0 * sizeof(double2) + 3.0 * sizeof(float2)), 26.0 * n);
+    R.account(PIC_POISSON_PHASE_DEFECT, n * (2.0 * sizeof(double2) + 3.0 * sizeof(float2)), (zero_x ? 6.0 : 26.0) * n);
     RUN(R, PIC_POISSON_PHASE_NORM, launch_check(P.ctrl, P.partials, counting, P.handle, R.use_handle ? 1 : 0, R.st));
     return PIC_POISSON_OK;
 }
@@ -214,13 +222,13 @@ int enqueue_prologue(Runner &R, int guess) {
     } else if (guess == 2) {
         RUN(R, PIC_POISSON_PHASE_FORWARD, launch_copy_guess(P.guess, P.g_fft, R.st));
         R.account(PIC_POISSON_PHASE_FORWARD, 2.0 * n0 * sizeof(double2), 0.0);
-    } else {
+    } else if (!mixed) {   // (the mixed form's first defect writes the zero iterate itself)
         for (const ProblemPlan &q : P.pr) {
             const size_t n = (size_t)q.lv[0].nr * q.lv[0].nz * q.nm;
             PP_CUDA(cudaMemsetAsync(q.dl[0].u, 0, n * sizeof(double2), R.st));
         }
     }
-    if (mixed) return mixed_defect_and_check(R, 0);
+    if (mixed) return mixed_defect_and_check(R, 0, guess == 0);
     if (P.Lmax > 1) {
         int rc = smooth_level(R, P.h64, 0, P.shared.pre_sweeps, false);
         if (rc) return rc;

@@ -1,9 +1,11 @@
 // Autotuner: picks the smoothing schedule (pre / post sweeps), the number of
 // FP32 V-cycles per FP64 defect correction (mixed precision) and the smoother's
-// block size by timing complete solves of the caller's own problems.
+// block size and strip by timing complete solves of the caller's own problems.
 //
 // Stage 1 times every schedule (and inner-cycle count) at the default block
-// size; stage 2 times the other block sizes for the best schedule.  Each
+// size and one entry per thread; stage 2 times the other block sizes for the
+// best schedule, stage 3 strips of 2 and 4 rows at the best block size, stage 4
+// over-relaxation factors with the short schedules.  Each
 // candidate gets its own plan, one untimed solve (which also captures the
 // graph when PIC_POISSON_GRAPH is set) and `repeats` timed solves; its score
 // is the median wall time of a solve call, which includes every host-side
@@ -19,8 +21,8 @@ namespace pp {
 namespace {
 
 struct Cand {
-    int pre, post, inner, threads;
-    double ms;
+    int pre, post, inner, threads, strip;
+    double omega, ms;
 };
 
 int time_candidate(const pic_poisson_desc *descs, int n, const double *const *rho, double *const *phi, double tol,
@@ -31,6 +33,8 @@ int time_candidate(const pic_poisson_desc *descs, int n, const double *const *rh
         x.post_sweeps = c.post;
         x.inner_cycles = c.inner;
         x.smooth_threads = c.threads;
+        x.smooth_strip = c.strip;
+        x.omega = c.omega;
         x.flags &= ~PIC_POISSON_PROFILE;
     }
     pic_poisson_plan_t plan = nullptr;
@@ -71,12 +75,12 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
     std::vector<Cand> cands;
     for (const auto &s : sched) {
         if (mixed) {
-            for (int inner = 1; inner <= 4; ++inner) cands.push_back({s[0], s[1], inner, 256, 0.0});
+            for (int inner = 1; inner <= 4; ++inner) cands.push_back({s[0], s[1], inner, 256, 0, 1.0, 0.0});
         } else {
-            cands.push_back({s[0], s[1], 2, 256, 0.0});
+            cands.push_back({s[0], s[1], 2, 256, 0, 1.0, 0.0});
         }
     }
-    Cand best{0, 0, 0, 0, 1e300};
+    Cand best{0, 0, 0, 0, 0, 1.0, 1e300};
     int last_err = PIC_POISSON_OK;
     auto record = [&](Cand &c) {
         const int rc = time_candidate(descs, n, rho_dev, phi_dev, tol, stream, repeats, c);
@@ -89,6 +93,8 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
             out->post_tried[k] = c.post;
             out->inner_tried[k] = c.inner;
             out->threads_tried[k] = c.threads;
+            out->strip_tried[k] = c.strip;
+            out->omega_tried[k] = c.omega;
         }
         if (c.ms < best.ms) best = c;
         return rc;
@@ -102,14 +108,29 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
         return last_err ? last_err : PIC_POISSON_ENOTCONVERGED;
     }
     for (int threads : {64, 128, 512}) {
-        Cand c{best.pre, best.post, best.inner, threads, 0.0};
+        Cand c{best.pre, best.post, best.inner, threads, 0, 1.0, 0.0};
         const int rc = record(c);
         if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;
     }
+    for (int strip : {2, 4}) {
+        Cand c{best.pre, best.post, best.inner, best.threads, strip, 1.0, 0.0};
+        const int rc = record(c);
+        if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;
+    }
+    static const int sor_sched[][2] = {{1, 1}, {1, 2}, {2, 1}, {2, 2}};
+    const Cand base = best;
+    for (double omega : {1.1, 1.2, 1.3})
+        for (const auto &s : sor_sched) {
+            Cand c{s[0], s[1], base.inner, base.threads, base.strip, omega, 0.0};
+            const int rc = record(c);
+            if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;
+        }
     out->pre_sweeps = best.pre;
     out->post_sweeps = best.post;
     out->inner_cycles = best.inner;
     out->smooth_threads = best.threads;
+    out->smooth_strip = best.strip;
+    out->omega = best.omega;
     out->ms = best.ms;
     return PIC_POISSON_OK;
 }

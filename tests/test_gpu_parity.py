@@ -120,6 +120,60 @@ def test_sweep_schedules_match_oracle(sweeps):
     assert rel_l2(phi.cpu().numpy(), ref) <= FP64_TOL, info
 
 
+@pytest.mark.parametrize("strip", [1, 2, 4])
+@pytest.mark.parametrize("dims", [(64, 32, 48), (96, 16, 38), (40, 8, 14)])
+def test_smoother_strips_match_oracle(strip, dims):
+    """The strip smoother (each thread updates `strip` same-parity rows) gives
+    the oracle's solution, FP64 and mixed, including strips that run past the
+    last row (nz = 38 and 14: ragged tails at every level) and levels with
+    fewer rows of one parity than the strip."""
+    p = with_bias_walls(W.annulus(*dims))
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=13)
+    ref, _ = oracle.solve3d(g, rho, tol=1e-15)
+    for prec, tol in ((B.FP64, FP64_TOL), (B.MIXED, 1e-10)):
+        with Plan(p, precision=prec, smooth_strip=strip) as plan:
+            phi, info = plan.solve(dev(rho), tol=0.0)
+        assert info["status"] == B.OK
+        assert rel_l2(phi.cpu().numpy(), ref) <= tol, (prec, info)
+
+
+@pytest.mark.parametrize("omega", [1.15, 1.3])
+@pytest.mark.parametrize("strip", [0, 2])
+def test_over_relaxed_smoother_matches_oracle(omega, strip):
+    """Red-black SOR (u <- u + omega (u_GS - u)) converges to the same discrete
+    solution, FP64 and mixed, with both smoother mappings."""
+    p = with_bias_walls(W.annulus(64, 32, 48))
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=15)
+    ref, _ = oracle.solve3d(g, rho, tol=1e-15)
+    for prec, tol in ((B.FP64, FP64_TOL), (B.MIXED, 1e-10)):
+        with Plan(p, precision=prec, omega=omega, smooth_strip=strip, pre_sweeps=1, post_sweeps=1) as plan:
+            phi, info = plan.solve(dev(rho), tol=0.0)
+        assert info["status"] == B.OK
+        assert rel_l2(phi.cpu().numpy(), ref) <= tol, (prec, info)
+
+
+def test_omega_outside_0_2_is_rejected():
+    with pytest.raises(PicPoissonError):
+        Plan(W.annulus(32, 8, 32), omega=2.0)
+
+
+def test_smoother_strip_is_deterministic_and_matches_one_entry_mapping():
+    """Strips change only the work assignment: every update reads the same
+    values, so the result is bitwise identical to one entry per thread."""
+    p = with_bias_walls(W.annulus(96, 16, 40))
+    rho = dev(W.rho_plasma(p, seed=14))
+    out = []
+    for strip in (0, 1, 2, 4):
+        with Plan(p, smooth_strip=strip) as plan:
+            phi, info = plan.solve(rho, tol=1e-10)
+        out.append((phi.cpu(), info["cycles"]))
+    for phi, cyc in out[1:]:
+        assert cyc == out[0][1]
+        assert torch.equal(phi, out[0][0])
+
+
 @pytest.mark.parametrize("tol", [1e-6, 1e-10])
 def test_stop_at_tolerance_reports_true_residual(tol):
     p = with_bias_walls(W.annulus(64, 32, 48))
