@@ -101,6 +101,9 @@ typedef struct {
                                   parity at one (radial cell, mode), loads of the strip issued together */
     double omega;              /* over-relaxation of the red-black smoother, u <- u + omega (u_GS - u),
                                   0 < omega < 2; <= 0 selects 1 (plain Gauss-Seidel) */
+    int smooth_fused;          /* mixed precision: 1 runs each pre- or post-smoothing of an FP32 level
+                                  (1 or 2 sweeps, omega = 1, even nr) as one fused pass; 0 separate
+                                  half-sweeps */
     unsigned flags;            /* PIC_POISSON_* flags */
 } pic_poisson_desc;
 
@@ -126,6 +129,7 @@ typedef struct {
     int smooth_threads;                    /* best smoother block size */
     int smooth_strip;                      /* best smoother strip (0: one entry per thread) */
     double omega;                          /* best over-relaxation factor */
+    int smooth_fused;                      /* best fused-smoother setting */
     double ms;                             /* its median wall time per solve call */
     int tried;                             /* candidates timed (entries below) */
     double ms_tried[PIC_POISSON_MAX_TUNE];
@@ -133,6 +137,7 @@ typedef struct {
     int inner_tried[PIC_POISSON_MAX_TUNE], threads_tried[PIC_POISSON_MAX_TUNE];
     int strip_tried[PIC_POISSON_MAX_TUNE];
     double omega_tried[PIC_POISSON_MAX_TUNE];
+    int fused_tried[PIC_POISSON_MAX_TUNE];
 } pic_poisson_tuning;
 
 typedef struct {
@@ -218,7 +223,9 @@ int pic_poisson_solve_batch(pic_poisson_plan_t plan, const double *const *rho_de
  * threads and one entry per thread; stage 2 times 64, 128 and 512 threads for
  * the winner; stage 3 strips of 2 and 4 rows at the best block size; stage 4
  * over-relaxation omega = 1.1, 1.2, 1.3 with the schedules (1,1), (1,2),
- * (2,1), (2,2) at the best block size, strip and inner cycles.  Each
+ * (2,1), (2,2) at the best block size, strip and inner cycles; stage 5
+ * (mixed precision) the fused smoother with the same four schedules and 1 to
+ * 4 inner cycles.  Each
  * candidate builds its own plan, runs
  * one untimed solve and `repeats` (1..16) timed ones; the score is the median
  * wall time of the solve call.  Results in *out; phi_dev is overwritten.

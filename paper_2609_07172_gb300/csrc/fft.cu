@@ -137,22 +137,25 @@ __device__ __forceinline__ void fft_stages(double2 *buf, const double2 *__restri
     }
 }
 
-__device__ __forceinline__ double block_sum(double v, double *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
+// Sum of v over the block, valid in thread 0; sh holds blockDim doubles.  The
+// values go through shared memory and one warp adds them, so the reduction
+// issues about blockDim/32 + 5 FP64 additions per block instead of 5 per
+// thread.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    __syncthreads();   // a previous reduction may still be reading sh
+    sh[threadIdx.x] = v;
     __syncthreads();
     double s = 0.0;
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    if (threadIdx.x < 32) {
+        for (int j = threadIdx.x; j < (int)blockDim.x; j += 32) s += sh[j];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     }
     return s;
 }
 
 __global__ void __launch_bounds__(FFT_THREADS) k_forward(const FFTTab *__restrict__ tab, double *__restrict__ partials) {
     extern __shared__ double2 sm[];
-    __shared__ double red[FFT_THREADS / 32];
+    __shared__ double red[FFT_THREADS];
     const int pr = find_problem(tab->start, tab->n, blockIdx.x);
     const FFTProb P = tab->p[pr];
     const int nr = P.nr, nt = P.nt, nz = P.nz;

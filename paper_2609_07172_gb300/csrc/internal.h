@@ -214,6 +214,26 @@ inline unsigned smooth_blocks(int nr, int nz, int nm, int strip, int threads) {
     const unsigned s0 = (unsigned)(((nz + 1) / 2 + strip - 1) / strip), s1 = (unsigned)((nz / 2 + strip - 1) / strip);
     return (s0 + s1) * bx;
 }
+// Fused multi-sweep smoother of one FP32 level of one problem (fused.cu).
+struct FusedProb {
+    LevelDev<float> L;            // the level (coefficient tables, b_hat; L.u is not used)
+    const float2 *in;             // iterate before the half-sweeps
+    float2 *out;                  // iterate after them (another buffer)
+    int G, ngroups;               // modes per block, mode groups
+    int P, ntiles;                // column pairs per block (halo included), column tiles
+    int R, nkr;                   // output rows per block, row ranges
+};
+struct FusedTab {
+    int n;
+    unsigned start[kMaxBatch + 1];
+    FusedProb p[kMaxBatch];
+};
+constexpr int FUSED_THREADS = 256;
+// nh = 2 or 4 half-sweeps, red first.
+cudaError_t launch_smooth_fused(const FusedTab *tab, unsigned grid, int nh, cudaStream_t st);
+// Block shape and count for an nr x nz level with nm modes (about target_blocks blocks).
+void fused_shape(int nr, int nz, int nm, int nh, int target_blocks, FusedProb &f, unsigned &blocks);
+
 constexpr int FFT_TI = 32;        // radial columns per transform CTA
 constexpr int FFT_THREADS = 256;
 size_t fft_smem_bytes(int nt);

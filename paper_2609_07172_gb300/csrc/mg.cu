@@ -47,15 +47,19 @@ template <class T> __device__ __forceinline__ V2<T> fma2(T a, V2<T> x, V2<T> y) 
 // m = nt/2, 2 otherwise (the conjugate partner of m carries the same energy).
 __device__ __forceinline__ double parseval_w(int m, int nt) { return (m == 0 || 2 * m == nt) ? 1.0 : 2.0; }
 
-__device__ __forceinline__ double block_sum(double v, double *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
+// Sum of v over the block, valid in thread 0; sh holds blockDim doubles.  The
+// values go through shared memory and one warp adds them, so the reduction
+// issues about blockDim/32 + 5 FP64 additions per block instead of 5 per
+// thread.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    __syncthreads();   // a previous reduction may still be reading sh
+    sh[threadIdx.x] = v;
     __syncthreads();
     double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    if (threadIdx.x < 32) {
+        for (int j = threadIdx.x; j < (int)blockDim.x; j += 32) s += sh[j];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
     return s;
 }
 
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(NT) k_smooth(const LaunchTab<T> *__restrict__ 
 template <class T, bool RED_ONLY>
 __global__ void __launch_bounds__(MG_THREADS)
 k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ partials) {
-    __shared__ double red[MG_THREADS / 32];
+    __shared__ double red[MG_THREADS];
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     const LevelDev<T> F = tab->f[p];
     const LevelDev<T> C = tab->c[p];
@@ -275,7 +279,7 @@ k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ p
 template <class T>
 __global__ void __launch_bounds__(MG_THREADS)
 k_residual(const LaunchTab<T> *__restrict__ tab, int write_r, double *__restrict__ partials, unsigned stride) {
-    __shared__ double red[MG_THREADS / 32];
+    __shared__ double red[MG_THREADS];
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     const LevelDev<T> L = tab->f[p];
     const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
@@ -406,7 +410,7 @@ __device__ __forceinline__ int pow2_exponent(double v) { return ((__double2hiint
 template <bool ZERO_X>
 __global__ void __launch_bounds__(MG_THREADS)
 k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, double *__restrict__ partials) {
-    __shared__ double red[MG_THREADS / 32];
+    __shared__ double red[MG_THREADS];
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     const LevelDev<double> D = tab->d[p];
     const LevelDev<float> S = tab->s[p];
@@ -658,7 +662,7 @@ __global__ void __launch_bounds__(1024) k_check(Ctrl *__restrict__ ctrl, const d
 
 // Deterministic single-CTA sum of n partials (fixed order per thread, fixed tree).
 __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ p, int n, double *__restrict__ out) {
-    __shared__ double red[32];
+    __shared__ double red[1024];
     double s = 0.0;
     for (int f = threadIdx.x; f < n; f += blockDim.x) s += p[f];
     const double t = block_sum(s, red);

@@ -8,6 +8,8 @@
 #include <cstring>
 #include <new>
 
+#include <type_traits>
+
 #include "plan.h"
 
 namespace pp {
@@ -47,6 +49,11 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
     if (d->smooth_threads <= 0) d->smooth_threads = MG_THREADS;
     if (d->smooth_strip < 0) d->smooth_strip = 0;
     if (d->omega <= 0) d->omega = 1.0;
+    if (d->smooth_fused < 0) d->smooth_fused = 0;
+    if (d->smooth_fused > 1) {
+        set_error("smooth_fused must be 0 or 1 (got %d)", d->smooth_fused);
+        return PIC_POISSON_EINVAL;
+    }
     if (!(d->omega < 2.0)) {
         set_error("omega must be in (0, 2) (got %g)", d->omega);
         return PIC_POISSON_EINVAL;
@@ -303,10 +310,16 @@ template <class T> void carve_hier(pic_poisson_plan_s &P, Carver &c, Hier<T> &H)
     H.smooth.assign(nl, nullptr);
     H.restr.assign(nl, nullptr);
     H.prolong.assign(nl, nullptr);
+    H.fpre.assign(nl, nullptr);
+    H.fpost.assign(nl, nullptr);
     for (int l = 0; l < nl; ++l) {
         H.smooth[l] = c.take<LaunchTab<T>>(1);
         H.restr[l] = c.take<LaunchTab<T>>(1);
         H.prolong[l] = c.take<LaunchTab<T>>(1);
+        if (H.fused) {
+            H.fpre[l] = c.take<FusedTab>(1);
+            H.fpost[l] = c.take<FusedTab>(1);
+        }
     }
     H.coarse = c.take<CoarseTab<T>>(1);
 }
@@ -328,6 +341,10 @@ void carve(pic_poisson_plan_s &P, Carver &c) {
             carve_level<float, float2>(q.lv[l], q.nm, nt, c, q.fl[l]);
             q.fl[l].relax = (float)(1.0 - q.d.omega);
         }
+        q.u2.assign(q.fl.size(), nullptr);
+        if (P.h32.fused)
+            for (int l = 0; l + 1 < (int)q.fl.size(); ++l)
+                q.u2[l] = c.take<float2>((size_t)q.lv[l].nr * q.lv[l].nz * q.nm);
         if (mixed) carve_coarse(q, c, q.cf);
         else carve_coarse(q, c, q.cd);
         const int M = nt / 2;
@@ -393,8 +410,15 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
     H.g_restr.assign(nl, 0);
     H.g_prolong.assign(nl, 0);
     H.strip.assign(nl, 1);
+    H.g_fpre.assign(nl, 0);
+    H.g_fpost.assign(nl, 0);
     for (int l = 0; l < nl; ++l) {
         LaunchTab<T> ts{}, tr{}, tp{};
+        FusedTab fa{}, fb{};
+        int nprob = 0;
+        for (int p = 0; p < P.n; ++p) nprob += l < P.pr[p].L - 1;
+        // fused smoother blocks per problem: one wave of two blocks per SM
+        const int target = std::max(1, 2 * 152 / std::max(nprob, 1));
         // smoother strip (0: one entry per thread); a strip longer than the
         // level's rows of one parity is cut to the next power of two that fits
         int strip = P.shared.smooth_strip;
@@ -420,10 +444,35 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
             tr.f[tr.n] = f;
             tr.c[tr.n] = v[l + 1];
             tr.start[tr.n + 1] = tr.start[tr.n] + mg_blocks(coarse_n);
-            ++tr.n;
             tp.f[tp.n] = f;
             tp.c[tp.n] = v[l + 1];
             tp.start[tp.n + 1] = tp.start[tp.n] + mg_blocks(post > 0 && P.shared.omega == 1.0 ? half : full);
+            if constexpr (std::is_same<T, float>::value) {
+                if (H.fused) {
+                    // pre-smoothing u -> u2; the restriction reads u2 and the
+                    // prolongation corrects u2; post-smoothing u2 -> u
+                    tr.f[tr.n].u = q.u2[l];
+                    tp.f[tp.n].u = q.u2[l];
+                    unsigned nb = 0;
+                    FusedProb a{};
+                    a.L = f;
+                    a.in = f.u;
+                    a.out = q.u2[l];
+                    fused_shape(f.nr, f.nz, f.nm, 2 * pre, target, a, nb);
+                    fa.p[fa.n] = a;
+                    fa.start[fa.n + 1] = fa.start[fa.n] + nb;
+                    ++fa.n;
+                    FusedProb b{};
+                    b.L = f;
+                    b.in = q.u2[l];
+                    b.out = f.u;
+                    fused_shape(f.nr, f.nz, f.nm, 2 * post, target, b, nb);
+                    fb.p[fb.n] = b;
+                    fb.start[fb.n + 1] = fb.start[fb.n] + nb;
+                    ++fb.n;
+                }
+            }
+            ++tr.n;
             ++tp.n;
         }
         H.g_smooth[l] = ts.start[ts.n];
@@ -436,6 +485,12 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
         blob_to_dev(ts, H.smooth[l], st, err);
         blob_to_dev(tr, H.restr[l], st, err);
         blob_to_dev(tp, H.prolong[l], st, err);
+        if (H.fused) {
+            H.g_fpre[l] = fa.start[fa.n];
+            H.g_fpost[l] = fb.start[fb.n];
+            blob_to_dev(fa, H.fpre[l], st, err);
+            blob_to_dev(fb, H.fpost[l], st, err);
+        }
     }
     CoarseTab<T> tc{};
     for (int p = 0; p < P.n; ++p) {
@@ -627,7 +682,8 @@ int upload(pic_poisson_plan_s &P) {
 int same_settings(const pic_poisson_desc &a, const pic_poisson_desc &b) {
     return a.precision == b.precision && a.max_cycles == b.max_cycles && a.pre_sweeps == b.pre_sweeps &&
            a.post_sweeps == b.post_sweeps && a.inner_cycles == b.inner_cycles && a.flags == b.flags &&
-           a.smooth_threads == b.smooth_threads && a.smooth_strip == b.smooth_strip && a.omega == b.omega;
+           a.smooth_threads == b.smooth_threads && a.smooth_strip == b.smooth_strip && a.omega == b.omega &&
+           a.smooth_fused == b.smooth_fused;
 }
 
 int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
@@ -643,14 +699,27 @@ int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
         if (rc) return rc;
         if (p == 0) P.shared = d;
         else if (!same_settings(P.shared, d)) {
-            set_error("problem %d: precision, max_cycles, sweeps, inner_cycles, smooth_threads, smooth_strip, omega "
-                      "and flags must match "
+            set_error("problem %d: precision, max_cycles, sweeps, inner_cycles, smooth_threads, smooth_strip, omega, "
+                      "smooth_fused and flags must match "
                       "problem 0", p);
             return PIC_POISSON_EINVAL;
         }
         rc = setup_problem(P.pr[p], d);
         if (rc) return rc;
         P.Lmax = std::max(P.Lmax, P.pr[p].L);
+    }
+    if (P.shared.smooth_fused) {
+        const pic_poisson_desc &s = P.shared;
+        bool ok = s.precision == PIC_POISSON_MIXED && s.omega == 1.0 && s.pre_sweeps >= 1 && s.pre_sweeps <= 2 &&
+                  s.post_sweeps >= 1 && s.post_sweeps <= 2;
+        for (const ProblemPlan &q : P.pr)
+            for (int l = 0; l + 1 < q.L; ++l) ok = ok && q.lv[l].nr % 2 == 0;
+        if (!ok) {
+            set_error("smooth_fused needs mixed precision, omega = 1, 1 or 2 pre- and post-sweeps and even nr on "
+                      "every smoothed level");
+            return PIC_POISSON_EINVAL;
+        }
+        P.h32.fused = true;
     }
     return PIC_POISSON_OK;
 }

@@ -13,6 +13,7 @@ struct ProblemPlan {
     std::vector<LevelHost> lv;
     std::vector<LevelDev<double>> dl;           // FP64 levels (all for FP64 plans, level 0 for mixed)
     std::vector<LevelDev<float>> fl;            // FP32 levels (mixed)
+    std::vector<float2 *> u2;                   // FP32 levels: second iterate buffer of the fused smoother
     CoarseDev<double> cd{};
     CoarseDev<float> cf{};
     const double *tw = nullptr, *tw2 = nullptr; // FFT twiddles
@@ -25,6 +26,9 @@ template <class T> struct Hier {
     std::vector<LaunchTab<T> *> smooth, restr, prolong;   // device tables (null when no problem takes part)
     std::vector<unsigned> g_smooth, g_restr, g_prolong;   // grids
     std::vector<int> strip;                               // smoother strip per level
+    bool fused = false;                                   // FP32 fused smoother (pre: u -> u2, post: u2 -> u)
+    std::vector<FusedTab *> fpre, fpost;
+    std::vector<unsigned> g_fpre, g_fpost;
     CoarseTab<T> *coarse = nullptr;
     unsigned g_coarse = 0;
     size_t smem_coarse = 0;

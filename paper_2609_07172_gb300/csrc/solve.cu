@@ -116,11 +116,23 @@ double fft_flops_all(const pic_poisson_plan_s &P, double *bytes3d) {
 // the kernel that initialised the level already performed the red half-sweep
 // from a zero iterate.  Half-sweep: 1.5 V, 14 flops per updated complex entry
 // (over-relaxed: 2 V, 18 flops -- the cell's own value is read and weighted).
+// With the fused FP32 smoother (H.fused) the sweeps of a pre- or
+// post-smoothing are one launch (pre: u -> u2, post: u2 -> u), starting red:
+// after a fused first red half-sweep from zero, repeating it gives the same
+// values, so skip_first_red needs no special case.  2 * sweeps half-sweeps
+// move 3 V (the iterate and b_hat read once, the iterate written once).
 template <class T>
-int smooth_level(Runner &R, const Hier<T> &H, int l, int sweeps, bool skip_first_red) {
+int smooth_level(Runner &R, const Hier<T> &H, int l, int sweeps, bool skip_first_red, bool post) {
     if (!H.smooth[l]) return PIC_POISSON_OK;
     const int ph = l == 0 ? PIC_POISSON_PHASE_SMOOTH : PIC_POISSON_PHASE_SMOOTH_COARSE;
     const double n = level_entries<T>(R.P, l);
+    if (H.fused) {
+        if (sweeps == 0) return PIC_POISSON_OK;
+        RUN(R, ph, launch_smooth_fused(post ? H.fpost[l] : H.fpre[l], post ? H.g_fpost[l] : H.g_fpre[l],
+                                       2 * sweeps, R.st));
+        R.account(ph, 3.0 * n * sizeof(V2<T>), 14.0 * sweeps * n);
+        return PIC_POISSON_OK;
+    }
     for (int s = 0; s < sweeps; ++s) {
         for (int color = (s == 0 && skip_first_red) ? 1 : 0; color < 2; ++color) {
             const bool sor = R.P.shared.omega != 1.0;
@@ -156,7 +168,7 @@ int descend_ascend(Runner &R, const Hier<T> &H) {
     pic_poisson_plan_s &P = R.P;
     const int nl = P.Lmax - 1, pre = P.shared.pre_sweeps, post = P.shared.post_sweeps;
     for (int l = 1; l < nl; ++l) {
-        int rc = smooth_level(R, H, l, pre, pre > 0);
+        int rc = smooth_level(R, H, l, pre, pre > 0, false);
         if (rc) return rc;
         rc = restrict_level(R, H, l, nullptr);
         if (rc) return rc;
@@ -173,7 +185,7 @@ int descend_ascend(Runner &R, const Hier<T> &H) {
         RUN(R, PIC_POISSON_PHASE_PROLONG, launch_prolong(H.prolong[l], H.g_prolong[l], black_only, R.st));
         const double n = level_entries<T>(P, l), frac = black_only ? 0.5 : 1.0;
         R.account(PIC_POISSON_PHASE_PROLONG, n * sizeof(V2<T>) * (0.25 + 2.0 * frac), 16.0 * frac * n);
-        int rc = smooth_level(R, H, l, post, false);
+        int rc = smooth_level(R, H, l, post, false, true);
         if (rc) return rc;
     }
     return PIC_POISSON_OK;
@@ -230,7 +242,7 @@ int enqueue_prologue(Runner &R, int guess) {
     }
     if (mixed) return mixed_defect_and_check(R, 0, guess == 0);
     if (P.Lmax > 1) {
-        int rc = smooth_level(R, P.h64, 0, P.shared.pre_sweeps, false);
+        int rc = smooth_level(R, P.h64, 0, P.shared.pre_sweeps, false, false);
         if (rc) return rc;
     }
     return fp64_residual_and_check(R, 0);
@@ -247,14 +259,14 @@ int enqueue_body(Runner &R) {
         int rc = descend_ascend(R, P.h64);
         if (rc) return rc;
         if (P.Lmax > 1) {
-            rc = smooth_level(R, P.h64, 0, pre, false);
+            rc = smooth_level(R, P.h64, 0, pre, false, false);
             if (rc) return rc;
         }
         return fp64_residual_and_check(R, 1);
     }
     for (int c = 0; c < P.shared.inner_cycles; ++c) {
         if (P.Lmax > 1) {
-            int rc = smooth_level(R, P.h32, 0, pre, c == 0 && pre > 0);
+            int rc = smooth_level(R, P.h32, 0, pre, c == 0 && pre > 0, false);
             if (rc) return rc;
             rc = restrict_level(R, P.h32, 0, nullptr);
             if (rc) return rc;
