@@ -318,6 +318,7 @@ def run_ours(args):
                                   "omega", "smooth_fused") if k in t}, t
 
     kw, tuned = tuned_kw(prec)
+    schedules = {args.precision: kw}
     # headline: each solve one CUDA graph (device-side convergence loop)
     plan = Plan(p, precision=prec, graph=True, **kw)
     ms_total, infos, clocks = time_form(plan, rhos, phi, args.steps, args.warmup, args.tol, world, dist,
@@ -392,6 +393,7 @@ def run_ours(args):
         other = MIXED if prec == FP64 else FP64
         name = "mixed" if other == MIXED else "fp64"
         kw2, _ = tuned_kw(other)
+        schedules[name] = kw2
         plan2 = Plan(p, precision=other, graph=True, **kw2)
         steps2 = max(4, args.steps // 2)
         phi2 = torch.empty_like(phi)
@@ -422,7 +424,7 @@ def run_ours(args):
     if not args.no_batch:
         line["batch_uneven"] = run_batch(args, dev)
     if not args.no_sequence:
-        line["sequence"] = run_sequence(args, dev, p)
+        line["sequence"] = run_sequence(args, dev, p, schedules)
     if args.learned:
         line["learned_warm_start"] = run_learned(args, dev, p)
 
@@ -487,18 +489,20 @@ def run_batch(args, dev):
             "autotune_candidates": len(tuned.get("tried", [])) or None}
 
 
-def run_sequence(args, dev, p):
+def run_sequence(args, dev, p, schedules):
     """Drifting m = 8 wave (one azimuthal cell per step) at the headline grid,
     solved back to back with the previous step's potential as initial guess,
-    against the zero initial guess, both graph-captured."""
+    against the zero initial guess, both graph-captured with the form's tuned
+    schedule."""
     import torch
     from paper_2609_07172_gb300 import FP64, MIXED, Plan
     from paper_2609_07172_gb300 import workloads as W
     out = {"workload": "%dx%dx%d drifting m=8 wave, %d steps, GPU-drawn Poisson counts (seeded)"
                        % (p.nr, p.ntheta, p.nz, args.sequence_steps), "tol": args.tol}
     for name, prec in (("fp64", FP64), ("mixed", MIXED)):
-        warm = Plan(p, precision=prec, graph=True, initial_guess=True)
-        zero = Plan(p, precision=prec, graph=True)
+        kw = schedules.get(name, {})
+        warm = Plan(p, precision=prec, graph=True, initial_guess=True, **kw)
+        zero = Plan(p, precision=prec, graph=True, **kw)
         phi = torch.zeros(p.shape, dtype=torch.float64, device=dev)
         tmp = torch.empty_like(phi)
         ms_w = ms_z = 0.0
@@ -522,7 +526,8 @@ def run_sequence(args, dev, p):
                 ms_z += e0.elapsed_time(e1)
                 cyc_z.append(iz["cycles"])
         n = args.sequence_steps - 1
-        out[name] = {"ms_per_step_prev_guess": ms_w / n, "cycles_per_step_prev_guess": sum(cyc_w) / n,
+        out[name] = {"schedule": kw or "defaults",
+                     "ms_per_step_prev_guess": ms_w / n, "cycles_per_step_prev_guess": sum(cyc_w) / n,
                      "ms_per_step_zero_guess": ms_z / len(cyc_z), "cycles_per_step_zero_guess":
                          sum(cyc_z) / len(cyc_z), "zero_guess_sampled_steps": len(cyc_z)}
         warm.close()

@@ -65,6 +65,7 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 
 constexpr int DEPTH = 8;          // rows in flight ahead of the window
 constexpr int RING = DEPTH + 1;   // ring slots (the slot being refilled is never the one just read)
+constexpr int PAD = 16;           // >= the largest mode group: neighbour reads of the outermost pairs stay in the array
 
 template <int NH>
 __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTab *__restrict__ tab) {
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
     constexpr int NT = FUSED_THREADS;
     extern __shared__ float2 dsm[];
     float2 *ring = dsm;                   // [RING][4][NT]: u col 0, u col 1, b_hat col 0, b_hat col 1
-    float2 *pubs = dsm + RING * 4 * NT;   // [2][NH][NT]
+    float2 *pubs = dsm + RING * 4 * NT + PAD;   // [2][NH][NT + 2 PAD], PAD entries before each row
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     const FusedProb &F = tab->p[p];
     const LevelDev<float> &L = F.L;
@@ -106,14 +107,15 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
     const float hz1 = L.hz[cls1 + c1], hw1 = L.hw[cls1 + c1], he1 = L.he[cls1 + c1];
 
     // fetch row `row` into ring slot `slot` (zeros for rows outside [ks, ke) and invalid cells)
+    const float2 *gin0 = F.in + c0, *gin1 = F.in + c1, *gb0 = L.bh + c0, *gb1 = L.bh + c1;
     auto fetch = [&](int row, int slot) {
         const bool ok = row < ke;
         const size_t o = (size_t)(ok ? row : ks) * rs;
-        float2 *r = ring + (size_t)slot * 4 * NT + t;
-        cp_async8(r, F.in + o + c0, ok && v0);
-        cp_async8(r + NT, F.in + o + c1, ok && v1);
-        cp_async8(r + 2 * NT, L.bh + o + c0, ok && v0);
-        cp_async8(r + 3 * NT, L.bh + o + c1, ok && v1);
+        float2 *r = ring + slot * 4 * NT + t;
+        cp_async8(r, gin0 + o, ok && v0);
+        cp_async8(r + NT, gin1 + o, ok && v1);
+        cp_async8(r + 2 * NT, gb0 + o, ok && v0);
+        cp_async8(r + 3 * NT, gb1 + o, ok && v1);
         cp_async_commit();
     };
 #pragma unroll
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
             // (a) row k from the ring into window slot ph; fetch row k + DEPTH
             cp_async_wait<DEPTH - 1>();
             {
-                const float2 *r = ring + (size_t)rslot * 4 * NT + t;
+                const float2 *r = ring + rslot * 4 * NT + t;
                 u0[ph] = r[0];
                 u1[ph] = r[NT];
                 b0[ph] = r[2 * NT];
@@ -155,10 +157,16 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                 const int ss = (ph - 2 - s + 2 * W) % W;   // row r - 1
                 const int q = (r + (s & 1)) & 1;           // the pair's cell of this colour (uniform)
                 const bool edge = r == 0 || r == nz - 1;
-                const float2 *pr = pubs + (size_t)((buf ^ 1) * NH + s) * NT;
+                const float2 *pr = pubs + (size_t)((buf ^ 1) * NH + s) * (NT + 2 * PAD);
+                // Rows outside the level are zero in the window and the wall
+                // columns have zero coefficients towards the wall (h_w = 0 at
+                // i = 0, h_e = 0 at i = nr - 1), so every update is the same
+                // four multiply-adds per part -- the neighbour that does not
+                // exist contributes exactly zero, as when it is left out.
+                // The pair beyond a block's outermost pair reads padding
+                // (halo cells only).
                 if (q == 0) {
-                    const float2 S = r > 0 ? u0[ss] : zero, N = r < nz - 1 ? u0[sn] : zero;
-                    const float2 vs = make_float2(S.x + N.x, S.y + N.y);
+                    const float2 vs = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
                     float hz = hz0, hw = hw0, he = he0;
                     if (edge) {
                         const size_t tb = (size_t)row_class(r, nz, ncls) * rs + c0;
@@ -166,16 +174,13 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                         hw = L.hw[tb];
                         he = L.he[tb];
                     }
+                    const float2 uw = pr[t - G];   // west: column 1 of the pair on the left
                     float2 acc = make_float2(fmaf(hz, vs.x, b0[sl].x), fmaf(hz, vs.y, b0[sl].y));
-                    if (i0 > 0) {   // west: column 1 of the pair on the left (from the previous step)
-                        const float2 uw = pl > 0 ? pr[t - G] : zero;
-                        acc = make_float2(fmaf(hw, uw.x, acc.x), fmaf(hw, uw.y, acc.y));
-                    }
-                    if (i0 < nr - 1) acc = make_float2(fmaf(he, u1[sl].x, acc.x), fmaf(he, u1[sl].y, acc.y));
+                    acc = make_float2(fmaf(hw, uw.x, acc.x), fmaf(hw, uw.y, acc.y));
+                    acc = make_float2(fmaf(he, u1[sl].x, acc.x), fmaf(he, u1[sl].y, acc.y));
                     if (v0) u0[sl] = acc;
                 } else {
-                    const float2 S = r > 0 ? u1[ss] : zero, N = r < nz - 1 ? u1[sn] : zero;
-                    const float2 vs = make_float2(S.x + N.x, S.y + N.y);
+                    const float2 vs = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
                     float hz = hz1, hw = hw1, he = he1;
                     if (edge) {
                         const size_t tb = (size_t)row_class(r, nz, ncls) * rs + c1;
@@ -183,23 +188,21 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                         hw = L.hw[tb];
                         he = L.he[tb];
                     }
+                    const float2 ue = pr[t + G];   // east: column 0 of the pair on the right
                     float2 acc = make_float2(fmaf(hz, vs.x, b1[sl].x), fmaf(hz, vs.y, b1[sl].y));
-                    acc = make_float2(fmaf(hw, u0[sl].x, acc.x), fmaf(hw, u0[sl].y, acc.y));   // i1 > 0 always
-                    if (i1 < nr - 1) {   // east: column 0 of the pair on the right
-                        const float2 ue = pl < P - 1 ? pr[t + G] : zero;
-                        acc = make_float2(fmaf(he, ue.x, acc.x), fmaf(he, ue.y, acc.y));
-                    }
+                    acc = make_float2(fmaf(hw, u0[sl].x, acc.x), fmaf(hw, u0[sl].y, acc.y));
+                    acc = make_float2(fmaf(he, ue.x, acc.x), fmaf(he, ue.y, acc.y));
                     if (v1) u1[sl] = acc;
                 }
             }
             // (c) publish for the next step: half-sweep s will update row k - s
             // and read the neighbouring pair's column of the other colour
-            float2 *pw = pubs + (size_t)(buf * NH) * NT + t;
+            float2 *pw = pubs + (size_t)(buf * NH) * (NT + 2 * PAD) + t;
 #pragma unroll
             for (int s = 0; s < NH; ++s) {
                 const int sl = (ph - s + 2 * W) % W;
                 const int qn = (k - s + (s & 1)) & 1;
-                pw[(size_t)s * NT] = qn == 0 ? u1[sl] : u0[sl];
+                pw[(size_t)s * (NT + 2 * PAD)] = qn == 0 ? u1[sl] : u0[sl];
             }
             // (d) the output row k - NH is final
             const int ro = k - NH;
@@ -219,7 +222,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
 }  // namespace
 
 template <int NH> cudaError_t launch_nh(const FusedTab *tab, unsigned grid, cudaStream_t st) {
-    const size_t smem = (size_t)(RING * 4 + 2 * NH) * FUSED_THREADS * sizeof(float2);
+    const size_t smem = ((size_t)RING * 4 * FUSED_THREADS + PAD + (size_t)2 * NH * (FUSED_THREADS + 2 * PAD)) *
+                        sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_smooth_fused<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_smooth_fused<NH><<<grid, FUSED_THREADS, smem, st>>>(tab);

@@ -122,7 +122,7 @@ __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i,
 // SOR: over-relaxation u <- (1 - omega) u + omega u_GS, the tables carrying
 // omega (one more load and multiply-add per component); otherwise omega = 1.
 template <class T, int NT, int S, bool SOR>
-__global__ void __launch_bounds__(NT) k_smooth(const LaunchTab<T> *__restrict__ tab, int color) {
+__global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const LaunchTab<T> *__restrict__ tab, int color) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     const LevelDev<T> L = tab->f[p];
     const unsigned nm = L.nm;
