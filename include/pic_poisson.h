@@ -121,7 +121,7 @@ typedef struct {
     double flops_phase[PIC_POISSON_NPHASE];/* algorithmic floating-point operations per kernel class */
 } pic_poisson_info;
 
-#define PIC_POISSON_MAX_TUNE 64
+#define PIC_POISSON_MAX_TUNE 96
 
 typedef struct {
     int pre_sweeps, post_sweeps;           /* best smoothing schedule */
@@ -225,7 +225,7 @@ int pic_poisson_solve_batch(pic_poisson_plan_t plan, const double *const *rho_de
  * over-relaxation omega = 1.1, 1.2, 1.3 with the schedules (1,1), (1,2),
  * (2,1), (2,2) at the best block size, strip and inner cycles; stage 5
  * (mixed precision) the fused smoother with the same four schedules and 1 to
- * 4 inner cycles.  Each
+ * 6 inner cycles.  Each
  * candidate builds its own plan, runs
  * one untimed solve and `repeats` (1..16) timed ones; the score is the median
  * wall time of the solve call.  Results in *out; phi_dev is overwritten.

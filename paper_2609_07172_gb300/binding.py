@@ -73,7 +73,7 @@ class Info(ctypes.Structure):
         }
 
 
-MAX_TUNE = 64
+MAX_TUNE = 96
 
 
 class Tuning(ctypes.Structure):

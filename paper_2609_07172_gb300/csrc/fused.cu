@@ -29,9 +29,10 @@
 // half-sweeps (same operations, same order per cell).
 //
 // Latency.  Each step needs the next row from HBM; rows are fetched DEPTH
-// steps ahead with cp.async into a shared-memory ring (zero-filled beyond
-// the level), so a thread's window registers are filled from shared memory
-// and DEPTH rows of loads stay in flight.
+// steps ahead with cp.async into shared-memory rings (zero-filled beyond the
+// level): the iterate's into a short ring read into the window registers,
+// b_hat (and b) into a ring that keeps each row until its last half-sweep,
+// so those values take no registers.
 #include <algorithm>
 
 #include "internal.h"
@@ -63,18 +64,37 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-constexpr int DEPTH = 8;          // rows in flight ahead of the window
-constexpr int RING = DEPTH + 1;   // ring slots (the slot being refilled is never the one just read)
+constexpr int DEPTH = 4;          // rows in flight ahead of the window
+constexpr int UR = DEPTH + 1;     // iterate ring slots (the slot refilled is never the one just read)
 constexpr int PAD = 16;           // >= the largest mode group: neighbour reads of the outermost pairs stay in the array
 
-template <int NH>
+// Slots of the ring that holds b_hat (and b) per row: a row's entries are read
+// by half-sweeps up to NH steps after it entered (the restriction NH + 1).
+template <int NH> __host__ __device__ constexpr int b_ring() { return DEPTH + NH + 2; }
+template <int NH, bool RES> constexpr size_t fused_smem_floats2() {
+    return (size_t)UR * 2 * FUSED_THREADS + (size_t)b_ring<NH>() * (RES ? 3 : 2) * FUSED_THREADS + PAD +
+           (size_t)2 * (NH + (RES ? 1 : 0)) * (FUSED_THREADS + 2 * PAD);
+}
+
+// RES (pre-smoothing of a level coarsened 2:1 in both directions): after the
+// last half-sweep, the kernel also evaluates the residual of the red cells
+// -- the black ones vanish after a black half-sweep -- and sums the two red
+// cells of each 2x2 block into the coarse right-hand side, exactly as
+// k_residual_restrict<float, RED_ONLY> (same operations in the same order).
+// The residual of row r needs the final values of rows r +- 1 and of the
+// neighbouring columns, so the halo grows by one row and one column pair.
+template <int NH, bool RES>
 __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTab *__restrict__ tab) {
-    constexpr int W = NH + 2;      // window rows: k-NH-1 .. k
-    constexpr int HP = NH / 2;     // halo pairs on each side
+    constexpr int W = NH + 2 + (RES ? 1 : 0);   // window rows: k-W+1 .. k
+    constexpr int HP = NH / 2 + (RES ? 1 : 0);  // halo pairs on each side
     constexpr int NT = FUSED_THREADS;
+    constexpr int NP = NH + (RES ? 1 : 0);      // published columns per step
+    constexpr int BR = b_ring<NH>();
+    constexpr int NB = RES ? 3 : 2;             // b_hat col 0, b_hat col 1 (, b of the red cell)
     extern __shared__ float2 dsm[];
-    float2 *ring = dsm;                   // [RING][4][NT]: u col 0, u col 1, b_hat col 0, b_hat col 1
-    float2 *pubs = dsm + RING * 4 * NT + PAD;   // [2][NH][NT + 2 PAD], PAD entries before each row
+    float2 *uring = dsm;                            // [UR][2][NT]
+    float2 *bring = uring + UR * 2 * NT;            // [BR][NB][NT]
+    float2 *pubs = bring + BR * NB * NT + PAD;      // [2][NP][NT + 2 PAD], PAD entries before each row
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     const FusedProb &F = tab->p[p];
     const LevelDev<float> &L = F.L;
@@ -95,9 +115,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
     const int i0 = 2 * j, i1 = 2 * j + 1;
     const bool v0 = mvalid && i0 >= 0 && i0 < nr, v1 = mvalid && i1 >= 0 && i1 < nr;
     const bool outpair = pl >= HP && pl < P - HP;
+    const int hr = NH + (RES ? 1 : 0);                       // halo rows
     const int k0 = kr * F.R, k1 = min(nz, k0 + F.R);
-    const int ks = max(0, k0 - NH), ke = min(nz, k1 + NH);   // rows read: [ks, ke)
-    const int klast = k1 - 1 + NH;                           // last step (its output row is k1 - 1)
+    const int ks = max(0, k0 - hr), ke = min(nz, k1 + hr);  // rows read: [ks, ke)
+    const int klast = k1 - 1 + hr;                           // last step
 
     const size_t rs = (size_t)nr * nm;
     const size_t c0 = (size_t)(v0 ? i0 : 0) * nm + (mvalid ? m : 0);
@@ -106,47 +127,62 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
     const float hz0 = L.hz[cls1 + c0], hw0 = L.hw[cls1 + c0], he0 = L.he[cls1 + c0];
     const float hz1 = L.hz[cls1 + c1], hw1 = L.hw[cls1 + c1], he1 = L.he[cls1 + c1];
 
-    // fetch row `row` into ring slot `slot` (zeros for rows outside [ks, ke) and invalid cells)
+    // fetch row `row` into ring slots (zeros for rows outside [ks, ke) and invalid cells)
     const float2 *gin0 = F.in + c0, *gin1 = F.in + c1, *gb0 = L.bh + c0, *gb1 = L.bh + c1;
-    auto fetch = [&](int row, int slot) {
+    auto fetch = [&](int row, int us, int bs) {
         const bool ok = row < ke;
         const size_t o = (size_t)(ok ? row : ks) * rs;
-        float2 *r = ring + slot * 4 * NT + t;
-        cp_async8(r, gin0 + o, ok && v0);
-        cp_async8(r + NT, gin1 + o, ok && v1);
-        cp_async8(r + 2 * NT, gb0 + o, ok && v0);
-        cp_async8(r + 3 * NT, gb1 + o, ok && v1);
+        float2 *ru = uring + us * 2 * NT + t;
+        float2 *rb = bring + bs * NB * NT + t;
+        cp_async8(ru, gin0 + o, ok && v0);
+        cp_async8(ru + NT, gin1 + o, ok && v1);
+        cp_async8(rb, gb0 + o, ok && v0);
+        cp_async8(rb + NT, gb1 + o, ok && v1);
+        if (RES) {   // b of the row's red cell: column parity = row parity
+            const bool q1 = (row & 1) != 0;
+            cp_async8(rb + 2 * NT, L.b + o + (q1 ? c1 : c0), ok && (q1 ? v1 : v0));
+        }
         cp_async_commit();
     };
 #pragma unroll
-    for (int d = 0; d < DEPTH; ++d) fetch(ks + d, d);
+    for (int d = 0; d < DEPTH; ++d) fetch(ks + d, d, d);
+
+    // residual coefficients of the pair's columns (RES)
+    float cz0 = 0.f, cw0 = 0.f, ce0 = 0.f, dg0 = 0.f, cz1 = 0.f, cw1 = 0.f, ce1 = 0.f, dg1 = 0.f;
+    if (RES) {
+        const int ii0 = v0 ? i0 : 0, ii1 = v1 ? i1 : 0;
+        cz0 = L.cz[ii0];
+        cw0 = L.cw[ii0];
+        ce0 = L.ce[ii0];
+        dg0 = L.diag[cls1 + c0];
+        cz1 = L.cz[ii1];
+        cw1 = L.cw[ii1];
+        ce1 = L.ce[ii1];
+        dg1 = L.diag[cls1 + c1];
+    }
+    float2 rsum = make_float2(0.f, 0.f);   // residual of the even row of a coarse cell (RES)
 
     const float2 zero = make_float2(0.f, 0.f);
-    float2 u0[W], u1[W], b0[W], b1[W];
+    float2 u0[W], u1[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) u0[w] = u1[w] = b0[w] = b1[w] = zero;
+    for (int w = 0; w < W; ++w) u0[w] = u1[w] = zero;
     int buf = 0;
-    int rslot = 0;   // ring slot of the row entering now
+    int uslot = 0, bslot = 0;   // ring slots of the row entering now
     for (int kb = ks; kb <= klast; kb += W) {
 #pragma unroll
         for (int ph = 0; ph < W; ++ph) {
             const int k = kb + ph;   // the row entering at this step
             if (k > klast) break;    // uniform over the block
-            // (a) row k from the ring into window slot ph; fetch row k + DEPTH
+            // (a) row k into window slot ph; fetch row k + DEPTH
             cp_async_wait<DEPTH - 1>();
+            u0[ph] = uring[uslot * 2 * NT + t];
+            u1[ph] = uring[uslot * 2 * NT + NT + t];
             {
-                const float2 *r = ring + rslot * 4 * NT + t;
-                u0[ph] = r[0];
-                u1[ph] = r[NT];
-                b0[ph] = r[2 * NT];
-                b1[ph] = r[3 * NT];
+                int us = uslot + DEPTH, bs = bslot + DEPTH;
+                if (us >= UR) us -= UR;
+                if (bs >= BR) bs -= BR;
+                fetch(k + DEPTH, us, bs);
             }
-            {
-                int fs = rslot + DEPTH;
-                if (fs >= RING) fs -= RING;
-                fetch(k + DEPTH, fs);
-            }
-            rslot = rslot + 1 == RING ? 0 : rslot + 1;
             // (b) half-sweep s on row k - 1 - s
 #pragma unroll
             for (int s = 0; s < NH; ++s) {
@@ -157,7 +193,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                 const int ss = (ph - 2 - s + 2 * W) % W;   // row r - 1
                 const int q = (r + (s & 1)) & 1;           // the pair's cell of this colour (uniform)
                 const bool edge = r == 0 || r == nz - 1;
-                const float2 *pr = pubs + (size_t)((buf ^ 1) * NH + s) * (NT + 2 * PAD);
+                const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + s) * (NT + 2 * PAD);
+                int rb = bslot - 1 - s;
+                if (rb < 0) rb += BR;
+                const float2 *bh = bring + rb * NB * NT + t;
                 // Rows outside the level are zero in the window and the wall
                 // columns have zero coefficients towards the wall (h_w = 0 at
                 // i = 0, h_e = 0 at i = nr - 1), so every update is the same
@@ -175,7 +214,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                         he = L.he[tb];
                     }
                     const float2 uw = pr[t - G];   // west: column 1 of the pair on the left
-                    float2 acc = make_float2(fmaf(hz, vs.x, b0[sl].x), fmaf(hz, vs.y, b0[sl].y));
+                    const float2 b = bh[0];
+                    float2 acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
                     acc = make_float2(fmaf(hw, uw.x, acc.x), fmaf(hw, uw.y, acc.y));
                     acc = make_float2(fmaf(he, u1[sl].x, acc.x), fmaf(he, u1[sl].y, acc.y));
                     if (v0) u0[sl] = acc;
@@ -189,31 +229,86 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                         he = L.he[tb];
                     }
                     const float2 ue = pr[t + G];   // east: column 0 of the pair on the right
-                    float2 acc = make_float2(fmaf(hz, vs.x, b1[sl].x), fmaf(hz, vs.y, b1[sl].y));
+                    const float2 b = bh[NT];
+                    float2 acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
                     acc = make_float2(fmaf(hw, u0[sl].x, acc.x), fmaf(hw, u0[sl].y, acc.y));
                     acc = make_float2(fmaf(he, ue.x, acc.x), fmaf(he, ue.y, acc.y));
                     if (v1) u1[sl] = acc;
                 }
             }
-            // (c) publish for the next step: half-sweep s will update row k - s
-            // and read the neighbouring pair's column of the other colour
-            float2 *pw = pubs + (size_t)(buf * NH) * (NT + 2 * PAD) + t;
+            // (c) residual of the red cell of row k - NH - 1 and the coarse
+            // right-hand side of its 2x2 block (RES)
+            if (RES) {
+                const int rr = k - NH - 1;
+                if (rr >= k0 && rr < k1) {   // uniform
+                    const int sl = (ph - NH - 1 + 2 * W) % W, sn = (ph - NH + 2 * W) % W, ss = (ph - NH - 2 + 2 * W) % W;
+                    const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + NH) * (NT + 2 * PAD);
+                    int rb = bslot - NH - 1;
+                    if (rb < 0) rb += BR;
+                    const float2 bred = bring[rb * NB * NT + 2 * NT + t];
+                    const bool edge = rr == 0 || rr == nz - 1;
+                    float2 res;
+                    if ((rr & 1) == 0) {   // red cell in column 0: west from the left pair
+                        const float d = edge ? L.diag[(size_t)row_class(rr, nz, ncls) * rs + c0] : dg0;
+                        const float2 s = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
+                        const float2 uw = pr[t - G];
+                        float2 a = make_float2(fmaf(cz0, s.x, bred.x), fmaf(cz0, s.y, bred.y));
+                        a = make_float2(fmaf(cw0, uw.x, a.x), fmaf(cw0, uw.y, a.y));
+                        a = make_float2(fmaf(ce0, u1[sl].x, a.x), fmaf(ce0, u1[sl].y, a.y));
+                        res = make_float2(fmaf(-d, u0[sl].x, a.x), fmaf(-d, u0[sl].y, a.y));
+                        rsum = res;
+                    } else {               // red cell in column 1: east from the right pair
+                        const float d = edge ? L.diag[(size_t)row_class(rr, nz, ncls) * rs + c1] : dg1;
+                        const float2 s = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
+                        const float2 ue = pr[t + G];
+                        float2 a = make_float2(fmaf(cz1, s.x, bred.x), fmaf(cz1, s.y, bred.y));
+                        a = make_float2(fmaf(cw1, u0[sl].x, a.x), fmaf(cw1, u0[sl].y, a.y));
+                        a = make_float2(fmaf(ce1, ue.x, a.x), fmaf(ce1, ue.y, a.y));
+                        res = make_float2(fmaf(-d, u1[sl].x, a.x), fmaf(-d, u1[sl].y, a.y));
+                        const float2 sum = make_float2(rsum.x + res.x, rsum.y + res.y);
+                        const LevelDev<float> &C = F.C;
+                        if (outpair && v0 && j < C.nr) {
+                            const int K = rr >> 1;
+                            const size_t e = ((size_t)K * C.nr + j) * C.nm + m;
+                            C.b[e] = sum;
+                            if (F.init > 0) {
+                                const float inv =
+                                    C.invd[((size_t)row_class(K, C.nz, C.ncls) * C.nr + j) * C.nm + m];
+                                const float2 bhc = make_float2(sum.x * inv, sum.y * inv);
+                                C.bh[e] = bhc;
+                                C.u[e] = (F.init == 2 && ((K + j) & 1) == 0) ? bhc : zero;
+                            }
+                        }
+                    }
+                }
+            }
+            // (d) publish for the next step: half-sweep s will update row k - s
+            // and read the neighbouring pair's column of the other colour;
+            // the restriction reads the final black column of row k - NH
+            float2 *pw = pubs + (size_t)(buf * NP) * (NT + 2 * PAD) + t;
 #pragma unroll
             for (int s = 0; s < NH; ++s) {
                 const int sl = (ph - s + 2 * W) % W;
                 const int qn = (k - s + (s & 1)) & 1;
                 pw[(size_t)s * (NT + 2 * PAD)] = qn == 0 ? u1[sl] : u0[sl];
             }
-            // (d) the output row k - NH is final
+            if (RES) {
+                const int sl = (ph - NH + 2 * W) % W;
+                const int qn = (k - NH) & 1;   // red column of row k - NH
+                pw[(size_t)NH * (NT + 2 * PAD)] = qn == 0 ? u1[sl] : u0[sl];
+            }
+            // (e) the output row k - NH is final
             const int ro = k - NH;
             if (outpair && ro >= k0 && ro < k1) {
-                const int so = (ph + 2) % W;   // (ph - NH) mod W
+                const int so = (ph - NH + 2 * W) % W;
                 const size_t o = (size_t)ro * rs;
                 if (v0) F.out[o + c0] = u0[so];
                 if (v1) F.out[o + c1] = u1[so];
             }
             __syncthreads();
             buf ^= 1;
+            uslot = uslot + 1 == UR ? 0 : uslot + 1;
+            bslot = bslot + 1 == BR ? 0 : bslot + 1;
         }
     }
     cp_async_wait<0>();   // no copy outlives the block
@@ -221,33 +316,36 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
 
 }  // namespace
 
-template <int NH> cudaError_t launch_nh(const FusedTab *tab, unsigned grid, cudaStream_t st) {
-    const size_t smem = ((size_t)RING * 4 * FUSED_THREADS + PAD + (size_t)2 * NH * (FUSED_THREADS + 2 * PAD)) *
-                        sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_smooth_fused<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int NH, bool RES> cudaError_t launch_nh(const FusedTab *tab, unsigned grid, cudaStream_t st) {
+    const size_t smem = fused_smem_floats2<NH, RES>() * sizeof(float2);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_smooth_fused<NH, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_smooth_fused<NH><<<grid, FUSED_THREADS, smem, st>>>(tab);
+    k_smooth_fused<NH, RES><<<grid, FUSED_THREADS, smem, st>>>(tab);
     return cudaGetLastError();
 }
 
-cudaError_t launch_smooth_fused(const FusedTab *tab, unsigned grid, int nh, cudaStream_t st) {
-    switch (nh) {
-    case 2: return launch_nh<2>(tab, grid, st);
-    case 4: return launch_nh<4>(tab, grid, st);
+cudaError_t launch_smooth_fused(const FusedTab *tab, unsigned grid, int nh, bool res, cudaStream_t st) {
+    switch (nh * 2 + (res ? 1 : 0)) {
+    case 4: return launch_nh<2, false>(tab, grid, st);
+    case 5: return launch_nh<2, true>(tab, grid, st);
+    case 8: return launch_nh<4, false>(tab, grid, st);
+    case 9: return launch_nh<4, true>(tab, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-void fused_shape(int nr, int nz, int nm, int nh, int target_blocks, FusedProb &f, unsigned &blocks) {
+void fused_shape(int nr, int nz, int nm, int nh, bool res, int target_blocks, FusedProb &f, unsigned &blocks) {
     f.ngroups = (nm + 15) / 16;
     f.G = (nm + f.ngroups - 1) / f.ngroups;
-    const int hp = nh / 2, pairs = nr / 2;
+    const int hp = nh / 2 + (res ? 1 : 0), pairs = nr / 2;
     f.P = std::min(FUSED_THREADS / f.G, pairs + 2 * hp);
     if (f.P < 2 * hp + 1) f.P = 2 * hp + 1;
     f.ntiles = (pairs + (f.P - 2 * hp) - 1) / (f.P - 2 * hp);
     const int per = f.ngroups * f.ntiles;
     int nkr = std::max(1, target_blocks / per);   // at most target_blocks: no partial last wave
     f.R = std::max(8, (nz + nkr - 1) / nkr);
+    f.R += f.R & 1;   // even: the two rows of a coarse cell belong to one block
     f.nkr = (nz + f.R - 1) / f.R;
     blocks = (unsigned)(per * f.nkr);
 }

@@ -217,6 +217,8 @@ inline unsigned smooth_blocks(int nr, int nz, int nm, int strip, int threads) {
 // Fused multi-sweep smoother of one FP32 level of one problem (fused.cu).
 struct FusedProb {
     LevelDev<float> L;            // the level (coefficient tables, b_hat; L.u is not used)
+    LevelDev<float> C;            // the next coarser level (restriction fused into pre-smoothing)
+    int init;                     // what the fused restriction writes into C (as LevelDev::init)
     const float2 *in;             // iterate before the half-sweeps
     float2 *out;                  // iterate after them (another buffer)
     int G, ngroups;               // modes per block, mode groups
@@ -229,10 +231,11 @@ struct FusedTab {
     FusedProb p[kMaxBatch];
 };
 constexpr int FUSED_THREADS = 256;
-// nh = 2 or 4 half-sweeps, red first.
-cudaError_t launch_smooth_fused(const FusedTab *tab, unsigned grid, int nh, cudaStream_t st);
+// nh = 2 or 4 half-sweeps, red first; res: also the red-cell residual and
+// its restriction into FusedProb::C (levels coarsened 2:1 in r and z).
+cudaError_t launch_smooth_fused(const FusedTab *tab, unsigned grid, int nh, bool res, cudaStream_t st);
 // Block shape and count for an nr x nz level with nm modes (about target_blocks blocks).
-void fused_shape(int nr, int nz, int nm, int nh, int target_blocks, FusedProb &f, unsigned &blocks);
+void fused_shape(int nr, int nz, int nm, int nh, bool res, int target_blocks, FusedProb &f, unsigned &blocks);
 
 constexpr int FFT_TI = 32;        // radial columns per transform CTA
 constexpr int FFT_THREADS = 256;

@@ -412,11 +412,19 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
     H.strip.assign(nl, 1);
     H.g_fpre.assign(nl, 0);
     H.g_fpost.assign(nl, 0);
+    H.fres.assign(nl, 0);
     for (int l = 0; l < nl; ++l) {
         LaunchTab<T> ts{}, tr{}, tp{};
         FusedTab fa{}, fb{};
         int nprob = 0;
-        for (int p = 0; p < P.n; ++p) nprob += l < P.pr[p].L - 1;
+        bool res = H.fused;   // restriction fused into pre-smoothing: every pair of levels halves r and z
+        for (int p = 0; p < P.n; ++p)
+            if (l < P.pr[p].L - 1) {
+                ++nprob;
+                const LevelHost &a = P.pr[p].lv[l], &b = P.pr[p].lv[l + 1];
+                res = res && b.nr * 2 == a.nr && b.nz * 2 == a.nz;
+            }
+        H.fres[l] = res;
         // fused smoother blocks per problem: one wave of two blocks per SM
         const int target = std::max(1, 2 * 152 / std::max(nprob, 1));
         // smoother strip (0: one entry per thread); a strip longer than the
@@ -456,9 +464,11 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
                     unsigned nb = 0;
                     FusedProb a{};
                     a.L = f;
+                    a.C = v[l + 1];
+                    a.init = f.init;
                     a.in = f.u;
                     a.out = q.u2[l];
-                    fused_shape(f.nr, f.nz, f.nm, 2 * pre, target, a, nb);
+                    fused_shape(f.nr, f.nz, f.nm, 2 * pre, res, target, a, nb);
                     fa.p[fa.n] = a;
                     fa.start[fa.n + 1] = fa.start[fa.n] + nb;
                     ++fa.n;
@@ -466,7 +476,7 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
                     b.L = f;
                     b.in = q.u2[l];
                     b.out = f.u;
-                    fused_shape(f.nr, f.nz, f.nm, 2 * post, target, b, nb);
+                    fused_shape(f.nr, f.nz, f.nm, 2 * post, false, target, b, nb);
                     fb.p[fb.n] = b;
                     fb.start[fb.n + 1] = fb.start[fb.n] + nb;
                     ++fb.n;

@@ -29,6 +29,7 @@ template <class T> struct Hier {
     bool fused = false;                                   // FP32 fused smoother (pre: u -> u2, post: u2 -> u)
     std::vector<FusedTab *> fpre, fpost;
     std::vector<unsigned> g_fpre, g_fpost;
+    std::vector<char> fres;                               // per level: pre-smoothing also restricts
     CoarseTab<T> *coarse = nullptr;
     unsigned g_coarse = 0;
     size_t smem_coarse = 0;

@@ -128,9 +128,12 @@ int smooth_level(Runner &R, const Hier<T> &H, int l, int sweeps, bool skip_first
     const double n = level_entries<T>(R.P, l);
     if (H.fused) {
         if (sweeps == 0) return PIC_POISSON_OK;
+        const bool res = !post && H.fres[l];
         RUN(R, ph, launch_smooth_fused(post ? H.fpost[l] : H.fpre[l], post ? H.g_fpost[l] : H.g_fpre[l],
-                                       2 * sweeps, R.st));
+                                       2 * sweeps, res, R.st));
         R.account(ph, 3.0 * n * sizeof(V2<T>), 14.0 * sweeps * n);
+        if (res)   // the fused restriction: b of the red cells, the coarse b, b_hat, u
+            R.account(PIC_POISSON_PHASE_RESTRICT, n * sizeof(V2<T>) * (0.5 + 0.75), 9.0 * n);
         return PIC_POISSON_OK;
     }
     for (int s = 0; s < sweeps; ++s) {
@@ -150,6 +153,7 @@ int smooth_level(Runner &R, const Hier<T> &H, int l, int sweeps, bool skip_first
 template <class T>
 int restrict_level(Runner &R, const Hier<T> &H, int l, double *partials) {
     if (!H.restr[l]) return PIC_POISSON_OK;
+    if (H.fused && H.fres[l] && !partials) return PIC_POISSON_OK;   // done by the fused pre-smoothing
     // after a Gauss-Seidel black half-sweep the black residuals vanish; an
     // over-relaxed one leaves them nonzero, so then every cell is evaluated
     const bool red_only = R.P.shared.pre_sweeps > 0 && R.P.shared.omega == 1.0;

@@ -6,7 +6,7 @@
 // size and one entry per thread; stage 2 times the other block sizes for the
 // best schedule, stage 3 strips of 2 and 4 rows at the best block size, stage 4
 // over-relaxation factors with the short schedules, stage 5 (mixed precision)
-// the fused FP32 smoother with the short schedules and 1 to 4 inner cycles.  Each
+// the fused FP32 smoother with the short schedules and 1 to 6 inner cycles.  Each
 // candidate gets its own plan, one untimed solve (which also captures the
 // graph when PIC_POISSON_GRAPH is set) and `repeats` timed solves; its score
 // is the median wall time of a solve call, which includes every host-side
@@ -132,7 +132,7 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
         }
     if (mixed)
         for (const auto &s : sor_sched)
-            for (int inner = 1; inner <= 4; ++inner) {
+            for (int inner = 1; inner <= 6; ++inner) {
                 Cand c{s[0], s[1], inner, base.threads, base.strip, 1.0, 1, 0.0};
                 const int rc = record(c);
                 if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;

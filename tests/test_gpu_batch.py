@@ -124,8 +124,8 @@ def test_autotune_picks_a_working_schedule(precision, tmp_path):
     cache = str(tmp_path / "tune.json")
     best = autotune([p], [rho], tol=1e-10, precision=precision, graph=True, repeats=1, cache=cache)
     n_sched = 7 * (4 if precision == MIXED else 1)
-    # + block sizes, strips 2, 4, 3 omegas x 4 schedules, and (mixed) the fused smoother x 4 schedules x 4
-    assert len(best["tried"]) == n_sched + 5 + 12 + (16 if precision == MIXED else 0)
+    # + block sizes, strips 2, 4, 3 omegas x 4 schedules, and (mixed) the fused smoother x 4 schedules x 6
+    assert len(best["tried"]) == n_sched + 5 + 12 + (24 if precision == MIXED else 0)
     assert best["smooth_threads"] in (64, 128, 256, 512)
     assert best["smooth_strip"] in (0, 2, 4)
     assert best["omega"] in (1.0, 1.1, 1.2, 1.3)
