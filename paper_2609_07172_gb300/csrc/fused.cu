@@ -168,15 +168,21 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
     for (int w = 0; w < W; ++w) u0[w] = u1[w] = zero;
     int buf = 0;
     int uslot = 0, bslot = 0;   // ring slots of the row entering now
-    for (int kb = ks; kb <= klast; kb += W) {
+    // The window holds row k - d at index W - 1 - d; it shifts by one row per
+    // step (register moves), which keeps the loop body a single copy -- an
+    // unrolled rotation would multiply the code by W.
+#pragma unroll 1
+    for (int k = ks; k <= klast; ++k) {   // the row entering at this step
+        {
+            // (a) row k into the window; fetch row k + DEPTH
 #pragma unroll
-        for (int ph = 0; ph < W; ++ph) {
-            const int k = kb + ph;   // the row entering at this step
-            if (k > klast) break;    // uniform over the block
-            // (a) row k into window slot ph; fetch row k + DEPTH
+            for (int w = 0; w + 1 < W; ++w) {
+                u0[w] = u0[w + 1];
+                u1[w] = u1[w + 1];
+            }
             cp_async_wait<DEPTH - 1>();
-            u0[ph] = uring[uslot * 2 * NT + t];
-            u1[ph] = uring[uslot * 2 * NT + NT + t];
+            u0[W - 1] = uring[uslot * 2 * NT + t];
+            u1[W - 1] = uring[uslot * 2 * NT + NT + t];
             {
                 int us = uslot + DEPTH, bs = bslot + DEPTH;
                 if (us >= UR) us -= UR;
@@ -188,9 +194,9 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
             for (int s = 0; s < NH; ++s) {
                 const int r = k - 1 - s;
                 if (r < ks || r >= ke) continue;           // uniform
-                const int sl = (ph - 1 - s + 2 * W) % W;   // row r
-                const int sn = (ph - s + 2 * W) % W;       // row r + 1
-                const int ss = (ph - 2 - s + 2 * W) % W;   // row r - 1
+                const int sl = W - 2 - s;   // row r
+                const int sn = W - 1 - s;   // row r + 1
+                const int ss = W - 3 - s;   // row r - 1
                 const int q = (r + (s & 1)) & 1;           // the pair's cell of this colour (uniform)
                 const bool edge = r == 0 || r == nz - 1;
                 const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + s) * (NT + 2 * PAD);
@@ -241,7 +247,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
             if (RES) {
                 const int rr = k - NH - 1;
                 if (rr >= k0 && rr < k1) {   // uniform
-                    const int sl = (ph - NH - 1 + 2 * W) % W, sn = (ph - NH + 2 * W) % W, ss = (ph - NH - 2 + 2 * W) % W;
+                    const int sl = W - 2 - NH, sn = W - 1 - NH, ss = W - 3 - NH;
                     const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + NH) * (NT + 2 * PAD);
                     int rb = bslot - NH - 1;
                     if (rb < 0) rb += BR;
@@ -288,19 +294,19 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
             float2 *pw = pubs + (size_t)(buf * NP) * (NT + 2 * PAD) + t;
 #pragma unroll
             for (int s = 0; s < NH; ++s) {
-                const int sl = (ph - s + 2 * W) % W;
+                const int sl = W - 1 - s;
                 const int qn = (k - s + (s & 1)) & 1;
                 pw[(size_t)s * (NT + 2 * PAD)] = qn == 0 ? u1[sl] : u0[sl];
             }
             if (RES) {
-                const int sl = (ph - NH + 2 * W) % W;
+                const int sl = W - 1 - NH;
                 const int qn = (k - NH) & 1;   // red column of row k - NH
                 pw[(size_t)NH * (NT + 2 * PAD)] = qn == 0 ? u1[sl] : u0[sl];
             }
             // (e) the output row k - NH is final
             const int ro = k - NH;
             if (outpair && ro >= k0 && ro < k1) {
-                const int so = (ph - NH + 2 * W) % W;
+                const int so = W - 1 - NH;
                 const size_t o = (size_t)ro * rs;
                 if (v0) F.out[o + c0] = u0[so];
                 if (v1) F.out[o + c1] = u1[so];
