@@ -104,6 +104,9 @@ typedef struct {
     int smooth_fused;          /* mixed precision: 1 runs each pre- or post-smoothing of an FP32 level
                                   (1 or 2 sweeps, omega = 1, even nr) as one fused pass; 0 separate
                                   half-sweeps */
+    int local_bottom;          /* 0: the level above the coarsest and the coarsest solve run per mode in
+                                  one block's shared memory where they fit (omega = 1, 3 or more levels);
+                                  -1: never (separate launches) */
     unsigned flags;            /* PIC_POISSON_* flags */
 } pic_poisson_desc;
 

@@ -49,7 +49,8 @@ class Desc(ctypes.Structure):
         ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
         ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int),
         ("inner_cycles", ctypes.c_int), ("smooth_threads", ctypes.c_int), ("smooth_strip", ctypes.c_int),
-        ("omega", ctypes.c_double), ("smooth_fused", ctypes.c_int), ("flags", ctypes.c_uint),
+        ("omega", ctypes.c_double), ("smooth_fused", ctypes.c_int), ("local_bottom", ctypes.c_int),
+        ("flags", ctypes.c_uint),
     ]
 
 
@@ -158,7 +159,7 @@ def _check(status, allow=(OK,)):
 
 
 def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1, flags=0, inner_cycles=0,
-              smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0):
+              smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0, local_bottom=0):
     """Descriptor for a workloads.Problem; returns (Desc, keep-alive buffers)."""
     keep = []
     d = Desc()
@@ -183,6 +184,7 @@ def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=
     d.smooth_strip = smooth_strip
     d.omega = omega
     d.smooth_fused = smooth_fused
+    d.local_bottom = local_bottom
     d.flags = flags
     return d, keep
 
@@ -226,14 +228,14 @@ class Plan:
 
     def __init__(self, problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
                  profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False,
-                 smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0):
+                 smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0, local_bottom=0):
         import torch
         self.problem = problem
         flags = ((PROFILE if profile else 0) | (USE_INITIAL_GUESS if initial_guess else 0)
                  | (GRAPH if graph else 0))
         self._desc, self._keep = make_desc(problem, precision, max_cycles, pre_sweeps, post_sweeps, flags,
                                            inner_cycles, smooth_threads, smooth_strip, omega,
-                                           smooth_fused)
+                                           smooth_fused, local_bottom)
         self.stream = torch.cuda.current_stream() if stream is None else stream
         self._plan = ctypes.c_void_p()
         _check(load().pic_poisson_plan(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
@@ -349,7 +351,7 @@ class BatchPlan:
 
     def __init__(self, problems, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
                  profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False,
-                 smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0):
+                 smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0, local_bottom=0):
         import torch
         self.problems = list(problems)
         n = len(self.problems)
@@ -361,7 +363,7 @@ class BatchPlan:
         self._keep = []
         for i, p in enumerate(self.problems):
             d, keep = make_desc(p, precision, max_cycles, pre_sweeps, post_sweeps, flags, inner_cycles,
-                                smooth_threads, smooth_strip, omega, smooth_fused)
+                                smooth_threads, smooth_strip, omega, smooth_fused, local_bottom)
             self._descs[i] = d
             self._keep.extend(keep)
         self.stream = torch.cuda.current_stream() if stream is None else stream

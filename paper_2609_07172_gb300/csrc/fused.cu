@@ -161,6 +161,15 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
         dg1 = L.diag[cls1 + c1];
     }
     float2 rsum = make_float2(0.f, 0.f);   // residual of the even row of a coarse cell (RES)
+    // the coarse level's outputs, in registers (the stores below must not make
+    // the compiler reload them from the launch table)
+    float2 *const cb = F.C.b, *const cbh = F.C.bh, *const cu = F.C.u;
+    const float *const cinvd = F.C.invd;
+    const int cnr = F.C.nr, cnz = F.C.nz, cncls = F.C.ncls, finit = F.init;
+    const bool cwrite = RES && outpair && v0 && j < cnr;
+    const size_t ccol = (size_t)(cwrite ? j : 0) * nm + (mvalid ? m : 0);
+    const float cinv1 = RES && cwrite ? cinvd[(cncls > 1 ? (size_t)cnr * nm : 0) + ccol] : 0.f;
+    float2 *const gout = F.out;
 
     const float2 zero = make_float2(0.f, 0.f);
     float2 u0[W], u1[W];
@@ -272,17 +281,17 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                         a = make_float2(fmaf(ce1, ue.x, a.x), fmaf(ce1, ue.y, a.y));
                         res = make_float2(fmaf(-d, u1[sl].x, a.x), fmaf(-d, u1[sl].y, a.y));
                         const float2 sum = make_float2(rsum.x + res.x, rsum.y + res.y);
-                        const LevelDev<float> &C = F.C;
-                        if (outpair && v0 && j < C.nr) {
+                        if (cwrite) {
                             const int K = rr >> 1;
-                            const size_t e = ((size_t)K * C.nr + j) * C.nm + m;
-                            C.b[e] = sum;
-                            if (F.init > 0) {
-                                const float inv =
-                                    C.invd[((size_t)row_class(K, C.nz, C.ncls) * C.nr + j) * C.nm + m];
+                            const size_t e = (size_t)K * cnr * nm + ccol;
+                            cb[e] = sum;
+                            if (finit > 0) {
+                                const float inv = (K == 0 || K == cnz - 1)
+                                                      ? cinvd[(size_t)row_class(K, cnz, cncls) * cnr * nm + ccol]
+                                                      : cinv1;
                                 const float2 bhc = make_float2(sum.x * inv, sum.y * inv);
-                                C.bh[e] = bhc;
-                                C.u[e] = (F.init == 2 && ((K + j) & 1) == 0) ? bhc : zero;
+                                cbh[e] = bhc;
+                                cu[e] = (finit == 2 && ((K + j) & 1) == 0) ? bhc : zero;
                             }
                         }
                     }
@@ -308,8 +317,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
             if (outpair && ro >= k0 && ro < k1) {
                 const int so = W - 1 - NH;
                 const size_t o = (size_t)ro * rs;
-                if (v0) F.out[o + c0] = u0[so];
-                if (v1) F.out[o + c1] = u1[so];
+                if (v0) gout[o + c0] = u0[so];
+                if (v1) gout[o + c1] = u1[so];
             }
             __syncthreads();
             buf ^= 1;

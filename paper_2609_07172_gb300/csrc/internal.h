@@ -237,6 +237,24 @@ cudaError_t launch_smooth_fused(const FusedTab *tab, unsigned grid, int nh, bool
 // Block shape and count for an nr x nz level with nm modes (about target_blocks blocks).
 void fused_shape(int nr, int nz, int nm, int nh, bool res, int target_blocks, FusedProb &f, unsigned &blocks);
 
+// Mode-local bottom of the V-cycle (bottom.cu): the level above the coarsest
+// (U) and the coarsest level's solve, one block per (problem, mode, part).
+template <class T> struct BottomProb {
+    LevelDev<T> U;
+    CoarseDev<T> D;
+    int pre, post;                // sweeps
+    int red_only, black_only;     // restriction of the red cells, prolongation to the black cells
+};
+template <class T> struct BottomTab {
+    int n;
+    unsigned start[kMaxBatch + 1];
+    BottomProb<T> p[kMaxBatch];
+};
+constexpr int BOTTOM_THREADS = 256;
+constexpr size_t BOTTOM_MAX_SMEM = 200 * 1024;
+template <class T> size_t bottom_smem_bytes(int nr, int nz, int ncls, int ncr, int ncz);
+template <class T> cudaError_t launch_bottom(const BottomTab<T> *tab, unsigned grid, size_t smem, cudaStream_t st);
+
 constexpr int FFT_TI = 32;        // radial columns per transform CTA
 constexpr int FFT_THREADS = 256;
 size_t fft_smem_bytes(int nt);

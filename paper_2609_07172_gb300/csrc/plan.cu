@@ -50,6 +50,10 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
     if (d->smooth_strip < 0) d->smooth_strip = 0;
     if (d->omega <= 0) d->omega = 1.0;
     if (d->smooth_fused < 0) d->smooth_fused = 0;
+    if (d->local_bottom != 0 && d->local_bottom != -1) {
+        set_error("local_bottom must be 0 or -1 (got %d)", d->local_bottom);
+        return PIC_POISSON_EINVAL;
+    }
     if (d->smooth_fused > 1) {
         set_error("smooth_fused must be 0 or 1 (got %d)", d->smooth_fused);
         return PIC_POISSON_EINVAL;
@@ -322,6 +326,7 @@ template <class T> void carve_hier(pic_poisson_plan_s &P, Carver &c, Hier<T> &H)
         }
     }
     H.coarse = c.take<CoarseTab<T>>(1);
+    H.bottom = c.take<BottomTab<T>>(1);
 }
 
 // Lay out (or size) the whole device workspace.
@@ -419,7 +424,7 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
         int nprob = 0;
         bool res = H.fused;   // restriction fused into pre-smoothing: every pair of levels halves r and z
         for (int p = 0; p < P.n; ++p)
-            if (l < P.pr[p].L - 1) {
+            if (l < P.pr[p].smoothed()) {
                 ++nprob;
                 const LevelHost &a = P.pr[p].lv[l], &b = P.pr[p].lv[l + 1];
                 res = res && b.nr * 2 == a.nr && b.nz * 2 == a.nz;
@@ -432,12 +437,12 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
         int strip = P.shared.smooth_strip;
         int zmax = 0;
         for (int p = 0; p < P.n; ++p)
-            if (l < P.pr[p].L - 1) zmax = std::max(zmax, (views(P.pr[p])[l].nz + 1) / 2);
+            if (l < P.pr[p].smoothed()) zmax = std::max(zmax, (views(P.pr[p])[l].nz + 1) / 2);
         while (strip > 1 && strip > zmax) strip >>= 1;
         H.strip[l] = strip;
         for (int p = 0; p < P.n; ++p) {
             const ProblemPlan &q = P.pr[p];
-            if (l >= q.L - 1) continue;
+            if (l >= q.smoothed()) continue;
             const std::vector<LevelDev<T>> &v = views(q);
             LevelDev<T> f = v[l];
             f.init = (l + 1 == q.L - 1) ? 0 : (pre > 0 ? 2 : 1);
@@ -503,9 +508,26 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
         }
     }
     CoarseTab<T> tc{};
+    BottomTab<T> tb{};
+    size_t smem_b = 0;
     for (int p = 0; p < P.n; ++p) {
         const ProblemPlan &q = P.pr[p];
         const CoarseDev<T> &cd = coarse(q);
+        if (q.bottom) {
+            const LevelDev<T> &U = views(q)[q.L - 2];
+            BottomProb<T> bp{};
+            bp.U = U;
+            bp.D = cd;
+            bp.pre = pre;
+            bp.post = post;
+            bp.red_only = pre > 0 && P.shared.omega == 1.0;
+            bp.black_only = post > 0 && P.shared.omega == 1.0;
+            tb.p[tb.n] = bp;
+            tb.start[tb.n + 1] = tb.start[tb.n] + 2u * (unsigned)q.nm;   // (mode, real / imaginary part)
+            smem_b = std::max(smem_b, bottom_smem_bytes<T>(U.nr, U.nz, U.ncls, cd.nr, cd.nz));
+            ++tb.n;
+            continue;
+        }
         tc.f[tc.n] = views(q)[q.L - 1];
         tc.c[tc.n] = cd;
         tc.start[tc.n + 1] = tc.start[tc.n] + 2u * (unsigned)q.nm;   // (mode, real / imaginary part)
@@ -516,6 +538,9 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
     H.g_coarse = tc.start[tc.n];
     H.smem_coarse = tc.smem;
     blob_to_dev(tc, H.coarse, st, err);
+    H.g_bottom = tb.start[tb.n];
+    H.smem_bottom = smem_b;
+    if (tb.n) blob_to_dev(tb, H.bottom, st, err);
 }
 
 int upload(pic_poisson_plan_s &P) {
@@ -693,7 +718,7 @@ int same_settings(const pic_poisson_desc &a, const pic_poisson_desc &b) {
     return a.precision == b.precision && a.max_cycles == b.max_cycles && a.pre_sweeps == b.pre_sweeps &&
            a.post_sweeps == b.post_sweeps && a.inner_cycles == b.inner_cycles && a.flags == b.flags &&
            a.smooth_threads == b.smooth_threads && a.smooth_strip == b.smooth_strip && a.omega == b.omega &&
-           a.smooth_fused == b.smooth_fused;
+           a.smooth_fused == b.smooth_fused && a.local_bottom == b.local_bottom;
 }
 
 int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
@@ -730,6 +755,17 @@ int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
             return PIC_POISSON_EINVAL;
         }
         P.h32.fused = true;
+    }
+    // mode-local bottom where the two coarsest levels fit in one block's shared memory
+    for (ProblemPlan &q : P.pr) {
+        q.bottom = false;
+        if (P.shared.local_bottom != 0 || P.shared.omega != 1.0 || q.L < 3) continue;
+        const LevelHost &U = q.lv[q.L - 2], &C = q.lv[q.L - 1];
+        if (U.nr % 2) continue;
+        const size_t smem = P.shared.precision == PIC_POISSON_MIXED
+                                ? bottom_smem_bytes<float>(U.nr, U.nz, U.ncls, C.nr, C.nz)
+                                : bottom_smem_bytes<double>(U.nr, U.nz, U.ncls, C.nr, C.nz);
+        q.bottom = smem <= BOTTOM_MAX_SMEM;
     }
     return PIC_POISSON_OK;
 }

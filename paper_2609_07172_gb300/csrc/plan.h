@@ -17,6 +17,8 @@ struct ProblemPlan {
     CoarseDev<double> cd{};
     CoarseDev<float> cf{};
     const double *tw = nullptr, *tw2 = nullptr; // FFT twiddles
+    bool bottom = false;                        // levels L-2 and L-1 solved by k_bottom
+    int smoothed() const { return L - 1 - (bottom ? 1 : 0); }   // levels 0 .. smoothed()-1 use the level kernels
     double *s0 = nullptr, *bD0 = nullptr;       // level-0 right-hand-side factors
 };
 
@@ -30,9 +32,12 @@ template <class T> struct Hier {
     std::vector<FusedTab *> fpre, fpost;
     std::vector<unsigned> g_fpre, g_fpost;
     std::vector<char> fres;                               // per level: pre-smoothing also restricts
-    CoarseTab<T> *coarse = nullptr;
+    CoarseTab<T> *coarse = nullptr;           // problems solved by k_coarse
     unsigned g_coarse = 0;
     size_t smem_coarse = 0;
+    BottomTab<T> *bottom = nullptr;           // problems with a mode-local bottom
+    unsigned g_bottom = 0;
+    size_t smem_bottom = 0;
 };
 
 // Algorithmic traffic / arithmetic / launches recorded per kernel class.

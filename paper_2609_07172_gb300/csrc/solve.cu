@@ -79,12 +79,13 @@ template <> const std::vector<LevelDev<float>> &views<float>(const ProblemPlan &
 template <class T> double level_entries(const pic_poisson_plan_s &P, int l) {
     double n = 0;
     for (const ProblemPlan &q : P.pr)
-        if (l < q.L - 1) n += (double)q.lv[l].nr * q.lv[l].nz * q.nm;
+        if (l < q.smoothed()) n += (double)q.lv[l].nr * q.lv[l].nz * q.nm;
     return n;
 }
 double coarse_entries(const pic_poisson_plan_s &P, double *flops_per) {
     double n = 0, f = 0;
     for (const ProblemPlan &q : P.pr) {
+        if (q.bottom) continue;
         const LevelHost &h = q.lv[q.L - 1];
         const double e = (double)h.nr * h.nz * q.nm;
         n += e;
@@ -179,8 +180,23 @@ int descend_ascend(Runner &R, const Hier<T> &H) {
     }
     double cf = 0;
     const double cn = coarse_entries(P, &cf);
-    RUN(R, PIC_POISSON_PHASE_COARSE, launch_coarse(H.coarse, H.g_coarse, H.smem_coarse, R.st));
-    R.account(PIC_POISSON_PHASE_COARSE, 2.0 * cn * sizeof(V2<T>) + cn * 2 * sizeof(T), cf);
+    if (H.g_coarse) {
+        RUN(R, PIC_POISSON_PHASE_COARSE, launch_coarse(H.coarse, H.g_coarse, H.smem_coarse, R.st));
+        R.account(PIC_POISSON_PHASE_COARSE, 2.0 * cn * sizeof(V2<T>) + cn * 2 * sizeof(T), cf);
+    }
+    if (H.g_bottom) {
+        // per mode and part: b, b_hat in, u out of the level above the coarsest
+        double nb = 0, fb = 0;
+        for (const ProblemPlan &q : P.pr) {
+            if (!q.bottom) continue;
+            const LevelHost &u = q.lv[q.L - 2], &c = q.lv[q.L - 1];
+            const double e = (double)u.nr * u.nz * q.nm, ec = (double)c.nr * c.nz * q.nm;
+            nb += e;
+            fb += e * 7.0 * (P.shared.pre_sweeps + P.shared.post_sweeps) + e * 13.0 + ec * (4.0 * c.nz + 12.0);
+        }
+        RUN(R, PIC_POISSON_PHASE_COARSE, launch_bottom(H.bottom, H.g_bottom, H.smem_bottom, R.st));
+        R.account(PIC_POISSON_PHASE_COARSE, 3.0 * nb * sizeof(V2<T>), fb);
+    }
     for (int l = nl - 1; l >= 0; --l) {
         if (!H.prolong[l]) continue;
         // the red half-sweep that follows overwrites the red cells unread

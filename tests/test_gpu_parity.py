@@ -260,3 +260,25 @@ def test_convergence_rate_independent_of_cell_aspect(dims):
     with Plan(p) as plan:
         _, info = plan.solve(dev(rho), tol=1e-10)
     assert info["status"] == B.OK and info["cycles"] <= 12, info["cycles"]
+
+
+BOTTOM_CASES = [(64, 32, 48), (96, 16, 40), (64, 8, 400), (256, 8, 32), (512, 128, 64), (40, 8, 24)]
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.MIXED], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("dims", BOTTOM_CASES, ids=[f"{a}x{b}x{c}" for a, b, c in BOTTOM_CASES])
+def test_local_bottom_is_bitwise_the_level_kernels(dims, prec):
+    """The mode-local bottom (the level above the coarsest and the coarsest
+    solve in one block per mode and part) runs the level kernels' operations
+    in their order: same cycles, bitwise the same potential, including
+    semi-coarsened bottoms (64x8x400, 256x8x32)."""
+    p = with_bias_walls(W.annulus(*dims))
+    rho = dev(W.rho_plasma(p, seed=41))
+    out = []
+    for lb in (-1, 0):
+        with Plan(p, precision=prec, local_bottom=lb, pre_sweeps=1, post_sweeps=2) as plan:
+            phi, info = plan.solve(rho, tol=1e-10)
+        assert info["status"] == B.OK
+        out.append((phi.cpu(), info["cycles"]))
+    assert out[0][1] == out[1][1]
+    assert torch.equal(out[0][0], out[1][0])
