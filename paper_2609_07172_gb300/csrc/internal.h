@@ -250,7 +250,7 @@ template <class T> struct BottomTab {
     unsigned start[kMaxBatch + 1];
     BottomProb<T> p[kMaxBatch];
 };
-constexpr int BOTTOM_THREADS = 256;
+constexpr int BOTTOM_THREADS = 1024;
 constexpr size_t BOTTOM_MAX_SMEM = 200 * 1024;
 template <class T> size_t bottom_smem_bytes(int nr, int nz, int ncls, int ncr, int ncz);
 template <class T> cudaError_t launch_bottom(const BottomTab<T> *tab, unsigned grid, size_t smem, cudaStream_t st);
