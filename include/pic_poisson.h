@@ -107,6 +107,9 @@ typedef struct {
     int local_bottom;          /* 0: the level above the coarsest and the coarsest solve run per mode in
                                   one block's shared memory where they fit (omega = 1, 3 or more levels);
                                   -1: never (separate launches) */
+    int fmg;                   /* FP64: 1 starts a solve from a zero iterate with a full-multigrid pass
+                                  (right-hand side restricted to every level, coarsest solve, then
+                                  prolongation and one V-cycle per level up to the finest); 0 from zero */
     unsigned flags;            /* PIC_POISSON_* flags */
 } pic_poisson_desc;
 
@@ -133,6 +136,7 @@ typedef struct {
     int smooth_strip;                      /* best smoother strip (0: one entry per thread) */
     double omega;                          /* best over-relaxation factor */
     int smooth_fused;                      /* best fused-smoother setting */
+    int fmg;                               /* best full-multigrid start setting (FP64) */
     double ms;                             /* its median wall time per solve call */
     int tried;                             /* candidates timed (entries below) */
     double ms_tried[PIC_POISSON_MAX_TUNE];
@@ -141,6 +145,7 @@ typedef struct {
     int strip_tried[PIC_POISSON_MAX_TUNE];
     double omega_tried[PIC_POISSON_MAX_TUNE];
     int fused_tried[PIC_POISSON_MAX_TUNE];
+    int fmg_tried[PIC_POISSON_MAX_TUNE];
 } pic_poisson_tuning;
 
 typedef struct {
@@ -228,7 +233,8 @@ int pic_poisson_solve_batch(pic_poisson_plan_t plan, const double *const *rho_de
  * over-relaxation omega = 1.1, 1.2, 1.3 with the schedules (1,1), (1,2),
  * (2,1), (2,2) at the best block size, strip and inner cycles; stage 5
  * (mixed precision) the fused smoother with the same four schedules and 1 to
- * 6 inner cycles.  Each
+ * 6 inner cycles, or (FP64) the full-multigrid start with the schedules (1,2),
+ * (2,1), (2,2).  Each
  * candidate builds its own plan, runs
  * one untimed solve and `repeats` (1..16) timed ones; the score is the median
  * wall time of the solve call.  Results in *out; phi_dev is overwritten.

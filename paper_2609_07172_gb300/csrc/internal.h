@@ -181,6 +181,9 @@ template <class T>
 cudaError_t launch_prolong(const LaunchTab<T> *tab, unsigned grid, bool black_only, cudaStream_t st);
 template <class T>
 cudaError_t launch_coarse(const CoarseTab<T> *tab, unsigned grid, size_t smem, cudaStream_t st);
+// Full-multigrid start: u_f = P u_c on every fine cell; coarse b = restricted fine b.
+template <class T> cudaError_t launch_interp(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st);
+template <class T> cudaError_t launch_rhs_restrict(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st);
 
 // zero_x: the FP64 iterate is zero (r = b; the kernel also writes x = 0).
 cudaError_t launch_defect(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, double *partials, bool zero_x,

@@ -314,7 +314,7 @@ k_residual(const LaunchTab<T> *__restrict__ tab, int write_r, double *__restrict
 // value is reflected with a sign change (the correction vanishes on the
 // Dirichlet face).  BLACK_ONLY: only black fine cells (the red half-sweep that
 // follows overwrites the red ones).
-template <class T, bool BLACK_ONLY>
+template <class T, bool BLACK_ONLY, bool ASSIGN = false>
 __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__restrict__ tab) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     const LevelDev<T> F = tab->f[p];
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
     const bool iin = I2 >= 0 && I2 < C.nr;
     const int Kx = kin ? K2 : K, Ix = iin ? I2 : I;
     const V2<T> c0 = C.u[((size_t)K * C.nr + I) * nm + m];
-    V2<T> u = F.u[idx];
+    V2<T> u = ASSIGN ? mk<T>(0, 0) : F.u[idx];   // ASSIGN: u = P c (full-multigrid interpolation)
     if (cz2 && cr2) {
         const V2<T> c1 = C.u[((size_t)K * C.nr + Ix) * nm + m];
         const V2<T> c2 = C.u[((size_t)Kx * C.nr + I) * nm + m];
@@ -359,6 +359,34 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
         u.y = fma(w1, c1.y, fma(T(0.75), c0.y, u.y));
     }
     F.u[idx] = u;
+}
+
+// Full-multigrid start: the right-hand side restricted to the next coarser
+// level (the finite-volume sum of b over the fine cells of each coarse cell,
+// the restriction the residuals get), b_hat = b / diag, and a zero iterate.
+template <class T>
+__global__ void __launch_bounds__(MG_THREADS) k_rhs_restrict(const LaunchTab<T> *__restrict__ tab) {
+    const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    const LevelDev<T> F = tab->f[p];
+    const LevelDev<T> C = tab->c[p];
+    const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
+    if (e >= (unsigned)C.nz * (unsigned)C.nr * (unsigned)C.nm) return;
+    const unsigned nm = C.nm;
+    const unsigned cc = e / nm;
+    const int m = (int)(e - cc * nm);
+    const int K = (int)(cc / (unsigned)C.nr);
+    const int I = (int)(cc - (unsigned)K * C.nr);
+    const int fz = F.nz == C.nz ? 1 : 2, fr = F.nr == C.nr ? 1 : 2;
+    V2<T> sum = F.b[((size_t)(fz * K) * F.nr + fr * I) * nm + m];
+    for (int c = 1; c < fz * fr; ++c) {
+        const int k = fz * K + (fr == 2 ? (c >> 1) : c), i = fr * I + (fr == 2 ? (c & 1) : 0);
+        const V2<T> b = F.b[((size_t)k * F.nr + i) * nm + m];
+        sum = mk<T>(sum.x + b.x, sum.y + b.y);
+    }
+    C.b[e] = sum;
+    const T inv = C.invd[((size_t)row_class(K, C.nz, C.ncls) * C.nr + I) * nm + m];
+    C.bh[e] = mk<T>(sum.x * inv, sum.y * inv);
+    C.u[e] = mk<T>(0, 0);
 }
 
 // Conversions between binary64 and binary32 with a power-of-two scale 2^s,
@@ -723,6 +751,16 @@ cudaError_t launch_prolong(const LaunchTab<T> *tab, unsigned grid, bool black_on
     return cudaGetLastError();
 }
 
+template <class T> cudaError_t launch_interp(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st) {
+    k_prolong<T, false, true><<<grid, MG_THREADS, 0, st>>>(tab);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_rhs_restrict(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st) {
+    k_rhs_restrict<T><<<grid, MG_THREADS, 0, st>>>(tab);
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_coarse(const CoarseTab<T> *tab, unsigned grid, size_t smem, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -766,6 +804,8 @@ cudaError_t launch_sum(const double *partials, int n, double *out, cudaStream_t 
     template cudaError_t launch_residual<T>(const LaunchTab<T> *, unsigned, bool, double *, unsigned,      \
                                             cudaStream_t);                                                 \
     template cudaError_t launch_prolong<T>(const LaunchTab<T> *, unsigned, bool, cudaStream_t);            \
+    template cudaError_t launch_interp<T>(const LaunchTab<T> *, unsigned, cudaStream_t);                   \
+    template cudaError_t launch_rhs_restrict<T>(const LaunchTab<T> *, unsigned, cudaStream_t);             \
     template cudaError_t launch_coarse<T>(const CoarseTab<T> *, unsigned, size_t, cudaStream_t);
 PP_INST(double)
 PP_INST(float)

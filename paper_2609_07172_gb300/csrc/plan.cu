@@ -50,6 +50,10 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
     if (d->smooth_strip < 0) d->smooth_strip = 0;
     if (d->omega <= 0) d->omega = 1.0;
     if (d->smooth_fused < 0) d->smooth_fused = 0;
+    if (d->fmg != 0 && (d->fmg != 1 || d->precision != PIC_POISSON_FP64)) {
+        set_error("fmg must be 0, or 1 with precision PIC_POISSON_FP64 (got %d)", d->fmg);
+        return PIC_POISSON_EINVAL;
+    }
     if (d->local_bottom != 0 && d->local_bottom != -1) {
         set_error("local_bottom must be 0 or -1 (got %d)", d->local_bottom);
         return PIC_POISSON_EINVAL;
@@ -316,6 +320,8 @@ template <class T> void carve_hier(pic_poisson_plan_s &P, Carver &c, Hier<T> &H)
     H.prolong.assign(nl, nullptr);
     H.fpre.assign(nl, nullptr);
     H.fpost.assign(nl, nullptr);
+    H.rhs.assign(nl, nullptr);
+    H.interp.assign(nl, nullptr);
     for (int l = 0; l < nl; ++l) {
         H.smooth[l] = c.take<LaunchTab<T>>(1);
         H.restr[l] = c.take<LaunchTab<T>>(1);
@@ -323,6 +329,10 @@ template <class T> void carve_hier(pic_poisson_plan_s &P, Carver &c, Hier<T> &H)
         if (H.fused) {
             H.fpre[l] = c.take<FusedTab>(1);
             H.fpost[l] = c.take<FusedTab>(1);
+        }
+        if (P.shared.fmg) {
+            H.rhs[l] = c.take<LaunchTab<T>>(1);
+            H.interp[l] = c.take<LaunchTab<T>>(1);
         }
     }
     H.coarse = c.take<CoarseTab<T>>(1);
@@ -505,6 +515,36 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
             H.g_fpost[l] = fb.start[fb.n];
             blob_to_dev(fa, H.fpre[l], st, err);
             blob_to_dev(fb, H.fpost[l], st, err);
+        }
+    }
+    H.g_rhs.assign(nl, 0);
+    H.g_interp.assign(nl, 0);
+    if (P.shared.fmg) {
+        // full-multigrid start: b restricted from l to l + 1 for every level pair
+        // of a problem, and u_l = P u_(l+1) for the levels the level kernels solve
+        for (int l = 0; l < nl; ++l) {
+            LaunchTab<T> trh{}, tin{};
+            for (int p = 0; p < P.n; ++p) {
+                const ProblemPlan &q = P.pr[p];
+                const std::vector<LevelDev<T>> &v = views(q);
+                if (l < q.L - 1) {
+                    trh.f[trh.n] = v[l];
+                    trh.c[trh.n] = v[l + 1];
+                    trh.start[trh.n + 1] =
+                        trh.start[trh.n] + mg_blocks((size_t)v[l + 1].nz * v[l + 1].nr * v[l].nm);
+                    ++trh.n;
+                }
+                if (l < q.smoothed()) {
+                    tin.f[tin.n] = v[l];
+                    tin.c[tin.n] = v[l + 1];
+                    tin.start[tin.n + 1] = tin.start[tin.n] + mg_blocks((size_t)v[l].nz * v[l].nr * v[l].nm);
+                    ++tin.n;
+                }
+            }
+            H.g_rhs[l] = trh.start[trh.n];
+            H.g_interp[l] = tin.start[tin.n];
+            if (trh.n) blob_to_dev(trh, H.rhs[l], st, err);
+            if (tin.n) blob_to_dev(tin, H.interp[l], st, err);
         }
     }
     CoarseTab<T> tc{};
@@ -718,7 +758,7 @@ int same_settings(const pic_poisson_desc &a, const pic_poisson_desc &b) {
     return a.precision == b.precision && a.max_cycles == b.max_cycles && a.pre_sweeps == b.pre_sweeps &&
            a.post_sweeps == b.post_sweeps && a.inner_cycles == b.inner_cycles && a.flags == b.flags &&
            a.smooth_threads == b.smooth_threads && a.smooth_strip == b.smooth_strip && a.omega == b.omega &&
-           a.smooth_fused == b.smooth_fused && a.local_bottom == b.local_bottom;
+           a.smooth_fused == b.smooth_fused && a.local_bottom == b.local_bottom && a.fmg == b.fmg;
 }
 
 int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {

@@ -35,6 +35,8 @@ template <class T> struct Hier {
     CoarseTab<T> *coarse = nullptr;           // problems solved by k_coarse
     unsigned g_coarse = 0;
     size_t smem_coarse = 0;
+    std::vector<LaunchTab<T> *> rhs, interp;  // full-multigrid start: b restricted to l + 1, u_l = P u_(l+1)
+    std::vector<unsigned> g_rhs, g_interp;
     BottomTab<T> *bottom = nullptr;           // problems with a mode-local bottom
     unsigned g_bottom = 0;
     size_t smem_bottom = 0;

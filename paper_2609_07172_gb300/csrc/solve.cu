@@ -165,19 +165,11 @@ int restrict_level(Runner &R, const Hier<T> &H, int l, double *partials) {
     return PIC_POISSON_OK;
 }
 
-// Coarse-grid correction below level 0: level 1 holds the restricted residual
-// and its initialised iterate; returns with the correction prolongated into
-// level 0 and post-smoothed there.
+// The coarsest levels: the separable solve (k_coarse) for the problems that
+// end there, the mode-local bottom (k_bottom) for the others.
 template <class T>
-int descend_ascend(Runner &R, const Hier<T> &H) {
+int coarse_and_bottom(Runner &R, const Hier<T> &H) {
     pic_poisson_plan_s &P = R.P;
-    const int nl = P.Lmax - 1, pre = P.shared.pre_sweeps, post = P.shared.post_sweeps;
-    for (int l = 1; l < nl; ++l) {
-        int rc = smooth_level(R, H, l, pre, pre > 0, false);
-        if (rc) return rc;
-        rc = restrict_level(R, H, l, nullptr);
-        if (rc) return rc;
-    }
     double cf = 0;
     const double cn = coarse_entries(P, &cf);
     if (H.g_coarse) {
@@ -197,7 +189,26 @@ int descend_ascend(Runner &R, const Hier<T> &H) {
         RUN(R, PIC_POISSON_PHASE_COARSE, launch_bottom(H.bottom, H.g_bottom, H.smem_bottom, R.st));
         R.account(PIC_POISSON_PHASE_COARSE, 3.0 * nb * sizeof(V2<T>), fb);
     }
-    for (int l = nl - 1; l >= 0; --l) {
+    return PIC_POISSON_OK;
+}
+
+// Coarse-grid correction below level lend: level lend + 1 holds the
+// restricted residual and its initialised iterate; returns with the
+// correction prolongated into level lend and post-smoothed there (lend = 0:
+// the V-cycle's coarse-grid correction of the finest level).
+template <class T>
+int descend_ascend(Runner &R, const Hier<T> &H, int lend = 0) {
+    pic_poisson_plan_s &P = R.P;
+    const int nl = P.Lmax - 1, pre = P.shared.pre_sweeps, post = P.shared.post_sweeps;
+    for (int l = lend + 1; l < nl; ++l) {
+        int rc = smooth_level(R, H, l, pre, pre > 0, false);
+        if (rc) return rc;
+        rc = restrict_level(R, H, l, nullptr);
+        if (rc) return rc;
+    }
+    int rc0 = coarse_and_bottom(R, H);
+    if (rc0) return rc0;
+    for (int l = nl - 1; l >= lend; --l) {
         if (!H.prolong[l]) continue;
         // the red half-sweep that follows overwrites the red cells unread
         // (Gauss-Seidel only: an over-relaxed update reads the old value)
@@ -237,6 +248,41 @@ int mixed_defect_and_check(Runner &R, int counting, bool zero_x = false) {
     return PIC_POISSON_OK;
 }
 
+// Full-multigrid start of a solve from a zero iterate (FP64 levels): the
+// right-hand side restricted to every level, the coarsest levels solved (the
+// separable solve, or the mode-local bottom), then from the coarsest level up
+// the iterate prolongated to the next finer level as its initial value and one
+// V-cycle there -- up to level 0, whose prolongated iterate starts the main
+// iteration.  The restriction of b is the residuals' (a finite-volume sum), so
+// each level's problem is the discretisation of the same field on its cells.
+int fmg_start(Runner &R) {
+    pic_poisson_plan_s &P = R.P;
+    const Hier<double> &H = P.h64;
+    const int nl = P.Lmax - 1, pre = P.shared.pre_sweeps;
+    for (int l = 0; l < nl; ++l) {
+        if (!H.g_rhs[l]) continue;
+        RUN(R, PIC_POISSON_PHASE_RESTRICT, launch_rhs_restrict(H.rhs[l], H.g_rhs[l], R.st));
+        const double n = level_entries<double>(P, l);
+        R.account(PIC_POISSON_PHASE_RESTRICT, n * sizeof(double2) * (1.0 + 0.75), 0.5 * n);
+    }
+    int rc = coarse_and_bottom(R, H);
+    if (rc) return rc;
+    for (int l = nl - 1; l >= 0; --l) {
+        if (!H.g_interp[l]) continue;
+        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_interp(H.interp[l], H.g_interp[l], R.st));
+        const double n = level_entries<double>(P, l);
+        R.account(PIC_POISSON_PHASE_PROLONG, n * sizeof(double2) * 1.25, 16.0 * n);
+        if (l == 0) break;   // the main iteration takes over on level 0
+        rc = smooth_level(R, H, l, pre, false, false);
+        if (rc) return rc;
+        rc = restrict_level(R, H, l, nullptr);
+        if (rc) return rc;
+        rc = descend_ascend(R, H, l);
+        if (rc) return rc;
+    }
+    return PIC_POISSON_OK;
+}
+
 // Forward transform + right-hand side, ||b||, initial iterate, first
 // evaluation of the residual and the first convergence test.
 // guess: 0 = zero initial iterate, 1 = transform of phi, 2 = mode-layout iterate.
@@ -254,6 +300,9 @@ int enqueue_prologue(Runner &R, int guess) {
     } else if (guess == 2) {
         RUN(R, PIC_POISSON_PHASE_FORWARD, launch_copy_guess(P.guess, P.g_fft, R.st));
         R.account(PIC_POISSON_PHASE_FORWARD, 2.0 * n0 * sizeof(double2), 0.0);
+    } else if (!mixed && P.shared.fmg && P.Lmax > 1) {
+        int rc = fmg_start(R);   // writes every level-0 iterate
+        if (rc) return rc;
     } else if (!mixed) {   // (the mixed form's first defect writes the zero iterate itself)
         for (const ProblemPlan &q : P.pr) {
             const size_t n = (size_t)q.lv[0].nr * q.lv[0].nz * q.nm;

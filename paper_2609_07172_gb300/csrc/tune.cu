@@ -6,7 +6,8 @@
 // size and one entry per thread; stage 2 times the other block sizes for the
 // best schedule, stage 3 strips of 2 and 4 rows at the best block size, stage 4
 // over-relaxation factors with the short schedules, stage 5 (mixed precision)
-// the fused FP32 smoother with the short schedules and 1 to 6 inner cycles.  Each
+// the fused FP32 smoother with the short schedules and 1 to 6 inner cycles
+// (FP64: the full-multigrid start with three schedules).  Each
 // candidate gets its own plan, one untimed solve (which also captures the
 // graph when PIC_POISSON_GRAPH is set) and `repeats` timed solves; its score
 // is the median wall time of a solve call, which includes every host-side
@@ -24,7 +25,7 @@ namespace {
 struct Cand {
     int pre, post, inner, threads, strip;
     double omega;
-    int fused;
+    int fused, fmg;
     double ms;
 };
 
@@ -39,6 +40,7 @@ int time_candidate(const pic_poisson_desc *descs, int n, const double *const *rh
         x.smooth_strip = c.strip;
         x.omega = c.omega;
         x.smooth_fused = c.fused;
+        x.fmg = c.fmg;
         x.flags &= ~PIC_POISSON_PROFILE;
     }
     pic_poisson_plan_t plan = nullptr;
@@ -79,12 +81,12 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
     std::vector<Cand> cands;
     for (const auto &s : sched) {
         if (mixed) {
-            for (int inner = 1; inner <= 4; ++inner) cands.push_back({s[0], s[1], inner, 256, 0, 1.0, 0, 0.0});
+            for (int inner = 1; inner <= 4; ++inner) cands.push_back({s[0], s[1], inner, 256, 0, 1.0, 0, 0, 0.0});
         } else {
-            cands.push_back({s[0], s[1], 2, 256, 0, 1.0, 0, 0.0});
+            cands.push_back({s[0], s[1], 2, 256, 0, 1.0, 0, 0, 0.0});
         }
     }
-    Cand best{0, 0, 0, 0, 0, 1.0, 0, 1e300};
+    Cand best{0, 0, 0, 0, 0, 1.0, 0, 0, 1e300};
     int last_err = PIC_POISSON_OK;
     auto record = [&](Cand &c) {
         const int rc = time_candidate(descs, n, rho_dev, phi_dev, tol, stream, repeats, c);
@@ -100,6 +102,7 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
             out->strip_tried[k] = c.strip;
             out->omega_tried[k] = c.omega;
             out->fused_tried[k] = c.fused;
+            out->fmg_tried[k] = c.fmg;
         }
         if (c.ms < best.ms) best = c;
         return rc;
@@ -113,12 +116,12 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
         return last_err ? last_err : PIC_POISSON_ENOTCONVERGED;
     }
     for (int threads : {64, 128, 512}) {
-        Cand c{best.pre, best.post, best.inner, threads, 0, 1.0, 0, 0.0};
+        Cand c{best.pre, best.post, best.inner, threads, 0, 1.0, 0, 0, 0.0};
         const int rc = record(c);
         if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;
     }
     for (int strip : {2, 4}) {
-        Cand c{best.pre, best.post, best.inner, best.threads, strip, 1.0, 0, 0.0};
+        Cand c{best.pre, best.post, best.inner, best.threads, strip, 1.0, 0, 0, 0.0};
         const int rc = record(c);
         if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;
     }
@@ -126,17 +129,24 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
     const Cand base = best;
     for (double omega : {1.1, 1.2, 1.3})
         for (const auto &s : sor_sched) {
-            Cand c{s[0], s[1], base.inner, base.threads, base.strip, omega, 0, 0.0};
+            Cand c{s[0], s[1], base.inner, base.threads, base.strip, omega, 0, 0, 0.0};
             const int rc = record(c);
             if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;
         }
     if (mixed)
         for (const auto &s : sor_sched)
             for (int inner = 1; inner <= 6; ++inner) {
-                Cand c{s[0], s[1], inner, base.threads, base.strip, 1.0, 1, 0.0};
+                Cand c{s[0], s[1], inner, base.threads, base.strip, 1.0, 1, 0, 0.0};
                 const int rc = record(c);
                 if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;
             }
+    static const int fmg_sched[][2] = {{1, 2}, {2, 1}, {2, 2}};
+    if (!mixed)
+        for (const auto &s : fmg_sched) {
+            Cand c{s[0], s[1], base.inner, base.threads, base.strip, 1.0, 0, 1, 0.0};
+            const int rc = record(c);
+            if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;
+        }
     out->pre_sweeps = best.pre;
     out->post_sweeps = best.post;
     out->inner_cycles = best.inner;
@@ -144,6 +154,7 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
     out->smooth_strip = best.strip;
     out->omega = best.omega;
     out->smooth_fused = best.fused;
+    out->fmg = best.fmg;
     out->ms = best.ms;
     return PIC_POISSON_OK;
 }

@@ -124,19 +124,20 @@ def test_autotune_picks_a_working_schedule(precision, tmp_path):
     cache = str(tmp_path / "tune.json")
     best = autotune([p], [rho], tol=1e-10, precision=precision, graph=True, repeats=1, cache=cache)
     n_sched = 7 * (4 if precision == MIXED else 1)
-    # + block sizes, strips 2, 4, 3 omegas x 4 schedules, and (mixed) the fused smoother x 4 schedules x 6
-    assert len(best["tried"]) == n_sched + 5 + 12 + (24 if precision == MIXED else 0)
+    # + block sizes, strips 2, 4, 3 omegas x 4 schedules, and the fused smoother x 4 schedules x 6 (mixed)
+    # or the full-multigrid start x 3 schedules (FP64)
+    assert len(best["tried"]) == n_sched + 5 + 12 + (24 if precision == MIXED else 3)
     assert best["smooth_threads"] in (64, 128, 256, 512)
     assert best["smooth_strip"] in (0, 2, 4)
     assert best["omega"] in (1.0, 1.1, 1.2, 1.3)
     assert best["ms"] == min(t["ms"] for t in best["tried"])
     again = autotune([p], [rho], tol=1e-10, precision=precision, graph=True, cache=cache)   # cached
     assert {k: again[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads", "smooth_strip", "omega",
-                               "smooth_fused")} == \
+                               "smooth_fused", "fmg")} == \
            {k: best[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads", "smooth_strip", "omega",
-                               "smooth_fused")}
+                               "smooth_fused", "fmg")}
     kw = {k: best[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads", "smooth_strip", "omega",
-                               "smooth_fused")}
+                               "smooth_fused", "fmg")}
     with Plan(p, precision=precision, graph=True, **kw) as plan:
         phi, info = plan.solve(rho, tol=1e-10)
     assert info["status"] == B.OK and info["rel_res"] <= 1e-10

@@ -282,3 +282,29 @@ def test_local_bottom_is_bitwise_the_level_kernels(dims, prec):
         out.append((phi.cpu(), info["cycles"]))
     assert out[0][1] == out[1][1]
     assert torch.equal(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("dims", [(64, 32, 48), (96, 16, 40), (64, 8, 400), (256, 8, 32), (40, 8, 24)])
+def test_full_multigrid_start_matches_oracle(dims):
+    """A solve started by a full-multigrid pass converges to the oracle's
+    solution and reaches a given tolerance in no more cycles than from zero."""
+    p = with_bias_walls(W.annulus(*dims))
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=43)
+    ref, _ = oracle.solve3d(g, rho, tol=1e-15)
+    with Plan(p, fmg=1) as plan:
+        phi, info = plan.solve(dev(rho), tol=0.0)
+    assert info["status"] == B.OK
+    assert rel_l2(phi.cpu().numpy(), ref) <= FP64_TOL, info
+    cyc = []
+    for f in (0, 1):
+        with Plan(p, fmg=f, graph=True) as plan:
+            _, info = plan.solve(dev(rho), tol=1e-10)
+        assert info["status"] == B.OK and info["rel_res"] <= 1e-10
+        cyc.append(info["cycles"])
+    assert cyc[1] <= cyc[0], cyc
+
+
+def test_full_multigrid_needs_fp64():
+    with pytest.raises(PicPoissonError):
+        Plan(W.annulus(32, 8, 32), precision=B.MIXED, fmg=1)
