@@ -63,6 +63,9 @@ extern "C" {
 #define PIC_POISSON_GRAPH 4u              /* run each solve as one CUDA graph: the convergence loop is a
                                              device-side while node (captured on the first solve; ignored
                                              together with PIC_POISSON_PROFILE) */
+#define PIC_POISSON_HOST_STAGED 8u        /* pic_poisson_solve_host always copies through device staging
+                                             buffers (default: mapped page-locked host buffers are read and
+                                             written in place by the transforms) */
 
 /* kernel classes, indices into pic_poisson_info.ms_phase / launches_phase */
 #define PIC_POISSON_PHASE_FORWARD 0   /* azimuthal rFFT + right-hand side */
@@ -115,7 +118,7 @@ typedef struct {
 
 typedef struct {
     int status;                /* return code of the call */
-    int cycles;                /* coarse-grid corrections applied */
+    int cycles;                /* coarse-grid corrections applied (to this problem, in a batch) */
     int outer_iterations;      /* FP64 defect corrections (mixed precision) */
     int launches;              /* kernels this call launched */
     double rel_res0;           /* relative residual at the first convergence test: of the initial iterate
@@ -213,8 +216,9 @@ int pic_poisson_solve(pic_poisson_plan_t plan, const double *rho_dev, double *ph
 /*
  * Solve every problem of a batched plan: rho_dev[p] -> phi_dev[p] (host
  * arrays of n device pointers, layouts as for pic_poisson_solve).  Iterates
- * until every problem meets tol (problems that already did keep being
- * iterated, so each returned phi has at least the reported accuracy).  infos
+ * until every problem meets tol; a problem that does is not iterated further
+ * (its kernels skip it), so each returned phi is the iterate whose residual is
+ * reported.  infos
  * (n entries, may be NULL): per-problem status, cycles and residuals; the
  * timing, byte and launch counters are those of the whole batched solve.
  * Returns ENONFINITE if any problem has it, else ENOTCONVERGED if any, else OK.
@@ -265,9 +269,15 @@ int pic_poisson_analyze(pic_poisson_plan_t plan, const double *phi_dev, double *
 int pic_poisson_get_modes(pic_poisson_plan_t plan, double *uhat_dev);
 
 /*
- * As pic_poisson_solve with host buffers (pinned or pageable): copies rho_host
- * to the device, solves, copies phi back; returns after phi_host is written.
- * The device staging buffers are part of the plan's workspace (allocated on
+ * As pic_poisson_solve with host buffers (pinned or pageable); returns after
+ * phi_host is written.  When both buffers are page-locked host memory mapped
+ * into the device's address space (cudaHostAlloc / cudaMallocHost, or
+ * cudaHostRegister with the mapped flag, under unified addressing) and the
+ * plan lacks PIC_POISSON_HOST_STAGED, the forward transform reads rho_host
+ * and the inverse transform writes phi_host in place over the CPU-GPU link,
+ * so the transfers overlap the transforms' arithmetic.  Otherwise rho_host is
+ * copied to a device staging buffer, the solve runs there and phi is copied
+ * back; the staging buffers are part of the plan's workspace (allocated on
  * first use).
  */
 int pic_poisson_solve_host(pic_poisson_plan_t plan, const double *rho_host, double *phi_host, double tol,

@@ -14,7 +14,7 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE = 0, 1, 2, 3, 4, 5
 FP64, MIXED = 0, 1
-USE_INITIAL_GUESS, PROFILE, GRAPH = 1, 2, 4
+USE_INITIAL_GUESS, PROFILE, GRAPH, HOST_STAGED = 1, 2, 4, 8
 MAX_BATCH = 64
 PHASES = ("forward", "smooth", "smooth_coarse", "restrict", "coarse", "prolong", "norm", "inverse", "defect")
 MAX_LEVELS = 16
@@ -229,11 +229,12 @@ class Plan:
 
     def __init__(self, problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
                  profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False,
-                 smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0, local_bottom=0, fmg=0):
+                 smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0, local_bottom=0, fmg=0,
+                 host_staged=False):
         import torch
         self.problem = problem
         flags = ((PROFILE if profile else 0) | (USE_INITIAL_GUESS if initial_guess else 0)
-                 | (GRAPH if graph else 0))
+                 | (GRAPH if graph else 0) | (HOST_STAGED if host_staged else 0))
         self._desc, self._keep = make_desc(problem, precision, max_cycles, pre_sweeps, post_sweeps, flags,
                                            inner_cycles, smooth_threads, smooth_strip, omega,
                                            smooth_fused, local_bottom, fmg)
@@ -282,7 +283,9 @@ class Plan:
         return phi, info.as_dict()
 
     def solve_host(self, rho_host, phi_host, tol=1e-10):
-        """Solve from host tensors (CPU, float64, contiguous; pinned for speed)."""
+        """Solve from host tensors (CPU, float64, contiguous).  Pinned tensors are
+        read and written in place by the transforms unless the plan was made
+        with host_staged=True; pageable ones go through device staging copies."""
         for t, name in ((rho_host, "rho_host"), (phi_host, "phi_host")):
             if t.is_cuda or not t.is_contiguous() or tuple(t.shape) != self.shape:
                 raise ValueError(f"{name} must be a contiguous CPU tensor of shape {self.shape}")

@@ -82,6 +82,7 @@ template <class T>
 __global__ void __launch_bounds__(BOTTOM_THREADS) k_bottom(const BottomTab<T> *__restrict__ tab) {
     extern __shared__ unsigned char smraw[];
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const BottomProb<T> &B = tab->p[p];
     const LevelDev<T> &U = B.U;
     const CoarseDev<T> &D = B.D;

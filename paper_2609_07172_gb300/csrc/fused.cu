@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
     float2 *bring = uring + UR * 2 * NT;            // [BR][NB][NT]
     float2 *pubs = bring + BR * NB * NT + PAD;      // [2][NP][NT + 2 PAD], PAD entries before each row
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const FusedProb &F = tab->p[p];
     const LevelDev<float> &L = F.L;
     const int nr = L.nr, nz = L.nz, nm = L.nm, ncls = L.ncls;

@@ -78,8 +78,13 @@ template <class T> struct CoarseDev {
 
 // Work of one launch over a batch of problems: problem p owns the blocks
 // [start[p], start[p+1]) of the grid; f / c are its fine / coarse level views.
+// done: the convergence loop's per-problem stop flags (Ctrl::done) or null;
+// blocks of a problem that has stopped return at once, so its iterate stays
+// the one whose residual was reported while other problems of the batch go on.
 template <class T> struct LaunchTab {
     int n;
+    const int *done;
+    int pid[kMaxBatch];           // problem index of each entry (entries list only the problems that take part)
     unsigned start[kMaxBatch + 1];
     LevelDev<T> f[kMaxBatch];
     LevelDev<T> c[kMaxBatch];
@@ -87,6 +92,8 @@ template <class T> struct LaunchTab {
 
 template <class T> struct CoarseTab {
     int n;
+    const int *done;
+    int pid[kMaxBatch];           // problem index of each entry (entries list only the problems that take part)
     unsigned start[kMaxBatch + 1];
     LevelDev<T> f[kMaxBatch];
     CoarseDev<T> c[kMaxBatch];
@@ -95,6 +102,8 @@ template <class T> struct CoarseTab {
 
 struct DefectTab {                // mixed precision: FP64 level 0 and FP32 level 0 of each problem
     int n;
+    const int *done;
+    int pid[kMaxBatch];           // problem index of each entry (entries list only the problems that take part)
     unsigned start[kMaxBatch + 1];
     LevelDev<double> d[kMaxBatch];
     LevelDev<float> s[kMaxBatch];
@@ -230,6 +239,8 @@ struct FusedProb {
 };
 struct FusedTab {
     int n;
+    const int *done;
+    int pid[kMaxBatch];           // problem index of each entry (entries list only the problems that take part)
     unsigned start[kMaxBatch + 1];
     FusedProb p[kMaxBatch];
 };
@@ -250,6 +261,8 @@ template <class T> struct BottomProb {
 };
 template <class T> struct BottomTab {
     int n;
+    const int *done;
+    int pid[kMaxBatch];           // problem index of each entry (entries list only the problems that take part)
     unsigned start[kMaxBatch + 1];
     BottomProb<T> p[kMaxBatch];
 };

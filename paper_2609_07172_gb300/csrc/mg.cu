@@ -124,6 +124,7 @@ __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i,
 template <class T, int NT, int S, bool SOR>
 __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const LaunchTab<T> *__restrict__ tab, int color) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const LevelDev<T> L = tab->f[p];
     const unsigned nm = L.nm;
     if constexpr (S == 0) {
@@ -213,6 +214,7 @@ __global__ void __launch_bounds__(MG_THREADS)
 k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ partials) {
     __shared__ double red[MG_THREADS];
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const LevelDev<T> F = tab->f[p];
     const LevelDev<T> C = tab->c[p];
     const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
@@ -281,6 +283,7 @@ __global__ void __launch_bounds__(MG_THREADS)
 k_residual(const LaunchTab<T> *__restrict__ tab, int write_r, double *__restrict__ partials, unsigned stride) {
     __shared__ double red[MG_THREADS];
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const LevelDev<T> L = tab->f[p];
     const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
     double ar = 0.0, ab = 0.0;
@@ -317,6 +320,7 @@ k_residual(const LaunchTab<T> *__restrict__ tab, int write_r, double *__restrict
 template <class T, bool BLACK_ONLY, bool ASSIGN = false>
 __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__restrict__ tab) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const LevelDev<T> F = tab->f[p];
     const LevelDev<T> C = tab->c[p];
     const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
@@ -367,6 +371,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
 template <class T>
 __global__ void __launch_bounds__(MG_THREADS) k_rhs_restrict(const LaunchTab<T> *__restrict__ tab) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const LevelDev<T> F = tab->f[p];
     const LevelDev<T> C = tab->c[p];
     const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
@@ -440,6 +445,7 @@ __global__ void __launch_bounds__(MG_THREADS)
 k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, double *__restrict__ partials) {
     __shared__ double red[MG_THREADS];
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const LevelDev<double> D = tab->d[p];
     const LevelDev<float> S = tab->s[p];
     const int init_red = tab->init_red[p];
@@ -476,6 +482,7 @@ k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, doubl
 // problem just solved; 1/sigma is an exact power of two).
 __global__ void __launch_bounds__(MG_THREADS) k_update(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const LevelDev<double> D = tab->d[p];
     const LevelDev<float> S = tab->s[p];
     const int ls = pow2_exponent(ctrl->inv_sigma_used[p]);
@@ -506,6 +513,7 @@ template <class T>
 __global__ void __launch_bounds__(MG_THREADS) k_coarse(const CoarseTab<T> *__restrict__ tab) {
     extern __shared__ unsigned char smraw[];
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const LevelDev<T> L = tab->f[p];
     const CoarseDev<T> D = tab->c[p];
     const int nr = D.nr, nz = D.nz, nm = D.nm;
@@ -627,8 +635,9 @@ __global__ void __launch_bounds__(1024) k_bnorm(Ctrl *__restrict__ ctrl, const F
 // residual scaled by sigma), rel = ||r|| / ||b||, and the stop rule: tol > 0
 // stops at rel <= tol; tol <= 0 stops once rel has not halved for two
 // evaluations (the rounding floor); non-finite stops with ENONFINITE; the
-// cycle cap with ENOTCONVERGED.  Problems that stopped keep being iterated
-// (their rel keeps describing the returned iterate) until all have stopped.
+// cycle cap with ENOTCONVERGED.  A problem that stopped is left alone: the
+// kernels skip its blocks (launch tables' done flags) and its rel stays the
+// residual of its returned iterate while the others go on.
 // counting: add ctrl->inc to the cycle count first (evaluations after a pass
 // of the loop body).  When use_handle, sets the graph's while-condition.
 __global__ void __launch_bounds__(1024) k_check(Ctrl *__restrict__ ctrl, const double *__restrict__ partials,
@@ -641,6 +650,7 @@ __global__ void __launch_bounds__(1024) k_check(Ctrl *__restrict__ ctrl, const d
     range_sums(partials, ctrl->rbegin, ctrl->rend, ctrl->n, sums, wsum);
     const double tol = ctrl->tol;
     for (int p = threadIdx.x; p < ctrl->n; p += blockDim.x) {
+        if (ctrl->done[p]) continue;   // stopped: its kernels no longer run, rel stays the reported one
         double rr2 = sums[p];
         if (ctrl->scaled) {
             const double su = ctrl->sigma_next[p];
@@ -653,7 +663,7 @@ __global__ void __launch_bounds__(1024) k_check(Ctrl *__restrict__ ctrl, const d
         const double rel = bb > 0.0 ? sqrt(rr2 / bb) : sqrt(rr2);
         ctrl->rel[p] = rel;
         if (!counting) ctrl->rel_first[p] = rel;
-        if (!ctrl->done[p]) {
+        {
             int stop = 0, status = PIC_POISSON_OK;
             if (isnan(rel) || isinf(rel)) {
                 stop = 1;

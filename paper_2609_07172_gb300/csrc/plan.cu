@@ -2,6 +2,7 @@
 // coefficient tables (step a-2), coarsest-level factors, device workspace and
 // the launch tables that let one kernel launch serve a batch of problems.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -32,7 +33,8 @@ constexpr double kEps0 = 8.8541878128e-12;   // F/m, CODATA 2018
 constexpr int kMaxNtheta = 256;
 constexpr int kMaxCoarseCells = 4096;
 constexpr int kMaxCoarseNz = 64;
-constexpr unsigned kKnownFlags = PIC_POISSON_USE_INITIAL_GUESS | PIC_POISSON_PROFILE | PIC_POISSON_GRAPH;
+constexpr unsigned kKnownFlags =
+    PIC_POISSON_USE_INITIAL_GUESS | PIC_POISSON_PROFILE | PIC_POISSON_GRAPH | PIC_POISSON_HOST_STAGED;
 
 int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
     if (!in) {
@@ -261,6 +263,13 @@ struct Carver {
     }
 };
 
+// Device address of the convergence loop's per-problem stop flags, for the
+// kernels' early exit; null for a single problem, whose loop simply ends.
+const int *ctrl_done(const pic_poisson_plan_s &P) {
+    if (P.n < 2) return nullptr;
+    return reinterpret_cast<const int *>(reinterpret_cast<const char *>(P.ctrl) + offsetof(Ctrl, done));
+}
+
 int setup_problem(ProblemPlan &q, const pic_poisson_desc &d) {
     q.d = d;
     if (d.phi_r_in_z) {
@@ -431,6 +440,7 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
     for (int l = 0; l < nl; ++l) {
         LaunchTab<T> ts{}, tr{}, tp{};
         FusedTab fa{}, fb{};
+        ts.done = tr.done = tp.done = fa.done = fb.done = ctrl_done(P);
         int nprob = 0;
         bool res = H.fused;   // restriction fused into pre-smoothing: every pair of levels halves r and z
         for (int p = 0; p < P.n; ++p)
@@ -458,6 +468,7 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
             f.init = (l + 1 == q.L - 1) ? 0 : (pre > 0 ? 2 : 1);
             const size_t half = (size_t)f.nz * (f.nr / 2) * f.nm, full = (size_t)f.nz * f.nr * f.nm;
             const size_t coarse_n = (size_t)v[l + 1].nz * v[l + 1].nr * f.nm;
+            ts.pid[ts.n] = tr.pid[tr.n] = tp.pid[tp.n] = p;
             ts.f[ts.n] = f;
             ts.f[ts.n].strip = strip;
             ts.start[ts.n + 1] = ts.start[ts.n] + (strip == 0 ? mg_blocks(half, P.shared.smooth_threads)
@@ -484,6 +495,7 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
                     a.in = f.u;
                     a.out = q.u2[l];
                     fused_shape(f.nr, f.nz, f.nm, 2 * pre, res, target, a, nb);
+                    fa.pid[fa.n] = p;
                     fa.p[fa.n] = a;
                     fa.start[fa.n + 1] = fa.start[fa.n] + nb;
                     ++fa.n;
@@ -492,6 +504,7 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
                     b.in = q.u2[l];
                     b.out = f.u;
                     fused_shape(f.nr, f.nz, f.nm, 2 * post, false, target, b, nb);
+                    fb.pid[fb.n] = p;
                     fb.p[fb.n] = b;
                     fb.start[fb.n + 1] = fb.start[fb.n] + nb;
                     ++fb.n;
@@ -549,6 +562,7 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
     }
     CoarseTab<T> tc{};
     BottomTab<T> tb{};
+    tc.done = tb.done = ctrl_done(P);
     size_t smem_b = 0;
     for (int p = 0; p < P.n; ++p) {
         const ProblemPlan &q = P.pr[p];
@@ -562,12 +576,14 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
             bp.post = post;
             bp.red_only = pre > 0 && P.shared.omega == 1.0;
             bp.black_only = post > 0 && P.shared.omega == 1.0;
+            tb.pid[tb.n] = p;
             tb.p[tb.n] = bp;
             tb.start[tb.n + 1] = tb.start[tb.n] + 2u * (unsigned)q.nm;   // (mode, real / imaginary part)
             smem_b = std::max(smem_b, bottom_smem_bytes<T>(U.nr, U.nz, U.ncls, cd.nr, cd.nz));
             ++tb.n;
             continue;
         }
+        tc.pid[tc.n] = p;
         tc.f[tc.n] = views(q)[q.L - 1];
         tc.c[tc.n] = cd;
         tc.start[tc.n + 1] = tc.start[tc.n] + 2u * (unsigned)q.nm;   // (mode, real / imaginary part)
@@ -693,15 +709,18 @@ int upload(pic_poisson_plan_s &P) {
     // single-level problems' residual norms; defect table; stage-call table
     LaunchTab<double> rs{};
     DefectTab dt{};
+    rs.done = dt.done = ctrl_done(P);
     for (int p = 0; p < P.n; ++p) {
         const ProblemPlan &q = P.pr[p];
         const size_t n0 = (size_t)q.lv[0].nr * q.lv[0].nz * q.nm;
         if (q.L == 1) {
+            rs.pid[rs.n] = p;
             rs.f[rs.n] = q.dl[0];
             rs.start[rs.n + 1] = rs.start[rs.n] + mg_blocks(n0);
             ++rs.n;
         }
         if (mixed) {
+            dt.pid[dt.n] = p;
             dt.d[dt.n] = q.dl[0];
             dt.s[dt.n] = q.fl[0];
             dt.init_red[dt.n] = (q.L > 1 && P.shared.pre_sweeps > 0) ? 1 : 0;

@@ -550,8 +550,8 @@ int solve_batch(pic_poisson_plan_s &P, const double *const *rho, double *const *
         pic_poisson_info &I = infos[p];
         memset(&I, 0, sizeof I);
         I.status = s;
-        I.cycles = C.cycles;
-        I.outer_iterations = P.shared.precision == PIC_POISSON_MIXED ? C.cycles / inc : 0;
+        I.cycles = C.done_cycles[p];   // a problem of a batch stops being iterated when it converges
+        I.outer_iterations = P.shared.precision == PIC_POISSON_MIXED ? C.done_cycles[p] / inc : 0;
         I.rel_res = C.rel[p];
         I.rel_res0 = C.rel_first[p];
         for (int ph = 0; ph < PIC_POISSON_NPHASE; ++ph) {
@@ -573,6 +573,17 @@ int single_only(const pic_poisson_plan_s &P, const char *what) {
         return PIC_POISSON_EINVAL;
     }
     return PIC_POISSON_OK;
+}
+
+// Device address of page-locked host memory mapped into the device's address
+// space, or null (pageable or unregistered memory: the caller stages).
+void *mapped_host(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 }  // namespace
@@ -629,6 +640,11 @@ int pic_poisson_solve_host(pic_poisson_plan_t plan, const double *rho_host, doub
     pic_poisson_plan_s &P = *plan;
     const pic_poisson_desc &d = P.pr[0].d;
     const size_t bytes = (size_t)d.nr * d.ntheta * d.nz * sizeof(double);
+    if (!(P.shared.flags & PIC_POISSON_HOST_STAGED)) {
+        const double *r = static_cast<const double *>(mapped_host(rho_host));
+        double *f = static_cast<double *>(mapped_host(phi_host));
+        if (r && f) return solve_batch(P, &r, &f, tol, info);   // synchronises before it returns
+    }
     if (!P.stage_rho) {
         cudaError_t err = cudaMalloc(&P.stage_rho, bytes);
         if (err == cudaSuccess) err = cudaMalloc(&P.stage_phi, bytes);

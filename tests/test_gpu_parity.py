@@ -234,10 +234,19 @@ def test_deterministic_and_host_entry_point_agree():
         b, _ = plan.solve(dev(rho), tol=1e-10)
         rho_h = torch.from_numpy(rho).pin_memory()
         phi_h = torch.empty(p.shape, dtype=torch.float64).pin_memory()
-        info = plan.solve_host(rho_h, phi_h, tol=1e-10)
+        info = plan.solve_host(rho_h, phi_h, tol=1e-10)          # mapped pinned buffers, read in place
+        phi_p = torch.zeros(p.shape, dtype=torch.float64)
+        info_p = plan.solve_host(torch.from_numpy(rho.copy()), phi_p, tol=1e-10)   # pageable: staged
+    with Plan(p, host_staged=True, graph=True) as plan:
+        phi_s = torch.zeros(p.shape, dtype=torch.float64).pin_memory()
+        info_s = plan.solve_host(rho_h, phi_s, tol=1e-10)       # pinned, forced through staging
+        phi_g = torch.zeros(p.shape, dtype=torch.float64).pin_memory()
+    with Plan(p, graph=True) as plan:
+        info_g = plan.solve_host(rho_h, phi_g, tol=1e-10)       # in place, inside the captured graph
     assert torch.equal(a, b)
-    assert torch.equal(a.cpu(), phi_h)
-    assert info["status"] == B.OK
+    for ph, inf in ((phi_h, info), (phi_p, info_p), (phi_s, info_s), (phi_g, info_g)):
+        assert torch.equal(a.cpu(), ph)
+        assert inf["status"] == B.OK
 
 
 def test_profile_counts_launches():
