@@ -64,17 +64,30 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-constexpr int DEPTH = 4;          // rows in flight ahead of the window
-constexpr int UR = DEPTH + 1;     // iterate ring slots (the slot refilled is never the one just read)
 constexpr int PAD = 16;           // >= the largest mode group: neighbour reads of the outermost pairs stay in the array
 
-// Slots of the ring that holds b_hat (and b) per row: a row's entries are read
-// by half-sweeps up to NH steps after it entered (the restriction NH + 1).
-template <int NH> __host__ __device__ constexpr int b_ring() { return DEPTH + NH + 2; }
-template <int NH, bool RES> constexpr size_t fused_smem_floats2() {
-    return (size_t)UR * 2 * FUSED_THREADS + (size_t)b_ring<NH>() * (RES ? 3 : 2) * FUSED_THREADS + PAD +
-           (size_t)2 * (NH + (RES ? 1 : 0)) * (FUSED_THREADS + 2 * PAD);
-}
+// Sizes of a variant.  A step touches W0 rows; the register window holds W
+// rows (W0 made even) and the row loop is unrolled by W, so in each unrolled
+// copy the register that holds a given row, the parity of every row (hence
+// the colour a half-sweep updates in a pair and the column a thread
+// publishes), the publication buffer and the iterate's ring slot are
+// compile-time constants: no register shifts, selects or slot arithmetic per
+// step.  The iterate's ring has UR slots (UR divides W) and is fetched
+// DEPTH = UR - 1 rows ahead; b_hat (and b) stay in a ring of BR slots until
+// their last half-sweep (the restriction: NH + 1 steps after the row entered).
+template <int NH, bool RES> struct FusedCfg {
+    static constexpr int W0 = NH + 2 + (RES ? 1 : 0);
+    static constexpr int W = W0 + (W0 & 1);
+    static constexpr int UR = (W % 6 == 0) ? 6 : 4;
+    static constexpr int DEPTH = UR - 1;
+    static constexpr int BR = DEPTH + NH + 2;
+    static constexpr int NB = RES ? 3 : 2;                  // b_hat col 0, b_hat col 1 (, b of the red cell)
+    static constexpr int NP = NH + (RES ? 1 : 0);           // published columns per step
+    static constexpr int PS = FUSED_THREADS + 2 * PAD;      // published row stride
+    static constexpr size_t smem_floats2 =
+        (size_t)UR * 2 * FUSED_THREADS + (size_t)BR * NB * FUSED_THREADS + PAD + (size_t)2 * NP * PS;
+    static_assert(W % UR == 0 && W % 2 == 0, "unrolled copies need static ring slots and parities");
+};
 
 // RES (pre-smoothing of a level coarsened 2:1 in both directions): after the
 // last half-sweep, the kernel also evaluates the residual of the red cells
@@ -85,16 +98,15 @@ template <int NH, bool RES> constexpr size_t fused_smem_floats2() {
 // neighbouring columns, so the halo grows by one row and one column pair.
 template <int NH, bool RES>
 __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTab *__restrict__ tab) {
-    constexpr int W = NH + 2 + (RES ? 1 : 0);   // window rows: k-W+1 .. k
+    using Cfg = FusedCfg<NH, RES>;
+    constexpr int W = Cfg::W, UR = Cfg::UR, DEPTH = Cfg::DEPTH, BR = Cfg::BR, NB = Cfg::NB, NP = Cfg::NP;
+    constexpr int PS = Cfg::PS;
     constexpr int HP = NH / 2 + (RES ? 1 : 0);  // halo pairs on each side
     constexpr int NT = FUSED_THREADS;
-    constexpr int NP = NH + (RES ? 1 : 0);      // published columns per step
-    constexpr int BR = b_ring<NH>();
-    constexpr int NB = RES ? 3 : 2;             // b_hat col 0, b_hat col 1 (, b of the red cell)
     extern __shared__ float2 dsm[];
     float2 *uring = dsm;                            // [UR][2][NT]
     float2 *bring = uring + UR * 2 * NT;            // [BR][NB][NT]
-    float2 *pubs = bring + BR * NB * NT + PAD;      // [2][NP][NT + 2 PAD], PAD entries before each row
+    float2 *pubs = bring + BR * NB * NT + PAD;      // [2][NP][PS], PAD entries before each row
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const FusedProb &F = tab->p[p];
@@ -118,7 +130,9 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
     const bool outpair = pl >= HP && pl < P - HP;
     const int hr = NH + (RES ? 1 : 0);                       // halo rows
     const int k0 = kr * F.R, k1 = min(nz, k0 + F.R);
-    const int ks = max(0, k0 - hr), ke = min(nz, k1 + hr);  // rows read: [ks, ke)
+    // rows read: [ks, ke); ks is even (one more halo row when k0 - hr is odd),
+    // so row k of unrolled copy c has the parity of c
+    const int ks = max(0, (k0 - hr) & ~1), ke = min(nz, k1 + hr);
     const int klast = k1 - 1 + hr;                           // last step
 
     const size_t rs = (size_t)nr * nm;
@@ -173,44 +187,40 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
     float2 *const gout = F.out;
 
     const float2 zero = make_float2(0.f, 0.f);
+    // window: row k - d lives in register (c - d) mod W at unrolled copy c
     float2 u0[W], u1[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) u0[w] = u1[w] = zero;
-    int buf = 0;
-    int uslot = 0, bslot = 0;   // ring slots of the row entering now
-    // The window holds row k - d at index W - 1 - d; it shifts by one row per
-    // step (register moves), which keeps the loop body a single copy -- an
-    // unrolled rotation would multiply the code by W.
+    int bsl = 0;   // b ring slot of the row entering now
+#define IX(d) ((((c) - (d)) % W + W) % W)
 #pragma unroll 1
-    for (int k = ks; k <= klast; ++k) {   // the row entering at this step
-        {
-            // (a) row k into the window; fetch row k + DEPTH
+    for (int n0 = 0;; n0 += W) {
 #pragma unroll
-            for (int w = 0; w + 1 < W; ++w) {
-                u0[w] = u0[w + 1];
-                u1[w] = u1[w + 1];
-            }
+        for (int c = 0; c < W; ++c) {
+            const int k = ks + n0 + c;   // the row entering at this step
+            if (k > klast) goto finished;   // uniform
+            const int buf = c & 1;          // publication buffer written at this step
+            // (a) row k into the window; fetch row k + DEPTH
             cp_async_wait<DEPTH - 1>();
-            u0[W - 1] = uring[uslot * 2 * NT + t];
-            u1[W - 1] = uring[uslot * 2 * NT + NT + t];
+            u0[IX(0)] = uring[(c % UR) * 2 * NT + t];
+            u1[IX(0)] = uring[(c % UR) * 2 * NT + NT + t];
             {
-                int us = uslot + DEPTH, bs = bslot + DEPTH;
-                if (us >= UR) us -= UR;
+                int bs = bsl + DEPTH;
                 if (bs >= BR) bs -= BR;
-                fetch(k + DEPTH, us, bs);
+                fetch(k + DEPTH, (c + DEPTH) % UR, bs);
             }
             // (b) half-sweep s on row k - 1 - s
 #pragma unroll
             for (int s = 0; s < NH; ++s) {
                 const int r = k - 1 - s;
                 if (r < ks || r >= ke) continue;           // uniform
-                const int sl = W - 2 - s;   // row r
-                const int sn = W - 1 - s;   // row r + 1
-                const int ss = W - 3 - s;   // row r - 1
-                const int q = (r + (s & 1)) & 1;           // the pair's cell of this colour (uniform)
+                const int sl = IX(1 + s);   // row r
+                const int sn = IX(s);       // row r + 1
+                const int ss = IX(2 + s);   // row r - 1
+                const int q = (c - 1 - s + (s & 1)) & 1;   // the pair's cell of this colour (static)
                 const bool edge = r == 0 || r == nz - 1;
-                const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + s) * (NT + 2 * PAD);
-                int rb = bslot - 1 - s;
+                const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + s) * PS;
+                int rb = bsl - 1 - s;
                 if (rb < 0) rb += BR;
                 const float2 *bh = bring + rb * NB * NT + t;
                 // Rows outside the level are zero in the window and the wall
@@ -257,14 +267,14 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
             if (RES) {
                 const int rr = k - NH - 1;
                 if (rr >= k0 && rr < k1) {   // uniform
-                    const int sl = W - 2 - NH, sn = W - 1 - NH, ss = W - 3 - NH;
-                    const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + NH) * (NT + 2 * PAD);
-                    int rb = bslot - NH - 1;
+                    const int sl = IX(NH + 1), sn = IX(NH), ss = IX(NH + 2);
+                    const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + NH) * PS;
+                    int rb = bsl - NH - 1;
                     if (rb < 0) rb += BR;
                     const float2 bred = bring[rb * NB * NT + 2 * NT + t];
                     const bool edge = rr == 0 || rr == nz - 1;
                     float2 res;
-                    if ((rr & 1) == 0) {   // red cell in column 0: west from the left pair
+                    if (((c - NH - 1) & 1) == 0) {   // red cell in column 0: west from the left pair
                         const float d = edge ? L.diag[(size_t)row_class(rr, nz, ncls) * rs + c0] : dg0;
                         const float2 s = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
                         const float2 uw = pr[t - G];
@@ -273,7 +283,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                         a = make_float2(fmaf(ce0, u1[sl].x, a.x), fmaf(ce0, u1[sl].y, a.y));
                         res = make_float2(fmaf(-d, u0[sl].x, a.x), fmaf(-d, u0[sl].y, a.y));
                         rsum = res;
-                    } else {               // red cell in column 1: east from the right pair
+                    } else {                          // red cell in column 1: east from the right pair
                         const float d = edge ? L.diag[(size_t)row_class(rr, nz, ncls) * rs + c1] : dg1;
                         const float2 s = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
                         const float2 ue = pr[t + G];
@@ -301,39 +311,33 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
             // (d) publish for the next step: half-sweep s will update row k - s
             // and read the neighbouring pair's column of the other colour;
             // the restriction reads the final black column of row k - NH
-            float2 *pw = pubs + (size_t)(buf * NP) * (NT + 2 * PAD) + t;
+            float2 *pw = pubs + (size_t)(buf * NP) * PS + t;
 #pragma unroll
             for (int s = 0; s < NH; ++s) {
-                const int sl = W - 1 - s;
-                const int qn = (k - s + (s & 1)) & 1;
-                pw[(size_t)s * (NT + 2 * PAD)] = qn == 0 ? u1[sl] : u0[sl];
+                const int qn = (c - s + (s & 1)) & 1;
+                pw[(size_t)s * PS] = qn == 0 ? u1[IX(s)] : u0[IX(s)];
             }
-            if (RES) {
-                const int sl = W - 1 - NH;
-                const int qn = (k - NH) & 1;   // red column of row k - NH
-                pw[(size_t)NH * (NT + 2 * PAD)] = qn == 0 ? u1[sl] : u0[sl];
-            }
+            if (RES) pw[(size_t)NH * PS] = ((c - NH) & 1) == 0 ? u1[IX(NH)] : u0[IX(NH)];
             // (e) the output row k - NH is final
             const int ro = k - NH;
             if (outpair && ro >= k0 && ro < k1) {
-                const int so = W - 1 - NH;
                 const size_t o = (size_t)ro * rs;
-                if (v0) gout[o + c0] = u0[so];
-                if (v1) gout[o + c1] = u1[so];
+                if (v0) gout[o + c0] = u0[IX(NH)];
+                if (v1) gout[o + c1] = u1[IX(NH)];
             }
             __syncthreads();
-            buf ^= 1;
-            uslot = uslot + 1 == UR ? 0 : uslot + 1;
-            bslot = bslot + 1 == BR ? 0 : bslot + 1;
+            bsl = bsl + 1 == BR ? 0 : bsl + 1;
         }
     }
+#undef IX
+finished:
     cp_async_wait<0>();   // no copy outlives the block
 }
 
 }  // namespace
 
 template <int NH, bool RES> cudaError_t launch_nh(const FusedTab *tab, unsigned grid, cudaStream_t st) {
-    const size_t smem = fused_smem_floats2<NH, RES>() * sizeof(float2);
+    const size_t smem = FusedCfg<NH, RES>::smem_floats2 * sizeof(float2);
     cudaError_t e =
         cudaFuncSetAttribute(k_smooth_fused<NH, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
