@@ -135,18 +135,25 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
     const int ks = max(0, (k0 - hr) & ~1), ke = min(nz, k1 + hr);
     const int klast = k1 - 1 + hr;                           // last step
 
-    const size_t rs = (size_t)nr * nm;
-    const size_t c0 = (size_t)(v0 ? i0 : 0) * nm + (mvalid ? m : 0);
-    const size_t c1 = (size_t)(v1 ? i1 : 0) * nm + (mvalid ? m : 0);
-    const size_t cls1 = ncls > 1 ? rs : 0;
-    const float hz0 = L.hz[cls1 + c0], hw0 = L.hw[cls1 + c0], he0 = L.he[cls1 + c0];
-    const float hz1 = L.hz[cls1 + c1], hw1 = L.hw[cls1 + c1], he1 = L.he[cls1 + c1];
+    // element offsets fit 32 bits: a plan rejects levels of 2^31 entries or more
+    const unsigned rs = (unsigned)nr * nm;
+    const unsigned c0 = (unsigned)(v0 ? i0 : 0) * nm + (mvalid ? m : 0);
+    const unsigned c1 = (unsigned)(v1 ? i1 : 0) * nm + (mvalid ? m : 0);
+    const unsigned cls1 = ncls > 1 ? rs : 0;
+    // Cells outside the level or the mode range get zero coefficients (and a
+    // zero b_hat from the zero-filled copies), so they stay exactly zero
+    // without a predicate on every update: a valid neighbour reads 0, as
+    // when it is left out.
+    const float hz0 = v0 ? L.hz[cls1 + c0] : 0.f, hw0 = v0 ? L.hw[cls1 + c0] : 0.f,
+                he0 = v0 ? L.he[cls1 + c0] : 0.f;
+    const float hz1 = v1 ? L.hz[cls1 + c1] : 0.f, hw1 = v1 ? L.hw[cls1 + c1] : 0.f,
+                he1 = v1 ? L.he[cls1 + c1] : 0.f;
 
     // fetch row `row` into ring slots (zeros for rows outside [ks, ke) and invalid cells)
     const float2 *gin0 = F.in + c0, *gin1 = F.in + c1, *gb0 = L.bh + c0, *gb1 = L.bh + c1;
     auto fetch = [&](int row, int us, int bs) {
         const bool ok = row < ke;
-        const size_t o = (size_t)(ok ? row : ks) * rs;
+        const unsigned o = (unsigned)(ok ? row : ks) * rs;
         float2 *ru = uring + us * 2 * NT + t;
         float2 *rb = bring + bs * NB * NT + t;
         cp_async8(ru, gin0 + o, ok && v0);
@@ -159,6 +166,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
         }
         cp_async_commit();
     };
+    // zero padding around the published rows: the outermost pairs read it
+    for (int e = t; e < 2 * NP * 2 * PAD; e += NT) {
+        const int row = e / (2 * PAD), x = e % (2 * PAD);
+        pubs[row * PS + (x < PAD ? x - PAD : NT + x - PAD)] = make_float2(0.f, 0.f);
+    }
 #pragma unroll
     for (int d = 0; d < DEPTH; ++d) fetch(ks + d, d, d);
 
@@ -182,8 +194,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
     const float *const cinvd = F.C.invd;
     const int cnr = F.C.nr, cnz = F.C.nz, cncls = F.C.ncls, finit = F.init;
     const bool cwrite = RES && outpair && v0 && j < cnr;
-    const size_t ccol = (size_t)(cwrite ? j : 0) * nm + (mvalid ? m : 0);
-    const float cinv1 = RES && cwrite ? cinvd[(cncls > 1 ? (size_t)cnr * nm : 0) + ccol] : 0.f;
+    const unsigned ccol = (unsigned)(cwrite ? j : 0) * nm + (mvalid ? m : 0);
+    const float cinv1 = RES && cwrite ? cinvd[(cncls > 1 ? (unsigned)cnr * nm : 0) + ccol] : 0.f;
     float2 *const gout = F.out;
 
     const float2 zero = make_float2(0.f, 0.f);
@@ -213,7 +225,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
 #pragma unroll
             for (int s = 0; s < NH; ++s) {
                 const int r = k - 1 - s;
-                if (r < ks || r >= ke) continue;           // uniform
+                if ((unsigned)(r - ks) >= (unsigned)(ke - ks)) continue;   // uniform: r outside [ks, ke)
                 const int sl = IX(1 + s);   // row r
                 const int sn = IX(s);       // row r + 1
                 const int ss = IX(2 + s);   // row r - 1
@@ -234,32 +246,32 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                     const float2 vs = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
                     float hz = hz0, hw = hw0, he = he0;
                     if (edge) {
-                        const size_t tb = (size_t)row_class(r, nz, ncls) * rs + c0;
-                        hz = L.hz[tb];
-                        hw = L.hw[tb];
-                        he = L.he[tb];
+                        const unsigned tb = (unsigned)row_class(r, nz, ncls) * rs + c0;
+                        hz = v0 ? L.hz[tb] : 0.f;
+                        hw = v0 ? L.hw[tb] : 0.f;
+                        he = v0 ? L.he[tb] : 0.f;
                     }
                     const float2 uw = pr[t - G];   // west: column 1 of the pair on the left
                     const float2 b = bh[0];
                     float2 acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
                     acc = make_float2(fmaf(hw, uw.x, acc.x), fmaf(hw, uw.y, acc.y));
                     acc = make_float2(fmaf(he, u1[sl].x, acc.x), fmaf(he, u1[sl].y, acc.y));
-                    if (v0) u0[sl] = acc;
+                    u0[sl] = acc;
                 } else {
                     const float2 vs = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
                     float hz = hz1, hw = hw1, he = he1;
                     if (edge) {
-                        const size_t tb = (size_t)row_class(r, nz, ncls) * rs + c1;
-                        hz = L.hz[tb];
-                        hw = L.hw[tb];
-                        he = L.he[tb];
+                        const unsigned tb = (unsigned)row_class(r, nz, ncls) * rs + c1;
+                        hz = v1 ? L.hz[tb] : 0.f;
+                        hw = v1 ? L.hw[tb] : 0.f;
+                        he = v1 ? L.he[tb] : 0.f;
                     }
                     const float2 ue = pr[t + G];   // east: column 0 of the pair on the right
                     const float2 b = bh[NT];
                     float2 acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
                     acc = make_float2(fmaf(hw, u0[sl].x, acc.x), fmaf(hw, u0[sl].y, acc.y));
                     acc = make_float2(fmaf(he, ue.x, acc.x), fmaf(he, ue.y, acc.y));
-                    if (v1) u1[sl] = acc;
+                    u1[sl] = acc;
                 }
             }
             // (c) residual of the red cell of row k - NH - 1 and the coarse
@@ -275,7 +287,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                     const bool edge = rr == 0 || rr == nz - 1;
                     float2 res;
                     if (((c - NH - 1) & 1) == 0) {   // red cell in column 0: west from the left pair
-                        const float d = edge ? L.diag[(size_t)row_class(rr, nz, ncls) * rs + c0] : dg0;
+                        const float d = edge ? L.diag[(unsigned)row_class(rr, nz, ncls) * rs + c0] : dg0;
                         const float2 s = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
                         const float2 uw = pr[t - G];
                         float2 a = make_float2(fmaf(cz0, s.x, bred.x), fmaf(cz0, s.y, bred.y));
@@ -284,7 +296,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                         res = make_float2(fmaf(-d, u0[sl].x, a.x), fmaf(-d, u0[sl].y, a.y));
                         rsum = res;
                     } else {                          // red cell in column 1: east from the right pair
-                        const float d = edge ? L.diag[(size_t)row_class(rr, nz, ncls) * rs + c1] : dg1;
+                        const float d = edge ? L.diag[(unsigned)row_class(rr, nz, ncls) * rs + c1] : dg1;
                         const float2 s = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
                         const float2 ue = pr[t + G];
                         float2 a = make_float2(fmaf(cz1, s.x, bred.x), fmaf(cz1, s.y, bred.y));
@@ -294,11 +306,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
                         const float2 sum = make_float2(rsum.x + res.x, rsum.y + res.y);
                         if (cwrite) {
                             const int K = rr >> 1;
-                            const size_t e = (size_t)K * cnr * nm + ccol;
+                            const unsigned e = (unsigned)K * cnr * nm + ccol;
                             cb[e] = sum;
                             if (finit > 0) {
                                 const float inv = (K == 0 || K == cnz - 1)
-                                                      ? cinvd[(size_t)row_class(K, cnz, cncls) * cnr * nm + ccol]
+                                                      ? cinvd[(unsigned)row_class(K, cnz, cncls) * cnr * nm + ccol]
                                                       : cinv1;
                                 const float2 bhc = make_float2(sum.x * inv, sum.y * inv);
                                 cbh[e] = bhc;
@@ -321,7 +333,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTa
             // (e) the output row k - NH is final
             const int ro = k - NH;
             if (outpair && ro >= k0 && ro < k1) {
-                const size_t o = (size_t)ro * rs;
+                const unsigned o = (unsigned)ro * rs;
                 if (v0) gout[o + c0] = u0[IX(NH)];
                 if (v1) gout[o + c1] = u1[IX(NH)];
             }
