@@ -208,7 +208,11 @@ int pic_poisson_set_stream(pic_poisson_plan_t plan, void *stream);
  * reads its flag after every test (one small copy and stream synchronisation
  * per cycle), with it the whole solve is one graph launch.  For a plan with
  * several problems use pic_poisson_solve_batch (this call returns EINVAL).
- * rho_dev and phi_dev may not alias.  `info` may be NULL.
+ * rho_dev and phi_dev may not alias.  `info` may be NULL.  The norms are
+ * binary64 sums of squares: right-hand sides whose entries lie outside about
+ * 1e-150 .. 1e150 (underflowing or overflowing squares) are not supported.
+ * The mixed form computes the forward transform in double-float arithmetic
+ * (b to about 1e-14 relative; its result stays within 1e-10 of the FP64 one).
  */
 int pic_poisson_solve(pic_poisson_plan_t plan, const double *rho_dev, double *phi_dev, double tol,
                       pic_poisson_info *info);

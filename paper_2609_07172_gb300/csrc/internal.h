@@ -115,6 +115,7 @@ struct FFTProb {
     int nr, nt, nz, nm, ncls, log2M;
     const double *tw;             // [max(M/2,1)] e^{-2 pi i t / M}, M = nt / 2, as (scale, ratio) pairs
     const double *tw2;            // [M+1] e^{-2 pi i m / nt}, same form (see tw_rot)
+    const float4 *twf, *tw2f;     // the same tables in double-float, (a_hi, a_lo, b_hi, b_lo)
     double half_inv_n;            // 1 / (2 nt)
     const double *s;              // [nr] s_i (Eq. mode_rhs); null: plain 1/N transform
     const double *bD;             // [nz][nr] Dirichlet right-hand side; may be null
@@ -164,6 +165,8 @@ struct Ctrl {
 // table's total block count (start[n]); tables live in device memory.
 cudaError_t launch_forward(const FFTTab *tab, unsigned grid, size_t smem, double *partials, cudaStream_t st);
 cudaError_t launch_inverse(const FFTTab *tab, unsigned grid, size_t smem, cudaStream_t st);
+// The forward transform in double-float arithmetic (fft_df.cu), for the mixed form.
+cudaError_t launch_forward_df(const FFTTab *tab, unsigned grid, size_t smem, double *partials, cudaStream_t st);
 // b = guess for every problem of the table (mode-layout initial iterates).
 cudaError_t launch_copy_guess(const FFTTab *tab, unsigned grid, cudaStream_t st);
 

@@ -374,6 +374,8 @@ void carve(pic_poisson_plan_s &P, Carver &c) {
         const int M = nt / 2;
         q.tw = (const double *)c.take<double2>(std::max(M / 2, 1));
         q.tw2 = (const double *)c.take<double2>(M + 1);
+        q.twf = c.take<float4>(std::max(M / 2, 1));
+        q.tw2f = c.take<float4>(M + 1);
         q.s0 = c.take<double>(q.lv[0].nr);
         q.bD0 = c.take<double>((size_t)q.lv[0].nr * q.lv[0].nz);
         const LevelHost &h0 = q.lv[0];
@@ -632,6 +634,17 @@ int upload(pic_poisson_plan_s &P) {
         for (int m = 0; m <= M; ++m) scale_ratio(&tw2[2 * m], m, nt);
         to_dev(tw, q.tw, st, err);
         to_dev(tw2, q.tw2, st, err);
+        // double-float copies: each binary64 entry as hi = its binary32 rounding, lo = the rest rounded
+        auto split = [](const std::vector<double> &v) {   // binary32 values, held exactly in binary64
+            std::vector<double> f(2 * v.size());
+            for (size_t e = 0; e < v.size(); ++e) {
+                f[2 * e] = (double)(float)v[e];
+                f[2 * e + 1] = (double)(float)(v[e] - f[2 * e]);
+            }
+            return f;
+        };
+        to_dev(split(tw), (float *)q.twf, st, err);
+        to_dev(split(tw2), (float *)q.tw2f, st, err);
         // level-0 right-hand-side factors: s_i (Eq. mode_rhs) and b^D (Eq. boundary_rhs_appendix)
         const LevelHost &h = q.lv[0];
         std::vector<double> s(h.nr), bD((size_t)h.nr * h.nz, 0.0);
@@ -673,6 +686,8 @@ int upload(pic_poisson_plan_s &P) {
         fp.log2M = lg;
         fp.tw = q.tw;
         fp.tw2 = q.tw2;
+        fp.twf = q.twf;
+        fp.tw2f = q.tw2f;
         fp.half_inv_n = 0.5 / q.d.ntheta;
         FFTProb f = fp, g = fp, iv = fp;
         f.s = q.s0;

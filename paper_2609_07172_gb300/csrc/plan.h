@@ -17,6 +17,7 @@ struct ProblemPlan {
     CoarseDev<double> cd{};
     CoarseDev<float> cf{};
     const double *tw = nullptr, *tw2 = nullptr; // FFT twiddles
+    const float4 *twf = nullptr, *tw2f = nullptr; // the same in double-float (mixed form)
     bool bottom = false;                        // levels L-2 and L-1 solved by k_bottom
     int smoothed() const { return L - 1 - (bottom ? 1 : 0); }   // levels 0 .. smoothed()-1 use the level kernels
     double *s0 = nullptr, *bD0 = nullptr;       // level-0 right-hand-side factors

@@ -291,11 +291,13 @@ int enqueue_prologue(Runner &R, int guess) {
     const bool mixed = P.shared.precision == PIC_POISSON_MIXED;
     double x3 = 0;
     const double ff = fft_flops_all(P, &x3), n0 = level0_entries(P, 0);
-    RUN(R, PIC_POISSON_PHASE_FORWARD, launch_forward(P.fwd, P.g_fft, P.smem_fft, P.partials_fwd, R.st));
+    // the mixed form's forward transform in double-float arithmetic (fft_df.cu)
+    auto forward = mixed ? launch_forward_df : launch_forward;
+    RUN(R, PIC_POISSON_PHASE_FORWARD, forward(P.fwd, P.g_fft, P.smem_fft, P.partials_fwd, R.st));
     R.account(PIC_POISSON_PHASE_FORWARD, x3 + (mixed ? 1.0 : 2.0) * n0 * sizeof(double2), ff);
     RUN(R, PIC_POISSON_PHASE_NORM, launch_bnorm(P.ctrl, P.fwd, P.partials_fwd, R.st));
     if (guess == 1) {
-        RUN(R, PIC_POISSON_PHASE_FORWARD, launch_forward(P.guess, P.g_fft, P.smem_fft, nullptr, R.st));
+        RUN(R, PIC_POISSON_PHASE_FORWARD, forward(P.guess, P.g_fft, P.smem_fft, nullptr, R.st));
         R.account(PIC_POISSON_PHASE_FORWARD, x3 + n0 * sizeof(double2), ff);
     } else if (guess == 2) {
         RUN(R, PIC_POISSON_PHASE_FORWARD, launch_copy_guess(P.guess, P.g_fft, R.st));
@@ -353,6 +355,8 @@ int enqueue_epilogue(Runner &R) {
     pic_poisson_plan_s &P = R.P;
     double x3 = 0;
     const double ff = fft_flops_all(P, &x3), n0 = level0_entries(P, 0);
+    // binary64 in both forms: an error in phi reaches the residual amplified by
+    // the operator (up to ~N^2 for its high frequencies), an error in b does not
     RUN(R, PIC_POISSON_PHASE_INVERSE, launch_inverse(P.inv, P.g_fft, P.smem_fft, R.st));
     R.account(PIC_POISSON_PHASE_INVERSE, x3 + n0 * sizeof(double2), ff);
     return PIC_POISSON_OK;
