@@ -252,20 +252,27 @@ __global__ void __launch_bounds__(FFT_THREADS) k_forward_df(const FFTTab *__rest
     const int i = i0 + lane;
     const bool valid = i < nr;
 
-    // the CTA's scale: its largest input gets exponent 0
+    // rho read once, as binary64 pairs into the transform buffer (a float4
+    // slot holds a double2); the CTA's scale makes its largest input's
+    // exponent 0; then each thread splits its own entries in place
     const double *src = P.rho + (size_t)k * nt * nr + i;
+    double2 *raw = reinterpret_cast<double2 *>(buf);
     int em = 0;
-    for (int n = warp; n < M; n += nw)
-        if (valid) em = max(em, max(exp_field(src[(size_t)(2 * n) * nr]), exp_field(src[(size_t)(2 * n + 1) * nr])));
+    for (int n = warp; n < M; n += nw) {
+        double a = 0.0, b = 0.0;
+        if (valid) {
+            a = src[(size_t)(2 * n) * nr];
+            b = src[(size_t)(2 * n + 1) * nr];
+        }
+        em = max(em, max(exp_field(a), exp_field(b)));
+        raw[bitrev(n, P.log2M) * LD + lane] = make_double2(a, b);
+    }
     const int emax = max(block_max(em, emx), 1);
     const int sc = emax - 1023;   // values carry the factor 2^-sc
     for (int n = warp; n < M; n += nw) {
-        dfc z = {{0.f, 0.f}, {0.f, 0.f}};
-        if (valid) {
-            z.x = split_scaled(src[(size_t)(2 * n) * nr], emax);
-            z.y = split_scaled(src[(size_t)(2 * n + 1) * nr], emax);
-        }
-        buf[bitrev(n, P.log2M) * LD + lane] = pack(z);
+        const int e = bitrev(n, P.log2M) * LD + lane;
+        const double2 v = raw[e];
+        buf[e] = pack({split_scaled(v.x, emax), split_scaled(v.y, emax)});
     }
     __syncthreads();
     fft_stages(buf, P.twf, M, P.log2M, lane, warp, nw);
