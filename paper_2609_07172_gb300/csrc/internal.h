@@ -160,6 +160,18 @@ struct Ctrl {
     unsigned rend[kMaxBatch];
 };
 
+// First stage of the residual-norm reduction: each block sums PSUM_CHUNK
+// consecutive block partials of one problem, so the convergence test (one
+// block) adds a few dozen numbers instead of tens of thousands -- on one SM
+// the FP64 additions alone took longer than the rest of the test.
+constexpr int PSUM_CHUNK = 2048;
+struct PsumTab {
+    int n;
+    unsigned start[kMaxBatch + 1];    // blocks (chunks) of problem p: [start[p], start[p+1])
+    unsigned in_begin[kMaxBatch];     // its first-level partials
+    unsigned in_end[kMaxBatch];
+};
+
 // ------------------------------------------------------------------ launchers
 // All launchers enqueue on `st` and return cudaGetLastError().  `grid` is the
 // table's total block count (start[n]); tables live in device memory.
@@ -207,6 +219,8 @@ cudaError_t launch_update(const DefectTab *tab, unsigned grid, const Ctrl *ctrl,
 cudaError_t launch_bnorm(Ctrl *ctrl, const FFTTab *fft, const double *partials, cudaStream_t st);
 // Convergence test: per-problem residual norms from partials, stop rule,
 // cycle count (+inc when counting), graph conditional (when use_handle).
+// out[start[p] + c] = sum of chunk c of problem p's partials (fixed order).
+cudaError_t launch_psum(const PsumTab *tab, unsigned grid, const double *partials, double *out, cudaStream_t st);
 cudaError_t launch_check(Ctrl *ctrl, const double *partials, int counting, cudaGraphConditionalHandle handle,
                          int use_handle, cudaStream_t st);
 // Plain sum of n partials into *out (single problem helpers).

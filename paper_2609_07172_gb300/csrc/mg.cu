@@ -441,7 +441,7 @@ __device__ __forceinline__ int pow2_exponent(double v) { return ((__double2hiint
 // guess), so r = b and the kernel also writes x = 0 -- a memory pass, no FP64
 // stencil.
 template <bool ZERO_X>
-__global__ void __launch_bounds__(MG_THREADS)
+__global__ void __launch_bounds__(MG_THREADS, 6)   // 48 warps per SM for the FP64 pipe (measured best)
 k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, double *__restrict__ partials) {
     __shared__ double red[MG_THREADS];
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
@@ -615,6 +615,22 @@ __device__ void range_sums(const double *__restrict__ partials, const unsigned *
         }
         __syncthreads();
     }
+}
+
+// First-stage sums of the residual-norm partials (PsumTab): block c of
+// problem p adds partials in_begin[p] + c PSUM_CHUNK .. (+ PSUM_CHUNK, at most
+// in_end[p]), each thread a strided subset in order, then the block tree.
+__global__ void __launch_bounds__(256) k_psum(const PsumTab *__restrict__ tab, const double *__restrict__ partials,
+                                              double *__restrict__ out) {
+    __shared__ double red[256];
+    const int p = find_problem(tab->start, tab->n, blockIdx.x);
+    const unsigned c = blockIdx.x - tab->start[p];
+    const unsigned b0 = tab->in_begin[p] + c * (unsigned)PSUM_CHUNK;
+    const unsigned b1 = min(tab->in_end[p], b0 + (unsigned)PSUM_CHUNK);
+    double s = 0.0;
+    for (unsigned b = b0 + threadIdx.x; b < b1; b += blockDim.x) s += partials[b];
+    const double tot = block_sum(s, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = tot;
 }
 
 // ||b||^2 per problem from the forward transform's block partials, and the
@@ -793,6 +809,11 @@ cudaError_t launch_update(const DefectTab *tab, unsigned grid, const Ctrl *ctrl,
 
 cudaError_t launch_bnorm(Ctrl *ctrl, const FFTTab *fft, const double *partials, cudaStream_t st) {
     k_bnorm<<<1, 1024, 0, st>>>(ctrl, fft, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psum(const PsumTab *tab, unsigned grid, const double *partials, double *out, cudaStream_t st) {
+    k_psum<<<grid, 256, 0, st>>>(tab, partials, out);
     return cudaGetLastError();
 }
 

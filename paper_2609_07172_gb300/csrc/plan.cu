@@ -400,6 +400,9 @@ void carve(pic_poisson_plan_s &P, Carver &c) {
     P.npartials_fwd = g_fft + 64;
     P.partials = c.take<double>(P.npartials);
     P.partials_fwd = c.take<double>(P.npartials_fwd);
+    // at most one chunk per PSUM_CHUNK partials plus one per problem
+    P.partials2 = c.take<double>(P.npartials / PSUM_CHUNK + (size_t)P.n + 64);
+    P.psum = c.take<PsumTab>(1);
     P.dsum = c.take<double>(8);
 }
 
@@ -781,6 +784,21 @@ int upload(pic_poisson_plan_s &P) {
             ++is;
         }
     }
+    // two-stage norm reduction: k_psum sums chunks of each problem's partials,
+    // the convergence test reads the chunk sums
+    PsumTab ps{};
+    ps.n = P.n;
+    for (int p = 0; p < P.n; ++p) {
+        const unsigned len = C.rend[p] - C.rbegin[p];
+        const unsigned chunks = std::max(1u, (len + PSUM_CHUNK - 1) / PSUM_CHUNK);
+        ps.in_begin[p] = C.rbegin[p];
+        ps.in_end[p] = C.rend[p];
+        ps.start[p + 1] = ps.start[p] + chunks;
+        C.rbegin[p] = ps.start[p];
+        C.rend[p] = ps.start[p + 1];
+    }
+    P.g_psum = ps.start[P.n];
+    blob_to_dev(ps, P.psum, st, err);
     if (err != cudaSuccess) {
         set_error("uploading plan tables failed: %s", cudaGetErrorString(err));
         return PIC_POISSON_ECUDA;

@@ -83,6 +83,9 @@ struct pic_poisson_plan_s {
     pp::Ctrl *hctrl_out = nullptr;              // pinned, results
     double *partials = nullptr, *partials_fwd = nullptr;
     size_t npartials = 0, npartials_fwd = 0;
+    double *partials2 = nullptr;                // first-stage sums of the residual partials (PsumTab)
+    pp::PsumTab *psum = nullptr;                // device, its table
+    unsigned g_psum = 0;                        // its blocks
     double *dsum = nullptr, *hsum = nullptr;    // small device / pinned scratch for stage calls
 
     // graphs of the whole solve (PIC_POISSON_GRAPH); [0]: initial iterate per

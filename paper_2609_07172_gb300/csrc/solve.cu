@@ -235,7 +235,8 @@ int fp64_residual_and_check(Runner &R, int counting) {
         const double n = level0_entries(P, 1);
         R.account(PIC_POISSON_PHASE_RESTRICT, 2.0 * n * sizeof(double2), 22.0 * n);
     }
-    RUN(R, PIC_POISSON_PHASE_NORM, launch_check(P.ctrl, P.partials, counting, P.handle, R.use_handle ? 1 : 0, R.st));
+    RUN(R, PIC_POISSON_PHASE_NORM, launch_psum(P.psum, P.g_psum, P.partials, P.partials2, R.st));
+    RUN(R, PIC_POISSON_PHASE_NORM, launch_check(P.ctrl, P.partials2, counting, P.handle, R.use_handle ? 1 : 0, R.st));
     return PIC_POISSON_OK;
 }
 
@@ -244,7 +245,8 @@ int mixed_defect_and_check(Runner &R, int counting, bool zero_x = false) {
     RUN(R, PIC_POISSON_PHASE_DEFECT, launch_defect(P.defect, P.g_defect, P.ctrl, P.partials, zero_x, R.st));
     const double n = level0_entries(P, 0);
     R.account(PIC_POISSON_PHASE_DEFECT, n * (2.0 * sizeof(double2) + 3.0 * sizeof(float2)), (zero_x ? 6.0 : 26.0) * n);
-    RUN(R, PIC_POISSON_PHASE_NORM, launch_check(P.ctrl, P.partials, counting, P.handle, R.use_handle ? 1 : 0, R.st));
+    RUN(R, PIC_POISSON_PHASE_NORM, launch_psum(P.psum, P.g_psum, P.partials, P.partials2, R.st));
+    RUN(R, PIC_POISSON_PHASE_NORM, launch_check(P.ctrl, P.partials2, counting, P.handle, R.use_handle ? 1 : 0, R.st));
     return PIC_POISSON_OK;
 }
 
