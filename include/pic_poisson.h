@@ -288,6 +288,24 @@ int pic_poisson_solve_host(pic_poisson_plan_t plan, const double *rho_host, doub
                            pic_poisson_info *info);
 
 /*
+ * Face-field reconstruction, the step after the solve in the PIC cycle
+ * (Sec. 2: fields live on cell faces): E = -grad phi on every cell face from
+ * the cell-centred potential phi_dev (nz, ntheta, nr), with the plan's wall
+ * potentials on the Dirichlet faces.  Writes (caller device memory, FP64):
+ *   er_dev (nz, ntheta, nr + 1): radial faces, face i between cells i - 1 and
+ *          i (face 0 the inner wall, face nr the outer wall);
+ *   ea_dev (nz, ntheta, nr): azimuthal faces j + 1/2 (periodic);
+ *   ez_dev (nz + 1, ntheta, nr): axial faces, face k between cells k - 1 and k.
+ * Distances as in the operator's face conductances (appendix Eqs.
+ * interior_face_conductances, dirichlet_face_conductances): centre to centre,
+ * centre to wall at a Dirichlet face, r_i dalpha azimuthally; so for the
+ * discrete solution the face fluxes of every cell sum to rho V / eps0.
+ * Single-problem plans; enqueued on the plan's stream (asynchronous).
+ */
+int pic_poisson_face_field(pic_poisson_plan_t plan, const double *phi_dev, double *er_dev, double *ea_dev,
+                           double *ez_dev);
+
+/*
  * Step a-1 alone: bhat_dev (mode layout) = s * rho_hat + b^D delta_m0 where
  * rho_hat is the forward DFT of rho_dev along theta with scale 1/N_theta
  * (Eqs. azimuthal_dft, mode_rhs).  Imaginary parts of m = 0 and m = N/2 are

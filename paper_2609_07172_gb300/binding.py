@@ -24,6 +24,7 @@ EXPORTS = (
     "pic_poisson_query", "pic_poisson_cell_coeffs", "pic_poisson_plan", "pic_poisson_plan_batch",
     "pic_poisson_set_stream", "pic_poisson_solve_batch",
     "pic_poisson_solve", "pic_poisson_solve_host", "pic_poisson_forward", "pic_poisson_inverse",
+    "pic_poisson_face_field",
     "pic_poisson_mode_residual", "pic_poisson_destroy", "pic_poisson_last_error",
     "pic_poisson_measure_fma_peaks", "pic_poisson_mode_residual_noalloc", "pic_poisson_autotune",
     "pic_poisson_solve_modes", "pic_poisson_analyze", "pic_poisson_get_modes",
@@ -129,6 +130,7 @@ def load(build_if_missing: bool = True):
         "pic_poisson_solve": ([vp, vp, vp, dp, vp], ip),
         "pic_poisson_solve_host": ([vp, vp, vp, dp, vp], ip),
         "pic_poisson_forward": ([vp, vp, vp], ip),
+        "pic_poisson_face_field": ([vp, vp, vp, vp, vp], ip),
         "pic_poisson_inverse": ([vp, vp, vp], ip),
         "pic_poisson_mode_residual": ([vp, vp, vp, vp, vp], ip),
         "pic_poisson_destroy": ([vp], ip),
@@ -323,6 +325,20 @@ class Plan:
             uhat = torch.empty(self.mode_shape, dtype=torch.float64, device="cuda")
         _check(load().pic_poisson_get_modes(self._plan, _dev_ptr(uhat, self.mode_shape, "uhat")))
         return uhat
+
+    def face_field(self, phi, er=None, ea=None, ez=None):
+        """E = -grad phi on the cell faces: (E_r (nz, nt, nr+1), E_alpha (nz, nt, nr),
+        E_z (nz+1, nt, nr)) as new or given CUDA float64 tensors."""
+        import torch
+        nz, nt, nr = self.shape
+        dev = phi.device
+        er = torch.empty((nz, nt, nr + 1), dtype=torch.float64, device=dev) if er is None else er
+        ea = torch.empty((nz, nt, nr), dtype=torch.float64, device=dev) if ea is None else ea
+        ez = torch.empty((nz + 1, nt, nr), dtype=torch.float64, device=dev) if ez is None else ez
+        _check(load().pic_poisson_face_field(self._plan, _dev_ptr(phi, self.shape, "phi"),
+                                             _dev_ptr(er, (nz, nt, nr + 1), "er"), _dev_ptr(ea, self.shape, "ea"),
+                                             _dev_ptr(ez, (nz + 1, nt, nr), "ez")))
+        return er, ea, ez
 
     def forward(self, rho, bhat=None):
         import torch

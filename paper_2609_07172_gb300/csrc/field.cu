@@ -1,0 +1,96 @@
+// Face-field reconstruction, the step that follows the Poisson solve in the
+// paper's particle-in-cell cycle (Sec. 2: electric fields are stored on cell
+// faces): E = -grad phi on every face of the three-dimensional cell grid,
+// from the cell-centred potential.  Radial and axial faces use the distances
+// of the operator's face conductances (appendix Eqs.
+// interior_face_conductances, dirichlet_face_conductances): centre to centre
+// between two cells, centre to face on a Dirichlet wall, where the potential
+// is the wall value; azimuthal faces the arc r_i dalpha of the angular
+// difference (Sec. 3.1), periodic.  So the face fluxes of a cell add up to its
+// charge (discrete Gauss law): sum over faces of area E.n = rho V / eps0 for
+// the discrete solution.
+//
+// One thread per cell, r fastest (coalesced): each cell writes its lower r,
+// azimuthal (j + 1/2) and lower z face, and the cells next to the upper walls
+// also the wall face.  The differences are binary64 (one subtraction and one
+// multiplication by a precomputed inverse distance per face), so on this GPU
+// the kernel is bound by the FP64 pipe rather than by its 4 arrays of traffic.
+#include "plan.h"
+
+namespace pp {
+namespace {
+
+struct FieldArgs {
+    int nr, nt, nz;
+    double inv_dr, inv_hdr, inv_dz, inv_hdz;   // 1 / centre distance, 1 / centre-to-wall distance
+    double phi_z0, phi_z1;
+    const double *win, *wout;                  // [nz] r-wall potentials
+    const double *inv_rda;                     // [nr] 1 / (r_i dalpha)
+    const double *phi;                         // (nz, nt, nr)
+    double *er, *ea, *ez;                      // (nz, nt, nr + 1), (nz, nt, nr), (nz + 1, nt, nr)
+};
+
+__global__ void __launch_bounds__(256) k_face_field(const FieldArgs a) {
+    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned nr = (unsigned)a.nr, row_n = (unsigned)a.nz * (unsigned)a.nt;
+    if (e >= row_n * nr) return;
+    const unsigned row = e / nr;                     // k * nt + j
+    const int i = (int)(e - row * nr);
+    const int k = (int)(row / (unsigned)a.nt), j = (int)(row - (unsigned)k * a.nt);
+    const double p = a.phi[e];
+    // radial face i (between cells i - 1 and i; the inner wall for i = 0)
+    const size_t fr = (size_t)row * (nr + 1) + i;
+    const double pw = i > 0 ? a.phi[e - 1] : a.win[k];
+    a.er[fr] = (pw - p) * (i > 0 ? a.inv_dr : a.inv_hdr);
+    if (i == a.nr - 1) a.er[fr + 1] = (p - a.wout[k]) * a.inv_hdr;
+    // azimuthal face j + 1/2, periodic
+    const int jn = j + 1 == a.nt ? 0 : j + 1;
+    a.ea[e] = (p - a.phi[((size_t)k * a.nt + jn) * nr + i]) * a.inv_rda[i];
+    // axial face k (between cells k - 1 and k; the wall z0 for k = 0)
+    const size_t plane = (size_t)a.nt * nr;
+    const double ps = k > 0 ? a.phi[e - plane] : a.phi_z0;
+    a.ez[e] = (ps - p) * (k > 0 ? a.inv_dz : a.inv_hdz);
+    if (k == a.nz - 1) a.ez[e + plane] = (p - a.phi_z1) * a.inv_hdz;
+}
+
+}  // namespace
+}  // namespace pp
+
+using namespace pp;
+
+extern "C" int pic_poisson_face_field(pic_poisson_plan_t plan, const double *phi_dev, double *er_dev, double *ea_dev,
+                                      double *ez_dev) {
+    int rc = plan_enter(plan);
+    if (rc) return rc;
+    if (plan->n != 1) {
+        set_error("pic_poisson_face_field needs a single-problem plan (this plan holds %d problems)", plan->n);
+        return PIC_POISSON_EINVAL;
+    }
+    if (!phi_dev || !er_dev || !ea_dev || !ez_dev) {
+        set_error("NULL pointer");
+        return PIC_POISSON_EINVAL;
+    }
+    const ProblemPlan &q = plan->pr[0];
+    const LevelHost &h = q.lv[0];
+    FieldArgs a{};
+    a.nr = h.nr;
+    a.nt = q.d.ntheta;
+    a.nz = h.nz;
+    a.inv_dr = 1.0 / h.dr;
+    a.inv_hdr = 1.0 / (0.5 * h.dr);
+    a.inv_dz = 1.0 / h.dz;
+    a.inv_hdz = 1.0 / (0.5 * h.dz);
+    a.phi_z0 = q.d.phi_z0;
+    a.phi_z1 = q.d.phi_z1;
+    a.win = q.fwin;
+    a.wout = q.fwout;
+    a.inv_rda = q.finv_rda;
+    a.phi = phi_dev;
+    a.er = er_dev;
+    a.ea = ea_dev;
+    a.ez = ez_dev;
+    const size_t n = (size_t)a.nz * a.nt * a.nr;
+    k_face_field<<<(unsigned)((n + 255) / 256), 256, 0, plan->stream>>>(a);
+    PP_CUDA(cudaGetLastError());
+    return PIC_POISSON_OK;
+}

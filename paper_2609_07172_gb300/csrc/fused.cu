@@ -75,10 +75,13 @@ constexpr int PAD = 16;           // >= the largest mode group: neighbour reads 
 // step.  The iterate's ring has UR slots (UR divides W) and is fetched
 // DEPTH = UR - 1 rows ahead; b_hat (and b) stay in a ring of BR slots until
 // their last half-sweep (the restriction: NH + 1 steps after the row entered).
+// Without the restriction the kernel needs 80 registers and, with a shorter
+// ring, under 75 KB of shared memory: three blocks per SM (24 warps) instead
+// of two -- more warps to hide the copies, which now run 2 rows ahead.
 template <int NH, bool RES> struct FusedCfg {
     static constexpr int W0 = NH + 2 + (RES ? 1 : 0);
     static constexpr int W = W0 + (W0 & 1);
-    static constexpr int UR = (W % 6 == 0) ? 6 : 4;
+    static constexpr int UR = RES ? ((W % 6 == 0) ? 6 : 4) : (W % 3 == 0 ? 3 : 4);
     static constexpr int DEPTH = UR - 1;
     static constexpr int BR = DEPTH + NH + 2;
     static constexpr int NB = RES ? 3 : 2;                  // b_hat col 0, b_hat col 1 (, b of the red cell)
@@ -97,7 +100,7 @@ template <int NH, bool RES> struct FusedCfg {
 // The residual of row r needs the final values of rows r +- 1 and of the
 // neighbouring columns, so the halo grows by one row and one column pair.
 template <int NH, bool RES>
-__global__ void __launch_bounds__(FUSED_THREADS, 2) k_smooth_fused(const FusedTab *__restrict__ tab) {
+__global__ void __launch_bounds__(FUSED_THREADS, RES ? 2 : 3) k_smooth_fused(const FusedTab *__restrict__ tab) {
     using Cfg = FusedCfg<NH, RES>;
     constexpr int W = Cfg::W, UR = Cfg::UR, DEPTH = Cfg::DEPTH, BR = Cfg::BR, NB = Cfg::NB, NP = Cfg::NP;
     constexpr int PS = Cfg::PS;

@@ -378,6 +378,9 @@ void carve(pic_poisson_plan_s &P, Carver &c) {
         q.tw2f = c.take<float4>(M + 1);
         q.s0 = c.take<double>(q.lv[0].nr);
         q.bD0 = c.take<double>((size_t)q.lv[0].nr * q.lv[0].nz);
+        q.fwin = c.take<double>(q.lv[0].nz);
+        q.fwout = c.take<double>(q.lv[0].nz);
+        q.finv_rda = c.take<double>(q.lv[0].nr);
         const LevelHost &h0 = q.lv[0];
         const size_t n0 = (size_t)h0.nr * h0.nz * q.nm;
         g_fft += (size_t)h0.nz * ((h0.nr + FFT_TI - 1) / FFT_TI);
@@ -508,7 +511,8 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
                     b.L = f;
                     b.in = q.u2[l];
                     b.out = f.u;
-                    fused_shape(f.nr, f.nz, f.nm, 2 * post, false, target, b, nb);
+                    // post-smoothing holds fewer registers: three blocks per SM on level 0
+                    fused_shape(f.nr, f.nz, f.nm, 2 * post, false, l == 0 ? target * 3 / 2 : target, b, nb);
                     fb.pid[fb.n] = p;
                     fb.p[fb.n] = b;
                     fb.start[fb.n + 1] = fb.start[fb.n] + nb;
@@ -667,6 +671,17 @@ int upload(pic_poisson_plan_s &P) {
             }
         to_dev(s, q.s0, st, err);
         to_dev(bD, q.bD0, st, err);
+        // face-field reconstruction: wall potentials and the azimuthal arcs
+        std::vector<double> win(h.nz), wout(h.nz), inv_rda(h.nr);
+        for (int k = 0; k < h.nz; ++k) {
+            win[k] = wall_rin(q.d, k);
+            wout[k] = wall_rout(q.d, k);
+        }
+        const double da = q.d.theta_span / q.d.ntheta;
+        for (int i = 0; i < h.nr; ++i) inv_rda[i] = 1.0 / ((q.d.r_in + (i + 0.5) * h.dr) * da);
+        to_dev(win, q.fwin, st, err);
+        to_dev(wout, q.fwout, st, err);
+        to_dev(inv_rda, q.finv_rda, st, err);
     }
 
     // transforms

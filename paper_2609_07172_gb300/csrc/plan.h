@@ -21,6 +21,8 @@ struct ProblemPlan {
     bool bottom = false;                        // levels L-2 and L-1 solved by k_bottom
     int smoothed() const { return L - 1 - (bottom ? 1 : 0); }   // levels 0 .. smoothed()-1 use the level kernels
     double *s0 = nullptr, *bD0 = nullptr;       // level-0 right-hand-side factors
+    double *fwin = nullptr, *fwout = nullptr;   // face-field reconstruction: r-wall potentials [nz]
+    double *finv_rda = nullptr;                 // and 1 / (r_i dalpha) [nr]
 };
 
 // Launch tables of one precision's hierarchy, per level l = 0 .. Lmax-2

@@ -16,6 +16,7 @@ import pytest
 import torch
 
 import oracle
+from oracle import fields as F
 from paper_2609_07172_gb300 import FP64, MIXED, Plan, binding as B, workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -84,3 +85,19 @@ def test_full_size_rhs_matches_dft_of_oracle_rhs(full):
             ref = (col * np.exp(-2j * np.pi * m * j / n)).sum() / n
             got = b[k, i, m, 0] + 1j * b[k, i, m, 1]
             assert abs(got - ref) <= 1e-12 * (np.abs(col).max() + 1e-300), (k, i, m, got, ref)
+
+
+def test_full_size_face_field_flux_balance_is_the_solver_residual(full, solutions):
+    """E = -grad phi of the returned potential: each cell's outward face fluxes
+    minus its charge is dalpha (A phi - b) of that cell, so the imbalance's
+    norm relative to dalpha ||b|| is the solve's relative residual."""
+    p, g, rho = full
+    phi, info = solutions["fp64"]
+    with Plan(p) as plan:
+        e = plan.face_field(torch.from_numpy(phi).cuda())
+        torch.cuda.synchronize()
+    res, _ = F.gauss_residual(g, rho, *[x.cpu().numpy() for x in e])
+    b = oracle.rhs3d(g, rho)
+    rel = np.linalg.norm(res) / (p.theta_span / p.ntheta * np.linalg.norm(b))
+    assert rel == pytest.approx(oracle.relres(g, rho, phi), rel=1e-3)
+    assert rel <= TOL * 1.05
