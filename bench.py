@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-field", action="store_true", help="skip the face-field reconstruction timing")
+    ap.add_argument("--no-deposit", action="store_true", help="skip the CIC deposit timing")
+    ap.add_argument("--deposit-ppc", type=int, default=4, help="macro-particles per cell and species (deposit timing)")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other precision form")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-problem uneven batch")
     ap.add_argument("--no-sequence", action="store_true", help="skip the drifting-wave sequence")
@@ -425,6 +427,10 @@ def run_ours(args):
                               "bound": "alu (FP64: 6 instructions per cell)",
                               "algorithmic_bytes": fbytes, "launches": len(evs)}
         del er, ea, ez
+
+    # ---- CIC deposit of two species and projection to rho (the PIC step before the solve)
+    if not args.no_deposit and args.deposit_ppc > 0:
+        line["deposit"] = run_deposit(args, plan, p)
     plan.close()
 
     # ---- the other form on the same GPU and inputs (mixed FP32/FP64 when the headline is FP64)
@@ -477,6 +483,59 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_deposit(args, plan, p):
+    """Ions and electrons, args.deposit_ppc per cell each, uniformly inside
+    their cells and in cell-major order (as a periodically sorted particle
+    array), deposited to the nodes and projected to rho; CUDA events."""
+    import torch
+    ppc = args.deposit_ppc
+    cells = p.nr * p.ntheta * p.nz
+    dr, dz, da = (p.r_out - p.r_in) / p.nr, (p.z1 - p.z0) / p.nz, p.theta_span / p.ntheta
+    gen = torch.Generator(device="cuda").manual_seed(11)
+
+    def species():
+        c = torch.arange(cells * ppc, device="cuda", dtype=torch.int64) // ppc
+        i, rest = c % p.nr, c // p.nr
+        j, k = rest % p.ntheta, rest // p.ntheta
+        u = torch.rand((3, c.numel()), device="cuda", dtype=torch.float64, generator=gen)
+        return (p.r_in + (i + u[0]) * dr, (j + u[1]) * da, p.z0 + (k + u[2]) * dz)
+
+    ions, elec = species(), species()
+    w, e = 1e8, 1.602176634e-19
+    ni = torch.zeros(plan.node_shape(), dtype=torch.float64, device="cuda")
+    ne = torch.zeros_like(ni)
+    rho = torch.empty(p.shape, dtype=torch.float64, device="cuda")
+
+    def step():
+        ni.zero_()
+        ne.zero_()
+        plan.deposit(*ions, w, ni)
+        plan.deposit(*elec, w, ne)
+        plan.project(ni, e, rho)
+        plan.project(ne, -e, rho, accumulate=True)
+
+    for _ in range(2):
+        step()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        a.record(plan.stream)
+        step()
+        b.record(plan.stream)
+    torch.cuda.synchronize()
+    ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+    n = 2 * cells * ppc
+    # charge check: the projected charge of the equal ion and electron counts is zero up to rounding
+    rc = p.r_in + (torch.arange(p.nr, device="cuda", dtype=torch.float64) + 0.5) * dr
+    qsum = float((rho * (rc * dr * da * dz)).sum())
+    out = {"ms": ms, "particles": n, "particles_per_s": n / (ms * 1e-3), "per_cell_per_species": ppc,
+           "order": "cell-major (sorted)", "kernels": "k_deposit x2 (warp-aggregated FP64 atomics), k_project x2",
+           "net_charge_over_ion_charge": qsum / (e * w * cells * ppc)}
+    del ions, elec, ni, ne, rho
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(args, dev):

@@ -288,6 +288,42 @@ int pic_poisson_solve_host(pic_poisson_plan_t plan, const double *rho_host, doub
                            pic_poisson_info *info);
 
 /*
+ * Cloud-in-cell deposit of one species' macro-particles (the step before the
+ * solve in the PIC cycle; Sec. "Warp-aggregated cylindrical CIC deposition",
+ * Eqs. cic_weights, particle_cic_update, warp_aggregated_cic).  Particle p at
+ * (r_dev[p], alpha_dev[p], z_dev[p]) (device FP64 arrays of np entries, alpha
+ * in [0, theta_span)) in cell (i, j, k) at normalised position (xi, eta,
+ * zeta) adds weight * w_r w_alpha w_z / V_nu to each of the cell's eight
+ * corner nodes, w^(0) = 1 - t, w^(1) = t; V_nu is the node's cylindrical
+ * control volume (cell centre to cell centre in r and z, cut at the walls;
+ * dalpha in alpha).  The sums are ADDED to nodes_dev, the nodal number
+ * density (nz + 1, ntheta, nr + 1) FP64 (node (c, j, a) at z-face c, alpha
+ * j dalpha, r-face a), which the caller zeroes before a step's first species.
+ * Lanes of a warp holding particles of one cell add their contributions in
+ * registers and one lane per run of equal cells issues the eight FP64
+ * atomics, so cell-sorted particles are cheapest; any order is correct (the
+ * order of the additions, hence rounding, varies from run to run).
+ * Particles outside the domain deposit nothing.  Single-problem plans; on
+ * the plan's stream (asynchronous).
+ */
+int pic_poisson_deposit(pic_poisson_plan_t plan, const double *r_dev, const double *alpha_dev, const double *z_dev,
+                        long long np, double weight, double *nodes_dev);
+
+/*
+ * Projection of nodal number density to cell-centred charge density
+ * (Sec. 2; reading of the paper's "volume-consistent projection"): each
+ * node's control volume is split into the octants in its adjacent cells and
+ * an octant's charge goes to its cell,
+ *   rho_q = charge * sum over the corners nu of q of n_nu V_(nu in q) / V_q,
+ * which conserves charge exactly.  rho_dev (nz, ntheta, nr) FP64 is
+ * overwritten (accumulate = 0) or added to (accumulate != 0; e.g. ions, then
+ * electrons with the opposite charge).  Single-problem plans; on the plan's
+ * stream (asynchronous).
+ */
+int pic_poisson_project(pic_poisson_plan_t plan, const double *nodes_dev, double charge, int accumulate,
+                        double *rho_dev);
+
+/*
  * Face-field reconstruction, the step after the solve in the PIC cycle
  * (Sec. 2: fields live on cell faces): E = -grad phi on every cell face from
  * the cell-centred potential phi_dev (nz, ntheta, nr), with the plan's wall

@@ -24,7 +24,7 @@ EXPORTS = (
     "pic_poisson_query", "pic_poisson_cell_coeffs", "pic_poisson_plan", "pic_poisson_plan_batch",
     "pic_poisson_set_stream", "pic_poisson_solve_batch",
     "pic_poisson_solve", "pic_poisson_solve_host", "pic_poisson_forward", "pic_poisson_inverse",
-    "pic_poisson_face_field",
+    "pic_poisson_face_field", "pic_poisson_deposit", "pic_poisson_project",
     "pic_poisson_mode_residual", "pic_poisson_destroy", "pic_poisson_last_error",
     "pic_poisson_measure_fma_peaks", "pic_poisson_mode_residual_noalloc", "pic_poisson_autotune",
     "pic_poisson_solve_modes", "pic_poisson_analyze", "pic_poisson_get_modes",
@@ -131,6 +131,8 @@ def load(build_if_missing: bool = True):
         "pic_poisson_solve_host": ([vp, vp, vp, dp, vp], ip),
         "pic_poisson_forward": ([vp, vp, vp], ip),
         "pic_poisson_face_field": ([vp, vp, vp, vp, vp], ip),
+        "pic_poisson_deposit": ([vp, vp, vp, vp, ctypes.c_longlong, ctypes.c_double, vp], ip),
+        "pic_poisson_project": ([vp, vp, ctypes.c_double, ctypes.c_int, vp], ip),
         "pic_poisson_inverse": ([vp, vp, vp], ip),
         "pic_poisson_mode_residual": ([vp, vp, vp, vp, vp], ip),
         "pic_poisson_destroy": ([vp], ip),
@@ -339,6 +341,34 @@ class Plan:
                                              _dev_ptr(er, (nz, nt, nr + 1), "er"), _dev_ptr(ea, self.shape, "ea"),
                                              _dev_ptr(ez, (nz + 1, nt, nr), "ez")))
         return er, ea, ez
+
+    def node_shape(self):
+        nz, nt, nr = self.shape
+        return (nz + 1, nt, nr + 1)
+
+    def deposit(self, r, alpha, z, weight, nodes=None):
+        """Add the CIC nodal number density of particles (CUDA float64 1-D
+        tensors r, alpha, z) to `nodes` (created zeroed if None); returns it."""
+        import torch
+        n = r.numel()
+        for t, name in ((r, "r"), (alpha, "alpha"), (z, "z")):
+            if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
+                raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of {n} entries")
+        if nodes is None:
+            nodes = torch.zeros(self.node_shape(), dtype=torch.float64, device=r.device)
+        _check(load().pic_poisson_deposit(self._plan, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(alpha.data_ptr()),
+                                          ctypes.c_void_p(z.data_ptr()), int(n), float(weight),
+                                          _dev_ptr(nodes, self.node_shape(), "nodes")))
+        return nodes
+
+    def project(self, nodes, charge, rho=None, accumulate=False):
+        """rho (=, or += if accumulate) charge * volume-consistent projection of `nodes`."""
+        import torch
+        if rho is None:
+            rho = torch.zeros(self.shape, dtype=torch.float64, device=nodes.device)
+        _check(load().pic_poisson_project(self._plan, _dev_ptr(nodes, self.node_shape(), "nodes"), float(charge),
+                                          1 if accumulate else 0, _dev_ptr(rho, self.shape, "rho")))
+        return rho
 
     def forward(self, rho, bhat=None):
         import torch

@@ -1,0 +1,196 @@
+// Cloud-in-cell deposit of macro-particles to the cell-corner nodes and the
+// projection of nodal density to cell-centred charge: the steps before the
+// Poisson solve in the paper's particle-in-cell cycle (Sec. 2, and Sec.
+// "Warp-aggregated cylindrical CIC deposition", Eqs. cic_weights,
+// particle_cic_update, warp_aggregated_cic).
+//
+// Deposit.  A particle in cell (i, j, k) at normalised position (xi, eta,
+// zeta) adds W w_r w_alpha w_z / V_nu to each of the cell's eight corner
+// nodes (w^(0) = 1 - t, w^(1) = t; V_nu the node's cylindrical control
+// volume, from cell centre to cell centre in r and z and cut at the walls, a
+// full dalpha in alpha).  Warp aggregation (Eq. warp_aggregated_cic): lanes
+// holding particles of the same cell -- runs of equal cell labels in lane
+// order, which cell-sorted input makes long -- add their eight contributions
+// with a segmented scan of register shuffles, and the last lane of each run
+// issues the run's eight FP64 atomic additions, each divided by the node's
+// volume once.  All weights and corners stay; only the order of the
+// additions changes.  Particles outside the domain deposit nothing.
+//
+// Projection (Sec. 2, "volume-consistent projection to cell-centred
+// charge"; the paper gives no formula -- the reading): each node's control
+// volume is split into the octants inside its adjacent cells and an
+// octant's charge goes to its cell, rho_q = charge * sum over the corners of
+// q of n_nu V_(nu in q) / V_q.  The radial octant share is the exact r dr
+// integral of the half cell (f_lo, f_hi below, f_lo + f_hi = 1), the
+// azimuthal and axial ones are 1/2; so charge is conserved exactly:
+// sum_q rho_q V_q = charge * sum_nu n_nu V_nu.
+#include "plan.h"
+
+namespace pp {
+namespace {
+
+struct DepositArgs {
+    int nr, nt, nz;
+    long long np;
+    double r_in, z0, inv_dr, inv_da, inv_dz, w;
+    const double *r, *al, *z;
+    const double *inv_vr;   // [nr + 1] 1 / (radial integral of r dr of node a's interval)
+    const double *inv_vz;   // [nz + 1] 1 / (dalpha * axial length of node c's interval)
+    double *nodes;          // (nz + 1, nt, nr + 1)
+};
+
+__global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    double tr = -1.0, ta = -1.0, tz = -1.0;
+    if (p < a.np) {
+        tr = (a.r[p] - a.r_in) * a.inv_dr;
+        ta = a.al[p] * a.inv_da;
+        tz = (a.z[p] - a.z0) * a.inv_dz;
+    }
+    const double fr = floor(tr), fa = floor(ta), fz = floor(tz);
+    // in range before any conversion (NaN compares false)
+    const bool ok = fr >= 0.0 && fr < (double)a.nr && fa >= 0.0 && fa < (double)a.nt && fz >= 0.0 &&
+                    fz < (double)a.nz;
+    const int ir = ok ? (int)fr : 0, ia = ok ? (int)fa : 0, iz = ok ? (int)fz : 0;
+    const double xr = ok ? tr - fr : 0.0, xa = ok ? ta - fa : 0.0, xz = ok ? tz - fz : 0.0;
+    const double w = ok ? a.w : 0.0;
+    // contributions to the corners (dz, dalpha, dr), index 4 dz + 2 dalpha + dr
+    const double wz0 = w * (1.0 - xz), wz1 = w * xz;
+    const double q00 = wz0 * (1.0 - xa), q01 = wz0 * xa, q10 = wz1 * (1.0 - xa), q11 = wz1 * xa;
+    const double xr0 = 1.0 - xr;
+    double c[8] = {q00 * xr0, q00 * xr, q01 * xr0, q01 * xr, q10 * xr0, q10 * xr, q11 * xr0, q11 * xr};
+    // runs of lanes with the same cell (lanes without a particle: a run each)
+    const long long label = ok ? ((long long)iz * a.nt + ia) * a.nr + ir : -1 - lane;
+    const long long prev = __shfl_up_sync(full, label, 1);
+    const unsigned heads = __ballot_sync(full, lane == 0 || prev != label);
+    const unsigned upto = lane == 31 ? full : ((2u << lane) - 1u);
+    const int start = 31 - __clz(heads & upto);   // first lane of this lane's run
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const double y = __shfl_up_sync(full, c[d], off);
+            if (lane - off >= start) c[d] += y;
+        }
+    }
+    const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (ok && last) {
+        const int ja = ia + 1 == a.nt ? 0 : ia + 1;
+        const size_t rs = (size_t)a.nr + 1, ps = (size_t)a.nt * rs;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int nzi = iz + (d >> 2), nai = (d & 2) ? ja : ia, nri = ir + (d & 1);
+            atomicAdd(a.nodes + (size_t)nzi * ps + (size_t)nai * rs + nri, c[d] * a.inv_vr[nri] * a.inv_vz[nzi]);
+        }
+    }
+}
+
+struct ProjectArgs {
+    int nr, nt, nz, accumulate;
+    double charge;
+    const double *flo, *fhi;   // [nr] radial shares of a cell's lower / upper corner nodes
+    const double *nodes;
+    double *rho;
+};
+
+__global__ void __launch_bounds__(256) k_project(const ProjectArgs a) {
+    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;   // (k, j, i), i fastest
+    const unsigned nr = (unsigned)a.nr;
+    if (e >= (unsigned)a.nz * a.nt * nr) return;
+    const unsigned row = e / nr;
+    const int i = (int)(e - row * nr);
+    const int k = (int)(row / (unsigned)a.nt), j = (int)(row - (unsigned)k * a.nt);
+    const int jn = j + 1 == a.nt ? 0 : j + 1;
+    const size_t rs = nr + 1, ps = (size_t)a.nt * rs;
+    const double *n0 = a.nodes + (size_t)k * ps, *n1 = n0 + ps;
+    // the four (alpha, z) nodes at radius a = i and at a = i + 1
+    const double lo = (n0[j * rs + i] + n0[jn * rs + i]) + (n1[j * rs + i] + n1[jn * rs + i]);
+    const double hi = (n0[j * rs + i + 1] + n0[jn * rs + i + 1]) + (n1[j * rs + i + 1] + n1[jn * rs + i + 1]);
+    const double v = a.charge * 0.25 * (a.flo[i] * lo + a.fhi[i] * hi);
+    a.rho[e] = a.accumulate ? a.rho[e] + v : v;
+}
+
+}  // namespace
+}  // namespace pp
+
+using namespace pp;
+
+namespace {
+int single(const pic_poisson_plan_s *P, const char *what) {
+    if (P->n != 1) {
+        set_error("%s needs a single-problem plan (this plan holds %d problems)", what, P->n);
+        return PIC_POISSON_EINVAL;
+    }
+    return PIC_POISSON_OK;
+}
+}  // namespace
+
+extern "C" int pic_poisson_deposit(pic_poisson_plan_t plan, const double *r_dev, const double *alpha_dev,
+                                   const double *z_dev, long long np, double weight, double *nodes_dev) {
+    int rc = plan_enter(plan);
+    if (rc) return rc;
+    rc = single(plan, "pic_poisson_deposit");
+    if (rc) return rc;
+    if (np < 0 || (np > 0 && (!r_dev || !alpha_dev || !z_dev)) || !nodes_dev) {
+        set_error("pic_poisson_deposit: NULL pointer or negative count");
+        return PIC_POISSON_EINVAL;
+    }
+    if (np == 0) return PIC_POISSON_OK;
+    const ProblemPlan &q = plan->pr[0];
+    const LevelHost &h = q.lv[0];
+    DepositArgs a{};
+    a.nr = h.nr;
+    a.nt = q.d.ntheta;
+    a.nz = h.nz;
+    a.np = np;
+    a.r_in = q.d.r_in;
+    a.z0 = q.d.z0;
+    a.inv_dr = 1.0 / h.dr;
+    a.inv_da = q.d.ntheta / q.d.theta_span;
+    a.inv_dz = 1.0 / h.dz;
+    a.w = weight;
+    a.r = r_dev;
+    a.al = alpha_dev;
+    a.z = z_dev;
+    a.inv_vr = q.dep_inv_vr;
+    a.inv_vz = q.dep_inv_vz;
+    a.nodes = nodes_dev;
+    const long long blocks = (np + 255) / 256;
+    if (blocks > 0x7fffffffLL) {
+        set_error("pic_poisson_deposit: too many particles for one launch (%lld)", np);
+        return PIC_POISSON_EINVAL;
+    }
+    k_deposit<<<(unsigned)blocks, 256, 0, plan->stream>>>(a);
+    PP_CUDA(cudaGetLastError());
+    return PIC_POISSON_OK;
+}
+
+extern "C" int pic_poisson_project(pic_poisson_plan_t plan, const double *nodes_dev, double charge, int accumulate,
+                                   double *rho_dev) {
+    int rc = plan_enter(plan);
+    if (rc) return rc;
+    rc = single(plan, "pic_poisson_project");
+    if (rc) return rc;
+    if (!nodes_dev || !rho_dev) {
+        set_error("pic_poisson_project: NULL pointer");
+        return PIC_POISSON_EINVAL;
+    }
+    const ProblemPlan &q = plan->pr[0];
+    const LevelHost &h = q.lv[0];
+    ProjectArgs a{};
+    a.nr = h.nr;
+    a.nt = q.d.ntheta;
+    a.nz = h.nz;
+    a.accumulate = accumulate ? 1 : 0;
+    a.charge = charge;
+    a.flo = q.dep_flo;
+    a.fhi = q.dep_fhi;
+    a.nodes = nodes_dev;
+    a.rho = rho_dev;
+    const size_t n = (size_t)a.nz * a.nt * a.nr;
+    k_project<<<(unsigned)((n + 255) / 256), 256, 0, plan->stream>>>(a);
+    PP_CUDA(cudaGetLastError());
+    return PIC_POISSON_OK;
+}

@@ -381,6 +381,10 @@ void carve(pic_poisson_plan_s &P, Carver &c) {
         q.fwin = c.take<double>(q.lv[0].nz);
         q.fwout = c.take<double>(q.lv[0].nz);
         q.finv_rda = c.take<double>(q.lv[0].nr);
+        q.dep_inv_vr = c.take<double>(q.lv[0].nr + 1);
+        q.dep_inv_vz = c.take<double>(q.lv[0].nz + 1);
+        q.dep_flo = c.take<double>(q.lv[0].nr);
+        q.dep_fhi = c.take<double>(q.lv[0].nr);
         const LevelHost &h0 = q.lv[0];
         const size_t n0 = (size_t)h0.nr * h0.nz * q.nm;
         g_fft += (size_t)h0.nz * ((h0.nr + FFT_TI - 1) / FFT_TI);
@@ -682,6 +686,25 @@ int upload(pic_poisson_plan_s &P) {
         to_dev(win, q.fwin, st, err);
         to_dev(wout, q.fwout, st, err);
         to_dev(inv_rda, q.finv_rda, st, err);
+        // CIC deposit and projection: node control volumes (centre to centre,
+        // cut at the walls; exact r dr integral) and the cells' radial octant shares
+        std::vector<double> ivr(h.nr + 1), ivz(h.nz + 1), flo(h.nr), fhi(h.nr);
+        auto rface = [&](int a) { return q.d.r_in + a * h.dr; };
+        auto rcen = [&](int i) { return q.d.r_in + (i + 0.5) * h.dr; };
+        for (int a = 0; a <= h.nr; ++a) {
+            const double lo = a == 0 ? rface(0) : rcen(a - 1), hi = a == h.nr ? rface(h.nr) : rcen(a);
+            ivr[a] = 1.0 / ((hi - lo) * (hi + lo) / 2);   // 1 / integral of r dr, factored
+        }
+        for (int c = 0; c <= h.nz; ++c) ivz[c] = 1.0 / (da * ((c == 0 || c == h.nz) ? 0.5 * h.dz : h.dz));
+        for (int i = 0; i < h.nr; ++i) {
+            const double r0 = rface(i), r1 = rface(i + 1), rc = rcen(i), all = (r1 - r0) * (r1 + r0);
+            flo[i] = (rc - r0) * (rc + r0) / all;
+            fhi[i] = (r1 - rc) * (r1 + rc) / all;
+        }
+        to_dev(ivr, q.dep_inv_vr, st, err);
+        to_dev(ivz, q.dep_inv_vz, st, err);
+        to_dev(flo, q.dep_flo, st, err);
+        to_dev(fhi, q.dep_fhi, st, err);
     }
 
     // transforms

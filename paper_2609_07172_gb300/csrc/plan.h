@@ -23,6 +23,8 @@ struct ProblemPlan {
     double *s0 = nullptr, *bD0 = nullptr;       // level-0 right-hand-side factors
     double *fwin = nullptr, *fwout = nullptr;   // face-field reconstruction: r-wall potentials [nz]
     double *finv_rda = nullptr;                 // and 1 / (r_i dalpha) [nr]
+    double *dep_inv_vr = nullptr, *dep_inv_vz = nullptr;   // CIC deposit: 1 / node-volume factors [nr+1], [nz+1]
+    double *dep_flo = nullptr, *dep_fhi = nullptr;         // projection: radial octant shares [nr]
 };
 
 // Launch tables of one precision's hierarchy, per level l = 0 .. Lmax-2
