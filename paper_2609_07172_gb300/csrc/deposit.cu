@@ -8,13 +8,14 @@
 // zeta) adds W w_r w_alpha w_z / V_nu to each of the cell's eight corner
 // nodes (w^(0) = 1 - t, w^(1) = t; V_nu the node's cylindrical control
 // volume, from cell centre to cell centre in r and z and cut at the walls, a
-// full dalpha in alpha).  Warp aggregation (Eq. warp_aggregated_cic): lanes
-// holding particles of the same cell -- runs of equal cell labels in lane
-// order, which cell-sorted input makes long -- add their eight contributions
-// with a segmented scan of register shuffles, and the last lane of each run
-// issues the run's eight FP64 atomic additions, each divided by the node's
-// volume once.  All weights and corners stay; only the order of the
-// additions changes.  Particles outside the domain deposit nothing.
+// full dalpha in alpha).  Aggregation (Eq. warp_aggregated_cic): a thread
+// first sums, in registers, its consecutive particles that share a cell;
+// then lanes whose last cells agree -- runs of equal cell labels in lane
+// order, which cell-sorted input makes long -- add their sums with a
+// segmented scan of register shuffles, and the last lane of each run issues
+// the run's eight FP64 atomic additions, each divided by the node's volume
+// once.  All weights and corners stay; only the order of the additions
+// changes.  Particles outside the domain deposit nothing.
 //
 // Projection (Sec. 2, "volume-consistent projection to cell-centred
 // charge"; the paper gives no formula -- the reading): each node's control
@@ -39,30 +40,81 @@ struct DepositArgs {
     double *nodes;          // (nz + 1, nt, nr + 1)
 };
 
-__global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const unsigned full = 0xffffffffu;
-    double tr = -1.0, ta = -1.0, tz = -1.0;
-    if (p < a.np) {
-        tr = (a.r[p] - a.r_in) * a.inv_dr;
-        ta = a.al[p] * a.inv_da;
-        tz = (a.z[p] - a.z0) * a.inv_dz;
-    }
+constexpr int DEP_PPT = 4;   // consecutive particles per thread
+
+// Cell and the eight corner contributions W w_r w_alpha w_z of particle p
+// (corner index 4 dz + 2 dalpha + dr); false when p is absent or outside.
+__device__ __forceinline__ bool cic_weights(const DepositArgs &a, long long p, int &ir, int &ia, int &iz,
+                                            double c[8]) {
+    if (p >= a.np) return false;
+    const double tr = (a.r[p] - a.r_in) * a.inv_dr, ta = a.al[p] * a.inv_da, tz = (a.z[p] - a.z0) * a.inv_dz;
     const double fr = floor(tr), fa = floor(ta), fz = floor(tz);
     // in range before any conversion (NaN compares false)
-    const bool ok = fr >= 0.0 && fr < (double)a.nr && fa >= 0.0 && fa < (double)a.nt && fz >= 0.0 &&
-                    fz < (double)a.nz;
-    const int ir = ok ? (int)fr : 0, ia = ok ? (int)fa : 0, iz = ok ? (int)fz : 0;
-    const double xr = ok ? tr - fr : 0.0, xa = ok ? ta - fa : 0.0, xz = ok ? tz - fz : 0.0;
-    const double w = ok ? a.w : 0.0;
-    // contributions to the corners (dz, dalpha, dr), index 4 dz + 2 dalpha + dr
-    const double wz0 = w * (1.0 - xz), wz1 = w * xz;
-    const double q00 = wz0 * (1.0 - xa), q01 = wz0 * xa, q10 = wz1 * (1.0 - xa), q11 = wz1 * xa;
-    const double xr0 = 1.0 - xr;
-    double c[8] = {q00 * xr0, q00 * xr, q01 * xr0, q01 * xr, q10 * xr0, q10 * xr, q11 * xr0, q11 * xr};
-    // runs of lanes with the same cell (lanes without a particle: a run each)
-    const long long label = ok ? ((long long)iz * a.nt + ia) * a.nr + ir : -1 - lane;
+    if (!(fr >= 0.0 && fr < (double)a.nr && fa >= 0.0 && fa < (double)a.nt && fz >= 0.0 && fz < (double)a.nz))
+        return false;
+    ir = (int)fr;
+    ia = (int)fa;
+    iz = (int)fz;
+    const double xr = tr - fr, xa = ta - fa, xz = tz - fz;
+    const double wz0 = a.w * (1.0 - xz), wz1 = a.w * xz;
+    const double xa0 = 1.0 - xa, xr0 = 1.0 - xr;
+    const double q00 = wz0 * xa0, q01 = wz0 * xa, q10 = wz1 * xa0, q11 = wz1 * xa;
+    c[0] = q00 * xr0;
+    c[1] = q00 * xr;
+    c[2] = q01 * xr0;
+    c[3] = q01 * xr;
+    c[4] = q10 * xr0;
+    c[5] = q10 * xr;
+    c[6] = q11 * xr0;
+    c[7] = q11 * xr;
+    return true;
+}
+
+// The eight atomic additions of a run's sums to the corners of cell (ir, ia, iz).
+__device__ __forceinline__ void add_corners(const DepositArgs &a, int ir, int ia, int iz, const double c[8]) {
+    const int ja = ia + 1 == a.nt ? 0 : ia + 1;
+    const size_t rs = (size_t)a.nr + 1, ps = (size_t)a.nt * rs;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const int nzi = iz + (d >> 2), nai = (d & 2) ? ja : ia, nri = ir + (d & 1);
+        atomicAdd(a.nodes + (size_t)nzi * ps + (size_t)nai * rs + nri, c[d] * a.inv_vr[nri] * a.inv_vz[nzi]);
+    }
+}
+
+// Each thread takes DEP_PPT consecutive particles and sums those of one cell
+// in registers (a cell change inside the chunk sends the finished run's sums
+// straight to the nodes); then the threads' last runs are aggregated across
+// the warp.
+__global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
+    const long long t0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * DEP_PPT;
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int cr = 0, ca = 0, cz = 0;
+    bool have = false;
+#pragma unroll
+    for (int t = 0; t < DEP_PPT; ++t) {
+        double c[8];
+        int ir, ia, iz;
+        if (!cic_weights(a, t0 + t, ir, ia, iz, c)) continue;
+        if (have && (ir != cr || ia != ca || iz != cz)) {
+            add_corners(a, cr, ca, cz, acc);
+            have = false;
+        }
+        if (!have) {
+#pragma unroll
+            for (int d = 0; d < 8; ++d) acc[d] = c[d];
+            cr = ir;
+            ca = ia;
+            cz = iz;
+            have = true;
+        } else {
+#pragma unroll
+            for (int d = 0; d < 8; ++d) acc[d] += c[d];
+        }
+    }
+    // runs of lanes with the same last cell (lanes with nothing left: a run each)
+    const long long label = have ? ((long long)cz * a.nt + ca) * a.nr + cr : -1 - lane;
     const long long prev = __shfl_up_sync(full, label, 1);
     const unsigned heads = __ballot_sync(full, lane == 0 || prev != label);
     const unsigned upto = lane == 31 ? full : ((2u << lane) - 1u);
@@ -71,20 +123,12 @@ __global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
     for (int d = 0; d < 8; ++d) {
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const double y = __shfl_up_sync(full, c[d], off);
-            if (lane - off >= start) c[d] += y;
+            const double y = __shfl_up_sync(full, acc[d], off);
+            if (lane - off >= start) acc[d] += y;
         }
     }
     const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
-    if (ok && last) {
-        const int ja = ia + 1 == a.nt ? 0 : ia + 1;
-        const size_t rs = (size_t)a.nr + 1, ps = (size_t)a.nt * rs;
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            const int nzi = iz + (d >> 2), nai = (d & 2) ? ja : ia, nri = ir + (d & 1);
-            atomicAdd(a.nodes + (size_t)nzi * ps + (size_t)nai * rs + nri, c[d] * a.inv_vr[nri] * a.inv_vz[nzi]);
-        }
-    }
+    if (have && last) add_corners(a, cr, ca, cz, acc);
 }
 
 struct ProjectArgs {
@@ -157,7 +201,7 @@ extern "C" int pic_poisson_deposit(pic_poisson_plan_t plan, const double *r_dev,
     a.inv_vr = q.dep_inv_vr;
     a.inv_vz = q.dep_inv_vz;
     a.nodes = nodes_dev;
-    const long long blocks = (np + 255) / 256;
+    const long long blocks = (np + 256LL * DEP_PPT - 1) / (256LL * DEP_PPT);
     if (blocks > 0x7fffffffLL) {
         set_error("pic_poisson_deposit: too many particles for one launch (%lld)", np);
         return PIC_POISSON_EINVAL;
