@@ -14,8 +14,11 @@
 // order, which cell-sorted input makes long -- add their sums with a
 // segmented scan of register shuffles, and the last lane of each run issues
 // the run's eight FP64 atomic additions, each divided by the node's volume
-// once.  All weights and corners stay; only the order of the additions
-// changes.  Particles outside the domain deposit nothing.
+// once.  The weights' products and the sums are double-float (df.h, about
+// 48 bits, on the FP32 pipe); the particle's cell and offset and the final
+// per-node values are binary64.  All weights and corners stay; only the
+// order of the additions changes.  Particles outside the domain deposit
+// nothing.
 //
 // Projection (Sec. 2, "volume-consistent projection to cell-centred
 // charge"; the paper gives no formula -- the reading): each node's control
@@ -25,6 +28,9 @@
 // integral of the half cell (f_lo, f_hi below, f_lo + f_hi = 1), the
 // azimuthal and axial ones are 1/2; so charge is conserved exactly:
 // sum_q rho_q V_q = charge * sum_nu n_nu V_nu.
+#include <cmath>
+
+#include "df.h"
 #include "plan.h"
 
 namespace pp {
@@ -33,7 +39,9 @@ namespace {
 struct DepositArgs {
     int nr, nt, nz;
     long long np;
-    double r_in, z0, inv_dr, inv_da, inv_dz, w;
+    double r_in, z0, inv_dr, inv_da, inv_dz;
+    float w_hi, w_lo;       // the weight W 2^-w_exp in double-float, in [1, 2)
+    int w_exp;
     const double *r, *al, *z;
     const double *inv_vr;   // [nr + 1] 1 / (radial integral of r dr of node a's interval)
     const double *inv_vz;   // [nz + 1] 1 / (dalpha * axial length of node c's interval)
@@ -42,10 +50,12 @@ struct DepositArgs {
 
 constexpr int DEP_PPT = 4;   // consecutive particles per thread
 
-// Cell and the eight corner contributions W w_r w_alpha w_z of particle p
-// (corner index 4 dz + 2 dalpha + dr); false when p is absent or outside.
-__device__ __forceinline__ bool cic_weights(const DepositArgs &a, long long p, int &ir, int &ia, int &iz,
-                                            double c[8]) {
+// Cell and the eight corner contributions W w_r w_alpha w_z 2^-w_exp of
+// particle p (corner index 4 dz + 2 dalpha + dr), in double-float; false
+// when p is absent or outside.  The position arithmetic (cell, offset in the
+// cell) is binary64; the weights' products are double-float, on the FP32
+// pipe -- the deposit's FP64 instructions were its bound.
+__device__ __forceinline__ bool cic_weights(const DepositArgs &a, long long p, int &ir, int &ia, int &iz, df c[8]) {
     if (p >= a.np) return false;
     const double tr = (a.r[p] - a.r_in) * a.inv_dr, ta = a.al[p] * a.inv_da, tz = (a.z[p] - a.z0) * a.inv_dz;
     const double fr = floor(tr), fa = floor(ta), fz = floor(tz);
@@ -55,29 +65,33 @@ __device__ __forceinline__ bool cic_weights(const DepositArgs &a, long long p, i
     ir = (int)fr;
     ia = (int)fa;
     iz = (int)fz;
-    const double xr = tr - fr, xa = ta - fa, xz = tz - fz;
-    const double wz0 = a.w * (1.0 - xz), wz1 = a.w * xz;
-    const double xa0 = 1.0 - xa, xr0 = 1.0 - xr;
-    const double q00 = wz0 * xa0, q01 = wz0 * xa, q10 = wz1 * xa0, q11 = wz1 * xa;
-    c[0] = q00 * xr0;
-    c[1] = q00 * xr;
-    c[2] = q01 * xr0;
-    c[3] = q01 * xr;
-    c[4] = q10 * xr0;
-    c[5] = q10 * xr;
-    c[6] = q11 * xr0;
-    c[7] = q11 * xr;
+    const double xr = tr - fr, xa = ta - fa, xz = tz - fz;   // exact, in [0, 1)
+    const df r1 = split_scaled(xr, 1023), r0 = split_scaled(1.0 - xr, 1023);
+    const df a1 = split_scaled(xa, 1023), a0 = split_scaled(1.0 - xa, 1023);
+    const df z1 = split_scaled(xz, 1023), z0 = split_scaled(1.0 - xz, 1023);
+    const df w = {a.w_hi, a.w_lo};
+    const df wz0 = df_mul(w, z0), wz1 = df_mul(w, z1);
+    const df q00 = df_mul(wz0, a0), q01 = df_mul(wz0, a1), q10 = df_mul(wz1, a0), q11 = df_mul(wz1, a1);
+    c[0] = df_mul(q00, r0);
+    c[1] = df_mul(q00, r1);
+    c[2] = df_mul(q01, r0);
+    c[3] = df_mul(q01, r1);
+    c[4] = df_mul(q10, r0);
+    c[5] = df_mul(q10, r1);
+    c[6] = df_mul(q11, r0);
+    c[7] = df_mul(q11, r1);
     return true;
 }
 
 // The eight atomic additions of a run's sums to the corners of cell (ir, ia, iz).
-__device__ __forceinline__ void add_corners(const DepositArgs &a, int ir, int ia, int iz, const double c[8]) {
+__device__ __forceinline__ void add_corners(const DepositArgs &a, int ir, int ia, int iz, const df c[8]) {
     const int ja = ia + 1 == a.nt ? 0 : ia + 1;
     const size_t rs = (size_t)a.nr + 1, ps = (size_t)a.nt * rs;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         const int nzi = iz + (d >> 2), nai = (d & 2) ? ja : ia, nri = ir + (d & 1);
-        atomicAdd(a.nodes + (size_t)nzi * ps + (size_t)nai * rs + nri, c[d] * a.inv_vr[nri] * a.inv_vz[nzi]);
+        atomicAdd(a.nodes + (size_t)nzi * ps + (size_t)nai * rs + nri,
+                  to_double(c[d], a.w_exp) * a.inv_vr[nri] * a.inv_vz[nzi]);
     }
 }
 
@@ -89,12 +103,14 @@ __global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
     const long long t0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * DEP_PPT;
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    df acc[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) acc[d] = {0.f, 0.f};
     int cr = 0, ca = 0, cz = 0;
     bool have = false;
 #pragma unroll
     for (int t = 0; t < DEP_PPT; ++t) {
-        double c[8];
+        df c[8];
         int ir, ia, iz;
         if (!cic_weights(a, t0 + t, ir, ia, iz, c)) continue;
         if (have && (ir != cr || ia != ca || iz != cz)) {
@@ -110,7 +126,7 @@ __global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
             have = true;
         } else {
 #pragma unroll
-            for (int d = 0; d < 8; ++d) acc[d] += c[d];
+            for (int d = 0; d < 8; ++d) acc[d] = df_add(acc[d], c[d]);
         }
     }
     // runs of lanes with the same last cell (lanes with nothing left: a run each)
@@ -123,8 +139,8 @@ __global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
     for (int d = 0; d < 8; ++d) {
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const double y = __shfl_up_sync(full, acc[d], off);
-            if (lane - off >= start) acc[d] += y;
+            const df y = {__shfl_up_sync(full, acc[d].hi, off), __shfl_up_sync(full, acc[d].lo, off)};
+            if (lane - off >= start) acc[d] = df_add(acc[d], y);
         }
     }
     const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
@@ -194,7 +210,13 @@ extern "C" int pic_poisson_deposit(pic_poisson_plan_t plan, const double *r_dev,
     a.inv_dr = 1.0 / h.dr;
     a.inv_da = q.d.ntheta / q.d.theta_span;
     a.inv_dz = 1.0 / h.dz;
-    a.w = weight;
+    // W = (w_hi + w_lo) 2^w_exp with w_hi + w_lo in [1, 2)
+    int e2 = 0;
+    const double m = std::frexp(weight, &e2);   // weight = m 2^e2, m in [0.5, 1)
+    a.w_exp = e2 - 1;
+    const double ws = 2.0 * m;
+    a.w_hi = (float)ws;
+    a.w_lo = (float)(ws - (double)a.w_hi);
     a.r = r_dev;
     a.al = alpha_dev;
     a.z = z_dev;
