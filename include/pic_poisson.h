@@ -93,6 +93,12 @@ typedef struct {
     double phi_z0, phi_z1;     /* Dirichlet potential on the z walls */
     const double *phi_r_in_z;  /* host, nz values or NULL: inner r-wall potential per axial cell */
     const double *phi_r_out_z; /* host, nz values or NULL: outer r-wall potential per axial cell */
+    const double *r_faces;     /* host, nr + 1 strictly increasing radial faces, or NULL: uniform from r_in
+                                  to r_out.  Given, they define r_in and r_out (the fields above are
+                                  ignored); cell centres are face midpoints and the coefficients follow
+                                  the appendix's face-conductance formulas on them.  The axial spacing
+                                  stays uniform.  pic_poisson_deposit and the no-allocation residual
+                                  need uniform faces. */
     double eps0;               /* vacuum permittivity; <= 0 selects 8.8541878128e-12 F/m */
     int precision;             /* PIC_POISSON_FP64 or PIC_POISSON_MIXED */
     int max_cycles;            /* V-cycle cap; <= 0 selects 200 */
@@ -374,7 +380,7 @@ int pic_poisson_mode_residual(pic_poisson_plan_t plan, const double *uhat_dev, c
  *
  * Needs no plan: the coefficients of A_m are computed inside the kernel from
  * desc's uniform geometry (only nr, ntheta, nz, r_in, r_out, z0, z1 and
- * theta_span are read).  Writes rhat_dev = bhat_dev - A_m uhat_dev (mode
+ * theta_span are read; r_faces must be NULL).  Writes rhat_dev = bhat_dev - A_m uhat_dev (mode
  * layout; rhat_dev may be NULL) and *rel_res_dev = Parseval-weighted
  * ||r|| / ||b|| (one device double) on `stream`, asynchronously: the results
  * are valid once the stream's work up to this call has completed.

@@ -197,8 +197,12 @@ extern "C" int pic_poisson_deposit(pic_poisson_plan_t plan, const double *r_dev,
         set_error("pic_poisson_deposit: NULL pointer or negative count");
         return PIC_POISSON_EINVAL;
     }
-    if (np == 0) return PIC_POISSON_OK;
     const ProblemPlan &q = plan->pr[0];
+    if (!q.uniform_r) {
+        set_error("pic_poisson_deposit needs a uniform radial mesh (the plan has r_faces)");
+        return PIC_POISSON_EINVAL;
+    }
+    if (np == 0) return PIC_POISSON_OK;
     const LevelHost &h = q.lv[0];
     DepositArgs a{};
     a.nr = h.nr;

@@ -22,7 +22,8 @@ namespace {
 
 struct FieldArgs {
     int nr, nt, nz;
-    double inv_dr, inv_hdr, inv_dz, inv_hdz;   // 1 / centre distance, 1 / centre-to-wall distance
+    double inv_dz, inv_hdz;                    // 1 / axial centre distance, 1 / centre-to-wall distance
+    const double *inv_rd;                      // [nr + 1] 1 / radial distance across face a
     double phi_z0, phi_z1;
     const double *win, *wout;                  // [nz] r-wall potentials
     const double *inv_rda;                     // [nr] 1 / (r_i dalpha)
@@ -41,8 +42,8 @@ __global__ void __launch_bounds__(256) k_face_field(const FieldArgs a) {
     // radial face i (between cells i - 1 and i; the inner wall for i = 0)
     const size_t fr = (size_t)row * (nr + 1) + i;
     const double pw = i > 0 ? a.phi[e - 1] : a.win[k];
-    a.er[fr] = (pw - p) * (i > 0 ? a.inv_dr : a.inv_hdr);
-    if (i == a.nr - 1) a.er[fr + 1] = (p - a.wout[k]) * a.inv_hdr;
+    a.er[fr] = (pw - p) * a.inv_rd[i];
+    if (i == a.nr - 1) a.er[fr + 1] = (p - a.wout[k]) * a.inv_rd[a.nr];
     // azimuthal face j + 1/2, periodic
     const int jn = j + 1 == a.nt ? 0 : j + 1;
     a.ea[e] = (p - a.phi[((size_t)k * a.nt + jn) * nr + i]) * a.inv_rda[i];
@@ -76,8 +77,7 @@ extern "C" int pic_poisson_face_field(pic_poisson_plan_t plan, const double *phi
     a.nr = h.nr;
     a.nt = q.d.ntheta;
     a.nz = h.nz;
-    a.inv_dr = 1.0 / h.dr;
-    a.inv_hdr = 1.0 / (0.5 * h.dr);
+    a.inv_rd = q.finv_rd;
     a.inv_dz = 1.0 / h.dz;
     a.inv_hdz = 1.0 / (0.5 * h.dz);
     a.phi_z0 = q.d.phi_z0;

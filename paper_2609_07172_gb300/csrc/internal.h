@@ -44,7 +44,9 @@ constexpr int kMaxBatch = PIC_POISSON_MAX_BATCH;
 // a half-distance Dirichlet face of conductance 2 cz) instead of 2.
 struct LevelHost {
     int nr = 0, nz = 0;
-    double dr = 0, dz = 0;
+    double dr = 0, dz = 0;        // dr: the mean radial width (the spacing itself on a uniform mesh)
+    std::vector<double> rf;       // [nr + 1] radial faces
+    std::vector<double> rc, drc;  // [nr] cell centres (face midpoints) and widths
     int ncls = 0;                 // distinct axial row classes: min(nz, 3)
     std::vector<double> cw, ce, cz, d0r, mu;   // per radial index
     std::vector<double> tz;       // per class

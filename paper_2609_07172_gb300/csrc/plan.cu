@@ -84,6 +84,15 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
         set_error("ntheta must be a power of two in [2, %d] (got %d)", kMaxNtheta, d->ntheta);
         return PIC_POISSON_EINVAL;
     }
+    if (d->r_faces && d->nr >= 1) {   // given faces define the radial walls
+        for (int a = 0; a <= d->nr; ++a)
+            if (!std::isfinite(d->r_faces[a]) || (a > 0 && !(d->r_faces[a] > d->r_faces[a - 1]))) {
+                set_error("r_faces must be nr + 1 finite, strictly increasing values");
+                return PIC_POISSON_EINVAL;
+            }
+        d->r_in = d->r_faces[0];
+        d->r_out = d->r_faces[d->nr];
+    }
     if (!(d->r_in > 0) || !(d->r_out > d->r_in) || !(d->z1 > d->z0) || !std::isfinite(d->r_out) ||
         !std::isfinite(d->z0) || !std::isfinite(d->z1)) {
         set_error("need 0 < r_in < r_out and z0 < z1 (finite)");
@@ -165,21 +174,41 @@ double lambda_m(const pic_poisson_desc &d, int m) {
 // Coefficients of one uniform level (appendix Eqs. interior_face_conductances,
 // dirichlet_face_conductances, mode_mass_coefficient), rediscretised on the
 // level's own cells.
-void build_level(const pic_poisson_desc &d, int nr, int nz, int nm, LevelHost &h) {
+// Uniform radial faces r_in + (r_out - r_in) a / nr.
+std::vector<double> uniform_faces(const pic_poisson_desc &d, int nr) {
+    std::vector<double> f(nr + 1);
+    for (int a = 0; a <= nr; ++a) f[a] = d.r_in + (d.r_out - d.r_in) * a / nr;
+    return f;
+}
+
+// Coefficients of one level on radial faces rf (appendix Eqs.
+// interior_face_conductances, dirichlet_face_conductances,
+// mode_mass_coefficient): a radial face between two cells uses the
+// centre-to-centre distance, a wall face the centre-to-wall distance; cell
+// centres are face midpoints.
+void build_level(const pic_poisson_desc &d, const std::vector<double> &rf, int nz, int nm, LevelHost &h) {
+    const int nr = (int)rf.size() - 1;
     h.nr = nr;
     h.nz = nz;
-    h.dr = (d.r_out - d.r_in) / nr;
+    h.rf = rf;
+    h.dr = (rf[nr] - rf[0]) / nr;
     h.dz = (d.z1 - d.z0) / nz;
-    const double dr = h.dr, dz = h.dz;
+    const double dz = h.dz;
+    h.rc.assign(nr, 0.0);
+    h.drc.assign(nr, 0.0);
+    for (int i = 0; i < nr; ++i) {
+        h.rc[i] = 0.5 * (rf[i] + rf[i + 1]);
+        h.drc[i] = rf[i + 1] - rf[i];
+    }
     h.cw.assign(nr, 0.0);
     h.ce.assign(nr, 0.0);
     h.cz.assign(nr, 0.0);
     h.d0r.assign(nr, 0.0);
     h.mu.assign(nr, 0.0);
     for (int i = 0; i < nr; ++i) {
-        const double rm = d.r_in + i * dr, rp = d.r_in + (i + 1) * dr, rc = d.r_in + (i + 0.5) * dr;
-        const double gw = (i > 0) ? rm * dz / dr : rm * dz / (0.5 * dr);
-        const double ge = (i < nr - 1) ? rp * dz / dr : rp * dz / (0.5 * dr);
+        const double rm = rf[i], rp = rf[i + 1], rc = h.rc[i], dr = h.drc[i];
+        const double gw = (i > 0) ? rm * dz / (rc - h.rc[i - 1]) : rm * dz / (rc - rm);
+        const double ge = (i < nr - 1) ? rp * dz / (h.rc[i + 1] - rc) : rp * dz / (rp - rc);
         h.cw[i] = (i > 0) ? gw : 0.0;
         h.ce[i] = (i < nr - 1) ? ge : 0.0;
         h.d0r[i] = gw + ge;
@@ -280,12 +309,23 @@ int setup_problem(ProblemPlan &q, const pic_poisson_desc &d) {
         q.rout_z.assign(d.phi_r_out_z, d.phi_r_out_z + d.nz);
         q.d.phi_r_out_z = q.rout_z.data();
     }
+    q.uniform_r = !d.r_faces;
+    q.rf0 = d.r_faces ? std::vector<double>(d.r_faces, d.r_faces + d.nr + 1) : uniform_faces(d, d.nr);
+    q.d.r_faces = q.rf0.data();
     int nr[PIC_POISSON_MAX_LEVELS], nz[PIC_POISSON_MAX_LEVELS];
     int rc = hierarchy(q.d, nr, nz, &q.L);
     if (rc) return rc;
     q.nm = d.ntheta / 2 + 1;
     q.lv.resize(q.L);
-    for (int l = 0; l < q.L; ++l) build_level(q.d, nr[l], nz[l], q.nm, q.lv[l]);
+    std::vector<double> rf = q.rf0;   // a level halved in r keeps every other face
+    for (int l = 0; l < q.L; ++l) {
+        if (l > 0 && nr[l] != nr[l - 1]) {
+            std::vector<double> c(nr[l] + 1);
+            for (int a = 0; a <= nr[l]; ++a) c[a] = rf[2 * a];
+            rf.swap(c);
+        }
+        build_level(q.d, rf, nz[l], q.nm, q.lv[l]);
+    }
     return PIC_POISSON_OK;
 }
 
@@ -381,6 +421,7 @@ void carve(pic_poisson_plan_s &P, Carver &c) {
         q.fwin = c.take<double>(q.lv[0].nz);
         q.fwout = c.take<double>(q.lv[0].nz);
         q.finv_rda = c.take<double>(q.lv[0].nr);
+        q.finv_rd = c.take<double>(q.lv[0].nr + 1);
         q.dep_inv_vr = c.take<double>(q.lv[0].nr + 1);
         q.dep_inv_vz = c.take<double>(q.lv[0].nz + 1);
         q.dep_flo = c.take<double>(q.lv[0].nr);
@@ -659,16 +700,13 @@ int upload(pic_poisson_plan_s &P) {
         // level-0 right-hand-side factors: s_i (Eq. mode_rhs) and b^D (Eq. boundary_rhs_appendix)
         const LevelHost &h = q.lv[0];
         std::vector<double> s(h.nr), bD((size_t)h.nr * h.nz, 0.0);
-        for (int i = 0; i < h.nr; ++i) {
-            const double rc = q.d.r_in + (i + 0.5) * h.dr;
-            s[i] = rc * h.dr * h.dz / q.d.eps0;
-        }
+        for (int i = 0; i < h.nr; ++i) s[i] = h.rc[i] * h.drc[i] * h.dz / q.d.eps0;
         for (int k = 0; k < h.nz; ++k)
             for (int i = 0; i < h.nr; ++i) {
                 double v = 0.0;
-                const double rm = q.d.r_in + i * h.dr, rp = q.d.r_in + (i + 1) * h.dr;
-                if (i == 0) v += rm * h.dz / (0.5 * h.dr) * wall_rin(q.d, k);
-                if (i == h.nr - 1) v += rp * h.dz / (0.5 * h.dr) * wall_rout(q.d, k);
+                const double rm = h.rf[i], rp = h.rf[i + 1];
+                if (i == 0) v += rm * h.dz / (h.rc[i] - rm) * wall_rin(q.d, k);
+                if (i == h.nr - 1) v += rp * h.dz / (rp - h.rc[i]) * wall_rout(q.d, k);
                 if (k == 0) v += 2.0 * h.cz[i] * q.d.phi_z0;
                 if (k == h.nz - 1) v += 2.0 * h.cz[i] * q.d.phi_z1;
                 bD[(size_t)k * h.nr + i] = v;
@@ -682,15 +720,19 @@ int upload(pic_poisson_plan_s &P) {
             wout[k] = wall_rout(q.d, k);
         }
         const double da = q.d.theta_span / q.d.ntheta;
-        for (int i = 0; i < h.nr; ++i) inv_rda[i] = 1.0 / ((q.d.r_in + (i + 0.5) * h.dr) * da);
+        for (int i = 0; i < h.nr; ++i) inv_rda[i] = 1.0 / (h.rc[i] * da);
+        std::vector<double> inv_rd(h.nr + 1);   // 1 / the distances of the radial faces' differences
+        for (int a = 0; a <= h.nr; ++a)
+            inv_rd[a] = 1.0 / (a == 0 ? h.rc[0] - h.rf[0] : (a == h.nr ? h.rf[a] - h.rc[a - 1] : h.rc[a] - h.rc[a - 1]));
+        to_dev(inv_rd, q.finv_rd, st, err);
         to_dev(win, q.fwin, st, err);
         to_dev(wout, q.fwout, st, err);
         to_dev(inv_rda, q.finv_rda, st, err);
         // CIC deposit and projection: node control volumes (centre to centre,
         // cut at the walls; exact r dr integral) and the cells' radial octant shares
         std::vector<double> ivr(h.nr + 1), ivz(h.nz + 1), flo(h.nr), fhi(h.nr);
-        auto rface = [&](int a) { return q.d.r_in + a * h.dr; };
-        auto rcen = [&](int i) { return q.d.r_in + (i + 0.5) * h.dr; };
+        auto rface = [&](int a) { return h.rf[a]; };
+        auto rcen = [&](int i) { return h.rc[i]; };
         for (int a = 0; a <= h.nr; ++a) {
             const double lo = a == 0 ? rface(0) : rcen(a - 1), hi = a == h.nr ? rface(h.nr) : rcen(a);
             ivr[a] = 1.0 / ((hi - lo) * (hi + lo) / 2);   // 1 / integral of r dr, factored
@@ -950,11 +992,12 @@ int pic_poisson_cell_coeffs(const pic_poisson_desc *desc, int i, int k, double *
         return PIC_POISSON_EINVAL;
     }
     LevelHost h;
-    build_level(d, d.nr, d.nz, 1, h);
+    build_level(d, d.r_faces ? std::vector<double>(d.r_faces, d.r_faces + d.nr + 1) : uniform_faces(d, d.nr), d.nz, 1,
+                h);
     const bool dw = i == 0, de = i == d.nr - 1, ds = k == 0, dn = k == d.nz - 1;
-    const double rm = d.r_in + i * h.dr, rp = d.r_in + (i + 1) * h.dr;
-    out[0] = dw ? rm * h.dz / (0.5 * h.dr) : h.cw[i];
-    out[1] = de ? rp * h.dz / (0.5 * h.dr) : h.ce[i];
+    const double rm = h.rf[i], rp = h.rf[i + 1];
+    out[0] = dw ? rm * h.dz / (h.rc[i] - rm) : h.cw[i];
+    out[1] = de ? rp * h.dz / (rp - h.rc[i]) : h.ce[i];
     out[2] = ds ? 2.0 * h.cz[i] : h.cz[i];
     out[3] = dn ? 2.0 * h.cz[i] : h.cz[i];
     out[4] = dw;
@@ -962,8 +1005,7 @@ int pic_poisson_cell_coeffs(const pic_poisson_desc *desc, int i, int k, double *
     out[6] = ds;
     out[7] = dn;
     out[8] = h.mu[i];
-    const double rc_ = d.r_in + (i + 0.5) * h.dr;
-    out[9] = rc_ * h.dr * h.dz / d.eps0;
+    out[9] = h.rc[i] * h.drc[i] * h.dz / d.eps0;
     const int tzc = d.nz == 1 ? 4 : ((k == 0 || k == d.nz - 1) ? 3 : 2);
     out[10] = h.d0r[i] + tzc * h.cz[i];
     double bd = 0.0;

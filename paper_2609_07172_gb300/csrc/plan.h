@@ -9,6 +9,8 @@ namespace pp {
 struct ProblemPlan {
     pic_poisson_desc d{};                       // resolved descriptor (wall arrays point below)
     std::vector<double> rin_z, rout_z;
+    std::vector<double> rf0;                    // level-0 radial faces (given or uniform)
+    bool uniform_r = true;
     int L = 0, nm = 0;
     std::vector<LevelHost> lv;
     std::vector<LevelDev<double>> dl;           // FP64 levels (all for FP64 plans, level 0 for mixed)
@@ -23,6 +25,7 @@ struct ProblemPlan {
     double *s0 = nullptr, *bD0 = nullptr;       // level-0 right-hand-side factors
     double *fwin = nullptr, *fwout = nullptr;   // face-field reconstruction: r-wall potentials [nz]
     double *finv_rda = nullptr;                 // and 1 / (r_i dalpha) [nr]
+    double *finv_rd = nullptr;                  // and 1 / radial face distances [nr + 1]
     double *dep_inv_vr = nullptr, *dep_inv_vz = nullptr;   // CIC deposit: 1 / node-volume factors [nr+1], [nz+1]
     double *dep_flo = nullptr, *dep_fhi = nullptr;         // projection: radial octant shares [nr]
 };

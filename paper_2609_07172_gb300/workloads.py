@@ -57,6 +57,7 @@ class Problem:
     eps0: float = EPS0
     phi_r_in_z: tuple | None = field(default=None, compare=False)
     phi_r_out_z: tuple | None = field(default=None, compare=False)
+    r_faces: tuple | None = field(default=None, compare=False)   # nr + 1 radial faces; None: uniform
 
     @property
     def shape(self):
@@ -67,6 +68,9 @@ class Problem:
         return self.ntheta // 2 + 1
 
     def r_centres(self):
+        if self.r_faces is not None:
+            f = np.asarray(self.r_faces, dtype=np.float64)
+            return 0.5 * (f[:-1] + f[1:])
         dr = (self.r_out - self.r_in) / self.nr
         return self.r_in + (np.arange(self.nr) + 0.5) * dr
 
@@ -78,9 +82,20 @@ class Problem:
         da = self.theta_span / self.ntheta
         return (np.arange(self.ntheta) + 0.5) * da
 
+    def with_r_faces(self, faces):
+        """The same problem on a non-uniform radial mesh (faces[0] and faces[-1] become the walls)."""
+        f = tuple(float(v) for v in faces)
+        return replace(self, r_faces=f, r_in=f[0], r_out=f[-1])
+
     def with_r_wall_data(self, phi_r_in_z, phi_r_out_z):
         return replace(self, phi_r_in_z=tuple(float(v) for v in phi_r_in_z),
                        phi_r_out_z=tuple(float(v) for v in phi_r_out_z))
+
+
+def stretched_radial_faces(r_in: float, r_out: float, nr: int, ratio: float) -> np.ndarray:
+    """nr + 1 radial faces from r_in to r_out, each cell `ratio` times as wide as the one inside it."""
+    w = ratio ** np.arange(nr)
+    return r_in + (r_out - r_in) * np.r_[0.0, np.cumsum(w)] / w.sum()
 
 
 def annulus(nr: int, ntheta: int, nz: int, **kw) -> Problem:

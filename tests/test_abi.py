@@ -97,8 +97,14 @@ def test_cell_coeffs_worked_example(golden):
     assert cd[11] == pytest.approx(g0["rhs_dirichlet_factor"][0] * 7.0, rel=1e-15)
 
 
-def test_cell_coeffs_match_oracle_everywhere():
+@pytest.mark.parametrize("radial", ["uniform", "stretched"])
+def test_cell_coeffs_match_oracle_everywhere(radial):
+    """Every coefficient of every cell against the oracle's, on a uniform and
+    on a geometrically stretched radial mesh (each cell 1.3 times the one
+    inside it: the centre-to-centre and centre-to-wall distances differ)."""
     p = W.annulus(9, 8, 7, phi_r_in=3.0, phi_r_out=-2.0, phi_z0=11.0, phi_z1=5.0)
+    if radial == "stretched":
+        p = p.with_r_faces(W.stretched_radial_faces(p.r_in, p.r_out, p.nr, 1.3))
     g = oracle.grid_from_problem(p)
     b = oracle.rhs3d(g, np.zeros(p.shape))
     for k in range(p.nz):
@@ -132,3 +138,11 @@ def test_batch_plan_rejects_mismatched_settings_before_touching_the_gpu():
 def test_unknown_flags_rejected():
     d, _ = B.make_desc(W.c0_problem(), flags=64)
     assert B.load().pic_poisson_query(ctypes.byref(d), None) == B.EINVAL
+
+
+def test_cell_coeffs_rejects_non_increasing_faces():
+    p = W.annulus(8, 4, 8)
+    bad = W.stretched_radial_faces(p.r_in, p.r_out, p.nr, 1.1)
+    bad[3] = bad[2]
+    with pytest.raises(B.PicPoissonError):
+        B.cell_coeffs(p.with_r_faces(bad), 0, 0)
