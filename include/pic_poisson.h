@@ -305,10 +305,13 @@ int pic_poisson_solve_host(pic_poisson_plan_t plan, const double *rho_host, doub
  * dalpha in alpha).  The sums are ADDED to nodes_dev, the nodal number
  * density (nz + 1, ntheta, nr + 1) FP64 (node (c, j, a) at z-face c, alpha
  * j dalpha, r-face a), which the caller zeroes before a step's first species.
- * Lanes of a warp holding particles of one cell add their contributions in
- * registers and one lane per run of equal cells issues the eight FP64
- * atomics, so cell-sorted particles are cheapest; any order is correct (the
- * order of the additions, hence rounding, varies from run to run).
+ * Each thread sums its 4 consecutive particles of one cell in registers, lanes
+ * of a warp holding the same cell add their sums with register shuffles, and
+ * one lane per run of equal cells issues the eight FP64 atomics, so
+ * cell-sorted particles are cheapest; any order is correct (the order of the
+ * additions, hence rounding, varies from run to run).  The weights' products
+ * and those sums are double-float (about 48 significant bits, ~1e-14
+ * relative); cell, offset and the atomics are binary64.
  * Particles outside the domain deposit nothing.  Single-problem plans; on
  * the plan's stream (asynchronous).
  */

@@ -17,6 +17,7 @@ CASES = {
     "small_rin": small_rin,
     "narrow_span": narrow_span,
     "ragged": lambda: W.annulus(37 * 2, 4, 19),
+    "one_cell_wide": lambda: W.annulus(1, 2, 3),
 }
 
 

@@ -47,6 +47,17 @@ def test_nonuniform_solve_matches_oracle(name, precision):
     assert oracle.relres(g, rho, got) <= 1e-12
 
 
+def test_nonuniform_full_multigrid_start_matches_oracle():
+    p = with_bias_walls(stretched(64, 16, 48, 1.03))
+    g = oracle.grid_from_problem(p)
+    rho = _rho(p, 6)
+    ref, _ = oracle.solve3d(g, rho, tol=1e-15)
+    with Plan(p, fmg=1, graph=True) as plan:
+        phi, info = plan.solve(torch.from_numpy(rho).cuda(), tol=0.0)
+    assert info["status"] == B.OK
+    assert rel_l2(phi.cpu().numpy(), ref) <= TOL[FP64], info
+
+
 def test_nonuniform_fused_smoother_matches_oracle():
     p = stretched(64, 16, 48, 1.03)
     g = oracle.grid_from_problem(p)
