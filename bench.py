@@ -166,8 +166,30 @@ def oracle_sample(max_seconds=20.0, min_iters=20):
     dt = time.perf_counter() - t0
     per_iter = dt / iters
     ms = per_iter * rec["iterations"] * 1e3
+    threads = oracle.get_threads()
+    # the same on one core (a shorter sample)
+    oracle.set_threads(1)
+    try:
+        it1 = max(2, int(3.0 / max(per_iter * threads, 1e-3)))
+        t0 = time.perf_counter()
+        oracle.cg_fixed_iterations(g, rho, it1)
+        per_iter1 = (time.perf_counter() - t0) / it1
+    finally:
+        oracle.set_threads(threads)
+    # the small case solved outright: to rel-res 1e-10 and to the rounding floor
+    p0 = W.c0_problem()
+    g0 = oracle.grid_from_problem(p0)
+    rho0 = W.rho_plasma(p0, 0)
+    t0 = time.perf_counter()
+    oracle.solve3d(g0, rho0, tol=1e-10)
+    c0_tol = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.solve3d(g0, rho0, tol=1e-15)
+    c0_floor = time.perf_counter() - t0
     return ms, {"iters_timed": iters, "seconds": dt, "per_iter_ms": per_iter * 1e3,
-                "iters_to_tol": rec["iterations"], "threads": oracle.get_threads()}
+                "iters_to_tol": rec["iterations"], "threads": threads,
+                "one_thread_ms": per_iter1 * rec["iterations"] * 1e3, "one_thread_iters_timed": it1,
+                "c0_seconds_to_1e-10": c0_tol, "c0_seconds_to_floor": c0_floor}
 
 
 def run_reference(args):
@@ -478,7 +500,13 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": det["threads"], "kind": "oracle",
                                 "sample": "%d CG iterations (%.1f s) of the FP64 oracle on the full 512x128x400 "
                                           "system, scaled by the %d iterations it needs to reach rel-res 1e-10"
-                                          % (det["iters_timed"], det["seconds"], det["iters_to_tol"])}
+                                          % (det["iters_timed"], det["seconds"], det["iters_to_tol"]),
+                                "one_thread": {"value": det["one_thread_ms"], "unit": UNIT, "cores": 1,
+                                               "sample": "%d CG iterations, scaled the same way"
+                                                         % det["one_thread_iters_timed"]},
+                                "c0_32x16x32_s": {"to_rel_res_1e-10": det["c0_seconds_to_1e-10"],
+                                                  "to_floor": det["c0_seconds_to_floor"],
+                                                  "cores": det["threads"]}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
