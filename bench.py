@@ -340,7 +340,7 @@ def run_ours(args):
         t = autotune([p], [rhos[0]], tol=args.tol, precision=precision, graph=True, repeats=2,
                      cache=args.tune_cache)
         return {k: t[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads", "smooth_strip",
-                                  "omega", "smooth_fused", "fmg") if k in t}, t
+                                  "omega", "smooth_fused", "fmg", "inner_first") if k in t}, t
 
     kw, tuned = tuned_kw(prec)
     schedules = {args.precision: kw}
@@ -365,7 +365,8 @@ def run_ours(args):
     sched = {"pre_sweeps": kw.get("pre_sweeps", 2), "post_sweeps": kw.get("post_sweeps", 2),
              "inner_cycles": kw.get("inner_cycles", 2), "smooth_threads": kw.get("smooth_threads", 256),
              "smooth_strip": kw.get("smooth_strip", 0), "omega": kw.get("omega", 1.0),
-             "smooth_fused": kw.get("smooth_fused", 0), "fmg": kw.get("fmg", 0)}
+             "smooth_fused": kw.get("smooth_fused", 0), "fmg": kw.get("fmg", 0),
+             "inner_first": kw.get("inner_first", 0)}
 
     line = {"metric": METRIC, "value": ms_per_solve, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_local, "higher_is_better": False, "scaling": "weak",
@@ -577,7 +578,7 @@ def run_batch(args, dev):
     rhos = [torch.from_numpy(W.rho_plasma(p, s)).to(dev) for p, s in probs]
     tuned = autotune(problems, rhos, tol=args.tol, precision=FP64, graph=True, repeats=2, cache=args.tune_cache)
     kw = {k: tuned[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads", "smooth_strip",
-                                "omega", "smooth_fused", "fmg") if k in tuned}
+                                "omega", "smooth_fused", "fmg", "inner_first") if k in tuned}
     bp = BatchPlan(problems, graph=True, **kw)
     phis = [torch.empty_like(r) for r in rhos]
     for _ in range(2):

@@ -119,6 +119,9 @@ typedef struct {
     int fmg;                   /* FP64: 1 starts a solve from a zero iterate with a full-multigrid pass
                                   (right-hand side restricted to every level, coarsest solve, then
                                   prolongation and one V-cycle per level up to the finest); 0 from zero */
+    int inner_first;           /* mixed precision: FP32 V-cycles of the first defect correction of a solve;
+                                  <= inner_cycles (0 included) selects inner_cycles.  A larger first
+                                  correction can save one FP64 defect, update and convergence test */
     unsigned flags;            /* PIC_POISSON_* flags */
 } pic_poisson_desc;
 
@@ -141,6 +144,7 @@ typedef struct {
 typedef struct {
     int pre_sweeps, post_sweeps;           /* best smoothing schedule */
     int inner_cycles;                      /* best FP32 V-cycles per defect correction (mixed) */
+    int inner_first;                       /* best FP32 V-cycles of the first correction (mixed) */
     int smooth_threads;                    /* best smoother block size */
     int smooth_strip;                      /* best smoother strip (0: one entry per thread) */
     double omega;                          /* best over-relaxation factor */
@@ -155,6 +159,7 @@ typedef struct {
     double omega_tried[PIC_POISSON_MAX_TUNE];
     int fused_tried[PIC_POISSON_MAX_TUNE];
     int fmg_tried[PIC_POISSON_MAX_TUNE];
+    int first_tried[PIC_POISSON_MAX_TUNE];
 } pic_poisson_tuning;
 
 typedef struct {
@@ -248,7 +253,9 @@ int pic_poisson_solve_batch(pic_poisson_plan_t plan, const double *const *rho_de
  * (2,1), (2,2) at the best block size, strip and inner cycles; stage 5
  * (mixed precision) the fused smoother with the same four schedules and 1 to
  * 6 inner cycles, or (FP64) the full-multigrid start with the schedules (1,2),
- * (2,1), (2,2).  Each
+ * (2,1), (2,2); stage 6 (mixed precision) 1 to 3 extra first-correction
+ * cycles (inner_first) with the best setting and with one inner cycle fewer.
+ * Each
  * candidate builds its own plan, runs
  * one untimed solve and `repeats` (1..16) timed ones; the score is the median
  * wall time of the solve call.  Results in *out; phi_dev is overwritten.

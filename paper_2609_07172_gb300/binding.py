@@ -51,7 +51,7 @@ class Desc(ctypes.Structure):
         ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int),
         ("inner_cycles", ctypes.c_int), ("smooth_threads", ctypes.c_int), ("smooth_strip", ctypes.c_int),
         ("omega", ctypes.c_double), ("smooth_fused", ctypes.c_int), ("local_bottom", ctypes.c_int),
-        ("fmg", ctypes.c_int), ("flags", ctypes.c_uint),
+        ("fmg", ctypes.c_int), ("inner_first", ctypes.c_int), ("flags", ctypes.c_uint),
     ]
 
 
@@ -81,12 +81,13 @@ MAX_TUNE = 96
 class Tuning(ctypes.Structure):
     _fields_ = [
         ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-        ("smooth_threads", ctypes.c_int), ("smooth_strip", ctypes.c_int), ("omega", ctypes.c_double),
+        ("inner_first", ctypes.c_int), ("smooth_threads", ctypes.c_int), ("smooth_strip", ctypes.c_int), ("omega", ctypes.c_double),
         ("smooth_fused", ctypes.c_int), ("fmg", ctypes.c_int), ("ms", ctypes.c_double), ("tried", ctypes.c_int),
         ("ms_tried", ctypes.c_double * MAX_TUNE), ("pre_tried", ctypes.c_int * MAX_TUNE), ("post_tried", ctypes.c_int * MAX_TUNE),
         ("inner_tried", ctypes.c_int * MAX_TUNE), ("threads_tried", ctypes.c_int * MAX_TUNE),
         ("strip_tried", ctypes.c_int * MAX_TUNE), ("omega_tried", ctypes.c_double * MAX_TUNE),
         ("fused_tried", ctypes.c_int * MAX_TUNE), ("fmg_tried", ctypes.c_int * MAX_TUNE),
+        ("first_tried", ctypes.c_int * MAX_TUNE),
     ]
 
 
@@ -163,7 +164,7 @@ def _check(status, allow=(OK,)):
 
 
 def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1, flags=0, inner_cycles=0,
-              smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0, local_bottom=0, fmg=0):
+              smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0, local_bottom=0, fmg=0, inner_first=0):
     """Descriptor for a workloads.Problem; returns (Desc, keep-alive buffers)."""
     keep = []
     d = Desc()
@@ -190,6 +191,7 @@ def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=
     d.smooth_fused = smooth_fused
     d.local_bottom = local_bottom
     d.fmg = fmg
+    d.inner_first = inner_first
     d.flags = flags
     return d, keep
 
@@ -234,14 +236,14 @@ class Plan:
     def __init__(self, problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
                  profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False,
                  smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0, local_bottom=0, fmg=0,
-                 host_staged=False):
+                 host_staged=False, inner_first=0):
         import torch
         self.problem = problem
         flags = ((PROFILE if profile else 0) | (USE_INITIAL_GUESS if initial_guess else 0)
                  | (GRAPH if graph else 0) | (HOST_STAGED if host_staged else 0))
         self._desc, self._keep = make_desc(problem, precision, max_cycles, pre_sweeps, post_sweeps, flags,
                                            inner_cycles, smooth_threads, smooth_strip, omega,
-                                           smooth_fused, local_bottom, fmg)
+                                           smooth_fused, local_bottom, fmg, inner_first)
         self.stream = torch.cuda.current_stream() if stream is None else stream
         self._plan = ctypes.c_void_p()
         _check(load().pic_poisson_plan(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
@@ -401,7 +403,8 @@ class BatchPlan:
 
     def __init__(self, problems, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=-1,
                  profile=False, initial_guess=False, stream=None, inner_cycles=0, graph=False,
-                 smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0, local_bottom=0, fmg=0):
+                 smooth_threads=0, smooth_strip=0, omega=0.0, smooth_fused=0, local_bottom=0, fmg=0,
+                 inner_first=0):
         import torch
         self.problems = list(problems)
         n = len(self.problems)
@@ -413,7 +416,7 @@ class BatchPlan:
         self._keep = []
         for i, p in enumerate(self.problems):
             d, keep = make_desc(p, precision, max_cycles, pre_sweeps, post_sweeps, flags, inner_cycles,
-                                smooth_threads, smooth_strip, omega, smooth_fused, local_bottom, fmg)
+                                smooth_threads, smooth_strip, omega, smooth_fused, local_bottom, fmg, inner_first)
             self._descs[i] = d
             self._keep.extend(keep)
         self.stream = torch.cuda.current_stream() if stream is None else stream
@@ -486,10 +489,11 @@ def autotune(problems, rhos, tol=1e-10, precision=FP64, graph=False, repeats=3, 
                                        ctypes.byref(out)))
     best = {"pre_sweeps": out.pre_sweeps, "post_sweeps": out.post_sweeps, "inner_cycles": out.inner_cycles,
             "smooth_threads": out.smooth_threads, "smooth_strip": out.smooth_strip, "omega": out.omega,
-            "smooth_fused": out.smooth_fused, "fmg": out.fmg}
+            "smooth_fused": out.smooth_fused, "fmg": out.fmg, "inner_first": out.inner_first}
     tried = [{"pre": out.pre_tried[i], "post": out.post_tried[i], "inner": out.inner_tried[i],
               "threads": out.threads_tried[i], "strip": out.strip_tried[i], "omega": out.omega_tried[i],
-              "fused": out.fused_tried[i], "fmg": out.fmg_tried[i], "ms": out.ms_tried[i]}
+              "fused": out.fused_tried[i], "fmg": out.fmg_tried[i], "first": out.first_tried[i],
+              "ms": out.ms_tried[i]}
              for i in range(out.tried)]
     if cache:
         table = {}

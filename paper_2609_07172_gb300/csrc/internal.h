@@ -142,6 +142,7 @@ struct Ctrl {
     double tol;                   // per solve
     int max_cycles;               // per solve
     int inc;                      // cycles added by one pass of the loop body
+    int inc_first;                // cycles added by the first pass (mixed: inner_first)
     int cycles;                   // V-cycles applied so far
     int cont;                     // 1 while some problem is still iterating
     int n;                        // problems
@@ -220,11 +221,12 @@ cudaError_t launch_update(const DefectTab *tab, unsigned grid, const Ctrl *ctrl,
 // scale of the mixed correction problem.
 cudaError_t launch_bnorm(Ctrl *ctrl, const FFTTab *fft, const double *partials, cudaStream_t st);
 // Convergence test: per-problem residual norms from partials, stop rule,
-// cycle count (+inc when counting), graph conditional (when use_handle).
+// cycle count (+inc when counting == 1, +inc_first when 2), graph
+// conditionals (use_handle bit 0: handle, bit 1: handle2).
 // out[start[p] + c] = sum of chunk c of problem p's partials (fixed order).
 cudaError_t launch_psum(const PsumTab *tab, unsigned grid, const double *partials, double *out, cudaStream_t st);
 cudaError_t launch_check(Ctrl *ctrl, const double *partials, int counting, cudaGraphConditionalHandle handle,
-                         int use_handle, cudaStream_t st);
+                         cudaGraphConditionalHandle handle2, int use_handle, cudaStream_t st);
 // Plain sum of n partials into *out (single problem helpers).
 cudaError_t launch_sum(const double *partials, int n, double *out, cudaStream_t st);
 

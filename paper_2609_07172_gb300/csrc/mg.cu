@@ -654,14 +654,17 @@ __global__ void __launch_bounds__(1024) k_bnorm(Ctrl *__restrict__ ctrl, const F
 // cycle cap with ENOTCONVERGED.  A problem that stopped is left alone: the
 // kernels skip its blocks (launch tables' done flags) and its rel stays the
 // residual of its returned iterate while the others go on.
-// counting: add ctrl->inc to the cycle count first (evaluations after a pass
-// of the loop body).  When use_handle, sets the graph's while-condition.
+// counting: 1 adds ctrl->inc to the cycle count first (evaluations after a
+// pass of the loop body), 2 adds ctrl->inc_first (after the first pass of a
+// solve whose first correction is larger).  use_handle bit 0 / bit 1 set the
+// graph conditionals `handle` / `handle2` to "some problem goes on".
 __global__ void __launch_bounds__(1024) k_check(Ctrl *__restrict__ ctrl, const double *__restrict__ partials,
-                                                int counting, cudaGraphConditionalHandle handle, int use_handle) {
+                                                int counting, cudaGraphConditionalHandle handle,
+                                                cudaGraphConditionalHandle handle2, int use_handle) {
     __shared__ double wsum[32];
     __shared__ double sums[kMaxBatch];
     __shared__ int s_any;
-    const int cycles = ctrl->cycles + (counting ? ctrl->inc : 0);
+    const int cycles = ctrl->cycles + (counting == 2 ? ctrl->inc_first : counting ? ctrl->inc : 0);
     if (threadIdx.x == 0) s_any = 0;
     range_sums(partials, ctrl->rbegin, ctrl->rend, ctrl->n, sums, wsum);
     const double tol = ctrl->tol;
@@ -710,7 +713,8 @@ __global__ void __launch_bounds__(1024) k_check(Ctrl *__restrict__ ctrl, const d
     if (threadIdx.x == 0) {
         ctrl->cycles = cycles;
         ctrl->cont = s_any;
-        if (use_handle) cudaGraphSetConditional(handle, s_any ? 1u : 0u);
+        if (use_handle & 1) cudaGraphSetConditional(handle, s_any ? 1u : 0u);
+        if (use_handle & 2) cudaGraphSetConditional(handle2, s_any ? 1u : 0u);
     }
 }
 
@@ -818,8 +822,8 @@ cudaError_t launch_psum(const PsumTab *tab, unsigned grid, const double *partial
 }
 
 cudaError_t launch_check(Ctrl *ctrl, const double *partials, int counting, cudaGraphConditionalHandle handle,
-                         int use_handle, cudaStream_t st) {
-    k_check<<<1, 1024, 0, st>>>(ctrl, partials, counting, handle, use_handle);
+                         cudaGraphConditionalHandle handle2, int use_handle, cudaStream_t st) {
+    k_check<<<1, 1024, 0, st>>>(ctrl, partials, counting, handle, handle2, use_handle);
     return cudaGetLastError();
 }
 

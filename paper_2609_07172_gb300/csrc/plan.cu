@@ -48,6 +48,7 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
     if (d->pre_sweeps < 0) d->pre_sweeps = 2;
     if (d->post_sweeps < 0) d->post_sweeps = 2;
     if (d->inner_cycles <= 0) d->inner_cycles = 2;
+    if (d->inner_first <= d->inner_cycles || d->precision != PIC_POISSON_MIXED) d->inner_first = d->inner_cycles;
     if (d->smooth_threads <= 0) d->smooth_threads = MG_THREADS;
     if (d->smooth_strip < 0) d->smooth_strip = 0;
     if (d->omega <= 0) d->omega = 1.0;
@@ -102,8 +103,9 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
         set_error("precision must be PIC_POISSON_FP64 or PIC_POISSON_MIXED");
         return PIC_POISSON_EINVAL;
     }
-    if (d->pre_sweeps + d->post_sweeps == 0 || d->pre_sweeps > 64 || d->post_sweeps > 64 || d->inner_cycles > 64) {
-        set_error("need 0 < pre_sweeps + post_sweeps, sweeps <= 64, inner_cycles <= 64");
+    if (d->pre_sweeps + d->post_sweeps == 0 || d->pre_sweeps > 64 || d->post_sweeps > 64 || d->inner_cycles > 64 ||
+        d->inner_first > 64) {
+        set_error("need 0 < pre_sweeps + post_sweeps, sweeps <= 64, inner_cycles and inner_first <= 64");
         return PIC_POISSON_EINVAL;
     }
     if (d->flags & ~kKnownFlags) {
@@ -842,6 +844,7 @@ int upload(pic_poisson_plan_s &P) {
     C.n = P.n;
     C.scaled = mixed ? 1 : 0;
     C.inc = mixed ? P.shared.inner_cycles : 1;
+    C.inc_first = mixed ? P.shared.inner_first : 1;
     const unsigned g_restr0 = (!mixed && P.Lmax > 1) ? P.h64.g_restr[0] : 0;
     P.res_single_offset = g_restr0;
     unsigned b0 = 0;
@@ -890,7 +893,8 @@ int same_settings(const pic_poisson_desc &a, const pic_poisson_desc &b) {
     return a.precision == b.precision && a.max_cycles == b.max_cycles && a.pre_sweeps == b.pre_sweeps &&
            a.post_sweeps == b.post_sweeps && a.inner_cycles == b.inner_cycles && a.flags == b.flags &&
            a.smooth_threads == b.smooth_threads && a.smooth_strip == b.smooth_strip && a.omega == b.omega &&
-           a.smooth_fused == b.smooth_fused && a.local_bottom == b.local_bottom && a.fmg == b.fmg;
+           a.smooth_fused == b.smooth_fused && a.local_bottom == b.local_bottom && a.fmg == b.fmg &&
+           a.inner_first == b.inner_first;
 }
 
 int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
@@ -906,7 +910,7 @@ int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
         if (rc) return rc;
         if (p == 0) P.shared = d;
         else if (!same_settings(P.shared, d)) {
-            set_error("problem %d: precision, max_cycles, sweeps, inner_cycles, smooth_threads, smooth_strip, omega, "
+            set_error("problem %d: precision, max_cycles, sweeps, inner_cycles, inner_first, smooth_threads, smooth_strip, omega, "
                       "smooth_fused and flags must match "
                       "problem 0", p);
             return PIC_POISSON_EINVAL;

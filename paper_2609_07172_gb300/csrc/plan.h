@@ -99,8 +99,9 @@ struct pic_poisson_plan_s {
     // the plan's flags, [1]: mode-layout initial iterate
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    cudaGraphConditionalHandle handle{};
-    pp::Tally seg[2][3];                        // prologue, loop body, epilogue (recorded at capture)
+    cudaGraphConditionalHandle handle{};        // the convergence loop's while node
+    cudaGraphConditionalHandle handle_first{};  // if node of a larger first pass (mixed, inner_first)
+    pp::Tally seg[2][4];                        // prologue, loop body, epilogue, first pass (at capture)
     const double *last_guess[pp::kMaxBatch] = {};
 
     std::vector<cudaEvent_t> evs;               // PROFILE events

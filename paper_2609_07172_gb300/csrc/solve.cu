@@ -4,6 +4,7 @@
 // repeats the body until the check kernel clears its condition.  Also the
 // stage entry points (forward / inverse transform, mode residual).
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -236,8 +237,14 @@ int fp64_residual_and_check(Runner &R, int counting) {
         R.account(PIC_POISSON_PHASE_RESTRICT, 2.0 * n * sizeof(double2), 22.0 * n);
     }
     RUN(R, PIC_POISSON_PHASE_NORM, launch_psum(P.psum, P.g_psum, P.partials, P.partials2, R.st));
-    RUN(R, PIC_POISSON_PHASE_NORM, launch_check(P.ctrl, P.partials2, counting, P.handle, R.use_handle ? 1 : 0, R.st));
+    RUN(R, PIC_POISSON_PHASE_NORM,
+        launch_check(P.ctrl, P.partials2, counting, P.handle, P.handle_first, R.use_handle ? 1 : 0, R.st));
     return PIC_POISSON_OK;
+}
+
+// The mixed form's first correction runs more FP32 V-cycles than the others.
+bool larger_first(const pic_poisson_plan_s &P) {
+    return P.shared.precision == PIC_POISSON_MIXED && P.shared.inner_first > P.shared.inner_cycles;
 }
 
 int mixed_defect_and_check(Runner &R, int counting, bool zero_x = false) {
@@ -246,7 +253,10 @@ int mixed_defect_and_check(Runner &R, int counting, bool zero_x = false) {
     const double n = level0_entries(P, 0);
     R.account(PIC_POISSON_PHASE_DEFECT, n * (2.0 * sizeof(double2) + 3.0 * sizeof(float2)), (zero_x ? 6.0 : 26.0) * n);
     RUN(R, PIC_POISSON_PHASE_NORM, launch_psum(P.psum, P.g_psum, P.partials, P.partials2, R.st));
-    RUN(R, PIC_POISSON_PHASE_NORM, launch_check(P.ctrl, P.partials2, counting, P.handle, R.use_handle ? 1 : 0, R.st));
+    // the first test also decides the if node of a larger first pass
+    const int which = R.use_handle ? (counting == 0 && larger_first(P) ? 3 : 1) : 0;
+    RUN(R, PIC_POISSON_PHASE_NORM,
+        launch_check(P.ctrl, P.partials2, counting, P.handle, P.handle_first, which, R.st));
     return PIC_POISSON_OK;
 }
 
@@ -323,9 +333,10 @@ int enqueue_prologue(Runner &R, int guess) {
 
 // One pass of the convergence loop: FP64, one V-cycle (coarse-grid correction
 // and post-smoothing of the current cycle, pre-smoothing and residual of the
-// next); mixed, inner_cycles FP32 V-cycles on the correction equation, the
-// FP64 update and the next FP64 defect.
-int enqueue_body(Runner &R) {
+// next); mixed, inner_cycles FP32 V-cycles on the correction equation (first:
+// inner_first, the solve's first pass), the FP64 update and the next FP64
+// defect.
+int enqueue_body(Runner &R, bool first = false) {
     pic_poisson_plan_s &P = R.P;
     const int pre = P.shared.pre_sweeps;
     if (P.shared.precision == PIC_POISSON_FP64) {
@@ -337,7 +348,8 @@ int enqueue_body(Runner &R) {
         }
         return fp64_residual_and_check(R, 1);
     }
-    for (int c = 0; c < P.shared.inner_cycles; ++c) {
+    const int inner = first ? P.shared.inner_first : P.shared.inner_cycles;
+    for (int c = 0; c < inner; ++c) {
         if (P.Lmax > 1) {
             int rc = smooth_level(R, P.h32, 0, pre, c == 0 && pre > 0, false);
             if (rc) return rc;
@@ -350,7 +362,7 @@ int enqueue_body(Runner &R) {
     RUN(R, PIC_POISSON_PHASE_DEFECT, launch_update(P.defect, P.g_defect, P.ctrl, R.st));
     const double n = level0_entries(P, 0);
     R.account(PIC_POISSON_PHASE_DEFECT, n * (2.0 * sizeof(double2) + sizeof(float2)), 4.0 * n);
-    return mixed_defect_and_check(R, 1);
+    return mixed_defect_and_check(R, first ? 2 : 1);
 }
 
 int enqueue_epilogue(Runner &R) {
@@ -406,8 +418,9 @@ int set_io(pic_poisson_plan_s &P, const double *const *rho, double *const *phi, 
 }
 
 int read_cont(pic_poisson_plan_s &P, int *cont) {
-    // the leading scalars of Ctrl (tol .. scaled) hold the loop flag
-    PP_CUDA(cudaMemcpyAsync(P.hctrl_out, P.ctrl, 32, cudaMemcpyDeviceToHost, P.stream));
+    // the leading scalars of Ctrl hold the loop flag
+    PP_CUDA(cudaMemcpyAsync(P.hctrl_out, P.ctrl, offsetof(Ctrl, cont) + sizeof(int), cudaMemcpyDeviceToHost,
+                            P.stream));
     PP_CUDA(cudaStreamSynchronize(P.stream));
     *cont = P.hctrl_out->cont;
     return PIC_POISSON_OK;
@@ -422,6 +435,12 @@ int run_host_loop(pic_poisson_plan_s &P, int guess, Tally &tally, double *ms) {
     int cont = 0;
     rc = read_cont(P, &cont);
     if (rc) return rc;
+    if (cont && larger_first(P)) {
+        rc = enqueue_body(R, true);
+        if (rc) return rc;
+        rc = read_cont(P, &cont);
+        if (rc) return rc;
+    }
     while (cont) {
         rc = enqueue_body(R);
         if (rc) return rc;
@@ -459,6 +478,11 @@ int capture_graph(pic_poisson_plan_s &P, int guess) {
         set_error("graph conditional handle creation failed");
         return fail(PIC_POISSON_ECUDA);
     }
+    const bool first = larger_first(P);
+    if (first && cudaGraphConditionalHandleCreate(&P.handle_first, graph, 0, 0) != cudaSuccess) {
+        set_error("graph conditional handle creation failed");
+        return fail(PIC_POISSON_ECUDA);
+    }
     Runner R0(P, P.cap0, false, true, P.seg[v][0]);
     int rc = enqueue_prologue(R0, guess);
     if (rc) return fail(rc);
@@ -467,6 +491,40 @@ int capture_graph(pic_poisson_plan_s &P, int guess) {
     if (cudaStreamGetCaptureInfo(P.cap0, &status, nullptr, &graph, &deps, nullptr, &ndeps) != cudaSuccess) {
         set_error("cudaStreamGetCaptureInfo failed");
         return fail(PIC_POISSON_ECUDA);
+    }
+    if (first) {
+        // the larger first pass: an if node on the first convergence test,
+        // ahead of the while node (whose condition that pass's test sets)
+        cudaGraphNodeParams ip{};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = P.handle_first;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t inode;
+        if (cudaGraphAddNode(&inode, graph, deps, nullptr, ndeps, &ip) != cudaSuccess ||
+            cudaStreamUpdateCaptureDependencies(P.cap0, &inode, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+                cudaSuccess) {
+            set_error("adding the if node failed");
+            return fail(PIC_POISSON_ECUDA);
+        }
+        cudaGraph_t fbody = ip.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(P.cap1, fbody, nullptr, nullptr, 0, mode) != cudaSuccess) {
+            set_error("capturing the first pass failed to start");
+            return fail(PIC_POISSON_ECUDA);
+        }
+        body_open = true;
+        Runner RF(P, P.cap1, false, true, P.seg[v][3]);
+        rc = enqueue_body(RF, true);
+        if (rc) return fail(rc);
+        body_open = false;
+        if (cudaStreamEndCapture(P.cap1, &fbody) != cudaSuccess) {
+            set_error("capturing the first pass failed");
+            return fail(PIC_POISSON_ECUDA);
+        }
+        if (cudaStreamGetCaptureInfo(P.cap0, &status, nullptr, &graph, &deps, nullptr, &ndeps) != cudaSuccess) {
+            set_error("cudaStreamGetCaptureInfo failed");
+            return fail(PIC_POISSON_ECUDA);
+        }
     }
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
@@ -538,14 +596,19 @@ int solve_batch(pic_poisson_plan_s &P, const double *const *rho, double *const *
     PP_CUDA(cudaMemcpyAsync(P.hctrl_out, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, P.stream));
     PP_CUDA(cudaStreamSynchronize(P.stream));
     const Ctrl &C = *P.hctrl_out;
-    const int inc = std::max(P.hctrl.inc, 1);
+    const int inc = std::max(P.hctrl.inc, 1), inc_first = std::max(P.hctrl.inc_first, 1);
+    const bool first = larger_first(P);
+    // passes of the loop body behind a cycle count (after the larger first pass, if any)
+    auto body_passes = [&](int cycles) { return first ? (cycles >= inc_first ? (cycles - inc_first) / inc : 0)
+                                                       : cycles / inc; };
     if (graph) {
-        const int passes = C.cycles / inc;
+        const int passes = body_passes(C.cycles), fp = first && C.cycles >= inc_first ? 1 : 0;
         for (int ph = 0; ph < PIC_POISSON_NPHASE; ++ph) {
             const Tally *sg = P.seg[v];
-            tally.bytes[ph] = sg[0].bytes[ph] + passes * sg[1].bytes[ph] + sg[2].bytes[ph];
-            tally.flops[ph] = sg[0].flops[ph] + passes * sg[1].flops[ph] + sg[2].flops[ph];
-            tally.launches[ph] = sg[0].launches[ph] + passes * sg[1].launches[ph] + sg[2].launches[ph];
+            tally.bytes[ph] = sg[0].bytes[ph] + passes * sg[1].bytes[ph] + sg[2].bytes[ph] + fp * sg[3].bytes[ph];
+            tally.flops[ph] = sg[0].flops[ph] + passes * sg[1].flops[ph] + sg[2].flops[ph] + fp * sg[3].flops[ph];
+            tally.launches[ph] =
+                sg[0].launches[ph] + passes * sg[1].launches[ph] + sg[2].launches[ph] + fp * sg[3].launches[ph];
         }
     }
     int worst = PIC_POISSON_OK;
@@ -557,7 +620,9 @@ int solve_batch(pic_poisson_plan_s &P, const double *const *rho, double *const *
         memset(&I, 0, sizeof I);
         I.status = s;
         I.cycles = C.done_cycles[p];   // a problem of a batch stops being iterated when it converges
-        I.outer_iterations = P.shared.precision == PIC_POISSON_MIXED ? C.done_cycles[p] / inc : 0;
+        const int dc = C.done_cycles[p];
+        I.outer_iterations = P.shared.precision != PIC_POISSON_MIXED ? 0
+                             : first ? (dc >= inc_first ? 1 + body_passes(dc) : 0) : dc / inc;
         I.rel_res = C.rel[p];
         I.rel_res0 = C.rel_first[p];
         for (int ph = 0; ph < PIC_POISSON_NPHASE; ++ph) {

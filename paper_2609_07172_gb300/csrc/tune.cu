@@ -7,7 +7,8 @@
 // best schedule, stage 3 strips of 2 and 4 rows at the best block size, stage 4
 // over-relaxation factors with the short schedules, stage 5 (mixed precision)
 // the fused FP32 smoother with the short schedules and 1 to 6 inner cycles
-// (FP64: the full-multigrid start with three schedules).  Each
+// (FP64: the full-multigrid start with three schedules), stage 6 (mixed) a
+// larger first correction (inner_first) for the best setting.  Each
 // candidate gets its own plan, one untimed solve (which also captures the
 // graph when PIC_POISSON_GRAPH is set) and `repeats` timed solves; its score
 // is the median wall time of a solve call, which includes every host-side
@@ -27,6 +28,7 @@ struct Cand {
     double omega;
     int fused, fmg;
     double ms;
+    int first = 0;   // FP32 V-cycles of the first correction (0: inner)
 };
 
 int time_candidate(const pic_poisson_desc *descs, int n, const double *const *rho, double *const *phi, double tol,
@@ -41,6 +43,7 @@ int time_candidate(const pic_poisson_desc *descs, int n, const double *const *rh
         x.omega = c.omega;
         x.smooth_fused = c.fused;
         x.fmg = c.fmg;
+        x.inner_first = c.first;
         x.flags &= ~PIC_POISSON_PROFILE;
     }
     pic_poisson_plan_t plan = nullptr;
@@ -103,6 +106,7 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
             out->omega_tried[k] = c.omega;
             out->fused_tried[k] = c.fused;
             out->fmg_tried[k] = c.fmg;
+            out->first_tried[k] = c.first;
         }
         if (c.ms < best.ms) best = c;
         return rc;
@@ -147,9 +151,23 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
             const int rc = record(c);
             if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;
         }
+    // a larger first correction: two outer iterations may then reach tol
+    // where three were needed (one FP64 defect, update and test fewer)
+    if (mixed) {
+        const Cand top = best;
+        for (int inner : {top.inner, top.inner - 1})
+            for (int extra = 1; inner >= 1 && extra <= 3; ++extra) {
+                Cand c = top;
+                c.inner = inner;
+                c.first = inner + extra;
+                const int rc = record(c);
+                if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;
+            }
+    }
     out->pre_sweeps = best.pre;
     out->post_sweeps = best.post;
     out->inner_cycles = best.inner;
+    out->inner_first = best.first > best.inner ? best.first : best.inner;
     out->smooth_threads = best.threads;
     out->smooth_strip = best.strip;
     out->omega = best.omega;

@@ -75,6 +75,13 @@ def test_precision_and_sweeps_validated():
     assert B.load().pic_poisson_query(ctypes.byref(d), None) == B.EINVAL
     d, _ = B.make_desc(W.c0_problem(), pre_sweeps=0, post_sweeps=0)
     assert B.load().pic_poisson_query(ctypes.byref(d), None) == B.EINVAL
+    lay = B.Layout()
+    for prec in (B.FP64, B.MIXED):
+        d, _ = B.make_desc(W.c0_problem(), precision=prec, inner_first=65)
+        assert B.load().pic_poisson_query(ctypes.byref(d), ctypes.byref(lay)) == (B.EINVAL if prec == B.MIXED
+                                                                                  else B.OK)
+        d, _ = B.make_desc(W.c0_problem(), precision=prec, inner_first=64)
+        assert B.load().pic_poisson_query(ctypes.byref(d), ctypes.byref(lay)) == B.OK
 
 
 def test_cell_coeffs_worked_example(golden):

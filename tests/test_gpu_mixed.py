@@ -134,3 +134,80 @@ def test_fused_smoother_rejects_unsupported_schedules():
             Plan(p, precision=MIXED, smooth_fused=1, **kw)
     with pytest.raises(B.PicPoissonError):
         Plan(p, smooth_fused=1)   # FP64 form
+
+
+@pytest.mark.parametrize("fused", [0, 1], ids=["halfsweeps", "fused"])
+@pytest.mark.parametrize("inner,first", [(1, 3), (3, 5), (2, 6)])
+def test_mixed_larger_first_correction(inner, first, fused):
+    """inner_first FP32 V-cycles on the first correction, inner_cycles on the
+    later ones: the loop reaches the oracle's floor, its cycle count is
+    first + inner (outer - 1), and the graph (an if node ahead of the while
+    node) gives the host loop's iterate bit for bit."""
+    p = with_bias_walls(W.annulus(96, 16, 40))
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=33)
+    ref, _ = oracle.solve3d(g, rho, tol=1e-15)
+    kw = dict(precision=MIXED, inner_cycles=inner, inner_first=first, smooth_fused=fused, pre_sweeps=2,
+              post_sweeps=2)
+    out = {}
+    for graph in (False, True):
+        with Plan(p, graph=graph, **kw) as plan:
+            out[graph] = plan.solve(dev(rho), tol=0.0)
+    (pa, ia), (pg, ig) = out[False], out[True]
+    assert ia["status"] == ig["status"] == B.OK
+    assert ia["outer_iterations"] >= 2
+    assert ia["cycles"] == first + inner * (ia["outer_iterations"] - 1)
+    for k in ("cycles", "outer_iterations", "rel_res", "launches", "bytes_phase"):
+        assert ia[k] == ig[k], k
+    assert torch.equal(pa, pg)
+    assert rel_l2(pg.cpu().numpy(), ref) <= MIXED_TOL
+
+
+def test_mixed_larger_first_correction_saves_a_defect():
+    """At tol 1e-10 a first correction of inner + 2 cycles needs no more FP32
+    cycles than plain inner-cycle corrections and no more FP64 defects."""
+    p = with_bias_walls(W.annulus(128, 32, 96))
+    g = oracle.grid_from_problem(p)
+    rho = dev(W.rho_plasma(p, seed=34))
+    res = {}
+    for first in (0, 5):
+        with Plan(p, precision=MIXED, inner_cycles=3, inner_first=first, graph=True) as plan:
+            phi, info = plan.solve(rho, tol=1e-10)
+        assert info["status"] == B.OK and info["rel_res"] <= 1e-10
+        assert oracle.relres(g, rho.cpu().numpy(), phi.cpu().numpy()) <= 1.05e-10
+        res[first] = info
+    assert res[5]["outer_iterations"] <= res[0]["outer_iterations"]
+    assert res[5]["launches_phase"]["defect"] <= res[0]["launches_phase"]["defect"]
+
+
+@pytest.mark.parametrize("graph", [False, True], ids=["hostloop", "graph"])
+def test_mixed_larger_first_correction_skipped_when_converged(graph):
+    """An initial iterate that already meets tol stops at the first test: the
+    if node of the larger first pass and the while node both stay closed."""
+    p = with_bias_walls(W.annulus(64, 16, 48))
+    rho = dev(W.rho_plasma(p, seed=35))
+    with Plan(p, precision=MIXED) as plan:
+        phi0, _ = plan.solve(rho, tol=1e-13)
+    with Plan(p, precision=MIXED, inner_cycles=2, inner_first=4, initial_guess=True, graph=graph) as plan:
+        phi = phi0.clone()
+        phi, info = plan.solve(rho, phi, tol=1e-10)
+        assert info["status"] == B.OK and info["cycles"] == 0 and info["outer_iterations"] == 0
+        assert info["rel_res"] <= 1e-10
+        # a looser start runs the first pass and then the loop
+        phi = (phi0 * 0.9).contiguous()
+        phi, info = plan.solve(rho, phi, tol=1e-10)
+        assert info["status"] == B.OK and info["rel_res"] <= 1e-10
+        assert info["cycles"] >= 4 and (info["cycles"] - 4) % 2 == 0
+
+
+def test_mixed_larger_first_correction_in_an_uneven_batch():
+    from paper_2609_07172_gb300 import BatchPlan
+    probs = [with_bias_walls(W.annulus(*d)) for d in [(32, 16, 32), (96, 16, 40), (15, 4, 9), (64, 32, 48)]]
+    rhos = [W.rho_plasma(q, seed=36 + i) for i, q in enumerate(probs)]
+    with BatchPlan(probs, precision=MIXED, inner_cycles=2, inner_first=4, graph=True) as bp:
+        phis, infos = bp.solve([dev(r) for r in rhos], tol=0.0)
+    for q, r, phi, info in zip(probs, rhos, phis, infos):
+        ref, _ = oracle.solve3d(oracle.grid_from_problem(q), r, tol=1e-15)
+        assert info["status"] == B.OK, info
+        assert info["cycles"] == 4 + 2 * (info["outer_iterations"] - 1)
+        assert rel_l2(phi.cpu().numpy(), ref) <= MIXED_TOL
