@@ -52,6 +52,7 @@ class _Grid(ctypes.Structure):
         ("L_alpha", ctypes.c_double), ("eps0", ctypes.c_double),
         ("phi_rin", ctypes.c_void_p), ("phi_rout", ctypes.c_void_p),
         ("phi_z0", ctypes.c_void_p), ("phi_z1", ctypes.c_void_p),
+        ("active", ctypes.c_void_p), ("phi_exposed", ctypes.c_double),
     ]
 
 
@@ -88,10 +89,16 @@ def _f64(a):
 
 
 class Grid:
-    """A cell grid given by explicit face coordinates and wall potentials."""
+    """A cell grid given by explicit face coordinates and wall potentials.
+
+    active: optional (nz, nr) boolean array of the composite domain's active
+    cells (Sec. 2.2: a union of rectangular patches); a face between an active
+    and an inactive cell is a Dirichlet face at phi_exposed.  Inactive cells
+    are not unknowns: their rows are the identity with b = 0.
+    """
 
     def __init__(self, r_faces, z_faces, ntheta, L_alpha, eps0,
-                 phi_rin, phi_rout, phi_z0, phi_z1):
+                 phi_rin, phi_rout, phi_z0, phi_z1, active=None, phi_exposed=0.0):
         self.r_faces = _f64(r_faces)
         self.z_faces = _f64(z_faces)
         self.nr = self.r_faces.size - 1
@@ -103,11 +110,15 @@ class Grid:
         self.phi_rout = _f64(np.broadcast_to(phi_rout, (self.nz,)))
         self.phi_z0 = _f64(np.broadcast_to(phi_z0, (self.nr,)))
         self.phi_z1 = _f64(np.broadcast_to(phi_z1, (self.nr,)))
+        self.active = None if active is None else np.ascontiguousarray(active, dtype=np.uint8).reshape(
+            self.nz, self.nr)
+        self.phi_exposed = float(phi_exposed)
         self._c = _Grid(self.nr, self.ntheta, self.nz,
                         self.r_faces.ctypes.data, self.z_faces.ctypes.data,
                         self.L_alpha, self.eps0,
                         self.phi_rin.ctypes.data, self.phi_rout.ctypes.data,
-                        self.phi_z0.ctypes.data, self.phi_z1.ctypes.data)
+                        self.phi_z0.ctypes.data, self.phi_z1.ctypes.data,
+                        None if self.active is None else self.active.ctypes.data, self.phi_exposed)
 
     @property
     def shape(self):
@@ -120,7 +131,7 @@ class Grid:
     def homogeneous(self):
         """The same grid with every wall potential set to zero."""
         return Grid(self.r_faces, self.z_faces, self.ntheta, self.L_alpha, self.eps0,
-                    0.0, 0.0, 0.0, 0.0)
+                    0.0, 0.0, 0.0, 0.0, self.active, 0.0)
 
 
 def grid_from_problem(p) -> Grid:
@@ -130,7 +141,15 @@ def grid_from_problem(p) -> Grid:
     z_faces = p.z0 + (p.z1 - p.z0) * np.arange(p.nz + 1) / p.nz
     rin = np.asarray(p.phi_r_in_z) if p.phi_r_in_z is not None else p.phi_r_in
     rout = np.asarray(p.phi_r_out_z) if p.phi_r_out_z is not None else p.phi_r_out
-    return Grid(r_faces, z_faces, p.ntheta, p.theta_span, p.eps0, rin, rout, p.phi_z0, p.phi_z1)
+    active = None
+    patches = getattr(p, "patches", None)
+    if patches:
+        # the composite domain: cells (i, k) with i0 <= i < i1, k0 <= k < k1 of some patch
+        active = np.zeros((p.nz, p.nr), dtype=bool)
+        for (i0, i1, k0, k1) in patches:
+            active[k0:k1, i0:i1] = True
+    return Grid(r_faces, z_faces, p.ntheta, p.theta_span, p.eps0, rin, rout, p.phi_z0, p.phi_z1,
+                active, getattr(p, "phi_exposed", 0.0))
 
 
 def set_threads(n: int) -> None:

@@ -42,6 +42,10 @@ typedef struct {
     const double *phi_rout; /* nz values: outer r wall */
     const double *phi_z0;   /* nr values: lower z wall, per radial cell */
     const double *phi_z1;   /* nr values: upper z wall */
+    const unsigned char *active; /* nz*nr cell flags (k-major), or NULL: every cell active.  The active
+                                    cells are the composite domain's union of patches (Sec. 2.2) */
+    double phi_exposed;     /* Dirichlet potential of an exposed face: a face between an active and an
+                               inactive cell */
 } oracle_grid;
 
 typedef struct {
@@ -70,12 +74,15 @@ static double rc(const oracle_grid *g, int i) { return 0.5 * (g->r_faces[i] + g-
 static double zc(const oracle_grid *g, int k) { return 0.5 * (g->z_faces[k] + g->z_faces[k + 1]); }
 static double drw(const oracle_grid *g, int i) { return g->r_faces[i + 1] - g->r_faces[i]; }
 static double dzw(const oracle_grid *g, int k) { return g->z_faces[k + 1] - g->z_faces[k]; }
+static int act(const oracle_grid *g, int i, int k) { return !g->active || g->active[(size_t)k * g->nr + i]; }
 
 /*
  * Coefficients of cell (i,k), appendix Eqs. interior_face_conductances and
  * dirichlet_face_conductances: a face between two active cells uses the
- * centre-to-centre distance; a face on the domain wall is a Dirichlet face and
- * uses the centre-to-face distance.
+ * centre-to-centre distance; a face on the domain wall, or between an active
+ * and an inactive cell (an exposed patch face, Sec. 2.2), is a Dirichlet face
+ * and uses the centre-to-face distance.  An inactive cell has all-zero
+ * coefficients (it is not an unknown of the system).
  * out[0..3] = conductance of the W (r-), E (r+), S (z-), N (z+) face
  * out[4..7] = 1 if that face is a Dirichlet face, else 0
  * out[8] = mu (Eq. mode_mass_coefficient), out[9] = s (Eq. mode_rhs),
@@ -86,13 +93,17 @@ void oracle_cell_coeffs(const oracle_grid *g, int i, int k, double *out) {
     const double rm = g->r_faces[i], rp = g->r_faces[i + 1];
     double gw, ge, gs, gn;
     int dw = 0, de = 0, ds = 0, dn = 0;
-    if (i > 0) gw = rm * dz / (r - rc(g, i - 1));
+    if (!act(g, i, k)) {
+        for (int a = 0; a < 11; ++a) out[a] = 0.0;
+        return;
+    }
+    if (i > 0 && act(g, i - 1, k)) gw = rm * dz / (r - rc(g, i - 1));
     else { gw = rm * dz / (r - rm); dw = 1; }
-    if (i < g->nr - 1) ge = rp * dz / (rc(g, i + 1) - r);
+    if (i < g->nr - 1 && act(g, i + 1, k)) ge = rp * dz / (rc(g, i + 1) - r);
     else { ge = rp * dz / (rp - r); de = 1; }
-    if (k > 0) gs = r * dr / (z - zc(g, k - 1));
+    if (k > 0 && act(g, i, k - 1)) gs = r * dr / (z - zc(g, k - 1));
     else { gs = r * dr / (z - g->z_faces[k]); ds = 1; }
-    if (k < g->nz - 1) gn = r * dr / (zc(g, k + 1) - z);
+    if (k < g->nz - 1 && act(g, i, k + 1)) gn = r * dr / (zc(g, k + 1) - z);
     else { gn = r * dr / (g->z_faces[k + 1] - z); dn = 1; }
     out[0] = gw; out[1] = ge; out[2] = gs; out[3] = gn;
     out[4] = dw; out[5] = de; out[6] = ds; out[7] = dn;
@@ -101,7 +112,8 @@ void oracle_cell_coeffs(const oracle_grid *g, int i, int k, double *out) {
     out[10] = gw + ge + gs + gn;
 }
 
-/* out = A phi (homogeneous: the Dirichlet values themselves enter only b). */
+/* out = A phi (homogeneous: the Dirichlet values themselves enter only b).
+   An inactive cell's row is the identity (its value is held at zero by b = 0). */
 void oracle_apply(const oracle_grid *g, const double *phi, double *out) {
     const int nr = g->nr, nt = g->ntheta, nz = g->nz;
     const double da = g->L_alpha / nt;
@@ -111,6 +123,10 @@ void oracle_apply(const oracle_grid *g, const double *phi, double *out) {
         double c[11];
         for (int i = 0; i < nr; ++i) {
             oracle_cell_coeffs(g, i, k, c);
+            if (!act(g, i, k)) {
+                for (int j = 0; j < nt; ++j) out[((size_t)k * nt + j) * nr + i] = phi[((size_t)k * nt + j) * nr + i];
+                continue;
+            }
             for (int j = 0; j < nt; ++j) {
                 const int jp = (j + 1) % nt, jm = (j + nt - 1) % nt;
                 const size_t q = ((size_t)k * nt + j) * nr + i;
@@ -136,7 +152,9 @@ void oracle_apply(const oracle_grid *g, const double *phi, double *out) {
     }
 }
 
-/* b = s rho + sum over Dirichlet faces of G^D phi^D (appendix Eq. full_finite_volume_row). */
+/* b = s rho + sum over Dirichlet faces of G^D phi^D (appendix Eq. full_finite_volume_row);
+   a face on the bounding wall takes that wall's potential, an exposed patch face
+   phi_exposed; an inactive cell has b = 0. */
 void oracle_rhs(const oracle_grid *g, const double *rho, double *b) {
     const int nr = g->nr, nt = g->ntheta, nz = g->nz;
 #pragma omp parallel for schedule(static) num_threads(nthreads())
@@ -145,10 +163,10 @@ void oracle_rhs(const oracle_grid *g, const double *rho, double *b) {
         for (int i = 0; i < nr; ++i) {
             oracle_cell_coeffs(g, i, k, c);
             double bd = 0.0;
-            if (c[4] != 0.0) bd += c[0] * g->phi_rin[k];
-            if (c[5] != 0.0) bd += c[1] * g->phi_rout[k];
-            if (c[6] != 0.0) bd += c[2] * g->phi_z0[i];
-            if (c[7] != 0.0) bd += c[3] * g->phi_z1[i];
+            if (c[4] != 0.0) bd += c[0] * (i == 0 ? g->phi_rin[k] : g->phi_exposed);
+            if (c[5] != 0.0) bd += c[1] * (i == nr - 1 ? g->phi_rout[k] : g->phi_exposed);
+            if (c[6] != 0.0) bd += c[2] * (k == 0 ? g->phi_z0[i] : g->phi_exposed);
+            if (c[7] != 0.0) bd += c[3] * (k == nz - 1 ? g->phi_z1[i] : g->phi_exposed);
             for (int j = 0; j < nt; ++j) {
                 const size_t q = ((size_t)k * nt + j) * nr + i;
                 b[q] = c[9] * rho[q] + bd;

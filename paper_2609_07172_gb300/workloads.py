@@ -18,6 +18,8 @@ and uneven cases built around it):
   counts (mean 27 per species, macroparticle weight 1e8), a Gaussian axial
   ionisation profile, and an m = 8 azimuthal ion-density wave of 5 %
   amplitude (rho = e (n_i - n_e), Eq. electrostatic_system).
+* :func:`channel_plume` -- the composite channel-plume domain (two patches of
+  the bounding annulus, grounded exposed faces); charge is zero outside it.
 * :func:`uneven_batch` -- 24 independent problems of mixed sizes.
 * :func:`drifting_rho` -- the same plasma with the m = 8 wave advanced by one
   azimuthal cell per step.
@@ -58,6 +60,10 @@ class Problem:
     phi_r_in_z: tuple | None = field(default=None, compare=False)
     phi_r_out_z: tuple | None = field(default=None, compare=False)
     r_faces: tuple | None = field(default=None, compare=False)   # nr + 1 radial faces; None: uniform
+    # composite domain (Sec. 2.2): active cells are the union of patches (i0, i1, k0, k1), cells
+    # i0 <= i < i1, k0 <= k < k1; None: the whole annulus.  Exposed patch faces are at phi_exposed.
+    patches: tuple | None = field(default=None, compare=False)
+    phi_exposed: float = 0.0
 
     @property
     def shape(self):
@@ -87,6 +93,19 @@ class Problem:
         f = tuple(float(v) for v in faces)
         return replace(self, r_faces=f, r_in=f[0], r_out=f[-1])
 
+    def with_patches(self, patches, phi_exposed: float = 0.0):
+        """The same bounding annulus restricted to a union of rectangular cell patches."""
+        return replace(self, patches=tuple(tuple(int(v) for v in q) for q in patches), phi_exposed=float(phi_exposed))
+
+    def active_cells(self) -> np.ndarray:
+        """(nz, nr) boolean mask of the cells the patches cover (all True without patches)."""
+        if not self.patches:
+            return np.ones((self.nz, self.nr), dtype=bool)
+        a = np.zeros((self.nz, self.nr), dtype=bool)
+        for (i0, i1, k0, k1) in self.patches:
+            a[k0:k1, i0:i1] = True
+        return a
+
     def with_r_wall_data(self, phi_r_in_z, phi_r_out_z):
         return replace(self, phi_r_in_z=tuple(float(v) for v in phi_r_in_z),
                        phi_r_out_z=tuple(float(v) for v in phi_r_out_z))
@@ -101,6 +120,16 @@ def stretched_radial_faces(r_in: float, r_out: float, nr: int, ratio: float) -> 
 def annulus(nr: int, ntheta: int, nz: int, **kw) -> Problem:
     """The paper-scale annular geometry and wall potentials at any resolution."""
     return Problem(nr=nr, ntheta=ntheta, nz=nz, **kw)
+
+
+def channel_plume(nr: int, ntheta: int, nz: int, **kw) -> Problem:
+    """Channel-plume composite domain of the paper's topology (Sec. 2.2): an
+    annular channel, radial cells [nr/4, nr/2), over the lower half of the
+    axis (its base on the 300 V wall at z = 0), opening into a plume that
+    fills the whole radial extent over the upper half.  Exposed channel and
+    exit-plane faces are grounded (0 V)."""
+    p = annulus(nr, ntheta, nz, **kw)
+    return p.with_patches(((nr // 4, nr // 2, 0, nz // 2), (0, nr, nz // 2, nz)), 0.0)
 
 
 def c0_problem() -> Problem:
@@ -153,7 +182,10 @@ def rho_plasma(p: Problem, seed, wave_phase: float = 0.0, mean_count: float = 27
     dz = L / p.nz
     da = p.theta_span / p.ntheta
     vol = p.r_centres() * dr * da * dz
-    return (E_CHARGE * weight) * (n_i - n_e).astype(np.float64) / vol[None, None, :]
+    rho = (E_CHARGE * weight) * (n_i - n_e).astype(np.float64) / vol[None, None, :]
+    if p.patches:
+        rho *= p.active_cells()[:, None, :]   # no charge outside the composite domain
+    return rho
 
 
 def uneven_batch(seed: int = 3, count: int = 24):
@@ -207,7 +239,10 @@ def rho_plasma_torch(p: Problem, seed: int, wave_phase: float = 0.0, device="cud
     dz = L / p.nz
     da = p.theta_span / p.ntheta
     vol = torch.as_tensor(p.r_centres() * dr * da * dz, device=device)
-    return (E_CHARGE * weight) * (n_i - n_e) / vol[None, None, :]
+    rho = (E_CHARGE * weight) * (n_i - n_e) / vol[None, None, :]
+    if p.patches:
+        rho = rho * torch.as_tensor(p.active_cells(), device=device)[:, None, :]
+    return rho
 
 
 def drifting_rho_torch(p: Problem, t: int, base_seed: int = 3, device="cuda"):
