@@ -81,6 +81,8 @@ extern "C" {
 
 #define PIC_POISSON_MAX_LEVELS 16
 #define PIC_POISSON_MAX_BATCH 64      /* problems per batched plan */
+#define PIC_POISSON_MAX_PATCHES 64    /* rectangles of one composite domain */
+#define PIC_POISSON_MAX_DENSE 1024    /* active cells of a composite domain's coarsest level */
 
 typedef struct pic_poisson_plan_s *pic_poisson_plan_t;
 
@@ -122,6 +124,22 @@ typedef struct {
     int inner_first;           /* mixed precision: FP32 V-cycles of the first defect correction of a solve;
                                   <= inner_cycles (0 included) selects inner_cycles.  A larger first
                                   correction can save one FP64 defect, update and convergence test */
+    int n_patches;             /* composite domain (Sec. 2.2): the active r-z cells are the union of
+                                  n_patches rectangles of the grid, 0 <= n_patches <= PIC_POISSON_MAX_PATCHES;
+                                  0 selects the whole annulus */
+    const int *patches;        /* host, 4 ints per patch: i0, i1, k0, k1 -- the cells i0 <= i < i1,
+                                  k0 <= k < k1; non-empty, inside the grid, pairwise disjoint (patches
+                                  may share faces: a shared face joins them).  A face between an active
+                                  and an inactive cell is an exposed face: a Dirichlet face at
+                                  phi_exposed with the centre-to-face distance, like a wall face; faces
+                                  on the grid's walls keep the wall potentials.  Charge outside the
+                                  patches is ignored and phi is returned as 0 there.  Coarsening halves
+                                  a direction only while every patch boundary in it lies on a coarse
+                                  face (protected faces); the coarsest level is solved densely and may
+                                  hold at most PIC_POISSON_MAX_DENSE active cells.  Not with
+                                  smooth_fused, pic_poisson_face_field, pic_poisson_deposit or the
+                                  no-allocation residual. */
+    double phi_exposed;        /* Dirichlet potential of the exposed faces (V) */
     unsigned flags;            /* PIC_POISSON_* flags */
 } pic_poisson_desc;
 
@@ -186,6 +204,8 @@ int pic_poisson_query(const pic_poisson_desc *desc, pic_poisson_layout *out);
  * out[4..7] = 1 for a Dirichlet face, else 0, out[8] = mu (Eq.
  * mode_mass_coefficient), out[9] = s (Eq. mode_rhs), out[10] = D0 (Eq.
  * base_diagonal_with_boundary), out[11] = b^D (Eq. boundary_rhs_appendix).
+ * In a composite domain an exposed face is a Dirichlet face at phi_exposed,
+ * and a cell outside the patches returns twelve zeros.
  * Host only.  `out` holds 12 doubles.
  */
 int pic_poisson_cell_coeffs(const pic_poisson_desc *desc, int i, int k, double *out);

@@ -51,7 +51,9 @@ class Desc(ctypes.Structure):
         ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int),
         ("inner_cycles", ctypes.c_int), ("smooth_threads", ctypes.c_int), ("smooth_strip", ctypes.c_int),
         ("omega", ctypes.c_double), ("smooth_fused", ctypes.c_int), ("local_bottom", ctypes.c_int),
-        ("fmg", ctypes.c_int), ("inner_first", ctypes.c_int), ("flags", ctypes.c_uint),
+        ("fmg", ctypes.c_int), ("inner_first", ctypes.c_int),
+        ("n_patches", ctypes.c_int), ("patches", ctypes.c_void_p), ("phi_exposed", ctypes.c_double),
+        ("flags", ctypes.c_uint),
     ]
 
 
@@ -179,6 +181,14 @@ def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=
             arr = (ctypes.c_double * len(vals))(*vals)
             keep.append(arr)
             setattr(d, name, ctypes.addressof(arr))
+    patches = getattr(problem, "patches", None)
+    if patches:
+        flat = [int(v) for q in patches for v in q]
+        arr = (ctypes.c_int * len(flat))(*flat)
+        keep.append(arr)
+        d.n_patches = len(patches)
+        d.patches = ctypes.addressof(arr)
+        d.phi_exposed = float(getattr(problem, "phi_exposed", 0.0))
     d.eps0 = problem.eps0
     d.precision = precision
     d.max_cycles = max_cycles

@@ -183,6 +183,10 @@ int single(const pic_poisson_plan_s *P, const char *what) {
         set_error("%s needs a single-problem plan (this plan holds %d problems)", what, P->n);
         return PIC_POISSON_EINVAL;
     }
+    if (P->pr[0].nact > 0) {
+        set_error("%s does not take a composite domain (the plan has patches)", what);
+        return PIC_POISSON_EINVAL;
+    }
     return PIC_POISSON_OK;
 }
 }  // namespace

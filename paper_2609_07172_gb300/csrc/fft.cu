@@ -188,7 +188,9 @@ __global__ void __launch_bounds__(FFT_THREADS) k_forward(const FFTTab *__restric
     //   X_m = hs (S - i T),  X_{M-m} = hs conj(S + i T);
     // X_0 = 2 hs (Re Z_0 + Im Z_0), X_M = 2 hs (Re Z_0 - Im Z_0), both exactly real.
     const double2 *tw2 = (const double2 *)P.tw2;
-    const double hs = (P.s ? P.s[valid ? i : 0] : 1.0) * P.half_inv_n;
+    // s_i, or per cell in a composite domain (zero outside its patches)
+    const size_t si = valid ? (P.s_rows ? (size_t)k * nr + i : (size_t)i) : 0;
+    const double hs = (P.s ? P.s[si] : 1.0) * P.half_inv_n;
     double acc_in = 0.0, acc_edge = 0.0;   // Parseval weight 2 (0 < m < M) and 1 (m = 0, M)
     double2 *ob = outb + lane * nm;
     for (int m = 1 + warp; 2 * m < M; m += nw) {
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_forward(const FFTTab *__restric
     for (int f = threadIdx.x; f < ncols * nm; f += blockDim.x) dst[f] = outb[f];
     if (P.bh && P.invd) {
         // b_hat = b / diag for the smoother (row class of plane k, cells i0.., all modes)
-        const int cls = k == 0 ? 0 : (k == nz - 1 ? P.ncls - 1 : 1);
+        const int cls = P.rcls ? P.rcls[k] : (k == 0 ? 0 : (k == nz - 1 ? P.ncls - 1 : 1));
         const double *inv = P.invd + ((size_t)cls * nr + i0) * nm;
         double2 *dh = P.bh + ((size_t)k * nr + i0) * nm;
         for (int f = threadIdx.x; f < ncols * nm; f += blockDim.x) {

@@ -198,7 +198,9 @@ __global__ void __launch_bounds__(FFT_THREADS) k_forward_df(const FFTTab *__rest
     fft_stages(buf, P.twf, M, P.log2M, lane, warp, nw);
 
     // unpack, modes m and M - m together (as fft.cu), hs = s_i / (2N)
-    const double hsd = (P.s ? P.s[valid ? i : 0] : 1.0) * P.half_inv_n;
+    // s_i, or per cell in a composite domain (zero outside its patches)
+    const size_t si = valid ? (P.s_rows ? (size_t)k * nr + i : (size_t)i) : 0;
+    const double hsd = (P.s ? P.s[si] : 1.0) * P.half_inv_n;
     const df hs = split_scaled(hsd, exp_field(hsd));      // hs 2^-(e - 1023): exact scaling below
     const int shs = exp_field(hsd) - 1023;
     const df two_hs = {2.f * hs.hi, 2.f * hs.lo};

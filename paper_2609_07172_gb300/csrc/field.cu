@@ -72,6 +72,10 @@ extern "C" int pic_poisson_face_field(pic_poisson_plan_t plan, const double *phi
         return PIC_POISSON_EINVAL;
     }
     const ProblemPlan &q = plan->pr[0];
+    if (q.nact > 0) {
+        set_error("pic_poisson_face_field does not take a composite domain (the plan has patches)");
+        return PIC_POISSON_EINVAL;
+    }
     const LevelHost &h = q.lv[0];
     FieldArgs a{};
     a.nr = h.nr;

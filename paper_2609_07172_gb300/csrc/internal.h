@@ -52,6 +52,13 @@ struct LevelHost {
     std::vector<double> tz;       // per class
     std::vector<double> invd, diag;             // [ncls][nr][nm]
     std::vector<double> hw, he, hz;             // [ncls][nr][nm]: cw, ce, cz divided by diag
+    // composite domain (empty otherwise): active flags [nz][nr], the coefficient
+    // class of every row [nz] (rows with the same active pattern in themselves
+    // and both neighbours share one), and each class's sum of face conductances
+    // D0 [ncls][nr] (zero for inactive cells)
+    std::vector<unsigned char> act;
+    std::vector<int> rcls;
+    std::vector<double> d0c;
 };
 
 // One level of one problem, as the kernels see it.
@@ -64,6 +71,9 @@ template <class T> struct LevelDev {
     const T *cw, *ce, *cz;        // [nr]
     const T *invd, *diag;         // [ncls][nr][nm]: omega / diag, diag
     const T *hw, *he, *hz;        // [ncls][nr][nm] omega * off-diagonal conductances / diag
+    const int *rcls;              // composite domain: coefficient class of each row [nz]; null: rows 0 and
+                                  // nz-1 are classes 0 and ncls-1, the others class 1.  An inactive cell
+                                  // has zero diag, invd and h entries, holds u = 0 and has no residual
     V2<T> *u;                     // iterate / correction, [nz][nr][nm]
     V2<T> *b;                     // right-hand side, [nz][nr][nm]
     V2<T> *bh;                    // right-hand side / diag, [nz][nr][nm]
@@ -76,6 +86,16 @@ template <class T> struct CoarseDev {
     const T *e;                   // [nr] off-diagonal -ce_i of the radial operator
     const T *piv;                 // [nm][nz][nr] inverse pivots of the Thomas factorisation
     const T *cpr;                 // [nm][nz][nr] upper multipliers of the Thomas factorisation
+    // composite domain (nact > 0): dense solve over the nact active cells,
+    // A_m = A_0 + lambda_m diag(mu) = M^(-1/2) Q (Lambda + lambda_m) Q^T M^(-1/2) with M = diag(mu)
+    int nact;
+    const int *aidx;              // [nact] cell index k nr + i of each active cell
+    const int *amap;              // [nz][nr] active index of a cell, -1 when inactive
+    const T *Q;                   // [nact][nact] eigenvectors, Q[a nact + j]
+    const T *QT;                  // [nact][nact] the transpose
+    const T *lam;                 // [nact] eigenvalues of M^(-1/2) A_0 M^(-1/2)
+    const T *isq;                 // [nact] 1 / sqrt(mu) of each active cell
+    const T *lamm;                // [nm] lambda_m
 };
 
 // Work of one launch over a batch of problems: problem p owns the blocks
@@ -119,7 +139,9 @@ struct FFTProb {
     const double *tw2;            // [M+1] e^{-2 pi i m / nt}, same form (see tw_rot)
     const float4 *twf, *tw2f;     // the same tables in double-float, (a_hi, a_lo, b_hi, b_lo)
     double half_inv_n;            // 1 / (2 nt)
-    const double *s;              // [nr] s_i (Eq. mode_rhs); null: plain 1/N transform
+    const double *s;              // [nr] s_i (Eq. mode_rhs), [nz][nr] when s_rows; null: plain 1/N transform
+    int s_rows;                   // composite domain: s per cell, 0 outside the patches
+    const int *rcls;              // composite domain: level-0 coefficient class per row (b_hat)
     const double *bD;             // [nz][nr] Dirichlet right-hand side; may be null
     const double *invd;           // level-0 inverse diagonal [ncls][nr][nm]; null: no b_hat
     double2 *b;                   // mode-layout output of the forward transform

@@ -39,6 +39,12 @@ __device__ __forceinline__ int row_class(int k, int nz, int ncls) {
     return k == 0 ? 0 : (k == nz - 1 ? ncls - 1 : 1);
 }
 
+// Coefficient class of row k of a level: its own per-row table in a composite
+// domain, else first / interior / last row.
+template <class T> __device__ __forceinline__ int lclass(const LevelDev<T> &L, int k) {
+    return L.rcls ? L.rcls[k] : row_class(k, L.nz, L.ncls);
+}
+
 template <class T> __device__ __forceinline__ V2<T> fma2(T a, V2<T> x, V2<T> y) {
     return mk<T>(fma(a, x.x, y.x), fma(a, x.y, y.y));
 }
@@ -100,8 +106,10 @@ __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i,
     V2<T> acc = fma2<T>(L.cz[i], s, L.b[idx]);
     if (i > 0) acc = fma2<T>(L.cw[i], L.u[idx - L.nm], acc);
     if (i < L.nr - 1) acc = fma2<T>(L.ce[i], L.u[idx + L.nm], acc);
-    const T d = L.diag[((size_t)row_class(k, L.nz, L.ncls) * L.nr + i) * L.nm + m];
-    return fma2<T>(-d, L.u[idx], acc);
+    const T d = L.diag[((size_t)lclass(L, k) * L.nr + i) * L.nm + m];
+    const V2<T> r = fma2<T>(-d, L.u[idx], acc);
+    // a cell outside a composite domain's patches (zero diagonal) has no residual
+    return (L.rcls && d == T(0)) ? mk<T>(0, 0) : r;
 }
 
 // One red-black Gauss-Seidel half-sweep over the cells of one colour:
@@ -135,7 +143,7 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
         int k, i;
         colour_cell(c, L.nr, color, k, i);
         const size_t idx = ((size_t)k * L.nr + i) * nm + m;
-        const size_t tb = ((size_t)row_class(k, L.nz, L.ncls) * L.nr + i) * nm + m;
+        const size_t tb = ((size_t)lclass(L, k) * L.nr + i) * nm + m;
         const size_t rowstride = (size_t)L.nr * nm;
         V2<T> s = mk<T>(0, 0);
         if (k > 0) s = L.u[idx - rowstride];
@@ -187,8 +195,9 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
             const int k = k0 + 2 * t;
             if (k >= L.nz) break;
             T hz = hz1, hw = hw1, he = he1;
-            if (k == 0 || k == L.nz - 1) {   // boundary rows have their own coefficient class
-                const size_t tb = (size_t)row_class(k, L.nz, L.ncls) * rs + tcol;
+            if (L.rcls || k == 0 || k == L.nz - 1) {   // boundary rows (every row of a composite
+                                                       // domain) have their own coefficient class
+                const size_t tb = (size_t)lclass(L, k) * rs + tcol;
                 hz = L.hz[tb];
                 hw = L.hw[tb];
                 he = L.he[tb];
@@ -262,7 +271,7 @@ k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ p
         }
         C.b[e] = sum;
         if (F.init > 0) {
-            const T inv = C.invd[((size_t)row_class(K, C.nz, C.ncls) * C.nr + I) * nm + m];
+            const T inv = C.invd[((size_t)lclass(C, K) * C.nr + I) * nm + m];
             const V2<T> bh = mk<T>(sum.x * inv, sum.y * inv);
             C.bh[e] = bh;
             C.u[e] = (F.init == 2 && ((K + I) & 1) == 0) ? bh : mk<T>(0, 0);
@@ -337,12 +346,21 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
         i = (int)(c - (unsigned)k * F.nr);
     }
     const size_t idx = ((size_t)k * F.nr + i) * nm + m;
+    // composite domain: a cell outside the patches keeps u = 0
+    if (F.rcls && F.diag[((size_t)F.rcls[k] * F.nr + i) * nm + m] == T(0)) {
+        if (ASSIGN) F.u[idx] = mk<T>(0, 0);
+        return;
+    }
     const bool cz2 = F.nz != C.nz, cr2 = F.nr != C.nr;
     const int K = cz2 ? (k >> 1) : k, I = cr2 ? (i >> 1) : i;
     const int K2 = K + ((k & 1) ? 1 : -1);
     const int I2 = I + ((i & 1) ? 1 : -1);
-    const bool kin = K2 >= 0 && K2 < C.nz;
-    const bool iin = I2 >= 0 && I2 < C.nr;
+    bool kin = K2 >= 0 && K2 < C.nz;
+    bool iin = I2 >= 0 && I2 < C.nr;
+    if (C.rcls) {   // an exposed face reflects like a wall: the correction vanishes on it
+        if (iin) iin = C.diag[((size_t)C.rcls[K] * C.nr + I2) * nm + m] != T(0);
+        if (kin) kin = C.diag[((size_t)C.rcls[K2] * C.nr + I) * nm + m] != T(0);
+    }
     const int Kx = kin ? K2 : K, Ix = iin ? I2 : I;
     const V2<T> c0 = C.u[((size_t)K * C.nr + I) * nm + m];
     V2<T> u = ASSIGN ? mk<T>(0, 0) : F.u[idx];   // ASSIGN: u = P c (full-multigrid interpolation)
@@ -389,7 +407,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_rhs_restrict(const LaunchTab<T> 
         sum = mk<T>(sum.x + b.x, sum.y + b.y);
     }
     C.b[e] = sum;
-    const T inv = C.invd[((size_t)row_class(K, C.nz, C.ncls) * C.nr + I) * nm + m];
+    const T inv = C.invd[((size_t)lclass(C, K) * C.nr + I) * nm + m];
     C.bh[e] = mk<T>(sum.x * inv, sum.y * inv);
     C.u[e] = mk<T>(0, 0);
 }
@@ -468,7 +486,7 @@ k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, doubl
         const float2 b32 = make_float2(f64_to_f32_pow2(r.x, ls), f64_to_f32_pow2(r.y, ls));
         const float w = (m == 0 || 2 * m == D.nt) ? 1.f : 2.f;
         acc = f32_to_f64_pow2(w * fmaf(b32.x, b32.x, b32.y * b32.y), 0);
-        const float inv = S.invd[((size_t)row_class(k, S.nz, S.ncls) * S.nr + i) * nm + m];
+        const float inv = S.invd[((size_t)lclass(S, k) * S.nr + i) * nm + m];
         const float2 bh = make_float2(b32.x * inv, b32.y * inv);
         S.b[e] = b32;
         S.bh[e] = bh;
@@ -519,6 +537,33 @@ __global__ void __launch_bounds__(MG_THREADS) k_coarse(const CoarseTab<T> *__res
     const int nr = D.nr, nz = D.nz, nm = D.nm;
     const int lb = (int)(blockIdx.x - tab->start[p]);
     const int m = lb >> 1, comp = lb & 1;
+    if (D.nact > 0) {
+        // composite domain: u = M^(-1/2) Q (Lambda + lambda_m)^(-1) Q^T M^(-1/2) b over the
+        // active cells (eigenvectors from plan time, shared by all modes); zero elsewhere
+        const int n = D.nact;
+        T *y = (T *)smraw, *z = y + n;
+        const T *bg = (const T *)L.b + comp;
+        for (int a = threadIdx.x; a < n; a += blockDim.x) y[a] = bg[2 * ((size_t)D.aidx[a] * nm + m)] * D.isq[a];
+        __syncthreads();
+        const T lm = D.lamm[m];
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {   // z = (Lambda + lambda_m)^(-1) Q^T y
+            T acc = 0;
+            for (int a = 0; a < n; ++a) acc = fma(D.Q[(size_t)a * n + j], y[a], acc);
+            z[j] = acc / (D.lam[j] + lm);
+        }
+        __syncthreads();
+        T *ug = (T *)L.u + comp;
+        for (int f = threadIdx.x; f < nr * nz; f += blockDim.x) {   // u = M^(-1/2) Q z
+            const int a = D.amap[f];
+            T x = 0;
+            if (a >= 0) {
+                for (int j = 0; j < n; ++j) x = fma(D.QT[(size_t)j * n + a], z[j], x);
+                x *= D.isq[a];
+            }
+            ug[2 * ((size_t)f * nm + m)] = x;
+        }
+        return;
+    }
     const int h = nz >> 1, hz = nz - h;      // mirror pairs, rows with k <= nz-1-k
     T *bs = (T *)smraw;                      // [nz][nr]: b, then P (rows < hz) and Q (row nz-1-k)
     const int lw = nr + 1;                   // padded rows: the Thomas threads walk rows

@@ -161,6 +161,10 @@ extern "C" int pic_poisson_mode_residual_noalloc(const pic_poisson_desc *desc, c
                   2 * (NA_MAX_MODES - 1));
         return PIC_POISSON_EINVAL;
     }
+    if (d.n_patches > 0) {
+        set_error("pic_poisson_mode_residual_noalloc does not take a composite domain (n_patches must be 0)");
+        return PIC_POISSON_EINVAL;
+    }
     if (d.r_faces) {
         set_error("pic_poisson_mode_residual_noalloc needs a uniform radial mesh (r_faces must be NULL)");
         return PIC_POISSON_EINVAL;

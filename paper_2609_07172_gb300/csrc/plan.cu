@@ -7,11 +7,13 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 
 #include <type_traits>
 
 #include "plan.h"
+#include "symeig.h"
 
 namespace pp {
 
@@ -112,6 +114,30 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
         set_error("unknown flag bits 0x%x", d->flags & ~kKnownFlags);
         return PIC_POISSON_EINVAL;
     }
+    if (d->n_patches < 0 || d->n_patches > PIC_POISSON_MAX_PATCHES || (d->n_patches > 0 && !d->patches)) {
+        set_error("n_patches must be in [0, %d] with a patches array", PIC_POISSON_MAX_PATCHES);
+        return PIC_POISSON_EINVAL;
+    }
+    for (int a = 0; a < d->n_patches; ++a) {
+        const int *x = d->patches + 4 * a;
+        if (!(0 <= x[0] && x[0] < x[1] && x[1] <= d->nr && 0 <= x[2] && x[2] < x[3] && x[3] <= d->nz)) {
+            set_error("patch %d (%d, %d, %d, %d) must be non-empty and inside the %d x %d grid", a, x[0], x[1],
+                      x[2], x[3], d->nr, d->nz);
+            return PIC_POISSON_EINVAL;
+        }
+        for (int b2 = 0; b2 < a; ++b2) {
+            const int *y = d->patches + 4 * b2;
+            if (x[0] < y[1] && y[0] < x[1] && x[2] < y[3] && y[2] < x[3]) {
+                set_error("patches %d and %d overlap", b2, a);
+                return PIC_POISSON_EINVAL;
+            }
+        }
+    }
+    if (d->n_patches > 0 && (d->smooth_fused || !std::isfinite(d->phi_exposed))) {
+        set_error("a composite domain needs smooth_fused = 0 and a finite phi_exposed");
+        return PIC_POISSON_EINVAL;
+    }
+    if (d->n_patches == 0) d->patches = nullptr;
     const double n = (double)d->nr * d->nz * (d->ntheta / 2 + 1);
     if (n > 2.0e9) {
         set_error("too many mode entries (nr*nz*(ntheta/2+1) = %.0f > 2e9)", n);
@@ -126,15 +152,26 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
 // only N_z, below 1/sqrt(2) halve only N_r, otherwise halve both; a halved
 // count must be even and at least 8, and the level being coarsened needs an
 // even N_r (it is smoothed red-black).  Stop when the preferred step is not
-// possible; the coarsest level is solved directly.
+// possible; the coarsest level is solved directly.  A composite domain's
+// patch boundaries are protected faces (Sec. 3.2): a direction is halved only
+// while every patch boundary in it lies on a face of the coarser level, so no
+// coarse cell straddles a patch edge.
 int hierarchy(const pic_poisson_desc &d, int *nr, int *nz, int *levels) {
     int L = 1, r = d.nr, z = d.nz;
     nr[0] = r;
     nz[0] = z;
     const double Lr = d.r_out - d.r_in, Lz = d.z1 - d.z0, s2 = std::sqrt(2.0);
+    int sr = 1, sz = 1;   // level-0 cells per cell of the current level
+    auto aligned = [&](int axis, int scale) {
+        for (int a = 0; a < d.n_patches; ++a) {
+            const int *x = d.patches + 4 * a + 2 * axis;
+            if (x[0] % scale || x[1] % scale) return false;
+        }
+        return true;
+    };
     while (L < PIC_POISSON_MAX_LEVELS && r % 2 == 0) {
         const double aspect = (Lr / r) / (Lz / z);
-        const bool can_r = r >= 8, can_z = z % 2 == 0 && z >= 8;
+        const bool can_r = r >= 8 && aligned(0, 2 * sr), can_z = z % 2 == 0 && z >= 8 && aligned(1, 2 * sz);
         int r2 = r, z2 = z;
         if (aspect > s2) {
             if (!can_z) break;
@@ -147,6 +184,8 @@ int hierarchy(const pic_poisson_desc &d, int *nr, int *nz, int *levels) {
             r2 = r / 2;
             z2 = z / 2;
         }
+        if (r2 != r) sr *= 2;
+        if (z2 != z) sz *= 2;
         r = r2;
         z = z2;
         nr[L] = r;
@@ -154,6 +193,20 @@ int hierarchy(const pic_poisson_desc &d, int *nr, int *nz, int *levels) {
         ++L;
     }
     *levels = L;
+    if (d.n_patches > 0) {   // dense coarsest solve over the active cells
+        long act = 0;
+        for (int a = 0; a < d.n_patches; ++a) {
+            const int *x = d.patches + 4 * a;
+            act += (long)((x[1] - x[0]) / sr) * ((x[3] - x[2]) / sz);
+        }
+        if (act > PIC_POISSON_MAX_DENSE) {
+            set_error("the composite domain's coarsest level %d x %d has %ld active cells (> %d): put the patch "
+                      "boundaries on multiples of larger powers of two",
+                      r, z, act, PIC_POISSON_MAX_DENSE);
+            return PIC_POISSON_EINVAL;
+        }
+        return PIC_POISSON_OK;
+    }
     if (z > kMaxCoarseNz || (long)r * z > kMaxCoarseCells) {
         set_error("coarsest level %d x %d (r x z) exceeds the direct-solve limit (nz <= %d, cells <= %d); "
                   "use cell counts with more factors of two",
@@ -244,6 +297,138 @@ void build_level(const pic_poisson_desc &d, const std::vector<double> &rf, int n
             }
 }
 
+// Face conductances of active cell (i, k) of level h (appendix Eqs.
+// interior_face_conductances, dirichlet_face_conductances): g[0..3] of the W,
+// E, S, N faces and dir[0..3] = 1 for a Dirichlet face -- a wall face or, in a
+// composite domain, an exposed face (the neighbour is inactive), both at the
+// centre-to-face distance.
+void cell_faces(const LevelHost &h, int i, int k, double *g, int *dir) {
+    auto on = [&](int ii, int kk) { return h.act.empty() || h.act[(size_t)kk * h.nr + ii] != 0; };
+    const double rm = h.rf[i], rp = h.rf[i + 1], rc = h.rc[i];
+    dir[0] = !(i > 0 && on(i - 1, k));
+    dir[1] = !(i < h.nr - 1 && on(i + 1, k));
+    dir[2] = !(k > 0 && on(i, k - 1));
+    dir[3] = !(k < h.nz - 1 && on(i, k + 1));
+    g[0] = dir[0] ? rm * h.dz / (rc - rm) : h.cw[i];
+    g[1] = dir[1] ? rp * h.dz / (rp - rc) : h.ce[i];
+    g[2] = dir[2] ? 2.0 * h.cz[i] : h.cz[i];
+    g[3] = dir[3] ? 2.0 * h.cz[i] : h.cz[i];
+}
+
+// Composite-domain level tables: rows are grouped into classes by their
+// active pattern and their neighbours' (each distinct pattern one class);
+// an inactive cell gets zero diag, invd and h entries (the smoother leaves
+// its u = 0 and the residual kernels skip it), an active cell the diagonal of
+// its own faces, exposed ones Dirichlet, and no coupling into inactive cells.
+void build_masked_tables(const pic_poisson_desc &d, int nm, LevelHost &h) {
+    const int nr = h.nr, nz = h.nz;
+    std::map<std::vector<unsigned char>, int> seen;
+    std::vector<int> rep;
+    h.rcls.assign(nz, 0);
+    for (int k = 0; k < nz; ++k) {
+        std::vector<unsigned char> sig(nr);
+        for (int i = 0; i < nr; ++i) {
+            const unsigned char a = h.act[(size_t)k * nr + i];
+            const unsigned char sb = k > 0 ? h.act[(size_t)(k - 1) * nr + i] : 0;
+            const unsigned char nb = k < nz - 1 ? h.act[(size_t)(k + 1) * nr + i] : 0;
+            sig[i] = (unsigned char)(a | (sb << 1) | (nb << 2));
+        }
+        auto it = seen.find(sig);
+        if (it == seen.end()) {
+            it = seen.emplace(sig, (int)rep.size()).first;
+            rep.push_back(k);
+        }
+        h.rcls[k] = it->second;
+    }
+    h.ncls = (int)rep.size();
+    const size_t nt = (size_t)h.ncls * nr * nm;
+    h.diag.assign(nt, 0.0);
+    h.invd.assign(nt, 0.0);
+    h.hw.assign(nt, 0.0);
+    h.he.assign(nt, 0.0);
+    h.hz.assign(nt, 0.0);
+    h.d0c.assign((size_t)h.ncls * nr, 0.0);
+    const double w = d.omega > 0 ? d.omega : 1.0;
+    for (int c = 0; c < h.ncls; ++c) {
+        const int k = rep[c];
+        for (int i = 0; i < nr; ++i) {
+            if (!h.act[(size_t)k * nr + i]) continue;
+            double g[4];
+            int dir[4];
+            cell_faces(h, i, k, g, dir);
+            const double d0 = g[0] + g[1] + g[2] + g[3];
+            h.d0c[(size_t)c * nr + i] = d0;
+            for (int m = 0; m < nm; ++m) {
+                const size_t t = ((size_t)c * nr + i) * nm + m;
+                const double dg = d0 + lambda_m(d, m) * h.mu[i];
+                h.diag[t] = dg;
+                h.invd[t] = w / dg;
+                h.hw[t] = dir[0] ? 0.0 : w * h.cw[i] / dg;
+                h.he[t] = dir[1] ? 0.0 : w * h.ce[i] / dg;
+                h.hz[t] = w * h.cz[i] / dg;
+            }
+        }
+    }
+}
+
+// Level-0 active flags [nz][nr] of a composite domain (empty: no patches).
+std::vector<unsigned char> patch_mask(const pic_poisson_desc &d) {
+    std::vector<unsigned char> a;
+    if (d.n_patches == 0) return a;
+    a.assign((size_t)d.nr * d.nz, 0);
+    for (int p = 0; p < d.n_patches; ++p) {
+        const int *x = d.patches + 4 * p;
+        for (int k = x[2]; k < x[3]; ++k)
+            for (int i = x[0]; i < x[1]; ++i) a[(size_t)k * d.nr + i] = 1;
+    }
+    return a;
+}
+
+// Dense factors of a composite domain's coarsest level: the symmetric
+// A_0 (face conductances, no azimuthal term) over the active cells, scaled
+// S = M^(-1/2) A_0 M^(-1/2) with M = diag(mu), and S = Q Lambda Q^T, so
+// that A_m^(-1) = M^(-1/2) Q (Lambda + lambda_m)^(-1) Q^T M^(-1/2) for every
+// mode from one factorisation.
+int dense_factors(const ProblemPlan &q, std::vector<int> &aidx, std::vector<int> &amap, std::vector<double> &Q,
+                  std::vector<double> &QT, std::vector<double> &lam, std::vector<double> &isq,
+                  std::vector<double> &lamm) {
+    const LevelHost &h = q.lv[q.L - 1];
+    const int nr = h.nr, nz = h.nz;
+    amap.assign((size_t)nr * nz, -1);
+    aidx.clear();
+    for (int k = 0; k < nz; ++k)
+        for (int i = 0; i < nr; ++i)
+            if (h.act[(size_t)k * nr + i]) {
+                amap[(size_t)k * nr + i] = (int)aidx.size();
+                aidx.push_back(k * nr + i);
+            }
+    const int n = (int)aidx.size();
+    isq.assign(n, 0.0);
+    for (int a = 0; a < n; ++a) isq[a] = 1.0 / std::sqrt(h.mu[aidx[a] % nr]);
+    std::vector<double> S((size_t)n * n, 0.0);
+    for (int a = 0; a < n; ++a) {
+        const int k = aidx[a] / nr, i = aidx[a] % nr;
+        double g[4];
+        int dir[4];
+        cell_faces(h, i, k, g, dir);
+        S[(size_t)a * n + a] = (g[0] + g[1] + g[2] + g[3]) * isq[a] * isq[a];
+        const int nb[4] = {dir[0] ? -1 : amap[(size_t)k * nr + i - 1], dir[1] ? -1 : amap[(size_t)k * nr + i + 1],
+                           dir[2] ? -1 : amap[(size_t)(k - 1) * nr + i], dir[3] ? -1 : amap[(size_t)(k + 1) * nr + i]};
+        for (int f = 0; f < 4; ++f)
+            if (nb[f] >= 0) S[(size_t)a * n + nb[f]] = -g[f] * isq[a] * isq[nb[f]];
+    }
+    if (!sym_eig(S, n, Q, lam)) {
+        set_error("the coarsest level's dense eigendecomposition did not converge");
+        return PIC_POISSON_EINVAL;
+    }
+    QT.assign((size_t)n * n, 0.0);
+    for (int a = 0; a < n; ++a)
+        for (int j = 0; j < n; ++j) QT[(size_t)j * n + a] = Q[(size_t)a * n + j];
+    lamm.assign(q.nm, 0.0);
+    for (int m = 0; m < q.nm; ++m) lamm[m] = lambda_m(q.d, m);
+    return PIC_POISSON_OK;
+}
+
 // Coarsest-level factors: axial eigenbasis (closed form for the uniform
 // cell-centred Dirichlet operator: V_kj ~ sin(pi (j+1)(k+1/2)/nz), eigenvalue
 // 4 sin^2(pi (j+1) / (2 nz))) and the Thomas factorisation of the radial
@@ -314,11 +499,14 @@ int setup_problem(ProblemPlan &q, const pic_poisson_desc &d) {
     q.uniform_r = !d.r_faces;
     q.rf0 = d.r_faces ? std::vector<double>(d.r_faces, d.r_faces + d.nr + 1) : uniform_faces(d, d.nr);
     q.d.r_faces = q.rf0.data();
+    q.patches.assign(d.patches, d.patches + 4 * d.n_patches);
+    q.d.patches = q.patches.empty() ? nullptr : q.patches.data();
     int nr[PIC_POISSON_MAX_LEVELS], nz[PIC_POISSON_MAX_LEVELS];
     int rc = hierarchy(q.d, nr, nz, &q.L);
     if (rc) return rc;
     q.nm = d.ntheta / 2 + 1;
     q.lv.resize(q.L);
+    const std::vector<unsigned char> act0 = patch_mask(q.d);
     std::vector<double> rf = q.rf0;   // a level halved in r keeps every other face
     for (int l = 0; l < q.L; ++l) {
         if (l > 0 && nr[l] != nr[l - 1]) {
@@ -326,8 +514,19 @@ int setup_problem(ProblemPlan &q, const pic_poisson_desc &d) {
             for (int a = 0; a <= nr[l]; ++a) c[a] = rf[2 * a];
             rf.swap(c);
         }
-        build_level(q.d, rf, nz[l], q.nm, q.lv[l]);
+        LevelHost &h = q.lv[l];
+        build_level(q.d, rf, nz[l], q.nm, h);
+        if (!act0.empty()) {   // protected faces: each coarse cell lies in one patch or none
+            const int sr = d.nr / nr[l], sz = d.nz / nz[l];
+            h.act.assign((size_t)nr[l] * nz[l], 0);
+            for (int k = 0; k < nz[l]; ++k)
+                for (int i = 0; i < nr[l]; ++i) h.act[(size_t)k * nr[l] + i] = act0[(size_t)(k * sz) * d.nr + i * sr];
+            build_masked_tables(q.d, q.nm, h);
+        }
     }
+    q.nact = 0;
+    if (!act0.empty())
+        for (unsigned char a : q.lv[q.L - 1].act) q.nact += a;
     return PIC_POISSON_OK;
 }
 
@@ -350,6 +549,7 @@ template <class T, class V> void carve_level(const LevelHost &h, int nm, int nt,
     v.hw = c.take<T>(ntab);
     v.he = c.take<T>(ntab);
     v.hz = c.take<T>(ntab);
+    v.rcls = h.rcls.empty() ? nullptr : c.take<int>(h.nz);
 }
 
 template <class T> void carve_coarse(const ProblemPlan &q, Carver &c, CoarseDev<T> &cd) {
@@ -358,6 +558,21 @@ template <class T> void carve_coarse(const ProblemPlan &q, Carver &c, CoarseDev<
     cd.nr = h.nr;
     cd.nz = h.nz;
     cd.nm = q.nm;
+    cd.nact = q.nact;
+    if (q.nact > 0) {   // composite domain: dense solve (coarse_factors' tables are not used)
+        const size_t na = (size_t)q.nact;
+        cd.V = cd.e = cd.piv = cd.cpr = nullptr;
+        cd.aidx = c.take<int>(na);
+        cd.amap = c.take<int>((size_t)h.nr * h.nz);
+        cd.Q = c.take<T>(na * na);
+        cd.QT = c.take<T>(na * na);
+        cd.lam = c.take<T>(na);
+        cd.isq = c.take<T>(na);
+        cd.lamm = c.take<T>(q.nm);
+        return;
+    }
+    cd.aidx = cd.amap = nullptr;
+    cd.Q = cd.QT = cd.lam = cd.isq = cd.lamm = nullptr;
     cd.V = c.take<T>((size_t)h.nz * h.nz);
     cd.e = c.take<T>(h.nr);
     cd.piv = c.take<T>(nf);
@@ -418,8 +633,9 @@ void carve(pic_poisson_plan_s &P, Carver &c) {
         q.tw2 = (const double *)c.take<double2>(M + 1);
         q.twf = c.take<float4>(std::max(M / 2, 1));
         q.tw2f = c.take<float4>(M + 1);
-        q.s0 = c.take<double>(q.lv[0].nr);
+        q.s0 = c.take<double>(q.lv[0].act.empty() ? q.lv[0].nr : (size_t)q.lv[0].nr * q.lv[0].nz);
         q.bD0 = c.take<double>((size_t)q.lv[0].nr * q.lv[0].nz);
+        q.mask0 = q.lv[0].act.empty() ? nullptr : c.take<double>((size_t)q.lv[0].nr * q.lv[0].nz);
         q.fwin = c.take<double>(q.lv[0].nz);
         q.fwout = c.take<double>(q.lv[0].nz);
         q.finv_rda = c.take<double>(q.lv[0].nr);
@@ -463,6 +679,12 @@ template <class T> void to_dev(const std::vector<double> &src, const T *dst, cud
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
 }
 
+void ints_to_dev(const std::vector<int> &src, const int *dst, cudaStream_t st, cudaError_t &err) {
+    if (err != cudaSuccess || src.empty() || !dst) return;
+    err = cudaMemcpyAsync((void *)dst, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+}
+
 template <class X> void blob_to_dev(const X &src, X *dst, cudaStream_t st, cudaError_t &err) {
     if (err != cudaSuccess || !dst) return;
     err = cudaMemcpyAsync(dst, &src, sizeof(X), cudaMemcpyHostToDevice, st);
@@ -470,6 +692,7 @@ template <class X> void blob_to_dev(const X &src, X *dst, cudaStream_t st, cudaE
 }
 
 template <class T> void upload_level(const LevelHost &h, const LevelDev<T> &v, cudaStream_t st, cudaError_t &err) {
+    ints_to_dev(h.rcls, v.rcls, st, err);
     to_dev(h.cw, v.cw, st, err);
     to_dev(h.ce, v.ce, st, err);
     to_dev(h.cz, v.cz, st, err);
@@ -643,8 +866,10 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
         tc.f[tc.n] = views(q)[q.L - 1];
         tc.c[tc.n] = cd;
         tc.start[tc.n + 1] = tc.start[tc.n] + 2u * (unsigned)q.nm;   // (mode, real / imaginary part)
-        tc.smem = std::max(tc.smem, ((size_t)cd.nr * cd.nz + (size_t)(cd.nr + 1) * cd.nz +
-                                     (size_t)(cd.nz - cd.nz / 2) * cd.nz) * sizeof(T));
+        const size_t sm = cd.nact > 0 ? 2 * (size_t)cd.nact * sizeof(T)   // dense: y and z
+                                       : ((size_t)cd.nr * cd.nz + (size_t)(cd.nr + 1) * cd.nz +
+                                          (size_t)(cd.nz - cd.nz / 2) * cd.nz) * sizeof(T);
+        tc.smem = std::max(tc.smem, sm);
         ++tc.n;
     }
     H.g_coarse = tc.start[tc.n];
@@ -664,17 +889,32 @@ int upload(pic_poisson_plan_s &P) {
         for (size_t l = 0; l < q.dl.size(); ++l) upload_level(q.lv[l], q.dl[l], st, err);
         for (size_t l = 0; l < q.fl.size(); ++l) upload_level(q.lv[l], q.fl[l], st, err);
         std::vector<double> V, e, piv, cpr;
-        coarse_factors(q, V, e, piv, cpr);
-        if (!mixed) {
-            to_dev(V, q.cd.V, st, err);
-            to_dev(e, q.cd.e, st, err);
-            to_dev(piv, q.cd.piv, st, err);
-            to_dev(cpr, q.cd.cpr, st, err);
+        if (q.nact > 0) {   // composite domain: dense coarsest solve
+            std::vector<int> aidx, amap;
+            std::vector<double> Q, QT, lam, isq, lamm;
+            const int rc = dense_factors(q, aidx, amap, Q, QT, lam, isq, lamm);
+            if (rc) return rc;
+            auto put = [&](auto &cd) {
+                ints_to_dev(aidx, cd.aidx, st, err);
+                ints_to_dev(amap, cd.amap, st, err);
+                to_dev(Q, cd.Q, st, err);
+                to_dev(QT, cd.QT, st, err);
+                to_dev(lam, cd.lam, st, err);
+                to_dev(isq, cd.isq, st, err);
+                to_dev(lamm, cd.lamm, st, err);
+            };
+            if (!mixed) put(q.cd);
+            else put(q.cf);
         } else {
-            to_dev(V, q.cf.V, st, err);
-            to_dev(e, q.cf.e, st, err);
-            to_dev(piv, q.cf.piv, st, err);
-            to_dev(cpr, q.cf.cpr, st, err);
+            coarse_factors(q, V, e, piv, cpr);
+            auto put = [&](auto &cd) {
+                to_dev(V, cd.V, st, err);
+                to_dev(e, cd.e, st, err);
+                to_dev(piv, cd.piv, st, err);
+                to_dev(cpr, cd.cpr, st, err);
+            };
+            if (!mixed) put(q.cd);
+            else put(q.cf);
         }
         const int nt = q.d.ntheta, M = nt / 2;
         std::vector<double> tw(2 * std::max(M / 2, 1), 0.0), tw2(2 * (M + 1), 0.0);
@@ -703,16 +943,39 @@ int upload(pic_poisson_plan_s &P) {
         const LevelHost &h = q.lv[0];
         std::vector<double> s(h.nr), bD((size_t)h.nr * h.nz, 0.0);
         for (int i = 0; i < h.nr; ++i) s[i] = h.rc[i] * h.drc[i] * h.dz / q.d.eps0;
-        for (int k = 0; k < h.nz; ++k)
-            for (int i = 0; i < h.nr; ++i) {
-                double v = 0.0;
-                const double rm = h.rf[i], rp = h.rf[i + 1];
-                if (i == 0) v += rm * h.dz / (h.rc[i] - rm) * wall_rin(q.d, k);
-                if (i == h.nr - 1) v += rp * h.dz / (rp - h.rc[i]) * wall_rout(q.d, k);
-                if (k == 0) v += 2.0 * h.cz[i] * q.d.phi_z0;
-                if (k == h.nz - 1) v += 2.0 * h.cz[i] * q.d.phi_z1;
-                bD[(size_t)k * h.nr + i] = v;
-            }
+        if (h.act.empty()) {
+            for (int k = 0; k < h.nz; ++k)
+                for (int i = 0; i < h.nr; ++i) {
+                    double v = 0.0;
+                    const double rm = h.rf[i], rp = h.rf[i + 1];
+                    if (i == 0) v += rm * h.dz / (h.rc[i] - rm) * wall_rin(q.d, k);
+                    if (i == h.nr - 1) v += rp * h.dz / (rp - h.rc[i]) * wall_rout(q.d, k);
+                    if (k == 0) v += 2.0 * h.cz[i] * q.d.phi_z0;
+                    if (k == h.nz - 1) v += 2.0 * h.cz[i] * q.d.phi_z1;
+                    bD[(size_t)k * h.nr + i] = v;
+                }
+        } else {
+            // composite domain: s per cell (zero outside the patches, so their charge is ignored);
+            // a Dirichlet face takes its wall's potential on the grid boundary, phi_exposed inside
+            std::vector<double> s2((size_t)h.nr * h.nz, 0.0);
+            for (int k = 0; k < h.nz; ++k)
+                for (int i = 0; i < h.nr; ++i) {
+                    if (!h.act[(size_t)k * h.nr + i]) continue;
+                    s2[(size_t)k * h.nr + i] = s[i];
+                    double g[4];
+                    int dir[4];
+                    cell_faces(h, i, k, g, dir);
+                    const double pe = q.d.phi_exposed;
+                    double v = 0.0;
+                    if (dir[0]) v += g[0] * (i == 0 ? wall_rin(q.d, k) : pe);
+                    if (dir[1]) v += g[1] * (i == h.nr - 1 ? wall_rout(q.d, k) : pe);
+                    if (dir[2]) v += g[2] * (k == 0 ? q.d.phi_z0 : pe);
+                    if (dir[3]) v += g[3] * (k == h.nz - 1 ? q.d.phi_z1 : pe);
+                    bD[(size_t)k * h.nr + i] = v;
+                }
+            s.swap(s2);
+            to_dev(std::vector<double>(h.act.begin(), h.act.end()), q.mask0, st, err);
+        }
         to_dev(s, q.s0, st, err);
         to_dev(bD, q.bD0, st, err);
         // face-field reconstruction: wall potentials and the azimuthal arcs
@@ -776,11 +1039,17 @@ int upload(pic_poisson_plan_s &P) {
         fp.half_inv_n = 0.5 / q.d.ntheta;
         FFTProb f = fp, g = fp, iv = fp;
         f.s = q.s0;
+        f.s_rows = q.lv[0].act.empty() ? 0 : 1;
+        f.rcls = d0.rcls;
         f.bD = q.bD0;
         f.invd = mixed ? nullptr : d0.invd;
         f.b = d0.b;
         f.bh = mixed ? nullptr : d0.bh;
         g.b = d0.u;                         // initial guess: plain 1/N transform of phi into u
+        if (q.mask0) {                      // (composite domain: held at 0 outside the patches)
+            g.s = q.mask0;
+            g.s_rows = 1;
+        }
         iv.uhat = d0.u;
         const unsigned blocks = (unsigned)(d0.nz * ((d0.nr + FFT_TI - 1) / FFT_TI));
         F.p[p] = f;
@@ -935,7 +1204,7 @@ int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
     // mode-local bottom where the two coarsest levels fit in one block's shared memory
     for (ProblemPlan &q : P.pr) {
         q.bottom = false;
-        if (P.shared.local_bottom != 0 || P.shared.omega != 1.0 || q.L < 3) continue;
+        if (P.shared.local_bottom != 0 || P.shared.omega != 1.0 || q.L < 3 || q.nact > 0) continue;
         const LevelHost &U = q.lv[q.L - 2], &C = q.lv[q.L - 1];
         if (U.nr % 2) continue;
         const size_t smem = P.shared.precision == PIC_POISSON_MIXED
@@ -998,6 +1267,26 @@ int pic_poisson_cell_coeffs(const pic_poisson_desc *desc, int i, int k, double *
     LevelHost h;
     build_level(d, d.r_faces ? std::vector<double>(d.r_faces, d.r_faces + d.nr + 1) : uniform_faces(d, d.nr), d.nz, 1,
                 h);
+    if (d.n_patches > 0) {   // composite domain: exposed faces are Dirichlet faces at phi_exposed
+        h.act = patch_mask(d);
+        for (int a = 0; a < 12; ++a) out[a] = 0.0;
+        if (!h.act[(size_t)k * d.nr + i]) return PIC_POISSON_OK;   // not an unknown
+        double g[4];
+        int dir[4];
+        cell_faces(h, i, k, g, dir);
+        const double wall[4] = {i == 0 ? (d.phi_r_in_z ? d.phi_r_in_z[k] : d.phi_r_in) : d.phi_exposed,
+                                i == d.nr - 1 ? (d.phi_r_out_z ? d.phi_r_out_z[k] : d.phi_r_out) : d.phi_exposed,
+                                k == 0 ? d.phi_z0 : d.phi_exposed, k == d.nz - 1 ? d.phi_z1 : d.phi_exposed};
+        for (int f = 0; f < 4; ++f) {
+            out[f] = g[f];
+            out[4 + f] = dir[f];
+            out[10] += g[f];
+            if (dir[f]) out[11] += g[f] * wall[f];
+        }
+        out[8] = h.mu[i];
+        out[9] = h.rc[i] * h.drc[i] * h.dz / d.eps0;
+        return PIC_POISSON_OK;
+    }
     const bool dw = i == 0, de = i == d.nr - 1, ds = k == 0, dn = k == d.nz - 1;
     const double rm = h.rf[i], rp = h.rf[i + 1];
     out[0] = dw ? rm * h.dz / (h.rc[i] - rm) : h.cw[i];

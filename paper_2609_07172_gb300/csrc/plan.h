@@ -10,6 +10,8 @@ struct ProblemPlan {
     pic_poisson_desc d{};                       // resolved descriptor (wall arrays point below)
     std::vector<double> rin_z, rout_z;
     std::vector<double> rf0;                    // level-0 radial faces (given or uniform)
+    std::vector<int> patches;                   // composite domain: 4 ints per patch (empty: the annulus)
+    int nact = 0;                               // composite domain: active cells of the coarsest level
     bool uniform_r = true;
     int L = 0, nm = 0;
     std::vector<LevelHost> lv;
@@ -23,6 +25,7 @@ struct ProblemPlan {
     bool bottom = false;                        // levels L-2 and L-1 solved by k_bottom
     int smoothed() const { return L - 1 - (bottom ? 1 : 0); }   // levels 0 .. smoothed()-1 use the level kernels
     double *s0 = nullptr, *bD0 = nullptr;       // level-0 right-hand-side factors
+    double *mask0 = nullptr;                    // composite domain: 1 on active cells, 0 elsewhere [nz][nr]
     double *fwin = nullptr, *fwout = nullptr;   // face-field reconstruction: r-wall potentials [nz]
     double *finv_rda = nullptr;                 // and 1 / (r_i dalpha) [nr]
     double *finv_rd = nullptr;                  // and 1 / radial face distances [nr + 1]

@@ -80,6 +80,8 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
     repeats = std::max(1, std::min(repeats, 16));
     memset(out, 0, sizeof *out);
     const bool mixed = descs[0].precision == PIC_POISSON_MIXED;
+    bool composite = false;   // the fused smoother does not take composite domains
+    for (int p = 0; p < n; ++p) composite = composite || descs[p].n_patches > 0;
     static const int sched[][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 2}, {2, 3}, {3, 3}};
     std::vector<Cand> cands;
     for (const auto &s : sched) {
@@ -137,7 +139,7 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
             const int rc = record(c);
             if (rc == PIC_POISSON_ENOMEM || rc == PIC_POISSON_ECUDA || rc == PIC_POISSON_EINVAL) return rc;
         }
-    if (mixed)
+    if (mixed && !composite)
         for (const auto &s : sor_sched)
             for (int inner = 1; inner <= 6; ++inner) {
                 Cand c{s[0], s[1], inner, base.threads, base.strip, 1.0, 1, 0, 0.0};
