@@ -124,9 +124,16 @@ def test_autotune_picks_a_working_schedule(precision, tmp_path):
     cache = str(tmp_path / "tune.json")
     best = autotune([p], [rho], tol=1e-10, precision=precision, graph=True, repeats=1, cache=cache)
     n_sched = 7 * (4 if precision == MIXED else 1)
-    # + block sizes, strips 2, 4, 3 omegas x 4 schedules, and the fused smoother x 4 schedules x 6 (mixed)
-    # or the full-multigrid start x 3 schedules (FP64)
-    assert len(best["tried"]) == n_sched + 5 + 12 + (24 if precision == MIXED else 3)
+    # + block sizes, strips 2, 4, 3 omegas x 4 schedules, and the fused smoother x 4 schedules x 6 and
+    # 1 to 3 extra first-correction cycles at the best and one fewer inner cycles (mixed), or the
+    # full-multigrid start x 3 schedules (FP64)
+    base = n_sched + 5 + 12 + (24 if precision == MIXED else 3)
+    if precision == MIXED:
+        assert len(best["tried"]) in (base + 3, base + 6)
+        assert sum(t["first"] > t["inner"] for t in best["tried"]) == len(best["tried"]) - base
+        assert best["inner_first"] >= best["inner_cycles"]
+    else:
+        assert len(best["tried"]) == base
     assert best["smooth_threads"] in (64, 128, 256, 512)
     assert best["smooth_strip"] in (0, 2, 4)
     assert best["omega"] in (1.0, 1.1, 1.2, 1.3)

@@ -140,3 +140,18 @@ def test_composite_plan_refuses_field_deposit_and_fused():
             plan.deposit(pos, pos, pos * 0.1, weight=1.0)
     with pytest.raises(B.PicPoissonError):
         Plan(p, precision=MIXED, smooth_fused=1)
+
+
+def test_autotune_on_a_composite_domain(tmp_path):
+    """The tuner leaves out the fused smoother (it does not take patches) and
+    still returns a working schedule."""
+    from paper_2609_07172_gb300 import autotune
+    p = W.channel_plume(64, 16, 48)
+    rho = dev(W.rho_plasma(p, seed=55))
+    best = autotune([p], [rho], tol=1e-10, precision=MIXED, graph=True, repeats=1)
+    assert not any(t["fused"] for t in best["tried"])
+    kw = {k: best[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads", "smooth_strip",
+                               "omega", "inner_first")}
+    with Plan(p, precision=MIXED, graph=True, **kw) as plan:
+        phi, info = plan.solve(rho, tol=1e-10)
+    assert info["status"] == B.OK and info["rel_res"] <= 1e-10
