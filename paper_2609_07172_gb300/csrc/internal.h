@@ -217,26 +217,31 @@ cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, int
 // Per problem, f.init selects what is written into the coarse level c: 0 = b only
 // (coarsest, solved directly); 1 = also b_hat and u = 0; 2 = also b_hat and
 // u = (red ? b_hat : 0), the first red half-sweep from zero.
+// masked: the plan holds a composite domain (class tables per row, no
+// residual or correction outside the patches); false runs the plain kernels.
 template <class T>
 cudaError_t launch_residual_restrict(const LaunchTab<T> *tab, unsigned grid, bool red_only, double *partials,
-                                     cudaStream_t st);
+                                     cudaStream_t st, bool masked = false);
 // r = b - A_m u on level f of every problem (r_out: optional per-problem output
 // in c[p].u), Parseval-weighted norms of r and b into partials[block] and
 // partials[partial_stride + block].
 template <class T>
 cudaError_t launch_residual(const LaunchTab<T> *tab, unsigned grid, bool write_r, double *partials,
-                            unsigned partial_stride, cudaStream_t st);
+                            unsigned partial_stride, cudaStream_t st, bool masked = false);
 template <class T>
-cudaError_t launch_prolong(const LaunchTab<T> *tab, unsigned grid, bool black_only, cudaStream_t st);
+cudaError_t launch_prolong(const LaunchTab<T> *tab, unsigned grid, bool black_only, cudaStream_t st,
+                           bool masked = false);
 template <class T>
 cudaError_t launch_coarse(const CoarseTab<T> *tab, unsigned grid, size_t smem, cudaStream_t st);
 // Full-multigrid start: u_f = P u_c on every fine cell; coarse b = restricted fine b.
-template <class T> cudaError_t launch_interp(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st);
-template <class T> cudaError_t launch_rhs_restrict(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st);
+template <class T>
+cudaError_t launch_interp(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st, bool masked = false);
+template <class T>
+cudaError_t launch_rhs_restrict(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st, bool masked = false);
 
 // zero_x: the FP64 iterate is zero (r = b; the kernel also writes x = 0).
 cudaError_t launch_defect(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, double *partials, bool zero_x,
-                          cudaStream_t st);
+                          cudaStream_t st, bool masked = false);
 cudaError_t launch_update(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, cudaStream_t st);
 
 // Sums of the forward transform's partials per problem -> ctrl->bnorm2; initial

@@ -94,7 +94,7 @@ __device__ __forceinline__ void colour_cell(unsigned c, int nr, int color, int &
 }
 
 // b - A_m u at entry (k, i, m), Eq. matrix_free_mode_operator.
-template <class T>
+template <class T, bool MASK>
 __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i, int m, size_t idx) {
     const size_t rowstride = (size_t)L.nr * L.nm;
     V2<T> s = mk<T>(0, 0);
@@ -106,10 +106,15 @@ __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i,
     V2<T> acc = fma2<T>(L.cz[i], s, L.b[idx]);
     if (i > 0) acc = fma2<T>(L.cw[i], L.u[idx - L.nm], acc);
     if (i < L.nr - 1) acc = fma2<T>(L.ce[i], L.u[idx + L.nm], acc);
-    const T d = L.diag[((size_t)lclass(L, k) * L.nr + i) * L.nm + m];
-    const V2<T> r = fma2<T>(-d, L.u[idx], acc);
-    // a cell outside a composite domain's patches (zero diagonal) has no residual
-    return (L.rcls && d == T(0)) ? mk<T>(0, 0) : r;
+    if constexpr (MASK) {
+        const T d = L.diag[((size_t)lclass(L, k) * L.nr + i) * L.nm + m];
+        const V2<T> r = fma2<T>(-d, L.u[idx], acc);
+        // a cell outside a composite domain's patches (zero diagonal) has no residual
+        return d == T(0) ? mk<T>(0, 0) : r;
+    } else {
+        const T d = L.diag[((size_t)row_class(k, L.nz, L.ncls) * L.nr + i) * L.nm + m];
+        return fma2<T>(-d, L.u[idx], acc);
+    }
 }
 
 // One red-black Gauss-Seidel half-sweep over the cells of one colour:
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
 // with optional Parseval-weighted squared-norm partials.  RED_ONLY: only the
 // two red fine cells (after a black half-sweep the black residuals vanish).
 // F.init selects what else the coarse level receives (see internal.h).
-template <class T, bool RED_ONLY>
+template <class T, bool RED_ONLY, bool MASK>
 __global__ void __launch_bounds__(MG_THREADS)
 k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ partials) {
     __shared__ double red[MG_THREADS];
@@ -251,11 +256,11 @@ k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ p
         };
         int k, i;
         cell(0, k, i);
-        V2<T> sum = residual_at(F, k, i, m, ((size_t)k * F.nr + i) * nm + m);
+        V2<T> sum = residual_at<T, MASK>(F, k, i, m, ((size_t)k * F.nr + i) * nm + m);
         if (partials) acc = fma((double)sum.y, (double)sum.y, (double)sum.x * (double)sum.x);
         auto more = [&](int c) {
             cell(c, k, i);
-            const V2<T> r = residual_at(F, k, i, m, ((size_t)k * F.nr + i) * nm + m);
+            const V2<T> r = residual_at<T, MASK>(F, k, i, m, ((size_t)k * F.nr + i) * nm + m);
             sum = mk<T>(sum.x + r.x, sum.y + r.y);
             if (partials) acc = fma((double)r.y, (double)r.y, fma((double)r.x, (double)r.x, acc));
         };
@@ -271,7 +276,7 @@ k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ p
         }
         C.b[e] = sum;
         if (F.init > 0) {
-            const T inv = C.invd[((size_t)lclass(C, K) * C.nr + I) * nm + m];
+            const T inv = C.invd[((size_t)(MASK ? lclass(C, K) : row_class(K, C.nz, C.ncls)) * C.nr + I) * nm + m];
             const V2<T> bh = mk<T>(sum.x * inv, sum.y * inv);
             C.bh[e] = bh;
             C.u[e] = (F.init == 2 && ((K + I) & 1) == 0) ? bh : mk<T>(0, 0);
@@ -287,7 +292,7 @@ k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ p
 // r = b - A_m u on level f (r written to c.u when write_r), Parseval-weighted
 // squared norms of r into partials[block] and, when stride > 0, of b into
 // partials[stride + block].
-template <class T>
+template <class T, bool MASK>
 __global__ void __launch_bounds__(MG_THREADS)
 k_residual(const LaunchTab<T> *__restrict__ tab, int write_r, double *__restrict__ partials, unsigned stride) {
     __shared__ double red[MG_THREADS];
@@ -302,7 +307,7 @@ k_residual(const LaunchTab<T> *__restrict__ tab, int write_r, double *__restrict
         const int m = (int)(e - c * nm);
         const int k = (int)(c / (unsigned)L.nr);
         const int i = (int)(c - (unsigned)k * L.nr);
-        const V2<T> r = residual_at(L, k, i, m, e);
+        const V2<T> r = residual_at<T, MASK>(L, k, i, m, e);
         if (write_r) tab->c[p].u[e] = r;
         const V2<T> b = L.b[e];
         const double w = parseval_w(m, L.nt);
@@ -326,7 +331,7 @@ k_residual(const LaunchTab<T> *__restrict__ tab, int write_r, double *__restrict
 // value is reflected with a sign change (the correction vanishes on the
 // Dirichlet face).  BLACK_ONLY: only black fine cells (the red half-sweep that
 // follows overwrites the red ones).
-template <class T, bool BLACK_ONLY, bool ASSIGN = false>
+template <class T, bool BLACK_ONLY, bool ASSIGN, bool MASK>
 __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__restrict__ tab) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
     }
     const size_t idx = ((size_t)k * F.nr + i) * nm + m;
     // composite domain: a cell outside the patches keeps u = 0
-    if (F.rcls && F.diag[((size_t)F.rcls[k] * F.nr + i) * nm + m] == T(0)) {
+    if (MASK && F.diag[((size_t)F.rcls[k] * F.nr + i) * nm + m] == T(0)) {
         if (ASSIGN) F.u[idx] = mk<T>(0, 0);
         return;
     }
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
     const int I2 = I + ((i & 1) ? 1 : -1);
     bool kin = K2 >= 0 && K2 < C.nz;
     bool iin = I2 >= 0 && I2 < C.nr;
-    if (C.rcls) {   // an exposed face reflects like a wall: the correction vanishes on it
+    if (MASK) {   // an exposed face reflects like a wall: the correction vanishes on it
         if (iin) iin = C.diag[((size_t)C.rcls[K] * C.nr + I2) * nm + m] != T(0);
         if (kin) kin = C.diag[((size_t)C.rcls[K2] * C.nr + I) * nm + m] != T(0);
     }
@@ -386,8 +391,9 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
 // Full-multigrid start: the right-hand side restricted to the next coarser
 // level (the finite-volume sum of b over the fine cells of each coarse cell,
 // the restriction the residuals get), b_hat = b / diag, and a zero iterate.
-template <class T>
+template <class T, bool MASK>
 __global__ void __launch_bounds__(MG_THREADS) k_rhs_restrict(const LaunchTab<T> *__restrict__ tab) {
+    // (MASK: the class tables of a composite domain's rows)
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
     const LevelDev<T> F = tab->f[p];
@@ -407,7 +413,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_rhs_restrict(const LaunchTab<T> 
         sum = mk<T>(sum.x + b.x, sum.y + b.y);
     }
     C.b[e] = sum;
-    const T inv = C.invd[((size_t)lclass(C, K) * C.nr + I) * nm + m];
+    const T inv = C.invd[((size_t)(MASK ? lclass(C, K) : row_class(K, C.nz, C.ncls)) * C.nr + I) * nm + m];
     C.bh[e] = mk<T>(sum.x * inv, sum.y * inv);
     C.u[e] = mk<T>(0, 0);
 }
@@ -458,7 +464,7 @@ __device__ __forceinline__ int pow2_exponent(double v) { return ((__double2hiint
 // ZERO_X: the iterate is zero (first defect of a solve from a zero initial
 // guess), so r = b and the kernel also writes x = 0 -- a memory pass, no FP64
 // stencil.
-template <bool ZERO_X>
+template <bool ZERO_X, bool MASK>
 __global__ void __launch_bounds__(MG_THREADS, 6)   // 48 warps per SM for the FP64 pipe (measured best)
 k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, double *__restrict__ partials) {
     __shared__ double red[MG_THREADS];
@@ -481,12 +487,12 @@ k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, doubl
             r = D.b[e];
             D.u[e] = make_double2(0.0, 0.0);
         } else {
-            r = residual_at(D, k, i, m, e);
+            r = residual_at<double, MASK>(D, k, i, m, e);
         }
         const float2 b32 = make_float2(f64_to_f32_pow2(r.x, ls), f64_to_f32_pow2(r.y, ls));
         const float w = (m == 0 || 2 * m == D.nt) ? 1.f : 2.f;
         acc = f32_to_f64_pow2(w * fmaf(b32.x, b32.x, b32.y * b32.y), 0);
-        const float inv = S.invd[((size_t)lclass(S, k) * S.nr + i) * nm + m];
+        const float inv = S.invd[((size_t)(MASK ? lclass(S, k) : row_class(k, S.nz, S.ncls)) * S.nr + i) * nm + m];
         const float2 bh = make_float2(b32.x * inv, b32.y * inv);
         S.b[e] = b32;
         S.bh[e] = bh;
@@ -806,33 +812,48 @@ cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, int
 
 template <class T>
 cudaError_t launch_residual_restrict(const LaunchTab<T> *tab, unsigned grid, bool red_only, double *partials,
-                                     cudaStream_t st) {
-    if (red_only) k_residual_restrict<T, true><<<grid, MG_THREADS, 0, st>>>(tab, partials);
-    else k_residual_restrict<T, false><<<grid, MG_THREADS, 0, st>>>(tab, partials);
+                                     cudaStream_t st, bool masked) {
+    if (masked) {
+        if (red_only) k_residual_restrict<T, true, true><<<grid, MG_THREADS, 0, st>>>(tab, partials);
+        else k_residual_restrict<T, false, true><<<grid, MG_THREADS, 0, st>>>(tab, partials);
+    } else {
+        if (red_only) k_residual_restrict<T, true, false><<<grid, MG_THREADS, 0, st>>>(tab, partials);
+        else k_residual_restrict<T, false, false><<<grid, MG_THREADS, 0, st>>>(tab, partials);
+    }
     return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_residual(const LaunchTab<T> *tab, unsigned grid, bool write_r, double *partials,
-                            unsigned partial_stride, cudaStream_t st) {
-    k_residual<T><<<grid, MG_THREADS, 0, st>>>(tab, write_r ? 1 : 0, partials, partial_stride);
+                            unsigned partial_stride, cudaStream_t st, bool masked) {
+    if (masked) k_residual<T, true><<<grid, MG_THREADS, 0, st>>>(tab, write_r ? 1 : 0, partials, partial_stride);
+    else k_residual<T, false><<<grid, MG_THREADS, 0, st>>>(tab, write_r ? 1 : 0, partials, partial_stride);
     return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_prolong(const LaunchTab<T> *tab, unsigned grid, bool black_only, cudaStream_t st) {
-    if (black_only) k_prolong<T, true><<<grid, MG_THREADS, 0, st>>>(tab);
-    else k_prolong<T, false><<<grid, MG_THREADS, 0, st>>>(tab);
+cudaError_t launch_prolong(const LaunchTab<T> *tab, unsigned grid, bool black_only, cudaStream_t st, bool masked) {
+    if (masked) {
+        if (black_only) k_prolong<T, true, false, true><<<grid, MG_THREADS, 0, st>>>(tab);
+        else k_prolong<T, false, false, true><<<grid, MG_THREADS, 0, st>>>(tab);
+    } else {
+        if (black_only) k_prolong<T, true, false, false><<<grid, MG_THREADS, 0, st>>>(tab);
+        else k_prolong<T, false, false, false><<<grid, MG_THREADS, 0, st>>>(tab);
+    }
     return cudaGetLastError();
 }
 
-template <class T> cudaError_t launch_interp(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st) {
-    k_prolong<T, false, true><<<grid, MG_THREADS, 0, st>>>(tab);
+template <class T>
+cudaError_t launch_interp(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st, bool masked) {
+    if (masked) k_prolong<T, false, true, true><<<grid, MG_THREADS, 0, st>>>(tab);
+    else k_prolong<T, false, true, false><<<grid, MG_THREADS, 0, st>>>(tab);
     return cudaGetLastError();
 }
 
-template <class T> cudaError_t launch_rhs_restrict(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st) {
-    k_rhs_restrict<T><<<grid, MG_THREADS, 0, st>>>(tab);
+template <class T>
+cudaError_t launch_rhs_restrict(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st, bool masked) {
+    if (masked) k_rhs_restrict<T, true><<<grid, MG_THREADS, 0, st>>>(tab);
+    else k_rhs_restrict<T, false><<<grid, MG_THREADS, 0, st>>>(tab);
     return cudaGetLastError();
 }
 
@@ -845,9 +866,14 @@ cudaError_t launch_coarse(const CoarseTab<T> *tab, unsigned grid, size_t smem, c
 }
 
 cudaError_t launch_defect(const DefectTab *tab, unsigned grid, const Ctrl *ctrl, double *partials, bool zero_x,
-                          cudaStream_t st) {
-    if (zero_x) k_defect<true><<<grid, MG_THREADS, 0, st>>>(tab, ctrl, partials);
-    else k_defect<false><<<grid, MG_THREADS, 0, st>>>(tab, ctrl, partials);
+                          cudaStream_t st, bool masked) {
+    if (masked) {
+        if (zero_x) k_defect<true, true><<<grid, MG_THREADS, 0, st>>>(tab, ctrl, partials);
+        else k_defect<false, true><<<grid, MG_THREADS, 0, st>>>(tab, ctrl, partials);
+    } else {
+        if (zero_x) k_defect<true, false><<<grid, MG_THREADS, 0, st>>>(tab, ctrl, partials);
+        else k_defect<false, false><<<grid, MG_THREADS, 0, st>>>(tab, ctrl, partials);
+    }
     return cudaGetLastError();
 }
 
@@ -880,12 +906,12 @@ cudaError_t launch_sum(const double *partials, int n, double *out, cudaStream_t 
 #define PP_INST(T)                                                                                         \
     template cudaError_t launch_smooth<T>(const LaunchTab<T> *, unsigned, int, int, int, bool, cudaStream_t); \
     template cudaError_t launch_residual_restrict<T>(const LaunchTab<T> *, unsigned, bool, double *,       \
-                                                     cudaStream_t);                                        \
+                                                     cudaStream_t, bool);                                  \
     template cudaError_t launch_residual<T>(const LaunchTab<T> *, unsigned, bool, double *, unsigned,      \
-                                            cudaStream_t);                                                 \
-    template cudaError_t launch_prolong<T>(const LaunchTab<T> *, unsigned, bool, cudaStream_t);            \
-    template cudaError_t launch_interp<T>(const LaunchTab<T> *, unsigned, cudaStream_t);                   \
-    template cudaError_t launch_rhs_restrict<T>(const LaunchTab<T> *, unsigned, cudaStream_t);             \
+                                            cudaStream_t, bool);                                           \
+    template cudaError_t launch_prolong<T>(const LaunchTab<T> *, unsigned, bool, cudaStream_t, bool);      \
+    template cudaError_t launch_interp<T>(const LaunchTab<T> *, unsigned, cudaStream_t, bool);             \
+    template cudaError_t launch_rhs_restrict<T>(const LaunchTab<T> *, unsigned, cudaStream_t, bool);       \
     template cudaError_t launch_coarse<T>(const CoarseTab<T> *, unsigned, size_t, cudaStream_t);
 PP_INST(double)
 PP_INST(float)

@@ -1201,6 +1201,8 @@ int setup_plan(pic_poisson_plan_s &P, const pic_poisson_desc *descs, int n) {
         }
         P.h32.fused = true;
     }
+    P.masked = false;
+    for (const ProblemPlan &q : P.pr) P.masked = P.masked || q.nact > 0;
     // mode-local bottom where the two coarsest levels fit in one block's shared memory
     for (ProblemPlan &q : P.pr) {
         q.bottom = false;

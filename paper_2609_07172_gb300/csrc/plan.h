@@ -112,6 +112,7 @@ struct pic_poisson_plan_s {
     const double *last_rho[pp::kMaxBatch] = {};
     double *last_phi[pp::kMaxBatch] = {};
     bool io_valid = false;
+    bool masked = false;                        // some problem is a composite domain (masked kernel variants)
 };
 
 namespace pp {

@@ -159,7 +159,7 @@ int restrict_level(Runner &R, const Hier<T> &H, int l, double *partials) {
     // after a Gauss-Seidel black half-sweep the black residuals vanish; an
     // over-relaxed one leaves them nonzero, so then every cell is evaluated
     const bool red_only = R.P.shared.pre_sweeps > 0 && R.P.shared.omega == 1.0;
-    RUN(R, PIC_POISSON_PHASE_RESTRICT, launch_residual_restrict(H.restr[l], H.g_restr[l], red_only, partials, R.st));
+    RUN(R, PIC_POISSON_PHASE_RESTRICT, launch_residual_restrict(H.restr[l], H.g_restr[l], red_only, partials, R.st, R.P.masked));
     const double n = level_entries<T>(R.P, l), frac = red_only ? 0.5 : 1.0;
     R.account(PIC_POISSON_PHASE_RESTRICT, n * sizeof(V2<T>) * (1.0 + frac + 0.75),
               frac * n * (partials ? 22.0 : 18.0) + n);
@@ -214,7 +214,7 @@ int descend_ascend(Runner &R, const Hier<T> &H, int lend = 0) {
         // the red half-sweep that follows overwrites the red cells unread
         // (Gauss-Seidel only: an over-relaxed update reads the old value)
         const bool black_only = post > 0 && P.shared.omega == 1.0;
-        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_prolong(H.prolong[l], H.g_prolong[l], black_only, R.st));
+        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_prolong(H.prolong[l], H.g_prolong[l], black_only, R.st, R.P.masked));
         const double n = level_entries<T>(P, l), frac = black_only ? 0.5 : 1.0;
         R.account(PIC_POISSON_PHASE_PROLONG, n * sizeof(V2<T>) * (0.25 + 2.0 * frac), 16.0 * frac * n);
         int rc = smooth_level(R, H, l, post, false, true);
@@ -232,7 +232,7 @@ int fp64_residual_and_check(Runner &R, int counting) {
     }
     if (P.g_res_single) {
         RUN(R, PIC_POISSON_PHASE_RESTRICT,
-            launch_residual(P.res_single, P.g_res_single, false, P.partials + P.res_single_offset, 0u, R.st));
+            launch_residual(P.res_single, P.g_res_single, false, P.partials + P.res_single_offset, 0u, R.st, P.masked));
         const double n = level0_entries(P, 1);
         R.account(PIC_POISSON_PHASE_RESTRICT, 2.0 * n * sizeof(double2), 22.0 * n);
     }
@@ -249,7 +249,7 @@ bool larger_first(const pic_poisson_plan_s &P) {
 
 int mixed_defect_and_check(Runner &R, int counting, bool zero_x = false) {
     pic_poisson_plan_s &P = R.P;
-    RUN(R, PIC_POISSON_PHASE_DEFECT, launch_defect(P.defect, P.g_defect, P.ctrl, P.partials, zero_x, R.st));
+    RUN(R, PIC_POISSON_PHASE_DEFECT, launch_defect(P.defect, P.g_defect, P.ctrl, P.partials, zero_x, R.st, P.masked));
     const double n = level0_entries(P, 0);
     R.account(PIC_POISSON_PHASE_DEFECT, n * (2.0 * sizeof(double2) + 3.0 * sizeof(float2)), (zero_x ? 6.0 : 26.0) * n);
     RUN(R, PIC_POISSON_PHASE_NORM, launch_psum(P.psum, P.g_psum, P.partials, P.partials2, R.st));
@@ -273,7 +273,7 @@ int fmg_start(Runner &R) {
     const int nl = P.Lmax - 1, pre = P.shared.pre_sweeps;
     for (int l = 0; l < nl; ++l) {
         if (!H.g_rhs[l]) continue;
-        RUN(R, PIC_POISSON_PHASE_RESTRICT, launch_rhs_restrict(H.rhs[l], H.g_rhs[l], R.st));
+        RUN(R, PIC_POISSON_PHASE_RESTRICT, launch_rhs_restrict(H.rhs[l], H.g_rhs[l], R.st, R.P.masked));
         const double n = level_entries<double>(P, l);
         R.account(PIC_POISSON_PHASE_RESTRICT, n * sizeof(double2) * (1.0 + 0.75), 0.5 * n);
     }
@@ -281,7 +281,7 @@ int fmg_start(Runner &R) {
     if (rc) return rc;
     for (int l = nl - 1; l >= 0; --l) {
         if (!H.g_interp[l]) continue;
-        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_interp(H.interp[l], H.g_interp[l], R.st));
+        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_interp(H.interp[l], H.g_interp[l], R.st, R.P.masked));
         const double n = level_entries<double>(P, l);
         R.account(PIC_POISSON_PHASE_PROLONG, n * sizeof(double2) * 1.25, 16.0 * n);
         if (l == 0) break;   // the main iteration takes over on level 0
@@ -793,7 +793,7 @@ int pic_poisson_mode_residual(pic_poisson_plan_t plan, const double *uhat_dev, c
     t.c[0].u = (double2 *)rhat_dev;
     PP_CUDA(cudaMemcpyAsync(P.api_res, &t, sizeof t, cudaMemcpyHostToDevice, P.stream));
     const unsigned g = P.g_api_res;
-    PP_CUDA(launch_residual(P.api_res, g, rhat_dev != nullptr, rel_res ? P.partials : nullptr, g, P.stream));
+    PP_CUDA(launch_residual(P.api_res, g, rhat_dev != nullptr, rel_res ? P.partials : nullptr, g, P.stream, P.masked));
     if (rel_res) {
         PP_CUDA(launch_sum(P.partials, (int)g, P.dsum, P.stream));
         PP_CUDA(launch_sum(P.partials + g, (int)g, P.dsum + 1, P.stream));
