@@ -289,7 +289,9 @@ int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const double *con
 /*
  * As pic_poisson_solve, starting from the mode-layout iterate uhat_guess_dev
  * (e.g. a previous solution from pic_poisson_get_modes, or a learned guess)
- * instead of zero or the transform of phi.  Single-problem plans.
+ * instead of zero or the transform of phi.  Single-problem plans.  In a
+ * composite domain the guess must be zero outside the patches (as the modes
+ * of a previous solve are).
  */
 int pic_poisson_solve_modes(pic_poisson_plan_t plan, const double *rho_dev, const double *uhat_guess_dev,
                             double *phi_dev, double tol, pic_poisson_info *info);
