@@ -138,7 +138,8 @@ def grid_from_problem(p) -> Grid:
     """Build the oracle's own uniform face arrays from a workloads.Problem."""
     rf = getattr(p, "r_faces", None)
     r_faces = np.asarray(rf, dtype=np.float64) if rf is not None else p.r_in + (p.r_out - p.r_in) * np.arange(p.nr + 1) / p.nr
-    z_faces = p.z0 + (p.z1 - p.z0) * np.arange(p.nz + 1) / p.nz
+    zf = getattr(p, "z_faces", None)
+    z_faces = np.asarray(zf, dtype=np.float64) if zf is not None else p.z0 + (p.z1 - p.z0) * np.arange(p.nz + 1) / p.nz
     rin = np.asarray(p.phi_r_in_z) if p.phi_r_in_z is not None else p.phi_r_in
     rout = np.asarray(p.phi_r_out_z) if p.phi_r_out_z is not None else p.phi_r_out
     active = None

@@ -60,6 +60,7 @@ class Problem:
     phi_r_in_z: tuple | None = field(default=None, compare=False)
     phi_r_out_z: tuple | None = field(default=None, compare=False)
     r_faces: tuple | None = field(default=None, compare=False)   # nr + 1 radial faces; None: uniform
+    z_faces: tuple | None = field(default=None, compare=False)   # nz + 1 axial faces; None: uniform
     # composite domain (Sec. 2.2): active cells are the union of patches (i0, i1, k0, k1), cells
     # i0 <= i < i1, k0 <= k < k1; None: the whole annulus.  Exposed patch faces are at phi_exposed.
     patches: tuple | None = field(default=None, compare=False)
@@ -81,6 +82,9 @@ class Problem:
         return self.r_in + (np.arange(self.nr) + 0.5) * dr
 
     def z_centres(self):
+        if self.z_faces is not None:
+            f = np.asarray(self.z_faces, dtype=np.float64)
+            return 0.5 * (f[:-1] + f[1:])
         dz = (self.z1 - self.z0) / self.nz
         return self.z0 + (np.arange(self.nz) + 0.5) * dz
 
@@ -92,6 +96,11 @@ class Problem:
         """The same problem on a non-uniform radial mesh (faces[0] and faces[-1] become the walls)."""
         f = tuple(float(v) for v in faces)
         return replace(self, r_faces=f, r_in=f[0], r_out=f[-1])
+
+    def with_z_faces(self, faces):
+        """The same problem on a non-uniform axial mesh (faces[0] and faces[-1] become the walls)."""
+        f = tuple(float(v) for v in faces)
+        return replace(self, z_faces=f, z0=f[0], z1=f[-1])
 
     def with_patches(self, patches, phi_exposed: float = 0.0):
         """The same bounding annulus restricted to a union of rectangular cell patches."""

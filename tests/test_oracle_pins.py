@@ -164,6 +164,32 @@ def test_linear_bias_is_exact():
     np.testing.assert_allclose(phi, phi_exact, rtol=1e-12, atol=1e-10)
 
 
+@pytest.mark.parametrize("ratio", [1.15, 0.8])
+def test_linear_bias_is_exact_on_a_stretched_axial_mesh(ratio):
+    """A potential linear in z is reproduced exactly by the cell-centred
+    finite volumes on any axial spacing: every z face carries the same flux
+    r dr c (the conductance's 1 / distance cancels the difference), the wall
+    faces included.  A conductance or volume built from a uniform dz, or a
+    wall distance of half the wrong cell, breaks it."""
+    p0 = W.annulus(12, 8, 14)
+    w = ratio ** np.arange(p0.nz)
+    zf = p0.z0 + (p0.z1 - p0.z0) * np.r_[0.0, np.cumsum(w)] / w.sum()
+    p0 = p0.with_z_faces(zf)
+    zc = p0.z_centres()
+    bias = 300.0 * (1.0 - (zc - p0.z0) / (p0.z1 - p0.z0))
+    p = p0.with_r_wall_data(bias, bias)
+    g = oracle.grid_from_problem(p)
+    phi_exact = np.broadcast_to(bias[:, None, None], p.shape)
+    rho = np.zeros(p.shape)
+    assert oracle.relres(g, rho, phi_exact) < 1e-14
+    phi, info = oracle.solve3d(g, rho, tol=1e-15)
+    np.testing.assert_allclose(phi, phi_exact, rtol=1e-12, atol=1e-10)
+    # the same field on a uniform mesh's centres is not a solution here
+    zu = p0.z0 + (np.arange(p0.nz) + 0.5) * (p0.z1 - p0.z0) / p0.nz
+    wrong = np.broadcast_to((300.0 * (1.0 - (zu - p0.z0) / (p0.z1 - p0.z0)))[:, None, None], p.shape)
+    assert oracle.relres(g, rho, wrong) > 1e-3
+
+
 def test_c0_discrete_manufactured():
     """C0: rho from the discrete operator reproduces the sampled potential."""
     p = W.c0_problem()
