@@ -526,11 +526,29 @@ def run_composite(args, schedules, world, dist):
     forms' schedules (the fused smoother does not take patches)."""
     import torch
     from paper_2609_07172_gb300 import FP64, MIXED, Plan, workloads as W
+    import numpy as np
     p = W.channel_plume(512, 128, 384)
-    rhos = [W.rho_plasma_torch(p, 900 + s) for s in range(4)]
-    phi = torch.empty(p.shape, dtype=torch.float64, device="cuda")
     out = {"workload": "channel_plume_512x128x384", "active_cells_rz": int(p.active_cells().sum()),
            "patches": [list(q) for q in p.patches]}
+    out.update(_time_forms(args, schedules, world, dist, p, 900))
+    # a non-uniform axial mesh on the headline grid: each cell 1.002 times as
+    # tall as the one below it (the top cell 2.2 times the bottom one)
+    q = W.annulus(512, 128, 400)
+    w = 1.002 ** np.arange(q.nz)
+    q = q.with_z_faces(q.z0 + (q.z1 - q.z0) * np.r_[0.0, np.cumsum(w)] / w.sum())
+    out["axial_stretched_512x128x400"] = dict(_time_forms(args, schedules, world, dist, q, 950),
+                                              ratio=1.002)
+    return out
+
+
+def _time_forms(args, schedules, world, dist, p, seed0):
+    """FP64 and mixed graph solves of problem p to the benchmark tolerance
+    with the headline forms' schedules (no fused smoother)."""
+    import torch
+    from paper_2609_07172_gb300 import FP64, MIXED, Plan, workloads as W
+    rhos = [W.rho_plasma_torch(p, seed0 + s) for s in range(4)]
+    phi = torch.empty(p.shape, dtype=torch.float64, device="cuda")
+    out = {}
     for name, prec in (("fp64", FP64), ("mixed", MIXED)):
         kw = dict(schedules.get(name) or {})
         kw["smooth_fused"] = 0

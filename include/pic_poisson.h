@@ -101,6 +101,12 @@ typedef struct {
                                   the appendix's face-conductance formulas on them.  The axial spacing
                                   stays uniform.  pic_poisson_deposit and the no-allocation residual
                                   need uniform faces. */
+    const double *z_faces;     /* host, nz + 1 strictly increasing axial faces, or NULL: uniform from z0
+                                  to z1.  Given, they define z0 and z1; the coefficients are built row by
+                                  row from them (per-row tables, a dense coarsest solve of at most
+                                  PIC_POISSON_MAX_DENSE cells).  Not with smooth_fused,
+                                  pic_poisson_face_field, pic_poisson_deposit or the no-allocation
+                                  residual. */
     double eps0;               /* vacuum permittivity; <= 0 selects 8.8541878128e-12 F/m */
     int precision;             /* PIC_POISSON_FP64 or PIC_POISSON_MIXED */
     int max_cycles;            /* V-cycle cap; <= 0 selects 200 */

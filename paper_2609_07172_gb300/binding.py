@@ -46,6 +46,7 @@ class Desc(ctypes.Structure):
         ("phi_r_in", ctypes.c_double), ("phi_r_out", ctypes.c_double),
         ("phi_z0", ctypes.c_double), ("phi_z1", ctypes.c_double),
         ("phi_r_in_z", ctypes.c_void_p), ("phi_r_out_z", ctypes.c_void_p), ("r_faces", ctypes.c_void_p),
+        ("z_faces", ctypes.c_void_p),
         ("eps0", ctypes.c_double),
         ("precision", ctypes.c_int), ("max_cycles", ctypes.c_int),
         ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int),
@@ -175,7 +176,7 @@ def make_desc(problem, precision=FP64, max_cycles=0, pre_sweeps=-1, post_sweeps=
     d.theta_span = problem.theta_span
     d.phi_r_in, d.phi_r_out = problem.phi_r_in, problem.phi_r_out
     d.phi_z0, d.phi_z1 = problem.phi_z0, problem.phi_z1
-    for name in ("phi_r_in_z", "phi_r_out_z", "r_faces"):
+    for name in ("phi_r_in_z", "phi_r_out_z", "r_faces", "z_faces"):
         vals = getattr(problem, name, None)
         if vals is not None:
             arr = (ctypes.c_double * len(vals))(*vals)

@@ -184,7 +184,7 @@ int single(const pic_poisson_plan_s *P, const char *what) {
         return PIC_POISSON_EINVAL;
     }
     if (P->pr[0].nact > 0) {
-        set_error("%s does not take a composite domain (the plan has patches)", what);
+        set_error("%s does not take a composite domain or non-uniform axial mesh (patches or z_faces)", what);
         return PIC_POISSON_EINVAL;
     }
     return PIC_POISSON_OK;

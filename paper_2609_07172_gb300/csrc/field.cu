@@ -73,7 +73,7 @@ extern "C" int pic_poisson_face_field(pic_poisson_plan_t plan, const double *phi
     }
     const ProblemPlan &q = plan->pr[0];
     if (q.nact > 0) {
-        set_error("pic_poisson_face_field does not take a composite domain (the plan has patches)");
+        set_error("pic_poisson_face_field does not take per-row tables (the plan has patches or z_faces)");
         return PIC_POISSON_EINVAL;
     }
     const LevelHost &h = q.lv[0];

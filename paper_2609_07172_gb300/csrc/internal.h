@@ -59,6 +59,13 @@ struct LevelHost {
     std::vector<unsigned char> act;
     std::vector<int> rcls;
     std::vector<double> d0c;
+    // non-uniform axial mesh (empty otherwise): faces [nz+1], centres and widths [nz]
+    std::vector<double> zf, zc, dzc;
+    // per-row tables (composite domain or non-uniform axial mesh): north
+    // coupling hn [ncls][nr][nm] (hz then holds the south one) and the four
+    // face conductances toward active neighbours [ncls][nr] (0 across a
+    // Dirichlet face) for the residual
+    std::vector<double> hn, ccw, cce, ccs, ccn;
 };
 
 // One level of one problem, as the kernels see it.
@@ -71,9 +78,12 @@ template <class T> struct LevelDev {
     const T *cw, *ce, *cz;        // [nr]
     const T *invd, *diag;         // [ncls][nr][nm]: omega / diag, diag
     const T *hw, *he, *hz;        // [ncls][nr][nm] omega * off-diagonal conductances / diag
-    const int *rcls;              // composite domain: coefficient class of each row [nz]; null: rows 0 and
-                                  // nz-1 are classes 0 and ncls-1, the others class 1.  An inactive cell
-                                  // has zero diag, invd and h entries, holds u = 0 and has no residual
+    const int *rcls;              // per-row tables (composite domain or non-uniform axial mesh): coefficient
+                                  // class of each row [nz]; null: rows 0 and nz-1 are classes 0 and
+                                  // ncls-1, the others class 1.  An inactive cell has zero diag, invd and
+                                  // h entries, holds u = 0 and has no residual
+    const T *hn;                  // per-row tables: omega * north conductance / diag (hz: the south one)
+    const T *ccw, *cce, *ccs, *ccn;   // per-row tables: face conductances [ncls][nr] for the residual
     V2<T> *u;                     // iterate / correction, [nz][nr][nm]
     V2<T> *b;                     // right-hand side, [nz][nr][nm]
     V2<T> *bh;                    // right-hand side / diag, [nz][nr][nm]

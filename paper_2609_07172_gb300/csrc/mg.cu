@@ -97,6 +97,21 @@ __device__ __forceinline__ void colour_cell(unsigned c, int nr, int color, int &
 template <class T, bool MASK>
 __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i, int m, size_t idx) {
     const size_t rowstride = (size_t)L.nr * L.nm;
+    if (MASK && L.rcls) {
+        // per-row tables (composite domain or non-uniform axial mesh; in a batch
+        // the plain problems take the path below): the row class's face
+        // conductances, zero across a Dirichlet face, south and north apart
+        const size_t ci = (size_t)L.rcls[k] * L.nr + i;
+        V2<T> acc = L.b[idx];
+        if (k > 0) acc = fma2<T>(L.ccs[ci], L.u[idx - rowstride], acc);
+        if (k < L.nz - 1) acc = fma2<T>(L.ccn[ci], L.u[idx + rowstride], acc);
+        if (i > 0) acc = fma2<T>(L.ccw[ci], L.u[idx - L.nm], acc);
+        if (i < L.nr - 1) acc = fma2<T>(L.cce[ci], L.u[idx + L.nm], acc);
+        const T d = L.diag[ci * L.nm + m];
+        const V2<T> r = fma2<T>(-d, L.u[idx], acc);
+        // a cell outside a composite domain's patches (zero diagonal) has no residual
+        return d == T(0) ? mk<T>(0, 0) : r;
+    }
     V2<T> s = mk<T>(0, 0);
     if (k > 0) s = L.u[idx - rowstride];
     if (k < L.nz - 1) {
@@ -106,15 +121,8 @@ __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i,
     V2<T> acc = fma2<T>(L.cz[i], s, L.b[idx]);
     if (i > 0) acc = fma2<T>(L.cw[i], L.u[idx - L.nm], acc);
     if (i < L.nr - 1) acc = fma2<T>(L.ce[i], L.u[idx + L.nm], acc);
-    if constexpr (MASK) {
-        const T d = L.diag[((size_t)lclass(L, k) * L.nr + i) * L.nm + m];
-        const V2<T> r = fma2<T>(-d, L.u[idx], acc);
-        // a cell outside a composite domain's patches (zero diagonal) has no residual
-        return d == T(0) ? mk<T>(0, 0) : r;
-    } else {
-        const T d = L.diag[((size_t)row_class(k, L.nz, L.ncls) * L.nr + i) * L.nm + m];
-        return fma2<T>(-d, L.u[idx], acc);
-    }
+    const T d = L.diag[((size_t)row_class(k, L.nz, L.ncls) * L.nr + i) * L.nm + m];
+    return fma2<T>(-d, L.u[idx], acc);
 }
 
 // One red-black Gauss-Seidel half-sweep over the cells of one colour:
@@ -150,13 +158,20 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
         const size_t idx = ((size_t)k * L.nr + i) * nm + m;
         const size_t tb = ((size_t)lclass(L, k) * L.nr + i) * nm + m;
         const size_t rowstride = (size_t)L.nr * nm;
-        V2<T> s = mk<T>(0, 0);
-        if (k > 0) s = L.u[idx - rowstride];
-        if (k < L.nz - 1) {
-            const V2<T> n = L.u[idx + rowstride];
-            s = (k > 0) ? mk<T>(s.x + n.x, s.y + n.y) : n;
+        V2<T> acc;
+        if (L.rcls) {   // per-row tables: south (hz) and north (hn) couplings apart
+            acc = L.bh[idx];
+            if (k > 0) acc = fma2<T>(L.hz[tb], L.u[idx - rowstride], acc);
+            if (k < L.nz - 1) acc = fma2<T>(L.hn[tb], L.u[idx + rowstride], acc);
+        } else {
+            V2<T> s = mk<T>(0, 0);
+            if (k > 0) s = L.u[idx - rowstride];
+            if (k < L.nz - 1) {
+                const V2<T> n = L.u[idx + rowstride];
+                s = (k > 0) ? mk<T>(s.x + n.x, s.y + n.y) : n;
+            }
+            acc = fma2<T>(L.hz[tb], s, L.bh[idx]);
         }
-        V2<T> acc = fma2<T>(L.hz[tb], s, L.bh[idx]);
         if (i > 0) acc = fma2<T>(L.hw[tb], L.u[idx - nm], acc);
         if (i < L.nr - 1) acc = fma2<T>(L.he[tb], L.u[idx + nm], acc);
         if (SOR) acc = fma2<T>(L.relax, L.u[idx], acc);
@@ -200,15 +215,23 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
             const int k = k0 + 2 * t;
             if (k >= L.nz) break;
             T hz = hz1, hw = hw1, he = he1;
-            if (L.rcls || k == 0 || k == L.nz - 1) {   // boundary rows (every row of a composite
-                                                       // domain) have their own coefficient class
-                const size_t tb = (size_t)lclass(L, k) * rs + tcol;
-                hz = L.hz[tb];
+            V2<T> acc;
+            if (L.rcls) {   // per-row tables: every row its class, south and north apart
+                const size_t tb = (size_t)L.rcls[k] * rs + tcol;
                 hw = L.hw[tb];
                 he = L.he[tb];
+                acc = fma2<T>(L.hz[tb], south, vb[t]);   // absent neighbours are zero
+                acc = fma2<T>(L.hn[tb], vn[t], acc);
+            } else {
+                if (k == 0 || k == L.nz - 1) {   // boundary rows have their own coefficient class
+                    const size_t tb = (size_t)row_class(k, L.nz, L.ncls) * rs + tcol;
+                    hz = L.hz[tb];
+                    hw = L.hw[tb];
+                    he = L.he[tb];
+                }
+                const V2<T> s = mk<T>(south.x + vn[t].x, south.y + vn[t].y);   // absent neighbours are zero
+                acc = fma2<T>(hz, s, vb[t]);
             }
-            const V2<T> s = mk<T>(south.x + vn[t].x, south.y + vn[t].y);   // absent neighbours are zero
-            V2<T> acc = fma2<T>(hz, s, vb[t]);
             if (i > 0) acc = fma2<T>(hw, vw[t], acc);
             if (i < L.nr - 1) acc = fma2<T>(he, ve[t], acc);
             if (SOR) acc = fma2<T>(L.relax, vo[t], acc);

@@ -161,8 +161,9 @@ extern "C" int pic_poisson_mode_residual_noalloc(const pic_poisson_desc *desc, c
                   2 * (NA_MAX_MODES - 1));
         return PIC_POISSON_EINVAL;
     }
-    if (d.n_patches > 0) {
-        set_error("pic_poisson_mode_residual_noalloc does not take a composite domain (n_patches must be 0)");
+    if (d.n_patches > 0 || d.z_faces) {
+        set_error("pic_poisson_mode_residual_noalloc does not take a composite domain or non-uniform axial mesh "
+                  "(n_patches must be 0, z_faces NULL)");
         return PIC_POISSON_EINVAL;
     }
     if (d.r_faces) {

@@ -96,6 +96,15 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
         d->r_in = d->r_faces[0];
         d->r_out = d->r_faces[d->nr];
     }
+    if (d->z_faces && d->nz >= 1) {   // given faces define the axial walls
+        for (int a = 0; a <= d->nz; ++a)
+            if (!std::isfinite(d->z_faces[a]) || (a > 0 && !(d->z_faces[a] > d->z_faces[a - 1]))) {
+                set_error("z_faces must be nz + 1 finite, strictly increasing values");
+                return PIC_POISSON_EINVAL;
+            }
+        d->z0 = d->z_faces[0];
+        d->z1 = d->z_faces[d->nz];
+    }
     if (!(d->r_in > 0) || !(d->r_out > d->r_in) || !(d->z1 > d->z0) || !std::isfinite(d->r_out) ||
         !std::isfinite(d->z0) || !std::isfinite(d->z1)) {
         set_error("need 0 < r_in < r_out and z0 < z1 (finite)");
@@ -135,6 +144,10 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
     }
     if (d->n_patches > 0 && (d->smooth_fused || !std::isfinite(d->phi_exposed))) {
         set_error("a composite domain needs smooth_fused = 0 and a finite phi_exposed");
+        return PIC_POISSON_EINVAL;
+    }
+    if (d->z_faces && d->smooth_fused) {
+        set_error("a non-uniform axial mesh needs smooth_fused = 0");
         return PIC_POISSON_EINVAL;
     }
     if (d->n_patches == 0) d->patches = nullptr;
@@ -193,15 +206,15 @@ int hierarchy(const pic_poisson_desc &d, int *nr, int *nz, int *levels) {
         ++L;
     }
     *levels = L;
-    if (d.n_patches > 0) {   // dense coarsest solve over the active cells
-        long act = 0;
+    if (d.n_patches > 0 || d.z_faces) {   // dense coarsest solve over the active cells
+        long act = d.n_patches > 0 ? 0 : (long)r * z;
         for (int a = 0; a < d.n_patches; ++a) {
             const int *x = d.patches + 4 * a;
             act += (long)((x[1] - x[0]) / sr) * ((x[3] - x[2]) / sz);
         }
         if (act > PIC_POISSON_MAX_DENSE) {
-            set_error("the composite domain's coarsest level %d x %d has %ld active cells (> %d): put the patch "
-                      "boundaries on multiples of larger powers of two",
+            set_error("the coarsest level %d x %d of this composite domain or non-uniform axial mesh has %ld "
+                      "active cells (> %d): use counts and patch boundaries with more factors of two",
                       r, z, act, PIC_POISSON_MAX_DENSE);
             return PIC_POISSON_EINVAL;
         }
@@ -309,23 +322,49 @@ void cell_faces(const LevelHost &h, int i, int k, double *g, int *dir) {
     dir[1] = !(i < h.nr - 1 && on(i + 1, k));
     dir[2] = !(k > 0 && on(i, k - 1));
     dir[3] = !(k < h.nz - 1 && on(i, k + 1));
-    g[0] = dir[0] ? rm * h.dz / (rc - rm) : h.cw[i];
-    g[1] = dir[1] ? rp * h.dz / (rp - rc) : h.ce[i];
-    g[2] = dir[2] ? 2.0 * h.cz[i] : h.cz[i];
-    g[3] = dir[3] ? 2.0 * h.cz[i] : h.cz[i];
+    if (h.zc.empty()) {   // uniform axial spacing
+        g[0] = dir[0] ? rm * h.dz / (rc - rm) : h.cw[i];
+        g[1] = dir[1] ? rp * h.dz / (rp - rc) : h.ce[i];
+        g[2] = dir[2] ? 2.0 * h.cz[i] : h.cz[i];
+        g[3] = dir[3] ? 2.0 * h.cz[i] : h.cz[i];
+        return;
+    }
+    // non-uniform axial faces: the row's own width and centre distances
+    const double dz = h.dzc[k], zc = h.zc[k], ar = rc * h.drc[i];
+    g[0] = rm * dz / (dir[0] ? rc - rm : rc - h.rc[i - 1]);
+    g[1] = rp * dz / (dir[1] ? rp - rc : h.rc[i + 1] - rc);
+    g[2] = ar / (dir[2] ? zc - h.zf[k] : zc - h.zc[k - 1]);
+    g[3] = ar / (dir[3] ? h.zf[k + 1] - zc : h.zc[k + 1] - zc);
 }
 
-// Composite-domain level tables: rows are grouped into classes by their
-// active pattern and their neighbours' (each distinct pattern one class);
-// an inactive cell gets zero diag, invd and h entries (the smoother leaves
-// its u = 0 and the residual kernels skip it), an active cell the diagonal of
-// its own faces, exposed ones Dirichlet, and no coupling into inactive cells.
-void build_masked_tables(const pic_poisson_desc &d, int nm, LevelHost &h) {
+// mu of cell (i, k) (Eq. mode_mass_coefficient) and its s (Eq. mode_rhs) times eps0.
+double mu_cell(const LevelHost &h, int i, int k) {
+    return h.zc.empty() ? h.mu[i] : h.drc[i] * h.dzc[k] / h.rc[i];
+}
+double s_eps0_cell(const LevelHost &h, int i, int k) {
+    return h.rc[i] * h.drc[i] * (h.zc.empty() ? h.dz : h.dzc[k]);
+}
+
+// Per-row level tables (a composite domain or a non-uniform axial mesh):
+// rows are grouped into classes by their active pattern and their
+// neighbours' (each distinct pattern one class; on a non-uniform axial mesh
+// every row is its own class); an inactive cell gets zero diag, invd and h
+// entries (the smoother leaves its u = 0 and the residual kernels skip it),
+// an active cell the diagonal of its own faces, exposed ones Dirichlet, and
+// no coupling across a Dirichlet face.  South and north couplings are kept
+// apart (hz and hn; ccs and ccn), as the axial distances may differ.
+void build_rowwise_tables(const pic_poisson_desc &d, int nm, LevelHost &h) {
     const int nr = h.nr, nz = h.nz;
     std::map<std::vector<unsigned char>, int> seen;
     std::vector<int> rep;
     h.rcls.assign(nz, 0);
+    if (h.act.empty()) h.act.assign((size_t)nr * nz, 1);
     for (int k = 0; k < nz; ++k) {
+        if (!h.zc.empty()) {   // every row its own class
+            h.rcls[k] = k;
+            rep.push_back(k);
+            continue;
+        }
         std::vector<unsigned char> sig(nr);
         for (int i = 0; i < nr; ++i) {
             const unsigned char a = h.act[(size_t)k * nr + i];
@@ -347,7 +386,9 @@ void build_masked_tables(const pic_poisson_desc &d, int nm, LevelHost &h) {
     h.hw.assign(nt, 0.0);
     h.he.assign(nt, 0.0);
     h.hz.assign(nt, 0.0);
+    h.hn.assign(nt, 0.0);
     h.d0c.assign((size_t)h.ncls * nr, 0.0);
+    for (auto *v : {&h.ccw, &h.cce, &h.ccs, &h.ccn}) v->assign((size_t)h.ncls * nr, 0.0);
     const double w = d.omega > 0 ? d.omega : 1.0;
     for (int c = 0; c < h.ncls; ++c) {
         const int k = rep[c];
@@ -356,16 +397,22 @@ void build_masked_tables(const pic_poisson_desc &d, int nm, LevelHost &h) {
             double g[4];
             int dir[4];
             cell_faces(h, i, k, g, dir);
-            const double d0 = g[0] + g[1] + g[2] + g[3];
-            h.d0c[(size_t)c * nr + i] = d0;
+            const double d0 = g[0] + g[1] + g[2] + g[3], mu = mu_cell(h, i, k);
+            const size_t ci = (size_t)c * nr + i;
+            h.d0c[ci] = d0;
+            h.ccw[ci] = dir[0] ? 0.0 : g[0];
+            h.cce[ci] = dir[1] ? 0.0 : g[1];
+            h.ccs[ci] = dir[2] ? 0.0 : g[2];
+            h.ccn[ci] = dir[3] ? 0.0 : g[3];
             for (int m = 0; m < nm; ++m) {
-                const size_t t = ((size_t)c * nr + i) * nm + m;
-                const double dg = d0 + lambda_m(d, m) * h.mu[i];
+                const size_t t = ci * nm + m;
+                const double dg = d0 + lambda_m(d, m) * mu;
                 h.diag[t] = dg;
                 h.invd[t] = w / dg;
-                h.hw[t] = dir[0] ? 0.0 : w * h.cw[i] / dg;
-                h.he[t] = dir[1] ? 0.0 : w * h.ce[i] / dg;
-                h.hz[t] = w * h.cz[i] / dg;
+                h.hw[t] = w * h.ccw[ci] / dg;
+                h.he[t] = w * h.cce[ci] / dg;
+                h.hz[t] = w * h.ccs[ci] / dg;
+                h.hn[t] = w * h.ccn[ci] / dg;
             }
         }
     }
@@ -404,7 +451,7 @@ int dense_factors(const ProblemPlan &q, std::vector<int> &aidx, std::vector<int>
             }
     const int n = (int)aidx.size();
     isq.assign(n, 0.0);
-    for (int a = 0; a < n; ++a) isq[a] = 1.0 / std::sqrt(h.mu[aidx[a] % nr]);
+    for (int a = 0; a < n; ++a) isq[a] = 1.0 / std::sqrt(mu_cell(h, aidx[a] % nr, aidx[a] / nr));
     std::vector<double> S((size_t)n * n, 0.0);
     for (int a = 0; a < n; ++a) {
         const int k = aidx[a] / nr, i = aidx[a] % nr;
@@ -500,6 +547,8 @@ int setup_problem(ProblemPlan &q, const pic_poisson_desc &d) {
     q.rf0 = d.r_faces ? std::vector<double>(d.r_faces, d.r_faces + d.nr + 1) : uniform_faces(d, d.nr);
     q.d.r_faces = q.rf0.data();
     q.patches.assign(d.patches, d.patches + 4 * d.n_patches);
+    if (d.z_faces) q.zf0.assign(d.z_faces, d.z_faces + d.nz + 1);
+    q.d.z_faces = q.zf0.empty() ? nullptr : q.zf0.data();
     q.d.patches = q.patches.empty() ? nullptr : q.patches.data();
     int nr[PIC_POISSON_MAX_LEVELS], nz[PIC_POISSON_MAX_LEVELS];
     int rc = hierarchy(q.d, nr, nz, &q.L);
@@ -508,24 +557,39 @@ int setup_problem(ProblemPlan &q, const pic_poisson_desc &d) {
     q.lv.resize(q.L);
     const std::vector<unsigned char> act0 = patch_mask(q.d);
     std::vector<double> rf = q.rf0;   // a level halved in r keeps every other face
+    std::vector<double> zf = q.zf0;   // non-uniform axial faces (empty: uniform)
     for (int l = 0; l < q.L; ++l) {
         if (l > 0 && nr[l] != nr[l - 1]) {
             std::vector<double> c(nr[l] + 1);
             for (int a = 0; a <= nr[l]; ++a) c[a] = rf[2 * a];
             rf.swap(c);
         }
+        if (l > 0 && nz[l] != nz[l - 1] && !zf.empty()) {   // likewise in z
+            std::vector<double> c(nz[l] + 1);
+            for (int a = 0; a <= nz[l]; ++a) c[a] = zf[2 * a];
+            zf.swap(c);
+        }
         LevelHost &h = q.lv[l];
         build_level(q.d, rf, nz[l], q.nm, h);
+        if (!zf.empty()) {
+            h.zf = zf;
+            h.zc.assign(nz[l], 0.0);
+            h.dzc.assign(nz[l], 0.0);
+            for (int k = 0; k < nz[l]; ++k) {
+                h.zc[k] = 0.5 * (zf[k] + zf[k + 1]);
+                h.dzc[k] = zf[k + 1] - zf[k];
+            }
+        }
         if (!act0.empty()) {   // protected faces: each coarse cell lies in one patch or none
             const int sr = d.nr / nr[l], sz = d.nz / nz[l];
             h.act.assign((size_t)nr[l] * nz[l], 0);
             for (int k = 0; k < nz[l]; ++k)
                 for (int i = 0; i < nr[l]; ++i) h.act[(size_t)k * nr[l] + i] = act0[(size_t)(k * sz) * d.nr + i * sr];
-            build_masked_tables(q.d, q.nm, h);
         }
+        if (!act0.empty() || !zf.empty()) build_rowwise_tables(q.d, q.nm, h);
     }
     q.nact = 0;
-    if (!act0.empty())
+    if (!act0.empty() || !zf.empty())
         for (unsigned char a : q.lv[q.L - 1].act) q.nact += a;
     return PIC_POISSON_OK;
 }
@@ -550,6 +614,13 @@ template <class T, class V> void carve_level(const LevelHost &h, int nm, int nt,
     v.he = c.take<T>(ntab);
     v.hz = c.take<T>(ntab);
     v.rcls = h.rcls.empty() ? nullptr : c.take<int>(h.nz);
+    const bool rw = !h.rcls.empty();
+    v.hn = rw ? c.take<T>(ntab) : nullptr;
+    const size_t nc = (size_t)h.ncls * h.nr;
+    v.ccw = rw ? c.take<T>(nc) : nullptr;
+    v.cce = rw ? c.take<T>(nc) : nullptr;
+    v.ccs = rw ? c.take<T>(nc) : nullptr;
+    v.ccn = rw ? c.take<T>(nc) : nullptr;
 }
 
 template <class T> void carve_coarse(const ProblemPlan &q, Carver &c, CoarseDev<T> &cd) {
@@ -693,6 +764,11 @@ template <class X> void blob_to_dev(const X &src, X *dst, cudaStream_t st, cudaE
 
 template <class T> void upload_level(const LevelHost &h, const LevelDev<T> &v, cudaStream_t st, cudaError_t &err) {
     ints_to_dev(h.rcls, v.rcls, st, err);
+    to_dev(h.hn, v.hn, st, err);
+    to_dev(h.ccw, v.ccw, st, err);
+    to_dev(h.cce, v.cce, st, err);
+    to_dev(h.ccs, v.ccs, st, err);
+    to_dev(h.ccn, v.ccn, st, err);
     to_dev(h.cw, v.cw, st, err);
     to_dev(h.ce, v.ce, st, err);
     to_dev(h.cz, v.cz, st, err);
@@ -961,7 +1037,7 @@ int upload(pic_poisson_plan_s &P) {
             for (int k = 0; k < h.nz; ++k)
                 for (int i = 0; i < h.nr; ++i) {
                     if (!h.act[(size_t)k * h.nr + i]) continue;
-                    s2[(size_t)k * h.nr + i] = s[i];
+                    s2[(size_t)k * h.nr + i] = s_eps0_cell(h, i, k) / q.d.eps0;
                     double g[4];
                     int dir[4];
                     cell_faces(h, i, k, g, dir);
@@ -1269,10 +1345,18 @@ int pic_poisson_cell_coeffs(const pic_poisson_desc *desc, int i, int k, double *
     LevelHost h;
     build_level(d, d.r_faces ? std::vector<double>(d.r_faces, d.r_faces + d.nr + 1) : uniform_faces(d, d.nr), d.nz, 1,
                 h);
-    if (d.n_patches > 0) {   // composite domain: exposed faces are Dirichlet faces at phi_exposed
+    if (d.n_patches > 0 || d.z_faces) {   // composite domain (exposed faces are Dirichlet faces at
+                                          // phi_exposed) or non-uniform axial faces
         h.act = patch_mask(d);
+        if (d.z_faces) {
+            h.zf.assign(d.z_faces, d.z_faces + d.nz + 1);
+            for (int a = 0; a < d.nz; ++a) {
+                h.zc.push_back(0.5 * (h.zf[a] + h.zf[a + 1]));
+                h.dzc.push_back(h.zf[a + 1] - h.zf[a]);
+            }
+        }
         for (int a = 0; a < 12; ++a) out[a] = 0.0;
-        if (!h.act[(size_t)k * d.nr + i]) return PIC_POISSON_OK;   // not an unknown
+        if (!h.act.empty() && !h.act[(size_t)k * d.nr + i]) return PIC_POISSON_OK;   // not an unknown
         double g[4];
         int dir[4];
         cell_faces(h, i, k, g, dir);
@@ -1285,8 +1369,8 @@ int pic_poisson_cell_coeffs(const pic_poisson_desc *desc, int i, int k, double *
             out[10] += g[f];
             if (dir[f]) out[11] += g[f] * wall[f];
         }
-        out[8] = h.mu[i];
-        out[9] = h.rc[i] * h.drc[i] * h.dz / d.eps0;
+        out[8] = mu_cell(h, i, k);
+        out[9] = s_eps0_cell(h, i, k) / d.eps0;
         return PIC_POISSON_OK;
     }
     const bool dw = i == 0, de = i == d.nr - 1, ds = k == 0, dn = k == d.nz - 1;

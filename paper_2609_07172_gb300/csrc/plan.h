@@ -11,6 +11,7 @@ struct ProblemPlan {
     std::vector<double> rin_z, rout_z;
     std::vector<double> rf0;                    // level-0 radial faces (given or uniform)
     std::vector<int> patches;                   // composite domain: 4 ints per patch (empty: the annulus)
+    std::vector<double> zf0;                    // level-0 axial faces when given (empty: uniform)
     int nact = 0;                               // composite domain: active cells of the coarsest level
     bool uniform_r = true;
     int L = 0, nm = 0;

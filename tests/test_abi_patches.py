@@ -87,3 +87,53 @@ def test_patch_limits_and_settings_rejected():
     fake = ctypes.c_void_p(256)   # never dereferenced: the descriptor is refused first
     assert B.load().pic_poisson_mode_residual_noalloc(ctypes.byref(d), fake, fake, fake, fake, 0) == B.EINVAL
     assert "composite" in B.last_error()
+
+
+def _stretched_z(p, ratio):
+    w = ratio ** np.arange(p.nz)
+    return p.with_z_faces(p.z0 + (p.z1 - p.z0) * np.r_[0.0, np.cumsum(w)] / w.sum())
+
+
+@pytest.mark.parametrize("kind", ["annulus", "stretched_r", "channel_plume"])
+def test_axial_faces_cell_coeffs_match_oracle_everywhere(kind):
+    """Non-uniform axial faces: every coefficient of every cell against the
+    oracle's (south and north conductances differ row by row)."""
+    p = W.annulus(10, 8, 12, phi_r_in=3.0, phi_r_out=-2.0, phi_z0=11.0, phi_z1=5.0)
+    if kind == "stretched_r":
+        p = p.with_r_faces(W.stretched_radial_faces(p.r_in, p.r_out, p.nr, 1.2))
+    if kind == "channel_plume":
+        p = W.channel_plume(16, 8, 12, phi_z0=11.0).with_patches(((4, 8, 0, 6), (0, 16, 6, 12)), 2.5)
+    p = _stretched_z(p, 1.17)
+    g = oracle.grid_from_problem(p)
+    b = oracle.rhs3d(g, np.zeros(p.shape))
+    act = p.active_cells()
+    for k in range(p.nz):
+        for i in range(p.nr):
+            lib = np.array(B.cell_coeffs(p, i, k))
+            orc = oracle.cell_coeffs(g, i, k)
+            if not act[k, i]:
+                assert np.all(lib == 0.0)
+                continue
+            np.testing.assert_allclose(lib[0:4], orc["G"], rtol=1e-14)
+            np.testing.assert_array_equal(lib[4:8].astype(bool), orc["dirichlet"])
+            assert lib[8] == pytest.approx(orc["mu"], rel=1e-14)
+            assert lib[9] == pytest.approx(orc["s"], rel=1e-14)
+            assert lib[10] == pytest.approx(orc["D0"], rel=1e-14)
+            assert lib[11] == pytest.approx(b[k, 0, i], rel=1e-14, abs=1e-12)
+
+
+def test_axial_faces_validated():
+    lay = B.Layout()
+    p = W.annulus(16, 8, 16)
+    bad = list(p.z0 + (p.z1 - p.z0) * np.arange(17) / 16)
+    bad[5] = bad[4]
+    d, _ = B.make_desc(p.with_z_faces(bad))
+    assert B.load().pic_poisson_query(ctypes.byref(d), ctypes.byref(lay)) == B.EINVAL
+    assert "z_faces" in B.last_error()
+    d, _ = B.make_desc(_stretched_z(p, 1.1), precision=MIXED, smooth_fused=1)
+    assert B.load().pic_poisson_query(ctypes.byref(d), ctypes.byref(lay)) == B.EINVAL
+    # the coarsest level is solved densely: at most PIC_POISSON_MAX_DENSE cells
+    d, _ = B.make_desc(_stretched_z(W.annulus(130, 8, 50), 1.01))   # coarsest 65 x 50
+    assert B.load().pic_poisson_query(ctypes.byref(d), ctypes.byref(lay)) == B.EINVAL
+    lay2 = B.query(_stretched_z(W.annulus(512, 8, 400), 1.002))
+    assert lay2["nr"][-1] * lay2["nz"][-1] <= 1024
