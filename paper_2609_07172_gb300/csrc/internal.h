@@ -222,7 +222,7 @@ cudaError_t launch_copy_guess(const FFTTab *tab, unsigned grid, cudaStream_t st)
 // strip: see pic_poisson_desc.smooth_strip; sor: over-relaxed update (omega != 1).
 template <class T>
 cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, int threads, int strip, bool sor,
-                          cudaStream_t st);
+                          cudaStream_t st, bool rowwise = false);
 // red_only: residual of the red fine cells only (valid right after a black half-sweep).
 // Per problem, f.init selects what is written into the coarse level c: 0 = b only
 // (coarsest, solved directly); 1 = also b_hat and u = 0; 2 = also b_hat and

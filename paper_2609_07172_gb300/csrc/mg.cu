@@ -142,7 +142,9 @@ __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i,
 // colour in cell-major, mode-fast order (blocks: mg_blocks of the entries).
 // SOR: over-relaxation u <- (1 - omega) u + omega u_GS, the tables carrying
 // omega (one more load and multiply-add per component); otherwise omega = 1.
-template <class T, int NT, int S, bool SOR>
+// RW: the plan holds per-row tables (composite domain or non-uniform axial
+// mesh); the plain variant keeps the three-class rule and no such branch.
+template <class T, int NT, int S, bool SOR, bool RW>
 __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const LaunchTab<T> *__restrict__ tab, int color) {
     const int p = find_problem(tab->start, tab->n, blockIdx.x);
     if (tab->done && tab->done[tab->pid[p]]) return;   // stopped problem of a batch
@@ -156,10 +158,10 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
         int k, i;
         colour_cell(c, L.nr, color, k, i);
         const size_t idx = ((size_t)k * L.nr + i) * nm + m;
-        const size_t tb = ((size_t)lclass(L, k) * L.nr + i) * nm + m;
+        const size_t tb = ((size_t)(RW ? lclass(L, k) : row_class(k, L.nz, L.ncls)) * L.nr + i) * nm + m;
         const size_t rowstride = (size_t)L.nr * nm;
         V2<T> acc;
-        if (L.rcls) {   // per-row tables: south (hz) and north (hn) couplings apart
+        if (RW && L.rcls) {   // per-row tables: south (hz) and north (hn) couplings apart
             acc = L.bh[idx];
             if (k > 0) acc = fma2<T>(L.hz[tb], L.u[idx - rowstride], acc);
             if (k < L.nz - 1) acc = fma2<T>(L.hn[tb], L.u[idx + rowstride], acc);
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
             if (k >= L.nz) break;
             T hz = hz1, hw = hw1, he = he1;
             V2<T> acc;
-            if (L.rcls) {   // per-row tables: every row its class, south and north apart
+            if (RW && L.rcls) {   // per-row tables: every row its class, south and north apart
                 const size_t tb = (size_t)L.rcls[k] * rs + tcol;
                 hw = L.hw[tb];
                 he = L.he[tb];
@@ -804,24 +806,24 @@ __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ p, int 
 
 }  // namespace
 
-template <class T, int S, bool SOR>
+template <class T, int S, bool SOR, bool RW>
 void launch_smooth_s(const LaunchTab<T> *tab, unsigned grid, int color, int threads, cudaStream_t st) {
     switch (threads) {
-    case 64: k_smooth<T, 64, S, SOR><<<grid, 64, 0, st>>>(tab, color); break;
-    case 128: k_smooth<T, 128, S, SOR><<<grid, 128, 0, st>>>(tab, color); break;
-    case 512: k_smooth<T, 512, S, SOR><<<grid, 512, 0, st>>>(tab, color); break;
-    default: k_smooth<T, 256, S, SOR><<<grid, 256, 0, st>>>(tab, color); break;
+    case 64: k_smooth<T, 64, S, SOR, RW><<<grid, 64, 0, st>>>(tab, color); break;
+    case 128: k_smooth<T, 128, S, SOR, RW><<<grid, 128, 0, st>>>(tab, color); break;
+    case 512: k_smooth<T, 512, S, SOR, RW><<<grid, 512, 0, st>>>(tab, color); break;
+    default: k_smooth<T, 256, S, SOR, RW><<<grid, 256, 0, st>>>(tab, color); break;
     }
 }
 
-template <class T, bool SOR>
+template <class T, bool SOR, bool RW>
 cudaError_t launch_smooth_r(const LaunchTab<T> *tab, unsigned grid, int color, int threads, int strip,
                             cudaStream_t st) {
     switch (strip) {
-    case 0: launch_smooth_s<T, 0, SOR>(tab, grid, color, threads, st); break;
-    case 1: launch_smooth_s<T, 1, SOR>(tab, grid, color, threads, st); break;
-    case 2: launch_smooth_s<T, 2, SOR>(tab, grid, color, threads, st); break;
-    case 4: launch_smooth_s<T, 4, SOR>(tab, grid, color, threads, st); break;
+    case 0: launch_smooth_s<T, 0, SOR, RW>(tab, grid, color, threads, st); break;
+    case 1: launch_smooth_s<T, 1, SOR, RW>(tab, grid, color, threads, st); break;
+    case 2: launch_smooth_s<T, 2, SOR, RW>(tab, grid, color, threads, st); break;
+    case 4: launch_smooth_s<T, 4, SOR, RW>(tab, grid, color, threads, st); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -829,9 +831,12 @@ cudaError_t launch_smooth_r(const LaunchTab<T> *tab, unsigned grid, int color, i
 
 template <class T>
 cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, int threads, int strip, bool sor,
-                          cudaStream_t st) {
-    return sor ? launch_smooth_r<T, true>(tab, grid, color, threads, strip, st)
-               : launch_smooth_r<T, false>(tab, grid, color, threads, strip, st);
+                          cudaStream_t st, bool rowwise) {
+    if (rowwise)
+        return sor ? launch_smooth_r<T, true, true>(tab, grid, color, threads, strip, st)
+                   : launch_smooth_r<T, false, true>(tab, grid, color, threads, strip, st);
+    return sor ? launch_smooth_r<T, true, false>(tab, grid, color, threads, strip, st)
+               : launch_smooth_r<T, false, false>(tab, grid, color, threads, strip, st);
 }
 
 template <class T>
@@ -928,7 +933,8 @@ cudaError_t launch_sum(const double *partials, int n, double *out, cudaStream_t 
 }
 
 #define PP_INST(T)                                                                                         \
-    template cudaError_t launch_smooth<T>(const LaunchTab<T> *, unsigned, int, int, int, bool, cudaStream_t); \
+    template cudaError_t launch_smooth<T>(const LaunchTab<T> *, unsigned, int, int, int, bool, cudaStream_t, \
+                                          bool);                                                           \
     template cudaError_t launch_residual_restrict<T>(const LaunchTab<T> *, unsigned, bool, double *,       \
                                                      cudaStream_t, bool);                                  \
     template cudaError_t launch_residual<T>(const LaunchTab<T> *, unsigned, bool, double *, unsigned,      \

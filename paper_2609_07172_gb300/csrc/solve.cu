@@ -142,7 +142,7 @@ int smooth_level(Runner &R, const Hier<T> &H, int l, int sweeps, bool skip_first
         for (int color = (s == 0 && skip_first_red) ? 1 : 0; color < 2; ++color) {
             const bool sor = R.P.shared.omega != 1.0;
             RUN(R, ph, launch_smooth(H.smooth[l], H.g_smooth[l], color, R.P.shared.smooth_threads, H.strip[l], sor,
-                                     R.st));
+                                     R.st, R.P.masked));
             R.account(ph, (sor ? 2.0 : 1.5) * n * sizeof(V2<T>), (sor ? 18.0 : 14.0) * 0.5 * n);
         }
     }
