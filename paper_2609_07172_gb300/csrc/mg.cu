@@ -161,10 +161,22 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
         const size_t tb = ((size_t)(RW ? lclass(L, k) : row_class(k, L.nz, L.ncls)) * L.nr + i) * nm + m;
         const size_t rowstride = (size_t)L.nr * nm;
         V2<T> acc;
-        if (RW && L.rcls) {   // per-row tables: south (hz) and north (hn) couplings apart
-            acc = L.bh[idx];
-            if (k > 0) acc = fma2<T>(L.hz[tb], L.u[idx - rowstride], acc);
-            if (k < L.nz - 1) acc = fma2<T>(L.hn[tb], L.u[idx + rowstride], acc);
+        if (RW && L.rcls) {
+            // per-row tables: u = invd (b + sum G u) from the row class's face
+            // conductances (small, cached) and one per-entry table, rather
+            // than four per-entry h tables (on a non-uniform axial mesh every
+            // row is a class, so those are as large as u)
+            const size_t ci = (size_t)L.rcls[k] * L.nr + i;
+            acc = L.b[idx];
+            if (k > 0) acc = fma2<T>(L.ccs[ci], L.u[idx - rowstride], acc);
+            if (k < L.nz - 1) acc = fma2<T>(L.ccn[ci], L.u[idx + rowstride], acc);
+            if (i > 0) acc = fma2<T>(L.ccw[ci], L.u[idx - nm], acc);
+            if (i < L.nr - 1) acc = fma2<T>(L.cce[ci], L.u[idx + nm], acc);
+            const T inv = L.invd[tb];
+            acc = mk<T>(acc.x * inv, acc.y * inv);
+            if (SOR) acc = fma2<T>(L.relax, L.u[idx], acc);
+            L.u[idx] = acc;
+            return;
         } else {
             V2<T> s = mk<T>(0, 0);
             if (k > 0) s = L.u[idx - rowstride];
@@ -208,7 +220,7 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
                 if (k < L.nz - 1) vn[t] = __ldg(L.u + idx + rs);
                 if (i > 0) vw[t] = __ldg(L.u + idx - nm);
                 if (i < L.nr - 1) ve[t] = __ldg(L.u + idx + nm);
-                vb[t] = __ldg(L.bh + idx);
+                vb[t] = __ldg(((RW && L.rcls) ? L.b : L.bh) + idx);   // per-row tables: b, else b_hat
                 if (SOR) vo[t] = L.u[idx];   // this colour: written below, so not through the read-only path
             }
         }
@@ -218,12 +230,19 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
             if (k >= L.nz) break;
             T hz = hz1, hw = hw1, he = he1;
             V2<T> acc;
-            if (RW && L.rcls) {   // per-row tables: every row its class, south and north apart
-                const size_t tb = (size_t)L.rcls[k] * rs + tcol;
-                hw = L.hw[tb];
-                he = L.he[tb];
-                acc = fma2<T>(L.hz[tb], south, vb[t]);   // absent neighbours are zero
-                acc = fma2<T>(L.hn[tb], vn[t], acc);
+            if (RW && L.rcls) {   // per-row tables: u = invd (b + sum G u), as in the S = 0 path
+                const size_t ci = (size_t)L.rcls[k] * L.nr + i;
+                const size_t idx = idx0 + (size_t)(2 * t) * rs;
+                acc = fma2<T>(L.ccs[ci], south, vb[t]);   // absent neighbours are zero
+                acc = fma2<T>(L.ccn[ci], vn[t], acc);
+                if (i > 0) acc = fma2<T>(L.ccw[ci], vw[t], acc);
+                if (i < L.nr - 1) acc = fma2<T>(L.cce[ci], ve[t], acc);
+                const T inv = L.invd[(size_t)L.rcls[k] * rs + tcol];
+                acc = mk<T>(acc.x * inv, acc.y * inv);
+                if (SOR) acc = fma2<T>(L.relax, vo[t], acc);
+                L.u[idx] = acc;
+                south = vn[t];
+                continue;
             } else {
                 if (k == 0 || k == L.nz - 1) {   // boundary rows have their own coefficient class
                     const size_t tb = (size_t)row_class(k, L.nz, L.ncls) * rs + tcol;
