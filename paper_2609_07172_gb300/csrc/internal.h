@@ -101,11 +101,12 @@ template <class T> struct CoarseDev {
     int nact;
     const int *aidx;              // [nact] cell index k nr + i of each active cell
     const int *amap;              // [nz][nr] active index of a cell, -1 when inactive
-    const T *Q;                   // [nact][nact] eigenvectors, Q[a nact + j]
-    const T *QT;                  // [nact][nact] the transpose
-    const T *lam;                 // [nact] eigenvalues of M^(-1/2) A_0 M^(-1/2)
-    const T *isq;                 // [nact] 1 / sqrt(mu) of each active cell
-    const T *lamm;                // [nm] lambda_m
+    // (applied in FP32 for both precisions: a coarse-grid correction)
+    const float *Q;               // [nact][nact] eigenvectors, Q[a nact + j]
+    const float *QT;              // [nact][nact] the transpose
+    const float *lam;             // [nact] eigenvalues of M^(-1/2) A_0 M^(-1/2)
+    const float *isq;             // [nact] 1 / sqrt(mu) of each active cell
+    const float *lamm;            // [nm] lambda_m
 };
 
 // Work of one launch over a batch of problems: problem p owns the blocks

@@ -161,11 +161,18 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
         const size_t tb = ((size_t)(RW ? lclass(L, k) : row_class(k, L.nz, L.ncls)) * L.nr + i) * nm + m;
         const size_t rowstride = (size_t)L.nr * nm;
         V2<T> acc;
-        if (RW && L.rcls) {
-            // per-row tables: u = invd (b + sum G u) from the row class's face
-            // conductances (small, cached) and one per-entry table, rather
+        if (RW && L.rcls && sizeof(T) == sizeof(double)) {   // per-row tables, FP64: south (hz) and
+                                                             // north (hn) couplings apart
+            acc = L.bh[idx];
+            if (k > 0) acc = fma2<T>(L.hz[tb], L.u[idx - rowstride], acc);
+            if (k < L.nz - 1) acc = fma2<T>(L.hn[tb], L.u[idx + rowstride], acc);
+        } else if (RW && L.rcls) {
+            // per-row tables, FP32: u = invd (b + sum G u) from the row class's
+            // face conductances (small, cached) and one per-entry table rather
             // than four per-entry h tables (on a non-uniform axial mesh every
-            // row is a class, so those are as large as u)
+            // row is a class, so those are as large as u).  Two more
+            // multiplies: worth it on the FP32 pipe, not on the FP64 one
+            // (measured both ways)
             const size_t ci = (size_t)L.rcls[k] * L.nr + i;
             acc = L.b[idx];
             if (k > 0) acc = fma2<T>(L.ccs[ci], L.u[idx - rowstride], acc);
@@ -220,7 +227,8 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
                 if (k < L.nz - 1) vn[t] = __ldg(L.u + idx + rs);
                 if (i > 0) vw[t] = __ldg(L.u + idx - nm);
                 if (i < L.nr - 1) ve[t] = __ldg(L.u + idx + nm);
-                vb[t] = __ldg(((RW && L.rcls) ? L.b : L.bh) + idx);   // per-row tables: b, else b_hat
+                // per-row tables in FP32: b (the update multiplies by invd), else b_hat
+                vb[t] = __ldg(((RW && L.rcls && sizeof(T) == sizeof(float)) ? L.b : L.bh) + idx);
                 if (SOR) vo[t] = L.u[idx];   // this colour: written below, so not through the read-only path
             }
         }
@@ -230,7 +238,13 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
             if (k >= L.nz) break;
             T hz = hz1, hw = hw1, he = he1;
             V2<T> acc;
-            if (RW && L.rcls) {   // per-row tables: u = invd (b + sum G u), as in the S = 0 path
+            if (RW && L.rcls && sizeof(T) == sizeof(double)) {   // per-row tables, FP64
+                const size_t tb = (size_t)L.rcls[k] * rs + tcol;
+                hw = L.hw[tb];
+                he = L.he[tb];
+                acc = fma2<T>(L.hz[tb], south, vb[t]);   // absent neighbours are zero
+                acc = fma2<T>(L.hn[tb], vn[t], acc);
+            } else if (RW && L.rcls) {   // per-row tables, FP32: u = invd (b + sum G u), as in the S = 0 path
                 const size_t ci = (size_t)L.rcls[k] * L.nr + i;
                 const size_t idx = idx0 + (size_t)(2 * t) * rs;
                 acc = fma2<T>(L.ccs[ci], south, vb[t]);   // absent neighbours are zero
@@ -589,29 +603,50 @@ __global__ void __launch_bounds__(MG_THREADS) k_coarse(const CoarseTab<T> *__res
     const int lb = (int)(blockIdx.x - tab->start[p]);
     const int m = lb >> 1, comp = lb & 1;
     if (D.nact > 0) {
-        // composite domain: u = M^(-1/2) Q (Lambda + lambda_m)^(-1) Q^T M^(-1/2) b over the
-        // active cells (eigenvectors from plan time, shared by all modes); zero elsewhere
+        // per-row tables (composite domain or non-uniform axial mesh):
+        // u = M^(-1/2) Q (Lambda + lambda_m)^(-1) Q^T M^(-1/2) b over the active
+        // cells (eigenvectors from plan time, shared by all modes); zero
+        // elsewhere.  In FP32 for both hierarchies: a coarse-grid correction
+        // needs no FP64 accuracy (the smoother and residual stay in the
+        // level's precision), and the FP32 pipe is 64 times the FP64 one.
+        // b is first scaled by a power of two (exact) that brings its largest
+        // value of this (mode, part) to O(1), so FP32 spans any FP64 range.
+        __shared__ int s_emax;
         const int n = D.nact;
-        T *y = (T *)smraw, *z = y + n;
+        float *y = (float *)smraw, *z = y + n;
         const T *bg = (const T *)L.b + comp;
-        for (int a = threadIdx.x; a < n; a += blockDim.x) y[a] = bg[2 * ((size_t)D.aidx[a] * nm + m)] * D.isq[a];
+        if (threadIdx.x == 0) s_emax = -1100;
         __syncthreads();
-        const T lm = D.lamm[m];
+        int em = -1100;
+        for (int a = threadIdx.x; a < n; a += blockDim.x) {
+            const double v = (double)bg[2 * ((size_t)D.aidx[a] * nm + m)];
+            int e = -1100;
+            if (v != 0.0) frexp(v, &e);
+            em = max(em, e);
+        }
+        atomicMax(&s_emax, em);
+        __syncthreads();
+        const int E = s_emax > -1100 ? s_emax : 0;
+        const double down = ldexp(1.0, -E), up = ldexp(1.0, E);
+        for (int a = threadIdx.x; a < n; a += blockDim.x)
+            y[a] = (float)((double)bg[2 * ((size_t)D.aidx[a] * nm + m)] * down) * D.isq[a];
+        __syncthreads();
+        const float lm = D.lamm[m];
         for (int j = threadIdx.x; j < n; j += blockDim.x) {   // z = (Lambda + lambda_m)^(-1) Q^T y
-            T acc = 0;
-            for (int a = 0; a < n; ++a) acc = fma(D.Q[(size_t)a * n + j], y[a], acc);
+            float acc = 0.f;
+            for (int a = 0; a < n; ++a) acc = fmaf(D.Q[(size_t)a * n + j], y[a], acc);
             z[j] = acc / (D.lam[j] + lm);
         }
         __syncthreads();
         T *ug = (T *)L.u + comp;
         for (int f = threadIdx.x; f < nr * nz; f += blockDim.x) {   // u = M^(-1/2) Q z
             const int a = D.amap[f];
-            T x = 0;
+            float x = 0.f;
             if (a >= 0) {
-                for (int j = 0; j < n; ++j) x = fma(D.QT[(size_t)j * n + a], z[j], x);
+                for (int j = 0; j < n; ++j) x = fmaf(D.QT[(size_t)j * n + a], z[j], x);
                 x *= D.isq[a];
             }
-            ug[2 * ((size_t)f * nm + m)] = x;
+            ug[2 * ((size_t)f * nm + m)] = (T)((double)x * up);
         }
         return;
     }

@@ -635,11 +635,11 @@ template <class T> void carve_coarse(const ProblemPlan &q, Carver &c, CoarseDev<
         cd.V = cd.e = cd.piv = cd.cpr = nullptr;
         cd.aidx = c.take<int>(na);
         cd.amap = c.take<int>((size_t)h.nr * h.nz);
-        cd.Q = c.take<T>(na * na);
-        cd.QT = c.take<T>(na * na);
-        cd.lam = c.take<T>(na);
-        cd.isq = c.take<T>(na);
-        cd.lamm = c.take<T>(q.nm);
+        cd.Q = c.take<float>(na * na);
+        cd.QT = c.take<float>(na * na);
+        cd.lam = c.take<float>(na);
+        cd.isq = c.take<float>(na);
+        cd.lamm = c.take<float>(q.nm);
         return;
     }
     cd.aidx = cd.amap = nullptr;
@@ -942,7 +942,7 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
         tc.f[tc.n] = views(q)[q.L - 1];
         tc.c[tc.n] = cd;
         tc.start[tc.n + 1] = tc.start[tc.n] + 2u * (unsigned)q.nm;   // (mode, real / imaginary part)
-        const size_t sm = cd.nact > 0 ? 2 * (size_t)cd.nact * sizeof(T)   // dense: y and z
+        const size_t sm = cd.nact > 0 ? 2 * (size_t)cd.nact * sizeof(float)   // dense: y and z
                                        : ((size_t)cd.nr * cd.nz + (size_t)(cd.nr + 1) * cd.nz +
                                           (size_t)(cd.nz - cd.nz / 2) * cd.nz) * sizeof(T);
         tc.smem = std::max(tc.smem, sm);
