@@ -228,8 +228,9 @@ cudaError_t launch_smooth(const LaunchTab<T> *tab, unsigned grid, int color, int
 // Per problem, f.init selects what is written into the coarse level c: 0 = b only
 // (coarsest, solved directly); 1 = also b_hat and u = 0; 2 = also b_hat and
 // u = (red ? b_hat : 0), the first red half-sweep from zero.
-// masked: the plan holds a composite domain (class tables per row, no
-// residual or correction outside the patches); false runs the plain kernels.
+// masked: the plan holds per-row tables -- a composite domain or a
+// non-uniform axial mesh (class tables per row, no residual or correction
+// outside the patches); false runs the plain kernels.
 template <class T>
 cudaError_t launch_residual_restrict(const LaunchTab<T> *tab, unsigned grid, bool red_only, double *partials,
                                      cudaStream_t st, bool masked = false);

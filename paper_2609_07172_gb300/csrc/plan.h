@@ -113,7 +113,8 @@ struct pic_poisson_plan_s {
     const double *last_rho[pp::kMaxBatch] = {};
     double *last_phi[pp::kMaxBatch] = {};
     bool io_valid = false;
-    bool masked = false;                        // some problem is a composite domain (masked kernel variants)
+    bool masked = false;                        // some problem has per-row tables (composite domain or
+                                                // non-uniform axial mesh): the masked kernel variants
 };
 
 namespace pp {
