@@ -102,15 +102,16 @@ __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i,
         // the plain problems take the path below): the row class's face
         // conductances, zero across a Dirichlet face, south and north apart
         const size_t ci = (size_t)L.rcls[k] * L.nr + i;
+        const T d = L.diag[ci * L.nm + m];
+        // a cell outside a composite domain's patches (zero diagonal) has no
+        // residual: nothing else is loaded for it
+        if (d == T(0)) return mk<T>(0, 0);
         V2<T> acc = L.b[idx];
         if (k > 0) acc = fma2<T>(L.ccs[ci], L.u[idx - rowstride], acc);
         if (k < L.nz - 1) acc = fma2<T>(L.ccn[ci], L.u[idx + rowstride], acc);
         if (i > 0) acc = fma2<T>(L.ccw[ci], L.u[idx - L.nm], acc);
         if (i < L.nr - 1) acc = fma2<T>(L.cce[ci], L.u[idx + L.nm], acc);
-        const T d = L.diag[ci * L.nm + m];
-        const V2<T> r = fma2<T>(-d, L.u[idx], acc);
-        // a cell outside a composite domain's patches (zero diagonal) has no residual
-        return d == T(0) ? mk<T>(0, 0) : r;
+        return fma2<T>(-d, L.u[idx], acc);
     }
     V2<T> s = mk<T>(0, 0);
     if (k > 0) s = L.u[idx - rowstride];
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
         const size_t tb = ((size_t)(RW ? lclass(L, k) : row_class(k, L.nz, L.ncls)) * L.nr + i) * nm + m;
         const size_t rowstride = (size_t)L.nr * nm;
         V2<T> acc;
+        if (RW && L.rcls && L.invd[tb] == T(0)) return;   // outside a composite domain: u stays 0
         if (RW && L.rcls && sizeof(T) == sizeof(double)) {   // per-row tables, FP64: south (hz) and
                                                              // north (hn) couplings apart
             acc = L.bh[idx];
@@ -236,6 +238,10 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
         for (int t = 0; t < S; ++t) {
             const int k = k0 + 2 * t;
             if (k >= L.nz) break;
+            if (RW && L.rcls && L.invd[(size_t)L.rcls[k] * rs + tcol] == T(0)) {   // outside the patches
+                south = vn[t];
+                continue;
+            }
             T hz = hz1, hw = hw1, he = he1;
             V2<T> acc;
             if (RW && L.rcls && sizeof(T) == sizeof(double)) {   // per-row tables, FP64
