@@ -82,6 +82,7 @@ template <class T> struct LevelDev {
                                   // class of each row [nz]; null: rows 0 and nz-1 are classes 0 and
                                   // ncls-1, the others class 1.  An inactive cell has zero diag, invd and
                                   // h entries, holds u = 0 and has no residual
+    int holes;                    // the level has cells outside a composite domain's patches
     const T *hn;                  // per-row tables: omega * north conductance / diag (hz: the south one)
     const T *ccw, *cce, *ccs, *ccn;   // per-row tables: face conductances [ncls][nr] for the residual
     V2<T> *u;                     // iterate / correction, [nz][nr][nm]

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
         const size_t tb = ((size_t)(RW ? lclass(L, k) : row_class(k, L.nz, L.ncls)) * L.nr + i) * nm + m;
         const size_t rowstride = (size_t)L.nr * nm;
         V2<T> acc;
-        if (RW && L.rcls && L.invd[tb] == T(0)) return;   // outside a composite domain: u stays 0
+        if (RW && L.holes && L.invd[tb] == T(0)) return;   // outside a composite domain: u stays 0
         if (RW && L.rcls && sizeof(T) == sizeof(double)) {   // per-row tables, FP64: south (hz) and
                                                              // north (hn) couplings apart
             acc = L.bh[idx];
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
         for (int t = 0; t < S; ++t) {
             const int k = k0 + 2 * t;
             if (k >= L.nz) break;
-            if (RW && L.rcls && L.invd[(size_t)L.rcls[k] * rs + tcol] == T(0)) {   // outside the patches
+            if (RW && L.holes && L.invd[(size_t)L.rcls[k] * rs + tcol] == T(0)) {   // outside the patches
                 south = vn[t];
                 continue;
             }

@@ -614,6 +614,7 @@ template <class T, class V> void carve_level(const LevelHost &h, int nm, int nt,
     v.he = c.take<T>(ntab);
     v.hz = c.take<T>(ntab);
     v.rcls = h.rcls.empty() ? nullptr : c.take<int>(h.nz);
+    v.holes = std::find(h.act.begin(), h.act.end(), (unsigned char)0) != h.act.end() ? 1 : 0;
     const bool rw = !h.rcls.empty();
     v.hn = rw ? c.take<T>(ntab) : nullptr;
     const size_t nc = (size_t)h.ncls * h.nr;
