@@ -71,7 +71,7 @@ struct Runner {
     } while (0)
 
 // ---------------------------------------------------------------- work models
-// Per-entry models.  A complex entry is sizeof(V2<T>)
+// Per-entry models of algorithmic bytes and flops.  A complex entry is sizeof(V2<T>)
 // bytes; FMA = 2 flops.  Sums run over the problems a table covers.
 template <class T> const std::vector<LevelDev<T>> &views(const ProblemPlan &q);
 template <> const std::vector<LevelDev<double>> &views<double>(const ProblemPlan &q) { return q.dl; }
