@@ -137,3 +137,20 @@ def test_axial_faces_validated():
     assert B.load().pic_poisson_query(ctypes.byref(d), ctypes.byref(lay)) == B.EINVAL
     lay2 = B.query(_stretched_z(W.annulus(512, 8, 400), 1.002))
     assert lay2["nr"][-1] * lay2["nz"][-1] <= 1024
+    # the no-allocation residual refuses axial faces before touching any pointer
+    d, _ = B.make_desc(_stretched_z(p, 1.1))
+    fake = ctypes.c_void_p(256)
+    assert B.load().pic_poisson_mode_residual_noalloc(ctypes.byref(d), fake, fake, fake, fake, 0) == B.EINVAL
+    assert "axial" in B.last_error()
+
+
+def test_per_row_tables_enlarge_the_workspace():
+    """Per-row tables (one coefficient class per row on an axial mesh) cost
+    workspace in proportion to the rows; a composite domain adds only its few
+    classes and the dense coarsest factors."""
+    p = W.annulus(64, 16, 48)
+    base = B.query(p)["workspace_bytes"]
+    axial = B.query(_stretched_z(p, 1.05))["workspace_bytes"]
+    comp = B.query(W.channel_plume(64, 16, 48))["workspace_bytes"]
+    assert axial > base and comp > base
+    assert axial - base > comp - base
