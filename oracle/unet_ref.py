@@ -13,6 +13,13 @@ Architecture (channels; H x W halves at each pooling):
   d1 = relu(conv([up(d2), e1], 64 -> 16));  d0 = relu(conv([up(d1), e0], 32 -> 16));
   y  = conv(d0, 16 -> 16)  (channels 0 and 1 are the prediction)
 Weights are given as {name: (w[9][cout][cin], b[cout])} with tap = 3 (dy + 1) + (dx + 1).
+
+Pins (tests/test_oracle_unet.py): the convolution against an explicit
+nine-tap sum, pooling and upsampling against their block definitions and
+each other's adjoint, every layer of forward() against the architecture
+above written with those explicit loops (a planted swap of the skip
+concatenation fails it), and the gradients of loss_and_grads() against
+central differences of its loss.
 """
 import torch
 import torch.nn.functional as F
@@ -27,18 +34,35 @@ def _conv(x, wb):
     return F.conv2d(x, k, b, padding=1)
 
 
-def forward(params, x):
-    """x: float64 [N, 16, H, W] (NCHW); returns y [N, 16, H, W]."""
+def pool(t):
+    """2x2 average pooling (each output the mean of its 2x2 input block)."""
+    return F.avg_pool2d(t, 2)
+
+
+def up(t):
+    """Nearest 2x upsampling (each input value copied to its 2x2 output block)."""
+    return F.interpolate(t, scale_factor=2, mode="nearest")
+
+
+def cat(a, b):
+    """Channel concatenation, a's channels first."""
+    return torch.cat([a, b], dim=1)
+
+
+def forward(params, x, acts=None):
+    """x: float64 [N, 16, H, W] (NCHW); returns y [N, 16, H, W].  If acts is a
+    dict, the layer outputs e0 .. d0 are stored in it."""
     r = torch.relu
     e0 = r(_conv(x, params["e0"]))
-    e1 = r(_conv(F.avg_pool2d(e0, 2), params["e1"]))
-    e2 = r(_conv(F.avg_pool2d(e1, 2), params["e2"]))
-    b1 = r(_conv(F.avg_pool2d(e2, 2), params["b1"]))
+    e1 = r(_conv(pool(e0), params["e1"]))
+    e2 = r(_conv(pool(e1), params["e2"]))
+    b1 = r(_conv(pool(e2), params["b1"]))
     b2 = r(_conv(b1, params["b2"]))
-    up = lambda t: F.interpolate(t, scale_factor=2, mode="nearest")
-    d2 = r(_conv(torch.cat([up(b2), e2], dim=1), params["d2"]))
-    d1 = r(_conv(torch.cat([up(d2), e1], dim=1), params["d1"]))
-    d0 = r(_conv(torch.cat([up(d1), e0], dim=1), params["d0"]))
+    d2 = r(_conv(cat(up(b2), e2), params["d2"]))
+    d1 = r(_conv(cat(up(d2), e1), params["d1"]))
+    d0 = r(_conv(cat(up(d1), e0), params["d0"]))
+    if acts is not None:
+        acts.update(e0=e0, e1=e1, e2=e2, b1=b1, b2=b2, d2=d2, d1=d1, d0=d0)
     return _conv(d0, params["out"])
 
 

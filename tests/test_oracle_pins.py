@@ -77,12 +77,59 @@ def test_worked_stencil_dirichlet_east(golden):
 
 
 def test_two_cell_shifted_family_golden(golden):
-    """A_m = A_0 + lambda M with the paper's two-cell numbers, then the same
-    identity on the oracle's own operator (mode restriction of A_3D)."""
+    """The appendix's two-cell example built as cells of a grid and assembled
+    by the oracle's 3-D operator.
+
+    The paper gives the two cells only through their numbers: a shared face
+    of conductance 2, mode-independent diagonals 8 and 9 "including their
+    other faces", mu = 0.5 and 0.4, lambda = 3.  Two axially adjacent cells
+    of one radial column, with radial neighbours on both sides and axial
+    neighbours above and below, realise them (the geometry below follows
+    from the appendix's conductance formulas); the 2 x 2 block of the
+    oracle's A_0 and A_m on those cells, read off apply3d with theta-constant
+    and cos(2 pi m j / N) inputs, must be the printed matrices."""
     g0 = golden("two_cell.txt")
-    A0 = np.array(g0["A0"]).reshape(2, 2)
-    M = np.diag(g0["M"])
-    np.testing.assert_array_equal(A0 + g0["lambda"][0] * M, np.array(g0["Am"]).reshape(2, 2))
+    A0_paper = np.array(g0["A0"]).reshape(2, 2)
+    Am_paper = np.array(g0["Am"]).reshape(2, 2)
+    mu1, mu2 = g0["M"]
+    lam_m = g0["lambda"][0]
+    G, D1, D2 = -A0_paper[0, 1], A0_paper[0, 0], A0_paper[1, 1]
+    # column of width a at centre c; heights h1, h2 = (mu2 / mu1) h1:
+    #   mu1 = a h1 / c and G = c a / ((h1 + h2) / 2) give a^2 = mu1 G (1 + mu2/mu1) / 2
+    h1 = 1.0
+    h2 = mu2 / mu1 * h1
+    a = math.sqrt(mu1 * G * (h1 + h2) / (2 * h1))
+    c = a * h1 / mu1
+    r1, r2 = c - a / 2, c + a / 2
+    # radial conductances per unit height X = r1/(c - c_w) + r2/(c_e - c), split evenly;
+    # the axial neighbours' conductances c a / d fill the rest of each diagonal
+    X = 5.0
+    cw = c - r1 / (X / 2)
+    ce = c + r2 / (X / 2)
+    r0, r3 = 2 * cw - r1, 2 * ce - r2
+    ds = c * a / (D1 - G - h1 * X)
+    dn = c * a / (D2 - G - h2 * X)
+    h0, h3 = 2 * ds - h1, 2 * dn - h2
+    assert 0 < r0 < r1 and r3 > r2 and h0 > 0 and h3 > 0
+    z = np.cumsum([0.0, h0, h1, h2, h3])
+    # lambda_m = 4 sin^2(pi m / N) / dalpha^2 = lam_m at N = 4, m = 1
+    n, m = 4, 1
+    dalpha = 2 * math.sin(math.pi * m / n) / math.sqrt(lam_m)
+    g = oracle.Grid([r0, r1, r2, r3], z, n, n * dalpha, W.EPS0, 0.0, 0.0, 0.0, 0.0)
+    cells = [(1, 1), (1, 2)]                     # (i, k): the two cells, k = 1 below k = 2
+    assert oracle.cell_coeffs(g, 1, 1)["mu"] == pytest.approx(mu1, rel=1e-14)
+    assert oracle.cell_coeffs(g, 1, 2)["mu"] == pytest.approx(mu2, rel=1e-14)
+    j = np.arange(n)
+    for mode, expect in ((0, A0_paper), (m, Am_paper)):
+        v = np.cos(2 * math.pi * mode * j / n)
+        block = np.zeros((2, 2))
+        for col, (i, k) in enumerate(cells):
+            f = np.zeros((g.nz, g.nr))
+            f[k, i] = 1.0
+            out = oracle.apply3d(g, f[:, None, :] * v[None, :, None])
+            for row, (ii, kk) in enumerate(cells):
+                block[row, col] = out[kk, 0, ii]        # v_0 = 1
+        np.testing.assert_allclose(block, expect, rtol=1e-13, atol=1e-13 * np.abs(expect).max())
 
 
 # ---------------------------------------------------------------- eigenvalue identity
