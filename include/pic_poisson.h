@@ -239,7 +239,9 @@ int pic_poisson_set_stream(pic_poisson_plan_t plan, void *stream);
  * Full solve: rho_dev (nz, ntheta, nr) FP64 charge density -> phi_dev (same
  * shape) FP64 potential.  V-cycles run until the relative residual of the
  * three-dimensional system, ||b - A phi||_2 / ||b||_2, is <= tol (tol <= 0:
- * until the residual stops decreasing, the rounding floor).  The residual is
+ * to the rounding floor -- until six convergence tests in a row have not
+ * brought the residual below half of its value at the last halving, or
+ * max_cycles).  The residual is
  * measured in mode space with Parseval weights 1 (m = 0, N/2) and 2 (others).
  * The convergence test runs on the device; without PIC_POISSON_GRAPH the host
  * reads its flag after every test (one small copy and stream synchronisation
@@ -429,7 +431,11 @@ int pic_poisson_mode_residual(pic_poisson_plan_t plan, const double *uhat_dev, c
  * and ntheta <= 256; larger problems are rejected with PIC_POISSON_EINVAL.
  * The first call on a device looks up that array's device address with
  * cudaGetSymbolAddress (device current at the call); make that first call
- * before any stream capture.  Every call reuses the same array; each call
+ * before any stream capture.  The address is kept per device together with
+ * the id of the context it was looked up in, and looked up again when the
+ * current context differs (after cudaDeviceReset, for example).  Non-finite
+ * r_in, r_out, z0, z1 or theta_span are rejected with PIC_POISSON_EINVAL
+ * (theta_span <= 0 selects 2 pi).  Every call reuses the same array; each call
  * writes every partial it later reads, so nothing needs clearing, but calls
  * whose work overlaps on the GPU (different streams, or devices sharing a
  * context) race on the array and must be serialised by the caller.

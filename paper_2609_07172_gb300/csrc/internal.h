@@ -172,6 +172,13 @@ struct FFTTab {
 };
 
 // Device-side state of the convergence loop (one per plan).
+// tol <= 0 (solve to the rounding floor): the loop stops once the relative
+// residual has not fallen below half of its last reference value (the value
+// at the last halving) in this many consecutive convergence tests.  Six
+// tolerates a contraction of up to 0.89 per test, as on strongly stretched
+// meshes where the point smoother loses much of its effect.
+constexpr int kFloorWindow = 6;
+
 struct Ctrl {
     double tol;                   // per solve
     int max_cycles;               // per solve
@@ -183,7 +190,7 @@ struct Ctrl {
     int scaled;                   // residual partials are of the sigma-scaled residual (mixed)
     double bnorm2[kMaxBatch];     // Parseval-weighted ||b||^2
     double rel[kMaxBatch];        // latest relative residual
-    double best[kMaxBatch];       // best relative residual (floor detection)
+    double best[kMaxBatch];       // reference relative residual: the value at the last halving (floor detection)
     double sigma_used[kMaxBatch]; // mixed: scale of the correction problem being solved
     double inv_sigma_used[kMaxBatch];
     double sigma_next[kMaxBatch]; // mixed: scale for the next defect

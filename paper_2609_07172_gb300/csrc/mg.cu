@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
         for (int t = 0; t < S; ++t) {
             const int k = k0 + 2 * t;
             if (k >= L.nz) break;
-            if (RW && L.holes && L.invd[(size_t)L.rcls[k] * rs + tcol] == T(0)) {   // outside the patches
+            if (RW && L.rcls && L.holes && L.invd[(size_t)L.rcls[k] * rs + tcol] == T(0)) {   // outside the patches
                 south = vn[t];
                 continue;
             }
@@ -826,12 +826,11 @@ __global__ void __launch_bounds__(1024) k_check(Ctrl *__restrict__ ctrl, const d
                 status = PIC_POISSON_ENONFINITE;
             } else if (tol > 0.0) {
                 stop = rel <= tol;
-            } else if (rel < 0.5 * ctrl->best[p]) {
+            } else if (rel < 0.5 * ctrl->best[p]) {   // halved since the last reference point
                 ctrl->best[p] = rel;
                 ctrl->stall[p] = 0;
-            } else {
-                ctrl->best[p] = fmin(ctrl->best[p], rel);
-                stop = ++ctrl->stall[p] >= 2;
+            } else {   // rounding floor: no halving within kFloorWindow tests in a row
+                stop = ++ctrl->stall[p] >= kFloorWindow;
             }
             if (!stop && cycles >= ctrl->max_cycles) {
                 stop = 1;

@@ -10,6 +10,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "internal.h"
 
 namespace pp {
@@ -117,10 +119,62 @@ __global__ void __launch_bounds__(1024) k_finish_noalloc(const double *__restric
 }
 
 std::mutex g_na_mutex;
-double *g_na_ptr[NA_MAX_DEVICES] = {};
+struct NAScratchAddr {
+    unsigned long long ctx_id;   // context the address belongs to
+    double *ptr;
+};
+NAScratchAddr g_na_addr[NA_MAX_DEVICES] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the array's name as a device address).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Unique id of the calling thread's current context (0 if none is current).
+// A context created after a device reset gets a new id even where its handle
+// value repeats, and the library's module -- with the scratch array -- may
+// then be loaded at another address.  Called with g_na_mutex held.
+int current_context_id(unsigned long long *id) {
+    *id = 0;
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            set_error("driver entry points cuCtxGetCurrent / cuCtxGetId unavailable");
+            return PIC_POISSON_ECUDA;
+        }
+        g_ctx_get_current = (CtxGetCurrentFn)f1;
+        g_ctx_get_id = (CtxGetIdFn)f2;
+    }
+    CUcontext c = nullptr;
+    if (g_ctx_get_current(&c) != CUDA_SUCCESS) {
+        set_error("cuCtxGetCurrent failed");
+        return PIC_POISSON_ECUDA;
+    }
+    if (c && g_ctx_get_id(c, id) != CUDA_SUCCESS) {
+        set_error("cuCtxGetId failed");
+        return PIC_POISSON_ECUDA;
+    }
+    return PIC_POISSON_OK;
+}
+
+int lookup_scratch(double **out) {
+    void *p = nullptr;
+    cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (err != cudaSuccess || !p) {
+        set_error("cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(err));
+        return PIC_POISSON_ECUDA;
+    }
+    *out = (double *)p;
+    return PIC_POISSON_OK;
+}
+
+// Device address of the scratch array in the current context.  Host code
+// cannot use the array's name as a device address, so the address is looked
+// up with cudaGetSymbolAddress once per device and context, and again when
+// the device's context has changed (for instance after cudaDeviceReset).
 int noalloc_scratch(double **out) {
     int dev = 0;
     PP_CUDA(cudaGetDevice(&dev));
@@ -129,16 +183,22 @@ int noalloc_scratch(double **out) {
         return PIC_POISSON_EINVAL;
     }
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (err != cudaSuccess || !p) {
-            set_error("cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(err));
-            return PIC_POISSON_ECUDA;
-        }
-        g_na_ptr[dev] = (double *)p;
+    unsigned long long id = 0;
+    int rc = current_context_id(&id);
+    if (rc) return rc;
+    if (id != 0 && g_na_addr[dev].ptr && g_na_addr[dev].ctx_id == id) {
+        *out = g_na_addr[dev].ptr;
+        return PIC_POISSON_OK;
     }
-    *out = g_na_ptr[dev];
+    double *p = nullptr;
+    rc = lookup_scratch(&p);   // also makes the runtime's context current if none was
+    if (rc) return rc;
+    if (id == 0) {
+        rc = current_context_id(&id);
+        if (rc) return rc;
+    }
+    g_na_addr[dev] = NAScratchAddr{id, p};
+    *out = p;
     return PIC_POISSON_OK;
 }
 
@@ -189,6 +249,11 @@ extern "C" int pic_poisson_mode_residual_noalloc(const pic_poisson_desc *desc, c
     P.r_in = d.r_in;
     P.dr = (d.r_out - d.r_in) / d.nr;
     P.dz = (d.z1 - d.z0) / d.nz;
+    if (!std::isfinite(d.theta_span) || !std::isfinite(d.r_in) || !std::isfinite(d.r_out) ||
+        !std::isfinite(d.z0) || !std::isfinite(d.z1)) {
+        set_error("r_in, r_out, z0, z1 and theta_span must be finite (theta_span <= 0 selects 2 pi)");
+        return PIC_POISSON_EINVAL;
+    }
     const double span = d.theta_span > 0 ? d.theta_span : 2.0 * 3.14159265358979323846;
     const double da = span / d.ntheta;
     for (int m = 0; m < nm; ++m) {

@@ -44,6 +44,12 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
         return PIC_POISSON_EINVAL;
     }
     *d = *in;
+    // face arrays, where given, replace r_in / r_out or z0 / z1 (checked below)
+    if (!std::isfinite(d->theta_span) || (!d->r_faces && !(std::isfinite(d->r_in) && std::isfinite(d->r_out))) ||
+        (!d->z_faces && !(std::isfinite(d->z0) && std::isfinite(d->z1)))) {
+        set_error("r_in, r_out, z0, z1 and theta_span must be finite (theta_span <= 0 selects 2 pi)");
+        return PIC_POISSON_EINVAL;
+    }
     if (d->theta_span <= 0) d->theta_span = 2.0 * kPi;
     if (d->eps0 <= 0) d->eps0 = kEps0;
     if (d->max_cycles <= 0) d->max_cycles = 200;

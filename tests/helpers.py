@@ -61,3 +61,26 @@ def with_bias_walls(p):
     zc = p.z_centres()
     bias = 300.0 * (1.0 - (zc - p.z0) / (p.z1 - p.z0))
     return p.with_r_wall_data(bias, 0.5 * bias)
+
+
+def cond_estimate(g, iters=60, seed=0):
+    """Upper estimate of the 2-norm condition number of the oracle's 3-D
+    operator A (SPD): lambda_max by power iteration on A (a Rayleigh quotient
+    from below, so raised by 25 % for the power iteration's slow convergence
+    at the top of the spectrum), lambda_min
+    by inverse iteration with the oracle's CG solves (from above, lowered by
+    1 %).  The operator is the homogeneous one; wall data only enter b."""
+    h = g.homogeneous()
+    s = oracle.rhs3d(h, np.ones(g.shape))          # b = s rho on the homogeneous grid
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(g.shape)
+    for _ in range(iters):
+        y = oracle.apply3d(h, x)
+        x = y / np.linalg.norm(y)
+    lmax = float(np.vdot(x, oracle.apply3d(h, x)))
+    x = rng.standard_normal(g.shape)
+    for _ in range(8):
+        y, _ = oracle.solve3d(h, x / s, tol=1e-13)  # A y = x
+        x = y / np.linalg.norm(y)
+    lmin = float(np.vdot(x, oracle.apply3d(h, x)))
+    return 1.25 * lmax / (0.99 * lmin)

@@ -7,6 +7,7 @@ pinned to the paper's worked stencil example and compared with the oracle's
 independent coefficient routine.
 """
 import ctypes
+import dataclasses
 import math
 import os
 import re
@@ -153,3 +154,15 @@ def test_cell_coeffs_rejects_non_increasing_faces():
     bad[3] = bad[2]
     with pytest.raises(B.PicPoissonError):
         B.cell_coeffs(p.with_r_faces(bad), 0, 0)
+
+
+@pytest.mark.parametrize("field,value", [("theta_span", float("nan")), ("theta_span", float("inf")),
+                                         ("r_in", float("nan")), ("r_out", float("inf")),
+                                         ("z0", float("-inf")), ("z1", float("inf"))])
+def test_non_finite_geometry_rejected(field, value):
+    """Both the planned entry points and the no-allocation residual refuse
+    non-finite geometry (a NaN span would otherwise propagate into lambda_m)."""
+    p = dataclasses.replace(W.c0_problem(), **{field: value})
+    d, _ = B.make_desc(p)
+    assert B.load().pic_poisson_query(ctypes.byref(d), None) == B.EINVAL
+    assert "finite" in B.last_error()

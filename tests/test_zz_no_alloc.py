@@ -7,6 +7,8 @@ its partial sums in a fixed device array.  This file is collected last so
 that a run stopping at the first failure has already run every other test.
 """
 import ctypes
+import dataclasses
+import math
 
 import numpy as np
 import pytest
@@ -29,9 +31,16 @@ def call_noalloc(p, uhat, bhat, rhat, rel):
     return status
 
 
-@pytest.mark.parametrize("dims", [(96, 16, 40), (512, 128, 200)])
-def test_noalloc_residual_matches_planned_twice(dims):
-    p = with_bias_walls(W.annulus(*dims))
+@pytest.mark.parametrize("dims,span", [
+    ((96, 16, 40), None), ((512, 128, 200), None),
+    # one and two axial rows (the 4- and 3-term Dirichlet axial coefficients),
+    # ntheta = 2 (m = 1 is the Nyquist mode, Parseval weight 1) and a
+    # quarter-annulus period (lambda_m from dalpha = span / ntheta)
+    ((8, 2, 1), None), ((8, 4, 2), None), ((16, 8, 6), math.pi / 2)],
+    ids=["96x16x40", "512x128x200", "8x2x1", "8x4x2", "16x8x6_quarter"])
+def test_noalloc_residual_matches_planned_twice(dims, span):
+    kw = {} if span is None else {"theta_span": span}
+    p = with_bias_walls(W.annulus(*dims, **kw))
     rng = np.random.default_rng(21)
     rho = torch.from_numpy(W.rho_plasma(p, seed=13)).cuda()
     with Plan(p) as plan:
@@ -59,3 +68,12 @@ def test_noalloc_rejects_oversize_problem():
     status = call_noalloc(p, dummy, dummy, None, dummy)
     assert status == B.EINVAL
     assert "at most 16777216 mode entries" in B.last_error()
+
+
+@pytest.mark.parametrize("field,value", [("theta_span", float("nan")), ("theta_span", float("inf")),
+                                         ("r_out", float("inf")), ("z1", float("inf"))])
+def test_noalloc_rejects_non_finite_geometry(field, value):
+    p = dataclasses.replace(W.annulus(16, 8, 6), **{field: value})
+    dummy = torch.zeros(2, dtype=torch.float64, device="cuda")
+    assert call_noalloc(p, dummy, dummy, None, dummy) == B.EINVAL
+    assert "finite" in B.last_error()
