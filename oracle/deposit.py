@@ -26,6 +26,14 @@ charge goes to its cell,
 
 so sum_q rho_q V_q = charge * sum_nu n_nu V_nu = charge * W * (particles
 deposited): charge is conserved by construction.
+
+Composite domain (Sec. 2.2, a union of rectangular patches; the reading):
+particles in inactive cells deposit nothing, a node's control volume counts
+only its octants in active cells, and inactive cells get no charge; the
+conservation identity then holds over the active cells.  Non-uniform faces
+need nothing more: offsets within a cell use its own faces, the node
+intervals run between the neighbouring centres, and a cell's axial octant
+share stays 1/2 (face to centre is half the cell).
 """
 from __future__ import annotations
 
@@ -43,12 +51,36 @@ def _node_extents(f):
 
 
 def node_volumes(g):
-    """V_nu, shape (nz+1, nr+1) (the same for every alpha node)."""
-    rlo, rhi = _node_extents(g.r_faces)
-    zlo, zhi = _node_extents(g.z_faces)
+    """V_nu, shape (nz+1, nr+1) (the same for every alpha node).
+
+    Composite domain (g.active set): only the octants of the node's control
+    volume that lie in active cells count, V_nu = sum over its active
+    neighbour cells q of V(nu in q), so that the projection below conserves
+    the charge deposited in active cells exactly (no particle sits in an
+    inactive cell, and no charge is projected there)."""
+    rf, zf = g.r_faces, g.z_faces
     da = g.L_alpha / g.ntheta
-    # the integral of r dr, (rhi^2 - rlo^2) / 2, factored (no cancellation far from the axis)
-    return da * (zhi - zlo)[:, None] * ((rhi - rlo) * (rhi + rlo) / 2)[None, :]
+    if g.active is None:
+        rlo, rhi = _node_extents(rf)
+        zlo, zhi = _node_extents(zf)
+        # the integral of r dr, (rhi^2 - rlo^2) / 2, factored (no cancellation far from the axis)
+        return da * (zhi - zlo)[:, None] * ((rhi - rlo) * (rhi + rlo) / 2)[None, :]
+    rc, zc = _centres(rf), _centres(zf)
+    nr, nz = rf.size - 1, zf.size - 1
+    # the half cells next to each face: cell i's part toward its lower face (lo) and its upper face (hi)
+    vr_lo = (rc - rf[:-1]) * (rc + rf[:-1]) / 2
+    vr_hi = (rf[1:] - rc) * (rf[1:] + rc) / 2
+    hz = np.diff(zf) / 2
+    act = g.active.astype(bool)
+    vol = np.zeros((nz + 1, nr + 1))
+    for k in range(nz):
+        for i in range(nr):
+            if not act[k, i]:
+                continue
+            for c, vz in ((k, hz[k]), (k + 1, hz[k])):
+                vol[c, i] += da * vz * vr_lo[i]
+                vol[c, i + 1] += da * vz * vr_hi[i]
+    return vol
 
 
 def deposit(g, r, alpha, z, weight):
@@ -62,6 +94,8 @@ def deposit(g, r, alpha, z, weight):
     iz = np.searchsorted(zf, z, side="right") - 1
     ia = np.floor(alpha / da).astype(np.int64)
     ok = (ir >= 0) & (ir < nr) & (iz >= 0) & (iz < nz) & (ia >= 0) & (ia < nt)
+    if g.active is not None:   # a particle in an inactive cell of a composite domain deposits nothing
+        ok[ok] = g.active.astype(bool)[iz[ok], ir[ok]]
     ir, iz, ia = ir[ok], iz[ok], ia[ok]
     xr = (r[ok] - rf[ir]) / (rf[ir + 1] - rf[ir])
     xz = (z[ok] - zf[iz]) / (zf[iz + 1] - zf[iz])
@@ -88,7 +122,10 @@ def project(g, nodes, charge):
     n = np.asarray(nodes, dtype=np.float64)
     ns = n + np.roll(n, -1, axis=1)              # the two alpha nodes of a cell
     nzs = ns[:-1] + ns[1:]                       # and its two z nodes
-    return charge * 0.25 * (flo * nzs[:, :, :-1] + fhi * nzs[:, :, 1:])
+    rho = charge * 0.25 * (flo * nzs[:, :, :-1] + fhi * nzs[:, :, 1:])
+    if g.active is not None:   # composite domain: no charge in inactive cells
+        rho = np.where(np.broadcast_to(g.active.astype(bool)[:, None, :], rho.shape), rho, 0.0)
+    return rho
 
 
 def cell_volumes(g):

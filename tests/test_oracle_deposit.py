@@ -90,3 +90,54 @@ def test_equal_radial_shares_would_break_conservation():
     rho_wrong = 0.25 * 0.5 * (nzs[:, :, :-1] + nzs[:, :, 1:])
     total = (rho_wrong * D.cell_volumes(g)).sum()
     assert abs(total / (W0 * 2000) - 1.0) > 1e-4
+
+
+# ---------------------------------------------------------------- composite domains, stretched faces
+
+def _composite_grid(stretch):
+    p = W.channel_plume(16, 4, 12)
+    if stretch:
+        p = p.with_r_faces(W.stretched_radial_faces(p.r_in, p.r_out, 16, 1.06))
+        w = 1.06 ** np.arange(12)
+        p = p.with_z_faces(p.z0 + (p.z1 - p.z0) * np.r_[0.0, np.cumsum(w)] / w.sum())
+    return oracle.grid_from_problem(p)
+
+
+@pytest.mark.parametrize("stretch", [False, True], ids=["uniform", "stretched"])
+def test_composite_deposit_conserves_the_charge_of_active_cells(stretch):
+    g = _composite_grid(stretch)
+    r, a, z = _particles(g, 6000, 3, outside=5)
+    ir = np.searchsorted(g.r_faces, r, side="right") - 1
+    iz = np.searchsorted(g.z_faces, z, side="right") - 1
+    inb = (ir >= 0) & (ir < g.nr) & (iz >= 0) & (iz < g.nz)
+    n_active = int(g.active.astype(bool)[iz[inb], ir[inb]].sum())
+    assert 0 < n_active < 6000 - 5
+    nodes = D.deposit(g, r, a, z, W0)
+    assert (nodes * D.node_volumes(g)[:, None, :]).sum() == pytest.approx(W0 * n_active, rel=1e-13)
+    rho = D.project(g, nodes, 1.602176634e-19)
+    assert (rho * D.cell_volumes(g)).sum() == pytest.approx(1.602176634e-19 * W0 * n_active, rel=1e-13)
+    act = np.broadcast_to(g.active.astype(bool)[:, None, :], rho.shape)
+    assert np.all(rho[~act] == 0.0)
+
+
+def test_composite_with_full_node_volumes_breaks_conservation():
+    """A planted mistake: nodes on an exposed face keep their whole control
+    volume (the inactive octants included)."""
+    g = _composite_grid(True)
+    r, a, z = _particles(g, 6000, 4)
+    nodes = D.deposit(g, r, a, z, W0)
+    plain = oracle.Grid(g.r_faces, g.z_faces, g.ntheta, g.L_alpha, g.eps0, 0.0, 0.0, 0.0, 0.0)
+    wrong = nodes * D.node_volumes(g)[:, None, :] / D.node_volumes(plain)[:, None, :]
+    rho = D.project(g, wrong, 1.0)
+    ir = np.searchsorted(g.r_faces, r, side="right") - 1
+    iz = np.searchsorted(g.z_faces, z, side="right") - 1
+    n_active = int(g.active.astype(bool)[iz, ir].sum())
+    assert abs((rho * D.cell_volumes(g)).sum() / (W0 * n_active) - 1.0) > 1e-3
+
+
+def test_all_active_composite_deposit_is_the_plain_deposit():
+    g = oracle.grid_from_problem(W.annulus(10, 8, 9))
+    ga = oracle.Grid(g.r_faces, g.z_faces, g.ntheta, g.L_alpha, g.eps0, 0.0, 0.0, 0.0, 0.0,
+                     np.ones((g.nz, g.nr), dtype=bool))
+    r, a, z = _particles(g, 3000, 5)
+    np.testing.assert_allclose(D.deposit(ga, r, a, z, W0), D.deposit(g, r, a, z, W0), rtol=1e-14, atol=0)

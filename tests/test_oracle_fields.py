@@ -64,3 +64,55 @@ def test_a_wrong_arc_length_fails_the_gauss_law():
     ea_wrong = ea * rc / g.r_faces[1:]
     res, scale = F.gauss_residual(g, rho, er, ea_wrong, ez)
     assert np.abs(res).max() > 1e-3 * scale
+
+
+# ---------------------------------------------------------------- composite domains, stretched faces
+
+def _channel_plume_stretched(nr=16, nt=4, nz=12, ratio=1.06):
+    """The channel-plume topology (Sec. 2.2) on faces stretched in r and z,
+    with exposed faces at 40 V."""
+    p = W.channel_plume(nr, nt, nz)
+    p = p.with_r_faces(W.stretched_radial_faces(p.r_in, p.r_out, nr, ratio))
+    w = ratio ** np.arange(nz)
+    p = p.with_z_faces(p.z0 + (p.z1 - p.z0) * np.r_[0.0, np.cumsum(w)] / w.sum())
+    return p.with_patches(p.patches, phi_exposed=40.0)
+
+
+@pytest.mark.parametrize("stretched", [False, True], ids=["uniform", "stretched"])
+def test_gauss_law_on_a_composite_domain(stretched):
+    p = _channel_plume_stretched() if stretched else W.channel_plume(16, 4, 12).with_patches(
+        W.channel_plume(16, 4, 12).patches, phi_exposed=40.0)
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=31)
+    phi, _ = oracle.solve3d(g, rho, tol=1e-15)
+    er, ea, ez = F.face_field(g, phi)
+    res, scale = F.gauss_residual(g, rho, er, ea, ez)
+    assert np.abs(res).max() <= 1e-11 * scale
+    # no field where no active cell is
+    act = g.active.astype(bool)
+    assert np.all(ea[:, :, :][np.broadcast_to(~act[:, None, :], ea.shape)] == 0.0)
+
+
+def test_exposed_faces_differenced_as_interior_faces_fail_the_gauss_law():
+    """A planted mistake: the face between an active and an inactive cell
+    differenced centre to centre against the inactive cell's phi = 0, as if
+    it were an interior face."""
+    p = _channel_plume_stretched()
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=32)
+    phi, _ = oracle.solve3d(g, rho, tol=1e-15)
+    plain = oracle.Grid(g.r_faces, g.z_faces, g.ntheta, g.L_alpha, g.eps0, g.phi_rin, g.phi_rout,
+                        g.phi_z0, g.phi_z1)
+    er, ea, ez = F.face_field(plain, phi)
+    res, scale = F.gauss_residual(g, rho, er, ea, ez)
+    assert np.abs(res).max() > 1e-3 * scale
+
+
+def test_all_active_composite_field_is_the_plain_field():
+    p = W.annulus(10, 4, 8)
+    g = oracle.grid_from_problem(p)
+    ga = oracle.Grid(g.r_faces, g.z_faces, g.ntheta, g.L_alpha, g.eps0, g.phi_rin, g.phi_rout, g.phi_z0,
+                     g.phi_z1, np.ones((g.nz, g.nr), dtype=bool), 77.0)
+    phi = np.random.default_rng(3).normal(size=g.shape)
+    for a, b in zip(F.face_field(g, phi), F.face_field(ga, phi)):
+        np.testing.assert_array_equal(a, b)
