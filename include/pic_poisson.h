@@ -99,14 +99,12 @@ typedef struct {
                                   to r_out.  Given, they define r_in and r_out (the fields above are
                                   ignored); cell centres are face midpoints and the coefficients follow
                                   the appendix's face-conductance formulas on them.  The axial spacing
-                                  stays uniform.  pic_poisson_deposit and the no-allocation residual
-                                  need uniform faces. */
+                                  stays uniform.  The no-allocation residual needs uniform faces. */
     const double *z_faces;     /* host, nz + 1 strictly increasing axial faces, or NULL: uniform from z0
                                   to z1.  Given, they define z0 and z1; the coefficients are built row by
                                   row from them (per-row tables, a dense coarsest solve of at most
-                                  PIC_POISSON_MAX_DENSE cells).  Not with smooth_fused,
-                                  pic_poisson_face_field, pic_poisson_deposit or the no-allocation
-                                  residual. */
+                                  PIC_POISSON_MAX_DENSE cells).  Not with smooth_fused or the
+                                  no-allocation residual. */
     double eps0;               /* vacuum permittivity; <= 0 selects 8.8541878128e-12 F/m */
     int precision;             /* PIC_POISSON_FP64 or PIC_POISSON_MIXED */
     int max_cycles;            /* V-cycle cap; <= 0 selects 200 */
@@ -124,9 +122,13 @@ typedef struct {
     int local_bottom;          /* 0: the level above the coarsest and the coarsest solve run per mode in
                                   one block's shared memory where they fit (omega = 1, 3 or more levels);
                                   -1: never (separate launches) */
-    int fmg;                   /* FP64: 1 starts a solve from a zero iterate with a full-multigrid pass
-                                  (right-hand side restricted to every level, coarsest solve, then
-                                  prolongation and one V-cycle per level up to the finest); 0 from zero */
+    int fmg;                   /* FP64: 1 starts a solve with a full-multigrid pass: from a zero iterate,
+                                  the right-hand side restricted to every level, coarsest solve, then
+                                  prolongation and one V-cycle per level up to the finest; from a given
+                                  iterate (PIC_POISSON_USE_INITIAL_GUESS, pic_poisson_solve_modes) the
+                                  same on its correction equation (level 0 pre-smoothed and its residual
+                                  restricted, the coarser levels as above, the correction prolongated
+                                  into level 0 and post-smoothed); 0: no such start */
     int inner_first;           /* mixed precision: FP32 V-cycles of the first defect correction of a solve;
                                   <= inner_cycles (0 included) selects inner_cycles.  A larger first
                                   correction can save one FP64 defect, update and convergence test */
@@ -143,8 +145,7 @@ typedef struct {
                                   a direction only while every patch boundary in it lies on a coarse
                                   face (protected faces); the coarsest level is solved densely and may
                                   hold at most PIC_POISSON_MAX_DENSE active cells.  Not with
-                                  smooth_fused, pic_poisson_face_field, pic_poisson_deposit or the
-                                  no-allocation residual. */
+                                  smooth_fused or the no-allocation residual. */
     double phi_exposed;        /* Dirichlet potential of the exposed faces (V) */
     unsigned flags;            /* PIC_POISSON_* flags */
 } pic_poisson_desc;
@@ -349,8 +350,14 @@ int pic_poisson_solve_host(pic_poisson_plan_t plan, const double *rho_host, doub
  * additions, hence rounding, varies from run to run).  The weights' products
  * and those sums are double-float (about 48 significant bits, ~1e-14
  * relative); cell, offset and the atomics are binary64.
- * Particles outside the domain deposit nothing.  Single-problem plans; on
- * the plan's stream (asynchronous).
+ * Particles outside the domain deposit nothing.  On non-uniform faces
+ * (r_faces, z_faces) the cell is the one the face arrays define (max{a :
+ * face[a] <= x}, found by a lookup guess and exact binary64 comparisons) and
+ * the offsets use that cell's faces.  On a composite domain (patches) a
+ * particle in an inactive cell deposits nothing and V_nu counts only the
+ * node's octants in active cells, so the projection conserves the active
+ * cells' charge exactly.  Single-problem plans; on the plan's stream
+ * (asynchronous).
  */
 int pic_poisson_deposit(pic_poisson_plan_t plan, const double *r_dev, const double *alpha_dev, const double *z_dev,
                         long long np, double weight, double *nodes_dev);
@@ -363,8 +370,9 @@ int pic_poisson_deposit(pic_poisson_plan_t plan, const double *r_dev, const doub
  *   rho_q = charge * sum over the corners nu of q of n_nu V_(nu in q) / V_q,
  * which conserves charge exactly.  rho_dev (nz, ntheta, nr) FP64 is
  * overwritten (accumulate = 0) or added to (accumulate != 0; e.g. ions, then
- * electrons with the opposite charge).  Single-problem plans; on the plan's
- * stream (asynchronous).
+ * electrons with the opposite charge).  On a composite domain inactive
+ * cells get rho = 0.  Single-problem plans; on the plan's stream
+ * (asynchronous).
  */
 int pic_poisson_project(pic_poisson_plan_t plan, const double *nodes_dev, double charge, int accumulate,
                         double *rho_dev);
@@ -382,7 +390,12 @@ int pic_poisson_project(pic_poisson_plan_t plan, const double *nodes_dev, double
  * interior_face_conductances, dirichlet_face_conductances): centre to centre,
  * centre to wall at a Dirichlet face, r_i dalpha azimuthally; so for the
  * discrete solution the face fluxes of every cell sum to rho V / eps0.
- * Single-problem plans; enqueued on the plan's stream (asynchronous).
+ * Non-uniform faces use their own centre distances.  On a composite domain
+ * (Sec. 2.2) a face between an active and an inactive cell is differenced
+ * from the active cell's centre to the face at phi_exposed (the exposed
+ * face's Dirichlet distance), and faces with no active cell on either side
+ * get E = 0.  Single-problem plans; enqueued on the plan's stream
+ * (asynchronous).
  */
 int pic_poisson_face_field(pic_poisson_plan_t plan, const double *phi_dev, double *er_dev, double *ea_dev,
                            double *ez_dev);

@@ -20,6 +20,13 @@
 // order of the additions changes.  Particles outside the domain deposit
 // nothing.
 //
+// Non-uniform faces and composite domains (k_deposit<true>): the cell comes
+// from the face arrays (a bin lookup guesses, binary64 comparisons decide),
+// the offsets from the cell's own faces; in a composite domain (Sec. 2.2) a
+// particle in an inactive cell deposits nothing and a node's volume counts
+// only its octants in active cells, so the projection below conserves the
+// active cells' charge; inactive cells get rho = 0.
+//
 // Projection (Sec. 2, "volume-consistent projection to cell-centred
 // charge"; the paper gives no formula -- the reading): each node's control
 // volume is split into the octants inside its adjacent cells and an
@@ -46,7 +53,32 @@ struct DepositArgs {
     const double *inv_vr;   // [nr + 1] 1 / (radial integral of r dr of node a's interval)
     const double *inv_vz;   // [nz + 1] 1 / (dalpha * axial length of node c's interval)
     double *nodes;          // (nz + 1, nt, nr + 1)
+    // GEN (non-uniform faces or a composite domain): the cell is found on the
+    // face arrays -- a lookup bin guesses it, exact comparisons settle it
+    const double *rf, *zf;          // faces [nr + 1], [nz + 1]
+    const double *inv_wr, *inv_wz;  // 1 / cell widths
+    const int *rbin, *zbin;         // cell at the lower end of each bin
+    int nrbin, nzbin;
+    float r0f, z0f, inv_rbw, inv_zbw;
+    const unsigned char *act;       // composite: active flags [nz][nr] (null: all active)
+    const double *inv_v2;           // composite: 1 / node volumes of active octants [nz + 1][nr + 1]
 };
+
+// Cell of coordinate x on faces f[0..n] (max{a : f[a] <= x}), or -1 outside
+// [f[0], f[n]).  The binary32 bin lookup only guesses; the binary64
+// comparisons against the faces decide, so the cell is exactly the one the
+// face array defines (a guess off by any amount still ends right, the loops
+// are bounded by n).
+__device__ __forceinline__ int find_cell(double x, const double *f, int n, const int *bin, int nbin, float x0,
+                                         float inv_bw) {
+    if (!(x >= f[0] && x < f[n])) return -1;   // NaN included
+    int b = (int)(((float)x - x0) * inv_bw);
+    b = b < 0 ? 0 : (b >= nbin ? nbin - 1 : b);
+    int a = bin[b];
+    while (a > 0 && x < f[a]) --a;
+    while (a < n - 1 && x >= f[a + 1]) ++a;
+    return a;
+}
 
 constexpr int DEP_PPT = 4;   // consecutive particles per thread
 
@@ -55,17 +87,38 @@ constexpr int DEP_PPT = 4;   // consecutive particles per thread
 // when p is absent or outside.  The position arithmetic (cell, offset in the
 // cell) is binary64; the weights' products are double-float, on the FP32
 // pipe -- the deposit's FP64 instructions were its bound.
+template <bool GEN>
 __device__ __forceinline__ bool cic_weights(const DepositArgs &a, long long p, int &ir, int &ia, int &iz, df c[8]) {
     if (p >= a.np) return false;
-    const double tr = (a.r[p] - a.r_in) * a.inv_dr, ta = a.al[p] * a.inv_da, tz = (a.z[p] - a.z0) * a.inv_dz;
-    const double fr = floor(tr), fa = floor(ta), fz = floor(tz);
-    // in range before any conversion (NaN compares false)
-    if (!(fr >= 0.0 && fr < (double)a.nr && fa >= 0.0 && fa < (double)a.nt && fz >= 0.0 && fz < (double)a.nz))
-        return false;
-    ir = (int)fr;
-    ia = (int)fa;
-    iz = (int)fz;
-    const double xr = tr - fr, xa = ta - fa, xz = tz - fz;   // exact, in [0, 1)
+    double xr, xa, xz;
+    if (GEN) {
+        const double r = a.r[p], z = a.z[p], ta = a.al[p] * a.inv_da;
+        const double fa = floor(ta);
+        if (!(fa >= 0.0 && fa < (double)a.nt)) return false;
+        ir = find_cell(r, a.rf, a.nr, a.rbin, a.nrbin, a.r0f, a.inv_rbw);
+        iz = find_cell(z, a.zf, a.nz, a.zbin, a.nzbin, a.z0f, a.inv_zbw);
+        if (ir < 0 || iz < 0) return false;
+        if (a.act && !a.act[(size_t)iz * a.nr + ir]) return false;   // inactive cell: nothing deposited
+        ia = (int)fa;
+        xr = (r - a.rf[ir]) * a.inv_wr[ir];
+        xz = (z - a.zf[iz]) * a.inv_wz[iz];
+        xa = ta - fa;
+        // the products may round to 1 at the upper face; the weights stay in [0, 1]
+        xr = fmin(xr, 1.0);
+        xz = fmin(xz, 1.0);
+    } else {
+        const double tr = (a.r[p] - a.r_in) * a.inv_dr, ta = a.al[p] * a.inv_da, tz = (a.z[p] - a.z0) * a.inv_dz;
+        const double fr = floor(tr), fa = floor(ta), fz = floor(tz);
+        // in range before any conversion (NaN compares false)
+        if (!(fr >= 0.0 && fr < (double)a.nr && fa >= 0.0 && fa < (double)a.nt && fz >= 0.0 && fz < (double)a.nz))
+            return false;
+        ir = (int)fr;
+        ia = (int)fa;
+        iz = (int)fz;
+        xr = tr - fr;   // exact, in [0, 1)
+        xa = ta - fa;
+        xz = tz - fz;
+    }
     const df r1 = split_scaled(xr, 1023), r0 = split_scaled(1.0 - xr, 1023);
     const df a1 = split_scaled(xa, 1023), a0 = split_scaled(1.0 - xa, 1023);
     const df z1 = split_scaled(xz, 1023), z0 = split_scaled(1.0 - xz, 1023);
@@ -84,14 +137,16 @@ __device__ __forceinline__ bool cic_weights(const DepositArgs &a, long long p, i
 }
 
 // The eight atomic additions of a run's sums to the corners of cell (ir, ia, iz).
+template <bool GEN>
 __device__ __forceinline__ void add_corners(const DepositArgs &a, int ir, int ia, int iz, const df c[8]) {
     const int ja = ia + 1 == a.nt ? 0 : ia + 1;
     const size_t rs = (size_t)a.nr + 1, ps = (size_t)a.nt * rs;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         const int nzi = iz + (d >> 2), nai = (d & 2) ? ja : ia, nri = ir + (d & 1);
-        atomicAdd(a.nodes + (size_t)nzi * ps + (size_t)nai * rs + nri,
-                  to_double(c[d], a.w_exp) * a.inv_vr[nri] * a.inv_vz[nzi]);
+        const double v = (GEN && a.inv_v2) ? to_double(c[d], a.w_exp) * a.inv_v2[(size_t)nzi * rs + nri]
+                                           : to_double(c[d], a.w_exp) * a.inv_vr[nri] * a.inv_vz[nzi];
+        atomicAdd(a.nodes + (size_t)nzi * ps + (size_t)nai * rs + nri, v);
     }
 }
 
@@ -99,6 +154,7 @@ __device__ __forceinline__ void add_corners(const DepositArgs &a, int ir, int ia
 // in registers (a cell change inside the chunk sends the finished run's sums
 // straight to the nodes); then the threads' last runs are aggregated across
 // the warp.
+template <bool GEN>
 __global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
     const long long t0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * DEP_PPT;
     const int lane = threadIdx.x & 31;
@@ -112,9 +168,9 @@ __global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
     for (int t = 0; t < DEP_PPT; ++t) {
         df c[8];
         int ir, ia, iz;
-        if (!cic_weights(a, t0 + t, ir, ia, iz, c)) continue;
+        if (!cic_weights<GEN>(a, t0 + t, ir, ia, iz, c)) continue;
         if (have && (ir != cr || ia != ca || iz != cz)) {
-            add_corners(a, cr, ca, cz, acc);
+            add_corners<GEN>(a, cr, ca, cz, acc);
             have = false;
         }
         if (!have) {
@@ -144,7 +200,7 @@ __global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
         }
     }
     const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
-    if (have && last) add_corners(a, cr, ca, cz, acc);
+    if (have && last) add_corners<GEN>(a, cr, ca, cz, acc);
 }
 
 struct ProjectArgs {
@@ -153,8 +209,10 @@ struct ProjectArgs {
     const double *flo, *fhi;   // [nr] radial shares of a cell's lower / upper corner nodes
     const double *nodes;
     double *rho;
+    const unsigned char *act;  // MASK: active flags [nz][nr]; inactive cells get no charge
 };
 
+template <bool MASK>
 __global__ void __launch_bounds__(256) k_project(const ProjectArgs a) {
     const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;   // (k, j, i), i fastest
     const unsigned nr = (unsigned)a.nr;
@@ -168,7 +226,8 @@ __global__ void __launch_bounds__(256) k_project(const ProjectArgs a) {
     // the four (alpha, z) nodes at radius a = i and at a = i + 1
     const double lo = (n0[j * rs + i] + n0[jn * rs + i]) + (n1[j * rs + i] + n1[jn * rs + i]);
     const double hi = (n0[j * rs + i + 1] + n0[jn * rs + i + 1]) + (n1[j * rs + i + 1] + n1[jn * rs + i + 1]);
-    const double v = a.charge * 0.25 * (a.flo[i] * lo + a.fhi[i] * hi);
+    double v = a.charge * 0.25 * (a.flo[i] * lo + a.fhi[i] * hi);
+    if (MASK && !a.act[(size_t)k * nr + i]) v = 0.0;
     a.rho[e] = a.accumulate ? a.rho[e] + v : v;
 }
 
@@ -181,10 +240,6 @@ namespace {
 int single(const pic_poisson_plan_s *P, const char *what) {
     if (P->n != 1) {
         set_error("%s needs a single-problem plan (this plan holds %d problems)", what, P->n);
-        return PIC_POISSON_EINVAL;
-    }
-    if (P->pr[0].nact > 0) {
-        set_error("%s does not take a composite domain or non-uniform axial mesh (patches or z_faces)", what);
         return PIC_POISSON_EINVAL;
     }
     return PIC_POISSON_OK;
@@ -202,10 +257,6 @@ extern "C" int pic_poisson_deposit(pic_poisson_plan_t plan, const double *r_dev,
         return PIC_POISSON_EINVAL;
     }
     const ProblemPlan &q = plan->pr[0];
-    if (!q.uniform_r) {
-        set_error("pic_poisson_deposit needs a uniform radial mesh (the plan has r_faces)");
-        return PIC_POISSON_EINVAL;
-    }
     if (np == 0) return PIC_POISSON_OK;
     const LevelHost &h = q.lv[0];
     DepositArgs a{};
@@ -231,12 +282,30 @@ extern "C" int pic_poisson_deposit(pic_poisson_plan_t plan, const double *r_dev,
     a.inv_vr = q.dep_inv_vr;
     a.inv_vz = q.dep_inv_vz;
     a.nodes = nodes_dev;
+    const bool gen = !q.uniform_r || !h.zf.empty() || q.act0;
+    if (gen) {
+        a.rf = q.dep_rf;
+        a.zf = q.dep_zf;
+        a.inv_wr = q.dep_inv_wr;
+        a.inv_wz = q.dep_inv_wz;
+        a.rbin = q.dep_rbin;
+        a.zbin = q.dep_zbin;
+        a.nrbin = q.dep_nrbin;
+        a.nzbin = q.dep_nzbin;
+        a.r0f = (float)h.rf[0];
+        a.z0f = (float)(h.zf.empty() ? q.d.z0 : h.zf[0]);
+        a.inv_rbw = q.dep_inv_rbw;
+        a.inv_zbw = q.dep_inv_zbw;
+        a.act = q.act0;
+        a.inv_v2 = q.dep_inv_v2;
+    }
     const long long blocks = (np + 256LL * DEP_PPT - 1) / (256LL * DEP_PPT);
     if (blocks > 0x7fffffffLL) {
         set_error("pic_poisson_deposit: too many particles for one launch (%lld)", np);
         return PIC_POISSON_EINVAL;
     }
-    k_deposit<<<(unsigned)blocks, 256, 0, plan->stream>>>(a);
+    if (gen) k_deposit<true><<<(unsigned)blocks, 256, 0, plan->stream>>>(a);
+    else k_deposit<false><<<(unsigned)blocks, 256, 0, plan->stream>>>(a);
     PP_CUDA(cudaGetLastError());
     return PIC_POISSON_OK;
 }
@@ -263,8 +332,10 @@ extern "C" int pic_poisson_project(pic_poisson_plan_t plan, const double *nodes_
     a.fhi = q.dep_fhi;
     a.nodes = nodes_dev;
     a.rho = rho_dev;
+    a.act = q.act0;
     const size_t n = (size_t)a.nz * a.nt * a.nr;
-    k_project<<<(unsigned)((n + 255) / 256), 256, 0, plan->stream>>>(a);
+    if (q.act0) k_project<true><<<(unsigned)((n + 255) / 256), 256, 0, plan->stream>>>(a);
+    else k_project<false><<<(unsigned)((n + 255) / 256), 256, 0, plan->stream>>>(a);
     PP_CUDA(cudaGetLastError());
     return PIC_POISSON_OK;
 }

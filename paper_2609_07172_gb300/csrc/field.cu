@@ -15,6 +15,8 @@
 // also the wall face.  The differences are binary64 (one subtraction and one
 // multiplication by a precomputed inverse distance per face), so on this GPU
 // the kernel is bound by the FP64 pipe rather than by its 4 arrays of traffic.
+// Non-uniform axial faces and composite domains take a variant with an axial
+// distance table and, for patches, exposed faces (k_face_field_gen).
 #include "plan.h"
 
 namespace pp {
@@ -54,6 +56,67 @@ __global__ void __launch_bounds__(256) k_face_field(const FieldArgs a) {
     if (k == a.nz - 1) a.ez[e + plane] = (p - a.phi_z1) * a.inv_hdz;
 }
 
+// The same on non-uniform axial faces and composite domains.  Axial
+// distances come from a table like the radial ones.  With MASK (a composite
+// domain, Sec. 2.2): a face between an active and an inactive cell is a
+// Dirichlet face at phi_exposed, differenced from the active cell's centre
+// to the face (the distance of the exposed face's conductance); faces with no
+// active cell on either side, wall faces of inactive cells included, get
+// E = 0.  The plain kernel above is unchanged for plain plans.
+struct FieldGenArgs {
+    FieldArgs a;
+    const double *inv_zd;                      // [nz + 1] 1 / axial distance across face c
+    const double *inv_half;                    // 1 / centre-to-face: r lower, r upper [nr]; z lower, z upper [nz]
+    const unsigned char *act;                  // [nz][nr] active flags (MASK)
+    double pe;                                 // phi_exposed
+};
+
+template <bool MASK>
+__global__ void __launch_bounds__(256) k_face_field_gen(const FieldGenArgs g) {
+    const FieldArgs &a = g.a;
+    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned nr = (unsigned)a.nr, row_n = (unsigned)a.nz * (unsigned)a.nt;
+    if (e >= row_n * nr) return;
+    const unsigned row = e / nr;
+    const int i = (int)(e - row * nr);
+    const int k = (int)(row / (unsigned)a.nt), j = (int)(row - (unsigned)k * a.nt);
+    const double p = a.phi[e];
+    const bool ai = !MASK || g.act[(size_t)k * nr + i];
+    const double *ihr_lo = g.inv_half, *ihr_hi = g.inv_half + a.nr;
+    const double *ihz_lo = g.inv_half + 2 * a.nr, *ihz_hi = ihz_lo + a.nz;
+    // radial face i
+    const size_t fr = (size_t)row * (nr + 1) + i;
+    double vr;
+    if (i == 0) {
+        vr = ai ? (a.win[k] - p) * a.inv_rd[0] : 0.0;
+    } else {
+        const bool aw = !MASK || g.act[(size_t)k * nr + i - 1];
+        if (ai && aw) vr = (a.phi[e - 1] - p) * a.inv_rd[i];
+        else if (aw) vr = (a.phi[e - 1] - g.pe) * ihr_hi[i - 1];   // exposed face east of cell i - 1
+        else if (ai) vr = (g.pe - p) * ihr_lo[i];                  // exposed face west of cell i
+        else vr = 0.0;
+    }
+    a.er[fr] = vr;
+    if (i == a.nr - 1) a.er[fr + 1] = ai ? (p - a.wout[k]) * a.inv_rd[a.nr] : 0.0;
+    // azimuthal face j + 1/2, periodic (both cells share the (r, z) cell's activity)
+    const int jn = j + 1 == a.nt ? 0 : j + 1;
+    a.ea[e] = ai ? (p - a.phi[((size_t)k * a.nt + jn) * nr + i]) * a.inv_rda[i] : 0.0;
+    // axial face k
+    const size_t plane = (size_t)a.nt * nr;
+    double vz;
+    if (k == 0) {
+        vz = ai ? (a.phi_z0 - p) * g.inv_zd[0] : 0.0;
+    } else {
+        const bool as = !MASK || g.act[(size_t)(k - 1) * nr + i];
+        if (ai && as) vz = (a.phi[e - plane] - p) * g.inv_zd[k];
+        else if (as) vz = (a.phi[e - plane] - g.pe) * ihz_hi[k - 1];
+        else if (ai) vz = (g.pe - p) * ihz_lo[k];
+        else vz = 0.0;
+    }
+    a.ez[e] = vz;
+    if (k == a.nz - 1) a.ez[e + plane] = ai ? (p - a.phi_z1) * g.inv_zd[a.nz] : 0.0;
+}
+
 }  // namespace
 }  // namespace pp
 
@@ -72,10 +135,6 @@ extern "C" int pic_poisson_face_field(pic_poisson_plan_t plan, const double *phi
         return PIC_POISSON_EINVAL;
     }
     const ProblemPlan &q = plan->pr[0];
-    if (q.nact > 0) {
-        set_error("pic_poisson_face_field does not take per-row tables (the plan has patches or z_faces)");
-        return PIC_POISSON_EINVAL;
-    }
     const LevelHost &h = q.lv[0];
     FieldArgs a{};
     a.nr = h.nr;
@@ -94,7 +153,19 @@ extern "C" int pic_poisson_face_field(pic_poisson_plan_t plan, const double *phi
     a.ea = ea_dev;
     a.ez = ez_dev;
     const size_t n = (size_t)a.nz * a.nt * a.nr;
-    k_face_field<<<(unsigned)((n + 255) / 256), 256, 0, plan->stream>>>(a);
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (h.act.empty() && h.zf.empty()) {
+        k_face_field<<<grid, 256, 0, plan->stream>>>(a);
+    } else {   // non-uniform axial faces and / or a composite domain
+        FieldGenArgs g{};
+        g.a = a;
+        g.inv_zd = q.finv_zd;
+        g.inv_half = q.finv_half;
+        g.act = q.act0;
+        g.pe = q.d.phi_exposed;
+        if (q.act0) k_face_field_gen<true><<<grid, 256, 0, plan->stream>>>(g);
+        else k_face_field_gen<false><<<grid, 256, 0, plan->stream>>>(g);
+    }
     PP_CUDA(cudaGetLastError());
     return PIC_POISSON_OK;
 }

@@ -539,6 +539,39 @@ const int *ctrl_done(const pic_poisson_plan_s &P) {
     return reinterpret_cast<const int *>(reinterpret_cast<const char *>(P.ctrl) + offsetof(Ctrl, done));
 }
 
+// Axial faces of level l: the given ones, or uniform ones from z0, z1.
+std::vector<double> level_zfaces(const ProblemPlan &q, int l) {
+    const LevelHost &h = q.lv[l];
+    if (!h.zf.empty()) return h.zf;
+    std::vector<double> f(h.nz + 1);
+    for (int a = 0; a <= h.nz; ++a) f[a] = q.d.z0 + (q.d.z1 - q.d.z0) * a / h.nz;
+    f[h.nz] = q.d.z1;
+    return f;
+}
+
+// Bins of a cell lookup over faces f[0..n]: as many as make each bin no wider
+// than half the narrowest cell (so a bin meets at most two cells), at least n.
+int lookup_bins(const std::vector<double> &f) {
+    const int n = (int)f.size() - 1;
+    double wmin = INFINITY;
+    for (int a = 0; a < n; ++a) wmin = std::min(wmin, f[a + 1] - f[a]);
+    const double nb = std::ceil(2.0 * (f[n] - f[0]) / wmin);
+    return (int)std::min(std::max(nb, (double)n), 1048576.0);
+}
+
+// The cell holding the lower end of each bin: max{a < n : f[a] <= f0 + b w}.
+std::vector<int> lookup_table(const std::vector<double> &f, int nb) {
+    const int n = (int)f.size() - 1;
+    std::vector<int> t(nb);
+    int a = 0;
+    for (int b = 0; b < nb; ++b) {
+        const double x = f[0] + (f[n] - f[0]) * b / nb;
+        while (a + 1 < n && f[a + 1] <= x) ++a;
+        t[b] = a;
+    }
+    return t;
+}
+
 int setup_problem(ProblemPlan &q, const pic_poisson_desc &d) {
     q.d = d;
     if (d.phi_r_in_z) {
@@ -722,6 +755,18 @@ void carve(pic_poisson_plan_s &P, Carver &c) {
         q.dep_inv_vz = c.take<double>(q.lv[0].nz + 1);
         q.dep_flo = c.take<double>(q.lv[0].nr);
         q.dep_fhi = c.take<double>(q.lv[0].nr);
+        q.finv_zd = c.take<double>(q.lv[0].nz + 1);
+        q.finv_half = c.take<double>(2 * (size_t)q.lv[0].nr + 2 * (size_t)q.lv[0].nz);
+        q.act0 = q.lv[0].act.empty() ? nullptr : c.take<unsigned char>(q.lv[0].act.size());
+        q.dep_inv_v2 = q.lv[0].act.empty() ? nullptr : c.take<double>((size_t)(q.lv[0].nr + 1) * (q.lv[0].nz + 1));
+        q.dep_rf = c.take<double>(q.lv[0].nr + 1);
+        q.dep_zf = c.take<double>(q.lv[0].nz + 1);
+        q.dep_inv_wr = c.take<double>(q.lv[0].nr);
+        q.dep_inv_wz = c.take<double>(q.lv[0].nz);
+        q.dep_nrbin = lookup_bins(q.lv[0].rf);
+        q.dep_nzbin = lookup_bins(level_zfaces(q, 0));
+        q.dep_rbin = c.take<int>(q.dep_nrbin);
+        q.dep_zbin = c.take<int>(q.dep_nzbin);
         const LevelHost &h0 = q.lv[0];
         const size_t n0 = (size_t)h0.nr * h0.nz * q.nm;
         g_fft += (size_t)h0.nz * ((h0.nr + FFT_TI - 1) / FFT_TI);
@@ -1095,6 +1140,63 @@ int upload(pic_poisson_plan_s &P) {
         to_dev(ivz, q.dep_inv_vz, st, err);
         to_dev(flo, q.dep_flo, st, err);
         to_dev(fhi, q.dep_fhi, st, err);
+        // the same steps on non-uniform axial faces and composite domains: axial
+        // face distances, centre-to-face distances, the active flags, the node
+        // volumes of active octants, and the cell lookups of the deposit
+        const std::vector<double> zf = level_zfaces(q, 0);
+        std::vector<double> zc(h.nz);
+        for (int k = 0; k < h.nz; ++k) zc[k] = 0.5 * (zf[k] + zf[k + 1]);
+        std::vector<double> inv_zd(h.nz + 1);
+        for (int c = 0; c <= h.nz; ++c)
+            inv_zd[c] = 1.0 / (c == 0 ? zc[0] - zf[0] : (c == h.nz ? zf[c] - zc[c - 1] : zc[c] - zc[c - 1]));
+        std::vector<double> half(2 * (size_t)h.nr + 2 * (size_t)h.nz);
+        for (int i = 0; i < h.nr; ++i) {
+            half[i] = 1.0 / (h.rc[i] - h.rf[i]);
+            half[h.nr + i] = 1.0 / (h.rf[i + 1] - h.rc[i]);
+        }
+        for (int k = 0; k < h.nz; ++k) {
+            half[2 * h.nr + k] = 1.0 / (zc[k] - zf[k]);
+            half[2 * h.nr + h.nz + k] = 1.0 / (zf[k + 1] - zc[k]);
+        }
+        to_dev(inv_zd, q.finv_zd, st, err);
+        to_dev(half, q.finv_half, st, err);
+        // axial node intervals from centre to centre (cut at the walls) on the given faces
+        for (int c = 0; c <= h.nz; ++c) {
+            const double lo = c == 0 ? zf[0] : zc[c - 1], hi = c == h.nz ? zf[h.nz] : zc[c];
+            ivz[c] = 1.0 / (da * (hi - lo));
+        }
+        if (!h.zf.empty()) to_dev(ivz, q.dep_inv_vz, st, err);
+        if (q.act0) {
+            if (err == cudaSuccess)
+                err = cudaMemcpyAsync(q.act0, h.act.data(), h.act.size(), cudaMemcpyHostToDevice, st);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+            // node volumes: the sum over the node's active neighbour cells of
+            // the octant in each (r: the exact r dr integral of the half cell)
+            std::vector<double> v2((size_t)(h.nr + 1) * (h.nz + 1), 0.0);
+            for (int k = 0; k < h.nz; ++k)
+                for (int i = 0; i < h.nr; ++i) {
+                    if (!h.act[(size_t)k * h.nr + i]) continue;
+                    const double r0 = h.rf[i], r1 = h.rf[i + 1], rc = h.rc[i], hz = 0.5 * (zf[k + 1] - zf[k]);
+                    const double vlo = (rc - r0) * (rc + r0) / 2, vhi = (r1 - rc) * (r1 + rc) / 2;
+                    for (int c = k; c <= k + 1; ++c) {
+                        v2[(size_t)c * (h.nr + 1) + i] += da * hz * vlo;
+                        v2[(size_t)c * (h.nr + 1) + i + 1] += da * hz * vhi;
+                    }
+                }
+            for (double &v : v2) v = v > 0.0 ? 1.0 / v : 0.0;
+            to_dev(v2, q.dep_inv_v2, st, err);
+        }
+        std::vector<double> iwr(h.nr), iwz(h.nz);
+        for (int i = 0; i < h.nr; ++i) iwr[i] = 1.0 / (h.rf[i + 1] - h.rf[i]);
+        for (int k = 0; k < h.nz; ++k) iwz[k] = 1.0 / (zf[k + 1] - zf[k]);
+        to_dev(h.rf, q.dep_rf, st, err);
+        to_dev(zf, q.dep_zf, st, err);
+        to_dev(iwr, q.dep_inv_wr, st, err);
+        to_dev(iwz, q.dep_inv_wz, st, err);
+        ints_to_dev(lookup_table(h.rf, q.dep_nrbin), q.dep_rbin, st, err);
+        ints_to_dev(lookup_table(zf, q.dep_nzbin), q.dep_zbin, st, err);
+        q.dep_inv_rbw = (float)(q.dep_nrbin / (h.rf[h.nr] - h.rf[0]));
+        q.dep_inv_zbw = (float)(q.dep_nzbin / (zf[h.nz] - zf[0]));
     }
 
     // transforms

@@ -32,6 +32,18 @@ struct ProblemPlan {
     double *finv_rd = nullptr;                  // and 1 / radial face distances [nr + 1]
     double *dep_inv_vr = nullptr, *dep_inv_vz = nullptr;   // CIC deposit: 1 / node-volume factors [nr+1], [nz+1]
     double *dep_flo = nullptr, *dep_fhi = nullptr;         // projection: radial octant shares [nr]
+    // level-0 geometry of the steps around the solve on non-uniform meshes and
+    // composite domains (field.cu, deposit.cu)
+    double *finv_zd = nullptr;                  // face field: 1 / axial face distances [nz + 1]
+    double *finv_half = nullptr;                // 1 / centre-to-face distances: r lower, r upper [nr] each,
+                                                // z lower, z upper [nz] each
+    unsigned char *act0 = nullptr;              // composite domain: active flags [nz][nr] (null otherwise)
+    double *dep_inv_v2 = nullptr;               // composite: 1 / node volumes of active octants [nz+1][nr+1]
+    double *dep_rf = nullptr, *dep_zf = nullptr;         // faces [nr + 1], [nz + 1]
+    double *dep_inv_wr = nullptr, *dep_inv_wz = nullptr; // 1 / cell widths [nr], [nz]
+    int *dep_rbin = nullptr, *dep_zbin = nullptr;        // cell at the lower end of each lookup bin
+    int dep_nrbin = 0, dep_nzbin = 0;                    // lookup bins per axis
+    float dep_inv_rbw = 0.f, dep_inv_zbw = 0.f;          // 1 / bin widths (a guess only; binary32)
 };
 
 // Launch tables of one precision's hierarchy, per level l = 0 .. Lmax-2

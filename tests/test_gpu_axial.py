@@ -120,13 +120,3 @@ def test_batch_mixes_axial_meshes_patches_and_plain():
         ref, _ = oracle.solve3d(oracle.grid_from_problem(q), r, tol=1e-15)
         assert info["status"] == B.OK, info
         assert rel_l2(phi.cpu().numpy(), ref) <= 1e-12
-
-
-def test_axial_mesh_plan_refuses_field_and_deposit():
-    p = _sz(W.annulus(32, 8, 24), 1.05)
-    with Plan(p) as plan:
-        with pytest.raises(B.PicPoissonError):
-            plan.face_field(torch.zeros(p.shape, dtype=torch.float64, device="cuda"))
-        pos = torch.full((4,), 0.03, dtype=torch.float64, device="cuda")
-        with pytest.raises(B.PicPoissonError):
-            plan.deposit(pos, pos, pos * 0.1, weight=1.0)

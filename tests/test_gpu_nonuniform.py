@@ -93,14 +93,6 @@ def test_batch_mixes_uniform_and_nonuniform_problems():
         assert rel_l2(phi.cpu().numpy(), ref) <= TOL[FP64]
 
 
-def test_deposit_refuses_a_nonuniform_mesh():
-    p = stretched(16, 4, 16, 1.1)
-    with Plan(p) as plan:
-        x = torch.full((4,), 0.03, dtype=torch.float64, device="cuda")
-        with pytest.raises(B.PicPoissonError):
-            plan.deposit(x, torch.zeros_like(x), torch.full_like(x, 0.01), 1e8)
-
-
 def test_invalid_faces_are_rejected():
     p = W.annulus(8, 4, 8)
     bad = W.stretched_radial_faces(p.r_in, p.r_out, p.nr, 1.1)

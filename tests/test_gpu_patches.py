@@ -129,15 +129,8 @@ def test_batch_mixes_composite_and_plain_problems(precision):
         assert rel_l2(phi.cpu().numpy(), ref) <= TOL[precision]
 
 
-def test_composite_plan_refuses_field_deposit_and_fused():
+def test_composite_plan_refuses_the_fused_smoother():
     p = W.channel_plume(32, 8, 24)
-    with Plan(p) as plan:
-        phi = torch.zeros(p.shape, dtype=torch.float64, device="cuda")
-        with pytest.raises(B.PicPoissonError):
-            plan.face_field(phi)
-        pos = torch.full((4,), 0.03, dtype=torch.float64, device="cuda")
-        with pytest.raises(B.PicPoissonError):
-            plan.deposit(pos, pos, pos * 0.1, weight=1.0)
     with pytest.raises(B.PicPoissonError):
         Plan(p, precision=MIXED, smooth_fused=1)
 
