@@ -31,6 +31,8 @@ METRIC = "ms per all-mode Poisson solve at 512x128x400 to rel-res 1e-10; % HBM r
 UNIT = "ms"
 GRID = (512, 128, 400)
 FALLBACK_HBM_GBS = 6800.7
+# committed ncu summaries holding the level-0 smoother's DRAM bytes per launch at 512x128x400
+SMOOTH_PROFILE = {"fp64": "smooth_fp64_512x128x200.md", "mixed": "smooth_fused_defect_transforms_mixed_512x128x400.md"}
 
 
 def parse():
@@ -403,7 +405,7 @@ def run_ours(args):
     pplan.close()
     ms_ph = sum_phase(pinfos, "ms_phase")
     # DRAM bytes of a level-0 half-sweep at 512x128x400 (ncu, scaled from 512x128x200 where valid)
-    traffic = traffic_from_profile("smooth_%s_512x128x200.md" % args.precision) if tag == "512x128x400" else None
+    traffic = traffic_from_profile(SMOOTH_PROFILE[args.precision]) if tag == "512x128x400" else None
     sched = {"pre_sweeps": kw.get("pre_sweeps", 2), "post_sweeps": kw.get("post_sweeps", 2),
              "inner_cycles": kw.get("inner_cycles", 2), "smooth_threads": kw.get("smooth_threads", 256),
              "smooth_strip": kw.get("smooth_strip", 0), "omega": kw.get("omega", 1.0),
@@ -537,7 +539,7 @@ def run_ours(args):
             "rel_l2_vs_headline_phi": diff,
             "phase_ms_per_solve": {k: v / len(pinfos2) for k, v in sum_phase(pinfos2, "ms_phase").items()},
             "roofline": roofline(pinfos2, other == FP64, fp64_gflops / 1e3, hbm_peak, hbm_src,
-                                 traffic_from_profile("smooth_%s_512x128x200.md" % name)
+                                 traffic_from_profile(SMOOTH_PROFILE[name])
                                  if tag == "512x128x400" else None),
             "hbm_roofline_solve": {"achieved_gbs": gbs2, "peak_gbs": hbm_peak, "frac": gbs2 / hbm_peak}}}
 
@@ -725,7 +727,9 @@ def run_batch(args, dev):
 
 def run_sequence(args, dev, p, schedules):
     """Drifting m = 8 wave (one azimuthal cell per step) at the headline grid,
-    solved back to back with the previous step's potential as initial guess,
+    solved back to back with the previous step's mode-space iterate as initial
+    guess (pic_poisson_get_modes, then pic_poisson_solve_modes; with fmg the
+    full-multigrid start runs on the guess's correction equation),
     against the zero initial guess, both graph-captured with the form's tuned
     schedule."""
     import torch
@@ -735,10 +739,11 @@ def run_sequence(args, dev, p, schedules):
                        % (p.nr, p.ntheta, p.nz, args.sequence_steps), "tol": args.tol}
     for name, prec in (("fp64", FP64), ("mixed", MIXED)):
         kw = schedules.get(name, {})
-        warm = Plan(p, precision=prec, graph=True, initial_guess=True, **kw)
+        warm = Plan(p, precision=prec, graph=True, **kw)
         zero = Plan(p, precision=prec, graph=True, **kw)
         phi = torch.zeros(p.shape, dtype=torch.float64, device=dev)
         tmp = torch.empty_like(phi)
+        uh = torch.zeros(warm.mode_shape, dtype=torch.float64, device=dev)
         ms_w = ms_z = 0.0
         cyc_w, cyc_z = [], []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -746,7 +751,9 @@ def run_sequence(args, dev, p, schedules):
             rho = W.drifting_rho_torch(p, t, device=dev)
             torch.cuda.synchronize()
             e0.record()
-            _, iw = warm.solve(rho, phi, tol=args.tol)
+            # the previous step's mode-space iterate as the initial guess (no transform of phi)
+            _, iw = warm.solve_modes(rho, uh, phi, tol=args.tol)
+            warm.get_modes(uh)
             e1.record()
             torch.cuda.synchronize()
             if t > 0:
