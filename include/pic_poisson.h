@@ -126,9 +126,9 @@ typedef struct {
                                   the right-hand side restricted to every level, coarsest solve, then
                                   prolongation and one V-cycle per level up to the finest; from a given
                                   iterate (PIC_POISSON_USE_INITIAL_GUESS, pic_poisson_solve_modes) the
-                                  same on its correction equation (level 0 pre-smoothed and its residual
-                                  restricted, the coarser levels as above, the correction prolongated
-                                  into level 0 and post-smoothed); 0: no such start */
+                                  same on its correction equation (its level-0 residual restricted, the
+                                  coarser levels as above, the correction prolongated into level 0);
+                                  0: no such start */
     int inner_first;           /* mixed precision: FP32 V-cycles of the first defect correction of a solve;
                                   <= inner_cycles (0 included) selects inner_cycles.  A larger first
                                   correction can save one FP64 defect, update and convergence test */

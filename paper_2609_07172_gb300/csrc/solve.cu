@@ -295,6 +295,55 @@ int fmg_start(Runner &R) {
     return PIC_POISSON_OK;
 }
 
+// Full-multigrid start from a given level-0 iterate (FP64 levels): the same
+// nested iteration on the correction equation.  The residual of the given
+// iterate is evaluated on every level-0 cell and restricted to level 1; that
+// right-hand side is restricted on to every coarser level, the coarsest
+// levels are solved, and from there up each level gets the prolongated
+// coarser correction and one V-cycle, up to level 1, whose correction is
+// prolongated into level 0.  The level-0 pre-smoothing of the solve follows
+// (its first red half-sweep overwrites the red cells, so the prolongation
+// corrects the black ones only).  A given iterate then keeps the
+// full-multigrid start that a zero iterate gets, for about the same work.
+int fmg_correction(Runner &R) {
+    pic_poisson_plan_s &P = R.P;
+    const Hier<double> &H = P.h64;
+    const int nl = P.Lmax - 1, pre = P.shared.pre_sweeps;
+    if (H.restr[0]) {   // r = b - A u on every cell (the given iterate is not smoothed)
+        RUN(R, PIC_POISSON_PHASE_RESTRICT,
+            launch_residual_restrict(H.restr[0], H.g_restr[0], false, nullptr, R.st, R.P.masked));
+        const double n = level_entries<double>(P, 0);
+        R.account(PIC_POISSON_PHASE_RESTRICT, n * sizeof(double2) * 2.75, 19.0 * n);
+    }
+    for (int l = 1; l < nl; ++l) {
+        if (!H.g_rhs[l]) continue;
+        RUN(R, PIC_POISSON_PHASE_RESTRICT, launch_rhs_restrict(H.rhs[l], H.g_rhs[l], R.st, R.P.masked));
+        const double n = level_entries<double>(P, l);
+        R.account(PIC_POISSON_PHASE_RESTRICT, n * sizeof(double2) * (1.0 + 0.75), 0.5 * n);
+    }
+    int rc = coarse_and_bottom(R, H);
+    if (rc) return rc;
+    for (int l = nl - 1; l >= 1; --l) {
+        if (!H.g_interp[l]) continue;
+        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_interp(H.interp[l], H.g_interp[l], R.st, R.P.masked));
+        const double n = level_entries<double>(P, l);
+        R.account(PIC_POISSON_PHASE_PROLONG, n * sizeof(double2) * 1.25, 16.0 * n);
+        rc = smooth_level(R, H, l, pre, false, false);
+        if (rc) return rc;
+        rc = restrict_level(R, H, l, nullptr);
+        if (rc) return rc;
+        rc = descend_ascend(R, H, l);
+        if (rc) return rc;
+    }
+    if (H.prolong[0]) {   // level 1's correction into the level-0 iterate
+        const bool black_only = pre > 0 && P.shared.omega == 1.0;
+        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_prolong(H.prolong[0], H.g_prolong[0], black_only, R.st, R.P.masked));
+        const double n = level_entries<double>(P, 0), frac = black_only ? 0.5 : 1.0;
+        R.account(PIC_POISSON_PHASE_PROLONG, n * sizeof(double2) * (0.25 + 2.0 * frac), 16.0 * frac * n);
+    }
+    return PIC_POISSON_OK;
+}
+
 // Forward transform + right-hand side, ||b||, initial iterate, first
 // evaluation of the residual and the first convergence test.
 // guess: 0 = zero initial iterate, 1 = transform of phi, 2 = mode-layout iterate.
@@ -314,6 +363,12 @@ int enqueue_prologue(Runner &R, int guess) {
     } else if (guess == 2) {
         RUN(R, PIC_POISSON_PHASE_FORWARD, launch_copy_guess(P.guess, P.g_fft, R.st));
         R.account(PIC_POISSON_PHASE_FORWARD, 2.0 * n0 * sizeof(double2), 0.0);
+    }
+    if (guess != 0) {
+        if (!mixed && P.shared.fmg && P.Lmax > 1) {
+            int rc = fmg_correction(R);   // full-multigrid start on the given iterate's correction
+            if (rc) return rc;
+        }
     } else if (!mixed && P.shared.fmg && P.Lmax > 1) {
         int rc = fmg_start(R);   // writes every level-0 iterate
         if (rc) return rc;

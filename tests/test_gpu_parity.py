@@ -317,3 +317,33 @@ def test_full_multigrid_start_matches_oracle(dims):
 def test_full_multigrid_needs_fp64():
     with pytest.raises(PicPoissonError):
         Plan(W.annulus(32, 8, 32), precision=B.MIXED, fmg=1)
+
+
+@pytest.mark.parametrize("graph", [False, True], ids=["hostloop", "graph"])
+@pytest.mark.parametrize("dims", [(64, 32, 48), (64, 8, 400), (40, 8, 24)])
+def test_full_multigrid_start_from_a_given_iterate(dims, graph):
+    """fmg with an initial iterate runs the full-multigrid pass on the
+    correction equation: the solve still reaches the oracle's solution, and a
+    tolerance in no more cycles than the same guess without it."""
+    p = with_bias_walls(W.annulus(*dims))
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=44)
+    ref, _ = oracle.solve3d(g, rho, tol=1e-15)
+    guess = oracle.solve3d(g, W.rho_plasma(p, seed=45), tol=1e-8)[0]   # a neighbouring step's solution
+    with Plan(p, fmg=1, initial_guess=True, graph=graph) as plan:
+        phi, info = plan.solve(dev(rho), dev(guess), tol=0.0)
+    assert info["status"] == B.OK
+    assert rel_l2(phi.cpu().numpy(), ref) <= FP64_TOL, info
+    cyc = []
+    for f in (0, 1):
+        with Plan(p, fmg=f, initial_guess=True, graph=graph) as plan:
+            _, info = plan.solve(dev(rho), dev(guess), tol=1e-10)
+        assert info["status"] == B.OK and info["rel_res"] <= 1e-10
+        cyc.append(info["cycles"])
+    assert cyc[1] <= cyc[0], cyc
+    # the mode-layout initial iterate takes the same start
+    with Plan(p, fmg=1, graph=graph) as plan:
+        uh = dev(to_modes(guess))       # the guess in mode layout
+        phi_m, info_m = plan.solve_modes(dev(rho), uh, tol=0.0)
+    assert info_m["status"] == B.OK
+    assert rel_l2(phi_m.cpu().numpy(), ref) <= FP64_TOL
