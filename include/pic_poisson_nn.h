@@ -30,10 +30,22 @@ extern "C" {
  * optional ReLU.  in: BF16 [n,h,w,cin], cin a multiple of 16; w: BF16
  * [9][cout][cin]; bias: FP32 [cout] or NULL; cout a multiple of 8, <= 128.
  * Writes out_bf16 (BF16 [n,h,w,cout]) and/or out_f32 (FP32, same shape).
- * BF16 tensor cores (mma.sync m16n8k16), FP32 accumulation.
+ * Runs on the tcgen05 tensor cores (an implicit GEMM: 128 output pixels x
+ * cout per tile, TMA-staged operands, FP32 accumulators in tensor memory)
+ * when cout is a multiple of 16, w is a multiple of 128 or 16, 32 or 64, and
+ * every tensor is 16-byte aligned; otherwise as pic_nn_conv3x3_mma_sync.
  */
 int pic_nn_conv3x3(const void *in, int cin, const void *w, const float *bias, void *out_bf16, float *out_f32, int cout,
                    int n, int h, int wd, int relu, void *stream);
+/* The same convolution on the legacy mma.sync m16n8k16 path (BF16 tensor
+ * cores, FP32 accumulation; any w), for comparison and as the fallback. */
+int pic_nn_conv3x3_mma_sync(const void *in, int cin, const void *w, const float *bias, void *out_bf16,
+                            float *out_f32, int cout, int n, int h, int wd, int relu, void *stream);
+/* Whether a bounded wait of the tcgen05 convolution ran out since the last
+ * call: *status = 0 (none) or 1 + the role that gave up (0 TMA producer,
+ * 1 MMA issuer, 2 epilogue, 3 / 4 the final drains); clears the flag.  Such a
+ * kernel ends early and its output is not valid.  Synchronous. */
+int pic_nn_conv_tc_status(int *status);
 
 /* Weights of the data-gradient convolution: wt[8-tap][ci][co] = w[tap][co][ci]
  * (so d_in = conv3x3(d_out, wt) with cin' = cout, cout' = cin). */

@@ -352,4 +352,10 @@ size_t fft_smem_bytes(int nt);
 // of u and a sign, done with integer instructions.
 __host__ __device__ inline bool tw_rot(int t, int n) { return !(8 * t <= n || 8 * t >= 3 * n); }
 
+// 3x3 convolution on the tcgen05 tensor cores (conv_tc.cu): 0 on success, 1
+// when the shape or alignment is not taken (run the mma.sync kernel), else a
+// PIC_POISSON_* error.
+int launch_conv3x3_tc(const void *in, int cin, const void *w, const float *bias, void *out, float *out32, int cout,
+                      int n, int h, int wd, int relu, cudaStream_t st);
+
 }  // namespace pp

@@ -529,6 +529,17 @@ extern "C" {
 int pic_nn_conv3x3(const void *in, int cin, const void *w, const float *bias, void *out_bf16, float *out_f32, int cout,
                    int n, int h, int wd, int relu, void *stream) {
     clear_error();
+    if (in && w && (out_bf16 || out_f32) && cin > 0 && cout > 0 && n > 0 && h > 0 && wd > 0) {
+        const int rc = launch_conv3x3_tc(in, cin, w, bias, out_bf16, out_f32, cout, n, h, wd, relu,
+                                         (cudaStream_t)stream);
+        if (rc != 1) return rc;   // done on the tcgen05 tensor cores, or an error
+    }
+    return pic_nn_conv3x3_mma_sync(in, cin, w, bias, out_bf16, out_f32, cout, n, h, wd, relu, stream);
+}
+
+int pic_nn_conv3x3_mma_sync(const void *in, int cin, const void *w, const float *bias, void *out_bf16, float *out_f32,
+                            int cout, int n, int h, int wd, int relu, void *stream) {
+    clear_error();
     if (!in || !w || (!out_bf16 && !out_f32) || cin <= 0 || cin % 16 || cout <= 0 || cout % 8 || cout > 128 ||
         n <= 0 || h <= 0 || wd <= 0) {
         set_error("conv3x3: need cin %% 16 == 0, cout %% 8 == 0 (<= 128), positive sizes, in/w/out");

@@ -3,8 +3,9 @@
 The network maps the normalised mode residual r_m of a previous-step iterate
 (two channels, Re and Im, plus the mode's shift ratio lambda_m mu / D) on the
 r-z grid of one mode to an approximate correction d_m ~ A_m^{-1} r_m.  Every
-layer runs in the library's kernels: BF16 3x3 convolutions on mma.sync tensor
-cores with FP32 accumulation, their data and weight gradients, pooling,
+layer runs in the library's kernels: BF16 3x3 convolutions on the tcgen05
+tensor cores (TMA-staged implicit GEMM, FP32 accumulators in tensor memory;
+mma.sync for widths the tensor-core tiling does not take), their data and weight gradients, pooling,
 upsampling, the loss and Adam on FP32 master weights.  This module only
 allocates tensors and sequences the calls.
 
@@ -32,6 +33,8 @@ OUT_USED = 2
 
 _SIGS = {
     "pic_nn_conv3x3": "vivvvvi iiiiv",
+    "pic_nn_conv3x3_mma_sync": "vivvvvi iiiiv",
+    "pic_nn_conv_tc_status": "v",
     "pic_nn_flip_weights": "viivv",
     "pic_nn_conv3x3_wgrad": "viviiiivvvsv",
     "pic_nn_relu_bwd": "vvlv",

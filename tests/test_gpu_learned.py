@@ -5,6 +5,7 @@ The U-Net runs in BF16 with FP32 accumulation, so its outputs and gradients
 agree with the FP64 oracle to BF16 accuracy (relative errors of a few 1e-3
 per layer); the tolerances below allow for that.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -48,6 +49,51 @@ def test_conv3x3_matches_cpu(cin, cout):
     ref = torch.relu(conv_ref(x.double(), wt.double(), bias.double()))
     assert rel(out32.cpu().double(), ref) < 1e-5            # FP32 accumulation of exact BF16 products
     assert rel(out.cpu().double(), ref) < 1e-2              # BF16 output rounding
+
+
+def tc_status():
+    st = ctypes.c_int(-1)
+    _ok(nn_lib().pic_nn_conv_tc_status(ctypes.byref(st)))
+    return st.value
+
+
+# widths the tcgen05 tiling takes: 128 pixels of a row (w a multiple of 128) or
+# 128 / w whole rows (w = 16, 32, 64; ragged last row block when h % (128 / w) != 0)
+TC_SHAPES = [(2, 5, 256), (3, 9, 128), (2, 7, 64), (2, 25, 32), (1, 11, 16)]
+TC_CHANNELS = [(16, 16), (16, 32), (32, 64), (64, 128), (128, 64), (128, 32), (64, 16), (32, 16), (16, 48)]
+
+
+@pytest.mark.parametrize("cin,cout", TC_CHANNELS)
+@pytest.mark.parametrize("n,h,w", TC_SHAPES)
+def test_conv3x3_tcgen05_matches_cpu_and_mma_sync(n, h, w, cin, cout):
+    """The tcgen05 implicit GEMM (TMA zero fill as the padding, FP32 in TMEM)
+    against the FP64 CPU convolution and against the mma.sync kernel."""
+    g = torch.Generator().manual_seed(n * 1000 + h * 100 + w + cin * 7 + cout)
+    x = bf(torch.randn(n, h, w, cin, generator=g))
+    wt = bf(torch.randn(9, cout, cin, generator=g) / math.sqrt(9 * cin))
+    bias = torch.randn(cout, generator=g)
+    xc, wc, bc = x.cuda(), wt.cuda(), bias.cuda()
+    outs = {}
+    for name in ("pic_nn_conv3x3", "pic_nn_conv3x3_mma_sync"):
+        out = torch.full((n, h, w, cout), float("nan"), dtype=torch.bfloat16, device="cuda")
+        out32 = torch.full((n, h, w, cout), float("nan"), dtype=torch.float32, device="cuda")
+        _ok(getattr(nn_lib(), name)(P(xc), cin, P(wc), P(bc), P(out), P(out32), cout, n, h, w, 1, _st()))
+        torch.cuda.synchronize()
+        outs[name] = (out.cpu(), out32.cpu())
+    assert tc_status() == 0
+    ref = torch.relu(conv_ref(x.double(), wt.double(), bias.double()))
+    out, out32 = outs["pic_nn_conv3x3"]
+    assert torch.isfinite(out32).all() and torch.isfinite(out.float()).all()
+    assert rel(out32.double(), ref) < 1e-5
+    assert rel(out.double(), ref) < 1e-2
+    # the same sums in another order: FP32 rounding apart
+    assert rel(out32.double(), outs["pic_nn_conv3x3_mma_sync"][1].double()) < 1e-5
+    # no ReLU, FP32 output only (the data-gradient convolution's form)
+    out32b = torch.full((n, h, w, cout), float("nan"), dtype=torch.float32, device="cuda")
+    _ok(nn_lib().pic_nn_conv3x3(P(xc), cin, P(wc), None, None, P(out32b), cout, n, h, w, 0, _st()))
+    torch.cuda.synchronize()
+    assert tc_status() == 0
+    assert rel(out32b.cpu().double(), conv_ref(x.double(), wt.double(), None)) < 1e-5
 
 
 def test_conv_gradients_match_autograd():
