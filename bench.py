@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--sequence-steps", type=int, default=200)
     ap.add_argument("--tune-cache", default=None, help="JSON file caching autotuner results")
     ap.add_argument("--learned", action="store_true", help="train and evaluate the learned warm start (~2 min)")
+    ap.add_argument("--no-conv", action="store_true", help="skip timing the U-Net convolutions and inference")
     ap.add_argument("--no-tune", action="store_true", help="default schedule instead of the autotuner's")
     ap.add_argument("--schedule", default=None,
                     help='JSON of Plan settings used instead of the autotuner\'s for every form, e.g. '
@@ -546,9 +547,11 @@ def run_ours(args):
     if not args.no_composite:
         line["composite_channel_plume"] = run_composite(args, schedules, world, dist)
     if not args.no_batch:
-        line["batch_uneven"] = run_batch(args, dev)
+        line["batch_uneven"] = run_batch(args, dev, hbm_peak, fp64_gflops / 1e3)
     if not args.no_sequence:
         line["sequence"] = run_sequence(args, dev, p, schedules)
+    if not args.no_conv:
+        line["learned_conv"] = run_conv(args, dev, p, ms_per_solve / max(statistics.median(cycles), 1))
     if args.learned:
         line["learned_warm_start"] = run_learned(args, dev, p)
 
@@ -676,7 +679,7 @@ def run_deposit(args, plan, p):
     return out
 
 
-def run_batch(args, dev):
+def run_batch(args, dev, hbm_peak, fp64_tflops):
     """24 independent problems of uneven sizes (seed 3) in one batched, autotuned,
     graph-captured plan vs one graph-captured plan per problem."""
     import torch
@@ -703,9 +706,21 @@ def run_batch(args, dev):
     ms_batch = e0.elapsed_time(e1) / steps
     launches = infos[0]["launches"]
     bp.close()
+    # the same batch through the host loop with events around every launch:
+    # the sum of its kernels' device times, against the graph's wall time (the
+    # gaps between launches are what one persistent launch would save)
+    pbp = BatchPlan(problems, profile=True, **kw)
+    _, pinf = pbp.solve(rhos, phis, tol=args.tol)
+    kernel_ms = sum(pinf[0]["ms_phase"].values())
+    pbp.close()
     plans = [Plan(q, graph=True, **kw) for q in problems]
+    # each problem's own algorithmic bytes and flops (its own cycle count): the
+    # work the batch has to do, for its roofline
+    alg_bytes = alg_flops = 0.0
     for pl, r, f in zip(plans, rhos, phis):
-        pl.solve(r, f, tol=args.tol)
+        _, inf1 = pl.solve(r, f, tol=args.tol)
+        alg_bytes += sum(inf1["bytes_phase"].values())
+        alg_flops += sum(inf1["flops_phase"].values())
     torch.cuda.synchronize()
     e0.record()
     for _ in range(steps):
@@ -722,6 +737,15 @@ def run_batch(args, dev):
             "ms_per_batch": ms_batch, "ms_one_plan_per_problem": ms_each, "steps": steps,
             "cycles": infos[0]["cycles"], "rel_res_max": max(i["rel_res"] for i in infos),
             "launches_per_batch": launches, "autotuned": dict(kw, ms=tuned.get("ms")),
+            "kernel_ms_per_batch": kernel_ms,
+            "gap_ms_per_batch": ms_batch - kernel_ms,
+            "roofline": {"algorithmic_bytes_per_batch": alg_bytes, "algorithmic_flops_per_batch": alg_flops,
+                         "achieved_gbs": alg_bytes / (ms_batch * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                         "hbm_frac": alg_bytes / (ms_batch * 1e-3) / 1e9 / hbm_peak,
+                         "fp64_tflops": alg_flops / (ms_batch * 1e-3) / 1e12, "fp64_peak_tflops": fp64_tflops,
+                         "fp64_frac": alg_flops / (ms_batch * 1e-3) / 1e12 / fp64_tflops,
+                         "note": "the sum of each problem's own algorithmic bytes and FP64 flops (its own cycles) "
+                                 "over the batched solve's time"},
             "autotune_candidates": len(tuned.get("tried", [])) or None}
 
 
@@ -776,6 +800,88 @@ def run_sequence(args, dev, p, schedules):
     return out
 
 
+def run_conv(args, dev, p, ms_per_cycle):
+    """The U-Net's convolutions at the warm start's size (65 modes on the
+    256 x 200 grid and its three coarser levels): tcgen05 implicit GEMM
+    (pic_nn_conv3x3) against the legacy mma.sync kernel, CUDA events, median
+    of 10; then the whole warm-start inference (residual, restriction, pack,
+    U-Net, unpack, prolongation, minimal-residual step; random weights -- the
+    cost does not depend on them) with each, against one V-cycle."""
+    import torch
+    from paper_2609_07172_gb300 import Plan, learned as LW
+    from paper_2609_07172_gb300.unet import P as TP, UNet, _ok, _st, nn_lib
+    lib = nn_lib()
+    n = p.ntheta // 2 + 1
+    h0, w0 = p.nz // 2, p.nr // 2
+    layers = [("e0", 0, 16, 16), ("e1", 1, 16, 32), ("e2", 2, 32, 64), ("b1", 3, 64, 128), ("b2", 3, 128, 64),
+              ("d2", 2, 128, 32), ("d1", 1, 64, 16), ("d0", 0, 32, 16), ("out", 0, 16, 16)]
+    g = torch.Generator(device=dev).manual_seed(17)
+    out = {}
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    st = torch.cuda.current_stream()
+    for name, lv, cin, cout in layers:
+        h, w = h0 >> lv, w0 >> lv
+        x = torch.randn(n, h, w, cin, device=dev, generator=g).to(torch.bfloat16)
+        wt = (torch.randn(9, cout, cin, device=dev, generator=g) / (9 * cin) ** 0.5).to(torch.bfloat16)
+        b = torch.randn(cout, device=dev, generator=g)
+        y = torch.empty(n, h, w, cout, dtype=torch.bfloat16, device=dev)
+        rec = {"shape": [n, h, w, cin, cout]}
+        for entry, key in (("pic_nn_conv3x3", "tcgen05"), ("pic_nn_conv3x3_mma_sync", "mma_sync")):
+            f = getattr(lib, entry)
+            for _ in range(3):
+                _ok(f(TP(x), cin, TP(wt), TP(b), TP(y), None, cout, n, h, w, 1, _st()))
+            torch.cuda.synchronize()
+            for a, e in evs:
+                a.record(st)
+                _ok(f(TP(x), cin, TP(wt), TP(b), TP(y), None, cout, n, h, w, 1, _st()))
+                e.record(st)
+            torch.cuda.synchronize()
+            rec[key + "_us"] = statistics.median(a.elapsed_time(e) for a, e in evs) * 1e3
+        pix = n * h * w
+        rec["algorithmic_bytes"] = 2.0 * pix * (cin + cout) + 2.0 * 9 * cin * cout
+        rec["flops"] = 2.0 * pix * cout * 9 * cin
+        t = rec["tcgen05_us"] * 1e-6
+        rec["tcgen05_gbs"] = rec["algorithmic_bytes"] / t / 1e9
+        rec["tcgen05_tflops"] = rec["flops"] / t / 1e12
+        out[name] = rec
+        del x, wt, b, y
+    st_err = conv_tc_status(lib)
+    # the whole warm-start inference with each convolution path
+    plan = Plan(p, graph=True)
+    net = UNet(seed=0)
+    ws = LW.WarmStart(net, 1.0, p, plan)
+    from paper_2609_07172_gb300 import workloads as W
+    bhat = plan.forward(W.drifting_rho_torch(p, 0))
+    u = torch.zeros(plan.mode_shape, dtype=torch.float64, device=dev)
+    inf = {}
+    for entry, key in (("pic_nn_conv3x3", "tcgen05"), ("pic_nn_conv3x3_mma_sync", "mma_sync")):
+        net.conv_entry = entry
+        for _ in range(2):
+            ws.guess(bhat, u)
+        torch.cuda.synchronize()
+        a, e = evs[0]
+        a.record(st)
+        for _ in range(5):
+            ws.guess(bhat, u)
+        e.record(st)
+        torch.cuda.synchronize()
+        inf[key + "_ms"] = a.elapsed_time(e) / 5
+    plan.close()
+    dom = max(out, key=lambda k: out[k]["tcgen05_us"])
+    return {"layers": out, "tc_wait_status": st_err, "warm_start_inference": inf,
+            "solve_ms_per_cycle": ms_per_cycle,
+            "dominant_layer": dom,
+            "note": "65 samples (modes) per layer on the 256x200 grid and its coarser levels; algorithmic bytes = "
+                    "input + output activations + weights in BF16; flops = 2 x pixels x cout x 9 cin"}
+
+
+def conv_tc_status(lib):
+    import ctypes
+    st = ctypes.c_int(-1)
+    lib.pic_nn_conv_tc_status(ctypes.byref(st))
+    return st.value
+
+
 def run_learned(args, dev, p):
     """Learned warm start: train the U-Net on 3000 (residual, correction) pairs from
     plain solves of a 256x64x200 drifting-wave sequence (seed 7), then solve the
@@ -796,6 +902,7 @@ def run_learned(args, dev, p):
     t_train = time.perf_counter() - t0
     del X, Y
     res = LW.evaluate_sequence(net, gain, p, steps=args.learned_steps, tol=args.tol, coarse=True, gpu_inputs=True,
+                               bound=True,
                                seed=3)
     # inference alone (pack, U-Net, unpack, prolongation, minimal-residual step)
     plan = None

@@ -166,23 +166,50 @@ class WarmStart:
         _ok(lib.pic_nn_unpack_modes(P(y), 16, P(rms), self.gain, pc.nr, pc.nz, nm, P(self.dc), st))
         if self.coarse:
             _ok(lib.pic_nn_prolong2(P(self.dc), p.nr, p.nz, nm, P(self.d), st))
+        return self._step(uprev)
+
+    def _step(self, uprev):
+        """uprev + alpha d, alpha minimising the residual (self.r holds b - A uprev)."""
         _ok(B.load().pic_poisson_mode_residual(self.plan._plan, P(self.d), P(self.zero), P(self.bd), None))
-        _ok(lib.pic_nn_minres_step(P(uprev), P(self.d), P(self.r), P(self.bd), self.r.numel() // 2, nm,
-                                   p.ntheta, -1.0, P(self.scratch), P(self.guess_buf), P(self.alpha), st))
+        _ok(nn_lib().pic_nn_minres_step(P(uprev), P(self.d), P(self.r), P(self.bd), self.r.numel() // 2, self.nm,
+                                        self.p.ntheta, -1.0, P(self.scratch), P(self.guess_buf), P(self.alpha),
+                                        _st()))
         return self.guess_buf
 
+    def coarse_bound(self, bhat, uprev, ucur):
+        """The best guess a predictor on the network's 2:1 coarse grid could
+        give: the exact correction ucur - uprev of this step (ucur the solved
+        modes), averaged onto the coarse grid and prolongated back, then the
+        same minimal-residual step -- an upper bound on what the learned
+        correction can achieve, since the network outputs coarse-grid fields."""
+        lib = nn_lib()
+        st = _st()
+        p, nm = self.p, self.nm
+        _ok(B.load().pic_poisson_mode_residual(self.plan._plan, P(uprev), P(bhat), P(self.r), None))
+        torch.sub(ucur, uprev, out=self.d)
+        if self.coarse:
+            _ok(lib.pic_nn_restrict2(P(self.d), p.nr, p.nz, nm, P(self.dc), st))
+            self.dc.mul_(0.25)   # the restriction sums the four fine cells: their average
+            _ok(lib.pic_nn_prolong2(P(self.dc), p.nr, p.nz, nm, P(self.d), st))
+        return self._step(uprev)
 
-def evaluate_sequence(net, gain, p, steps, tol=1e-10, coarse=True, gpu_inputs=True, seed=3, precision=B.FP64):
+
+def evaluate_sequence(net, gain, p, steps, tol=1e-10, coarse=True, gpu_inputs=True, seed=3, precision=B.FP64,
+                      bound=False):
     """Drifting-wave sequence solved back to back from (a) the previous-step
     guess and (b) the learned warm start; per-step cycles and device ms
     (the learned side includes its forward transform, residual, inference and
-    step).  Returns a dict of summaries and per-step records."""
+    step).  With bound, also (c) the coarse-grid predictor bound of
+    WarmStart.coarse_bound (not timed: it uses the step's solution).  Returns a
+    dict of summaries and per-step records."""
     dev = torch.device("cuda")
     base = B.Plan(p, graph=True, precision=precision)
     lrn = B.Plan(p, graph=True, precision=precision)
     ws = WarmStart(net, gain, p, lrn, coarse=coarse)
     ub = torch.zeros(base.mode_shape, dtype=torch.float64, device=dev)
     ul = torch.zeros_like(ub)
+    ub_prev = torch.zeros_like(ub)
+    ucur = torch.zeros_like(ub)
     phi = torch.empty(p.shape, dtype=torch.float64, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     rec = []
@@ -204,15 +231,25 @@ def evaluate_sequence(net, gain, p, steps, tol=1e-10, coarse=True, gpu_inputs=Tr
         torch.cuda.synchronize()
         ms_l = e0.elapsed_time(e1)
         lrn.get_modes(ul)
-        rec.append({"t": t, "cycles_prev": ib["cycles"], "cycles_learned": il["cycles"],
-                    "rel0_prev": ib["rel_res0"], "rel0_learned": il["rel_res0"], "ms_prev": ms_b,
-                    "ms_learned": ms_l, "alpha": float(ws.alpha.item()),
-                    "ok": ib["status"] == B.OK and il["status"] == B.OK})
+        r = {"t": t, "cycles_prev": ib["cycles"], "cycles_learned": il["cycles"],
+             "rel0_prev": ib["rel_res0"], "rel0_learned": il["rel_res0"], "ms_prev": ms_b,
+             "ms_learned": ms_l, "alpha": float(ws.alpha.item()),
+             "ok": ib["status"] == B.OK and il["status"] == B.OK}
+        if bound and t > 0:   # the coarse-grid predictor bound, from the previous step's base solution
+            gb = ws.coarse_bound(bhat, ub_prev, base.get_modes(ucur))
+            _, ibd = lrn.solve_modes(rho, gb, phi, tol=tol)
+            r.update(cycles_bound=ibd["cycles"], rel0_bound=ibd["rel_res0"])
+        if bound:
+            base.get_modes(ub_prev)
+        rec.append(r)
     base.close()
     lrn.close()
     body = rec[1:]     # step 0 starts both from zero
     mean = lambda k: sum(r[k] for r in body) / len(body)
-    return {"steps": steps, "cycles_prev": mean("cycles_prev"), "cycles_learned": mean("cycles_learned"),
-            "ms_prev": mean("ms_prev"), "ms_learned": mean("ms_learned"),
-            "rel0_prev": mean("rel0_prev"), "rel0_learned": mean("rel0_learned"),
-            "alpha_mean": mean("alpha"), "all_converged": all(r["ok"] for r in rec), "records": rec}
+    out = {"steps": steps, "cycles_prev": mean("cycles_prev"), "cycles_learned": mean("cycles_learned"),
+           "ms_prev": mean("ms_prev"), "ms_learned": mean("ms_learned"),
+           "rel0_prev": mean("rel0_prev"), "rel0_learned": mean("rel0_learned"),
+           "alpha_mean": mean("alpha"), "all_converged": all(r["ok"] for r in rec), "records": rec}
+    if bound:
+        out.update(cycles_coarse_bound=mean("cycles_bound"), rel0_coarse_bound=mean("rel0_bound"))
+    return out

@@ -162,3 +162,32 @@ def test_gpu_generator_matches_recipe_statistics():
     wa = np.abs(np.fft.rfft(a.mean(axis=(0, 2)))[8])
     wb = np.abs(np.fft.rfft(b.mean(axis=(0, 2)))[8])
     assert wb == pytest.approx(wa, rel=0.2)
+
+
+def reduced_uneven_draw():
+    """The benchmark's 24-problem draw (seed 3: N_r, N_theta, N_z and the
+    charge-density seeds), each problem scaled down about four-fold in every
+    direction -- N_r / 4, N_theta / 4, N_z 64 / 200 / 400 -> 16 / 48 / 96, even
+    counts that keep a multigrid hierarchy -- so that the oracle solves all of
+    them to the floor in the test."""
+    nz_map = {64: 16, 200: 48, 400: 96}
+    return [(W.annulus(p.nr // 4, p.ntheta // 4, nz_map[p.nz]), seed) for p, seed in W.uneven_batch(3)]
+
+
+@pytest.fixture(scope="module")
+def reduced_refs():
+    draw = reduced_uneven_draw()
+    probs = [q for q, _ in draw]
+    rhos = [W.rho_plasma(q, seed=s) for q, s in draw]
+    refs = [oracle.solve3d(oracle.grid_from_problem(q), r, tol=1e-15)[0] for q, r in zip(probs, rhos)]
+    return probs, rhos, refs
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_reduced_benchmark_batch_matches_oracle(reduced_refs, precision):
+    probs, rhos, refs = reduced_refs
+    with BatchPlan(probs, precision=precision, graph=True) as bp:
+        phis, infos = bp.solve([dev(r) for r in rhos], tol=0.0)
+    for q, ref, phi, info in zip(probs, refs, phis, infos):
+        assert info["status"] == B.OK, (q.shape, info)
+        assert rel_l2(phi.cpu().numpy(), ref) <= TOL[precision], (q.shape, info)
