@@ -14,7 +14,8 @@
 // row, which TMA swizzles into the canonical K-major layout the MMA's shared
 // memory descriptors name.
 //
-// Roles (192 threads): warp 4 issues the TMA loads into a 4-stage ring,
+// Roles (192 threads): warp 4 issues the TMA loads into a ring of 4 stages (8
+// for 16-channel chunks),
 // warp 5 issues the MMAs (KC / 16 per stage, M = 128, N = cout, K = 16) into
 // one of two TMEM accumulators, warps 0-3 drain an accumulator (tcgen05.ld,
 // each warp its 32 TMEM lanes = 32 pixels), add the bias, apply ReLU and
@@ -41,7 +42,7 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int TC_M = 128;                      // pixels per tile (MMA M)
-constexpr int TC_STAGES = 4;
+constexpr int TC_MAX_STAGES = 8;                 // ring slots: 8 for 16-channel chunks (a tile's 9 loads), else 4
 constexpr int TC_THREADS = 192;                // warps 0-3 epilogue, 4 TMA, 5 MMA
 constexpr unsigned TC_SPIN_LIMIT = 1u << 23;   // try_wait rounds before a wait gives up
 
@@ -59,7 +60,20 @@ struct ConvTCArgs {
     bf16 *out;
     float *out32;
     int relu;
+    int stages;                      // ring slots in use (<= TC_MAX_STAGES)
+    // halo variant (k_conv3x3_tc_halo): no-swizzle K-major operands
+    unsigned lbo_a;                  // bytes from one 8-channel group of the halo tile to the next
+    unsigned lbo_b;                  // bytes from one 8-channel group of a tap's weights to the next
+    unsigned w_bytes;                // all nine taps' weights (resident)
 };
+
+// No-swizzle K-major descriptor: 8-row core matrices of 16-byte rows; LBO =
+// the step to the next 8 channels (K), SBO = 128 (the next 8 rows follow
+// directly), so the start may sit on any 16-byte row.
+__device__ __forceinline__ uint64_t smem_desc_plain(unsigned addr, unsigned lbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)(128u >> 4) << 32) | ((uint64_t)1 << 46);
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -172,18 +186,19 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
     const unsigned raw = smem_u32(dsm);
     const unsigned pad = (1024u - (raw & 1023u)) & 1023u;
     const unsigned stage0 = raw + pad;
-    unsigned char *tail = dsm + pad + TC_STAGES * a.stage_bytes;
-    const unsigned full0 = smem_u32(tail);                   // [TC_STAGES] TMA bytes landed
-    const unsigned empty0 = full0 + 8 * TC_STAGES;           // [TC_STAGES] stage read by the MMAs
-    const unsigned tfull0 = empty0 + 8 * TC_STAGES;          // [2] accumulator complete
+    const int S = a.stages;
+    unsigned char *tail = dsm + pad + S * a.stage_bytes;
+    const unsigned full0 = smem_u32(tail);                   // [S] TMA bytes landed
+    const unsigned empty0 = full0 + 8 * TC_MAX_STAGES;       // [S] stage read by the MMAs
+    const unsigned tfull0 = empty0 + 8 * TC_MAX_STAGES;      // [2] accumulator complete
     const unsigned tempty0 = tfull0 + 16;                    // [2] accumulator drained
     const unsigned drain = tempty0 + 16;                     // every MMA of this CTA complete
-    unsigned *tmem_slot = reinterpret_cast<unsigned *>(tail + 8 * (2 * TC_STAGES + 5));
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(tail + 8 * (2 * TC_MAX_STAGES + 5));
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *never = reinterpret_cast<volatile int *>(tmem_slot + 2);   // stays 0: a wait that ignores *abort
     const unsigned ncols = 2 * a.tmem_cols;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
@@ -217,7 +232,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
                 int nn, x0, y0;
                 tile_origin(a, tile, nn, x0, y0);
                 for (int k = 0; k < kiters; ++k, ++it) {
-                    const unsigned s = it % TC_STAGES, u = it / TC_STAGES;
+                    const unsigned s = it % S, u = it / S;
                     if (!mbar_wait(empty0 + 8 * s, (u & 1u) ^ 1u, abort)) {
                         give_up(abort, 0);
                         ok = false;
@@ -232,9 +247,9 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
             }
             // the last copies land before the CTA exits (on the normal path
             // the MMAs have consumed them already and these waits return at once)
-            const unsigned first = it > (unsigned)TC_STAGES ? it - TC_STAGES : 0u;
+            const unsigned first = it > (unsigned)S ? it - S : 0u;
             for (unsigned j = first; j < it; ++j)
-                if (!mbar_wait(full0 + 8 * (j % TC_STAGES), (j / TC_STAGES) & 1u, never)) give_up(abort, 3);
+                if (!mbar_wait(full0 + 8 * (j % S), (j / S) & 1u, never)) give_up(abort, 3);
         }
     } else if (warp == 5) {
         // ---------------- MMA issuer
@@ -250,7 +265,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
                 tc_fence_after();
                 const unsigned d = tmem + buf * a.tmem_cols;
                 for (int k = 0; k < kiters; ++k, ++it) {
-                    const unsigned s = it % TC_STAGES, us = it / TC_STAGES;
+                    const unsigned s = it % S, us = it / S;
                     if (!mbar_wait(full0 + 8 * s, us & 1u, abort)) {
                         give_up(abort, 1);
                         ok = false;
@@ -319,6 +334,181 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUt
     }
 }
 
+// Halo variant for image rows of 128 pixels or more (tiles of one row) and
+// small weight sets (the full- and half-resolution layers, which are bound by
+// data movement): per tile and chunk of KC channels, TMA brings the three input
+// rows y - 1 .. y + 1 over pixels x0 - 1 .. x0 + 128 once, as 8-channel groups
+// of 390 16-byte rows (no swizzle, K-major core matrices); the nine taps are
+// the same buffer seen from nine start rows, (1 + dy) * 130 + 1 + dx.  All
+// nine taps' weights stay resident from the CTA's start.  A tile then moves
+// 3 * 130 * cin instead of 9 * 128 * cin input values.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_conv3x3_tc_halo(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const ConvTCArgs a) {
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned raw = smem_u32(dsm);
+    const unsigned pad = (1024u - (raw & 1023u)) & 1023u;
+    const unsigned wbase = raw + pad;                                  // resident weights
+    const unsigned stage0 = wbase + ((a.w_bytes + 1023u) & ~1023u);   // halo tiles
+    const int S = a.stages;
+    unsigned char *tail = dsm + pad + ((a.w_bytes + 1023u) & ~1023u) + S * a.stage_bytes;
+    const unsigned full0 = smem_u32(tail);
+    const unsigned empty0 = full0 + 8 * TC_MAX_STAGES;
+    const unsigned tfull0 = empty0 + 8 * TC_MAX_STAGES;
+    const unsigned tempty0 = tfull0 + 16;
+    const unsigned drain = tempty0 + 16;
+    const unsigned wbar = drain + 8;                                   // weights landed
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(tail + 8 * (2 * TC_MAX_STAGES + 6));
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *never = reinterpret_cast<volatile int *>(tmem_slot + 2);
+    const unsigned ncols = 2 * a.tmem_cols;
+    const int groups = a.kc / 8;                 // 8-channel groups per chunk
+    const int cgroups = a.cin / 8;               // per tap of the weights
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull0 + 8 * b, 1);
+            mbar_init(tempty0 + 8 * b, 4 * 32);
+        }
+        mbar_init(drain, 1);
+        mbar_init(wbar, 1);
+        *abort = 0;
+        *never = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+
+    if (warp == 4) {
+        // ---------------- TMA producer: the weights once, then the halo tiles
+        if (lane == 0) {
+            mbar_expect_tx(wbar, a.w_bytes);
+            for (int tap = 0; tap < 9; ++tap)
+                for (int g = 0; g < cgroups; ++g)
+                    tma_load_3d(wbase + (unsigned)(tap * cgroups + g) * a.lbo_b, &tb, 8 * g, 0, tap, wbar);
+            unsigned it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < a.tiles; tile += gridDim.x) {
+                int nn, x0, y0;
+                tile_origin(a, tile, nn, x0, y0);
+                for (int c = 0; c < a.nchunks; ++c, ++it) {
+                    const unsigned s = it % S, u = it / S;
+                    if (!mbar_wait(empty0 + 8 * s, (u & 1u) ^ 1u, abort)) {
+                        give_up(abort, 0);
+                        ok = false;
+                        break;
+                    }
+                    const unsigned sa = stage0 + s * a.stage_bytes;
+                    mbar_expect_tx(full0 + 8 * s, a.a_bytes);
+                    for (int g = 0; g < groups; ++g)
+                        tma_load_4d(sa + (unsigned)g * a.lbo_a, &ta, c * a.kc + 8 * g, x0 - 1, y0 - 1, nn,
+                                    full0 + 8 * s);
+                }
+            }
+            const unsigned first = it > (unsigned)S ? it - S : 0u;
+            for (unsigned j = first; j < it; ++j)
+                if (!mbar_wait(full0 + 8 * (j % S), (j / S) & 1u, never)) give_up(abort, 3);
+            if (!mbar_wait(wbar, 0, never)) give_up(abort, 3);
+        }
+    } else if (warp == 5) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            unsigned it = 0, tc = 0;
+            bool ok = mbar_wait(wbar, 0, abort);
+            if (!ok) give_up(abort, 1);
+            tc_fence_after();
+            for (int tile = blockIdx.x; ok && tile < a.tiles; tile += gridDim.x, ++tc) {
+                const unsigned buf = tc & 1u, u = tc >> 1;
+                if (!mbar_wait(tempty0 + 8 * buf, (u & 1u) ^ 1u, abort)) {
+                    give_up(abort, 1);
+                    break;
+                }
+                tc_fence_after();
+                const unsigned d = tmem + buf * a.tmem_cols;
+                for (int c = 0; c < a.nchunks; ++c, ++it) {
+                    const unsigned s = it % S, us = it / S;
+                    if (!mbar_wait(full0 + 8 * s, us & 1u, abort)) {
+                        give_up(abort, 1);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned sa = stage0 + s * a.stage_bytes;
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const unsigned row0 = (unsigned)((tap / 3) * (a.bx + 2) + tap % 3);   // (1 + dy) W' + 1 + dx
+                        for (int kk = 0; kk < a.kc / 16; ++kk) {   // K = 16: two 8-channel groups
+                            const unsigned adr = sa + 2u * kk * a.lbo_a + 16u * row0;
+                            const unsigned bdr = wbase + (unsigned)(tap * cgroups + c * groups + 2 * kk) * a.lbo_b;
+                            umma_bf16(d, smem_desc_plain(adr, a.lbo_a), smem_desc_plain(bdr, a.lbo_b), a.idesc,
+                                      (c | tap | kk) != 0 ? 1u : 0u);
+                        }
+                    }
+                    umma_commit(empty0 + 8 * s);
+                }
+                if (!ok) break;
+                umma_commit(tfull0 + 8 * buf);
+            }
+            umma_commit(drain);
+            if (!mbar_wait(drain, 0, never)) give_up(abort, 4);
+        }
+    } else {
+        // ---------------- epilogue (as in k_conv3x3_tc; tiles are one row)
+        const int row = threadIdx.x;
+        unsigned tc = 0;
+        for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, ++tc) {
+            const unsigned buf = tc & 1u, u = tc >> 1;
+            if (!mbar_wait(tfull0 + 8 * buf, u & 1u, abort)) {
+                give_up(abort, 2);
+                break;
+            }
+            tc_fence_after();
+            int nn, x0, y0;
+            tile_origin(a, tile, nn, x0, y0);
+            const size_t p = ((size_t)nn * a.h + y0) * a.wd + x0 + row;
+            const unsigned taddr = tmem + buf * a.tmem_cols + ((unsigned)(warp * 32) << 16);
+            for (int c = 0; c < a.cout; c += 16) {
+                float v[16];
+                tmem_ld16(taddr + (unsigned)c, v);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    float t = v[e] + (a.bias ? a.bias[c + e] : 0.f);
+                    v[e] = a.relu ? fmaxf(t, 0.f) : t;
+                }
+                if (a.out) {
+                    uint4 *o = reinterpret_cast<uint4 *>(a.out + p * a.cout + c);
+                    o[0] = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+                    o[1] = make_uint4(pack2(v[8], v[9]), pack2(v[10], v[11]), pack2(v[12], v[13]),
+                                      pack2(v[14], v[15]));
+                }
+                if (a.out32) {
+                    float4 *o = reinterpret_cast<float4 *>(a.out32 + p * a.cout + c);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tempty0 + 8 * buf);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host side
@@ -349,6 +539,80 @@ EncodeTiledFn encoder() {
 }
 
 }  // namespace
+
+// CTAs per SM of a kernel: shared memory (1 KB reserved per CTA), registers,
+// threads, and tensor memory (512 columns per SM: no CTA waits for an allocation).
+int conv_tc_occupancy(const void *kernel, size_t smem, unsigned tmem_cols_per_cta, int *grid_cap) {
+    int dev = 0, sms = 0, smem_sm = 0;
+    PP_CUDA(cudaGetDevice(&dev));
+    PP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PP_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    cudaFuncAttributes fa;
+    PP_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    const int regs = std::max(1, (fa.numRegs + 7) & ~7) * TC_THREADS;
+    const int occ = std::min({(int)(smem_sm / (smem + 1024)), 65536 / regs, 2048 / TC_THREADS, 32,
+                              (int)(512u / tmem_cols_per_cta)});
+    *grid_cap = sms * std::max(1, occ);
+    return PIC_POISSON_OK;
+}
+
+int set_smem(const void *kernel, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)   // all of the SM's unified memory as shared memory, so several CTAs fit
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) {
+        set_error("conv3x3 (tcgen05): %s", cudaGetErrorString(e));
+        return PIC_POISSON_ECUDA;
+    }
+    return PIC_POISSON_OK;
+}
+
+// The halo variant's operands: no-swizzle 4-D boxes of 8 channels x 130
+// pixels x 3 rows of the input, 3-D boxes of 8 channels x cout of each tap's
+// weights.
+int launch_halo(ConvTCArgs a, const void *in, const void *w, EncodeTiledFn enc, cudaStream_t st) {
+    a.kc = a.cin % 32 == 0 ? 32 : 16;
+    a.nchunks = a.cin / a.kc;
+    const unsigned groups = (unsigned)a.kc / 8, rows = 3u * (unsigned)(a.bx + 2);
+    a.lbo_a = (rows * 16u + 127u) & ~127u;           // 128-byte aligned TMA destinations
+    a.a_bytes = groups * rows * 16u;                  // TMA bytes of one chunk
+    a.stage_bytes = (groups * a.lbo_a + 1023u) & ~1023u;
+    a.lbo_b = (unsigned)a.cout * 16u;
+    a.w_bytes = 9u * (unsigned)a.cout * (unsigned)a.cin * 2u;
+    a.stages = a.kc == 16 ? 4 : 3;
+    CUtensorMap ta, tb;
+    const cuuint64_t gdim_a[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.wd, (cuuint64_t)a.h, (cuuint64_t)a.n};
+    const cuuint64_t gstr_a[3] = {(cuuint64_t)a.cin * 2, (cuuint64_t)a.cin * 2 * a.wd,
+                                  (cuuint64_t)a.cin * 2 * a.wd * a.h};
+    const cuuint32_t box_a[4] = {8, (cuuint32_t)(a.bx + 2), 3, 1};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    if (enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(in), gdim_a, gstr_a, box_a, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return 1;
+    const cuuint64_t gdim_b[3] = {(cuuint64_t)a.cin, (cuuint64_t)a.cout, 9};
+    const cuuint64_t gstr_b[2] = {(cuuint64_t)a.cin * 2, (cuuint64_t)a.cin * 2 * a.cout};
+    const cuuint32_t box_b[3] = {8, (cuuint32_t)a.cout, 1};
+    if (enc(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(w), gdim_b, gstr_b, box_b, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return 1;
+    const size_t smem = 1024 + ((a.w_bytes + 1023u) & ~1023u) + (size_t)a.stages * a.stage_bytes +
+                        8 * (2 * TC_MAX_STAGES + 6) + 16;
+    int rc = set_smem((const void *)k_conv3x3_tc_halo, smem);
+    if (rc) return rc;
+    int cap = 0;
+    rc = conv_tc_occupancy((const void *)k_conv3x3_tc_halo, smem, 2u * a.tmem_cols, &cap);
+    if (rc) return rc;
+    k_conv3x3_tc_halo<<<std::min(a.tiles, cap), TC_THREADS, smem, st>>>(ta, tb, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("conv3x3 (tcgen05, halo) launch failed: %s", cudaGetErrorString(e));
+        return PIC_POISSON_ECUDA;
+    }
+    return PIC_POISSON_OK;
+}
 
 // Tile shape of a W-wide image: 128 pixels of a row (W a multiple of 128) or
 // 128 / W whole rows (W = 16, 32 or 64); 0 when the tensor-core path does not
@@ -401,6 +665,9 @@ int launch_conv3x3_tc(const void *in, int cin, const void *w, const float *bias,
     a.out = (bf16 *)out;
     a.out32 = out32;
     a.relu = relu;
+    // halo variant: one-row tiles and weights small enough to stay resident
+    const unsigned w_all = 9u * (unsigned)cout * (unsigned)cin * 2u;
+    if (a.by == 1 && w_all <= 48u * 1024u) return launch_halo(a, in, w, enc, st);
     const CUtensorMapSwizzle sw = a.kc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
                                              : (a.kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
     // activations: (c, x, y, n), zero fill outside
@@ -421,20 +688,16 @@ int launch_conv3x3_tc(const void *in, int cin, const void *w, const float *bias,
             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return 1;
-    const size_t smem = 1024 + (size_t)TC_STAGES * a.stage_bytes + 8 * (2 * TC_STAGES + 5) + 16;
-    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) {
-        set_error("conv3x3 (tcgen05): %s", cudaGetErrorString(e));
-        return PIC_POISSON_ECUDA;
-    }
-    int dev = 0, sms = 0, occ = 0;
-    PP_CUDA(cudaGetDevice(&dev));
-    PP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    PP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3x3_tc, TC_THREADS, smem));
-    occ = std::max(1, std::min(occ, (int)(512u / (2u * a.tmem_cols))));   // no CTA waits for tensor memory
-    const int grid = (int)std::min<long>(tiles, (long)sms * occ);
+    a.stages = a.kc == 16 ? 8 : 4;
+    const size_t smem = 1024 + (size_t)a.stages * a.stage_bytes + 8 * (2 * TC_MAX_STAGES + 5) + 16;
+    int rc = set_smem((const void *)k_conv3x3_tc, smem);
+    if (rc) return rc;
+    int cap = 0;
+    rc = conv_tc_occupancy((const void *)k_conv3x3_tc, smem, 2u * a.tmem_cols, &cap);
+    if (rc) return rc;
+    const int grid = std::min(a.tiles, cap);
     k_conv3x3_tc<<<grid, TC_THREADS, smem, st>>>(ta, tb, a);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("conv3x3 (tcgen05) launch failed: %s", cudaGetErrorString(e));
         return PIC_POISSON_ECUDA;
