@@ -166,3 +166,14 @@ def test_non_finite_geometry_rejected(field, value):
     d, _ = B.make_desc(p)
     assert B.load().pic_poisson_query(ctypes.byref(d), None) == B.EINVAL
     assert "finite" in B.last_error()
+
+
+def test_library_exports_every_network_function():
+    """Every entry point include/pic_poisson_nn.h declares (the learned warm
+    start's kernels, the tcgen05 convolution and its status query) is exported."""
+    text = open(os.path.join(ROOT, "include", "pic_poisson_nn.h")).read()
+    names = sorted(set(re.findall(r"^\s*(?:int|size_t)\s*(pic_nn_\w+)\s*\(", text, re.M)))
+    assert len(names) >= 18 and "pic_nn_conv3x3_mma_sync" in names and "pic_nn_conv_tc_status" in names
+    lib = B.load()
+    for n in names:
+        assert hasattr(lib, n), n
