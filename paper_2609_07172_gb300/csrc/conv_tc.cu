@@ -540,19 +540,47 @@ EncodeTiledFn encoder() {
 
 }  // namespace
 
-// CTAs per SM of a kernel: shared memory (1 KB reserved per CTA), registers,
-// threads, and tensor memory (512 columns per SM: no CTA waits for an allocation).
-int conv_tc_occupancy(const void *kernel, size_t smem, unsigned tmem_cols_per_cta, int *grid_cap) {
-    int dev = 0, sms = 0, smem_sm = 0;
+namespace {
+
+// Per device: SM count, shared memory per SM, and each kernel's registers per
+// thread (fixed properties, queried once).
+struct TCDeviceInfo {
+    bool valid = false;
+    int sms = 0, smem_sm = 0;
+    int regs[2] = {0, 0};   // k_conv3x3_tc, k_conv3x3_tc_halo
+};
+TCDeviceInfo g_tc_info[64];
+
+int conv_tc_occupancy(int which, size_t smem, unsigned tmem_cols_per_cta, int *grid_cap) {
+    int dev = 0;
     PP_CUDA(cudaGetDevice(&dev));
-    PP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    PP_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    cudaFuncAttributes fa;
-    PP_CUDA(cudaFuncGetAttributes(&fa, kernel));
-    const int regs = std::max(1, (fa.numRegs + 7) & ~7) * TC_THREADS;
-    const int occ = std::min({(int)(smem_sm / (smem + 1024)), 65536 / regs, 2048 / TC_THREADS, 32,
+    if (dev < 0 || dev >= 64) {
+        set_error("device ordinal %d beyond 64", dev);
+        return PIC_POISSON_EINVAL;
+    }
+    TCDeviceInfo info;
+    {
+        std::lock_guard<std::mutex> lock(g_tc_mutex);
+        info = g_tc_info[dev];
+    }
+    if (!info.valid) {
+        PP_CUDA(cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev));
+        PP_CUDA(cudaDeviceGetAttribute(&info.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        cudaFuncAttributes fa;
+        PP_CUDA(cudaFuncGetAttributes(&fa, (const void *)k_conv3x3_tc));
+        info.regs[0] = fa.numRegs;
+        PP_CUDA(cudaFuncGetAttributes(&fa, (const void *)k_conv3x3_tc_halo));
+        info.regs[1] = fa.numRegs;
+        info.valid = true;
+        std::lock_guard<std::mutex> lock(g_tc_mutex);
+        g_tc_info[dev] = info;
+    }
+    // CTAs per SM: shared memory (1 KB reserved per CTA), registers, threads,
+    // and tensor memory (512 columns per SM: no CTA waits for an allocation)
+    const int regs = std::max(1, (info.regs[which] + 7) & ~7) * TC_THREADS;
+    const int occ = std::min({(int)(info.smem_sm / (smem + 1024)), 65536 / regs, 2048 / TC_THREADS, 32,
                               (int)(512u / tmem_cols_per_cta)});
-    *grid_cap = sms * std::max(1, occ);
+    *grid_cap = info.sms * std::max(1, occ);
     return PIC_POISSON_OK;
 }
 
@@ -603,7 +631,7 @@ int launch_halo(ConvTCArgs a, const void *in, const void *w, EncodeTiledFn enc, 
     int rc = set_smem((const void *)k_conv3x3_tc_halo, smem);
     if (rc) return rc;
     int cap = 0;
-    rc = conv_tc_occupancy((const void *)k_conv3x3_tc_halo, smem, 2u * a.tmem_cols, &cap);
+    rc = conv_tc_occupancy(1, smem, 2u * a.tmem_cols, &cap);
     if (rc) return rc;
     k_conv3x3_tc_halo<<<std::min(a.tiles, cap), TC_THREADS, smem, st>>>(ta, tb, a);
     cudaError_t e = cudaGetLastError();
@@ -622,6 +650,8 @@ int conv_tc_tile_x(int wd) {
     if (wd == 16 || wd == 32 || wd == 64) return wd;
     return 0;
 }
+
+}  // namespace
 
 // The tensor-core convolution, or 1 when it does not apply (the caller then
 // runs the mma.sync kernel): cout a multiple of 16 up to 128, cin a multiple of
@@ -693,7 +723,7 @@ int launch_conv3x3_tc(const void *in, int cin, const void *w, const float *bias,
     int rc = set_smem((const void *)k_conv3x3_tc, smem);
     if (rc) return rc;
     int cap = 0;
-    rc = conv_tc_occupancy((const void *)k_conv3x3_tc, smem, 2u * a.tmem_cols, &cap);
+    rc = conv_tc_occupancy(0, smem, 2u * a.tmem_cols, &cap);
     if (rc) return rc;
     const int grid = std::min(a.tiles, cap);
     k_conv3x3_tc<<<grid, TC_THREADS, smem, st>>>(ta, tb, a);

@@ -20,7 +20,7 @@
 // order of the additions changes.  Particles outside the domain deposit
 // nothing.
 //
-// Non-uniform faces and composite domains (k_deposit<true>): the cell comes
+// Non-uniform faces and composite domains (k_deposit_faces): the cell comes
 // from the face arrays (a bin lookup guesses, binary64 comparisons decide),
 // the offsets from the cell's own faces; in a composite domain (Sec. 2.2) a
 // particle in an inactive cell deposits nothing and a node's volume counts
@@ -53,8 +53,11 @@ struct DepositArgs {
     const double *inv_vr;   // [nr + 1] 1 / (radial integral of r dr of node a's interval)
     const double *inv_vz;   // [nz + 1] 1 / (dalpha * axial length of node c's interval)
     double *nodes;          // (nz + 1, nt, nr + 1)
-    // GEN (non-uniform faces or a composite domain): the cell is found on the
-    // face arrays -- a lookup bin guesses it, exact comparisons settle it
+};
+
+// Non-uniform faces or a composite domain (k_deposit_faces): the cell is found
+// on the face arrays -- a lookup bin guesses it, exact comparisons settle it.
+struct DepositGeo {
     const double *rf, *zf;          // faces [nr + 1], [nz + 1]
     const double *inv_wr, *inv_wz;  // 1 / cell widths
     const int *rbin, *zbin;         // cell at the lower end of each bin
@@ -82,43 +85,10 @@ __device__ __forceinline__ int find_cell(double x, const double *f, int n, const
 
 constexpr int DEP_PPT = 4;   // consecutive particles per thread
 
-// Cell and the eight corner contributions W w_r w_alpha w_z 2^-w_exp of
-// particle p (corner index 4 dz + 2 dalpha + dr), in double-float; false
-// when p is absent or outside.  The position arithmetic (cell, offset in the
-// cell) is binary64; the weights' products are double-float, on the FP32
-// pipe -- the deposit's FP64 instructions were its bound.
-template <bool GEN>
-__device__ __forceinline__ bool cic_weights(const DepositArgs &a, long long p, int &ir, int &ia, int &iz, df c[8]) {
-    if (p >= a.np) return false;
-    double xr, xa, xz;
-    if (GEN) {
-        const double r = a.r[p], z = a.z[p], ta = a.al[p] * a.inv_da;
-        const double fa = floor(ta);
-        if (!(fa >= 0.0 && fa < (double)a.nt)) return false;
-        ir = find_cell(r, a.rf, a.nr, a.rbin, a.nrbin, a.r0f, a.inv_rbw);
-        iz = find_cell(z, a.zf, a.nz, a.zbin, a.nzbin, a.z0f, a.inv_zbw);
-        if (ir < 0 || iz < 0) return false;
-        if (a.act && !a.act[(size_t)iz * a.nr + ir]) return false;   // inactive cell: nothing deposited
-        ia = (int)fa;
-        xr = (r - a.rf[ir]) * a.inv_wr[ir];
-        xz = (z - a.zf[iz]) * a.inv_wz[iz];
-        xa = ta - fa;
-        // the products may round to 1 at the upper face; the weights stay in [0, 1]
-        xr = fmin(xr, 1.0);
-        xz = fmin(xz, 1.0);
-    } else {
-        const double tr = (a.r[p] - a.r_in) * a.inv_dr, ta = a.al[p] * a.inv_da, tz = (a.z[p] - a.z0) * a.inv_dz;
-        const double fr = floor(tr), fa = floor(ta), fz = floor(tz);
-        // in range before any conversion (NaN compares false)
-        if (!(fr >= 0.0 && fr < (double)a.nr && fa >= 0.0 && fa < (double)a.nt && fz >= 0.0 && fz < (double)a.nz))
-            return false;
-        ir = (int)fr;
-        ia = (int)fa;
-        iz = (int)fz;
-        xr = tr - fr;   // exact, in [0, 1)
-        xa = ta - fa;
-        xz = tz - fz;
-    }
+// The eight corner contributions W w_r w_alpha w_z 2^-w_exp (corner index
+// 4 dz + 2 dalpha + dr) of offsets (xr, xa, xz) in the cell, in double-float
+// on the FP32 pipe -- the deposit's FP64 instructions were its bound.
+__device__ __forceinline__ bool weights8(const DepositArgs &a, double xr, double xa, double xz, df c[8]) {
     const df r1 = split_scaled(xr, 1023), r0 = split_scaled(1.0 - xr, 1023);
     const df a1 = split_scaled(xa, 1023), a0 = split_scaled(1.0 - xa, 1023);
     const df z1 = split_scaled(xz, 1023), z0 = split_scaled(1.0 - xz, 1023);
@@ -136,17 +106,65 @@ __device__ __forceinline__ bool cic_weights(const DepositArgs &a, long long p, i
     return true;
 }
 
+// Cell and corner contributions of particle p; false when p is absent or
+// outside.  The position arithmetic (cell, offset in the cell) is binary64.
+__device__ __forceinline__ bool cic_weights(const DepositArgs &a, long long p, int &ir, int &ia, int &iz, df c[8]) {
+    if (p >= a.np) return false;
+    const double tr = (a.r[p] - a.r_in) * a.inv_dr, ta = a.al[p] * a.inv_da, tz = (a.z[p] - a.z0) * a.inv_dz;
+    const double fr = floor(tr), fa = floor(ta), fz = floor(tz);
+    // in range before any conversion (NaN compares false)
+    if (!(fr >= 0.0 && fr < (double)a.nr && fa >= 0.0 && fa < (double)a.nt && fz >= 0.0 && fz < (double)a.nz))
+        return false;
+    ir = (int)fr;
+    ia = (int)fa;
+    iz = (int)fz;
+    const double xr = tr - fr, xa = ta - fa, xz = tz - fz;   // exact, in [0, 1)
+    return weights8(a, xr, xa, xz, c);
+}
+
+// The same on face arrays; false also for a particle in an inactive cell.
+__device__ __forceinline__ bool cic_weights_faces(const DepositArgs &a, const DepositGeo &g, long long p, int &ir,
+                                                  int &ia, int &iz, df c[8]) {
+    if (p >= a.np) return false;
+    const double r = a.r[p], z = a.z[p], ta = a.al[p] * a.inv_da;
+    const double fa = floor(ta);
+    if (!(fa >= 0.0 && fa < (double)a.nt)) return false;
+    ir = find_cell(r, g.rf, a.nr, g.rbin, g.nrbin, g.r0f, g.inv_rbw);
+    iz = find_cell(z, g.zf, a.nz, g.zbin, g.nzbin, g.z0f, g.inv_zbw);
+    if (ir < 0 || iz < 0) return false;
+    if (g.act && !g.act[(size_t)iz * a.nr + ir]) return false;   // inactive cell: nothing deposited
+    ia = (int)fa;
+    // the products may round to 1 at the upper face; the weights stay in [0, 1]
+    const double xr = fmin((r - g.rf[ir]) * g.inv_wr[ir], 1.0), xz = fmin((z - g.zf[iz]) * g.inv_wz[iz], 1.0);
+    return weights8(a, xr, ta - fa, xz, c);
+}
+
 // The eight atomic additions of a run's sums to the corners of cell (ir, ia, iz).
-template <bool GEN>
 __device__ __forceinline__ void add_corners(const DepositArgs &a, int ir, int ia, int iz, const df c[8]) {
     const int ja = ia + 1 == a.nt ? 0 : ia + 1;
     const size_t rs = (size_t)a.nr + 1, ps = (size_t)a.nt * rs;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         const int nzi = iz + (d >> 2), nai = (d & 2) ? ja : ia, nri = ir + (d & 1);
-        const double v = (GEN && a.inv_v2) ? to_double(c[d], a.w_exp) * a.inv_v2[(size_t)nzi * rs + nri]
-                                           : to_double(c[d], a.w_exp) * a.inv_vr[nri] * a.inv_vz[nzi];
-        atomicAdd(a.nodes + (size_t)nzi * ps + (size_t)nai * rs + nri, v);
+        atomicAdd(a.nodes + (size_t)nzi * ps + (size_t)nai * rs + nri,
+                  to_double(c[d], a.w_exp) * a.inv_vr[nri] * a.inv_vz[nzi]);
+    }
+}
+
+// The same with the composite domain's node volumes of active octants.
+__device__ __forceinline__ void add_corners_faces(const DepositArgs &a, const DepositGeo &g, int ir, int ia, int iz,
+                                                  const df c[8]) {
+    if (!g.inv_v2) {
+        add_corners(a, ir, ia, iz, c);
+        return;
+    }
+    const int ja = ia + 1 == a.nt ? 0 : ia + 1;
+    const size_t rs = (size_t)a.nr + 1, ps = (size_t)a.nt * rs;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const int nzi = iz + (d >> 2), nai = (d & 2) ? ja : ia, nri = ir + (d & 1);
+        atomicAdd(a.nodes + (size_t)nzi * ps + (size_t)nai * rs + nri,
+                  to_double(c[d], a.w_exp) * g.inv_v2[(size_t)nzi * rs + nri]);
     }
 }
 
@@ -154,7 +172,6 @@ __device__ __forceinline__ void add_corners(const DepositArgs &a, int ir, int ia
 // in registers (a cell change inside the chunk sends the finished run's sums
 // straight to the nodes); then the threads' last runs are aggregated across
 // the warp.
-template <bool GEN>
 __global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
     const long long t0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * DEP_PPT;
     const int lane = threadIdx.x & 31;
@@ -168,9 +185,9 @@ __global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
     for (int t = 0; t < DEP_PPT; ++t) {
         df c[8];
         int ir, ia, iz;
-        if (!cic_weights<GEN>(a, t0 + t, ir, ia, iz, c)) continue;
+        if (!cic_weights(a, t0 + t, ir, ia, iz, c)) continue;
         if (have && (ir != cr || ia != ca || iz != cz)) {
-            add_corners<GEN>(a, cr, ca, cz, acc);
+            add_corners(a, cr, ca, cz, acc);
             have = false;
         }
         if (!have) {
@@ -200,7 +217,57 @@ __global__ void __launch_bounds__(256) k_deposit(const DepositArgs a) {
         }
     }
     const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
-    if (have && last) add_corners<GEN>(a, cr, ca, cz, acc);
+    if (have && last) add_corners(a, cr, ca, cz, acc);
+}
+
+// The same on face arrays and composite domains (kept a separate kernel so
+// that the plain one's code stays as it is).
+__global__ void __launch_bounds__(256) k_deposit_faces(const DepositArgs a, const DepositGeo g) {
+    const long long t0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * DEP_PPT;
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    df acc[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) acc[d] = {0.f, 0.f};
+    int cr = 0, ca = 0, cz = 0;
+    bool have = false;
+#pragma unroll
+    for (int t = 0; t < DEP_PPT; ++t) {
+        df c[8];
+        int ir, ia, iz;
+        if (!cic_weights_faces(a, g, t0 + t, ir, ia, iz, c)) continue;
+        if (have && (ir != cr || ia != ca || iz != cz)) {
+            add_corners_faces(a, g, cr, ca, cz, acc);
+            have = false;
+        }
+        if (!have) {
+#pragma unroll
+            for (int d = 0; d < 8; ++d) acc[d] = c[d];
+            cr = ir;
+            ca = ia;
+            cz = iz;
+            have = true;
+        } else {
+#pragma unroll
+            for (int d = 0; d < 8; ++d) acc[d] = df_add(acc[d], c[d]);
+        }
+    }
+    // runs of lanes with the same last cell (lanes with nothing left: a run each)
+    const long long label = have ? ((long long)cz * a.nt + ca) * a.nr + cr : -1 - lane;
+    const long long prev = __shfl_up_sync(full, label, 1);
+    const unsigned heads = __ballot_sync(full, lane == 0 || prev != label);
+    const unsigned upto = lane == 31 ? full : ((2u << lane) - 1u);
+    const int start = 31 - __clz(heads & upto);   // first lane of this lane's run
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const df y = {__shfl_up_sync(full, acc[d].hi, off), __shfl_up_sync(full, acc[d].lo, off)};
+            if (lane - off >= start) acc[d] = df_add(acc[d], y);
+        }
+    }
+    const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (have && last) add_corners_faces(a, g, cr, ca, cz, acc);
 }
 
 struct ProjectArgs {
@@ -283,29 +350,30 @@ extern "C" int pic_poisson_deposit(pic_poisson_plan_t plan, const double *r_dev,
     a.inv_vz = q.dep_inv_vz;
     a.nodes = nodes_dev;
     const bool gen = !q.uniform_r || !h.zf.empty() || q.act0;
+    DepositGeo g{};
     if (gen) {
-        a.rf = q.dep_rf;
-        a.zf = q.dep_zf;
-        a.inv_wr = q.dep_inv_wr;
-        a.inv_wz = q.dep_inv_wz;
-        a.rbin = q.dep_rbin;
-        a.zbin = q.dep_zbin;
-        a.nrbin = q.dep_nrbin;
-        a.nzbin = q.dep_nzbin;
-        a.r0f = (float)h.rf[0];
-        a.z0f = (float)(h.zf.empty() ? q.d.z0 : h.zf[0]);
-        a.inv_rbw = q.dep_inv_rbw;
-        a.inv_zbw = q.dep_inv_zbw;
-        a.act = q.act0;
-        a.inv_v2 = q.dep_inv_v2;
+        g.rf = q.dep_rf;
+        g.zf = q.dep_zf;
+        g.inv_wr = q.dep_inv_wr;
+        g.inv_wz = q.dep_inv_wz;
+        g.rbin = q.dep_rbin;
+        g.zbin = q.dep_zbin;
+        g.nrbin = q.dep_nrbin;
+        g.nzbin = q.dep_nzbin;
+        g.r0f = (float)h.rf[0];
+        g.z0f = (float)(h.zf.empty() ? q.d.z0 : h.zf[0]);
+        g.inv_rbw = q.dep_inv_rbw;
+        g.inv_zbw = q.dep_inv_zbw;
+        g.act = q.act0;
+        g.inv_v2 = q.dep_inv_v2;
     }
     const long long blocks = (np + 256LL * DEP_PPT - 1) / (256LL * DEP_PPT);
     if (blocks > 0x7fffffffLL) {
         set_error("pic_poisson_deposit: too many particles for one launch (%lld)", np);
         return PIC_POISSON_EINVAL;
     }
-    if (gen) k_deposit<true><<<(unsigned)blocks, 256, 0, plan->stream>>>(a);
-    else k_deposit<false><<<(unsigned)blocks, 256, 0, plan->stream>>>(a);
+    if (gen) k_deposit_faces<<<(unsigned)blocks, 256, 0, plan->stream>>>(a, g);
+    else k_deposit<<<(unsigned)blocks, 256, 0, plan->stream>>>(a);
     PP_CUDA(cudaGetLastError());
     return PIC_POISSON_OK;
 }

@@ -191,3 +191,17 @@ def test_reduced_benchmark_batch_matches_oracle(reduced_refs, precision):
     for q, ref, phi, info in zip(probs, refs, phis, infos):
         assert info["status"] == B.OK, (q.shape, info)
         assert rel_l2(phi.cpu().numpy(), ref) <= TOL[precision], (q.shape, info)
+
+
+def test_largest_batch_matches_oracle():
+    """64 problems, the most one plan takes (sizes and azimuthal resolutions
+    cycling over small grids, one of them single-level)."""
+    dims = [(8, 4, 8), (16, 2, 8), (12, 8, 10), (8, 16, 16), (6, 4, 4), (16, 4, 12), (10, 2, 14), (8, 8, 24)]
+    probs = [W.annulus(*dims[i % len(dims)]) for i in range(64)]
+    rhos = [W.rho_plasma(q, seed=500 + i) for i, q in enumerate(probs)]
+    with BatchPlan(probs, graph=True) as bp:
+        phis, infos = bp.solve([dev(r) for r in rhos], tol=0.0)
+    for q, r, phi, info in zip(probs, rhos, phis, infos):
+        ref, _ = oracle.solve3d(oracle.grid_from_problem(q), r, tol=1e-15)
+        assert info["status"] == B.OK, (q.shape, info)
+        assert rel_l2(phi.cpu().numpy(), ref) <= TOL[FP64], (q.shape, info)

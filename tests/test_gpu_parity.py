@@ -347,3 +347,19 @@ def test_full_multigrid_start_from_a_given_iterate(dims, graph):
         phi_m, info_m = plan.solve_modes(dev(rho), uh, tol=0.0)
     assert info_m["status"] == B.OK
     assert rel_l2(phi_m.cpu().numpy(), ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("kw", [dict(precision=B.FP64), dict(precision=B.MIXED),
+                                dict(precision=B.MIXED, smooth_fused=1, pre_sweeps=2, post_sweeps=2)],
+                         ids=["fp64", "mixed", "mixed_fused"])
+def test_largest_azimuthal_resolution_matches_oracle(kw):
+    """N_theta = 256, the largest the plan takes: 129 modes (the transforms'
+    longest columns, nine mode groups of the fused smoother)."""
+    p = with_bias_walls(W.annulus(32, 256, 24))
+    g = oracle.grid_from_problem(p)
+    rho = W.rho_plasma(p, seed=46)
+    ref, _ = oracle.solve3d(g, rho, tol=1e-15)
+    with Plan(p, graph=True, **kw) as plan:
+        phi, info = plan.solve(dev(rho), tol=0.0)
+    assert info["status"] == B.OK
+    assert rel_l2(phi.cpu().numpy(), ref) <= (FP64_TOL if kw["precision"] == B.FP64 else 1e-10), info
