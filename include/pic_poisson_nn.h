@@ -103,6 +103,17 @@ int pic_nn_to_bf16(const float *a, void *b, long count, void *stream);
 int pic_nn_pack_modes(const double *x, const float *shift, int nr, int nz, int nm, float *rms, double *scratch,
                       void *out, void *stream);
 
+/* Training target of a complex FP64 mode-layout field x (nz, nr, nm): per
+ * mode the RMS of |x| over the cells (rms, FP32 [nm]) and out = FP32
+ * [nm, nz, nr, 2] = (Re x, Im x) * sqrt(2) / rms, each real component at
+ * unit RMS.  scratch: 256 * nm doubles. */
+int pic_nn_pack_target(const double *x, int nr, int nz, int nm, float *rms, double *scratch, float *out,
+                       void *stream);
+/* A training batch: xb[b] = X[idx[b]] (BF16 [pixels][16] per sample) with
+ * channels 0-1 multiplied by sign[b], yb[b] = sign[b] * Y[idx[b]] (FP32
+ * [pixels][2]); idx (int64) and sign (FP32, +-1) device arrays of batch entries. */
+int pic_nn_gather_batch(const void *X, const float *Y, const long *idx, const float *sign, int batch, long pixels,
+                        void *xb, float *yb, void *stream);
 /* d (FP64 mode layout) = gain * rms[m] * (y[m,k,i,0] + i y[m,k,i,1]), y FP32 with c channels. */
 int pic_nn_unpack_modes(const float *y, int c, const float *rms, float gain, int nr, int nz, int nm, double *d,
                         void *stream);

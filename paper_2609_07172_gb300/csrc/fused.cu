@@ -99,7 +99,7 @@ template <int NH, bool RES> struct FusedCfg {
 // k_residual_restrict<float, RED_ONLY> (same operations in the same order).
 // The residual of row r needs the final values of rows r +- 1 and of the
 // neighbouring columns, so the halo grows by one row and one column pair.
-template <int NH, bool RES>
+template <int NH, bool RES, bool RW>
 __global__ void __launch_bounds__(FUSED_THREADS, RES ? 2 : 3) k_smooth_fused(const FusedTab *__restrict__ tab) {
     using Cfg = FusedCfg<NH, RES>;
     constexpr int W = Cfg::W, UR = Cfg::UR, DEPTH = Cfg::DEPTH, BR = Cfg::BR, NB = Cfg::NB, NP = Cfg::NP;
@@ -115,6 +115,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, RES ? 2 : 3) k_smooth_fused(con
     const FusedProb &F = tab->p[p];
     const LevelDev<float> &L = F.L;
     const int nr = L.nr, nz = L.nz, nm = L.nm, ncls = L.ncls;
+    // per-row coefficient classes (a composite domain): every row's class from
+    // its table, south and north couplings apart (plain problems of a mixed
+    // batch keep the three-class path)
+    const bool rw = RW && L.rcls != nullptr;
     const int G = F.G, P = F.P;
     const unsigned lb = blockIdx.x - tab->start[p];
     const int g = (int)(lb % (unsigned)F.ngroups);
@@ -196,6 +200,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, RES ? 2 : 3) k_smooth_fused(con
     float2 *const cb = F.C.b, *const cbh = F.C.bh, *const cu = F.C.u;
     const float *const cinvd = F.C.invd;
     const int cnr = F.C.nr, cnz = F.C.nz, cncls = F.C.ncls, finit = F.init;
+    const int *const crcls = RW ? F.C.rcls : nullptr;   // the coarse level's row classes (per-row tables)
     const bool cwrite = RES && outpair && v0 && j < cnr;
     const unsigned ccol = (unsigned)(cwrite ? j : 0) * nm + (mvalid ? m : 0);
     const float cinv1 = RES && cwrite ? cinvd[(cncls > 1 ? (unsigned)cnr * nm : 0) + ccol] : 0.f;
@@ -246,32 +251,52 @@ __global__ void __launch_bounds__(FUSED_THREADS, RES ? 2 : 3) k_smooth_fused(con
                 // The pair beyond a block's outermost pair reads padding
                 // (halo cells only).
                 if (q == 0) {
-                    const float2 vs = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
-                    float hz = hz0, hw = hw0, he = he0;
-                    if (edge) {
-                        const unsigned tb = (unsigned)row_class(r, nz, ncls) * rs + c0;
-                        hz = v0 ? L.hz[tb] : 0.f;
-                        hw = v0 ? L.hw[tb] : 0.f;
-                        he = v0 ? L.he[tb] : 0.f;
-                    }
                     const float2 uw = pr[t - G];   // west: column 1 of the pair on the left
                     const float2 b = bh[0];
-                    float2 acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
+                    float hz = hz0, hw = hw0, he = he0;
+                    float2 acc;
+                    if (rw) {   // the row's class: south and north apart
+                        const unsigned tb = (unsigned)L.rcls[r] * rs + c0;
+                        const float hs = v0 ? L.hz[tb] : 0.f, hn = v0 ? L.hn[tb] : 0.f;
+                        hw = v0 ? L.hw[tb] : 0.f;
+                        he = v0 ? L.he[tb] : 0.f;
+                        acc = make_float2(fmaf(hs, u0[ss].x, b.x), fmaf(hs, u0[ss].y, b.y));
+                        acc = make_float2(fmaf(hn, u0[sn].x, acc.x), fmaf(hn, u0[sn].y, acc.y));
+                    } else {
+                        const float2 vs = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
+                        if (edge) {
+                            const unsigned tb = (unsigned)row_class(r, nz, ncls) * rs + c0;
+                            hz = v0 ? L.hz[tb] : 0.f;
+                            hw = v0 ? L.hw[tb] : 0.f;
+                            he = v0 ? L.he[tb] : 0.f;
+                        }
+                        acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
+                    }
                     acc = make_float2(fmaf(hw, uw.x, acc.x), fmaf(hw, uw.y, acc.y));
                     acc = make_float2(fmaf(he, u1[sl].x, acc.x), fmaf(he, u1[sl].y, acc.y));
                     u0[sl] = acc;
                 } else {
-                    const float2 vs = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
-                    float hz = hz1, hw = hw1, he = he1;
-                    if (edge) {
-                        const unsigned tb = (unsigned)row_class(r, nz, ncls) * rs + c1;
-                        hz = v1 ? L.hz[tb] : 0.f;
-                        hw = v1 ? L.hw[tb] : 0.f;
-                        he = v1 ? L.he[tb] : 0.f;
-                    }
                     const float2 ue = pr[t + G];   // east: column 0 of the pair on the right
                     const float2 b = bh[NT];
-                    float2 acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
+                    float hz = hz1, hw = hw1, he = he1;
+                    float2 acc;
+                    if (rw) {
+                        const unsigned tb = (unsigned)L.rcls[r] * rs + c1;
+                        const float hs = v1 ? L.hz[tb] : 0.f, hn = v1 ? L.hn[tb] : 0.f;
+                        hw = v1 ? L.hw[tb] : 0.f;
+                        he = v1 ? L.he[tb] : 0.f;
+                        acc = make_float2(fmaf(hs, u1[ss].x, b.x), fmaf(hs, u1[ss].y, b.y));
+                        acc = make_float2(fmaf(hn, u1[sn].x, acc.x), fmaf(hn, u1[sn].y, acc.y));
+                    } else {
+                        const float2 vs = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
+                        if (edge) {
+                            const unsigned tb = (unsigned)row_class(r, nz, ncls) * rs + c1;
+                            hz = v1 ? L.hz[tb] : 0.f;
+                            hw = v1 ? L.hw[tb] : 0.f;
+                            he = v1 ? L.he[tb] : 0.f;
+                        }
+                        acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
+                    }
                     acc = make_float2(fmaf(hw, u0[sl].x, acc.x), fmaf(hw, u0[sl].y, acc.y));
                     acc = make_float2(fmaf(he, ue.x, acc.x), fmaf(he, ue.y, acc.y));
                     u1[sl] = acc;
@@ -290,21 +315,45 @@ __global__ void __launch_bounds__(FUSED_THREADS, RES ? 2 : 3) k_smooth_fused(con
                     const bool edge = rr == 0 || rr == nz - 1;
                     float2 res;
                     if (((c - NH - 1) & 1) == 0) {   // red cell in column 0: west from the left pair
-                        const float d = edge ? L.diag[(unsigned)row_class(rr, nz, ncls) * rs + c0] : dg0;
-                        const float2 s = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
                         const float2 uw = pr[t - G];
-                        float2 a = make_float2(fmaf(cz0, s.x, bred.x), fmaf(cz0, s.y, bred.y));
-                        a = make_float2(fmaf(cw0, uw.x, a.x), fmaf(cw0, uw.y, a.y));
-                        a = make_float2(fmaf(ce0, u1[sl].x, a.x), fmaf(ce0, u1[sl].y, a.y));
+                        float d, cw = cw0, ce = ce0;
+                        float2 a;
+                        if (rw) {   // the row's class: face conductances toward active neighbours
+                            const unsigned cl = (unsigned)L.rcls[rr];
+                            const unsigned ci = cl * nr + (v0 ? i0 : 0);
+                            d = v0 ? L.diag[cl * rs + c0] : 0.f;
+                            cw = L.ccw[ci];
+                            ce = L.cce[ci];
+                            a = make_float2(fmaf(L.ccs[ci], u0[ss].x, bred.x), fmaf(L.ccs[ci], u0[ss].y, bred.y));
+                            a = make_float2(fmaf(L.ccn[ci], u0[sn].x, a.x), fmaf(L.ccn[ci], u0[sn].y, a.y));
+                        } else {
+                            d = edge ? L.diag[(unsigned)row_class(rr, nz, ncls) * rs + c0] : dg0;
+                            const float2 s = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
+                            a = make_float2(fmaf(cz0, s.x, bred.x), fmaf(cz0, s.y, bred.y));
+                        }
+                        a = make_float2(fmaf(cw, uw.x, a.x), fmaf(cw, uw.y, a.y));
+                        a = make_float2(fmaf(ce, u1[sl].x, a.x), fmaf(ce, u1[sl].y, a.y));
                         res = make_float2(fmaf(-d, u0[sl].x, a.x), fmaf(-d, u0[sl].y, a.y));
                         rsum = res;
                     } else {                          // red cell in column 1: east from the right pair
-                        const float d = edge ? L.diag[(unsigned)row_class(rr, nz, ncls) * rs + c1] : dg1;
-                        const float2 s = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
                         const float2 ue = pr[t + G];
-                        float2 a = make_float2(fmaf(cz1, s.x, bred.x), fmaf(cz1, s.y, bred.y));
-                        a = make_float2(fmaf(cw1, u0[sl].x, a.x), fmaf(cw1, u0[sl].y, a.y));
-                        a = make_float2(fmaf(ce1, ue.x, a.x), fmaf(ce1, ue.y, a.y));
+                        float d, cw = cw1, ce = ce1;
+                        float2 a;
+                        if (rw) {
+                            const unsigned cl = (unsigned)L.rcls[rr];
+                            const unsigned ci = cl * nr + (v1 ? i1 : 0);
+                            d = v1 ? L.diag[cl * rs + c1] : 0.f;
+                            cw = L.ccw[ci];
+                            ce = L.cce[ci];
+                            a = make_float2(fmaf(L.ccs[ci], u1[ss].x, bred.x), fmaf(L.ccs[ci], u1[ss].y, bred.y));
+                            a = make_float2(fmaf(L.ccn[ci], u1[sn].x, a.x), fmaf(L.ccn[ci], u1[sn].y, a.y));
+                        } else {
+                            d = edge ? L.diag[(unsigned)row_class(rr, nz, ncls) * rs + c1] : dg1;
+                            const float2 s = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
+                            a = make_float2(fmaf(cz1, s.x, bred.x), fmaf(cz1, s.y, bred.y));
+                        }
+                        a = make_float2(fmaf(cw, u0[sl].x, a.x), fmaf(cw, u0[sl].y, a.y));
+                        a = make_float2(fmaf(ce, ue.x, a.x), fmaf(ce, ue.y, a.y));
                         res = make_float2(fmaf(-d, u1[sl].x, a.x), fmaf(-d, u1[sl].y, a.y));
                         const float2 sum = make_float2(rsum.x + res.x, rsum.y + res.y);
                         if (cwrite) {
@@ -312,9 +361,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, RES ? 2 : 3) k_smooth_fused(con
                             const unsigned e = (unsigned)K * cnr * nm + ccol;
                             cb[e] = sum;
                             if (finit > 0) {
-                                const float inv = (K == 0 || K == cnz - 1)
-                                                      ? cinvd[(unsigned)row_class(K, cnz, cncls) * cnr * nm + ccol]
-                                                      : cinv1;
+                                const float inv =
+                                    crcls ? cinvd[(unsigned)crcls[K] * cnr * nm + ccol]
+                                    : (K == 0 || K == cnz - 1)
+                                        ? cinvd[(unsigned)row_class(K, cnz, cncls) * cnr * nm + ccol]
+                                        : cinv1;
                                 const float2 bhc = make_float2(sum.x * inv, sum.y * inv);
                                 cbh[e] = bhc;
                                 cu[e] = (finit == 2 && ((K + j) & 1) == 0) ? bhc : zero;
@@ -351,21 +402,25 @@ finished:
 
 }  // namespace
 
-template <int NH, bool RES> cudaError_t launch_nh(const FusedTab *tab, unsigned grid, cudaStream_t st) {
+template <int NH, bool RES, bool RW> cudaError_t launch_nh(const FusedTab *tab, unsigned grid, cudaStream_t st) {
     const size_t smem = FusedCfg<NH, RES>::smem_floats2 * sizeof(float2);
     cudaError_t e =
-        cudaFuncSetAttribute(k_smooth_fused<NH, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_smooth_fused<NH, RES, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_smooth_fused<NH, RES><<<grid, FUSED_THREADS, smem, st>>>(tab);
+    k_smooth_fused<NH, RES, RW><<<grid, FUSED_THREADS, smem, st>>>(tab);
     return cudaGetLastError();
 }
 
-cudaError_t launch_smooth_fused(const FusedTab *tab, unsigned grid, int nh, bool res, cudaStream_t st) {
-    switch (nh * 2 + (res ? 1 : 0)) {
-    case 4: return launch_nh<2, false>(tab, grid, st);
-    case 5: return launch_nh<2, true>(tab, grid, st);
-    case 8: return launch_nh<4, false>(tab, grid, st);
-    case 9: return launch_nh<4, true>(tab, grid, st);
+cudaError_t launch_smooth_fused(const FusedTab *tab, unsigned grid, int nh, bool res, cudaStream_t st, bool rw) {
+    switch (nh * 4 + (res ? 2 : 0) + (rw ? 1 : 0)) {
+    case 8: return launch_nh<2, false, false>(tab, grid, st);
+    case 9: return launch_nh<2, false, true>(tab, grid, st);
+    case 10: return launch_nh<2, true, false>(tab, grid, st);
+    case 11: return launch_nh<2, true, true>(tab, grid, st);
+    case 16: return launch_nh<4, false, false>(tab, grid, st);
+    case 17: return launch_nh<4, false, true>(tab, grid, st);
+    case 18: return launch_nh<4, true, false>(tab, grid, st);
+    case 19: return launch_nh<4, true, true>(tab, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }

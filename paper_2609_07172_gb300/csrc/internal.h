@@ -315,7 +315,9 @@ struct FusedTab {
 constexpr int FUSED_THREADS = 256;
 // nh = 2 or 4 half-sweeps, red first; res: also the red-cell residual and
 // its restriction into FusedProb::C (levels coarsened 2:1 in r and z).
-cudaError_t launch_smooth_fused(const FusedTab *tab, unsigned grid, int nh, bool res, cudaStream_t st);
+// rw: per-row coefficient classes (composite domains; plain problems of the
+// batch keep the three-class path).
+cudaError_t launch_smooth_fused(const FusedTab *tab, unsigned grid, int nh, bool res, cudaStream_t st, bool rw);
 // Block shape and count for an nr x nz level with nm modes (about target_blocks blocks).
 void fused_shape(int nr, int nz, int nm, int nh, bool res, int target_blocks, FusedProb &f, unsigned &blocks);
 

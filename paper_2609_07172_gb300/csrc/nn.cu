@@ -376,6 +376,47 @@ __global__ void k_pack(const double2 *__restrict__ x, const float *__restrict__ 
     reinterpret_cast<uint4 *>(o)[1] = z;
 }
 
+// Training target from a complex FP64 mode-layout field (the correction
+// of a step): FP32 [nm, nz, nr, 2] = x / (rms_m / sqrt 2), rms_m the RMS of
+// |x| over the mode's cells -- each real component at unit RMS.
+__global__ void k_pack_target(const double2 *__restrict__ x, const float *__restrict__ rms, int nr, int nz, int nm,
+                              float *__restrict__ out) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;   // over (m, k, i)
+    const long total = (long)nm * nz * nr;
+    if (e >= total) return;
+    const int i = (int)(e % nr);
+    const long t = e / nr;
+    const int k = (int)(t % nz);
+    const int m = (int)(t / nz);
+    const double2 v = x[((long)k * nr + i) * nm + m];
+    const double inv = 1.4142135623730951 / (double)rms[m];
+    reinterpret_cast<float2 *>(out)[e] = make_float2((float)(v.x * inv), (float)(v.y * inv));
+}
+
+// A training batch: samples idx[b] of X (BF16 [n][pix][16]) and Y (FP32
+// [n][pix][2]) copied into xb, yb, channels 0-1 of x and both of y multiplied
+// by sign[b] (+1 or -1: the correction is odd in the residual).
+__global__ void k_gather_batch(const bf16 *__restrict__ X, const float *__restrict__ Y, const long *__restrict__ idx,
+                               const float *__restrict__ sign, int batch, long pix, bf16 *__restrict__ xb,
+                               float *__restrict__ yb) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;   // over (b, pixel)
+    if (e >= (long)batch * pix) return;
+    const int b = (int)(e / pix);
+    const long q = e - (long)b * pix;
+    const long src = idx[b] * pix + q;
+    const float sg = sign[b];
+    const uint4 *xs = reinterpret_cast<const uint4 *>(X + src * 16);
+    uint4 *xd = reinterpret_cast<uint4 *>(xb + e * 16);
+    uint4 a = xs[0];
+    __nv_bfloat162 c01 = *reinterpret_cast<__nv_bfloat162 *>(&a.x);
+    const float2 f = __bfloat1622float2(c01);
+    a.x = pack_bf16(f.x * sg, f.y * sg);   // exact: a sign change
+    xd[0] = a;
+    xd[1] = xs[1];
+    const float2 y = reinterpret_cast<const float2 *>(Y)[src];
+    reinterpret_cast<float2 *>(yb)[e] = make_float2(y.x * sg, y.y * sg);
+}
+
 // Network output (FP32 NHWC, channels 0/1 of c) back to a complex FP64 mode
 // layout, scaled per mode: d = gain * rms_m * y.
 __global__ void k_unpack(const float *__restrict__ y, int c, const float *__restrict__ rms, float gain, int nr, int nz,
@@ -670,6 +711,37 @@ int pic_nn_pack_modes(const double *x, const float *shift, int nr, int nz, int n
     k_mode_ss<<<g1, 256, 0, st>>>((const double2 *)x, cells, nm, scratch);
     k_mode_rms<<<grid1(nm), 256, 0, st>>>(scratch, chunks, nm, cells, rms);
     k_pack<<<grid1((long)nm * cells), 256, 0, st>>>((const double2 *)x, rms, shift, nr, nz, nm, (bf16 *)out);
+    NN_CHECK();
+    return PIC_POISSON_OK;
+}
+
+int pic_nn_pack_target(const double *x, int nr, int nz, int nm, float *rms, double *scratch, float *out,
+                       void *stream) {
+    clear_error();
+    if (!x || !rms || !scratch || !out || nr <= 0 || nz <= 0 || nm <= 0) {
+        set_error("pack_target: bad arguments");
+        return PIC_POISSON_EINVAL;
+    }
+    const cudaStream_t st = (cudaStream_t)stream;
+    const long cells = (long)nr * nz;
+    const int chunks = 256;
+    dim3 g1(chunks, (nm + 31) / 32);
+    k_mode_ss<<<g1, 256, 0, st>>>((const double2 *)x, cells, nm, scratch);
+    k_mode_rms<<<grid1(nm), 256, 0, st>>>(scratch, chunks, nm, cells, rms);
+    k_pack_target<<<grid1((long)nm * cells), 256, 0, st>>>((const double2 *)x, rms, nr, nz, nm, out);
+    NN_CHECK();
+    return PIC_POISSON_OK;
+}
+
+int pic_nn_gather_batch(const void *X, const float *Y, const long *idx, const float *sign, int batch, long pixels,
+                        void *xb, float *yb, void *stream) {
+    clear_error();
+    if (!X || !Y || !idx || !sign || !xb || !yb || batch <= 0 || pixels <= 0) {
+        set_error("gather_batch: bad arguments");
+        return PIC_POISSON_EINVAL;
+    }
+    k_gather_batch<<<grid1((long)batch * pixels), 256, 0, (cudaStream_t)stream>>>(
+        (const bf16 *)X, Y, idx, sign, batch, pixels, (bf16 *)xb, yb);
     NN_CHECK();
     return PIC_POISSON_OK;
 }

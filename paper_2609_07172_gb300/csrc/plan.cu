@@ -148,8 +148,8 @@ int resolve(const pic_poisson_desc *in, pic_poisson_desc *d) {
             }
         }
     }
-    if (d->n_patches > 0 && (d->smooth_fused || !std::isfinite(d->phi_exposed))) {
-        set_error("a composite domain needs smooth_fused = 0 and a finite phi_exposed");
+    if (d->n_patches > 0 && !std::isfinite(d->phi_exposed)) {
+        set_error("a composite domain needs a finite phi_exposed");
         return PIC_POISSON_EINVAL;
     }
     if (d->z_faces && d->smooth_fused) {

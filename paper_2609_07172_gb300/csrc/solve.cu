@@ -132,7 +132,7 @@ int smooth_level(Runner &R, const Hier<T> &H, int l, int sweeps, bool skip_first
         if (sweeps == 0) return PIC_POISSON_OK;
         const bool res = !post && H.fres[l];
         RUN(R, ph, launch_smooth_fused(post ? H.fpost[l] : H.fpre[l], post ? H.g_fpost[l] : H.g_fpre[l],
-                                       2 * sweeps, res, R.st));
+                                       2 * sweeps, res, R.st, R.P.masked));
         R.account(ph, 3.0 * n * sizeof(V2<T>), 14.0 * sweeps * n);
         if (res)   // the fused restriction: b of the red cells, the coarse b, b_hat, u
             R.account(PIC_POISSON_PHASE_RESTRICT, n * sizeof(V2<T>) * (0.5 + 0.75), 9.0 * n);

@@ -80,8 +80,8 @@ extern "C" int pic_poisson_autotune(const pic_poisson_desc *descs, int n, const 
     repeats = std::max(1, std::min(repeats, 16));
     memset(out, 0, sizeof *out);
     const bool mixed = descs[0].precision == PIC_POISSON_MIXED;
-    bool composite = false;   // the fused smoother does not take composite domains
-    for (int p = 0; p < n; ++p) composite = composite || descs[p].n_patches > 0 || descs[p].z_faces;
+    bool composite = false;   // the fused smoother does not take non-uniform axial meshes
+    for (int p = 0; p < n; ++p) composite = composite || descs[p].z_faces;
     static const int sched[][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 2}, {2, 3}, {3, 3}};
     std::vector<Cand> cands;
     for (const auto &s : sched) {

@@ -75,6 +75,7 @@ def training_pairs(p, steps, seed=7, limit=None, tol=1e-11):
     pk = Packer(p)
     nm = pk.nm
     xs, es, rr = [], [], []
+    rms_t = torch.empty(nm, dtype=torch.float32, device=dev)   # the targets' per-mode RMS
     with B.Plan(p, graph=True) as plan:
         uprev = torch.zeros(plan.mode_shape, dtype=torch.float64, device=dev)
         for t in range(steps):
@@ -87,9 +88,9 @@ def training_pairs(p, steps, seed=7, limit=None, tol=1e-11):
             x, rms_r = pk.pack(r)
             xs.append(x.clone())
             rr.append(rms_r.clone())
-            em = e.permute(2, 0, 1, 3).contiguous()
-            rms_e = em.pow(2).mean(dim=(1, 2, 3)).sqrt().clamp_min(1e-300)
-            es.append((em / rms_e.view(nm, 1, 1, 1)).float())
+            y = torch.empty(nm, p.nz, p.nr, 2, dtype=torch.float32, device=dev)
+            _ok(nn_lib().pic_nn_pack_target(P(e), p.nr, p.nz, nm, P(rms_t), P(pk.scratch), P(y), _st()))
+            es.append(y)
             uprev = u
     X = torch.cat(xs)
     Y = torch.cat(es)
@@ -104,21 +105,24 @@ def train(net, X, Y, epochs=20, batch=16, lr=1e-3, seed=0, log=None):
     returns the mean loss of every epoch."""
     g = torch.Generator(device="cpu").manual_seed(seed)
     n = X.shape[0]
+    pix = X.shape[1] * X.shape[2]
     steps = max(1, n // batch) * epochs
     losses = []
     t0 = time.time()
     k = 0
+    xb = torch.empty((batch,) + tuple(X.shape[1:]), dtype=X.dtype, device=X.device)
+    yb = torch.empty((batch,) + tuple(Y.shape[1:]), dtype=Y.dtype, device=Y.device)
     for ep in range(epochs):
         ep_losses = []
         perm = torch.randperm(n, generator=g)
         for s in range(n // batch):
-            idx = perm[s * batch:(s + 1) * batch].to(X.device)
-            sign = (torch.randint(0, 2, (batch,), generator=g) * 2 - 1).to(X.device)
-            x = X[idx].clone()
-            x[..., :2] = x[..., :2] * sign.view(-1, 1, 1, 1).to(x.dtype)
-            y = Y[idx] * sign.view(-1, 1, 1, 1).float()
-            net.forward(x)
-            loss = net.loss_backward(y.contiguous())
+            # the batch's sample order and sign flips are drawn on the host;
+            # the gather and the flips run in a kernel
+            idx = perm[s * batch:(s + 1) * batch].to(torch.int64).to(X.device)
+            sign = (torch.randint(0, 2, (batch,), generator=g) * 2 - 1).float().to(X.device)
+            _ok(nn_lib().pic_nn_gather_batch(P(X), P(Y), P(idx), P(sign), batch, pix, P(xb), P(yb), _st()))
+            net.forward(xb)
+            loss = net.loss_backward(yb)
             cur = lr * 0.5 * (1.0 + math.cos(math.pi * k / steps))
             net.adam(cur)
             k += 1

@@ -47,6 +47,8 @@ _SIGS = {
     "pic_nn_to_bf16": "vvlv",
     "pic_nn_pack_modes": "vviiivvvv",
     "pic_nn_unpack_modes": "vivfiiivv",
+    "pic_nn_pack_target": "viiivvvv",
+    "pic_nn_gather_batch": "vvvvilvvv",
     "pic_nn_restrict2": "viiivv",
     "pic_nn_prolong2": "viiivv",
     "pic_nn_minres_step": "vvvvliidvvvv",
@@ -173,11 +175,14 @@ class UNet:
         return buf
 
     # ------------------------------------------------------------------ passes
+    # pic_nn_conv3x3 (tcgen05 where the shape tiles) or pic_nn_conv3x3_mma_sync (legacy path, for comparison)
+    conv_entry = "pic_nn_conv3x3"
+
     def _conv(self, name, x, cin, y, cout, n, hw, relu, y32=None, transposed=False):
         w = self.wt[name] if transposed else self.wb[name]
         bias = None if transposed else self.b[name]
-        _ok(nn_lib().pic_nn_conv3x3(P(x), cin, P(w), P(bias), P(y), P(y32), cout, n, hw[0], hw[1], int(relu),
-                                    _st()))
+        _ok(getattr(nn_lib(), self.conv_entry)(P(x), cin, P(w), P(bias), P(y), P(y32), cout, n, hw[0], hw[1],
+                                               int(relu), _st()))
 
     def forward(self, x):
         """x: BF16 [n, h, w, 16]; returns the FP32 output [n, h, w, 16] (a buffer, reused)."""

@@ -74,9 +74,9 @@ def test_patch_limits_and_settings_rejected():
     p = W.annulus(130, 8, 8).with_patches([(2 * a, 2 * a + 2, 0, 8) for a in range(65)])
     d, _ = B.make_desc(p)
     assert B.load().pic_poisson_query(ctypes.byref(d), ctypes.byref(lay)) == B.EINVAL
-    # the fused smoother does not take composite domains
+    # the fused smoother takes composite domains (per-row coefficient classes)
     d, _ = B.make_desc(W.channel_plume(64, 8, 48), precision=MIXED, smooth_fused=1)
-    assert B.load().pic_poisson_query(ctypes.byref(d), ctypes.byref(lay)) == B.EINVAL
+    assert B.load().pic_poisson_query(ctypes.byref(d), ctypes.byref(lay)) == B.OK
     # patch edges on odd cells leave a coarsest level beyond the dense limit
     p = W.annulus(256, 8, 64).with_patches([(1, 255, 1, 63)])
     d, _ = B.make_desc(p)

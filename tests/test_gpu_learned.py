@@ -200,3 +200,34 @@ def test_training_reduces_loss_and_warm_start_beats_previous_guess():
         gu = ws.guess(b1, u0)
         _, r_new = plan.mode_residual(gu, b1)
     assert r_new <= r_prev * (1 + 1e-12)
+
+
+def test_training_target_and_batch_gather_kernels():
+    """pic_nn_pack_target (per-mode unit-RMS FP32 targets) and
+    pic_nn_gather_batch (sample gather with sign flips) against plain torch."""
+    lib = nn_lib()
+    nr, nz, nm = 24, 16, 9
+    g = torch.Generator(device="cpu").manual_seed(8)
+    x = torch.randn(nz, nr, nm, 2, generator=g, dtype=torch.float64).cuda() * torch.arange(1, nm + 1).view(1, 1, nm, 1).cuda()
+    rms = torch.empty(nm, dtype=torch.float32, device="cuda")
+    scratch = torch.empty(256 * nm, dtype=torch.float64, device="cuda")
+    y = torch.empty(nm, nz, nr, 2, dtype=torch.float32, device="cuda")
+    _ok(lib.pic_nn_pack_target(P(x), nr, nz, nm, P(rms), P(scratch), P(y), _st()))
+    em = x.permute(2, 0, 1, 3)
+    comp_rms = em.pow(2).mean(dim=(1, 2, 3)).sqrt()          # per real component
+    assert torch.allclose(rms.double(), comp_rms * 2 ** 0.5, rtol=1e-6)   # of |x|
+    assert torch.allclose(y.double(), em / comp_rms.view(nm, 1, 1, 1), rtol=1e-6, atol=1e-6)
+    # gather with signs
+    n, pix = 7, nz * nr
+    X = torch.randn(n, nz, nr, 16, generator=g).to(torch.bfloat16).cuda()
+    Y = torch.randn(n, nz, nr, 2, generator=g).cuda()
+    idx = torch.tensor([5, 0, 3, 3], dtype=torch.int64).cuda()
+    sign = torch.tensor([1.0, -1.0, -1.0, 1.0]).cuda()
+    xb = torch.empty(4, nz, nr, 16, dtype=torch.bfloat16, device="cuda")
+    yb = torch.empty(4, nz, nr, 2, device="cuda")
+    _ok(lib.pic_nn_gather_batch(P(X), P(Y), P(idx), P(sign), 4, pix, P(xb), P(yb), _st()))
+    torch.cuda.synchronize()
+    want_x = X[idx].clone()
+    want_x[..., :2] *= sign.view(-1, 1, 1, 1).to(torch.bfloat16)
+    assert torch.equal(xb, want_x)
+    assert torch.equal(yb, Y[idx] * sign.view(-1, 1, 1, 1))

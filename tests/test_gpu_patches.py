@@ -129,22 +129,56 @@ def test_batch_mixes_composite_and_plain_problems(precision):
         assert rel_l2(phi.cpu().numpy(), ref) <= TOL[precision]
 
 
-def test_composite_plan_refuses_the_fused_smoother():
-    p = W.channel_plume(32, 8, 24)
+@pytest.mark.parametrize("graph", [False, True], ids=["hostloop", "graph"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_composite_domain_fused_smoother_matches_oracle(refs, name, graph):
+    """The fused FP32 smoother on per-row coefficient classes (south and north
+    couplings apart, the restriction's face conductances per class)."""
+    p, g, rho, ref = refs[name]
+    with Plan(p, precision=MIXED, smooth_fused=1, pre_sweeps=2, post_sweeps=2, graph=graph) as plan:
+        phi, info = plan.solve(dev(rho), tol=0.0)
+    got = phi.cpu().numpy()
+    assert info["status"] == B.OK, info
+    assert rel_l2(got, ref) <= TOL[MIXED], info
+    assert oracle.relres(g, rho, got) <= 1e-12
+    assert np.all(got.transpose(0, 2, 1)[~p.active_cells()] == 0.0)
+
+
+def test_fused_smoother_batch_mixes_composite_and_plain(refs):
+    """A batch of composite and plain problems: the per-row variant keeps the
+    three-class path for the plain ones."""
+    names = ["channel_plume_64x16x48", "island_128x32x64"]
+    probs = [refs[n][0] for n in names] + [with_bias_walls(W.annulus(64, 16, 48))]
+    rhos = [refs[n][2] for n in names] + [W.rho_plasma(probs[-1], seed=52)]
+    ref_plain, _ = oracle.solve3d(oracle.grid_from_problem(probs[-1]), rhos[-1], tol=1e-15)
+    refs_all = [refs[n][3] for n in names] + [ref_plain]
+    with BatchPlan(probs, precision=MIXED, smooth_fused=1, pre_sweeps=2, post_sweeps=1, graph=True) as bp:
+        phis, infos = bp.solve([dev(r) for r in rhos], tol=0.0)
+    for phi, ref, info in zip(phis, refs_all, infos):
+        assert info["status"] == B.OK, info
+        assert rel_l2(phi.cpu().numpy(), ref) <= TOL[MIXED]
+
+
+def test_fused_smoother_refused_on_axial_faces_only():
+    w = 1.02 ** np.arange(24)
+    q = W.annulus(32, 8, 24)
+    q = q.with_z_faces(q.z0 + (q.z1 - q.z0) * np.r_[0.0, np.cumsum(w)] / w.sum())
     with pytest.raises(B.PicPoissonError):
-        Plan(p, precision=MIXED, smooth_fused=1)
+        Plan(q, precision=MIXED, smooth_fused=1)
+    with Plan(W.channel_plume(32, 8, 24), precision=MIXED, smooth_fused=1):
+        pass
 
 
 def test_autotune_on_a_composite_domain(tmp_path):
-    """The tuner leaves out the fused smoother (it does not take patches) and
-    still returns a working schedule."""
+    """The tuner tries the fused smoother on a composite domain too and
+    returns a working schedule."""
     from paper_2609_07172_gb300 import autotune
     p = W.channel_plume(64, 16, 48)
     rho = dev(W.rho_plasma(p, seed=55))
     best = autotune([p], [rho], tol=1e-10, precision=MIXED, graph=True, repeats=1)
-    assert not any(t["fused"] for t in best["tried"])
+    assert any(t["fused"] for t in best["tried"])
     kw = {k: best[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads", "smooth_strip",
-                               "omega", "inner_first")}
+                               "omega", "inner_first", "smooth_fused")}
     with Plan(p, precision=MIXED, graph=True, **kw) as plan:
         phi, info = plan.solve(rho, tol=1e-10)
     assert info["status"] == B.OK and info["rel_res"] <= 1e-10
