@@ -144,8 +144,9 @@ typedef struct {
                                   patches is ignored and phi is returned as 0 there.  Coarsening halves
                                   a direction only while every patch boundary in it lies on a coarse
                                   face (protected faces); the coarsest level is solved densely and may
-                                  hold at most PIC_POISSON_MAX_DENSE active cells.  Not with
-                                  smooth_fused or the no-allocation residual. */
+                                  hold at most PIC_POISSON_MAX_DENSE active cells.  smooth_fused
+                                  takes composite domains (per-row coefficient classes); the
+                                  no-allocation residual does not. */
     double phi_exposed;        /* Dirichlet potential of the exposed faces (V) */
     unsigned flags;            /* PIC_POISSON_* flags */
 } pic_poisson_desc;
@@ -280,8 +281,9 @@ int pic_poisson_solve_batch(pic_poisson_plan_t plan, const double *const *rho_de
  * the winner; stage 3 strips of 2 and 4 rows at the best block size; stage 4
  * over-relaxation omega = 1.1, 1.2, 1.3 with the schedules (1,1), (1,2),
  * (2,1), (2,2) at the best block size, strip and inner cycles; stage 5
- * (mixed precision) the fused smoother with the same four schedules and 1 to
- * 6 inner cycles, or (FP64) the full-multigrid start with the schedules (1,2),
+ * (mixed precision; not with axial faces) the fused smoother with the same
+ * four schedules and 1 to 6 inner cycles, or (FP64) the full-multigrid start
+ * with the schedules (1,2),
  * (2,1), (2,2); stage 6 (mixed precision) 1 to 3 extra first-correction
  * cycles (inner_first) with the best setting and with one inner cycle fewer.
  * Each
