@@ -34,6 +34,8 @@
 // b_hat (and b) into a ring that keeps each row until its last half-sweep,
 // so those values take no registers.
 #include <algorithm>
+#include <cstdlib>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -66,30 +68,41 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 
 constexpr int PAD = 16;           // >= the largest mode group: neighbour reads of the outermost pairs stay in the array
 
-// Sizes of a variant.  A step touches W0 rows; the register window holds W
-// rows (W0 made even) and the row loop is unrolled by W, so in each unrolled
-// copy the register that holds a given row, the parity of every row (hence
-// the colour a half-sweep updates in a pair and the column a thread
-// publishes), the publication buffer and the iterate's ring slot are
-// compile-time constants: no register shifts, selects or slot arithmetic per
-// step.  The iterate's ring has UR slots (UR divides W) and is fetched
-// DEPTH = UR - 1 rows ahead; b_hat (and b) stay in a ring of BR slots until
-// their last half-sweep (the restriction: NH + 1 steps after the row entered).
-// Without the restriction the kernel needs 80 registers and, with a shorter
-// ring, under 75 KB of shared memory: three blocks per SM (24 warps) instead
-// of two -- more warps to hide the copies, which now run 2 rows ahead.
+// Sizes of a variant.  The row loop runs in groups of U = 8 steps, each
+// unrolled, and every per-row resource cycles with a period dividing U: the
+// register window (U rows; a step touches at most NH + 3), the iterate's ring
+// (UR slots, fetched DEPTH rows ahead), the ring that keeps b_hat (and b)
+// from its fetch until its last half-sweep (BR slots; the restriction reads
+// b NH + 1 steps after the row entered) and the two publication buffers.  So
+// in each unrolled copy the register that holds a given row, the parity of
+// every row (hence the colour a half-sweep updates in a pair and the column a
+// thread publishes) and every ring slot are compile-time constants: no
+// register shifts, selects or slot arithmetic per step.
+//
+// Shared memory against L1.  The rows arrive by cp.async through L1, which
+// shares each SM's 256 KB with shared memory in fixed carveouts (..., 132,
+// 164, 196, 228 KB of shared memory).  Without the restriction the kernel
+// needs about 80 registers, so three blocks fit an SM; with NH = 4, a 4-slot
+// iterate ring (2 rows ahead) takes 67.7 KB per block and the three blocks
+// the 228 KB carveout, leaving L1 28 KB -- measured 0.4 ms slower per mixed
+// solve than a 2-slot ring fetched one row ahead (59.5 KB, the 196 KB
+// carveout, L1 60 KB).  With the restriction (two blocks per SM) the 4-slot
+// ring fits the 196 KB carveout, and there the deeper prefetch is faster
+// than a shorter ring in the 164 KB carveout.
 template <int NH, bool RES> struct FusedCfg {
-    static constexpr int W0 = NH + 2 + (RES ? 1 : 0);
-    static constexpr int W = W0 + (W0 & 1);
-    static constexpr int UR = RES ? ((W % 6 == 0) ? 6 : 4) : (W % 3 == 0 ? 3 : 4);
-    static constexpr int DEPTH = UR - 1;
-    static constexpr int BR = DEPTH + NH + 2;
+    static constexpr bool SHORT = !RES && NH == 4;
+    static constexpr int U = 8;
+    static constexpr int UR = SHORT ? 2 : 4;
+    static constexpr int DEPTH = SHORT ? 1 : 2;
+    static constexpr int BR = 8;
     static constexpr int NB = RES ? 3 : 2;                  // b_hat col 0, b_hat col 1 (, b of the red cell)
     static constexpr int NP = NH + (RES ? 1 : 0);           // published columns per step
     static constexpr int PS = FUSED_THREADS + 2 * PAD;      // published row stride
     static constexpr size_t smem_floats2 =
         (size_t)UR * 2 * FUSED_THREADS + (size_t)BR * NB * FUSED_THREADS + PAD + (size_t)2 * NP * PS;
-    static_assert(W % UR == 0 && W % 2 == 0, "unrolled copies need static ring slots and parities");
+    static_assert(NH + 2 + (RES ? 1 : 0) <= U, "the window holds every row a step touches");
+    static_assert(DEPTH < UR && DEPTH + NH + 2 <= BR, "a ring slot is refilled only after its last read");
+    static_assert(U % UR == 0 && U % BR == 0 && U % 2 == 0, "static ring slots, parities and buffers");
 };
 
 // RES (pre-smoothing of a level coarsened 2:1 in both directions): after the
@@ -102,7 +115,7 @@ template <int NH, bool RES> struct FusedCfg {
 template <int NH, bool RES, bool RW>
 __global__ void __launch_bounds__(FUSED_THREADS, RES ? 2 : 3) k_smooth_fused(const FusedTab *__restrict__ tab) {
     using Cfg = FusedCfg<NH, RES>;
-    constexpr int W = Cfg::W, UR = Cfg::UR, DEPTH = Cfg::DEPTH, BR = Cfg::BR, NB = Cfg::NB, NP = Cfg::NP;
+    constexpr int U = Cfg::U, UR = Cfg::UR, DEPTH = Cfg::DEPTH, BR = Cfg::BR, NB = Cfg::NB, NP = Cfg::NP;
     constexpr int PS = Cfg::PS;
     constexpr int HP = NH / 2 + (RES ? 1 : 0);  // halo pairs on each side
     constexpr int NT = FUSED_THREADS;
@@ -156,20 +169,25 @@ __global__ void __launch_bounds__(FUSED_THREADS, RES ? 2 : 3) k_smooth_fused(con
     const float hz1 = v1 ? L.hz[cls1 + c1] : 0.f, hw1 = v1 ? L.hw[cls1 + c1] : 0.f,
                 he1 = v1 ? L.he[cls1 + c1] : 0.f;
 
-    // fetch row `row` into ring slots (zeros for rows outside [ks, ke) and invalid cells)
+    // Fetch row `row` into the ring slots of unrolled copy cs (ring slots and
+    // the row's parity follow from cs: ks is even and a group has U steps);
+    // zeros for rows at or beyond ke and for invalid cells.  FAST: the row is
+    // known to lie below ke.
     const float2 *gin0 = F.in + c0, *gin1 = F.in + c1, *gb0 = L.bh + c0, *gb1 = L.bh + c1;
-    auto fetch = [&](int row, int us, int bs) {
-        const bool ok = row < ke;
+    const float2 *gr0 = L.b + c0, *gr1 = L.b + c1;
+    auto fetch = [&](int row, const int cs, auto fast_tag) {
+        constexpr bool FAST = decltype(fast_tag)::value;
+        const bool ok = FAST || row < ke;
         const unsigned o = (unsigned)(ok ? row : ks) * rs;
-        float2 *ru = uring + us * 2 * NT + t;
-        float2 *rb = bring + bs * NB * NT + t;
+        float2 *ru = uring + (cs % UR) * 2 * NT + t;
+        float2 *rb = bring + (cs % BR) * NB * NT + t;
         cp_async8(ru, gin0 + o, ok && v0);
         cp_async8(ru + NT, gin1 + o, ok && v1);
         cp_async8(rb, gb0 + o, ok && v0);
         cp_async8(rb + NT, gb1 + o, ok && v1);
         if (RES) {   // b of the row's red cell: column parity = row parity
-            const bool q1 = (row & 1) != 0;
-            cp_async8(rb + 2 * NT, L.b + o + (q1 ? c1 : c0), ok && (q1 ? v1 : v0));
+            if ((cs & 1) == 0) cp_async8(rb + 2 * NT, gr0 + o, ok && v0);
+            else cp_async8(rb + 2 * NT, gr1 + o, ok && v1);
         }
         cp_async_commit();
     };
@@ -179,7 +197,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, RES ? 2 : 3) k_smooth_fused(con
         pubs[row * PS + (x < PAD ? x - PAD : NT + x - PAD)] = make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int d = 0; d < DEPTH; ++d) fetch(ks + d, d, d);
+    for (int d = 0; d < DEPTH; ++d) fetch(ks + d, d, std::false_type{});
 
     // residual coefficients of the pair's columns (RES)
     float cz0 = 0.f, cw0 = 0.f, ce0 = 0.f, dg0 = 0.f, cz1 = 0.f, cw1 = 0.f, ce1 = 0.f, dg1 = 0.f;
@@ -207,194 +225,203 @@ __global__ void __launch_bounds__(FUSED_THREADS, RES ? 2 : 3) k_smooth_fused(con
     float2 *const gout = F.out;
 
     const float2 zero = make_float2(0.f, 0.f);
-    // window: row k - d lives in register (c - d) mod W at unrolled copy c
-    float2 u0[W], u1[W];
+    // window: row k - d lives in register (c - d) mod U at unrolled copy c
+    float2 u0[U], u1[U];
 #pragma unroll
-    for (int w = 0; w < W; ++w) u0[w] = u1[w] = zero;
-    int bsl = 0;   // b ring slot of the row entering now
-#define IX(d) ((((c) - (d)) % W + W) % W)
-#pragma unroll 1
-    for (int n0 = 0;; n0 += W) {
+    for (int w = 0; w < U; ++w) u0[w] = u1[w] = zero;
+#define IX(d) ((((c) - (d)) % U + U) % U)
+#define SLOT(d, N) ((((c) - (d)) % (N) + (N)) % (N))
+    // One step: row k enters at unrolled copy c.  FAST (decided per step,
+    // uniformly): every row the step updates, evaluates or writes lies inside
+    // the block's rows and off the level's first and last rows, row k + DEPTH
+    // lies below ke, and the level has the plain coefficient classes -- the
+    // interior of the sweep, where no range, edge or class test remains.
+    auto step = [&](const int c, const int k, auto fast_tag) {
+        constexpr bool FAST = decltype(fast_tag)::value;
+        const int buf = c & 1;   // publication buffer written at this step
+        // (a) row k into the window; fetch row k + DEPTH
+        cp_async_wait<DEPTH - 1>();
+        u0[IX(0)] = uring[(c % UR) * 2 * NT + t];
+        u1[IX(0)] = uring[(c % UR) * 2 * NT + NT + t];
+        fetch(k + DEPTH, c + DEPTH, fast_tag);
+        // (b) half-sweep s on row k - 1 - s
 #pragma unroll
-        for (int c = 0; c < W; ++c) {
-            const int k = ks + n0 + c;   // the row entering at this step
-            if (k > klast) goto finished;   // uniform
-            const int buf = c & 1;          // publication buffer written at this step
-            // (a) row k into the window; fetch row k + DEPTH
-            cp_async_wait<DEPTH - 1>();
-            u0[IX(0)] = uring[(c % UR) * 2 * NT + t];
-            u1[IX(0)] = uring[(c % UR) * 2 * NT + NT + t];
-            {
-                int bs = bsl + DEPTH;
-                if (bs >= BR) bs -= BR;
-                fetch(k + DEPTH, (c + DEPTH) % UR, bs);
-            }
-            // (b) half-sweep s on row k - 1 - s
-#pragma unroll
-            for (int s = 0; s < NH; ++s) {
-                const int r = k - 1 - s;
-                if ((unsigned)(r - ks) >= (unsigned)(ke - ks)) continue;   // uniform: r outside [ks, ke)
-                const int sl = IX(1 + s);   // row r
-                const int sn = IX(s);       // row r + 1
-                const int ss = IX(2 + s);   // row r - 1
-                const int q = (c - 1 - s + (s & 1)) & 1;   // the pair's cell of this colour (static)
-                const bool edge = r == 0 || r == nz - 1;
-                const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + s) * PS;
-                int rb = bsl - 1 - s;
-                if (rb < 0) rb += BR;
-                const float2 *bh = bring + rb * NB * NT + t;
-                // Rows outside the level are zero in the window and the wall
-                // columns have zero coefficients towards the wall (h_w = 0 at
-                // i = 0, h_e = 0 at i = nr - 1), so every update is the same
-                // four multiply-adds per part -- the neighbour that does not
-                // exist contributes exactly zero, as when it is left out.
-                // The pair beyond a block's outermost pair reads padding
-                // (halo cells only).
-                if (q == 0) {
-                    const float2 uw = pr[t - G];   // west: column 1 of the pair on the left
-                    const float2 b = bh[0];
-                    float hz = hz0, hw = hw0, he = he0;
-                    float2 acc;
-                    if (rw) {   // the row's class: south and north apart
-                        const unsigned tb = (unsigned)L.rcls[r] * rs + c0;
-                        const float hs = v0 ? L.hz[tb] : 0.f, hn = v0 ? L.hn[tb] : 0.f;
+        for (int s = 0; s < NH; ++s) {
+            const int r = k - 1 - s;
+            if (!FAST && (unsigned)(r - ks) >= (unsigned)(ke - ks)) continue;   // uniform: r outside [ks, ke)
+            const int sl = IX(1 + s);   // row r
+            const int sn = IX(s);       // row r + 1
+            const int ss = IX(2 + s);   // row r - 1
+            const int q = (c - 1 - s + (s & 1)) & 1;   // the pair's cell of this colour (static)
+            const bool edge = !FAST && (r == 0 || r == nz - 1);
+            const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + s) * PS;
+            const float2 *bh = bring + SLOT(1 + s, BR) * NB * NT + t;
+            // Rows outside the level are zero in the window and the wall
+            // columns have zero coefficients towards the wall (h_w = 0 at
+            // i = 0, h_e = 0 at i = nr - 1), so every update is the same
+            // four multiply-adds per part -- the neighbour that does not
+            // exist contributes exactly zero, as when it is left out.
+            // The pair beyond a block's outermost pair reads padding
+            // (halo cells only).
+            if (q == 0) {
+                const float2 uw = pr[t - G];   // west: column 1 of the pair on the left
+                const float2 b = bh[0];
+                float hz = hz0, hw = hw0, he = he0;
+                float2 acc;
+                if (!FAST && rw) {   // the row's class: south and north apart
+                    const unsigned tb = (unsigned)L.rcls[r] * rs + c0;
+                    const float hs = v0 ? L.hz[tb] : 0.f, hn = v0 ? L.hn[tb] : 0.f;
+                    hw = v0 ? L.hw[tb] : 0.f;
+                    he = v0 ? L.he[tb] : 0.f;
+                    acc = make_float2(fmaf(hs, u0[ss].x, b.x), fmaf(hs, u0[ss].y, b.y));
+                    acc = make_float2(fmaf(hn, u0[sn].x, acc.x), fmaf(hn, u0[sn].y, acc.y));
+                } else {
+                    const float2 vs = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
+                    if (edge) {
+                        const unsigned tb = (unsigned)row_class(r, nz, ncls) * rs + c0;
+                        hz = v0 ? L.hz[tb] : 0.f;
                         hw = v0 ? L.hw[tb] : 0.f;
                         he = v0 ? L.he[tb] : 0.f;
-                        acc = make_float2(fmaf(hs, u0[ss].x, b.x), fmaf(hs, u0[ss].y, b.y));
-                        acc = make_float2(fmaf(hn, u0[sn].x, acc.x), fmaf(hn, u0[sn].y, acc.y));
-                    } else {
-                        const float2 vs = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
-                        if (edge) {
-                            const unsigned tb = (unsigned)row_class(r, nz, ncls) * rs + c0;
-                            hz = v0 ? L.hz[tb] : 0.f;
-                            hw = v0 ? L.hw[tb] : 0.f;
-                            he = v0 ? L.he[tb] : 0.f;
-                        }
-                        acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
                     }
-                    acc = make_float2(fmaf(hw, uw.x, acc.x), fmaf(hw, uw.y, acc.y));
-                    acc = make_float2(fmaf(he, u1[sl].x, acc.x), fmaf(he, u1[sl].y, acc.y));
-                    u0[sl] = acc;
+                    acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
+                }
+                acc = make_float2(fmaf(hw, uw.x, acc.x), fmaf(hw, uw.y, acc.y));
+                acc = make_float2(fmaf(he, u1[sl].x, acc.x), fmaf(he, u1[sl].y, acc.y));
+                u0[sl] = acc;
+            } else {
+                const float2 ue = pr[t + G];   // east: column 0 of the pair on the right
+                const float2 b = bh[NT];
+                float hz = hz1, hw = hw1, he = he1;
+                float2 acc;
+                if (!FAST && rw) {
+                    const unsigned tb = (unsigned)L.rcls[r] * rs + c1;
+                    const float hs = v1 ? L.hz[tb] : 0.f, hn = v1 ? L.hn[tb] : 0.f;
+                    hw = v1 ? L.hw[tb] : 0.f;
+                    he = v1 ? L.he[tb] : 0.f;
+                    acc = make_float2(fmaf(hs, u1[ss].x, b.x), fmaf(hs, u1[ss].y, b.y));
+                    acc = make_float2(fmaf(hn, u1[sn].x, acc.x), fmaf(hn, u1[sn].y, acc.y));
                 } else {
-                    const float2 ue = pr[t + G];   // east: column 0 of the pair on the right
-                    const float2 b = bh[NT];
-                    float hz = hz1, hw = hw1, he = he1;
-                    float2 acc;
-                    if (rw) {
-                        const unsigned tb = (unsigned)L.rcls[r] * rs + c1;
-                        const float hs = v1 ? L.hz[tb] : 0.f, hn = v1 ? L.hn[tb] : 0.f;
+                    const float2 vs = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
+                    if (edge) {
+                        const unsigned tb = (unsigned)row_class(r, nz, ncls) * rs + c1;
+                        hz = v1 ? L.hz[tb] : 0.f;
                         hw = v1 ? L.hw[tb] : 0.f;
                         he = v1 ? L.he[tb] : 0.f;
-                        acc = make_float2(fmaf(hs, u1[ss].x, b.x), fmaf(hs, u1[ss].y, b.y));
-                        acc = make_float2(fmaf(hn, u1[sn].x, acc.x), fmaf(hn, u1[sn].y, acc.y));
+                    }
+                    acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
+                }
+                acc = make_float2(fmaf(hw, u0[sl].x, acc.x), fmaf(hw, u0[sl].y, acc.y));
+                acc = make_float2(fmaf(he, ue.x, acc.x), fmaf(he, ue.y, acc.y));
+                u1[sl] = acc;
+            }
+        }
+        // (c) residual of the red cell of row k - NH - 1 and the coarse
+        // right-hand side of its 2x2 block (RES)
+        if (RES) {
+            const int rr = k - NH - 1;
+            if (FAST || (rr >= k0 && rr < k1)) {   // uniform
+                const int sl = IX(NH + 1), sn = IX(NH), ss = IX(NH + 2);
+                const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + NH) * PS;
+                const float2 bred = bring[SLOT(NH + 1, BR) * NB * NT + 2 * NT + t];
+                const bool edge = !FAST && (rr == 0 || rr == nz - 1);
+                float2 res;
+                if (((c - NH - 1) & 1) == 0) {   // red cell in column 0: west from the left pair
+                    const float2 uw = pr[t - G];
+                    float d, cw = cw0, ce = ce0;
+                    float2 a;
+                    if (!FAST && rw) {   // the row's class: face conductances toward active neighbours
+                        const unsigned cl = (unsigned)L.rcls[rr];
+                        const unsigned ci = cl * nr + (v0 ? i0 : 0);
+                        d = v0 ? L.diag[cl * rs + c0] : 0.f;
+                        cw = L.ccw[ci];
+                        ce = L.cce[ci];
+                        a = make_float2(fmaf(L.ccs[ci], u0[ss].x, bred.x), fmaf(L.ccs[ci], u0[ss].y, bred.y));
+                        a = make_float2(fmaf(L.ccn[ci], u0[sn].x, a.x), fmaf(L.ccn[ci], u0[sn].y, a.y));
                     } else {
-                        const float2 vs = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
-                        if (edge) {
-                            const unsigned tb = (unsigned)row_class(r, nz, ncls) * rs + c1;
-                            hz = v1 ? L.hz[tb] : 0.f;
-                            hw = v1 ? L.hw[tb] : 0.f;
-                            he = v1 ? L.he[tb] : 0.f;
-                        }
-                        acc = make_float2(fmaf(hz, vs.x, b.x), fmaf(hz, vs.y, b.y));
+                        d = edge ? L.diag[(unsigned)row_class(rr, nz, ncls) * rs + c0] : dg0;
+                        const float2 s = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
+                        a = make_float2(fmaf(cz0, s.x, bred.x), fmaf(cz0, s.y, bred.y));
                     }
-                    acc = make_float2(fmaf(hw, u0[sl].x, acc.x), fmaf(hw, u0[sl].y, acc.y));
-                    acc = make_float2(fmaf(he, ue.x, acc.x), fmaf(he, ue.y, acc.y));
-                    u1[sl] = acc;
-                }
-            }
-            // (c) residual of the red cell of row k - NH - 1 and the coarse
-            // right-hand side of its 2x2 block (RES)
-            if (RES) {
-                const int rr = k - NH - 1;
-                if (rr >= k0 && rr < k1) {   // uniform
-                    const int sl = IX(NH + 1), sn = IX(NH), ss = IX(NH + 2);
-                    const float2 *pr = pubs + (size_t)((buf ^ 1) * NP + NH) * PS;
-                    int rb = bsl - NH - 1;
-                    if (rb < 0) rb += BR;
-                    const float2 bred = bring[rb * NB * NT + 2 * NT + t];
-                    const bool edge = rr == 0 || rr == nz - 1;
-                    float2 res;
-                    if (((c - NH - 1) & 1) == 0) {   // red cell in column 0: west from the left pair
-                        const float2 uw = pr[t - G];
-                        float d, cw = cw0, ce = ce0;
-                        float2 a;
-                        if (rw) {   // the row's class: face conductances toward active neighbours
-                            const unsigned cl = (unsigned)L.rcls[rr];
-                            const unsigned ci = cl * nr + (v0 ? i0 : 0);
-                            d = v0 ? L.diag[cl * rs + c0] : 0.f;
-                            cw = L.ccw[ci];
-                            ce = L.cce[ci];
-                            a = make_float2(fmaf(L.ccs[ci], u0[ss].x, bred.x), fmaf(L.ccs[ci], u0[ss].y, bred.y));
-                            a = make_float2(fmaf(L.ccn[ci], u0[sn].x, a.x), fmaf(L.ccn[ci], u0[sn].y, a.y));
-                        } else {
-                            d = edge ? L.diag[(unsigned)row_class(rr, nz, ncls) * rs + c0] : dg0;
-                            const float2 s = make_float2(u0[ss].x + u0[sn].x, u0[ss].y + u0[sn].y);
-                            a = make_float2(fmaf(cz0, s.x, bred.x), fmaf(cz0, s.y, bred.y));
-                        }
-                        a = make_float2(fmaf(cw, uw.x, a.x), fmaf(cw, uw.y, a.y));
-                        a = make_float2(fmaf(ce, u1[sl].x, a.x), fmaf(ce, u1[sl].y, a.y));
-                        res = make_float2(fmaf(-d, u0[sl].x, a.x), fmaf(-d, u0[sl].y, a.y));
-                        rsum = res;
-                    } else {                          // red cell in column 1: east from the right pair
-                        const float2 ue = pr[t + G];
-                        float d, cw = cw1, ce = ce1;
-                        float2 a;
-                        if (rw) {
-                            const unsigned cl = (unsigned)L.rcls[rr];
-                            const unsigned ci = cl * nr + (v1 ? i1 : 0);
-                            d = v1 ? L.diag[cl * rs + c1] : 0.f;
-                            cw = L.ccw[ci];
-                            ce = L.cce[ci];
-                            a = make_float2(fmaf(L.ccs[ci], u1[ss].x, bred.x), fmaf(L.ccs[ci], u1[ss].y, bred.y));
-                            a = make_float2(fmaf(L.ccn[ci], u1[sn].x, a.x), fmaf(L.ccn[ci], u1[sn].y, a.y));
-                        } else {
-                            d = edge ? L.diag[(unsigned)row_class(rr, nz, ncls) * rs + c1] : dg1;
-                            const float2 s = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
-                            a = make_float2(fmaf(cz1, s.x, bred.x), fmaf(cz1, s.y, bred.y));
-                        }
-                        a = make_float2(fmaf(cw, u0[sl].x, a.x), fmaf(cw, u0[sl].y, a.y));
-                        a = make_float2(fmaf(ce, ue.x, a.x), fmaf(ce, ue.y, a.y));
-                        res = make_float2(fmaf(-d, u1[sl].x, a.x), fmaf(-d, u1[sl].y, a.y));
-                        const float2 sum = make_float2(rsum.x + res.x, rsum.y + res.y);
-                        if (cwrite) {
-                            const int K = rr >> 1;
-                            const unsigned e = (unsigned)K * cnr * nm + ccol;
-                            cb[e] = sum;
-                            if (finit > 0) {
-                                const float inv =
-                                    crcls ? cinvd[(unsigned)crcls[K] * cnr * nm + ccol]
-                                    : (K == 0 || K == cnz - 1)
-                                        ? cinvd[(unsigned)row_class(K, cnz, cncls) * cnr * nm + ccol]
-                                        : cinv1;
-                                const float2 bhc = make_float2(sum.x * inv, sum.y * inv);
-                                cbh[e] = bhc;
-                                cu[e] = (finit == 2 && ((K + j) & 1) == 0) ? bhc : zero;
-                            }
+                    a = make_float2(fmaf(cw, uw.x, a.x), fmaf(cw, uw.y, a.y));
+                    a = make_float2(fmaf(ce, u1[sl].x, a.x), fmaf(ce, u1[sl].y, a.y));
+                    res = make_float2(fmaf(-d, u0[sl].x, a.x), fmaf(-d, u0[sl].y, a.y));
+                    rsum = res;
+                } else {                          // red cell in column 1: east from the right pair
+                    const float2 ue = pr[t + G];
+                    float d, cw = cw1, ce = ce1;
+                    float2 a;
+                    if (!FAST && rw) {
+                        const unsigned cl = (unsigned)L.rcls[rr];
+                        const unsigned ci = cl * nr + (v1 ? i1 : 0);
+                        d = v1 ? L.diag[cl * rs + c1] : 0.f;
+                        cw = L.ccw[ci];
+                        ce = L.cce[ci];
+                        a = make_float2(fmaf(L.ccs[ci], u1[ss].x, bred.x), fmaf(L.ccs[ci], u1[ss].y, bred.y));
+                        a = make_float2(fmaf(L.ccn[ci], u1[sn].x, a.x), fmaf(L.ccn[ci], u1[sn].y, a.y));
+                    } else {
+                        d = edge ? L.diag[(unsigned)row_class(rr, nz, ncls) * rs + c1] : dg1;
+                        const float2 s = make_float2(u1[ss].x + u1[sn].x, u1[ss].y + u1[sn].y);
+                        a = make_float2(fmaf(cz1, s.x, bred.x), fmaf(cz1, s.y, bred.y));
+                    }
+                    a = make_float2(fmaf(cw, u0[sl].x, a.x), fmaf(cw, u0[sl].y, a.y));
+                    a = make_float2(fmaf(ce, ue.x, a.x), fmaf(ce, ue.y, a.y));
+                    res = make_float2(fmaf(-d, u1[sl].x, a.x), fmaf(-d, u1[sl].y, a.y));
+                    const float2 sum = make_float2(rsum.x + res.x, rsum.y + res.y);
+                    if (cwrite) {
+                        const int K = rr >> 1;
+                        const unsigned e = (unsigned)K * cnr * nm + ccol;
+                        cb[e] = sum;
+                        if (finit > 0) {
+                            const float inv =
+                                crcls ? cinvd[(unsigned)crcls[K] * cnr * nm + ccol]
+                                : (K == 0 || K == cnz - 1)
+                                    ? cinvd[(unsigned)row_class(K, cnz, cncls) * cnr * nm + ccol]
+                                    : cinv1;
+                            const float2 bhc = make_float2(sum.x * inv, sum.y * inv);
+                            cbh[e] = bhc;
+                            cu[e] = (finit == 2 && ((K + j) & 1) == 0) ? bhc : zero;
                         }
                     }
                 }
             }
-            // (d) publish for the next step: half-sweep s will update row k - s
-            // and read the neighbouring pair's column of the other colour;
-            // the restriction reads the final black column of row k - NH
-            float2 *pw = pubs + (size_t)(buf * NP) * PS + t;
+        }
+        // (d) publish for the next step: half-sweep s will update row k - s
+        // and read the neighbouring pair's column of the other colour;
+        // the restriction reads the final black column of row k - NH
+        float2 *pw = pubs + (size_t)(buf * NP) * PS + t;
 #pragma unroll
-            for (int s = 0; s < NH; ++s) {
-                const int qn = (c - s + (s & 1)) & 1;
-                pw[(size_t)s * PS] = qn == 0 ? u1[IX(s)] : u0[IX(s)];
+        for (int s = 0; s < NH; ++s) {
+            const int qn = (c - s + (s & 1)) & 1;
+            pw[(size_t)s * PS] = qn == 0 ? u1[IX(s)] : u0[IX(s)];
+        }
+        if (RES) pw[(size_t)NH * PS] = ((c - NH) & 1) == 0 ? u1[IX(NH)] : u0[IX(NH)];
+        // (e) the output row k - NH is final
+        const int ro = k - NH;
+        if (outpair && (FAST || (ro >= k0 && ro < k1))) {
+            const unsigned o = (unsigned)ro * rs;
+            if (v0) gout[o + c0] = u0[IX(NH)];
+            if (v1) gout[o + c1] = u1[IX(NH)];
+        }
+        __syncthreads();
+    };
+    // the steps that take the FAST body: kf0 <= k < kf0 + nfast (none for
+    // per-row classes; an empty range when the block's rows are too few)
+    const int kf0 = max(k0, 1) + NH + (RES ? 1 : 0);
+    const unsigned nfast = rw ? 0u : (unsigned)max(min(ke - DEPTH - 1, k1 + NH - 1) - kf0 + 1, 0);
+#pragma unroll 1
+    for (int n0 = 0;; n0 += U) {
+#pragma unroll
+        for (int c = 0; c < U; ++c) {
+            const int k = ks + n0 + c;   // the row entering at this step
+            if ((unsigned)(k - kf0) < nfast) {   // uniform
+                step(c, k, std::true_type{});
+            } else {
+                if (k > klast) goto finished;   // uniform
+                step(c, k, std::false_type{});
             }
-            if (RES) pw[(size_t)NH * PS] = ((c - NH) & 1) == 0 ? u1[IX(NH)] : u0[IX(NH)];
-            // (e) the output row k - NH is final
-            const int ro = k - NH;
-            if (outpair && ro >= k0 && ro < k1) {
-                const unsigned o = (unsigned)ro * rs;
-                if (v0) gout[o + c0] = u0[IX(NH)];
-                if (v1) gout[o + c1] = u1[IX(NH)];
-            }
-            __syncthreads();
-            bsl = bsl + 1 == BR ? 0 : bsl + 1;
         }
     }
+#undef SLOT
 #undef IX
 finished:
     cp_async_wait<0>();   // no copy outlives the block
@@ -403,7 +430,8 @@ finished:
 }  // namespace
 
 template <int NH, bool RES, bool RW> cudaError_t launch_nh(const FusedTab *tab, unsigned grid, cudaStream_t st) {
-    const size_t smem = FusedCfg<NH, RES>::smem_floats2 * sizeof(float2);
+    size_t smem = FusedCfg<NH, RES>::smem_floats2 * sizeof(float2);
+    if (!RES) if (const char *ev = getenv("PIC_FUSED_POST_SMEM")) smem = std::max(smem, (size_t)atoi(ev));   // TEMP
     cudaError_t e =
         cudaFuncSetAttribute(k_smooth_fused<NH, RES, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

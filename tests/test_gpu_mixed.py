@@ -111,11 +111,18 @@ def test_fused_smoother_matches_oracle(dims, sweeps):
     assert rel_l2(phi.cpu().numpy(), ref) <= MIXED_TOL, info
 
 
+BITWISE_CASES = [(96, 32, 72), (512, 128, 64), (256, 64, 200)]
+
+
 @pytest.mark.parametrize("sweeps", [(1, 2), (2, 2)])
-def test_fused_smoother_is_bitwise_the_separate_half_sweeps(sweeps):
+@pytest.mark.parametrize("dims", BITWISE_CASES, ids=[f"{a}x{b}x{c}" for a, b, c in BITWISE_CASES])
+def test_fused_smoother_is_bitwise_the_separate_half_sweeps(dims, sweeps):
     """Fusing changes where values live and when they move, not the arithmetic:
-    the solve is bitwise identical to separate half-sweeps, cycle for cycle."""
-    p = with_bias_walls(W.annulus(96, 32, 72))
+    the solve is bitwise identical to separate half-sweeps, cycle for cycle.
+    The larger cases give each block long row ranges, so most row steps take
+    the kernel's interior body (no range, wall-row or class tests) and the
+    rest its general body."""
+    p = with_bias_walls(W.annulus(*dims))
     rho = dev(W.rho_plasma(p, seed=32))
     out = []
     for fused in (0, 1):
