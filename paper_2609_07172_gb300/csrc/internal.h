@@ -108,6 +108,9 @@ template <class T> struct CoarseDev {
     const float *lam;             // [nact] eigenvalues of M^(-1/2) A_0 M^(-1/2)
     const float *isq;             // [nact] 1 / sqrt(mu) of each active cell
     const float *lamm;            // [nm] lambda_m
+    float *Y, *Z;                 // [2 nm][nact] scratch of the dense solve: y = M^(-1/2) b scaled, then
+                                  // z = (Lambda + lambda_m)^(-1) Q^T y, one column per (mode, part)
+    double *up;                   // [2 nm] the power of two each column was scaled down by
 };
 
 // Work of one launch over a batch of problems: problem p owns the blocks
@@ -132,6 +135,19 @@ template <class T> struct CoarseTab {
     LevelDev<T> f[kMaxBatch];
     CoarseDev<T> c[kMaxBatch];
     size_t smem;                  // dynamic shared memory of the largest problem
+};
+
+// The dense coarsest solves of a batch (csrc/dense.cu): problem p owns the
+// blocks [start[p], start[p+1]) of the preparation launch (one per mode and
+// part) and [gstart[p], gstart[p+1]) of each GEMM launch (one per tile).
+template <class T> struct DenseTab {
+    int n;
+    const int *done;
+    int pid[kMaxBatch];
+    unsigned start[kMaxBatch + 1];
+    unsigned gstart[kMaxBatch + 1];
+    LevelDev<T> f[kMaxBatch];     // the coarsest level (b in, u out)
+    CoarseDev<T> c[kMaxBatch];
 };
 
 struct DefectTab {                // mixed precision: FP64 level 0 and FP32 level 0 of each problem
@@ -253,6 +269,10 @@ cudaError_t launch_prolong(const LaunchTab<T> *tab, unsigned grid, bool black_on
                            bool masked = false);
 template <class T>
 cudaError_t launch_coarse(const CoarseTab<T> *tab, unsigned grid, size_t smem, cudaStream_t st);
+// Dense coarsest solves, in stage order: 0 preparation (g_prep blocks), 1 and 2 the two GEMMs (g_gemm blocks).
+template <class T>
+cudaError_t launch_dense(const DenseTab<T> *tab, int stage, unsigned g_prep, unsigned g_gemm, cudaStream_t st);
+unsigned dense_gemm_blocks(int nact, int nm);   // GEMM blocks of one problem
 // Full-multigrid start: u_f = P u_c on every fine cell; coarse b = restricted fine b.
 template <class T>
 cudaError_t launch_interp(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st, bool masked = false);

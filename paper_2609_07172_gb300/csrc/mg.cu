@@ -608,54 +608,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_coarse(const CoarseTab<T> *__res
     const int nr = D.nr, nz = D.nz, nm = D.nm;
     const int lb = (int)(blockIdx.x - tab->start[p]);
     const int m = lb >> 1, comp = lb & 1;
-    if (D.nact > 0) {
-        // per-row tables (composite domain or non-uniform axial mesh):
-        // u = M^(-1/2) Q (Lambda + lambda_m)^(-1) Q^T M^(-1/2) b over the active
-        // cells (eigenvectors from plan time, shared by all modes); zero
-        // elsewhere.  In FP32 for both hierarchies: a coarse-grid correction
-        // needs no FP64 accuracy (the smoother and residual stay in the
-        // level's precision), and the FP32 pipe is 64 times the FP64 one.
-        // b is first scaled by a power of two (exact) that brings its largest
-        // value of this (mode, part) to O(1), so FP32 spans any FP64 range.
-        __shared__ int s_emax;
-        const int n = D.nact;
-        float *y = (float *)smraw, *z = y + n;
-        const T *bg = (const T *)L.b + comp;
-        if (threadIdx.x == 0) s_emax = -1100;
-        __syncthreads();
-        int em = -1100;
-        for (int a = threadIdx.x; a < n; a += blockDim.x) {
-            const double v = (double)bg[2 * ((size_t)D.aidx[a] * nm + m)];
-            int e = -1100;
-            if (v != 0.0) frexp(v, &e);
-            em = max(em, e);
-        }
-        atomicMax(&s_emax, em);
-        __syncthreads();
-        const int E = s_emax > -1100 ? s_emax : 0;
-        const double down = ldexp(1.0, -E), up = ldexp(1.0, E);
-        for (int a = threadIdx.x; a < n; a += blockDim.x)
-            y[a] = (float)((double)bg[2 * ((size_t)D.aidx[a] * nm + m)] * down) * D.isq[a];
-        __syncthreads();
-        const float lm = D.lamm[m];
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {   // z = (Lambda + lambda_m)^(-1) Q^T y
-            float acc = 0.f;
-            for (int a = 0; a < n; ++a) acc = fmaf(D.Q[(size_t)a * n + j], y[a], acc);
-            z[j] = acc / (D.lam[j] + lm);
-        }
-        __syncthreads();
-        T *ug = (T *)L.u + comp;
-        for (int f = threadIdx.x; f < nr * nz; f += blockDim.x) {   // u = M^(-1/2) Q z
-            const int a = D.amap[f];
-            float x = 0.f;
-            if (a >= 0) {
-                for (int j = 0; j < n; ++j) x = fmaf(D.QT[(size_t)j * n + a], z[j], x);
-                x *= D.isq[a];
-            }
-            ug[2 * ((size_t)f * nm + m)] = (T)((double)x * up);
-        }
-        return;
-    }
+    // (a composite domain or non-uniform axial mesh takes the dense solve of csrc/dense.cu)
     const int h = nz >> 1, hz = nz - h;      // mirror pairs, rows with k <= nz-1-k
     T *bs = (T *)smraw;                      // [nz][nr]: b, then P (rows < hz) and Q (row nz-1-k)
     const int lw = nr + 1;                   // padded rows: the Thomas threads walk rows

@@ -680,10 +680,15 @@ template <class T> void carve_coarse(const ProblemPlan &q, Carver &c, CoarseDev<
         cd.lam = c.take<float>(na);
         cd.isq = c.take<float>(na);
         cd.lamm = c.take<float>(q.nm);
+        cd.Y = c.take<float>(na * 2 * q.nm);
+        cd.Z = c.take<float>(na * 2 * q.nm);
+        cd.up = c.take<double>(2 * (size_t)q.nm);
         return;
     }
     cd.aidx = cd.amap = nullptr;
     cd.Q = cd.QT = cd.lam = cd.isq = cd.lamm = nullptr;
+    cd.Y = cd.Z = nullptr;
+    cd.up = nullptr;
     cd.V = c.take<T>((size_t)h.nz * h.nz);
     cd.e = c.take<T>(h.nr);
     cd.piv = c.take<T>(nf);
@@ -713,6 +718,7 @@ template <class T> void carve_hier(pic_poisson_plan_s &P, Carver &c, Hier<T> &H)
         }
     }
     H.coarse = c.take<CoarseTab<T>>(1);
+    H.dense = c.take<DenseTab<T>>(1);
     H.bottom = c.take<BottomTab<T>>(1);
 }
 
@@ -968,8 +974,9 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
         }
     }
     CoarseTab<T> tc{};
+    DenseTab<T> td{};
     BottomTab<T> tb{};
-    tc.done = tb.done = ctrl_done(P);
+    tc.done = td.done = tb.done = ctrl_done(P);
     size_t smem_b = 0;
     for (int p = 0; p < P.n; ++p) {
         const ProblemPlan &q = P.pr[p];
@@ -990,19 +997,30 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
             ++tb.n;
             continue;
         }
+        if (cd.nact > 0) {   // dense coarsest solve: two GEMMs over all modes
+            td.pid[td.n] = p;
+            td.f[td.n] = views(q)[q.L - 1];
+            td.c[td.n] = cd;
+            td.start[td.n + 1] = td.start[td.n] + 2u * (unsigned)q.nm;
+            td.gstart[td.n + 1] = td.gstart[td.n] + dense_gemm_blocks(cd.nact, q.nm);
+            ++td.n;
+            continue;
+        }
         tc.pid[tc.n] = p;
         tc.f[tc.n] = views(q)[q.L - 1];
         tc.c[tc.n] = cd;
         tc.start[tc.n + 1] = tc.start[tc.n] + 2u * (unsigned)q.nm;   // (mode, real / imaginary part)
-        const size_t sm = cd.nact > 0 ? 2 * (size_t)cd.nact * sizeof(float)   // dense: y and z
-                                       : ((size_t)cd.nr * cd.nz + (size_t)(cd.nr + 1) * cd.nz +
-                                          (size_t)(cd.nz - cd.nz / 2) * cd.nz) * sizeof(T);
+        const size_t sm = ((size_t)cd.nr * cd.nz + (size_t)(cd.nr + 1) * cd.nz +
+                           (size_t)(cd.nz - cd.nz / 2) * cd.nz) * sizeof(T);
         tc.smem = std::max(tc.smem, sm);
         ++tc.n;
     }
     H.g_coarse = tc.start[tc.n];
     H.smem_coarse = tc.smem;
     blob_to_dev(tc, H.coarse, st, err);
+    H.g_dense_prep = td.start[td.n];
+    H.g_dense_gemm = td.gstart[td.n];
+    if (td.n) blob_to_dev(td, H.dense, st, err);
     H.g_bottom = tb.start[tb.n];
     H.smem_bottom = smem_b;
     if (tb.n) blob_to_dev(tb, H.bottom, st, err);

@@ -56,7 +56,9 @@ template <class T> struct Hier {
     std::vector<FusedTab *> fpre, fpost;
     std::vector<unsigned> g_fpre, g_fpost;
     std::vector<char> fres;                               // per level: pre-smoothing also restricts
-    CoarseTab<T> *coarse = nullptr;           // problems solved by k_coarse
+    CoarseTab<T> *coarse = nullptr;           // problems solved by k_coarse (separable coarsest level)
+    DenseTab<T> *dense = nullptr;             // problems with a dense coarsest solve (csrc/dense.cu)
+    unsigned g_dense_prep = 0, g_dense_gemm = 0;
     unsigned g_coarse = 0;
     size_t smem_coarse = 0;
     std::vector<LaunchTab<T> *> rhs, interp;  // full-multigrid start: b restricted to l + 1, u_l = P u_(l+1)

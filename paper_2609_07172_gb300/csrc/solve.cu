@@ -86,13 +86,29 @@ template <class T> double level_entries(const pic_poisson_plan_s &P, int l) {
 double coarse_entries(const pic_poisson_plan_s &P, double *flops_per) {
     double n = 0, f = 0;
     for (const ProblemPlan &q : P.pr) {
-        if (q.bottom) continue;
+        if (q.bottom || q.nact > 0) continue;
         const LevelHost &h = q.lv[q.L - 1];
         const double e = (double)h.nr * h.nz * q.nm;
         n += e;
         f += e * (4.0 * h.nz + 12.0);   // folded axial transforms (2 nz FMA) + Thomas, two parts
     }
     *flops_per = f;
+    return n;
+}
+// Dense coarsest solves: the level's complex entries, the eigenvector
+// matrices (read by the two GEMMs) and the FP32 multiply-adds.
+double dense_work(const pic_poisson_plan_s &P, double *qbytes, double *flops) {
+    double n = 0, qb = 0, f = 0;
+    for (const ProblemPlan &q : P.pr) {
+        if (q.bottom || q.nact == 0) continue;
+        const LevelHost &h = q.lv[q.L - 1];
+        const double na = q.nact;
+        n += (double)h.nr * h.nz * q.nm;
+        qb += 2.0 * na * na * sizeof(float);
+        f += 2.0 * 2.0 * na * na * 2.0 * q.nm;   // two n x n by n x 2 nm products
+    }
+    *qbytes = qb;
+    *flops = f;
     return n;
 }
 double level0_entries(const pic_poisson_plan_s &P, int which /*0 all, 1 single-level only*/) {
@@ -176,6 +192,18 @@ int coarse_and_bottom(Runner &R, const Hier<T> &H) {
     if (H.g_coarse) {
         RUN(R, PIC_POISSON_PHASE_COARSE, launch_coarse(H.coarse, H.g_coarse, H.smem_coarse, R.st));
         R.account(PIC_POISSON_PHASE_COARSE, 2.0 * cn * sizeof(V2<T>) + cn * 2 * sizeof(T), cf);
+    }
+    if (H.g_dense_prep) {
+        double qb = 0, df = 0;
+        const double dn = dense_work(P, &qb, &df);
+        // y: b in, y out; each GEMM: Q, one FP32 column block in, one out
+        RUN(R, PIC_POISSON_PHASE_COARSE, launch_dense(H.dense, 0, H.g_dense_prep, H.g_dense_gemm, R.st));
+        R.account(PIC_POISSON_PHASE_COARSE, dn * (sizeof(V2<T>) + sizeof(float2)), 0.0);
+        for (int stage = 1; stage <= 2; ++stage) {
+            RUN(R, PIC_POISSON_PHASE_COARSE, launch_dense(H.dense, stage, H.g_dense_prep, H.g_dense_gemm, R.st));
+            R.account(PIC_POISSON_PHASE_COARSE, 0.5 * qb + dn * (stage == 1 ? 2 * sizeof(float2) : sizeof(float2) + sizeof(V2<T>)),
+                      0.5 * df);
+        }
     }
     if (H.g_bottom) {
         // per mode and part: b, b_hat in, u out of the level above the coarsest
