@@ -416,8 +416,9 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
     }
     const size_t idx = ((size_t)k * F.nr + i) * nm + m;
     // composite domain: a cell outside the patches keeps u = 0 (in a batch the
-    // masked variant also runs the plain problems, whose rcls is null)
-    if (MASK && F.rcls && F.diag[((size_t)F.rcls[k] * F.nr + i) * nm + m] == T(0)) {
+    // masked variant also runs the plain problems, whose rcls is null; a level
+    // without inactive cells -- a non-uniform axial mesh -- reads no diag)
+    if (MASK && F.rcls && F.holes && F.diag[((size_t)F.rcls[k] * F.nr + i) * nm + m] == T(0)) {
         if (ASSIGN) F.u[idx] = mk<T>(0, 0);
         return;
     }
@@ -427,7 +428,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
     const int I2 = I + ((i & 1) ? 1 : -1);
     bool kin = K2 >= 0 && K2 < C.nz;
     bool iin = I2 >= 0 && I2 < C.nr;
-    if (MASK && C.rcls) {   // an exposed face reflects like a wall: the correction vanishes on it
+    if (MASK && C.rcls && C.holes) {   // an exposed face reflects like a wall: the correction vanishes on it
         if (iin) iin = C.diag[((size_t)C.rcls[K] * C.nr + I2) * nm + m] != T(0);
         if (kin) kin = C.diag[((size_t)C.rcls[K2] * C.nr + I) * nm + m] != T(0);
     }
