@@ -617,10 +617,15 @@ def _time_forms(args, schedules, world, dist, p, seed0):
         with Plan(p, precision=prec, graph=True, **kw) as plan:
             steps = max(4, args.steps // 4)
             ms, infos, _ = time_form(plan, rhos, phi, steps, 2, args.tol, world, dist)
+        # one profiled host-loop solve: where the time goes (CUDA events
+        # around every launch; not the timed figure above)
+        with Plan(p, precision=prec, profile=True, **kw) as plan:
+            _, pinfo = plan.solve(rhos[0], phi, tol=args.tol)
         out[name] = {"ms_per_solve": ms / steps, "steps": steps, "schedule": kw,
                      "cycles_median": statistics.median(i["cycles"] for i in infos),
                      "rel_res_max": max(i["rel_res"] for i in infos),
-                     "status": sorted({i["status"] for i in infos})}
+                     "status": sorted({i["status"] for i in infos}),
+                     "profiled_phase_ms": {k: v for k, v in pinfo["ms_phase"].items() if v > 0}}
     del rhos, phi
     torch.cuda.empty_cache()
     return out

@@ -150,8 +150,9 @@ int smooth_level(Runner &R, const Hier<T> &H, int l, int sweeps, bool skip_first
         RUN(R, ph, launch_smooth_fused(post ? H.fpost[l] : H.fpre[l], post ? H.g_fpost[l] : H.g_fpre[l],
                                        2 * sweeps, res, R.st, R.P.masked));
         R.account(ph, 3.0 * n * sizeof(V2<T>), 14.0 * sweeps * n);
-        if (res)   // the fused restriction: b of the red cells, the coarse b, b_hat, u
-            R.account(PIC_POISSON_PHASE_RESTRICT, n * sizeof(V2<T>) * (0.5 + 0.75), 9.0 * n);
+        if (res)   // the fused restriction: b of the red cells, the coarse b, b_hat, u -- booked
+                   // with the launch that moves them, so a phase's bytes and time match
+            R.account(ph, n * sizeof(V2<T>) * (0.5 + 0.75), 9.0 * n);
         return PIC_POISSON_OK;
     }
     for (int s = 0; s < sweeps; ++s) {
