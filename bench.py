@@ -584,8 +584,9 @@ def run_composite(args, schedules, world, dist):
     grounded exposed faces, charge only inside) at 512 x 128 x 384: the
     headline grid with 384 axial cells, so that the exit plane at nz / 2 stays
     on a coarse face down to a small dense coarsest level.  FP64 and mixed
-    solves to the benchmark tolerance, each one CUDA graph, with the headline
-    forms' schedules (the fused smoother does not take patches)."""
+    solves to the benchmark tolerance, each one CUDA graph, each with the
+    autotuner's schedule for that problem and form (_time_forms).  Then the
+    same for a non-uniform axial mesh on the headline grid."""
     import torch
     from paper_2609_07172_gb300 import FP64, MIXED, Plan, workloads as W
     import numpy as np
@@ -604,16 +605,25 @@ def run_composite(args, schedules, world, dist):
 
 
 def _time_forms(args, schedules, world, dist, p, seed0):
-    """FP64 and mixed graph solves of problem p to the benchmark tolerance
-    with the headline forms' schedules (no fused smoother)."""
+    """FP64 and mixed graph solves of problem p to the benchmark tolerance,
+    each with the autotuner's schedule for this problem (cached with
+    --tune-cache; with --schedule or --no-tune: the headline forms' settings
+    without the fused smoother)."""
     import torch
     from paper_2609_07172_gb300 import FP64, MIXED, Plan, workloads as W
     rhos = [W.rho_plasma_torch(p, seed0 + s) for s in range(4)]
     phi = torch.empty(p.shape, dtype=torch.float64, device="cuda")
     out = {}
     for name, prec in (("fp64", FP64), ("mixed", MIXED)):
-        kw = dict(schedules.get(name) or {})
-        kw["smooth_fused"] = 0
+        if args.schedule or args.no_tune:
+            kw = dict(schedules.get(name) or {})
+            kw["smooth_fused"] = 0
+        else:
+            from paper_2609_07172_gb300 import autotune
+            t = autotune([p], [rhos[0]], tol=args.tol, precision=prec, graph=True, repeats=2,
+                         cache=args.tune_cache)
+            kw = {k: t[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads", "smooth_strip",
+                                    "omega", "smooth_fused", "fmg", "inner_first") if k in t}
         with Plan(p, precision=prec, graph=True, **kw) as plan:
             steps = max(4, args.steps // 4)
             ms, infos, _ = time_form(plan, rhos, phi, steps, 2, args.tol, world, dist)

@@ -477,7 +477,15 @@ def autotune(problems, rhos, tol=1e-10, precision=FP64, graph=False, repeats=3, 
     import os
     import torch
     problems = list(problems)
-    key = "|".join("%dx%dx%d" % (p.nr, p.ntheta, p.nz) for p in problems) + "|%d|%d|%g" % (precision, graph, tol)
+
+    def geometry(p):   # sizes, plus a digest of the face arrays and patches when a problem has them
+        extra = (p.r_faces, p.z_faces, p.patches, p.phi_exposed if p.patches else None)
+        tag = "%dx%dx%d" % (p.nr, p.ntheta, p.nz)
+        if any(x is not None for x in extra[:3]):
+            import hashlib
+            tag += ":" + hashlib.sha1(repr(extra).encode()).hexdigest()[:12]
+        return tag
+    key = "|".join(geometry(p) for p in problems) + "|%d|%d|%g" % (precision, graph, tol)
     if cache and os.path.exists(cache):
         with open(cache) as f:
             table = json.load(f)
