@@ -120,3 +120,27 @@ def test_batch_mixes_axial_meshes_patches_and_plain():
         ref, _ = oracle.solve3d(oracle.grid_from_problem(q), r, tol=1e-15)
         assert info["status"] == B.OK, info
         assert rel_l2(phi.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_uniform_faces_take_the_dense_coarsest_solve_and_agree(precision):
+    """Axial faces given at the uniform positions: the plan builds per-row
+    tables and solves the coarsest level densely (the 2 N_m right-hand sides
+    through the two GEMMs of the dense solve: 34 of them, a partial column
+    tile, over 120 coarsest cells, a partial row tile), while the plan without
+    faces takes the separable solve and the mode-local bottom.  Two
+    independent coarsest solvers, the same discrete system: at the floor the
+    potentials agree with each other and with the oracle."""
+    p = with_bias_walls(W.annulus(96, 32, 80))
+    q = p.with_z_faces(np.linspace(p.z0, p.z1, p.nz + 1))
+    rho = W.rho_plasma(p, seed=73)
+    with Plan(p, precision=precision) as a:
+        phi_a, ia = a.solve(dev(rho), tol=0.0)
+    with Plan(q, precision=precision) as b:
+        phi_b, ib = b.solve(dev(rho), tol=0.0)
+    assert ia["status"] == B.OK and ib["status"] == B.OK
+    got_a, got_b = phi_a.cpu().numpy(), phi_b.cpu().numpy()
+    assert rel_l2(got_b, got_a) <= TOL[precision]
+    g = oracle.grid_from_problem(q)
+    ref = oracle.solve3d(g, rho, tol=1e-15)[0]
+    assert rel_l2(got_b, ref) <= TOL[precision]
