@@ -34,7 +34,6 @@
 // b_hat (and b) into a ring that keeps each row until its last half-sweep,
 // so those values take no registers.
 #include <algorithm>
-#include <cstdlib>
 #include <type_traits>
 
 #include "internal.h"
@@ -430,8 +429,7 @@ finished:
 }  // namespace
 
 template <int NH, bool RES, bool RW> cudaError_t launch_nh(const FusedTab *tab, unsigned grid, cudaStream_t st) {
-    size_t smem = FusedCfg<NH, RES>::smem_floats2 * sizeof(float2);
-    if (!RES) if (const char *ev = getenv("PIC_FUSED_POST_SMEM")) smem = std::max(smem, (size_t)atoi(ev));   // TEMP
+    const size_t smem = FusedCfg<NH, RES>::smem_floats2 * sizeof(float2);
     cudaError_t e =
         cudaFuncSetAttribute(k_smooth_fused<NH, RES, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
