@@ -746,6 +746,30 @@ def run_batch(args, dev, hbm_peak, fp64_tflops):
     ms_each = e0.elapsed_time(e1) / steps
     for pl in plans:
         pl.close()
+    # the same batch in the mixed form (FP32 V-cycles in FP64 defect
+    # correction), autotuned on the batch
+    from paper_2609_07172_gb300 import MIXED
+    try:
+        mt = autotune(problems, rhos, tol=args.tol, precision=MIXED, graph=True, repeats=2, cache=args.tune_cache)
+        mkw = {k: mt[k] for k in ("pre_sweeps", "post_sweeps", "inner_cycles", "smooth_threads", "smooth_strip",
+                                  "omega", "smooth_fused", "fmg", "inner_first") if k in mt}
+        mbp = BatchPlan(problems, precision=MIXED, graph=True, **mkw)
+        for _ in range(2):
+            mbp.solve(rhos, phis, tol=args.tol)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            _, minfos = mbp.solve(rhos, phis, tol=args.tol)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_mixed = e0.elapsed_time(e1) / steps
+        mbp.close()
+        mixed = {"ms_per_batch": ms_mixed, "cycles": minfos[0]["cycles"],
+                 "outer_iterations": minfos[0]["outer_iterations"],
+                 "rel_res_max": max(i["rel_res"] for i in minfos), "autotuned": dict(mkw, ms=mt.get("ms")),
+                 "status": sorted({i["status"] for i in minfos})}
+    except RuntimeError as exc:   # reported, not fatal to the benchmark line
+        mixed = {"error": str(exc)}
     return {"workload": "24 problems, N_r in {64..512}, N_theta in {16..128}, N_z in {64,200,400} (seed 3), "
                         "FP64, rel-res %g" % args.tol,
             "cells_total": int(sum(q.nr * q.ntheta * q.nz for q in problems)),
@@ -761,7 +785,8 @@ def run_batch(args, dev, hbm_peak, fp64_tflops):
                          "fp64_frac": alg_flops / (ms_batch * 1e-3) / 1e12 / fp64_tflops,
                          "note": "the sum of each problem's own algorithmic bytes and FP64 flops (its own cycles) "
                                  "over the batched solve's time"},
-            "autotune_candidates": len(tuned.get("tried", [])) or None}
+            "autotune_candidates": len(tuned.get("tried", [])) or None,
+            "mixed": mixed}
 
 
 def run_sequence(args, dev, p, schedules):
