@@ -467,6 +467,22 @@ class BatchPlan:
         return phis, [i.as_dict() for i in infos]
 
 
+def tune_key(problems, precision, graph, tol):
+    """Cache key of an autotuning: every problem's sizes, plus a digest of its
+    face arrays and patches when it has them (two problems of one size but
+    different meshes or domains are tuned apart), the precision, the graph
+    flag and the tolerance."""
+    import hashlib
+
+    def geometry(p):
+        extra = (p.r_faces, p.z_faces, p.patches, p.phi_exposed if p.patches else None)
+        tag = "%dx%dx%d" % (p.nr, p.ntheta, p.nz)
+        if any(x is not None for x in extra[:3]):
+            tag += ":" + hashlib.sha1(repr(extra).encode()).hexdigest()[:12]
+        return tag
+    return "|".join(geometry(p) for p in problems) + "|%d|%d|%g" % (precision, graph, tol)
+
+
 def autotune(problems, rhos, tol=1e-10, precision=FP64, graph=False, repeats=3, cache=None):
     """Tuned solver settings for `problems` (pic_poisson_autotune), as Plan keyword arguments.
 
@@ -477,15 +493,7 @@ def autotune(problems, rhos, tol=1e-10, precision=FP64, graph=False, repeats=3, 
     import os
     import torch
     problems = list(problems)
-
-    def geometry(p):   # sizes, plus a digest of the face arrays and patches when a problem has them
-        extra = (p.r_faces, p.z_faces, p.patches, p.phi_exposed if p.patches else None)
-        tag = "%dx%dx%d" % (p.nr, p.ntheta, p.nz)
-        if any(x is not None for x in extra[:3]):
-            import hashlib
-            tag += ":" + hashlib.sha1(repr(extra).encode()).hexdigest()[:12]
-        return tag
-    key = "|".join(geometry(p) for p in problems) + "|%d|%d|%g" % (precision, graph, tol)
+    key = tune_key(problems, precision, graph, tol)
     if cache and os.path.exists(cache):
         with open(cache) as f:
             table = json.load(f)

@@ -177,3 +177,24 @@ def test_library_exports_every_network_function():
     lib = B.load()
     for n in names:
         assert hasattr(lib, n), n
+
+
+def test_autotune_cache_key_separates_geometries(tmp_path):
+    """The autotuner's cache key carries each problem's sizes and, when it has
+    them, a digest of its face arrays and patches: the headline grid, the same
+    grid with stretched axial faces and a composite domain of the same size are
+    tuned apart, and a cached entry is returned without touching a GPU."""
+    p = W.annulus(64, 16, 48)
+    w = 1.02 ** np.arange(p.nz)
+    q = p.with_z_faces(p.z0 + (p.z1 - p.z0) * np.r_[0.0, np.cumsum(w)] / w.sum())
+    c = p.with_patches([(0, 32, 0, 48), (32, 64, 16, 32)], phi_exposed=12.0)
+    keys = {B.tune_key([x], B.FP64, True, 1e-10) for x in (p, q, c)}
+    assert len(keys) == 3
+    assert B.tune_key([p], B.FP64, True, 1e-10) == B.tune_key([W.annulus(64, 16, 48)], B.FP64, True, 1e-10)
+    assert B.tune_key([p], B.FP64, True, 1e-10) != B.tune_key([p], B.MIXED, True, 1e-10)
+    cache = tmp_path / "tune.json"
+    best = {"pre_sweeps": 1, "post_sweeps": 2, "inner_cycles": 2, "smooth_threads": 128, "smooth_strip": 0,
+            "omega": 1.2, "smooth_fused": 0, "fmg": 0, "inner_first": 2}
+    import json
+    cache.write_text(json.dumps({B.tune_key([q], B.FP64, True, 1e-10): {"best": best, "ms": 1.0, "tried": []}}))
+    assert B.autotune([q], [None], tol=1e-10, precision=B.FP64, graph=True, cache=str(cache)) == best
