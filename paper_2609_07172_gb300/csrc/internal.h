@@ -273,9 +273,12 @@ cudaError_t launch_coarse(const CoarseTab<T> *tab, unsigned grid, size_t smem, c
 template <class T>
 cudaError_t launch_dense(const DenseTab<T> *tab, int stage, unsigned g_prep, unsigned g_gemm, cudaStream_t st);
 unsigned dense_gemm_blocks(int nact, int nm);   // GEMM blocks of one problem
-// Full-multigrid start: u_f = P u_c on every fine cell; coarse b = restricted fine b.
+// Full-multigrid start: u_f = P u_c on every fine cell (black_only: on the
+// black ones, for a red Gauss-Seidel half-sweep to follow); coarse b =
+// restricted fine b.
 template <class T>
-cudaError_t launch_interp(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st, bool masked = false);
+cudaError_t launch_interp(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st, bool masked = false,
+                          bool black_only = false);
 template <class T>
 cudaError_t launch_rhs_restrict(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st, bool masked = false);
 

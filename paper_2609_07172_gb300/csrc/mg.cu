@@ -886,9 +886,14 @@ cudaError_t launch_prolong(const LaunchTab<T> *tab, unsigned grid, bool black_on
 }
 
 template <class T>
-cudaError_t launch_interp(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st, bool masked) {
-    if (masked) k_prolong<T, false, true, true><<<grid, MG_THREADS, 0, st>>>(tab);
-    else k_prolong<T, false, true, false><<<grid, MG_THREADS, 0, st>>>(tab);
+cudaError_t launch_interp(const LaunchTab<T> *tab, unsigned grid, cudaStream_t st, bool masked, bool black_only) {
+    if (black_only) {
+        if (masked) k_prolong<T, true, true, true><<<grid, MG_THREADS, 0, st>>>(tab);
+        else k_prolong<T, true, true, false><<<grid, MG_THREADS, 0, st>>>(tab);
+    } else {
+        if (masked) k_prolong<T, false, true, true><<<grid, MG_THREADS, 0, st>>>(tab);
+        else k_prolong<T, false, true, false><<<grid, MG_THREADS, 0, st>>>(tab);
+    }
     return cudaGetLastError();
 }
 
@@ -953,7 +958,7 @@ cudaError_t launch_sum(const double *partials, int n, double *out, cudaStream_t 
     template cudaError_t launch_residual<T>(const LaunchTab<T> *, unsigned, bool, double *, unsigned,      \
                                             cudaStream_t, bool);                                           \
     template cudaError_t launch_prolong<T>(const LaunchTab<T> *, unsigned, bool, cudaStream_t, bool);      \
-    template cudaError_t launch_interp<T>(const LaunchTab<T> *, unsigned, cudaStream_t, bool);             \
+    template cudaError_t launch_interp<T>(const LaunchTab<T> *, unsigned, cudaStream_t, bool, bool);       \
     template cudaError_t launch_rhs_restrict<T>(const LaunchTab<T> *, unsigned, cudaStream_t, bool);       \
     template cudaError_t launch_coarse<T>(const CoarseTab<T> *, unsigned, size_t, cudaStream_t);
 PP_INST(double)

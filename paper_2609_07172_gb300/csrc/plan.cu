@@ -947,7 +947,10 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
     H.g_interp.assign(nl, 0);
     if (P.shared.fmg) {
         // full-multigrid start: b restricted from l to l + 1 for every level pair
-        // of a problem, and u_l = P u_(l+1) for the levels the level kernels solve
+        // of a problem, and u_l = P u_(l+1) for the levels the level kernels
+        // solve -- on the black cells only when a Gauss-Seidel red half-sweep
+        // follows (it overwrites the red ones without reading them)
+        H.interp_black = pre > 0 && P.shared.omega == 1.0;
         for (int l = 0; l < nl; ++l) {
             LaunchTab<T> trh{}, tin{};
             for (int p = 0; p < P.n; ++p) {
@@ -963,7 +966,9 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
                 if (l < q.smoothed()) {
                     tin.f[tin.n] = v[l];
                     tin.c[tin.n] = v[l + 1];
-                    tin.start[tin.n + 1] = tin.start[tin.n] + mg_blocks((size_t)v[l].nz * v[l].nr * v[l].nm);
+                    tin.start[tin.n + 1] =
+                        tin.start[tin.n] +
+                        mg_blocks((size_t)v[l].nz * (H.interp_black ? v[l].nr / 2 : v[l].nr) * v[l].nm);
                     ++tin.n;
                 }
             }

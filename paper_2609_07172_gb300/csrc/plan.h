@@ -62,6 +62,8 @@ template <class T> struct Hier {
     unsigned g_coarse = 0;
     size_t smem_coarse = 0;
     std::vector<LaunchTab<T> *> rhs, interp;  // full-multigrid start: b restricted to l + 1, u_l = P u_(l+1)
+    bool interp_black = false;                // u_l = P u_(l+1) on the black cells only (the red half-sweep
+                                              // that follows overwrites the red ones unread)
     std::vector<unsigned> g_rhs, g_interp;
     BottomTab<T> *bottom = nullptr;           // problems with a mode-local bottom
     unsigned g_bottom = 0;

@@ -310,9 +310,10 @@ int fmg_start(Runner &R) {
     if (rc) return rc;
     for (int l = nl - 1; l >= 0; --l) {
         if (!H.g_interp[l]) continue;
-        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_interp(H.interp[l], H.g_interp[l], R.st, R.P.masked));
-        const double n = level_entries<double>(P, l);
-        R.account(PIC_POISSON_PHASE_PROLONG, n * sizeof(double2) * 1.25, 16.0 * n);
+        RUN(R, PIC_POISSON_PHASE_PROLONG,
+            launch_interp(H.interp[l], H.g_interp[l], R.st, R.P.masked, H.interp_black));
+        const double n = level_entries<double>(P, l), frac = H.interp_black ? 0.5 : 1.0;
+        R.account(PIC_POISSON_PHASE_PROLONG, n * sizeof(double2) * (0.25 + frac), 16.0 * frac * n);
         if (l == 0) break;   // the main iteration takes over on level 0
         rc = smooth_level(R, H, l, pre, false, false);
         if (rc) return rc;
@@ -354,9 +355,10 @@ int fmg_correction(Runner &R) {
     if (rc) return rc;
     for (int l = nl - 1; l >= 1; --l) {
         if (!H.g_interp[l]) continue;
-        RUN(R, PIC_POISSON_PHASE_PROLONG, launch_interp(H.interp[l], H.g_interp[l], R.st, R.P.masked));
-        const double n = level_entries<double>(P, l);
-        R.account(PIC_POISSON_PHASE_PROLONG, n * sizeof(double2) * 1.25, 16.0 * n);
+        RUN(R, PIC_POISSON_PHASE_PROLONG,
+            launch_interp(H.interp[l], H.g_interp[l], R.st, R.P.masked, H.interp_black));
+        const double n = level_entries<double>(P, l), frac = H.interp_black ? 0.5 : 1.0;
+        R.account(PIC_POISSON_PHASE_PROLONG, n * sizeof(double2) * (0.25 + frac), 16.0 * frac * n);
         rc = smooth_level(R, H, l, pre, false, false);
         if (rc) return rc;
         rc = restrict_level(R, H, l, nullptr);
@@ -399,7 +401,7 @@ int enqueue_prologue(Runner &R, int guess) {
             if (rc) return rc;
         }
     } else if (!mixed && P.shared.fmg && P.Lmax > 1) {
-        int rc = fmg_start(R);   // writes every level-0 iterate
+        int rc = fmg_start(R);   // with the red half-sweep below, writes every level-0 iterate
         if (rc) return rc;
     } else if (!mixed) {   // (the mixed form's first defect writes the zero iterate itself)
         for (const ProblemPlan &q : P.pr) {
