@@ -364,6 +364,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.load(build_if_missing=True)
+    # wall seconds of each leg of this run (setup and tuning included), for the record
+    legs, t_leg = {}, [time.perf_counter()]
+
+    def leg(name):
+        now = time.perf_counter()
+        legs[name] = round(now - t_leg[0], 2)
+        t_leg[0] = now
 
     prec = FP64 if args.precision == "fp64" else MIXED
     p = W.annulus(*args.grid) if args.grid else W.c1_problem()
@@ -438,6 +445,7 @@ def run_ours(args):
             "host_loop_profiled_ms_per_solve": ms_prof / args.steps}
     if tuned:
         line["autotune"] = {"candidates": len(tuned.get("tried", [])), "best_ms": tuned.get("ms")}
+    leg("headline (tuning, timed and profiled solves)")
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     if not args.no_e2e:
@@ -468,6 +476,7 @@ def run_ours(args):
                        "steps": ne, "api": "pic_poisson_solve_host (pinned host buffers, read and written in place "
                                            "by the transforms)",
                        "staged_ms_per_solve": staged_ms}
+        leg("e2e")
     ref_phi = phi.clone()
     # seed-0 solutions for the element-wise comparison with the oracle (cpu_baseline leg)
     want_parity = not args.no_cpu_baseline and rank == 0 and world == 1 and tag == "512x128x400"
@@ -477,6 +486,7 @@ def run_ours(args):
             plan.solve(rhos[0], phi, tol=t)
             torch.cuda.synchronize()
             gpu_phis["%s_%s" % (args.precision, label)] = phi.cpu().numpy()
+        leg("seed-0 solves for the oracle comparison")
 
     # ---- face-field reconstruction of the solved potential (the PIC step after the solve)
     if not args.no_field:
@@ -501,10 +511,12 @@ def run_ours(args):
                               "bound": "alu (FP64: 6 instructions per cell)",
                               "algorithmic_bytes": fbytes, "launches": len(evs)}
         del er, ea, ez
+        leg("face field")
 
     # ---- CIC deposit of two species and projection to rho (the PIC step before the solve)
     if not args.no_deposit and args.deposit_ppc > 0:
         line["deposit"] = run_deposit(args, plan, p)
+        leg("deposit")
     plan.close()
 
     # ---- the other form on the same GPU and inputs (mixed FP32/FP64 when the headline is FP64)
@@ -544,20 +556,26 @@ def run_ours(args):
                                  traffic_from_profile(SMOOTH_PROFILE[name])
                                  if tag == "512x128x400" else None),
             "hbm_roofline_solve": {"achieved_gbs": gbs2, "peak_gbs": hbm_peak, "frac": gbs2 / hbm_peak}}}
+        leg("other form")
 
     if not args.no_composite:
         line["composite_channel_plume"] = run_composite(args, schedules, world, dist)
+        leg("composite and axial-mesh workloads")
     if not args.no_batch:
         line["batch_uneven"] = run_batch(args, dev, hbm_peak, fp64_gflops / 1e3)
+        leg("uneven batch")
     if not args.no_sequence:
         line["sequence"] = run_sequence(args, dev, p, schedules)
+        leg("sequence")
     if not args.no_conv:
         line["learned_conv"] = run_conv(args, dev, p, ms_per_solve / max(statistics.median(cycles), 1))
+        leg("tcgen05 convolution")
     if not args.no_learned:
         try:
             line["learned_warm_start"] = run_learned(args, dev, p)
         except RuntimeError as exc:   # reported, not fatal to the benchmark line
             line["learned_warm_start"] = {"error": str(exc)}
+        leg("learned warm start")
 
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         det = oracle_baseline(gpu_phis, args.tol)
@@ -577,6 +595,8 @@ def run_ours(args):
                 "seed 0; GPU forms solved to rel-res %g (tol) and to their rounding floor (floor), each "
                 "against the oracle's CG solution continued to its floor; per_mode_max: largest per-mode "
                 "error norm over the whole solution's norm" % args.tol))
+        leg("CPU oracle")
+    line["leg_seconds"] = legs
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

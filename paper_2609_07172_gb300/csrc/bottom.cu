@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(BOTTOM_THREADS) k_bottom(const BottomTab<T> *_
     const int fz = nz == ncz ? 1 : 2, fr = nr == ncr ? 1 : 2;
 
     // shared memory (element type T): U: u, b_hat, b [n]; tables [ncls][nr] x 4, [nr] x 3;
-    // C: right-hand side / correction [nc]; separable solve: w [ncz][ncr + 1], V [ceil(ncz/2)][ncz]
+    // C: right-hand side / correction [nc]; separable solve: w [ncz][ncr + 1], V [ceil(ncz/2)][ncz],
+    // this mode's Thomas factorisation piv, cpr [ncz][ncr + 1] and the off-diagonal e [ncr]
     T *u = (T *)smraw;
     T *bh = u + n;
     T *b = bh + n;
@@ -108,26 +109,54 @@ __global__ void __launch_bounds__(BOTTOM_THREADS) k_bottom(const BottomTab<T> *_
     const int lw = ncr + 1, hzc = ncz - ncz / 2, hc = ncz / 2;
     T *ws = bc + nc;
     T *Vs = ws + ncz * lw;
+    T *ps = Vs + hzc * ncz;
+    T *cs = ps + ncz * lw;
+    T *es = cs + ncz * lw;
 
+    // Every load of the block is issued at once (cp.async) in two groups: what
+    // the pre-smoothing reads (b_hat, the smoother's tables), then what only
+    // the restriction and the coarsest solve read (b -- of the red cells when
+    // only those carry a residual -- the residual's tables, V and this mode's
+    // factorisation), which arrives while the pre-smoothing runs.
     const T *gb = (const T *)U.b + part, *gbh = (const T *)U.bh + part;
     for (int f = threadIdx.x; f < n; f += blockDim.x) {
-        b[f] = gb[2 * ((size_t)f * nm + m)];
-        bh[f] = gbh[2 * ((size_t)f * nm + m)];
+        cp_async_elem(bh + f, gbh + 2 * ((size_t)f * nm + m));
         u[f] = 0;
     }
     for (int f = threadIdx.x; f < ncls * nr; f += blockDim.x) {
         const size_t t = (size_t)f * nm + m;   // (class, i) -> ((class * nr + i) * nm + m)
-        hz[f] = U.hz[t];
-        hw[f] = U.hw[t];
-        he[f] = U.he[t];
-        dg[f] = U.diag[t];
+        cp_async_elem(hz + f, U.hz + t);
+        cp_async_elem(hw + f, U.hw + t);
+        cp_async_elem(he + f, U.he + t);
     }
+    cp_async_group_close();
+    if (B.red_only) {
+        const int hr = nr >> 1;
+        for (int c = threadIdx.x; c < nz * hr; c += blockDim.x) {
+            const int k = c / hr, f = k * nr + 2 * (c - k * hr) + (k & 1);   // (k + i) even
+            cp_async_elem(b + f, gb + 2 * ((size_t)f * nm + m));
+        }
+    } else {
+        for (int f = threadIdx.x; f < n; f += blockDim.x) cp_async_elem(b + f, gb + 2 * ((size_t)f * nm + m));
+    }
+    for (int f = threadIdx.x; f < ncls * nr; f += blockDim.x) cp_async_elem(dg + f, U.diag + (size_t)f * nm + m);
     for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-        cw[i] = U.cw[i];
-        ce[i] = U.ce[i];
-        cz[i] = U.cz[i];
+        cp_async_elem(cw + i, U.cw + i);
+        cp_async_elem(ce + i, U.ce + i);
+        cp_async_elem(cz + i, U.cz + i);
     }
-    for (int f = threadIdx.x; f < hzc * ncz; f += blockDim.x) Vs[f] = D.V[f];
+    for (int f = threadIdx.x; f < hzc * ncz; f += blockDim.x) cp_async_elem(Vs + f, D.V + f);
+    {
+        const T *gp = D.piv + (size_t)m * ncz * ncr, *gc = D.cpr + (size_t)m * ncz * ncr;
+        for (int f = threadIdx.x; f < ncz * ncr; f += blockDim.x) {
+            const int j = f / ncr, i = f - j * ncr;
+            cp_async_elem(ps + j * lw + i, gp + f);
+            cp_async_elem(cs + j * lw + i, gc + f);
+        }
+        for (int i = threadIdx.x; i + 1 < ncr; i += blockDim.x) cp_async_elem(es + i, D.e + i);
+    }
+    cp_async_group_close();
+    cp_async_group_wait<1>();
     __syncthreads();
 
     // pre-smoothing from zero (the restriction's fused first red half-sweep
@@ -136,6 +165,8 @@ __global__ void __launch_bounds__(BOTTOM_THREADS) k_bottom(const BottomTab<T> *_
         half_sweep(u, bh, hz, hw, he, nr, nz, ncls, 0);
         half_sweep(u, bh, hz, hw, he, nr, nz, ncls, 1);
     }
+    cp_async_group_wait<0>();
+    __syncthreads();
     // residual of the fine cells of each coarse cell, summed (red cells only
     // after a black half-sweep), as k_residual_restrict
     for (int e = threadIdx.x; e < nc; e += blockDim.x) {
@@ -177,22 +208,7 @@ __global__ void __launch_bounds__(BOTTOM_THREADS) k_bottom(const BottomTab<T> *_
         ws[j * lw + i] = a;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < ncz; j += blockDim.x) {
-        const T *piv = D.piv + ((size_t)m * ncz + j) * ncr;
-        const T *cpr = D.cpr + ((size_t)m * ncz + j) * ncr;
-        T *row = ws + (size_t)j * lw;
-        T y = row[0] * piv[0];
-        row[0] = y;
-        for (int i = 1; i < ncr; ++i) {
-            y = (row[i] - D.e[i - 1] * y) * piv[i];
-            row[i] = y;
-        }
-        T x = y;
-        for (int i = ncr - 2; i >= 0; --i) {
-            x = row[i] - cpr[i] * x;
-            row[i] = x;
-        }
-    }
+    thomas_rows(ws, ps, cs, es, ncz, ncr, lw);
     __syncthreads();
     for (int f = threadIdx.x; f < hzc * ncr; f += blockDim.x) {   // correction into bc
         const int k = f / ncr, i = f - k * ncr;
@@ -256,8 +272,8 @@ __global__ void __launch_bounds__(BOTTOM_THREADS) k_bottom(const BottomTab<T> *_
 
 template <class T> size_t bottom_smem_bytes(int nr, int nz, int ncls, int ncr, int ncz) {
     const size_t n = (size_t)nr * nz, nc = (size_t)ncr * ncz;
-    return (3 * n + 4 * (size_t)ncls * nr + 3 * (size_t)nr + nc + (size_t)ncz * (ncr + 1) +
-            (size_t)(ncz - ncz / 2) * ncz) * sizeof(T);
+    return (3 * n + 4 * (size_t)ncls * nr + 3 * (size_t)nr + nc + 3 * (size_t)ncz * (ncr + 1) +
+            (size_t)(ncz - ncz / 2) * ncz + (size_t)ncr) * sizeof(T);
 }
 
 template <class T> cudaError_t launch_bottom(const BottomTab<T> *tab, unsigned grid, size_t smem, cudaStream_t st) {

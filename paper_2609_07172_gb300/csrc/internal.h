@@ -364,6 +364,54 @@ constexpr size_t BOTTOM_MAX_SMEM = 200 * 1024;
 template <class T> size_t bottom_smem_bytes(int nr, int nz, int ncls, int ncr, int ncz);
 template <class T> cudaError_t launch_bottom(const BottomTab<T> *tab, unsigned grid, size_t smem, cudaStream_t st);
 
+// Pieces of the separable coarsest-level solve shared by k_coarse (mg.cu) and
+// k_bottom (bottom.cu).
+//
+// One element copied from global to shared memory by cp.async (4 or 8
+// bytes, no register round trip): a block issues every load of its problem
+// before it waits once, instead of one L2 round trip per loop step.
+template <class T> __device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"((int)sizeof(T)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Close the thread's current group of copies; wait until at most N groups are in flight.
+__device__ __forceinline__ void cp_async_group_close() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_group_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The radial tridiagonal solves of the separable coarsest solve, one per
+// axial eigenvector j < nz, in place on the rows ws[j][0 .. nr) (row stride
+// lw): forward y_i = (w_i - e_(i-1) y_(i-1)) piv_i, back x_i = y_i - cpr_i x_(i+1),
+// with the factorisation piv, cpr ([nz][lw]) and e ([nr - 1]) staged in shared
+// memory, so that a step of the recurrence waits on shared memory rather than
+// on L2.  The nz recurrences are spread over the block's first four warps
+// (one per SM sub-partition; the block has at least 128 threads).
+template <class T>
+__device__ __forceinline__ void thomas_rows(T *ws, const T *ps, const T *cs, const T *es, int nz, int nr, int lw) {
+    const int w = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31), per = (nz + 3) >> 2;
+    if (w >= 4) return;
+    for (int l = lane; l < per; l += 32) {
+        const int j = w * per + l;
+        if (j >= nz) break;
+        const T *piv = ps + (size_t)j * lw, *cpr = cs + (size_t)j * lw;
+        T *row = ws + (size_t)j * lw;
+        T y = row[0] * piv[0];
+        row[0] = y;
+        for (int i = 1; i < nr; ++i) {
+            y = (row[i] - es[i - 1] * y) * piv[i];
+            row[i] = y;
+        }
+        T x = y;
+        for (int i = nr - 2; i >= 0; --i) {
+            x = row[i] - cpr[i] * x;
+            row[i] = x;
+        }
+    }
+}
+
 constexpr int FFT_TI = 32;        // radial columns per transform CTA
 constexpr int FFT_THREADS = 256;
 size_t fft_smem_bytes(int nt);

@@ -615,9 +615,23 @@ __global__ void __launch_bounds__(MG_THREADS) k_coarse(const CoarseTab<T> *__res
     const int lw = nr + 1;                   // padded rows: the Thomas threads walk rows
     T *ws = bs + (size_t)nz * nr;            // [nz][lw]
     T *Vs = ws + (size_t)nz * lw;            // [hz][nz]
+    T *ps = Vs + (size_t)hz * nz;            // [nz][lw] this mode's inverse pivots
+    T *cs = ps + (size_t)nz * lw;            // [nz][lw] and upper multipliers
+    T *es = cs + (size_t)nz * lw;            // [nr] off-diagonal
+    // every load of the block is in flight before the one wait (cp.async)
     const T *bg = (const T *)L.b + comp;
-    for (int f = threadIdx.x; f < nz * nr; f += blockDim.x) bs[f] = bg[2 * ((size_t)f * nm + m)];
-    for (int f = threadIdx.x; f < hz * nz; f += blockDim.x) Vs[f] = D.V[f];
+    for (int f = threadIdx.x; f < nz * nr; f += blockDim.x) cp_async_elem(bs + f, bg + 2 * ((size_t)f * nm + m));
+    for (int f = threadIdx.x; f < hz * nz; f += blockDim.x) cp_async_elem(Vs + f, D.V + f);
+    {
+        const T *gp = D.piv + (size_t)m * nz * nr, *gc = D.cpr + (size_t)m * nz * nr;
+        for (int f = threadIdx.x; f < nz * nr; f += blockDim.x) {
+            const int j = f / nr, i = f - j * nr;
+            cp_async_elem(ps + j * lw + i, gp + f);
+            cp_async_elem(cs + j * lw + i, gc + f);
+        }
+        for (int i = threadIdx.x; i + 1 < nr; i += blockDim.x) cp_async_elem(es + i, D.e + i);
+    }
+    cp_async_wait_all();
     __syncthreads();
     for (int f = threadIdx.x; f < h * nr; f += blockDim.x) {
         const int k = f / nr, i = f - k * nr;
@@ -638,23 +652,8 @@ __global__ void __launch_bounds__(MG_THREADS) k_coarse(const CoarseTab<T> *__res
         ws[j * lw + i] = a;
     }
     __syncthreads();
-    // tridiagonal solves along r, one thread per axial eigenvector j
-    for (int j = threadIdx.x; j < nz; j += blockDim.x) {
-        const T *piv = D.piv + ((size_t)m * nz + j) * nr;
-        const T *cpr = D.cpr + ((size_t)m * nz + j) * nr;
-        T *row = ws + (size_t)j * lw;
-        T y = row[0] * piv[0];
-        row[0] = y;
-        for (int i = 1; i < nr; ++i) {
-            y = (row[i] - D.e[i - 1] * y) * piv[i];
-            row[i] = y;
-        }
-        T x = y;
-        for (int i = nr - 2; i >= 0; --i) {
-            x = row[i] - cpr[i] * x;
-            row[i] = x;
-        }
-    }
+    // tridiagonal solves along r, one per axial eigenvector j
+    thomas_rows(ws, ps, cs, es, nz, nr, lw);
     __syncthreads();
     // u[k][i] = sum_j V[k][j] w[j][i] = E +- O for the mirror pair (k, nz-1-k)
     T *ug = (T *)L.u + comp;

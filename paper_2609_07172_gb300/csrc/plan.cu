@@ -1015,8 +1015,8 @@ void build_hier(pic_poisson_plan_s &P, Hier<T> &H, Views views, Coarse coarse, c
         tc.f[tc.n] = views(q)[q.L - 1];
         tc.c[tc.n] = cd;
         tc.start[tc.n + 1] = tc.start[tc.n] + 2u * (unsigned)q.nm;   // (mode, real / imaginary part)
-        const size_t sm = ((size_t)cd.nr * cd.nz + (size_t)(cd.nr + 1) * cd.nz +
-                           (size_t)(cd.nz - cd.nz / 2) * cd.nz) * sizeof(T);
+        const size_t sm = ((size_t)cd.nr * cd.nz + 3 * (size_t)(cd.nr + 1) * cd.nz +
+                           (size_t)(cd.nz - cd.nz / 2) * cd.nz + (size_t)cd.nr) * sizeof(T);
         tc.smem = std::max(tc.smem, sm);
         ++tc.n;
     }
