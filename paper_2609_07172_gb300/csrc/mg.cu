@@ -85,14 +85,6 @@ __device__ __forceinline__ int find_problem(const unsigned *__restrict__ start, 
     return lo;
 }
 
-// (k, i) of the c-th cell of colour `color` ((i + k) % 2 == color) on a level
-// with an even number of radial cells.
-__device__ __forceinline__ void colour_cell(unsigned c, int nr, int color, int &k, int &i) {
-    const unsigned hr = (unsigned)nr >> 1;
-    k = (int)(c / hr);
-    i = 2 * (int)(c - (unsigned)k * hr) + ((k + color) & 1);
-}
-
 // b - A_m u at entry (k, i, m), Eq. matrix_free_mode_operator.
 template <class T, bool MASK>
 __device__ __forceinline__ V2<T> residual_at(const LevelDev<T> &L, int k, int i, int m, size_t idx) {
@@ -154,10 +146,13 @@ __global__ void __launch_bounds__(NT, S == 0 ? 2048 / NT : 1) k_smooth(const Lau
     if constexpr (S == 0) {
         const unsigned e = (blockIdx.x - tab->start[p]) * NT + threadIdx.x;
         if (e >= (unsigned)L.nz * (unsigned)(L.nr >> 1) * nm) return;
+        // (plain divisions: this kernel is capped at 32 registers for full
+        // occupancy, and the multiply-high form needs more)
         const unsigned c = e / nm;
         const int m = (int)(e - c * nm);
-        int k, i;
-        colour_cell(c, L.nr, color, k, i);
+        const unsigned hr = (unsigned)L.nr >> 1;
+        const int k = (int)(c / hr);
+        const int i = 2 * (int)(c - (unsigned)k * hr) + ((k + color) & 1);
         const size_t idx = ((size_t)k * L.nr + i) * nm + m;
         const size_t tb = ((size_t)(RW ? lclass(L, k) : row_class(k, L.nz, L.ncls)) * L.nr + i) * nm + m;
         const size_t rowstride = (size_t)L.nr * nm;
@@ -299,9 +294,11 @@ k_residual_restrict(const LaunchTab<T> *__restrict__ tab, double *__restrict__ p
     double acc = 0.0;
     if (e < (unsigned)C.nz * (unsigned)C.nr * (unsigned)C.nm) {
         const unsigned nm = C.nm;
-        const unsigned cc = e / nm;
+        // multiply-high divisions on the FP32 pipe's kernel only: with them
+        // the FP64 kernel ran 6 % slower (measured)
+        const unsigned cc = sizeof(T) == sizeof(float) ? fdiv(e, nm, C.rnm) : e / nm;
         const int m = (int)(e - cc * nm);
-        const int K = (int)(cc / (unsigned)C.nr);
+        const int K = (int)(sizeof(T) == sizeof(float) ? fdiv(cc, (unsigned)C.nr, C.rnr) : cc / (unsigned)C.nr);
         const int I = (int)(cc - (unsigned)K * C.nr);
         // coarsening factors of this level pair (semi-coarsening keeps one direction)
         const int fz = F.nz == C.nz ? 1 : 2, fr = F.nr == C.nr ? 1 : 2;
@@ -367,9 +364,9 @@ k_residual(const LaunchTab<T> *__restrict__ tab, int write_r, double *__restrict
     double ar = 0.0, ab = 0.0;
     if (e < (unsigned)L.nz * (unsigned)L.nr * (unsigned)L.nm) {
         const unsigned nm = L.nm;
-        const unsigned c = e / nm;
+        const unsigned c = fdiv(e, nm, L.rnm);
         const int m = (int)(e - c * nm);
-        const int k = (int)(c / (unsigned)L.nr);
+        const int k = (int)fdiv(c, (unsigned)L.nr, L.rnr);
         const int i = (int)(c - (unsigned)k * L.nr);
         const V2<T> r = residual_at<T, MASK>(L, k, i, m, e);
         if (write_r) tab->c[p].u[e] = r;
@@ -405,16 +402,21 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
     const unsigned nm = F.nm;
     const unsigned total = (unsigned)F.nz * (unsigned)(BLACK_ONLY ? (F.nr >> 1) : F.nr) * nm;
     if (e >= total) return;
-    const unsigned c = e / nm;
+    // 32-bit offsets (a plan rejects levels of 2^31 entries or more) and
+    // divisions by multiply-high: the FP32 kernel is bound by instruction
+    // issue, and these were most of its instructions
+    const unsigned c = fdiv(e, nm, F.rnm);
     const int m = (int)(e - c * nm);
     int k, i;
     if (BLACK_ONLY) {
-        colour_cell(c, F.nr, 1, k, i);
+        const unsigned hr = (unsigned)F.nr >> 1;
+        k = (int)fdiv(c, hr, F.rhr);
+        i = 2 * (int)(c - (unsigned)k * hr) + ((k + 1) & 1);
     } else {
-        k = (int)(c / (unsigned)F.nr);
+        k = (int)fdiv(c, (unsigned)F.nr, F.rnr);
         i = (int)(c - (unsigned)k * F.nr);
     }
-    const size_t idx = ((size_t)k * F.nr + i) * nm + m;
+    const unsigned idx = ((unsigned)k * F.nr + i) * nm + m;
     // composite domain: a cell outside the patches keeps u = 0 (in a batch the
     // masked variant also runs the plain problems, whose rcls is null; a level
     // without inactive cells -- a non-uniform axial mesh -- reads no diag)
@@ -433,12 +435,14 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
         if (kin) kin = C.diag[((size_t)C.rcls[K2] * C.nr + I) * nm + m] != T(0);
     }
     const int Kx = kin ? K2 : K, Ix = iin ? I2 : I;
-    const V2<T> c0 = C.u[((size_t)K * C.nr + I) * nm + m];
+    const unsigned crow = (unsigned)C.nr * nm;   // coarse row stride
+    const V2<T> *cu = C.u + m;
+    const V2<T> c0 = cu[(unsigned)K * crow + (unsigned)I * nm];
     V2<T> u = ASSIGN ? mk<T>(0, 0) : F.u[idx];   // ASSIGN: u = P c (full-multigrid interpolation)
     if (cz2 && cr2) {
-        const V2<T> c1 = C.u[((size_t)K * C.nr + Ix) * nm + m];
-        const V2<T> c2 = C.u[((size_t)Kx * C.nr + I) * nm + m];
-        const V2<T> c3 = C.u[((size_t)Kx * C.nr + Ix) * nm + m];
+        const V2<T> c1 = cu[(unsigned)K * crow + (unsigned)Ix * nm];
+        const V2<T> c2 = cu[(unsigned)Kx * crow + (unsigned)I * nm];
+        const V2<T> c3 = cu[(unsigned)Kx * crow + (unsigned)Ix * nm];
         // signed weights by selection (no FP64 multiply), four multiply-adds per part
         const T w1 = iin ? T(0.1875) : T(-0.1875), w2 = kin ? T(0.1875) : T(-0.1875);
         const T w3 = iin == kin ? T(0.0625) : T(-0.0625);
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
         u.y = fma(w3, c3.y, fma(w2, c2.y, fma(w1, c1.y, fma(T(0.5625), c0.y, u.y))));
     } else {
         // linear along the coarsened direction
-        const V2<T> c1 = cz2 ? C.u[((size_t)Kx * C.nr + I) * nm + m] : C.u[((size_t)K * C.nr + Ix) * nm + m];
+        const V2<T> c1 = cz2 ? cu[(unsigned)Kx * crow + (unsigned)I * nm] : cu[(unsigned)K * crow + (unsigned)Ix * nm];
         const T w1 = (cz2 ? kin : iin) ? T(0.25) : T(-0.25);
         u.x = fma(w1, c1.x, fma(T(0.75), c0.x, u.x));
         u.y = fma(w1, c1.y, fma(T(0.75), c0.y, u.y));
@@ -467,9 +471,9 @@ __global__ void __launch_bounds__(MG_THREADS) k_rhs_restrict(const LaunchTab<T> 
     const unsigned e = (blockIdx.x - tab->start[p]) * blockDim.x + threadIdx.x;
     if (e >= (unsigned)C.nz * (unsigned)C.nr * (unsigned)C.nm) return;
     const unsigned nm = C.nm;
-    const unsigned cc = e / nm;
+    const unsigned cc = fdiv(e, nm, C.rnm);
     const int m = (int)(e - cc * nm);
-    const int K = (int)(cc / (unsigned)C.nr);
+    const int K = (int)fdiv(cc, (unsigned)C.nr, C.rnr);
     const int I = (int)(cc - (unsigned)K * C.nr);
     const int fz = F.nz == C.nz ? 1 : 2, fr = F.nr == C.nr ? 1 : 2;
     V2<T> sum = F.b[((size_t)(fz * K) * F.nr + fr * I) * nm + m];
@@ -544,9 +548,9 @@ k_defect(const DefectTab *__restrict__ tab, const Ctrl *__restrict__ ctrl, doubl
     double acc = 0.0;
     if (e < (unsigned)D.nz * (unsigned)D.nr * (unsigned)D.nm) {
         const unsigned nm = D.nm;
-        const unsigned c = e / nm;
+        const unsigned c = fdiv(e, nm, D.rnm);
         const int m = (int)(e - c * nm);
-        const int k = (int)(c / (unsigned)D.nr);
+        const int k = (int)fdiv(c, (unsigned)D.nr, D.rnr);
         const int i = (int)(c - (unsigned)k * D.nr);
         double2 r;
         if (ZERO_X) {

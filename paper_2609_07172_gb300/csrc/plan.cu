@@ -638,6 +638,9 @@ template <class T, class V> void carve_level(const LevelHost &h, int nm, int nt,
     v.nz = h.nz;
     v.nm = nm;
     v.ncls = h.ncls;
+    v.rnm = fdiv_rcp((unsigned)nm);
+    v.rnr = fdiv_rcp((unsigned)h.nr);
+    v.rhr = fdiv_rcp((unsigned)h.nr / 2);
     v.nt = nt;
     v.init = 0;
     const size_t n = (size_t)h.nr * h.nz * nm, ntab = (size_t)h.ncls * h.nr * nm;
