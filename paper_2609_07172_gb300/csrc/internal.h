@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "fastdiv.h"
 #include "pic_poisson.h"
 
 namespace pp {
@@ -71,7 +72,7 @@ struct LevelHost {
 // One level of one problem, as the kernels see it.
 template <class T> struct LevelDev {
     int nr, nz, nm, ncls;
-    unsigned rnm, rnr, rhr;       // floor((2^32 - 1) / d) for d = nm, nr, nr / 2 (fdiv)
+    unsigned rnm, rnr, rhr;       // floor((2^32 - 1) / d) for d = nm, nr, nr / 2 (fdiv, fastdiv.h)
     int nt;                       // azimuthal cells (Parseval weights of the norms)
     int init;                     // what a restriction into the next level writes (see launch_residual_restrict)
     int strip;                    // smoother: rows of one parity updated per thread (1, 2 or 4; 0: one entry)
@@ -90,19 +91,6 @@ template <class T> struct LevelDev {
     V2<T> *b;                     // right-hand side, [nz][nr][nm]
     V2<T> *bh;                    // right-hand side / diag, [nz][nr][nm]
 };
-
-// n / d for n < 2^31 and d >= 1, given r = floor((2^32 - 1) / d): the
-// estimate floor(n r / 2^32) is the quotient or one less (n r / 2^32 lies
-// within n (1 + d) / (d 2^32) < 1 of n / d), so one correction makes it
-// exact -- a multiply-high and a compare instead of a 32-bit division.
-__host__ __device__ inline unsigned fdiv_rcp(unsigned d) { return d ? 0xFFFFFFFFu / d : 0u; }
-#ifdef __CUDACC__
-__device__ __forceinline__ unsigned fdiv(unsigned n, unsigned d, unsigned r) {
-    unsigned q = __umulhi(n, r);
-    if (n - q * d >= d) ++q;
-    return q;
-}
-#endif
 
 // Coarsest level: separable direct solve (z eigenbasis, tridiagonal in r).
 template <class T> struct CoarseDev {
