@@ -403,8 +403,9 @@ __global__ void __launch_bounds__(MG_THREADS) k_prolong(const LaunchTab<T> *__re
     const unsigned total = (unsigned)F.nz * (unsigned)(BLACK_ONLY ? (F.nr >> 1) : F.nr) * nm;
     if (e >= total) return;
     // 32-bit offsets (a plan rejects levels of 2^31 entries or more) and
-    // divisions by multiply-high: the FP32 kernel is bound by instruction
-    // issue, and these were most of its instructions
+    // divisions by multiply-high (fastdiv.h): the FP32 kernel is bound by
+    // instruction issue, and the two 32-bit divisions and 64-bit offsets were
+    // a large part of what it issued per entry
     const unsigned c = fdiv(e, nm, F.rnm);
     const int m = (int)(e - c * nm);
     int k, i;
