@@ -32,7 +32,7 @@ UNIT = "ms"
 GRID = (512, 128, 400)
 FALLBACK_HBM_GBS = 6800.7
 # committed ncu summaries holding the level-0 smoother's DRAM bytes per launch at 512x128x400
-SMOOTH_PROFILE = {"fp64": "smooth_fp64_512x128x200.md", "mixed": "smooth_fused_defect_transforms_mixed_512x128x400.md"}
+SMOOTH_PROFILE = {"fp64": "smooth_fp64_512x128x400.md", "mixed": "smooth_fused_defect_transforms_mixed_512x128x400.md"}
 
 
 def parse():
