@@ -46,3 +46,13 @@ def test_two_replicas_take_the_slowest_rank():
 def test_single_rank_is_its_own_time():
     assert bench.max_over_ranks(7.5, 1, None, "cpu") == 7.5
     assert bench.job_ms_per_solve(100.0, 20, 1) == 5.0
+
+
+def test_roofline_traffic_comes_from_committed_profiles():
+    # the bench's `roofline.traffic` of each form's dominant kernel class is
+    # read from a committed ncu summary measured at the headline size
+    for form, name in bench.SMOOTH_PROFILE.items():
+        assert name.endswith("512x128x400.md"), name
+        t = bench.traffic_from_profile(name)
+        assert t is not None and 1e8 < t < 1e9, (form, name, t)
+    assert bench.traffic_from_profile("no_such_profile.md") is None
