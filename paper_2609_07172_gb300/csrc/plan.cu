@@ -470,7 +470,7 @@ int dense_factors(const ProblemPlan &q, std::vector<int> &aidx, std::vector<int>
         for (int f = 0; f < 4; ++f)
             if (nb[f] >= 0) S[(size_t)a * n + nb[f]] = -g[f] * isq[a] * isq[nb[f]];
     }
-    if (!sym_eig(S, n, Q, lam)) {
+    if (!sym_eig_cached(S, n, Q, lam)) {
         set_error("the coarsest level's dense eigendecomposition did not converge");
         return PIC_POISSON_EINVAL;
     }

@@ -10,6 +10,8 @@
 #pragma once
 
 #include <cmath>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 namespace pp {
@@ -110,6 +112,48 @@ inline bool sym_eig(std::vector<double> a, int n, std::vector<double> &q, std::v
         }
     }
     lam = d;
+    return true;
+}
+
+// sym_eig with the last kSymEigKept results kept for the process: the plans
+// of one problem (the autotuner builds one per candidate schedule, a batch
+// may repeat a geometry) factor the same coarsest-level matrix, at about two
+// seconds for n = 800.  A result is reused only for a byte-identical input
+// matrix, so a hit returns exactly what the factorisation would.
+constexpr size_t kSymEigKept = 2;
+
+// Reuses so far (for the tests).
+inline size_t &sym_eig_cache_hits() {
+    static size_t hits = 0;
+    return hits;
+}
+
+inline bool sym_eig_cached(const std::vector<double> &a, int n, std::vector<double> &q, std::vector<double> &lam) {
+    struct Kept {
+        int n;
+        std::vector<double> a, q, lam;
+    };
+    static std::mutex mu;
+    static std::vector<Kept> kept;   // least recently used first
+    const size_t bytes = (size_t)n * n * sizeof(double);
+    if (a.size() != (size_t)n * n) return sym_eig(a, n, q, lam);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (size_t i = 0; i < kept.size(); ++i) {
+            if (kept[i].n != n || (bytes && std::memcmp(kept[i].a.data(), a.data(), bytes) != 0)) continue;
+            q = kept[i].q;
+            lam = kept[i].lam;
+            ++sym_eig_cache_hits();
+            Kept hit = std::move(kept[i]);
+            kept.erase(kept.begin() + (long)i);
+            kept.push_back(std::move(hit));
+            return true;
+        }
+    }
+    if (!sym_eig(a, n, q, lam)) return false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (kept.size() >= kSymEigKept) kept.erase(kept.begin());
+    kept.push_back(Kept{n, a, q, lam});
     return true;
 }
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "../../paper_2609_07172_gb300/csrc/symeig.h"
@@ -99,6 +100,35 @@ int main() {
         report("one", B, 1, &eb);
         std::vector<double> C = {2, 1, 1, 2}, ec = {1, 3};
         report("two", C, 2, &ec);
+    }
+    {   // the memoised solver: the same results, bit for bit, as a fresh
+        // factorisation, for a repeated input, after other inputs, after an
+        // eviction, and for inputs that differ in one bit only
+        const int n = 50;
+        auto random_sym = [&](int seed) {
+            state = 0x9E3779B97F4A7C15ull ^ (uint64_t)seed;
+            std::vector<double> A((size_t)n * n);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j <= i; ++j) A[(size_t)i * n + j] = A[(size_t)j * n + i] = urand();
+            return A;
+        };
+        const std::vector<double> A = random_sym(1), B = random_sym(2), C = random_sym(3);
+        std::vector<double> D = A;
+        D[7 * n + 3] = std::nextafter(D[7 * n + 3], 2.0);   // one ulp off, symmetric
+        D[3 * n + 7] = D[7 * n + 3];
+        auto same = [&](const std::vector<double> &M) {
+            std::vector<double> q0, l0, q1, l1;
+            if (!pp::sym_eig(M, n, q0, l0) || !pp::sym_eig_cached(M, n, q1, l1)) return false;
+            return q0.size() == q1.size() && l0.size() == l1.size() &&
+                   std::memcmp(q0.data(), q1.data(), q0.size() * sizeof(double)) == 0 &&
+                   std::memcmp(l0.data(), l1.data(), l0.size() * sizeof(double)) == 0;
+        };
+        const size_t h0 = pp::sym_eig_cache_hits();
+        const bool ok = same(A) && same(A) && same(B) && same(A) && same(C) && same(B) && same(D) && same(A) &&
+                        same(D);
+        // two kept: hits are A (2nd), A (4th) and D (last); B after C and A
+        // after D were evicted, D is not A
+        printf("cached %s %zu\n", ok ? "ok" : "FAIL", pp::sym_eig_cache_hits() - h0);
     }
     return 0;
 }
